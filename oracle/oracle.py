@@ -1,0 +1,270 @@
+"""Python front end of the FP64 CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+CPU-baseline leg are the only callers.  Nothing here is used by, or uses, the
+CUDA path; inputs arrive as plain arrays or duck-typed camera objects with
+attributes fx, fy, cx, cy, width, height, R (3x3, camera-to-world) and T.
+
+Functions and the passages they follow (RT-GuIDE, arXiv 2409.18122):
+  project      Sec. III projection mu_2D = K R^T (mu - T) / d, d = e3^T R^T (mu - T),
+               generalised to the EWA 2D covariance; FP32 cull/key/rect decisions.
+  render       Sec. III compositing C(p) = sum_i c_i f_i prod_{j<i} (1 - f_j), depth
+               with d_i in place of c_i, uncertainty u_i (Sec. IV-A) likewise.
+  grad         Eq. (2): gradient of a linear functional of the rendered images
+               with respect to every map parameter (chain rule, FP64).
+  info_gain    Eq. (nbv) with the binary-sparsity Jacobian (Sec. IV-A): per-view
+               mean of the composited uncertainty channel.
+  bin_sort     Sec. III "sorted in increasing order of depth": pairs (tile, Gaussian)
+               ordered by (view, tile, depth, record index).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, asdict
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so from oracle.c with gcc (FP contraction off)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               "-shared", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        I64 = ctypes.c_int64
+        I = ctypes.c_int
+        D = ctypes.c_double
+        lib.or_num_threads.restype = I
+        lib.ex32.argtypes = [ctypes.c_float]
+        lib.ex32.restype = ctypes.c_float
+        lib.lg32.argtypes = [ctypes.c_float]
+        lib.lg32.restype = ctypes.c_float
+        lib.or_project.argtypes = [I64, P, P, P, P, P, P, I, P, P, P, P, P, P, P, P, P, P, P]
+        lib.or_project.restype = None
+        lib.or_render.argtypes = [I64, P, P, P, P, P, P, P, I, P, P, P, I64, P, D, P, P, P, P, P, P]
+        lib.or_render.restype = None
+        lib.or_grad.argtypes = [I64, P, P, P, P, P, P, P, I, P, P, P, P, P, P, P, P, P]
+        lib.or_grad.restype = None
+        lib.or_bin_count.argtypes = [I64, P]
+        lib.or_bin_count.restype = I64
+        lib.or_bin.argtypes = [I64, P, P, P, P, P, I64, P, P, P]
+        lib.or_bin.restype = None
+        _lib = lib
+    return _lib
+
+
+def num_threads() -> int:
+    return int(_load().or_num_threads())
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+@dataclass
+class Params:
+    """Rendering constants the paper leaves unstated (readings, see module doc of oracle.c)."""
+    tile_w: int = 16
+    tile_h: int = 16
+    eps2d: float = 0.3
+    near: float = 0.2
+    guard: float = 1.3
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    T_min: float = 1e-4
+
+    def block(self) -> np.ndarray:
+        # values pass through float32 exactly as the GPU receives them
+        f = lambda x: float(np.float32(x))
+        return np.array([self.tile_w, self.tile_h, f(self.eps2d), f(self.near), f(self.guard),
+                         f(self.alpha_min), f(self.alpha_max), f(self.T_min)], np.float64)
+
+
+def smooth_params(**kw) -> Params:
+    """No discrete events: no skip, no stop, no clamp (for finite differences)."""
+    p = Params(alpha_min=0.0, alpha_max=1.0, T_min=0.0)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _cams(cams):
+    V = len(cams)
+    cf = np.zeros((V, 16), np.float32)
+    wh = np.zeros((V, 2), np.int32)
+    for v, c in enumerate(cams):
+        cf[v, 0:4] = [c.fx, c.fy, c.cx, c.cy]
+        cf[v, 4:13] = np.asarray(c.R, np.float32).reshape(9)
+        cf[v, 13:16] = np.asarray(c.T, np.float32).reshape(3)
+        wh[v] = [c.width, c.height]
+    return cf, wh
+
+
+def _map(gmap, values=None):
+    """FP32 arrays (decisions) and FP64 arrays (values; defaults to the FP32 ones promoted)."""
+    m32 = [np.ascontiguousarray(a, np.float32) for a in (gmap.mo, gmap.su, gmap.q, gmap.rgb)]
+    if values is None:
+        m64 = [a.astype(np.float64) for a in m32]
+    else:
+        m64 = [np.ascontiguousarray(a, np.float64) for a in values]
+    return m32, m64
+
+
+def project(gmap, cams, params: Params = Params()):
+    """Dense [V, N] projection: visibility, depth key bits, tile rect and FP64 values."""
+    lib = _load()
+    (mo, su, q, rgb), (mo64, su64, q64, _) = _map(gmap)
+    N, V = mo.shape[0], len(cams)
+    cf, wh = _cams(cams)
+    prm = params.block()
+    out = dict(vis=np.zeros((V, N), np.int8), dkey=np.zeros((V, N), np.uint32), rect=np.zeros((V, N, 4), np.int32),
+               mean2d=np.zeros((V, N, 2)), conic=np.zeros((V, N, 3)), cov2d=np.zeros((V, N, 3)),
+               depth=np.zeros((V, N)), opac=np.zeros((V, N)))
+    lib.or_project(N, _p(mo), _p(su), _p(q), _p(mo64), _p(su64), _p(q64), V, _p(cf), _p(wh), _p(prm),
+                   _p(out["vis"]), _p(out["dkey"]), _p(out["rect"]), _p(out["mean2d"]), _p(out["conic"]),
+                   _p(out["cov2d"]), _p(out["depth"]), _p(out["opac"]))
+    return out
+
+
+def all_pixels(cams, views=None) -> np.ndarray:
+    views = range(len(cams)) if views is None else views
+    chunks = []
+    for v in views:
+        W, H = cams[v].width, cams[v].height
+        vv, uu = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+        chunks.append(np.stack([np.full(W * H, v), uu.ravel(), vv.ravel()], axis=1))
+    return np.ascontiguousarray(np.concatenate(chunks), np.int32) if chunks else np.zeros((0, 3), np.int32)
+
+
+def render(gmap, cams, params: Params = Params(), pixels=None, delta: float = 1e-3, values=None):
+    """Brute-force compositing of the listed pixels (K x 3: view, u, v); all pixels if None.
+
+    Returns dict with rgb [K,3], depth [K], unc [K], T [K], last_id [K], n_contrib [K],
+    n_clamp [K], knife [K] (1 where a skip/stop decision lies within relative `delta`
+    of its threshold).  `values` optionally overrides the FP64 parameter values
+    (mo, su, q, rgb) while decisions keep using gmap's FP32 values.
+    """
+    lib = _load()
+    (mo, su, q, rgb), (mo64, su64, q64, rgb64) = _map(gmap, values)
+    pix = all_pixels(cams) if pixels is None else np.ascontiguousarray(pixels, np.int32)
+    K = pix.shape[0]
+    cf, wh = _cams(cams)
+    prm = params.block()
+    out = np.zeros((K, 5))
+    T = np.zeros(K)
+    last = np.zeros(K, np.int64)
+    nc = np.zeros(K, np.int32)
+    ncl = np.zeros(K, np.int32)
+    kn = np.zeros(K, np.int8)
+    lib.or_render(mo.shape[0], _p(mo), _p(su), _p(q), _p(mo64), _p(su64), _p(q64), _p(rgb64), len(cams), _p(cf),
+                  _p(wh), _p(prm), K, _p(pix), float(delta), _p(out), _p(T), _p(last), _p(nc), _p(ncl), _p(kn))
+    return dict(rgb=out[:, :3], depth=out[:, 3], unc=out[:, 4], T=T, last_id=last, n_contrib=nc, n_clamp=ncl,
+                knife=kn.astype(bool), pixels=pix)
+
+
+def render_images(gmap, cams, params: Params = Params(), delta: float = 1e-3, values=None):
+    """Full images per view: list of dicts with [H, W(, 3)] arrays."""
+    r = render(gmap, cams, params, None, delta, values)
+    res, off = [], 0
+    for c in cams:
+        n = c.width * c.height
+        sl = slice(off, off + n)
+        shp = (c.height, c.width)
+        res.append(dict(rgb=r["rgb"][sl].reshape(shp + (3,)), depth=r["depth"][sl].reshape(shp),
+                        unc=r["unc"][sl].reshape(shp), T=r["T"][sl].reshape(shp),
+                        last_id=r["last_id"][sl].reshape(shp), n_contrib=r["n_contrib"][sl].reshape(shp),
+                        n_clamp=r["n_clamp"][sl].reshape(shp), knife=r["knife"][sl].reshape(shp)))
+        off += n
+    return res
+
+
+def info_gain(gmap, cams, params: Params = Params()):
+    """Per-view mean of the composited uncertainty channel, and the images it came from."""
+    imgs = render_images(gmap, cams, params)
+    return np.array([im["unc"].mean() for im in imgs]), imgs
+
+
+def grad(gmap, cams, dimg, params: Params = Params(), values=None, want_2d: bool = False):
+    """Analytic FP64 gradient of L = sum_views sum_pixels <dimg, (R, G, B, depth)>.
+
+    dimg: list (one per view) of [H, W, 4] arrays.  Returns dict of [N, 4] arrays
+    dmo (mu, logit), dsu (log-scales, 0), dq (quaternion), drgb (colour, 0) and, if
+    want_2d, g2d [V, N, 8] = (dmean_x, dmean_y, dconic_a, dconic_b, dconic_c,
+    dopacity, ddepth, 0) per view.
+    """
+    lib = _load()
+    (mo, su, q, rgb), (mo64, su64, q64, rgb64) = _map(gmap, values)
+    N = mo.shape[0]
+    cf, wh = _cams(cams)
+    prm = params.block()
+    d = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).reshape(-1, 4) for x in dimg]))
+    assert d.shape[0] == sum(c.width * c.height for c in cams)
+    out = {k: np.zeros((N, 4)) for k in ("dmo", "dsu", "dq", "drgb")}
+    g2d = np.zeros((len(cams), N, 8)) if want_2d else None
+    lib.or_grad(N, _p(mo), _p(su), _p(q), _p(mo64), _p(su64), _p(q64), _p(rgb64), len(cams), _p(cf), _p(wh),
+                _p(prm), _p(d), _p(out["dmo"]), _p(out["dsu"]), _p(out["dq"]), _p(out["drgb"]),
+                _p(g2d) if want_2d else None)
+    if want_2d:
+        out["g2d"] = g2d
+    return out
+
+
+def tile_grid(cams, params: Params = Params()):
+    """tiles_x per view and global tile base offsets (length V+1)."""
+    tx = np.array([-(-c.width // params.tile_w) for c in cams], np.int32)
+    ty = np.array([-(-c.height // params.tile_h) for c in cams], np.int32)
+    base = np.zeros(len(cams) + 1, np.int64)
+    base[1:] = np.cumsum(tx.astype(np.int64) * ty)
+    return tx, base
+
+
+def records_from_projection(proj):
+    """Visible (view, gaussian) entries as records in (gaussian id, view) order."""
+    vis = proj["vis"].astype(bool)           # [V, N]
+    g_idx, v_idx = np.nonzero(vis.T)          # row-major over (N, V): gaussian-major
+    return dict(gid=g_idx.astype(np.uint32), view=v_idx.astype(np.uint32),
+                rect=np.ascontiguousarray(proj["rect"][v_idx, g_idx]).astype(np.int32),
+                dkey=np.ascontiguousarray(proj["dkey"][v_idx, g_idx]).astype(np.uint32))
+
+
+def bin_sort(records, cams, params: Params = Params()):
+    """Sorted pair list: keys u64 ((global tile << 32) | depth bits), vals (record index), ranges [T, 2]."""
+    lib = _load()
+    view = np.ascontiguousarray(records["view"], np.uint32)
+    rect = np.ascontiguousarray(records["rect"], np.int32)
+    dkey = np.ascontiguousarray(records["dkey"], np.uint32)
+    R = view.shape[0]
+    tx, base = tile_grid(cams, params)
+    total = int(base[-1])
+    P = int(lib.or_bin_count(R, _p(rect)))
+    keys = np.zeros(P, np.uint64)
+    vals = np.zeros(P, np.uint32)
+    ranges = np.zeros((total, 2), np.int64)
+    lib.or_bin(R, _p(view), _p(rect), _p(dkey), _p(tx), _p(base), total, _p(keys), _p(vals), _p(ranges))
+    return dict(keys=keys, vals=vals, ranges=ranges, n_pairs=P, tile_base=base, tiles_x=tx)
+
+
+def ex32(x: float) -> np.float32:
+    return np.float32(_load().ex32(float(x)))
+
+
+def lg32(x: float) -> np.float32:
+    return np.float32(_load().lg32(float(x)))

@@ -1,0 +1,389 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a closed form,
+a library routine, brute force, an invariant or finite differences.  Equation
+references are to RT-GuIDE (arXiv 2409.18122), Sec. III "Gaussian Splatting"
+(projection and compositing) and Eq. (2) (mapping by back-propagation).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+from oracle import oracle as O
+from paper_2409_18122_gb300.scenes import Camera, GaussianMap, random_scene
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def gmap_from(mu, ls, q, logit, rgb, u):
+    n = len(mu)
+    mo = np.zeros((n, 4), np.float32)
+    mo[:, :3] = mu
+    mo[:, 3] = logit
+    su = np.zeros((n, 4), np.float32)
+    su[:, :3] = ls
+    su[:, 3] = u
+    c = np.zeros((n, 4), np.float32)
+    c[:, :3] = rgb
+    return GaussianMap(mo, su, np.asarray(q, np.float32), c)
+
+
+def sig(x):
+    return 1.0 / (1.0 + math.exp(-float(np.float32(x))))
+
+
+AMAX = float(np.float32(0.99))      # rendering constants reach both implementations as float32
+AMIN = float(np.float32(1 / 255))
+
+
+CAM = Camera(128.0, 128.0, 64.0, 48.0, 128, 96)   # f = 128 so pixel centres are dyadic ray slopes
+NOEPS = O.Params(eps2d=0.0)
+
+
+def on_pixel(u, v, tz, cam=CAM):
+    """World point (camera at origin, R = I) that projects exactly onto pixel centre (u+.5, v+.5)."""
+    return [(u + 0.5 - cam.cx) / cam.fx * tz, (v + 0.5 - cam.cy) / cam.fy * tz, tz]
+
+
+# ----------------------------------------------------------------------------- exp / log
+def test_ex32_lg32_against_libm():
+    xs = np.linspace(-80, 80, 20001, dtype=np.float32)
+    ex = np.array([O.ex32(x) for x in xs[::7]], np.float64)
+    ref = np.exp(xs[::7].astype(np.float64))
+    assert np.max(np.abs(ex / ref - 1)) < 3e-7          # ~2.5 ulp of float32
+    ys = np.exp(np.linspace(-20, 20, 4001)).astype(np.float32)
+    lg = np.array([O.lg32(y) for y in ys], np.float64)
+    ref = np.log(ys.astype(np.float64))
+    err = np.abs(lg - ref) / np.maximum(np.abs(ref), 1.0)
+    assert err.max() < 3e-7
+
+
+# ----------------------------------------------------------------------------- lone Gaussian
+@pytest.mark.parametrize("logit", [0.3, 6.0])      # below and above the 0.99 opacity clamp
+def test_lone_gaussian_at_its_centre(logit):
+    u0, v0, tz = 40, 30, 2.0
+    g = gmap_from([on_pixel(u0, v0, tz)], [[-2.5, -2.0, -2.2]], [[0.9, 0.1, -0.3, 0.2]], [logit],
+                  [[0.2, 0.5, 0.9]], [0.7])
+    r = O.render(g, [CAM], O.Params(), pixels=[[0, u0, v0]])
+    a = min(AMAX, sig(logit))
+    np.testing.assert_allclose(r["rgb"][0], a * np.float32([0.2, 0.5, 0.9]).astype(float), rtol=1e-12)
+    np.testing.assert_allclose(r["depth"][0], a * tz, rtol=1e-12)
+    np.testing.assert_allclose(r["unc"][0], a * float(np.float32(0.7)), rtol=1e-12)
+    np.testing.assert_allclose(r["T"][0], 1 - a, rtol=1e-12)
+    assert r["last_id"][0] == 0 and r["n_contrib"][0] == 1
+
+
+def test_off_centre_axis_aligned_falloff():
+    """Axis-aligned Gaussian on the optical axis: Sigma_2D = (f/d)^2 diag(sx^2, sy^2) + eps I."""
+    ls = np.float32([-2.0, -2.6, -1.9])
+    tz, logit = 3.0, 0.4
+    g = gmap_from([[0.0, 0.0, tz]], [ls], [[1, 0, 0, 0]], [logit], [[1, 1, 1]], [1.0])
+    p = O.Params()
+    eps = float(np.float32(p.eps2d))
+    s = np.exp(ls.astype(np.float64))
+    sxx = (CAM.fx / tz) ** 2 * s[0] ** 2 + eps
+    syy = (CAM.fy / tz) ** 2 * s[1] ** 2 + eps
+    pix = np.array([[0, 64 + du, 48 + dv] for du in (-9, -3, 0, 2, 7) for dv in (-5, 0, 4)], np.int32)
+    r = O.render(g, [CAM], p, pixels=pix)
+    dx = pix[:, 1] + 0.5 - 64.0
+    dy = pix[:, 2] + 0.5 - 48.0
+    a = sig(logit) * np.exp(-0.5 * (dx ** 2 / sxx + dy ** 2 / syy))
+    a = np.where(a < AMIN, 0.0, np.minimum(a, AMAX))
+    np.testing.assert_allclose(r["unc"], a, rtol=1e-12, atol=1e-15)
+
+
+def test_ewa_off_axis_closed_form():
+    """Off-axis axis-aligned Gaussian: J has the -f t_x / t_z^2 term (2D covariance in closed form)."""
+    ls = np.float32([-2.2, -2.4, -1.6])
+    tx, tz = 0.75, 2.5
+    g = gmap_from([[tx, 0.0, tz]], [ls], [[1, 0, 0, 0]], [1.0], [[1, 1, 1]], [1.0])
+    pr = O.project(g, [CAM], NOEPS)
+    s2 = np.exp(2 * ls.astype(np.float64))
+    f = CAM.fx
+    sxx = (f / tz) ** 2 * s2[0] + (f * tx / tz ** 2) ** 2 * s2[2]
+    syy = (f / tz) ** 2 * s2[1]
+    np.testing.assert_allclose(pr["cov2d"][0, 0], [sxx, 0.0, syy], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(pr["mean2d"][0, 0], [f * tx / tz + CAM.cx, CAM.cy], rtol=1e-14)
+
+
+def test_paper_isotropic_formula_on_axis():
+    """Sec. III: f_i(p) = alpha exp(-|p - mu_2D|^2 / (2 r_2D^2)), r_2D = f r / d (isotropic, on axis, no dilation)."""
+    r_world, tz, logit = 0.04, 2.0, -0.2
+    lr = float(np.float32(math.log(r_world)))
+    g = gmap_from([[0.0, 0.0, tz]], [[lr, lr, lr]], [[0.3, 0.5, -0.1, 0.8]], [logit], [[1, 1, 1]], [1.0])
+    pix = np.array([[0, 64 + du, 48 + dv] for du in range(-6, 6) for dv in range(-6, 6)], np.int32)
+    r = O.render(g, [CAM], NOEPS, pixels=pix)
+    r2d = CAM.fx * math.exp(lr) / tz
+    d2 = (pix[:, 1] + 0.5 - 64.0) ** 2 + (pix[:, 2] + 0.5 - 48.0) ** 2
+    f = sig(logit) * np.exp(-d2 / (2 * r2d ** 2))
+    f = np.where(f < AMIN, 0.0, f)
+    np.testing.assert_allclose(r["unc"], f, rtol=1e-11, atol=1e-15)
+
+
+# ----------------------------------------------------------------------------- several Gaussians
+def test_three_gaussians_hand_expanded_front_to_back():
+    u0, v0 = 70, 50
+    depths = [3.0, 2.0, 4.0]                       # ids are not in depth order
+    logits = [0.5, -0.3, 1.2]
+    cols = [[0.9, 0.1, 0.2], [0.3, 0.8, 0.4], [0.1, 0.2, 0.95]]
+    us = [0.25, 0.5, 0.75]
+    g = gmap_from([on_pixel(u0, v0, d) for d in depths], [[-2.3, -2.3, -2.3]] * 3, [[1, 0, 0, 0]] * 3,
+                  logits, cols, us)
+    r = O.render(g, [CAM], O.Params(), pixels=[[0, u0, v0]])
+    a = [sig(l) for l in logits]
+    c = np.float32(cols).astype(float)
+    order = [1, 0, 2]                              # by depth
+    T, rgb, dep, unc = 1.0, np.zeros(3), 0.0, 0.0
+    for i in order:
+        rgb += a[i] * T * c[i]
+        dep += a[i] * T * depths[i]
+        unc += a[i] * T * float(np.float32(us[i]))
+        T *= 1 - a[i]
+    np.testing.assert_allclose(r["rgb"][0], rgb, rtol=1e-12)
+    np.testing.assert_allclose(r["depth"][0], dep, rtol=1e-12)
+    np.testing.assert_allclose(r["unc"][0], unc, rtol=1e-12)
+    np.testing.assert_allclose(r["T"][0], T, rtol=1e-12)
+    assert r["last_id"][0] == 2 and r["n_contrib"][0] == 3
+
+
+def test_equal_depth_ties_break_by_id():
+    u0, v0 = 20, 20
+    g = gmap_from([on_pixel(u0, v0, 2.0)] * 2, [[-2.3] * 3] * 2, [[1, 0, 0, 0]] * 2, [0.0, 0.0],
+                  [[1, 0, 0], [0, 1, 0]], [0, 0])
+    r = O.render(g, [CAM], O.Params(), pixels=[[0, u0, v0]])
+    np.testing.assert_allclose(r["rgb"][0], [0.5, 0.25, 0.0], rtol=1e-12)   # id 0 in front
+
+
+def test_termination_before_sixth_layer():
+    """alpha = 0.8 layers: T after 5 = 0.2^5 = 3.2e-4 >= 1e-4 > 0.2^6, so layer 6 is never added."""
+    u0, v0 = 60, 40
+    n = 8
+    logit = float(np.float32(math.log(4.0)))       # sigmoid = 0.8
+    cols = np.random.default_rng(0).uniform(size=(n, 3))
+    g = gmap_from([on_pixel(u0, v0, 1.0 + 0.5 * k) for k in range(n)], [[-2.0] * 3] * n, [[1, 0, 0, 0]] * n,
+                  [logit] * n, cols, [1.0] * n)
+    r = O.render(g, [CAM], O.Params(), pixels=[[0, u0, v0]])
+    a = sig(logit)
+    assert r["n_contrib"][0] == 5 and r["last_id"][0] == 4
+    np.testing.assert_allclose(r["T"][0], (1 - a) ** 5, rtol=1e-12)
+    c = np.float32(cols).astype(float)
+    exp_rgb = sum(a * (1 - a) ** k * c[k] for k in range(5))
+    np.testing.assert_allclose(r["rgb"][0], exp_rgb, rtol=1e-12)
+
+
+def test_weights_plus_transmittance_is_one():
+    """Constant colour k gives k (1 - T); all Gaussians at depth z give z (1 - T)."""
+    cam = Camera(40.0, 40.0, 24.0, 16.0, 48, 32)
+    g = random_scene(5, 300, [cam])
+    g.rgb[:, :3] = 0.625
+    g.su[:, 3] = 1.0
+    g.mo[:, 2] = 2.75
+    im = O.render_images(g, [cam])[0]
+    assert (im["n_contrib"] > 0).mean() > 0.5
+    np.testing.assert_allclose(im["rgb"], np.repeat(0.625 * (1 - im["T"])[..., None], 3, axis=2), atol=1e-12)
+    np.testing.assert_allclose(im["unc"], 1 - im["T"], atol=1e-12)
+    np.testing.assert_allclose(im["depth"], 2.75 * (1 - im["T"]), atol=1e-11)
+    ig, _ = O.info_gain(g, [cam])
+    np.testing.assert_allclose(ig[0], np.mean(1 - im["T"]), rtol=1e-12)
+
+
+# ----------------------------------------------------------------------------- projection vs libraries
+def test_projection_against_scipy_rotation_and_numeric_jacobian():
+    rng = np.random.default_rng(3)
+    cam_R = Rotation.from_euler("xyz", [0.2, -0.4, 0.3]).as_matrix()
+    cam_T = np.array([0.3, -0.2, -1.0])
+    cam = Camera(300.0, 280.0, 160.0, 120.0, 320, 240, cam_R, cam_T)
+    n = 64
+    t_cam = np.stack([rng.uniform(-0.8, 0.8, n), rng.uniform(-0.6, 0.6, n), rng.uniform(2, 6, n)], 1)
+    mu = (cam.R.astype(float) @ t_cam.T).T + cam.T.astype(float)
+    q = rng.normal(size=(n, 4))
+    ls = rng.normal(-3, 0.5, size=(n, 3))
+    g = gmap_from(mu, ls, q, rng.normal(size=n) + 1.0, rng.uniform(size=(n, 3)), rng.uniform(size=n))
+    p = O.Params()
+    pr = O.project(g, [cam], p)
+    assert pr["vis"].all()
+    R = cam.R.astype(float)
+    T = cam.T.astype(float)
+    K = np.array([[cam.fx, 0, cam.cx], [0, cam.fy, cam.cy], [0, 0, 1.0]])
+    eps = float(np.float32(p.eps2d))
+    for i in range(n):
+        m = g.mo[i, :3].astype(float)
+        t = R.T @ (m - T)
+        uvw = K @ t
+        np.testing.assert_allclose(pr["mean2d"][0, i], uvw[:2] / uvw[2], rtol=1e-12)
+        np.testing.assert_allclose(pr["depth"][0, i], t[2], rtol=1e-12)
+        qq = g.q[i].astype(float)
+        Rq = Rotation.from_quat([qq[1], qq[2], qq[3], qq[0]]).as_matrix()   # scipy is scalar-last
+        S3 = Rq @ np.diag(np.exp(2 * g.su[i, :3].astype(float))) @ Rq.T
+        proj = lambda tt: np.array([cam.fx * tt[0] / tt[2] + cam.cx, cam.fy * tt[1] / tt[2] + cam.cy])
+        h = 1e-6
+        J = np.stack([(proj(t + h * e) - proj(t - h * e)) / (2 * h) for e in np.eye(3)], 1)
+        C2 = J @ R.T @ S3 @ R @ J.T + eps * np.eye(2)
+        np.testing.assert_allclose(pr["cov2d"][0, i], [C2[0, 0], C2[0, 1], C2[1, 1]], rtol=1e-7,
+                                   atol=1e-7 * abs(C2).max())
+        conic = pr["conic"][0, i]
+        Cm = np.array([[conic[0], conic[1]], [conic[1], conic[2]]])
+        Sm = np.array([[pr["cov2d"][0, i, 0], pr["cov2d"][0, i, 1]], [pr["cov2d"][0, i, 1], pr["cov2d"][0, i, 2]]])
+        np.testing.assert_allclose(Cm @ Sm, np.eye(2), atol=1e-12)
+
+
+def test_support_rect_covers_every_pixel_above_alpha_min():
+    """The FP32 tile rectangle contains every pixel whose FP64 alpha clears the skip threshold."""
+    cam = Camera(60.0, 60.0, 40.0, 30.0, 80, 60)
+    g = random_scene(11, 400, [cam], box=((-2, -1.5, 0.5), (2, 1.5, 4)), log_scale=(-2.5, 0.7))
+    p = O.Params(tile_w=8, tile_h=8)
+    pr = O.project(g, [cam], p)
+    vv, uu = np.meshgrid(np.arange(cam.height) + 0.5, np.arange(cam.width) + 0.5, indexing="ij")
+    amin = float(np.float32(p.alpha_min))
+    checked = 0
+    for i in np.nonzero(pr["vis"][0])[0]:
+        mx, my = pr["mean2d"][0, i]
+        a, b, c = pr["conic"][0, i]
+        dx, dy = uu - mx, vv - my
+        al = pr["opac"][0, i] * np.exp(-0.5 * (a * dx * dx + 2 * b * dx * dy + c * dy * dy))
+        ys, xs = np.nonzero(al >= amin * (1 + 1e-5))
+        x0, y0, x1, y1 = pr["rect"][0, i]
+        if len(xs):
+            checked += 1
+            assert (xs // 8 >= x0).all() and (xs // 8 < x1).all() and (ys // 8 >= y0).all() and (ys // 8 < y1).all()
+    assert checked > 100
+
+
+def test_opacity_floor_and_near_plane():
+    cam = Camera(60.0, 60.0, 40.5, 30.5, 80, 60)     # the Gaussians sit exactly on a pixel centre
+    n = 200
+    logit = np.linspace(-5.6, -5.47, n)             # straddles -ln 254
+    g = gmap_from([[0, 0, 2.0]] * n, [[-2.0] * 3] * n, [[1, 0, 0, 0]] * n, logit, [[1, 1, 1]] * n, [1] * n)
+    pr = O.project(g, [cam])
+    o = 1 / (1 + np.exp(-g.mo[:, 3].astype(float)))
+    far = np.abs(o * 255 - 1) > 1e-5
+    np.testing.assert_array_equal(pr["vis"][0].astype(bool)[far], (o * 255 >= 1)[far])
+    z = np.float32([0.1, 0.2, 0.2000001, 0.3])
+    g2 = gmap_from([[0, 0, zz] for zz in z], [[-4.0] * 3] * 4, [[1, 0, 0, 0]] * 4, [3.0] * 4, [[1, 1, 1]] * 4, [1] * 4)
+    np.testing.assert_array_equal(O.project(g2, [cam])["vis"][0], [0, 0, 1, 1])
+
+
+# ----------------------------------------------------------------------------- binning / sort
+def test_bin_sort_against_brute_force():
+    from paper_2409_18122_gb300.scenes import synthetic_records
+    cams = [Camera(50, 50, 20, 20, 40, 40), Camera(50, 50, 40, 30, 80, 56), Camera(50, 50, 8, 8, 16, 16)]
+    rec = synthetic_records(4, 60, cams, tile_w=16, tile_h=16, max_extent=4, tie_frac=0.3)
+    rec["dkey"] = rec["depth"].view(np.uint32)
+    b = O.bin_sort(rec, cams)
+    tx, base = O.tile_grid(cams)
+    pairs = []
+    for r in range(len(rec["gid"])):
+        v = int(rec["view"][r])
+        x0, y0, x1, y1 = rec["rect"][r]
+        for y in range(y0, y1):
+            for x in range(x0, x1):
+                gt = int(base[v]) + y * int(tx[v]) + x
+                pairs.append((gt, float(rec["depth"][r]), r))
+    pairs.sort()
+    assert b["n_pairs"] == len(pairs)
+    np.testing.assert_array_equal(b["vals"], [p[2] for p in pairs])
+    np.testing.assert_array_equal(b["keys"] >> np.uint64(32), [p[0] for p in pairs])
+    np.testing.assert_array_equal((b["keys"] & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32),
+                                  np.float32([p[1] for p in pairs]))
+    for t in range(int(base[-1])):
+        idx = [i for i, p in enumerate(pairs) if p[0] == t]
+        if idx:
+            assert tuple(b["ranges"][t]) == (idx[0], idx[-1] + 1)
+        else:
+            assert tuple(b["ranges"][t]) == (0, 0)
+
+
+def test_depth_key_bits_are_monotone():
+    d = np.sort(np.random.default_rng(1).uniform(0.2, 100.0, 10000).astype(np.float32))
+    k = d.view(np.uint32)
+    assert (np.diff(k.astype(np.int64)) >= 0).all()
+
+
+# ----------------------------------------------------------------------------- gradients
+def _loss(g, cams, dimg, params, values):
+    imgs = O.render_images(g, cams, params, values=values)
+    L = 0.0
+    for im, d in zip(imgs, dimg):
+        L += np.sum(im["rgb"] * d[..., :3]) + np.sum(im["depth"] * d[..., 3])
+    return L, [(im["n_contrib"].copy(), im["n_clamp"].copy()) for im in imgs]
+
+
+def _fd_check(g, cams, params, seed, rtol, n_param_max=None):
+    rng = np.random.default_rng(seed)
+    dimg = [rng.normal(size=(c.height, c.width, 4)) for c in cams]
+    an = O.grad(g, cams, dimg, params)
+    base = [a.astype(np.float64) for a in (g.mo, g.su, g.q, g.rgb)]
+    names = [("dmo", 0, range(4)), ("dsu", 1, range(3)), ("dq", 2, range(4)), ("drgb", 3, range(3))]
+    checked = skipped = 0
+    worst = 0.0
+    scale = {k: max(np.abs(an[k]).max(), 1e-30) for k, _, _ in names}
+    for key, ai, comps in names:
+        for i in range(g.n):
+            for c in comps:
+                th = base[ai][i, c]
+                h = 1e-6 * max(1.0, abs(th))
+                vals_p = [b.copy() for b in base]
+                vals_m = [b.copy() for b in base]
+                vals_p[ai][i, c] += h
+                vals_m[ai][i, c] -= h
+                Lp, ep = _loss(g, cams, dimg, params, vals_p)
+                Lm, em = _loss(g, cams, dimg, params, vals_m)
+                if any((a[0] != b[0]).any() or (a[1] != b[1]).any() for a, b in zip(ep, em)):
+                    skipped += 1
+                    continue
+                fd = (Lp - Lm) / (2 * h)
+                a = an[key][i, c]
+                err = abs(fd - a) / max(abs(a), 1e-3 * scale[key])
+                worst = max(worst, err)
+                assert err < rtol, (key, i, c, fd, a)
+                checked += 1
+    return checked, skipped, worst
+
+
+def test_gradient_matches_finite_differences_standard_rules():
+    cams = [Camera(30.0, 30.0, 16.0, 12.0, 32, 24),
+            Camera(30.0, 30.0, 16.0, 12.0, 32, 24, Rotation.from_euler("y", 0.3).as_matrix(), [-0.5, 0.1, 0.2])]
+    g = random_scene(21, 14, cams, box=((-1, -0.8, 2), (1, 0.8, 4)), log_scale=(-2.0, 0.3))
+    checked, skipped, worst = _fd_check(g, cams, O.Params(), 7, 1e-5)
+    assert checked > 0.8 * (checked + skipped) and checked > 100
+
+
+def test_gradient_matches_finite_differences_smooth_rules():
+    cams = [Camera(30.0, 30.0, 16.0, 12.0, 32, 24)]
+    g = random_scene(22, 10, cams, box=((-1, -0.8, 2), (1, 0.8, 4)), log_scale=(-2.0, 0.3))
+    checked, skipped, worst = _fd_check(g, cams, O.smooth_params(), 8, 1e-5)
+    assert skipped == 0 and checked == 14 * 10
+
+
+def test_gradient_colour_is_blend_weight():
+    """dC/dc_i = w_i = alpha_i T_i: two Gaussians on one pixel centre."""
+    u0, v0 = 30, 20
+    logits = [0.2, -0.4]
+    g = gmap_from([on_pixel(u0, v0, 2.0), on_pixel(u0, v0, 3.0)], [[-2.2] * 3] * 2, [[1, 0, 0, 0]] * 2, logits,
+                  [[0.3, 0.3, 0.3]] * 2, [0, 0])
+    d = np.zeros((CAM.height, CAM.width, 4))
+    d[v0, u0, 0] = 1.0
+    gr = O.grad(g, [CAM], [d])
+    a0, a1 = sig(logits[0]), sig(logits[1])
+    np.testing.assert_allclose(gr["drgb"][:, 0], [a0, (1 - a0) * a1], rtol=1e-12)
+    np.testing.assert_allclose(gr["drgb"][:, 1:], 0)
+
+
+def test_gradient_opacity_single_gaussian():
+    """Below the clamp: dC/do = exp(-q/2) c, so dC/dlogit = exp(-q/2) c o (1 - o)."""
+    logit, col = 0.1, 0.6
+    g = gmap_from([[0.0, 0.0, 2.5]], [[-2.0, -2.3, -2.1]], [[0.8, 0.2, 0.1, -0.3]], [logit], [[col, 0, 0]], [0])
+    pix = (70, 45)
+    d = np.zeros((CAM.height, CAM.width, 4))
+    d[pix[1], pix[0], 0] = 1.0
+    pr = O.project(g, [CAM])
+    mx, my = pr["mean2d"][0, 0]
+    a, b, c = pr["conic"][0, 0]
+    dx, dy = pix[0] + 0.5 - mx, pix[1] + 0.5 - my
+    G = math.exp(-0.5 * (a * dx * dx + 2 * b * dx * dy + c * dy * dy))
+    o = sig(logit)
+    assert o * G > 1 / 255
+    gr = O.grad(g, [CAM], [d])
+    np.testing.assert_allclose(gr["dmo"][0, 3], G * float(np.float32(col)) * o * (1 - o), rtol=1e-12)
