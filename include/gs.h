@@ -1,0 +1,286 @@
+/*
+ * gs.h -- C ABI of the GB300 tile-based Gaussian-splatting library (libgs103.so).
+ *
+ * The operations follow RT-GuIDE (arXiv 2409.18122):
+ *   Sec. III "Gaussian Splatting": Gaussians are sorted by increasing depth
+ *     relative to the camera pose and splatted onto the image plane with
+ *     mu_2D = K R^T (mu - T) / d, d = e3^T R^T (mu - T); pixel colour
+ *     C(p) = sum_i c_i f_i(p) prod_{j<i} (1 - f_j(p)); depth by replacing c_i with d_i.
+ *   Eq. (2): the map is the minimiser of the rendering loss over the keyframes,
+ *     refined by back-propagation (Sec. IV-A).
+ *   Eq. (nbv) and Sec. IV-A: information gain of a candidate view scored from the
+ *     per-Gaussian uncertainty u_i = |mu_k - mu_{k-1}| of the Gaussians it sees.
+ *
+ * Conventions shared by every entry point
+ *   - All array pointers are DEVICE pointers owned by the caller (e.g. PyTorch
+ *     tensors), except where a comment says HOST.  The library never allocates
+ *     device memory, never synchronises the stream and never prints; every
+ *     entry point only enqueues kernels on `stream` (a cudaStream_t passed as
+ *     void*, NULL = legacy default stream), so a sequence of calls can be
+ *     captured into a CUDA graph.
+ *   - Host-detectable argument errors return immediately with a gs_status code
+ *     and enqueue nothing.  Conditions only the device can see (pair or range
+ *     capacity exceeded, a camera with no pixels, non-finite Gaussian
+ *     parameters) are OR-ed as GS_FLAG_* bits into the caller's device status
+ *     word, which gs_read_status reads after the stream has been synchronised.
+ *     Outputs of a call whose status carries GS_FLAG_PAIR_OVERFLOW or
+ *     GS_FLAG_RANGE_OVERFLOW are incomplete and must be discarded.
+ *   - Float4-typed arrays ([n][4] floats) must be 16-byte aligned; all other
+ *     arrays 4-byte aligned; workspaces 256-byte aligned.
+ *   - Rendering constants the paper leaves unstated are fields of gs_params.
+ */
+#ifndef GS103_GS_H
+#define GS103_GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+typedef int32_t gs_status;
+enum {
+  GS_OK = 0,
+  GS_ERR_NULL = 1,          /* a required pointer is NULL                          */
+  GS_ERR_ALIGN = 2,         /* a pointer violates the alignment stated above        */
+  GS_ERR_ARG = 3,           /* a count, size or parameter is out of range           */
+  GS_ERR_WORKSPACE = 4,     /* workspace smaller than gs_workspace_size reports     */
+  GS_ERR_CUDA = 5,          /* a CUDA runtime call or kernel launch failed          */
+  GS_ERR_DEVICE = 6         /* the device status word carries an error flag          */
+};
+
+/* device status word bits */
+enum {
+  GS_FLAG_PAIR_OVERFLOW = 1u << 0,   /* more (tile, Gaussian) pairs than gs_bins.pair_capacity */
+  GS_FLAG_RANGE_OVERFLOW = 1u << 1,  /* more tiles over all views than gs_bins.tile_capacity   */
+  GS_FLAG_BAD_CAMERA = 1u << 2,      /* a camera has width*height <= 0 or non-positive focal   */
+  GS_FLAG_NONFINITE = 1u << 3,       /* informational: Gaussians with non-finite parameters were culled */
+  GS_FLAG_RECORD_OVERFLOW = 1u << 4  /* more visible (Gaussian, view) records than capacity    */
+};
+#define GS_FLAG_ERROR_MASK (GS_FLAG_PAIR_OVERFLOW | GS_FLAG_RANGE_OVERFLOW | GS_FLAG_BAD_CAMERA | GS_FLAG_RECORD_OVERFLOW)
+
+/* ------------------------------------------------------------------ inputs */
+
+/* Pinhole camera (Sec. III: intrinsics K, pose R_k, T_k in the world frame).
+ * R is camera-to-world, row-major; world-to-camera is t = R^T (mu - T).
+ * Axes: x right, y down, z forward.  Pixel (u, v) samples (u + 0.5, v + 0.5).
+ * 72 bytes; arrays of cameras are DEVICE arrays. */
+typedef struct {
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float R[9];
+  float T[3];
+} gs_camera;
+
+/* Gaussian map (Sec. III: colour c, position mu, size, opacity; anisotropic
+ * generalisation with three log-scales and a rotation quaternion; Sec. IV-A:
+ * uncertainty u).  Four DEVICE float arrays of shape [n][4], 16-byte aligned:
+ *   mo  = (mu_x, mu_y, mu_z, opacity logit)   opacity o = 1 / (1 + exp(-logit))
+ *   su  = (log s_0, log s_1, log s_2, u)
+ *   q   = (w, x, y, z)  rotation quaternion, need not be normalised
+ *   rgb = (r, g, b, unused)                                                  */
+typedef struct {
+  const float* mo;
+  const float* su;
+  const float* q;
+  const float* rgb;
+  int64_t n;
+} gs_map;
+
+/* Rendering constants (readings where the paper is silent).
+ *   tile_w, tile_h  screen tile in pixels; tile_w * tile_h in {64,128,256,512,1024}, tile_w <= 64
+ *   eps2d           added to the diagonal of every 2D covariance (low-pass), px^2, >= 0
+ *   near_plane      Gaussians with view depth <= near_plane are culled, > 0
+ *   guard           centres with |t_x / t_z| > guard * (W/2) / f_x (same for y) are culled, > 0
+ *   alpha_min       a Gaussian whose alpha at a pixel is below this is skipped, in [0, 1)
+ *   alpha_max       alpha = min(alpha_max, o * exp(-q/2)), in (0, 1]
+ *   T_min           compositing stops before adding a Gaussian that would take T below this, >= 0
+ * Defaults: 16, 16, 0.3, 0.2, 1.3, 1/255, 0.99, 1e-4. */
+typedef struct {
+  int32_t tile_w, tile_h;
+  float eps2d, near_plane, guard, alpha_min, alpha_max, T_min;
+} gs_params;
+
+/* ------------------------------------------------------------- projection */
+
+/* Projected records, one per visible (Gaussian, view), in ascending
+ * (Gaussian id, view) order.  DEVICE buffers of `capacity` entries; capacity
+ * >= n * n_views never overflows.
+ *   count      [1]        number of records written
+ *   status     [1]        device status word (GS_FLAG_* bits), OR-ed by every call
+ *   view_info  [V+1][2]   per view: (first global tile, first pixel); entry V holds the totals
+ *   gid, view  [cap]      Gaussian index and view index of the record
+ *   xyod       [cap][4]   (mu_2D x, mu_2D y, opacity, depth t_z)
+ *   conic_u    [cap][4]   (inverse 2D covariance a, b, c with q = a dx^2 + 2 b dx dy + c dy^2, u)
+ *   rect       [cap][4]   uint16 tile rectangle (x0, y0, x1, y1), ends exclusive
+ *   depth_key  [cap]      IEEE-754 bits of the float32 depth (the sort key)
+ *   g_first    [n+1]      index of each Gaussian's first record; g_first[n] = count    */
+typedef struct {
+  int64_t capacity;
+  uint32_t* count;
+  uint32_t* status;
+  uint32_t* view_info;
+  uint32_t* gid;
+  uint32_t* view;
+  float* xyod;
+  float* conic_u;
+  uint16_t* rect;
+  uint32_t* depth_key;
+  uint32_t* g_first;
+} gs_proj;
+
+/* gs_project -- EWA projection of every Gaussian into every view (Sec. III
+ * projection, anisotropic generalisation).  Per Gaussian: normalised quaternion
+ * -> rotation, Sigma = R_q diag(exp(2 log s)) R_q^T, o = sigmoid(logit).  Per view:
+ * t = R^T (mu - T); cull if t_z <= near_plane, outside the guard band, or o < alpha_min;
+ * J = [[fx/t_z, 0, -fx t_x/t_z^2], [0, fy/t_z, -fy t_y/t_z^2]];
+ * Sigma_2D = J R^T Sigma R J^T + eps2d I; conic = Sigma_2D^-1 (cull if det <= 0);
+ * mu_2D = (fx t_x/t_z + cx, fy t_y/t_z + cy); support box from
+ * q <= Q = 2 ln(o / alpha_min): half-widths sqrt(Q Sigma_2D,xx), sqrt(Q Sigma_2D,yy),
+ * clipped to the image and converted to tiles (cull if empty).
+ * Records are written to `out` in (Gaussian, view) order.
+ * ws: DEVICE workspace of gs_workspace_size(GS_OP_PROJECT, ...) bytes.
+ * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG (n < 0, n_views < 1,
+ * n >= 2^32, bad params), GS_ERR_WORKSPACE, GS_ERR_CUDA; device flags
+ * GS_FLAG_BAD_CAMERA, GS_FLAG_NONFINITE, GS_FLAG_RECORD_OVERFLOW. */
+gs_status gs_project(const gs_map* map, const gs_camera* cams, int32_t n_views, const gs_params* prm,
+                     gs_proj* out, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------- binning / sort */
+
+/* Tile-sorted pair list.  DEVICE buffers:
+ *   count   [1]               number of (tile, record) pairs P (may exceed capacity: overflow flag)
+ *   tile    [pair_capacity]   global tile id of each pair, ascending
+ *   rec     [pair_capacity]   record index of each pair
+ *   ranges  [tile_capacity][2] per global tile: [start, end) into tile/rec
+ * Global tile id of tile (x, y) of view v = view_info[v].first_tile + y * tiles_x(v) + x,
+ * tiles_x(v) = ceil(W_v / tile_w), tiles_y(v) = ceil(H_v / tile_h). */
+typedef struct {
+  int64_t pair_capacity;
+  int64_t tile_capacity;
+  uint32_t* count;
+  uint32_t* tile;
+  uint32_t* rec;
+  uint32_t* ranges;
+} gs_bins;
+
+/* gs_bin_sort -- Sec. III "sorted in increasing order of depth": emits one pair
+ * per tile covered by each record's rectangle and orders all pairs by
+ * (view, tile, float32 depth, record index) -- bit-exact, deterministic.
+ * Implementation: stable LSD radix sort of the records by depth bits, emission
+ * in that order, stable LSD radix sort of the pairs by global tile id, then
+ * per-tile [start, end) ranges.
+ * ws: DEVICE workspace of gs_workspace_size(GS_OP_BIN_SORT, ...) bytes.
+ * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG, GS_ERR_WORKSPACE, GS_ERR_CUDA;
+ * device flags GS_FLAG_PAIR_OVERFLOW, GS_FLAG_RANGE_OVERFLOW. */
+gs_status gs_bin_sort(const gs_proj* proj, const gs_camera* cams, int32_t n_views, const gs_params* prm,
+                      gs_bins* out, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------- compositing */
+
+/* Rendered images of all views, concatenated: view v starts at pixel
+ * view_info[v].first_pixel (P_v = W_v H_v pixels, row-major).  DEVICE buffers:
+ *   rgb   [sum_v 3 P_v]  planar per view: channel c of view v at 3*first_pixel + c*P_v
+ *   depth [sum_v P_v]    sum_i w_i t_z,i      (Sec. III, c_i replaced by d_i)
+ *   unc   [sum_v P_v]    sum_i w_i u_i        (uncertainty channel)
+ *   T     [sum_v P_v]    final transmittance prod_i (1 - alpha_i)
+ *   last  [sum_v P_v]    1 + position (within the tile's range) of the last Gaussian added, 0 if none
+ * Any of rgb/depth/unc may be NULL to skip writing it; T and last are
+ * required when the images will be differentiated (gs_render_bwd). */
+typedef struct {
+  float* rgb;
+  float* depth;
+  float* unc;
+  float* T;
+  int32_t* last;
+} gs_image;
+
+/* gs_render_fwd -- Sec. III front-to-back compositing.  For every pixel p and
+ * the Gaussians of its tile in depth order: alpha = min(alpha_max, o exp(-q/2)),
+ * skip if alpha < alpha_min, stop (without adding) if T (1 - alpha) < T_min,
+ * else w = alpha T, accumulate w c (RGB), w t_z (depth), w u (uncertainty) and
+ * T <- T (1 - alpha).  Background is zero.
+ * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG, GS_ERR_CUDA. */
+gs_status gs_render_fwd(const gs_map* map, const gs_proj* proj, const gs_bins* bins, const gs_camera* cams,
+                        int32_t n_views, const gs_params* prm, gs_image* out, void* stream);
+
+/* Image-space gradient dL/d(rgb, depth), same layouts as gs_image.rgb / .depth.
+ * Either may be NULL (treated as zero).  The uncertainty channel is not
+ * differentiated: u_i is not a learned parameter. */
+typedef struct {
+  const float* rgb;
+  const float* depth;
+} gs_image_grad;
+
+/* Gradient with respect to every map parameter, DEVICE [n][4] arrays laid out
+ * like gs_map (dmo = (dmu, dlogit), dsu = (dlog s, 0), dq, drgb = (dc, 0)).
+ * Overwritten (not accumulated) by gs_render_bwd. */
+typedef struct {
+  float* dmo;
+  float* dsu;
+  float* dq;
+  float* drgb;
+} gs_map_grad;
+
+/* gs_render_bwd -- Eq. (2): the adjoint of gs_render_fwd and gs_project.
+ * Each tile is replayed back to front from the saved final transmittance and
+ * last index (T_i = T_{i+1} / (1 - alpha_i)), keeping suffix sums
+ * S = sum_{j>i} w_j x_j; dL/dalpha_i = sum_ch g_ch (x_i T_i - S_ch / (1 - alpha_i)).
+ * Screen-space gradients are reduced per Gaussian with warp shuffles before one
+ * atomic add per warp, then mapped through the projection to dmu, dlog s, dq
+ * (through the normalisation), dlogit and dc.  Float atomics make the last bits
+ * of the result depend on scheduling.
+ * ws: DEVICE workspace of gs_workspace_size(GS_OP_RENDER_BWD, ...) bytes.
+ * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG, GS_ERR_WORKSPACE, GS_ERR_CUDA. */
+gs_status gs_render_bwd(const gs_map* map, const gs_proj* proj, const gs_bins* bins, const gs_image* fwd,
+                        const gs_image_grad* grad, const gs_camera* cams, int32_t n_views, const gs_params* prm,
+                        gs_map_grad* out, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------- information gain */
+enum { GS_IG_RENDER_MEAN = 0 };
+
+/* gs_info_gain_batch -- Eq. (nbv) with the Jacobian replaced by the per-pixel
+ * blend weights: IG_v = (1 / P_v) sum_p sum_i w_i(p) u_i, the mean of the
+ * composited uncertainty channel of view v.  All n_views candidate views (of
+ * any mix of resolutions) are projected, sorted and composited together:
+ * projection and sort as gs_project / gs_bin_sort over the whole batch, then
+ * one persistent compositing kernel that takes (view, tile) work items from a
+ * device queue and writes each tile's sum of U to a fixed slot, then a
+ * fixed-order per-view reduction.  Same alpha / skip / stop rules as
+ * gs_render_fwd.  ig_out: DEVICE float[n_views].
+ * status: DEVICE uint32[1] status word (OR-ed).
+ * pair_capacity / tile_capacity: capacities used inside ws (see gs_workspace_size).
+ * Errors: as gs_project and gs_bin_sort. */
+gs_status gs_info_gain_batch(const gs_map* map, const gs_camera* cams, int32_t n_views, const gs_params* prm,
+                             int32_t mode, float* ig_out, uint32_t* status, int64_t pair_capacity,
+                             int64_t tile_capacity, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------- utilities */
+enum { GS_OP_PROJECT = 0, GS_OP_BIN_SORT = 1, GS_OP_RENDER_BWD = 2, GS_OP_INFO_GAIN = 3 };
+
+/* gs_workspace_size -- HOST.  Bytes of workspace `op` needs:
+ *   n, n_views      map size and number of views
+ *   rec_capacity    record capacity of the gs_proj in use (GS_OP_INFO_GAIN: ignored, n * n_views)
+ *   pair_capacity   pair capacity of the gs_bins in use
+ *   tile_capacity   tile capacity of the gs_bins in use
+ * Writes the byte count to *bytes (HOST).  Errors: GS_ERR_NULL, GS_ERR_ARG, GS_ERR_CUDA. */
+gs_status gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t rec_capacity, int64_t pair_capacity,
+                            int64_t tile_capacity, size_t* bytes);
+
+/* gs_read_status -- copies the device status word to *flags (HOST) with a
+ * blocking cudaMemcpy (synchronises with the device).  Returns GS_ERR_DEVICE if
+ * any GS_FLAG_ERROR_MASK bit is set, else GS_OK. */
+gs_status gs_read_status(const uint32_t* status, uint32_t* flags);
+
+/* Human-readable name of a status code (static string, HOST). */
+const char* gs_status_str(gs_status s);
+
+/* Library version, "major.minor.patch" (static string, HOST). */
+const char* gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS103_GS_H */

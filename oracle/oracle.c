@@ -81,11 +81,11 @@ float ex32(float x) {
   float kf = rintf(x * log2e);
   float r = fmaf(-kf, ln2_hi, x);
   r = fmaf(-kf, ln2_lo, r);
-  float p = 1.0f / 5040.0f;
-  p = fmaf(p, r, 1.0f / 720.0f);
-  p = fmaf(p, r, 1.0f / 120.0f);
-  p = fmaf(p, r, 1.0f / 24.0f);
-  p = fmaf(p, r, 1.0f / 6.0f);
+  float p = 0x1.a01a02p-13f;                  /* float(1/5040) */
+  p = fmaf(p, r, 0x1.6c16c2p-10f);            /* 1/720 */
+  p = fmaf(p, r, 0x1.111112p-7f);             /* 1/120 */
+  p = fmaf(p, r, 0x1.555556p-5f);             /* 1/24 */
+  p = fmaf(p, r, 0x1.555556p-3f);             /* 1/6 */
   p = fmaf(p, r, 0.5f);
   p = fmaf(p, r, 1.0f);
   p = fmaf(p, r, 1.0f);
@@ -104,12 +104,12 @@ float lg32(float y) {
   if (m > 1.41421354f) { m = m * 0.5f; e += 1; }
   float s = (m - 1.0f) / (m + 1.0f);
   float s2 = s * s;
-  float p = 1.0f / 13.0f;
-  p = fmaf(p, s2, 1.0f / 11.0f);
-  p = fmaf(p, s2, 1.0f / 9.0f);
-  p = fmaf(p, s2, 1.0f / 7.0f);
-  p = fmaf(p, s2, 1.0f / 5.0f);
-  p = fmaf(p, s2, 1.0f / 3.0f);
+  float p = 0x1.3b13b2p-4f;                   /* float(1/13) */
+  p = fmaf(p, s2, 0x1.745d18p-4f);            /* 1/11 */
+  p = fmaf(p, s2, 0x1.c71c72p-4f);            /* 1/9 */
+  p = fmaf(p, s2, 0x1.24924ap-3f);            /* 1/7 */
+  p = fmaf(p, s2, 0x1.99999ap-3f);            /* 1/5 */
+  p = fmaf(p, s2, 0x1.555556p-2f);            /* 1/3 */
   float t = s * s2;
   float lm = fmaf(t, p, s);
   lm = lm + lm;
@@ -441,10 +441,11 @@ void or_render(int64_t N, const float* mo32, const float* su32, const float* q32
 
 /* ------------------------------------------------------------------------- */
 /* analytic gradient                                                          */
-/* dimg: per view, H x W x 4 doubles (dL/dR, dL/dG, dL/dB, dL/dDepth), views   */
-/* concatenated in order.  Outputs per Gaussian (N x 4 each, zero-initialised  */
-/* here): dmo = (dmu_x, dmu_y, dmu_z, dlogit), dsu = (dls_0..2, 0),            */
-/* dq = (dw, dx, dy, dz), drgb = (dr, dg, db, 0).                              */
+/* Pixels with a non-zero image gradient are listed explicitly: pix is K x 3   */
+/* int32 (view, u, v) and gpix K x 4 doubles (dL/dR, dL/dG, dL/dB, dL/dDepth). */
+/* Outputs per Gaussian (N x 4 each, zero-initialised here): dmo = (dmu_x,      */
+/* dmu_y, dmu_z, dlogit), dsu = (dls_0..2, 0), dq = (dw, dx, dy, dz),          */
+/* drgb = (dr, dg, db, 0).                                                     */
 /* g2d (optional, V x N x 8): per view screen-space gradients                  */
 /*   (dmean_x, dmean_y, dconic_a, dconic_b, dconic_c, dopacity, ddepth, 0).    */
 /* ------------------------------------------------------------------------- */
@@ -455,7 +456,8 @@ static void atomic_add(double* p, double v) {
 
 void or_grad(int64_t N, const float* mo32, const float* su32, const float* q32,
              const double* mo64, const double* su64, const double* q64, const double* rgb64,
-             int V, const float* cam, const int* camwh, const double* prm, const double* dimg,
+             int V, const float* cam, const int* camwh, const double* prm,
+             int64_t K, const int32_t* pix, const double* gpix_all,
              double* dmo, double* dsu, double* dq, double* drgb, double* g2d) {
   const double amin = prm[P_ALPHA_MIN], amax = prm[P_ALPHA_MAX], tmin = prm[P_T_MIN];
   memset(dmo, 0, sizeof(double) * 4 * (size_t)N);
@@ -463,10 +465,11 @@ void or_grad(int64_t N, const float* mo32, const float* su32, const float* q32,
   memset(dq, 0, sizeof(double) * 4 * (size_t)N);
   memset(drgb, 0, sizeof(double) * 4 * (size_t)N);
   double* G = (double*)calloc((size_t)V * (size_t)N * 8 + 1, sizeof(double));
-  int64_t img_off = 0;
   for (int v = 0; v < V; ++v) {
     const float* camf = cam + CAMF * v;
-    int W = camwh[2 * v], H = camwh[2 * v + 1];
+    int64_t any = 0;
+    for (int64_t k = 0; k < K; ++k) any |= (pix[3 * k] == v);
+    if (!any) continue;
     view_list L;
     build_view_list(N, mo32, su32, q32, mo64, su64, q64, camf, camwh + 2 * v, prm, &L);
     double* Gv = G + (size_t)v * (size_t)N * 8;
@@ -479,10 +482,10 @@ void or_grad(int64_t N, const float* mo32, const float* su32, const float* q32,
       double* cG = (double*)malloc(sizeof(double) * (size_t)cap);        /* exp(-q/2) */
       char* cc = (char*)malloc((size_t)cap);                               /* clamped */
 #pragma omp for schedule(dynamic, 16)
-      for (int64_t p = 0; p < (int64_t)W * H; ++p) {
-        int pu = (int)(p % W), pv = (int)(p / W);
-        double px = pu + 0.5, py = pv + 0.5;
-        const double* gpix = dimg + 4 * (img_off + p);
+      for (int64_t kp = 0; kp < K; ++kp) {
+        if (pix[3 * kp] != v) continue;
+        double px = pix[3 * kp + 1] + 0.5, py = pix[3 * kp + 2] + 0.5;
+        const double* gpix = gpix_all + 4 * kp;
         double T = 1.0;
         int64_t n = 0;
         for (int64_t i = 0; i < L.n; ++i) {
@@ -607,10 +610,9 @@ void or_grad(int64_t N, const float* mo32, const float* su32, const float* q32,
       for (int k = 0; k < 3; ++k) dsu[4 * g + k] += gs2[k] * 2.0 * P->s2[k];
       for (int k = 0; k < 4; ++k) dq[4 * g + k] += gqv[k];
     }
-    if (g2d) memcpy(g2d + (size_t)v * (size_t)N * 8, Gv, sizeof(double) * 8 * (size_t)N);
     free_view_list(&L);
-    img_off += (int64_t)W * H;
   }
+  if (g2d) memcpy(g2d, G, sizeof(double) * 8 * (size_t)N * (size_t)V);
   free(G);
 }
 

@@ -60,7 +60,7 @@ def _load():
         lib.or_project.restype = None
         lib.or_render.argtypes = [I64, P, P, P, P, P, P, P, I, P, P, P, I64, P, D, P, P, P, P, P, P]
         lib.or_render.restype = None
-        lib.or_grad.argtypes = [I64, P, P, P, P, P, P, P, I, P, P, P, P, P, P, P, P, P]
+        lib.or_grad.argtypes = [I64, P, P, P, P, P, P, P, I, P, P, P, I64, P, P, P, P, P, P, P]
         lib.or_grad.restype = None
         lib.or_bin_count.argtypes = [I64, P]
         lib.or_bin_count.restype = I64
@@ -205,23 +205,35 @@ def info_gain(gmap, cams, params: Params = Params()):
 def grad(gmap, cams, dimg, params: Params = Params(), values=None, want_2d: bool = False):
     """Analytic FP64 gradient of L = sum_views sum_pixels <dimg, (R, G, B, depth)>.
 
-    dimg: list (one per view) of [H, W, 4] arrays.  Returns dict of [N, 4] arrays
-    dmo (mu, logit), dsu (log-scales, 0), dq (quaternion), drgb (colour, 0) and, if
-    want_2d, g2d [V, N, 8] = (dmean_x, dmean_y, dconic_a, dconic_b, dconic_c,
-    dopacity, ddepth, 0) per view.
+    dimg: list (one per view) of [H, W, 4] arrays.  Only pixels with a non-zero
+    image gradient are visited.  Returns dict of [N, 4] arrays dmo (mu, logit),
+    dsu (log-scales, 0), dq (quaternion), drgb (colour, 0) and, if want_2d,
+    g2d [V, N, 8] = (dmean_x, dmean_y, dconic_a, dconic_b, dconic_c, dopacity,
+    ddepth, 0) per view.
     """
+    pix, gp = [], []
+    for v, d in enumerate(dimg):
+        d = np.asarray(d, np.float64)
+        ys, xs = np.nonzero(np.any(d != 0, axis=2))
+        pix.append(np.stack([np.full(len(xs), v), xs, ys], 1))
+        gp.append(d[ys, xs])
+    return grad_pixels(gmap, cams, np.concatenate(pix), np.concatenate(gp), params, values, want_2d)
+
+
+def grad_pixels(gmap, cams, pixels, gpix, params: Params = Params(), values=None, want_2d: bool = False):
+    """As `grad`, for an explicit list of pixels (K x 3: view, u, v) with gradients gpix (K x 4)."""
     lib = _load()
     (mo, su, q, rgb), (mo64, su64, q64, rgb64) = _map(gmap, values)
     N = mo.shape[0]
     cf, wh = _cams(cams)
     prm = params.block()
-    d = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).reshape(-1, 4) for x in dimg]))
-    assert d.shape[0] == sum(c.width * c.height for c in cams)
+    pix = np.ascontiguousarray(pixels, np.int32).reshape(-1, 3)
+    gp = np.ascontiguousarray(gpix, np.float64).reshape(-1, 4)
     out = {k: np.zeros((N, 4)) for k in ("dmo", "dsu", "dq", "drgb")}
     g2d = np.zeros((len(cams), N, 8)) if want_2d else None
     lib.or_grad(N, _p(mo), _p(su), _p(q), _p(mo64), _p(su64), _p(q64), _p(rgb64), len(cams), _p(cf), _p(wh),
-                _p(prm), _p(d), _p(out["dmo"]), _p(out["dsu"]), _p(out["dq"]), _p(out["drgb"]),
-                _p(g2d) if want_2d else None)
+                _p(prm), pix.shape[0], _p(pix), _p(gp), _p(out["dmo"]), _p(out["dsu"]), _p(out["dq"]),
+                _p(out["drgb"]), _p(g2d) if want_2d else None)
     if want_2d:
         out["g2d"] = g2d
     return out

@@ -1,0 +1,120 @@
+"""ctypes binding of libgs103.so (the C ABI declared in include/gs.h).
+
+Argument marshalling only: struct layouts mirror include/gs.h field for field
+and every function is bound with its exact prototype.  There is no fallback:
+if the library is missing or fails to load, `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import c_float, c_int32, c_int64, c_size_t, c_uint32, c_void_p, POINTER
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libgs103.so")
+
+# status codes and device flags (include/gs.h)
+GS_OK, GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG, GS_ERR_WORKSPACE, GS_ERR_CUDA, GS_ERR_DEVICE = range(7)
+GS_FLAG_PAIR_OVERFLOW = 1 << 0
+GS_FLAG_RANGE_OVERFLOW = 1 << 1
+GS_FLAG_BAD_CAMERA = 1 << 2
+GS_FLAG_NONFINITE = 1 << 3
+GS_FLAG_RECORD_OVERFLOW = 1 << 4
+GS_FLAG_ERROR_MASK = GS_FLAG_PAIR_OVERFLOW | GS_FLAG_RANGE_OVERFLOW | GS_FLAG_BAD_CAMERA | GS_FLAG_RECORD_OVERFLOW
+GS_IG_RENDER_MEAN = 0
+GS_OP_PROJECT, GS_OP_BIN_SORT, GS_OP_RENDER_BWD, GS_OP_INFO_GAIN = range(4)
+
+
+class gs_camera(ctypes.Structure):
+    _fields_ = [("fx", c_float), ("fy", c_float), ("cx", c_float), ("cy", c_float),
+                ("width", c_int32), ("height", c_int32), ("R", c_float * 9), ("T", c_float * 3)]
+
+
+class gs_map(ctypes.Structure):
+    _fields_ = [("mo", c_void_p), ("su", c_void_p), ("q", c_void_p), ("rgb", c_void_p), ("n", c_int64)]
+
+
+class gs_params(ctypes.Structure):
+    _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("eps2d", c_float), ("near_plane", c_float),
+                ("guard", c_float), ("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float)]
+
+
+class gs_proj(ctypes.Structure):
+    _fields_ = [("capacity", c_int64), ("count", c_void_p), ("status", c_void_p), ("view_info", c_void_p),
+                ("gid", c_void_p), ("view", c_void_p), ("xyod", c_void_p), ("conic_u", c_void_p),
+                ("rect", c_void_p), ("depth_key", c_void_p), ("g_first", c_void_p)]
+
+
+class gs_bins(ctypes.Structure):
+    _fields_ = [("pair_capacity", c_int64), ("tile_capacity", c_int64), ("count", c_void_p), ("tile", c_void_p),
+                ("rec", c_void_p), ("ranges", c_void_p)]
+
+
+class gs_image(ctypes.Structure):
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("unc", c_void_p), ("T", c_void_p), ("last", c_void_p)]
+
+
+class gs_image_grad(ctypes.Structure):
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p)]
+
+
+class gs_map_grad(ctypes.Structure):
+    _fields_ = [("dmo", c_void_p), ("dsu", c_void_p), ("dq", c_void_p), ("drgb", c_void_p)]
+
+
+assert ctypes.sizeof(gs_camera) == 72
+assert ctypes.sizeof(gs_params) == 32
+
+# name -> (restype, argtypes); the exported C ABI
+PROTOTYPES = {
+    "gs_project": (c_int32, [POINTER(gs_map), c_void_p, c_int32, POINTER(gs_params), POINTER(gs_proj), c_void_p,
+                             c_size_t, c_void_p]),
+    "gs_bin_sort": (c_int32, [POINTER(gs_proj), c_void_p, c_int32, POINTER(gs_params), POINTER(gs_bins), c_void_p,
+                              c_size_t, c_void_p]),
+    "gs_render_fwd": (c_int32, [POINTER(gs_map), POINTER(gs_proj), POINTER(gs_bins), c_void_p, c_int32,
+                                POINTER(gs_params), POINTER(gs_image), c_void_p]),
+    "gs_render_bwd": (c_int32, [POINTER(gs_map), POINTER(gs_proj), POINTER(gs_bins), POINTER(gs_image),
+                                POINTER(gs_image_grad), c_void_p, c_int32, POINTER(gs_params), POINTER(gs_map_grad),
+                                c_void_p, c_size_t, c_void_p]),
+    "gs_info_gain_batch": (c_int32, [POINTER(gs_map), c_void_p, c_int32, POINTER(gs_params), c_int32, c_void_p,
+                                     c_void_p, c_int64, c_int64, c_void_p, c_size_t, c_void_p]),
+    "gs_workspace_size": (c_int32, [c_int32, c_int64, c_int32, c_int64, c_int64, c_int64, POINTER(c_size_t)]),
+    "gs_read_status": (c_int32, [c_void_p, POINTER(c_uint32)]),
+    "gs_status_str": (ctypes.c_char_p, [c_int32]),
+    "gs_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+class GSError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libgs103.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise GSError("libgs103.so is not built (expected at %s); run `python -c \"import __graft_entry__ as g; "
+                          "g.build()\"`" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in PROTOTYPES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status: int, what: str):
+    if status != GS_OK:
+        msg = lib().gs_status_str(status).decode()
+        raise GSError("%s failed: %s" % (what, msg))
+
+
+def workspace_size(op: int, n: int, n_views: int, rec_cap: int = 0, pair_cap: int = 0, tile_cap: int = 0) -> int:
+    out = c_size_t(0)
+    check(lib().gs_workspace_size(op, n, n_views, rec_cap, pair_cap, tile_cap, ctypes.byref(out)),
+          "gs_workspace_size")
+    return int(out.value)

@@ -1,0 +1,198 @@
+// api.cu -- the extern "C" entry points declared in include/gs.h: argument
+// validation on the host, then the launches of the stage kernels on the
+// caller's stream.  Nothing here allocates, synchronises or prints.
+#include <stdint.h>
+
+#include "gs_internal.h"
+
+namespace gs {
+
+int device_sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (dev < 64 && cached[dev] > 0) return cached[dev];
+  int n = 1;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  if (dev < 64) cached[dev] = n;
+  return n;
+}
+
+namespace {
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+gs_status check_params(const gs_params* p) {
+  if (!p) return GS_ERR_NULL;
+  const int B = p->tile_w * p->tile_h;
+  if (p->tile_w < 1 || p->tile_h < 1 || p->tile_w > 64 || (B != 64 && B != 128 && B != 256 && B != 512 && B != 1024))
+    return GS_ERR_ARG;
+  if (!(p->eps2d >= 0.f) || !(p->near_plane > 0.f) || !(p->guard > 0.f)) return GS_ERR_ARG;
+  if (!(p->alpha_min >= 0.f && p->alpha_min < 1.f)) return GS_ERR_ARG;
+  if (!(p->alpha_max > 0.f && p->alpha_max <= 1.f)) return GS_ERR_ARG;
+  if (!(p->T_min >= 0.f && p->T_min < 1.f)) return GS_ERR_ARG;
+  return GS_OK;
+}
+
+gs_status check_map(const gs_map* m) {
+  if (!m) return GS_ERR_NULL;
+  if (m->n < 0 || m->n >= ((int64_t)1 << 32) - 1) return GS_ERR_ARG;
+  if (m->n == 0) return GS_OK;
+  if (!m->mo || !m->su || !m->q || !m->rgb) return GS_ERR_NULL;
+  if (!aligned(m->mo, 16) || !aligned(m->su, 16) || !aligned(m->q, 16) || !aligned(m->rgb, 16)) return GS_ERR_ALIGN;
+  return GS_OK;
+}
+
+gs_status check_views(const gs_camera* cams, int32_t n_views) {
+  if (n_views < 1 || n_views > (1 << 20)) return GS_ERR_ARG;
+  if (!cams) return GS_ERR_NULL;
+  if (!aligned(cams, 4)) return GS_ERR_ALIGN;
+  return GS_OK;
+}
+
+gs_status check_proj(const gs_proj* p) {
+  if (!p) return GS_ERR_NULL;
+  if (p->capacity < 0 || p->capacity >= ((int64_t)1 << 32) - 1) return GS_ERR_ARG;
+  if (!p->count || !p->status || !p->view_info || !p->g_first) return GS_ERR_NULL;
+  if (p->capacity > 0 && (!p->gid || !p->view || !p->xyod || !p->conic_u || !p->rect || !p->depth_key))
+    return GS_ERR_NULL;
+  if (!aligned(p->xyod, 16) || !aligned(p->conic_u, 16) || !aligned(p->rect, 8) || !aligned(p->gid, 4) ||
+      !aligned(p->view, 4) || !aligned(p->depth_key, 4) || !aligned(p->count, 4) || !aligned(p->status, 4) ||
+      !aligned(p->view_info, 4) || !aligned(p->g_first, 4))
+    return GS_ERR_ALIGN;
+  return GS_OK;
+}
+
+gs_status check_bins(const gs_bins* b) {
+  if (!b) return GS_ERR_NULL;
+  if (b->pair_capacity < 1 || b->pair_capacity >= ((int64_t)1 << 32) - 1) return GS_ERR_ARG;
+  if (b->tile_capacity < 1 || b->tile_capacity >= ((int64_t)1 << 31)) return GS_ERR_ARG;
+  if (!b->count || !b->tile || !b->rec || !b->ranges) return GS_ERR_NULL;
+  if (!aligned(b->count, 4) || !aligned(b->tile, 4) || !aligned(b->rec, 4) || !aligned(b->ranges, 8)) return GS_ERR_ALIGN;
+  return GS_OK;
+}
+
+gs_status check_ws(void* ws, size_t have, size_t need) {
+  if (need == 0) return GS_OK;
+  if (!ws) return GS_ERR_NULL;
+  if (!aligned(ws, 256)) return GS_ERR_ALIGN;
+  if (have < need) return GS_ERR_WORKSPACE;
+  return GS_OK;
+}
+
+gs_status from_cuda(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
+
+}  // namespace
+}  // namespace gs
+
+using namespace gs;
+
+#define GS_TRY(x)                   \
+  do {                              \
+    gs_status s__ = (x);            \
+    if (s__ != GS_OK) return s__;   \
+  } while (0)
+
+extern "C" {
+
+gs_status gs_project(const gs_map* map, const gs_camera* cams, int32_t n_views, const gs_params* prm, gs_proj* out,
+                     void* ws, size_t ws_bytes, void* stream) {
+  GS_TRY(check_map(map));
+  GS_TRY(check_views(cams, n_views));
+  GS_TRY(check_params(prm));
+  GS_TRY(check_proj(out));
+  GS_TRY(check_ws(ws, ws_bytes, project_ws_bytes(map->n, n_views)));
+  return from_cuda(launch_project(*map, cams, n_views, *prm, *out, ws, (cudaStream_t)stream));
+}
+
+gs_status gs_bin_sort(const gs_proj* proj, const gs_camera* cams, int32_t n_views, const gs_params* prm,
+                      gs_bins* out, void* ws, size_t ws_bytes, void* stream) {
+  GS_TRY(check_proj(proj));
+  GS_TRY(check_views(cams, n_views));
+  GS_TRY(check_params(prm));
+  GS_TRY(check_bins(out));
+  GS_TRY(check_ws(ws, ws_bytes, bin_ws_bytes(proj->capacity, out->pair_capacity, out->tile_capacity)));
+  return from_cuda(launch_bin_sort(*proj, cams, n_views, *prm, *out, ws, (cudaStream_t)stream));
+}
+
+gs_status gs_render_fwd(const gs_map* map, const gs_proj* proj, const gs_bins* bins, const gs_camera* cams,
+                        int32_t n_views, const gs_params* prm, gs_image* out, void* stream) {
+  GS_TRY(check_map(map));
+  GS_TRY(check_proj(proj));
+  GS_TRY(check_bins(bins));
+  GS_TRY(check_views(cams, n_views));
+  GS_TRY(check_params(prm));
+  if (!out) return GS_ERR_NULL;
+  return from_cuda(launch_render_fwd(*map, *proj, *bins, cams, n_views, *prm, *out, (cudaStream_t)stream));
+}
+
+gs_status gs_render_bwd(const gs_map* map, const gs_proj* proj, const gs_bins* bins, const gs_image* fwd,
+                        const gs_image_grad* grad, const gs_camera* cams, int32_t n_views, const gs_params* prm,
+                        gs_map_grad* out, void* ws, size_t ws_bytes, void* stream) {
+  GS_TRY(check_map(map));
+  GS_TRY(check_proj(proj));
+  GS_TRY(check_bins(bins));
+  GS_TRY(check_views(cams, n_views));
+  GS_TRY(check_params(prm));
+  if (!fwd || !grad || !out) return GS_ERR_NULL;
+  if (!fwd->T || !fwd->last) return GS_ERR_NULL;
+  if (map->n > 0 && (!out->dmo || !out->dsu || !out->dq || !out->drgb)) return GS_ERR_NULL;
+  if (!aligned(out->dmo, 16) || !aligned(out->dsu, 16) || !aligned(out->dq, 16) || !aligned(out->drgb, 16))
+    return GS_ERR_ALIGN;
+  GS_TRY(check_ws(ws, ws_bytes, bwd_ws_bytes(proj->capacity)));
+  return from_cuda(
+      launch_render_bwd(*map, *proj, *bins, *fwd, *grad, cams, n_views, *prm, *out, ws, (cudaStream_t)stream));
+}
+
+gs_status gs_info_gain_batch(const gs_map* map, const gs_camera* cams, int32_t n_views, const gs_params* prm,
+                             int32_t mode, float* ig_out, uint32_t* status, int64_t pair_capacity,
+                             int64_t tile_capacity, void* ws, size_t ws_bytes, void* stream) {
+  GS_TRY(check_map(map));
+  GS_TRY(check_views(cams, n_views));
+  GS_TRY(check_params(prm));
+  if (mode != GS_IG_RENDER_MEAN) return GS_ERR_ARG;
+  if (!ig_out || !status) return GS_ERR_NULL;
+  if (!aligned(ig_out, 4) || !aligned(status, 4)) return GS_ERR_ALIGN;
+  if (pair_capacity < 1 || pair_capacity >= ((int64_t)1 << 32) - 1) return GS_ERR_ARG;
+  if (tile_capacity < 1 || tile_capacity >= ((int64_t)1 << 31)) return GS_ERR_ARG;
+  if (map->n * (int64_t)n_views >= ((int64_t)1 << 32) - 1) return GS_ERR_ARG;
+  GS_TRY(check_ws(ws, ws_bytes, ig_ws_bytes(map->n, n_views, pair_capacity, tile_capacity)));
+  return from_cuda(launch_info_gain(*map, cams, n_views, *prm, ig_out, status, pair_capacity, tile_capacity, ws,
+                                    (cudaStream_t)stream));
+}
+
+gs_status gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t rec_capacity, int64_t pair_capacity,
+                            int64_t tile_capacity, size_t* bytes) {
+  if (!bytes) return GS_ERR_NULL;
+  if (n < 0 || n_views < 1 || rec_capacity < 0 || pair_capacity < 0 || tile_capacity < 0) return GS_ERR_ARG;
+  switch (op) {
+    case GS_OP_PROJECT: *bytes = project_ws_bytes(n, n_views); return GS_OK;
+    case GS_OP_BIN_SORT: *bytes = bin_ws_bytes(rec_capacity, pair_capacity, tile_capacity); return GS_OK;
+    case GS_OP_RENDER_BWD: *bytes = bwd_ws_bytes(rec_capacity); return GS_OK;
+    case GS_OP_INFO_GAIN: *bytes = ig_ws_bytes(n, n_views, pair_capacity, tile_capacity); return GS_OK;
+    default: return GS_ERR_ARG;
+  }
+}
+
+gs_status gs_read_status(const uint32_t* status, uint32_t* flags) {
+  if (!status || !flags) return GS_ERR_NULL;
+  if (cudaMemcpy(flags, status, sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess) return GS_ERR_CUDA;
+  return (*flags & GS_FLAG_ERROR_MASK) ? GS_ERR_DEVICE : GS_OK;
+}
+
+const char* gs_status_str(gs_status s) {
+  switch (s) {
+    case GS_OK: return "GS_OK";
+    case GS_ERR_NULL: return "GS_ERR_NULL: a required pointer is NULL";
+    case GS_ERR_ALIGN: return "GS_ERR_ALIGN: a pointer is not aligned as required";
+    case GS_ERR_ARG: return "GS_ERR_ARG: a count, size or parameter is out of range";
+    case GS_ERR_WORKSPACE: return "GS_ERR_WORKSPACE: workspace too small";
+    case GS_ERR_CUDA: return "GS_ERR_CUDA: a CUDA call or kernel launch failed";
+    case GS_ERR_DEVICE: return "GS_ERR_DEVICE: the device status word carries an error flag";
+    default: return "unknown gs_status";
+  }
+}
+
+const char* gs_version(void) { return "0.1.0"; }
+
+}  // extern "C"

@@ -1,0 +1,267 @@
+// gs_common.cuh -- device-side building blocks shared by the splatting kernels.
+//
+// Projection arithmetic follows RT-GuIDE (arXiv 2409.18122) Sec. III: world-to-
+// camera t = R^T (mu - T), depth d = t_z, mu_2D = K t / t_z, generalised to the
+// EWA 2D covariance J W Sigma W^T J^T of an anisotropic Gaussian.
+//
+// The integer outcomes of the projection -- whether a Gaussian is culled for a
+// view, its depth sort key and its tile rectangle -- are computed with a fixed
+// sequence of correctly rounded IEEE-754 float operations written as explicit
+// __f*_rn intrinsics (never contracted or reordered by the compiler), plus the
+// exp/log below.  The results are therefore reproducible bit for bit by any
+// IEEE-754 implementation that performs the same operations.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+// ---------------------------------------------------------------- constants
+constexpr int kMaxViewsPerChunk = 128;   // cameras staged in shared memory at a time
+
+// view_info layout: [V+1][2] = (first global tile, first pixel)
+struct ViewInfo {
+  uint32_t tile_base;
+  uint32_t pix_base;
+};
+
+// Per-view constants derived from a gs_camera, staged in shared memory.
+struct CamC {
+  float fx, fy, cx, cy;
+  float R[9];
+  float T[3];
+  float gx, gy;          // guard-band slopes guard * (W/2) / fx, guard * (H/2) / fy
+  int W, H;
+  int tiles_x, tiles_y;
+  uint32_t tile_base;
+  uint32_t pix_base;
+};
+
+// ---------------------------------------------------------------- float math
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// e^x for the projection: Cody & Waite additive range reduction x = k ln2 + r
+// (ln 2 split into 355/512 and a correction so that k * hi is exact), the
+// Taylor series of e^r to r^7 in Horner form, and 2^k from the exponent bits.
+// Input clamped to [-87, 88] so 2^k stays normal.
+__device__ __forceinline__ float ex32(float x) {
+  if (x < -87.0f) x = -87.0f;
+  if (x > 88.0f) x = 88.0f;
+  float kf = rintf(fmul(x, 1.44269504088896341f));
+  float r = ffma(-kf, 0.693359375f, x);
+  r = ffma(-kf, -2.12194440054690583e-4f, r);
+  float p = 0x1.a01a02p-13f;       // 1/7!
+  p = ffma(p, r, 0x1.6c16c2p-10f);  // 1/6!
+  p = ffma(p, r, 0x1.111112p-7f);   // 1/5!
+  p = ffma(p, r, 0x1.555556p-5f);   // 1/4!
+  p = ffma(p, r, 0x1.555556p-3f);   // 1/3!
+  p = ffma(p, r, 0.5f);
+  p = ffma(p, r, 1.0f);
+  p = ffma(p, r, 1.0f);
+  int k = (int)kf;
+  float scale = __uint_as_float((uint32_t)(k + 127) << 23);
+  return fmul(p, scale);
+}
+
+// ln y for finite normal y > 0: y = m 2^e, m in [sqrt(1/2), sqrt(2)),
+// ln m = 2 atanh(s) with s = (m - 1)/(m + 1), odd series to s^13.
+__device__ __forceinline__ float lg32(float y) {
+  uint32_t b = __float_as_uint(y);
+  int e = (int)((b >> 23) & 0xffu) - 127;
+  float m = __uint_as_float((b & 0x7fffffu) | 0x3f800000u);
+  if (m > 1.41421354f) { m = fmul(m, 0.5f); e += 1; }
+  float s = fdiv(fsub(m, 1.0f), fadd(m, 1.0f));
+  float s2 = fmul(s, s);
+  float p = 0x1.3b13b2p-4f;          // 1/13
+  p = ffma(p, s2, 0x1.745d18p-4f);   // 1/11
+  p = ffma(p, s2, 0x1.c71c72p-4f);   // 1/9
+  p = ffma(p, s2, 0x1.24924ap-3f);   // 1/7
+  p = ffma(p, s2, 0x1.99999ap-3f);   // 1/5
+  p = ffma(p, s2, 0x1.555556p-2f);   // 1/3
+  float t = fmul(s, s2);
+  float lm = ffma(t, p, s);
+  lm = fadd(lm, lm);
+  float ef = (float)e;
+  return ffma(ef, 0.693359375f, ffma(ef, -2.12194440054690583e-4f, lm));
+}
+
+// ---------------------------------------------------------------- per Gaussian
+// View-independent part of the projection.
+struct GaussPre {
+  bool valid;
+  float S[6];     // 3D covariance upper triangle 00 01 02 11 12 22
+  float Q;        // alpha >= alpha_min  <=>  q <= Q
+  float o;        // opacity
+};
+
+__device__ __forceinline__ bool finite4(float4 a) {
+  return isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(a.w);
+}
+
+__device__ __forceinline__ float sym3(const float* S, int i, int j) {
+  // upper-triangle index of (i, j)
+  int a = i < j ? i : j, b = i < j ? j : i;
+  return S[a == 0 ? b : (a == 1 ? 2 + b : 5)];
+}
+
+// Rotation matrix (row-major) of the normalised quaternion (w, x, y, z), with the
+// same operation order as the decision arithmetic requires.
+__device__ __forceinline__ void quat_rot_dec(float w, float x, float y, float z, float* R) {
+  float xx = fmul(x, x), yy = fmul(y, y), zz = fmul(z, z);
+  float xy = fmul(x, y), xz = fmul(x, z), yz = fmul(y, z);
+  float wx = fmul(w, x), wy = fmul(w, y), wz = fmul(w, z), t;
+  t = fadd(yy, zz); R[0] = fsub(1.0f, fadd(t, t));
+  t = fsub(xy, wz); R[1] = fadd(t, t);
+  t = fadd(xz, wy); R[2] = fadd(t, t);
+  t = fadd(xy, wz); R[3] = fadd(t, t);
+  t = fadd(xx, zz); R[4] = fsub(1.0f, fadd(t, t));
+  t = fsub(yz, wx); R[5] = fadd(t, t);
+  t = fsub(xz, wy); R[6] = fadd(t, t);
+  t = fadd(yz, wx); R[7] = fadd(t, t);
+  t = fadd(xx, yy); R[8] = fsub(1.0f, fadd(t, t));
+}
+
+__device__ __forceinline__ GaussPre gauss_pre(float4 mo, float4 su, float4 q, float alpha_min) {
+  GaussPre g;
+  g.valid = false;
+  g.Q = 0.f;
+  g.o = 0.f;
+  if (!finite4(mo) || !isfinite(su.x) || !isfinite(su.y) || !isfinite(su.z) || !finite4(q)) return g;
+  float n2 = ffma(q.x, q.x, ffma(q.y, q.y, ffma(q.z, q.z, fmul(q.w, q.w))));
+  if (!(n2 > 0.0f) || !isfinite(n2)) return g;
+  float rn = __fsqrt_rn(n2);
+  float w = fdiv(q.x, rn), x = fdiv(q.y, rn), y = fdiv(q.z, rn), z = fdiv(q.w, rn);
+  float R[9];
+  quat_rot_dec(w, x, y, z, R);
+  float s2[3] = {ex32(fadd(su.x, su.x)), ex32(fadd(su.y, su.y)), ex32(fadd(su.z, su.z))};
+  float A[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) A[3 * i + k] = fmul(R[3 * i + k], s2[k]);
+  const int I[6] = {0, 0, 0, 1, 1, 2}, J[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    int i = I[e], j = J[e];
+    g.S[e] = ffma(A[3 * i + 0], R[3 * j + 0], ffma(A[3 * i + 1], R[3 * j + 1], fmul(A[3 * i + 2], R[3 * j + 2])));
+  }
+  float o = fdiv(1.0f, fadd(1.0f, ex32(-mo.w)));
+  g.o = o;
+  if (alpha_min > 0.0f) {
+    float inv = fdiv(1.0f, alpha_min);
+    float xo = fmul(o, inv);
+    if (!(xo >= 1.0f)) return g;
+    float l = lg32(xo);
+    g.Q = fadd(l, l);
+  } else {
+    if (!(o > 0.0f)) return g;
+    g.Q = __int_as_float(0x7f800000);  // +inf: unbounded support
+  }
+  g.valid = true;
+  return g;
+}
+
+// ---------------------------------------------------------------- per view
+struct ViewProj {
+  float mx, my;      // mu_2D
+  float depth;       // t_z
+  float ca, cb, cc;  // conic
+  int x0, y0, x1, y1;  // tile rect, ends exclusive
+};
+
+// Returns true if the Gaussian is visible in the view and fills `vp`.
+__device__ __forceinline__ bool view_proj(float4 mo, const GaussPre& g, const CamC& c, float near_plane,
+                                          float eps2d, int tile_w, int tile_h, ViewProj& vp) {
+  if (!g.valid) return false;
+  const float* R = c.R;
+  float dx = fsub(mo.x, c.T[0]), dy = fsub(mo.y, c.T[1]), dz = fsub(mo.z, c.T[2]);
+  float tx = ffma(R[6], dz, ffma(R[3], dy, fmul(R[0], dx)));
+  float ty = ffma(R[7], dz, ffma(R[4], dy, fmul(R[1], dx)));
+  float tz = ffma(R[8], dz, ffma(R[5], dy, fmul(R[2], dx)));
+  if (!(tz > near_plane)) return false;
+  if (fabsf(tx) > fmul(c.gx, tz)) return false;
+  if (fabsf(ty) > fmul(c.gy, tz)) return false;
+  float iz = fdiv(1.0f, tz);
+  float u = fmul(tx, iz), v = fmul(ty, iz);
+  float mux = ffma(c.fx, u, c.cx), muy = ffma(c.fy, v, c.cy);
+  float j00 = fmul(c.fx, iz), j11 = fmul(c.fy, iz);
+  float j02 = -fmul(j00, u), j12 = -fmul(j11, v);
+  float T0[3], T1[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    T0[m] = ffma(j00, R[3 * m + 0], fmul(j02, R[3 * m + 2]));
+    T1[m] = ffma(j11, R[3 * m + 1], fmul(j12, R[3 * m + 2]));
+  }
+  float B0[3], B1[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    B0[m] = ffma(T0[0], sym3(g.S, 0, m), ffma(T0[1], sym3(g.S, 1, m), fmul(T0[2], sym3(g.S, 2, m))));
+    B1[m] = ffma(T1[0], sym3(g.S, 0, m), ffma(T1[1], sym3(g.S, 1, m), fmul(T1[2], sym3(g.S, 2, m))));
+  }
+  float a = fadd(ffma(B0[0], T0[0], ffma(B0[1], T0[1], fmul(B0[2], T0[2]))), eps2d);
+  float b = ffma(B0[0], T1[0], ffma(B0[1], T1[1], fmul(B0[2], T1[2])));
+  float cc = fadd(ffma(B1[0], T1[0], ffma(B1[1], T1[1], fmul(B1[2], T1[2]))), eps2d);
+  float det = ffma(a, cc, -fmul(b, b));
+  if (!(det > 0.0f)) return false;
+  float rx = __fsqrt_rn(fmul(g.Q, a)), ry = __fsqrt_rn(fmul(g.Q, cc));
+  float px = fsub(mux, 0.5f), py = fsub(muy, 0.5f);
+  float xlo = ceilf(fsub(px, rx)), xhi = floorf(fadd(px, rx));
+  float ylo = ceilf(fsub(py, ry)), yhi = floorf(fadd(py, ry));
+  xlo = fmaxf(xlo, 0.0f);
+  ylo = fmaxf(ylo, 0.0f);
+  xhi = fminf(xhi, (float)(c.W - 1));
+  yhi = fminf(yhi, (float)(c.H - 1));
+  if (!(xlo <= xhi) || !(ylo <= yhi)) return false;
+  vp.x0 = (int)xlo / tile_w;
+  vp.y0 = (int)ylo / tile_h;
+  vp.x1 = (int)xhi / tile_w + 1;
+  vp.y1 = (int)yhi / tile_h + 1;
+  vp.mx = mux;
+  vp.my = muy;
+  vp.depth = tz;
+  float idet = fdiv(1.0f, det);
+  vp.ca = fmul(cc, idet);
+  vp.cb = -fmul(b, idet);
+  vp.cc = fmul(a, idet);
+  return true;
+}
+
+// Camera -> per-view constants (guard slopes computed with the same operations
+// on every device so the cull decision is reproducible).
+__device__ __forceinline__ void load_cam(const gs_camera& g, float guard, int tile_w, int tile_h, CamC& c) {
+  c.fx = g.fx; c.fy = g.fy; c.cx = g.cx; c.cy = g.cy;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) c.R[i] = g.R[i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) c.T[i] = g.T[i];
+  c.W = g.width;
+  c.H = g.height;
+  c.gx = fdiv(fmul(guard, fmul(0.5f, (float)g.width)), g.fx);
+  c.gy = fdiv(fmul(guard, fmul(0.5f, (float)g.height)), g.fy);
+  c.tiles_x = (g.width + tile_w - 1) / tile_w;
+  c.tiles_y = (g.height + tile_h - 1) / tile_h;
+}
+
+// ---------------------------------------------------------------- misc
+__device__ __forceinline__ void set_flag(uint32_t* status, uint32_t f) {
+  if (status) atomicOr(status, f);
+}
+
+__device__ __forceinline__ int find_view(const uint32_t* view_info, int n_views, uint32_t tile) {
+  // largest v with tile_base[v] <= tile
+  int lo = 0, hi = n_views - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (view_info[2 * mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+}  // namespace gs

@@ -1,0 +1,80 @@
+// gs_internal.h -- host-side launchers shared between the translation units of
+// libgs103.so.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+// ------------------------------------------------------------------ helpers
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Carves consecutive 256-byte aligned sub-buffers out of a workspace.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  template <class T>
+  T* take(size_t count) {
+    off = align_up(off, 256);
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+int device_sm_count();
+
+// ------------------------------------------------------------------ scan
+// Exclusive prefix sum of n uint32 values into out[0..n]; out[n] = total.
+// n = min(*n_dev, n_cap) when n_dev != NULL, else n_cap.  Prefixes saturate at
+// 0xFFFFFFFF.  If total_out != NULL, the (saturated) total is also stored there.
+size_t scan_temp_bytes(int64_t n_cap);
+cudaError_t scan_exclusive(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, int64_t n_cap,
+                           uint32_t* total_out, void* temp, cudaStream_t st);
+
+// ------------------------------------------------------------------ radix sort
+// Stable LSD radix sort of (key, value) uint32 pairs on bits [bit_begin, bit_end).
+// Input: keys_in (nullable: then keys are read as key_src[val]), vals_in
+// (nullable: identity 0..n-1).  Buffers a/b are ping-pong storage of n_cap
+// entries each; the sorted result ends in a if the number of 8-bit passes is
+// even, else in b.  *result_in_a tells which.  n = min(*n_dev, n_cap).
+struct SortBufs {
+  uint32_t* keys_a;
+  uint32_t* vals_a;
+  uint32_t* keys_b;
+  uint32_t* vals_b;
+};
+size_t sort_temp_bytes(int64_t n_cap);
+int sort_passes(int bit_begin, int bit_end);
+cudaError_t radix_sort(const uint32_t* keys_in, const uint32_t* key_src, const uint32_t* vals_in, SortBufs bufs,
+                       const uint32_t* n_dev, int64_t n_cap, int bit_begin, int bit_end, void* temp,
+                       cudaStream_t st, bool* result_in_a);
+
+// ------------------------------------------------------------------ pipeline stages
+size_t project_ws_bytes(int64_t n, int n_views);
+cudaError_t launch_project(const gs_map& map, const gs_camera* cams, int n_views, const gs_params& p,
+                           const gs_proj& out, void* ws, cudaStream_t st);
+
+size_t bin_ws_bytes(int64_t rec_cap, int64_t pair_cap, int64_t tile_cap);
+cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_views, const gs_params& p,
+                            const gs_bins& out, void* ws, cudaStream_t st);
+
+cudaError_t launch_render_fwd(const gs_map& map, const gs_proj& proj, const gs_bins& bins, const gs_camera* cams,
+                              int n_views, const gs_params& p, const gs_image& img, cudaStream_t st);
+
+size_t bwd_ws_bytes(int64_t rec_cap);
+cudaError_t launch_render_bwd(const gs_map& map, const gs_proj& proj, const gs_bins& bins, const gs_image& fwd,
+                              const gs_image_grad& g, const gs_camera* cams, int n_views, const gs_params& p,
+                              const gs_map_grad& out, void* ws, cudaStream_t st);
+
+size_t ig_ws_bytes(int64_t n, int n_views, int64_t pair_cap, int64_t tile_cap);
+cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_views, const gs_params& p,
+                             float* ig_out, uint32_t* status, int64_t pair_cap, int64_t tile_cap, void* ws,
+                             cudaStream_t st);
+
+}  // namespace gs

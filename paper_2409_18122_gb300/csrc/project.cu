@@ -1,0 +1,163 @@
+// project.cu -- gs_project: EWA projection of every Gaussian into every view.
+//
+// Sec. III of RT-GuIDE: mu_2D = K R^T (mu - T) / d, d = e3^T R^T (mu - T), with the
+// anisotropic EWA covariance in place of the isotropic r_2D = f r / d.
+//
+// Gaussian-major: one thread per Gaussian reads its 64 bytes of parameters once
+// (coalesced float4 SoA loads), computes the view-independent part (rotation,
+// 3D covariance, opacity, support bound) once, and loops over the cameras held
+// in shared memory.  Records are compacted in (Gaussian, view) order with two
+// passes (count, exclusive scan, write) so that the order is deterministic and
+// no block waits on another.
+#include "gs_common.cuh"
+#include "gs_internal.h"
+
+namespace gs {
+namespace {
+
+constexpr int kBlock = 256;
+
+// Per-view table: tile and pixel offsets (prefix sums over views), camera checks.
+__global__ void __launch_bounds__(1024) k_view_info(const gs_camera* __restrict__ cams, int n_views, int tile_w,
+                                                    int tile_h, uint32_t* __restrict__ view_info,
+                                                    uint32_t* status) {
+  __shared__ unsigned long long s_tiles[32], s_pix[32];
+  const int per = (n_views + blockDim.x - 1) / blockDim.x;
+  const int v0 = threadIdx.x * per;
+  int v1 = v0 + per;
+  if (v1 > n_views) v1 = n_views;
+  unsigned long long t = 0, p = 0;
+  bool bad = false;
+  for (int v = v0; v < v1; ++v) {
+    const gs_camera& c = cams[v];
+    const bool ok = c.width > 0 && c.height > 0 && c.fx > 0.f && c.fy > 0.f && isfinite(c.fx) && isfinite(c.fy);
+    if (!ok) { bad = true; continue; }
+    t += (unsigned long long)((c.width + tile_w - 1) / tile_w) * (unsigned long long)((c.height + tile_h - 1) / tile_h);
+    p += (unsigned long long)c.width * (unsigned long long)c.height;
+  }
+  if (bad) set_flag(status, GS_FLAG_BAD_CAMERA);
+  // block exclusive scan of (t, p)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long xt = t, xp = p;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    unsigned long long yt = __shfl_up_sync(0xffffffffu, xt, d), yp = __shfl_up_sync(0xffffffffu, xp, d);
+    if (lane >= d) { xt += yt; xp += yp; }
+  }
+  if (lane == 31) { s_tiles[warp] = xt; s_pix[warp] = xp; }
+  __syncthreads();
+  unsigned long long bt = 0, bp = 0;
+  for (int w = 0; w < warp; ++w) { bt += s_tiles[w]; bp += s_pix[w]; }
+  unsigned long long et = bt + xt - t, ep = bp + xp - p;
+  for (int v = v0; v < v1; ++v) {
+    const gs_camera& c = cams[v];
+    view_info[2 * v] = (uint32_t)et;
+    view_info[2 * v + 1] = (uint32_t)ep;
+    const bool ok = c.width > 0 && c.height > 0 && c.fx > 0.f && c.fy > 0.f && isfinite(c.fx) && isfinite(c.fy);
+    if (ok) {
+      et += (unsigned long long)((c.width + tile_w - 1) / tile_w) * (unsigned long long)((c.height + tile_h - 1) / tile_h);
+      ep += (unsigned long long)c.width * (unsigned long long)c.height;
+    }
+  }
+  if (threadIdx.x == blockDim.x - 1) {
+    if (et > 0xFFFFFFFFull || ep > 0xFFFFFFFFull) set_flag(status, GS_FLAG_RANGE_OVERFLOW);
+    view_info[2 * n_views] = (uint32_t)et;
+    view_info[2 * n_views + 1] = (uint32_t)ep;
+  }
+}
+
+__device__ __forceinline__ void stage_cams(const gs_camera* __restrict__ cams, const uint32_t* __restrict__ view_info,
+                                           int v0, int nv, const gs_params& p, CamC* s_cam) {
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    const gs_camera g = cams[v0 + i];
+    CamC c;
+    load_cam(g, p.guard, p.tile_w, p.tile_h, c);
+    if (!(g.width > 0 && g.height > 0 && g.fx > 0.f && g.fy > 0.f && isfinite(g.fx) && isfinite(g.fy))) {
+      c.W = 0;  // marks the view unusable
+      c.H = 0;
+    }
+    c.tile_base = view_info[2 * (v0 + i)];
+    c.pix_base = view_info[2 * (v0 + i) + 1];
+    s_cam[i] = c;
+  }
+}
+
+template <bool kWrite>
+__global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera* __restrict__ cams, int n_views,
+                                                     gs_params p, const uint32_t* __restrict__ view_info,
+                                                     uint32_t* __restrict__ counts, gs_proj out) {
+  __shared__ CamC s_cam[kMaxViewsPerChunk];
+  const int64_t g = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  const bool active = g < map.n;
+  float4 mo = make_float4(0.f, 0.f, 0.f, 0.f), su = mo, q = mo;
+  GaussPre pre;
+  pre.valid = false;
+  if (active) {
+    mo = __ldg(reinterpret_cast<const float4*>(map.mo) + g);
+    su = __ldg(reinterpret_cast<const float4*>(map.su) + g);
+    q = __ldg(reinterpret_cast<const float4*>(map.q) + g);
+    pre = gauss_pre(mo, su, q, p.alpha_min);
+    if (!kWrite && !(finite4(mo) && isfinite(su.x) && isfinite(su.y) && isfinite(su.z) && finite4(q)))
+      set_flag(out.status, GS_FLAG_NONFINITE);
+  }
+  uint32_t n_vis = 0;
+  uint32_t dst = 0;
+  if (kWrite && active) dst = out.g_first[g];
+  for (int v0 = 0; v0 < n_views; v0 += kMaxViewsPerChunk) {
+    const int nv = min(kMaxViewsPerChunk, n_views - v0);
+    __syncthreads();
+    stage_cams(cams, view_info, v0, nv, p, s_cam);
+    __syncthreads();
+    if (!active || !pre.valid) continue;
+    for (int i = 0; i < nv; ++i) {
+      const CamC& c = s_cam[i];
+      if (c.W <= 0) continue;
+      ViewProj vp;
+      if (!view_proj(mo, pre, c, p.near_plane, p.eps2d, p.tile_w, p.tile_h, vp)) continue;
+      if (kWrite) {
+        if ((int64_t)dst < out.capacity) {
+          out.gid[dst] = (uint32_t)g;
+          out.view[dst] = (uint32_t)(v0 + i);
+          reinterpret_cast<float4*>(out.xyod)[dst] = make_float4(vp.mx, vp.my, pre.o, vp.depth);
+          reinterpret_cast<float4*>(out.conic_u)[dst] = make_float4(vp.ca, vp.cb, vp.cc, su.w);
+          reinterpret_cast<ushort4*>(out.rect)[dst] =
+              make_ushort4((unsigned short)vp.x0, (unsigned short)vp.y0, (unsigned short)vp.x1, (unsigned short)vp.y1);
+          out.depth_key[dst] = __float_as_uint(vp.depth);
+        }
+        ++dst;
+      } else {
+        ++n_vis;
+      }
+    }
+  }
+  if (!kWrite && active) counts[g] = n_vis;
+}
+
+__global__ void k_record_count(const gs_proj out, int64_t n) {
+  const uint32_t total = out.g_first[n];
+  *out.count = (int64_t)total > out.capacity ? (uint32_t)out.capacity : total;
+  if ((int64_t)total > out.capacity) set_flag(out.status, GS_FLAG_RECORD_OVERFLOW);
+}
+
+}  // namespace
+
+size_t project_ws_bytes(int64_t n, int /*n_views*/) {
+  return align_up(sizeof(uint32_t) * (size_t)(n + 1), 256) + scan_temp_bytes(n);
+}
+
+cudaError_t launch_project(const gs_map& map, const gs_camera* cams, int n_views, const gs_params& p,
+                           const gs_proj& out, void* ws, cudaStream_t st) {
+  Carver c(ws);
+  uint32_t* counts = c.take<uint32_t>((size_t)map.n + 1);
+  void* scan_tmp = c.take<char>(scan_temp_bytes(map.n));
+  k_view_info<<<1, 1024, 0, st>>>(cams, n_views, p.tile_w, p.tile_h, out.view_info, out.status);
+  const int64_t blocks = (map.n + kBlock - 1) / kBlock;
+  if (blocks > 0) k_project<false><<<(unsigned)blocks, kBlock, 0, st>>>(map, cams, n_views, p, out.view_info, counts, out);
+  cudaError_t e = scan_exclusive(counts, out.g_first, nullptr, map.n, nullptr, scan_tmp, st);
+  if (e != cudaSuccess) return e;
+  if (blocks > 0) k_project<true><<<(unsigned)blocks, kBlock, 0, st>>>(map, cams, n_views, p, out.view_info, counts, out);
+  k_record_count<<<1, 1, 0, st>>>(out, map.n);
+  return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,294 @@
+// render_bwd.cu -- gs_render_bwd: adjoint of the compositing and the projection.
+//
+// Eq. (2) of RT-GuIDE refines the map by back-propagating the rendering loss.
+// For a pixel with contributors i = 1..n (front to back), w_i = alpha_i T_i and
+// out_ch = sum_i w_i x_i,ch, the derivative with respect to alpha_i is
+//   dL/dalpha_i = sum_ch g_ch (x_i,ch T_i - S_i,ch / (1 - alpha_i)),
+//   S_i,ch = sum_{j>i} w_j x_j,ch.
+// The kernel replays each tile back to front starting from the saved final
+// transmittance and last index, recovering T_i = T_{i+1} / (1 - alpha_i), so no
+// per-pixel contributor list is stored.  Per-Gaussian screen-space gradients are
+// summed over the 32 pixels of a warp with shuffles and added with one float4
+// atomic per warp; a second kernel maps them through the projection per
+// Gaussian (records of one Gaussian are contiguous), without atomics.
+#include "gs_common.cuh"
+#include "gs_internal.h"
+#include "render_common.cuh"
+
+namespace gs {
+namespace {
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  return v;
+}
+
+__global__ void __launch_bounds__(1024) k_render_bwd(gs_map map, gs_proj proj, gs_bins bins,
+                                                      const gs_camera* __restrict__ cams, int n_views, gs_params p,
+                                                      gs_image fwd, gs_image_grad grad, float4* __restrict__ g2d) {
+  extern __shared__ float4 s_buf[];
+  const int B = blockDim.x;
+  float4* s_xyod = s_buf;
+  float4* s_con = s_buf + B;
+  float4* s_rgb = s_buf + 2 * B;
+  uint32_t* s_rec = reinterpret_cast<uint32_t*>(s_buf + 3 * B);
+  __shared__ TileInfo ti;
+  __shared__ int s_max_last;
+  const uint32_t tile = blockIdx.x;
+  if (threadIdx.x == 0) s_max_last = 0;
+  if (!tile_setup(proj, bins, cams, n_views, p, tile, ti)) return;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int px = ti.x0 + tid % p.tile_w, py = ti.y0 + tid / p.tile_w;
+  const bool inside = px < ti.W && py < ti.H;
+  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+  const size_t P = (size_t)ti.W * ti.H;
+  const size_t pix = (size_t)py * ti.W + px;
+  const size_t o = (size_t)ti.pix_base + pix;
+  float T = 1.f, gr = 0.f, gg = 0.f, gb = 0.f, gd = 0.f;
+  int last = 0;
+  if (inside) {
+    T = fwd.T[o];
+    last = fwd.last[o];
+    if (grad.rgb) {
+      const float* base = grad.rgb + 3 * (size_t)ti.pix_base;
+      gr = base[pix];
+      gg = base[P + pix];
+      gb = base[2 * P + pix];
+    }
+    if (grad.depth) gd = grad.depth[o];
+    atomicMax(&s_max_last, last);
+  }
+  __syncthreads();
+  const int n_todo = s_max_last;
+  float Sr = 0.f, Sg = 0.f, Sb = 0.f, Sd = 0.f;
+  for (int hi = n_todo; hi > 0; hi -= B) {
+    const int lo = hi - B > 0 ? hi - B : 0;
+    const int cnt = hi - lo;
+    __syncthreads();
+    if (tid < cnt) {
+      const uint32_t r = bins.rec[ti.beg + lo + tid];
+      s_rec[tid] = r;
+      s_xyod[tid] = __ldg(reinterpret_cast<const float4*>(proj.xyod) + r);
+      s_con[tid] = __ldg(reinterpret_cast<const float4*>(proj.conic_u) + r);
+      s_rgb[tid] = __ldg(reinterpret_cast<const float4*>(map.rgb) + proj.gid[r]);
+    }
+    __syncthreads();
+    for (int j = cnt - 1; j >= 0; --j) {
+      const int pos = lo + j;   // position in the tile's list
+      bool contrib = inside && pos < last;
+      float a_ = 0.f, G = 0.f;
+      const float4 a = s_xyod[j];
+      const float4 k = s_con[j];
+      float dx = 0.f, dy = 0.f;
+      if (contrib) {
+        a_ = splat_alpha_dxy(a, k, pxc, pyc, p.alpha_max, dx, dy, G);
+        if (a_ < p.alpha_min) contrib = false;
+      }
+      if (!__any_sync(0xffffffffu, contrib)) continue;
+      float v[10];
+#pragma unroll
+      for (int q = 0; q < 10; ++q) v[q] = 0.f;
+      if (contrib) {
+        const float4 c = s_rgb[j];
+        const float om = 1.f - a_;
+        const float Ti = T / om;
+        const float w = a_ * Ti;
+        const float dalpha = (gr * c.x + gg * c.y + gb * c.z + gd * a.w) * Ti -
+                             (gr * Sr + gg * Sg + gb * Sb + gd * Sd) / om;
+        Sr += w * c.x;
+        Sg += w * c.y;
+        Sb += w * c.z;
+        Sd += w * a.w;
+        T = Ti;
+        v[7] = gr * w;
+        v[8] = gg * w;
+        v[9] = gb * w;
+        v[6] = gd * w;
+        if (__fmul_rn(a.z, G) < p.alpha_max) {   // not clamped
+          v[5] = dalpha * G;                       // dL/do
+          const float dq = -0.5f * a_ * dalpha;    // dL/dq
+          v[0] = dq * 2.f * (k.x * dx + k.y * dy); // dL/dmu_x (dx = mu_x - p_x)
+          v[1] = dq * 2.f * (k.y * dx + k.z * dy); // dL/dmu_y
+          v[2] = dq * dx * dx;                     // dL/da
+          v[3] = dq * 2.f * dx * dy;               // dL/db
+          v[4] = dq * dy * dy;                     // dL/dc
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 10; ++q) v[q] = warp_sum(v[q]);
+      if (lane == 0) {
+        float4* dst = g2d + 3 * (size_t)s_rec[j];
+        atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
+        atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], 0.f));
+        atomicAdd(dst + 2, make_float4(v[7], v[8], v[9], 0.f));
+      }
+    }
+  }
+}
+
+__global__ void k_zero_g2d(float4* __restrict__ g2d, const uint32_t* count, int64_t cap) {
+  int64_t n = (int64_t)*count;
+  if (n > cap) n = cap;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n; i += (int64_t)gridDim.x * blockDim.x)
+    g2d[i] = z;
+}
+
+// Projection adjoint: one thread per Gaussian, summing over its records.
+__global__ void __launch_bounds__(256) k_proj_adjoint(gs_map map, gs_proj proj, const gs_camera* __restrict__ cams,
+                                                      const float4* __restrict__ g2d, gs_map_grad out) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= map.n) return;
+  int64_t nrec = (int64_t)*proj.count;
+  uint32_t r0 = proj.g_first[g], r1 = proj.g_first[g + 1];
+  if ((int64_t)r1 > nrec) r1 = (uint32_t)nrec;
+  float gmu[3] = {0.f, 0.f, 0.f}, go = 0.f, grgb[3] = {0.f, 0.f, 0.f};
+  float M3[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  const float4 mo = reinterpret_cast<const float4*>(map.mo)[g];
+  const float4 su = reinterpret_cast<const float4*>(map.su)[g];
+  const float4 qv = reinterpret_cast<const float4*>(map.q)[g];
+  float Rq[9], s2[3], S3[3][3], qn[4], qnorm = 1.f;
+  const bool any = r0 < r1;
+  if (any) {
+    qnorm = sqrtf(qv.x * qv.x + qv.y * qv.y + qv.z * qv.z + qv.w * qv.w);
+    const float w = qv.x / qnorm, x = qv.y / qnorm, y = qv.z / qnorm, z = qv.w / qnorm;
+    qn[0] = w; qn[1] = x; qn[2] = y; qn[3] = z;
+    Rq[0] = 1.f - 2.f * (y * y + z * z); Rq[1] = 2.f * (x * y - w * z);       Rq[2] = 2.f * (x * z + w * y);
+    Rq[3] = 2.f * (x * y + w * z);       Rq[4] = 1.f - 2.f * (x * x + z * z); Rq[5] = 2.f * (y * z - w * x);
+    Rq[6] = 2.f * (x * z - w * y);       Rq[7] = 2.f * (y * z + w * x);       Rq[8] = 1.f - 2.f * (x * x + y * y);
+    s2[0] = expf(2.f * su.x); s2[1] = expf(2.f * su.y); s2[2] = expf(2.f * su.z);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        S3[i][j] = Rq[3 * i] * s2[0] * Rq[3 * j] + Rq[3 * i + 1] * s2[1] * Rq[3 * j + 1] + Rq[3 * i + 2] * s2[2] * Rq[3 * j + 2];
+  }
+  for (uint32_t r = r0; r < r1; ++r) {
+    const float4 A = g2d[3 * (size_t)r], Bv = g2d[3 * (size_t)r + 1], Cv = g2d[3 * (size_t)r + 2];
+    grgb[0] += Cv.x; grgb[1] += Cv.y; grgb[2] += Cv.z;
+    go += Bv.y;
+    const float gmx = A.x, gmy = A.y, ga = A.z, gb = A.w, gc = Bv.x, gdep = Bv.z;
+    const gs_camera& cam = cams[proj.view[r]];
+    const float* R = cam.R;
+    const float dx = mo.x - cam.T[0], dy = mo.y - cam.T[1], dz = mo.z - cam.T[2];
+    const float tx = R[0] * dx + R[3] * dy + R[6] * dz;
+    const float ty = R[1] * dx + R[4] * dy + R[7] * dz;
+    const float tz = R[2] * dx + R[5] * dy + R[8] * dz;
+    const float4 con = reinterpret_cast<const float4*>(proj.conic_u)[r];
+    // dL/dSigma2D = -C G_C C (symmetric-matrix gradients)
+    const float C00 = con.x, C01 = con.y, C11 = con.z;
+    const float G00 = ga, G01 = 0.5f * gb, G11 = gc;
+    const float t00 = G00 * C00 + G01 * C01, t01 = G00 * C01 + G01 * C11;
+    const float t10 = G01 * C00 + G11 * C01, t11 = G01 * C01 + G11 * C11;
+    const float S00 = -(C00 * t00 + C01 * t10), S01 = -(C00 * t01 + C01 * t11);
+    const float S11 = -(C01 * t01 + C11 * t11);
+    const float iz = 1.f / tz, iz2 = iz * iz;
+    const float J00 = cam.fx * iz, J02 = -cam.fx * tx * iz2, J11 = cam.fy * iz, J12 = -cam.fy * ty * iz2;
+    float T3[2][3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      T3[0][m] = J00 * R[3 * m + 0] + J02 * R[3 * m + 2];
+      T3[1][m] = J11 * R[3 * m + 1] + J12 * R[3 * m + 2];
+    }
+    const float GS[2][2] = {{S00, S01}, {S01, S11}};
+    // M3 += T3^T GS T3
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float u0 = GS[0][0] * T3[0][i] + GS[1][0] * T3[1][i];
+      const float u1 = GS[0][1] * T3[0][i] + GS[1][1] * T3[1][i];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) M3[i][j] += u0 * T3[0][j] + u1 * T3[1][j];
+    }
+    // GT3 = 2 GS T3 S3; GJ = GT3 R (GJ[r][k] = sum_m GT3[r][m] R[m][k])
+    float GT3[2][3];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      const float h0 = GS[rr][0] * T3[0][0] + GS[rr][1] * T3[1][0];
+      const float h1 = GS[rr][0] * T3[0][1] + GS[rr][1] * T3[1][1];
+      const float h2 = GS[rr][0] * T3[0][2] + GS[rr][1] * T3[1][2];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) GT3[rr][m] = 2.f * (h0 * S3[0][m] + h1 * S3[1][m] + h2 * S3[2][m]);
+    }
+    float GJ[2][3];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk) GJ[rr][kk] = GT3[rr][0] * R[kk] + GT3[rr][1] * R[3 + kk] + GT3[rr][2] * R[6 + kk];
+    const float iz3 = iz2 * iz;
+    const float gtx = GJ[0][2] * (-cam.fx * iz2) + gmx * cam.fx * iz;
+    const float gty = GJ[1][2] * (-cam.fy * iz2) + gmy * cam.fy * iz;
+    const float gtz = GJ[0][0] * (-cam.fx * iz2) + GJ[0][2] * (2.f * cam.fx * tx * iz3) + GJ[1][1] * (-cam.fy * iz2) +
+                      GJ[1][2] * (2.f * cam.fy * ty * iz3) - gmx * cam.fx * tx * iz2 - gmy * cam.fy * ty * iz2 + gdep;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) gmu[m] += R[3 * m + 0] * gtx + R[3 * m + 1] * gty + R[3 * m + 2] * gtz;
+  }
+  float4 dmo = make_float4(0.f, 0.f, 0.f, 0.f), dsu = dmo, dq = dmo, drgb = dmo;
+  if (any) {
+    // dL/dRq = 2 M3 Rq diag(s2); dL/ds2_k = (Rq^T M3 Rq)_kk
+    float GR[9], gs2[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk)
+        GR[3 * i + kk] = 2.f * (M3[i][0] * Rq[kk] + M3[i][1] * Rq[3 + kk] + M3[i][2] * Rq[6 + kk]) * s2[kk];
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+      float s = 0.f;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) s += Rq[3 * i + kk] * M3[i][j] * Rq[3 * j + kk];
+      gs2[kk] = s;
+    }
+    const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+    const float gw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+    const float gx = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6] + w * GR[7] -
+                            2.f * x * GR[8]);
+    const float gy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] - w * GR[6] + z * GR[7] -
+                            2.f * y * GR[8]);
+    const float gz = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] + y * GR[5] + x * GR[6] +
+                            y * GR[7]);
+    const float dot = w * gw + x * gx + y * gy + z * gz;
+    const float inv = 1.f / qnorm;
+    dq = make_float4((gw - w * dot) * inv, (gx - x * dot) * inv, (gy - y * dot) * inv, (gz - z * dot) * inv);
+    const float o = 1.f / (1.f + expf(-mo.w));
+    dmo = make_float4(gmu[0], gmu[1], gmu[2], go * o * (1.f - o));
+    dsu = make_float4(2.f * s2[0] * gs2[0], 2.f * s2[1] * gs2[1], 2.f * s2[2] * gs2[2], 0.f);
+    drgb = make_float4(grgb[0], grgb[1], grgb[2], 0.f);
+  }
+  reinterpret_cast<float4*>(out.dmo)[g] = dmo;
+  reinterpret_cast<float4*>(out.dsu)[g] = dsu;
+  reinterpret_cast<float4*>(out.dq)[g] = dq;
+  reinterpret_cast<float4*>(out.drgb)[g] = drgb;
+}
+
+}  // namespace
+
+size_t bwd_ws_bytes(int64_t rec_cap) { return align_up(sizeof(float4) * 3 * (size_t)rec_cap, 256); }
+
+cudaError_t launch_render_bwd(const gs_map& map, const gs_proj& proj, const gs_bins& bins, const gs_image& fwd,
+                              const gs_image_grad& g, const gs_camera* cams, int n_views, const gs_params& p,
+                              const gs_map_grad& out, void* ws, cudaStream_t st) {
+  float4* g2d = (float4*)ws;
+  int64_t zb = (3 * proj.capacity + 255) / 256;
+  if (zb > 4096) zb = 4096;
+  if (zb < 1) zb = 1;
+  k_zero_g2d<<<(unsigned)zb, 256, 0, st>>>(g2d, proj.count, proj.capacity);
+  const int B = p.tile_w * p.tile_h;
+  const size_t smem = 3 * sizeof(float4) * B + sizeof(uint32_t) * B;
+  static bool attr[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !attr[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_render_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    if (e != cudaSuccess) return e;
+    attr[dev] = true;
+  }
+  if (bins.tile_capacity > 0)
+    k_render_bwd<<<(unsigned)bins.tile_capacity, B, smem, st>>>(map, proj, bins, cams, n_views, p, fwd, g, g2d);
+  if (map.n > 0) k_proj_adjoint<<<(unsigned)((map.n + 255) / 256), 256, 0, st>>>(map, proj, cams, g2d, out);
+  return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,89 @@
+// render_common.cuh -- per-tile setup and the per-(pixel, Gaussian) opacity
+// shared by the forward, backward and information-gain compositing kernels, so
+// that all of them take identical skip / stop decisions.
+#pragma once
+
+#include "gs_common.cuh"
+
+namespace gs {
+
+struct TileInfo {
+  bool valid;
+  int view;
+  int W, H;
+  int x0, y0;          // pixel origin of the tile
+  uint32_t pix_base;   // first pixel of the view in the concatenated images
+  uint32_t beg, end;   // range in the sorted pair list
+};
+
+// Called by every thread of the block; returns whether the tile exists.
+__device__ __forceinline__ bool tile_setup(const gs_proj& proj, const gs_bins& bins, const gs_camera* cams,
+                                           int n_views, const gs_params& p, uint32_t tile, TileInfo& ti) {
+  if (threadIdx.x == 0) {
+    const uint32_t total = proj.view_info[2 * n_views];
+    ti.valid = tile < total && (int64_t)tile < bins.tile_capacity;
+    if (ti.valid) {
+      const int v = find_view(proj.view_info, n_views, tile);
+      const uint32_t local = tile - proj.view_info[2 * v];
+      const int W = cams[v].width, H = cams[v].height;
+      const uint32_t tx = (uint32_t)((W + p.tile_w - 1) / p.tile_w);
+      ti.view = v;
+      ti.W = W;
+      ti.H = H;
+      ti.x0 = (int)(local % tx) * p.tile_w;
+      ti.y0 = (int)(local / tx) * p.tile_h;
+      ti.pix_base = proj.view_info[2 * v + 1];
+      uint32_t n_pairs = *bins.count;
+      if ((int64_t)n_pairs > bins.pair_capacity) n_pairs = (uint32_t)bins.pair_capacity;
+      uint32_t b = bins.ranges[2 * (size_t)tile], e = bins.ranges[2 * (size_t)tile + 1];
+      if (e > n_pairs) e = n_pairs;
+      if (b > e) b = e;
+      ti.beg = b;
+      ti.end = e;
+    }
+  }
+  __syncthreads();
+  return ti.valid;
+}
+
+// alpha = min(alpha_max, o exp(-q/2)), q = a dx^2 + 2 b dx dy + c dy^2 with
+// (dx, dy) = mu_2D - pixel centre.  xyod = (mu_x, mu_y, o, depth), con = (a, b, c, u).
+// Written with explicit round-to-nearest intrinsics so that the forward,
+// backward and information-gain kernels compute bit-identical alphas (and so
+// take identical skip and stop decisions) whatever the compiler contracts.
+// Also returns (dx, dy) and G = exp(-q/2).
+__device__ __forceinline__ float splat_alpha_dxy(const float4& xyod, const float4& con, float pxc, float pyc,
+                                                 float alpha_max, float& dx, float& dy, float& G) {
+  dx = __fsub_rn(xyod.x, pxc);
+  dy = __fsub_rn(xyod.y, pyc);
+  float q = __fmul_rn(__fmul_rn(con.z, dy), dy);
+  q = __fmaf_rn(__fmul_rn(con.x, dx), dx, q);
+  q = __fmaf_rn(__fmul_rn(__fadd_rn(con.y, con.y), dx), dy, q);
+  G = __expf(__fmul_rn(-0.5f, q));
+  return fminf(alpha_max, __fmul_rn(xyod.z, G));
+}
+
+__device__ __forceinline__ float splat_alpha(const float4& xyod, const float4& con, float pxc, float pyc,
+                                             float alpha_max) {
+  float dx, dy, G;
+  return splat_alpha_dxy(xyod, con, pxc, pyc, alpha_max, dx, dy, G);
+}
+
+// Fixed-tree block sum (deterministic for a fixed block size); result valid in thread 0.
+__device__ __forceinline__ float block_sum_fixed(float v, float* s_red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  if (lane == 0) s_red[warp] = v;
+  __syncthreads();
+  float s = 0.f;
+  if (warp == 0) {
+    s = lane < nw ? s_red[lane] : 0.f;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
+  }
+  __syncthreads();
+  return s;
+}
+
+}  // namespace gs

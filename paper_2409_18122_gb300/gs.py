@@ -1,0 +1,328 @@
+"""PyTorch front end of libgs103.so: device buffers, streams, autograd.
+
+Every step of the splatting path runs in the library's CUDA kernels; this
+module only allocates tensors (PyTorch owns all device memory), passes their
+pointers and the current stream through the C ABI, and wraps the forward and
+backward entry points in a torch.autograd.Function.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+CAMERA_DTYPE = np.dtype([("fx", "<f4"), ("fy", "<f4"), ("cx", "<f4"), ("cy", "<f4"), ("width", "<i4"),
+                         ("height", "<i4"), ("R", "<f4", (9,)), ("T", "<f4", (3,))])
+assert CAMERA_DTYPE.itemsize == 72
+
+
+@dataclass
+class RenderParams:
+    """Rendering constants the paper leaves unstated (see include/gs.h gs_params)."""
+    tile_w: int = 16
+    tile_h: int = 16
+    eps2d: float = 0.3
+    near: float = 0.2
+    guard: float = 1.3
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    T_min: float = 1e-4
+
+    def c(self) -> L.gs_params:
+        return L.gs_params(self.tile_w, self.tile_h, self.eps2d, self.near, self.guard, self.alpha_min,
+                           self.alpha_max, self.T_min)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def pack_cameras(cams) -> np.ndarray:
+    """Cameras (objects with fx, fy, cx, cy, width, height, R, T) -> gs_camera records."""
+    a = np.zeros(len(cams), CAMERA_DTYPE)
+    for i, c in enumerate(cams):
+        a[i] = (c.fx, c.fy, c.cx, c.cy, c.width, c.height, np.asarray(c.R, np.float32).reshape(9),
+                np.asarray(c.T, np.float32).reshape(3))
+    return a
+
+
+def cameras_to_device(cams, device="cuda") -> torch.Tensor:
+    return torch.from_numpy(pack_cameras(cams).view(np.uint8).copy()).to(device)
+
+
+def tile_grid(cams, params: RenderParams):
+    tx = np.array([-(-c.width // params.tile_w) for c in cams], np.int64)
+    ty = np.array([-(-c.height // params.tile_h) for c in cams], np.int64)
+    tiles = tx * ty
+    pix = np.array([c.width * c.height for c in cams], np.int64)
+    tile_base = np.concatenate([[0], np.cumsum(tiles)])
+    pix_base = np.concatenate([[0], np.cumsum(pix)])
+    return tx, ty, tile_base, pix_base
+
+
+class GaussianMapTensors:
+    """The four [N, 4] float32 device arrays of include/gs.h gs_map."""
+
+    def __init__(self, mo: torch.Tensor, su: torch.Tensor, q: torch.Tensor, rgb: torch.Tensor):
+        self.mo, self.su, self.q, self.rgb = mo, su, q, rgb
+
+    @staticmethod
+    def from_numpy(g, device="cuda") -> "GaussianMapTensors":
+        return GaussianMapTensors(*(torch.from_numpy(np.ascontiguousarray(a)).to(device) for a in
+                                    (g.mo, g.su, g.q, g.rgb)))
+
+    @property
+    def n(self) -> int:
+        return int(self.mo.shape[0])
+
+    def c(self) -> L.gs_map:
+        return make_map(self.mo, self.su, self.q, self.rgb)
+
+
+def make_map(mo, su, q, rgb) -> L.gs_map:
+    for t in (mo, su, q, rgb):
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.dim() != 2 or t.shape[1] != 4:
+            raise ValueError("map arrays must be contiguous float32 CUDA tensors of shape [N, 4]")
+    return L.gs_map(_ptr(mo), _ptr(su), _ptr(q), _ptr(rgb), int(mo.shape[0]))
+
+
+def _alloc_u32(n, device):
+    return torch.empty(max(int(n), 1), dtype=torch.int32, device=device)
+
+
+class Frame:
+    """Device buffers for projecting, binning and rendering one map into a fixed camera set.
+
+    pair_capacity bounds the number of (tile, Gaussian) pairs; exceeding it sets
+    GS_FLAG_PAIR_OVERFLOW (see `check_status` / `grow_if_needed`).
+    """
+
+    def __init__(self, n: int, cams: Sequence, params: RenderParams = RenderParams(),
+                 pair_capacity: Optional[int] = None, device="cuda"):
+        self.device = torch.device(device)
+        self.params = params
+        self.cams = list(cams)
+        self.V = len(self.cams)
+        self.n = int(n)
+        self.cams_dev = cameras_to_device(self.cams, self.device)
+        self.tiles_x, self.tiles_y, self.tile_base, self.pix_base = tile_grid(self.cams, params)
+        self.n_tiles = int(self.tile_base[-1])
+        self.n_pixels = int(self.pix_base[-1])
+        self.rec_capacity = max(self.n * self.V, 1)
+        if pair_capacity is None:
+            pair_capacity = min(max(1 << 20, 8 * self.n * self.V), (1 << 31) - 1)
+        self._alloc(int(pair_capacity))
+
+    def _alloc(self, pair_capacity: int):
+        d, rc = self.device, self.rec_capacity
+        self.pair_capacity = pair_capacity
+        self.status = torch.zeros(1, dtype=torch.int32, device=d)
+        self.rec_count = torch.zeros(1, dtype=torch.int32, device=d)
+        self.view_info = torch.zeros(2 * (self.V + 1), dtype=torch.int32, device=d)
+        self.gid = _alloc_u32(rc, d)
+        self.view = _alloc_u32(rc, d)
+        self.xyod = torch.empty((rc, 4), dtype=torch.float32, device=d)
+        self.conic_u = torch.empty((rc, 4), dtype=torch.float32, device=d)
+        self.rect = torch.empty((rc, 4), dtype=torch.int16, device=d)
+        self.depth_key = _alloc_u32(rc, d)
+        self.g_first = _alloc_u32(self.n + 1, d)
+        self.pair_count = torch.zeros(1, dtype=torch.int32, device=d)
+        self.pair_tile = _alloc_u32(pair_capacity, d)
+        self.pair_rec = _alloc_u32(pair_capacity, d)
+        self.ranges = torch.zeros((max(self.n_tiles, 1), 2), dtype=torch.int32, device=d)
+        ws = max(L.workspace_size(L.GS_OP_PROJECT, self.n, self.V),
+                 L.workspace_size(L.GS_OP_BIN_SORT, self.n, self.V, rc, pair_capacity, max(self.n_tiles, 1)),
+                 L.workspace_size(L.GS_OP_RENDER_BWD, self.n, self.V, rc))
+        self.ws = torch.empty(max(ws, 256), dtype=torch.uint8, device=d)
+        self.c_proj = L.gs_proj(rc, _ptr(self.rec_count), _ptr(self.status), _ptr(self.view_info), _ptr(self.gid),
+                                _ptr(self.view), _ptr(self.xyod), _ptr(self.conic_u), _ptr(self.rect),
+                                _ptr(self.depth_key), _ptr(self.g_first))
+        self.c_bins = L.gs_bins(pair_capacity, max(self.n_tiles, 1), _ptr(self.pair_count), _ptr(self.pair_tile),
+                                _ptr(self.pair_rec), _ptr(self.ranges))
+        self.c_params = self.params.c()
+
+    # -------------------------------------------------------------- stages
+    def project(self, gmap: GaussianMapTensors, stream=None):
+        if gmap.n != self.n:
+            raise ValueError("map has %d Gaussians, frame was built for %d" % (gmap.n, self.n))
+        m = gmap.c()
+        L.check(L.lib().gs_project(ctypes.byref(m), _ptr(self.cams_dev), self.V, ctypes.byref(self.c_params),
+                                   ctypes.byref(self.c_proj), _ptr(self.ws), self.ws.numel(), _stream(stream)),
+                "gs_project")
+
+    def bin_sort(self, stream=None):
+        L.check(L.lib().gs_bin_sort(ctypes.byref(self.c_proj), _ptr(self.cams_dev), self.V,
+                                    ctypes.byref(self.c_params), ctypes.byref(self.c_bins), _ptr(self.ws),
+                                    self.ws.numel(), _stream(stream)), "gs_bin_sort")
+
+    def new_images(self, with_rgb=True, with_depth=True, with_unc=True):
+        d, P = self.device, self.n_pixels
+        return dict(rgb=torch.empty(3 * P, dtype=torch.float32, device=d) if with_rgb else None,
+                    depth=torch.empty(P, dtype=torch.float32, device=d) if with_depth else None,
+                    unc=torch.empty(P, dtype=torch.float32, device=d) if with_unc else None,
+                    T=torch.empty(P, dtype=torch.float32, device=d),
+                    last=torch.empty(P, dtype=torch.int32, device=d))
+
+    def render_fwd(self, gmap: GaussianMapTensors, images=None, stream=None):
+        img = self.new_images() if images is None else images
+        c_img = L.gs_image(_ptr(img["rgb"]), _ptr(img["depth"]), _ptr(img["unc"]), _ptr(img["T"]),
+                           _ptr(img["last"]))
+        m = gmap.c()
+        L.check(L.lib().gs_render_fwd(ctypes.byref(m), ctypes.byref(self.c_proj), ctypes.byref(self.c_bins),
+                                      _ptr(self.cams_dev), self.V, ctypes.byref(self.c_params), ctypes.byref(c_img),
+                                      _stream(stream)), "gs_render_fwd")
+        return img
+
+    def render_bwd(self, gmap: GaussianMapTensors, images, d_rgb=None, d_depth=None, grads=None, stream=None):
+        g = grads
+        if g is None:
+            g = {k: torch.empty((self.n, 4), dtype=torch.float32, device=self.device) for k in
+                 ("dmo", "dsu", "dq", "drgb")}
+        c_img = L.gs_image(_ptr(images["rgb"]), _ptr(images["depth"]), _ptr(images["unc"]), _ptr(images["T"]),
+                           _ptr(images["last"]))
+        c_g = L.gs_image_grad(_ptr(d_rgb), _ptr(d_depth))
+        c_out = L.gs_map_grad(_ptr(g["dmo"]), _ptr(g["dsu"]), _ptr(g["dq"]), _ptr(g["drgb"]))
+        m = gmap.c()
+        L.check(L.lib().gs_render_bwd(ctypes.byref(m), ctypes.byref(self.c_proj), ctypes.byref(self.c_bins),
+                                      ctypes.byref(c_img), ctypes.byref(c_g), _ptr(self.cams_dev), self.V,
+                                      ctypes.byref(self.c_params), ctypes.byref(c_out), _ptr(self.ws),
+                                      self.ws.numel(), _stream(stream)), "gs_render_bwd")
+        return g
+
+    def forward(self, gmap: GaussianMapTensors, images=None, stream=None):
+        """project -> bin_sort -> render_fwd."""
+        self.project(gmap, stream)
+        self.bin_sort(stream)
+        return self.render_fwd(gmap, images, stream)
+
+    # -------------------------------------------------------------- status
+    def reset_status(self):
+        self.status.zero_()
+
+    def read_status(self) -> int:
+        flags = ctypes.c_uint32(0)
+        L.lib().gs_read_status(_ptr(self.status), ctypes.byref(flags))
+        return int(flags.value)
+
+    def check_status(self):
+        f = self.read_status()
+        if f & L.GS_FLAG_ERROR_MASK:
+            raise L.GSError("device status flags 0x%x (pairs %d / capacity %d)" %
+                            (f, int(self.pair_count.item()) & 0xFFFFFFFF, self.pair_capacity))
+        return f
+
+    def grow_if_needed(self, margin: float = 1.25) -> bool:
+        """After a synchronised forward: if pairs overflowed, reallocate with room for them (returns True)."""
+        f = self.read_status()
+        if f & L.GS_FLAG_PAIR_OVERFLOW:
+            need = int(self.pair_count.item()) & 0xFFFFFFFF
+            if need == 0xFFFFFFFF:
+                need = 2 * self.pair_capacity
+            self._alloc(min(int(need * margin) + 1024, (1 << 32) - 2))
+            return True
+        return False
+
+    # -------------------------------------------------------------- views of the images
+    def split_images(self, img):
+        """Per-view dict of [3,H,W] rgb and [H,W] depth/unc/T/last views into the flat buffers."""
+        out = []
+        for v, c in enumerate(self.cams):
+            p0, P = int(self.pix_base[v]), c.width * c.height
+            d = {}
+            if img.get("rgb") is not None:
+                d["rgb"] = img["rgb"][3 * p0:3 * (p0 + P)].view(3, c.height, c.width)
+            for k in ("depth", "unc", "T", "last"):
+                if img.get(k) is not None:
+                    d[k] = img[k][p0:p0 + P].view(c.height, c.width)
+            out.append(d)
+        return out
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, mo, su, q, rgb, frame: Frame):
+        gmap = GaussianMapTensors(mo, su, q, rgb)
+        img = frame.forward(gmap)
+        ctx.frame = frame
+        ctx.img = img
+        ctx.save_for_backward(mo, su, q, rgb)
+        return img["rgb"], img["depth"], img["unc"]
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_unc):
+        mo, su, q, rgb = ctx.saved_tensors
+        gmap = GaussianMapTensors(mo, su, q, rgb)
+        g_rgb = None if g_rgb is None else g_rgb.contiguous()
+        g_depth = None if g_depth is None else g_depth.contiguous()
+        g = ctx.frame.render_bwd(gmap, ctx.img, g_rgb, g_depth)
+        return g["dmo"], g["dsu"], g["dq"], g["drgb"], None
+
+
+def render(mo, su, q, rgb, frame: Frame):
+    """Differentiable render of all views of `frame`: flat (rgb [3P], depth [P], unc [P]) tensors.
+
+    Gradients flow to mo (means, opacity logit), su (log-scales; the uncertainty
+    column gets zero), q and rgb through gs_render_bwd.
+    """
+    return _RenderFn.apply(mo, su, q, rgb, frame)
+
+
+class InfoGain:
+    """Batched information gain over a fixed candidate set (gs_info_gain_batch)."""
+
+    def __init__(self, n: int, cams: Sequence, params: RenderParams = RenderParams(),
+                 pair_capacity: Optional[int] = None, device="cuda"):
+        self.device = torch.device(device)
+        self.params = params
+        self.c_params = params.c()
+        self.cams = list(cams)
+        self.V = len(self.cams)
+        self.n = int(n)
+        self.cams_dev = cameras_to_device(self.cams, self.device)
+        _, _, tile_base, _ = tile_grid(self.cams, params)
+        self.n_tiles = max(int(tile_base[-1]), 1)
+        if pair_capacity is None:
+            pair_capacity = min(max(1 << 20, 4 * self.n * self.V), (1 << 31) - 1)
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.out = torch.zeros(self.V, dtype=torch.float32, device=self.device)
+        self._alloc(int(pair_capacity))
+
+    def _alloc(self, pair_capacity):
+        self.pair_capacity = pair_capacity
+        ws = L.workspace_size(L.GS_OP_INFO_GAIN, self.n, self.V, 0, pair_capacity, self.n_tiles)
+        self.ws = None
+        torch.cuda.empty_cache()
+        self.ws = torch.empty(ws, dtype=torch.uint8, device=self.device)
+
+    def __call__(self, gmap: GaussianMapTensors, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        o = self.out if out is None else out
+        m = gmap.c()
+        L.check(L.lib().gs_info_gain_batch(ctypes.byref(m), _ptr(self.cams_dev), self.V,
+                                           ctypes.byref(self.c_params), L.GS_IG_RENDER_MEAN, _ptr(o),
+                                           _ptr(self.status), self.pair_capacity, self.n_tiles, _ptr(self.ws),
+                                           self.ws.numel(), _stream(stream)), "gs_info_gain_batch")
+        return o
+
+    def read_status(self) -> int:
+        flags = ctypes.c_uint32(0)
+        L.lib().gs_read_status(_ptr(self.status), ctypes.byref(flags))
+        return int(flags.value)
+
+    def grow_if_needed(self) -> bool:
+        """After a synchronised call: if pairs overflowed, double the capacity (returns True)."""
+        f = self.read_status()
+        if f & L.GS_FLAG_PAIR_OVERFLOW:
+            self.status.zero_()
+            self._alloc(min(2 * self.pair_capacity, (1 << 32) - 2))
+            return True
+        return False

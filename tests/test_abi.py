@@ -1,0 +1,129 @@
+"""Host-only checks of the C ABI (no GPU needed).
+
+- libgs103.so loads and exports every function declared in include/gs.h;
+- the ctypes structures match the C layouts field by field (checked against
+  offsetof/sizeof printed by a C program compiled from the header);
+- argument errors are rejected on the host before anything is enqueued.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2409_18122_gb300 import _lib as L
+from paper_2409_18122_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gs.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch  # noqa: F401  (loads the CUDA runtime the library links against)
+    B.build()
+    return L.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:gs_status|const char\*)\s+(gs_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in L.PROTOTYPES, n
+
+
+def test_struct_layouts_match_header(tmp_path):
+    structs = {
+        "gs_camera": L.gs_camera, "gs_map": L.gs_map, "gs_params": L.gs_params, "gs_proj": L.gs_proj,
+        "gs_bins": L.gs_bins, "gs_image": L.gs_image, "gs_image_grad": L.gs_image_grad, "gs_map_grad": L.gs_map_grad,
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gs.h"', "int main(void) {"]
+    for s, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (s, s))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (s, f, s, f))
+    lines.append("return 0; }")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)])
+    out = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().splitlines())
+    for s, cls in structs.items():
+        assert int(out[s]) == ctypes.sizeof(cls), s
+        for f, _ in cls._fields_:
+            assert int(out["%s.%s" % (s, f)]) == getattr(cls, f).offset, (s, f)
+
+
+def test_status_strings_and_version(lib):
+    assert lib.gs_version().decode().count(".") == 2
+    for code in range(7):
+        assert lib.gs_status_str(code).decode().startswith("GS_")
+
+
+def test_workspace_sizes(lib):
+    a = L.workspace_size(L.GS_OP_BIN_SORT, 1000, 2, 2000, 10_000, 100)
+    b = L.workspace_size(L.GS_OP_BIN_SORT, 1000, 2, 2000, 20_000, 100)
+    assert 0 < a < b and a % 256 == 0
+    assert L.workspace_size(L.GS_OP_RENDER_BWD, 10, 1, 10) >= 48 * 10
+    assert L.workspace_size(L.GS_OP_INFO_GAIN, 100, 3, 0, 1000, 64) > 0
+    out = ctypes.c_size_t(0)
+    assert lib.gs_workspace_size(99, 1, 1, 1, 1, 1, ctypes.byref(out)) == L.GS_ERR_ARG
+    assert lib.gs_workspace_size(0, -1, 1, 1, 1, 1, ctypes.byref(out)) == L.GS_ERR_ARG
+    assert lib.gs_workspace_size(0, 1, 1, 1, 1, 1, None) == L.GS_ERR_NULL
+
+
+def _params(**kw):
+    d = dict(tile_w=16, tile_h=16, eps2d=0.3, near_plane=0.2, guard=1.3, alpha_min=1 / 255, alpha_max=0.99, T_min=1e-4)
+    d.update(kw)
+    return L.gs_params(*d.values())
+
+
+def test_host_side_argument_errors(lib):
+    """Invalid arguments come back as status codes; nothing touches a device."""
+    fake = ctypes.c_void_p(0x10000)          # never dereferenced: validation fails first
+    m = L.gs_map(fake, fake, fake, fake, 10)
+    prm = _params()
+    proj = L.gs_proj(10, fake, fake, fake, fake, fake, fake, fake, fake, fake, fake)
+    P = ctypes.byref
+    # null map / cameras / params
+    assert lib.gs_project(None, fake, 1, P(prm), P(proj), fake, 1 << 20, None) == L.GS_ERR_NULL
+    assert lib.gs_project(P(m), None, 1, P(prm), P(proj), fake, 1 << 20, None) == L.GS_ERR_NULL
+    assert lib.gs_project(P(m), fake, 1, None, P(proj), fake, 1 << 20, None) == L.GS_ERR_NULL
+    # bad counts
+    assert lib.gs_project(P(m), fake, 0, P(prm), P(proj), fake, 1 << 20, None) == L.GS_ERR_ARG
+    neg = L.gs_map(fake, fake, fake, fake, -1)
+    assert lib.gs_project(P(neg), fake, 1, P(prm), P(proj), fake, 1 << 20, None) == L.GS_ERR_ARG
+    # bad parameters
+    for bad in (_params(tile_w=10), _params(tile_w=128, tile_h=2), _params(near_plane=0.0), _params(alpha_max=0.0),
+                _params(alpha_min=1.0), _params(eps2d=-1.0), _params(T_min=1.0), _params(guard=float("nan"))):
+        assert lib.gs_project(P(m), fake, 1, P(bad), P(proj), fake, 1 << 20, None) == L.GS_ERR_ARG
+    # misaligned map pointer
+    mis = L.gs_map(ctypes.c_void_p(0x10004), fake, fake, fake, 10)
+    assert lib.gs_project(P(mis), fake, 1, P(prm), P(proj), fake, 1 << 20, None) == L.GS_ERR_ALIGN
+    # workspace too small / misaligned
+    assert lib.gs_project(P(m), fake, 1, P(prm), P(proj), fake, 8, None) == L.GS_ERR_WORKSPACE
+    assert lib.gs_project(P(m), fake, 1, P(prm), P(proj), ctypes.c_void_p(0x10010), 1 << 20, None) == L.GS_ERR_ALIGN
+    # bins capacity
+    bins = L.gs_bins(0, 10, fake, fake, fake, fake)
+    assert lib.gs_bin_sort(P(proj), fake, 1, P(prm), P(bins), fake, 1 << 30, None) == L.GS_ERR_ARG
+    # info gain: unknown mode, null output
+    assert lib.gs_info_gain_batch(P(m), fake, 1, P(prm), 7, fake, fake, 100, 10, fake, 1 << 30, None) == L.GS_ERR_ARG
+    assert lib.gs_info_gain_batch(P(m), fake, 1, P(prm), 0, None, fake, 100, 10, fake, 1 << 30, None) == L.GS_ERR_NULL
+    # read_status: null
+    f = ctypes.c_uint32(0)
+    assert lib.gs_read_status(None, P(f)) == L.GS_ERR_NULL
+
+
+def test_python_binding_raises_without_library(monkeypatch):
+    monkeypatch.setattr(L, "LIB_PATH", "/nonexistent/libgs103.so")
+    monkeypatch.setattr(L, "_lib", None)
+    with pytest.raises(L.GSError):
+        L.lib()
