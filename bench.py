@@ -1,0 +1,444 @@
+#!/usr/bin/env python
+"""Benchmark of the splatting hot path on one GB300 (or N replicas).
+
+One step = one mapping iteration (Eq. (2) of RT-GuIDE: render 4 keyframes of a
+500,000-Gaussian room map at 640x480, L1 colour + 0.1 L1 depth loss, hand-written
+adjoint, Adam update) followed by one batched information-gain pass (Eq. (nbv):
+256 candidate views, one third each at 80x60 / 160x120 / 320x240, over a
+1,000,000-Gaussian room map).  Inputs are seeded synthetic scenes shaped like the
+paper's onboard maps (the paper's iTHOR / MP3D scenes are not available).
+
+Printed: ONE JSON line.  `value` is candidate views/s of the batched pass
+(256 / device time of the pass); `fwd_bwd` carries mapping iterations/s of the
+500k-Gaussian step.  Both are measured with CUDA events on the launching stream
+over exactly --steps steps after --warmup untimed steps; an L2 flush (a 256 MB
+write) separates every timed part and is not timed.  `e2e` repeats the loop
+through the public API with the inputs copied each step from pinned host
+memory and the results read back.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (candidates 0 and 1 per step, 80x60 and 160x120,
+scaled to the 256-view resolution mix by pixel count).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "candidate views/sec (batched info-gain) and fwd+bwd iters/sec at 500k Gaussians"
+WORKLOAD = ("ig: 1,000,000 room Gaussians, 256 candidates (80x60/160x120/320x240 thirds); "
+            "map: 500,000 room Gaussians, 4 keyframes 640x480, fwd+bwd+Adam")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graph", type=int, default=1, help="capture the information-gain pass in a CUDA graph")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- workloads
+class MapStep:
+    """One mapping iteration on the 500k-Gaussian, 4-keyframe map."""
+
+    def __init__(self, gs, scenes):
+        import torch
+        self.torch = torch
+        self.gs = gs
+        sc = scenes.config2()
+        self.scene = sc
+        gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
+        self.frame = gs.Frame(gm.n, sc.cams)
+        tgt = gs.GaussianMapTensors.from_numpy(scenes.perturbed(sc.gmap, seed=2002))
+        while True:
+            self.frame.reset_status()
+            img = self.frame.forward(tgt)
+            torch.cuda.synchronize()
+            if not self.frame.grow_if_needed():
+                break
+        self.frame.check_status()
+        self.tgt_rgb = img["rgb"].clone()
+        self.tgt_depth = img["depth"].clone()
+        self.params = [t.clone().requires_grad_(True) for t in (gm.mo, gm.su, gm.q, gm.rgb)]
+        self.host = [t.detach().cpu().pin_memory() for t in self.params]
+        self.host_tgt = [self.tgt_rgb.cpu().pin_memory(), self.tgt_depth.cpu().pin_memory()]
+        self.opt = torch.optim.Adam(self.params, lr=1e-4, fused=True)
+        self.loss_host = torch.zeros(1, dtype=torch.float32).pin_memory()
+
+    def __call__(self):
+        gs, torch = self.gs, self.torch
+        self.opt.zero_grad(set_to_none=True)
+        rgb, depth, _ = gs.render(*self.params, self.frame)
+        loss = (rgb - self.tgt_rgb).abs().mean() + 0.1 * (depth - self.tgt_depth).abs().mean()
+        loss.backward()
+        self.opt.step()
+        return loss
+
+    def e2e(self):
+        """Host inputs -> device, step, loss -> host (all enqueued on the current stream)."""
+        with self.torch.no_grad():
+            for d, h in zip(self.params, self.host):
+                d.copy_(h, non_blocking=True)
+            self.tgt_rgb.copy_(self.host_tgt[0], non_blocking=True)
+            self.tgt_depth.copy_(self.host_tgt[1], non_blocking=True)
+        loss = self()
+        self.loss_host.copy_(loss.detach().reshape(1), non_blocking=True)
+
+    def h2d_bytes(self):
+        return sum(h.numel() * h.element_size() for h in self.host + self.host_tgt)
+
+
+class IGStep:
+    """The batched information-gain pass over 256 candidate views of a 1M-Gaussian map."""
+
+    def __init__(self, gs, scenes, graph: bool):
+        import torch
+        self.torch = torch
+        self.gs = gs
+        sc = scenes.config3()
+        self.scene = sc
+        self.gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
+        self.ig = gs.InfoGain(self.gm.n, sc.cams)
+        while True:
+            self.ig.status.zero_()
+            self.ig(self.gm)
+            torch.cuda.synchronize()
+            if not self.ig.grow_if_needed():
+                break
+        assert not (self.ig.read_status() & gs.L.GS_FLAG_ERROR_MASK)
+        self.out = torch.zeros(len(sc.cams), dtype=torch.float32, device="cuda")
+        self.host = [t.cpu().pin_memory() for t in (self.gm.mo, self.gm.su, self.gm.q, self.gm.rgb)]
+        self.host_cams = self.ig.cams_dev.cpu().pin_memory()
+        self.out_host = torch.zeros(len(sc.cams), dtype=torch.float32).pin_memory()
+        self.graph = None
+        self.kernels_per_replay = 0
+        if graph:
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                self.ig(self.gm, self.out)
+            torch.cuda.current_stream().wait_stream(s)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            k0 = gs.L.lib().gs_kernel_launches()
+            with torch.cuda.graph(g):
+                self.ig(self.gm, self.out)
+            self.kernels_per_replay = int(gs.L.lib().gs_kernel_launches() - k0)
+            self.graph = g
+
+    @property
+    def n_views(self):
+        return len(self.scene.cams)
+
+    def __call__(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.ig(self.gm, self.out)
+        return self.out
+
+    def e2e(self):
+        with self.torch.no_grad():
+            for d, h in zip((self.gm.mo, self.gm.su, self.gm.q, self.gm.rgb), self.host):
+                d.copy_(h, non_blocking=True)
+            self.ig.cams_dev.copy_(self.host_cams, non_blocking=True)
+        self()
+        self.out_host.copy_(self.out, non_blocking=True)
+
+    def h2d_bytes(self):
+        return sum(h.numel() * h.element_size() for h in self.host) + self.host_cams.numel()
+
+
+# ----------------------------------------------------------------------------- timing loops
+def timed_loop(torch, steps, parts, flush):
+    """Per part: list of per-step device milliseconds (events on the current stream)."""
+    ev = {name: [] for name, _ in parts}
+    st = torch.cuda.current_stream()
+    for _ in range(steps):
+        for name, fn in parts:
+            flush()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            ev[name].append((e0, e1))
+    torch.cuda.synchronize()
+    return {name: [a.elapsed_time(b) for a, b in lst] for name, lst in ev.items()}
+
+
+def work_stats(torch, gs, mstep):
+    """Pairs, records and evaluated / contributing (pixel, Gaussian) counts of one mapping forward."""
+    fr = mstep.frame
+    gm = gs.GaussianMapTensors(*(p.detach() for p in mstep.params))
+    img = fr.new_images(with_counts=True)
+    fr.forward(gm, img)
+    torch.cuda.synchronize()
+    return dict(pairs=int(fr.pair_count.item()) & 0xFFFFFFFF, records=int(fr.rec_count.item()),
+                evaluated=int(img["last"].to(torch.int64).sum().item()),
+                contributing=int(img["n_contrib"].to(torch.int64).sum().item()),
+                pixels=fr.n_pixels, tiles=fr.n_tiles)
+
+
+def mix_pixels_per_view(cams):
+    return sum(c.width * c.height for c in cams) / len(cams)
+
+
+def oracle_sample(sc3):
+    """IG of candidates 0 (80x60) and 1 (160x120) by the oracle; returns (seconds, pixels)."""
+    from oracle import oracle as O
+    cams = [sc3.cams[0], sc3.cams[1]]
+    t0 = time.perf_counter()
+    O.info_gain(sc3.gmap, cams)
+    return time.perf_counter() - t0, sum(c.width * c.height for c in cams)
+
+
+def cpu_baseline(sc3):
+    """The FP64 oracle, as it stands, on the host cores (bounded sample, scaled per pixel)."""
+    from oracle import oracle as O
+    t, px = oracle_sample(sc3)
+    value = px / t / mix_pixels_per_view(sc3.cams)
+    return {"value": value, "unit": "views/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": "FP64 brute-force information gain of candidates 0 (80x60) and 1 (160x120) over the full "
+                      "1M-Gaussian map (%.1f s for %d pixels), scaled to the 256-view mix by pixel count "
+                      "(%.0f pixels per view)" % (t, px, mix_pixels_per_view(sc3.cams))}
+
+
+# ----------------------------------------------------------------------------- arms
+def run_ours(args):
+    import torch
+    from paper_2409_18122_gb300 import build as B
+    B.build()
+    from paper_2409_18122_gb300 import gs, scenes
+
+    rank, world, local = dist_setup()
+    torch.backends.cuda.matmul.allow_tf32 = False
+    mstep = MapStep(gs, scenes)
+    istep = IGStep(gs, scenes, graph=bool(args.graph))
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = lambda: flush_buf.fill_(1.0)
+    parts = [("map", mstep), ("ig", istep)]
+
+    for _ in range(args.warmup):
+        for _, fn in parts:
+            fn()
+    torch.cuda.synchronize()
+
+    # stage-level events inside the mapping step (entry points of the C ABI)
+    gs.TIMER = gs.StageTimer()
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    k0 = gs.L.lib().gs_kernel_launches()
+    times = timed_loop(torch, args.steps, parts, flush)
+    torch.cuda.synchronize()
+    launches = int(gs.L.lib().gs_kernel_launches() - k0) + args.steps * istep.kernels_per_replay
+    barrier(world)
+    clocks = sampler.stop()
+    stage_ms = {k: statistics.mean(gs.TIMER.durations_ms(k)) for k in list(gs.TIMER.events)}
+    gs.TIMER = None
+
+    t_map = sum(times["map"]) / 1e3
+    t_ig = sum(times["ig"]) / 1e3
+    t_map_all = max_over_ranks(t_map, world)
+    t_ig_all = max_over_ranks(t_ig, world)
+    views = istep.n_views * args.steps * world
+    value = views / t_ig_all
+    fwd_bwd = args.steps * world / t_map_all
+    ms_per_step = (max_over_ranks(t_map + t_ig, world) / args.steps) * 1e3
+
+    e2e = None
+    if not args.no_e2e:
+        for _ in range(2):
+            mstep.e2e()
+            istep.e2e()
+        torch.cuda.synchronize()
+        et = timed_loop(torch, args.steps, [("map", mstep.e2e), ("ig", istep.e2e)], flush)
+        e_ig = max_over_ranks(sum(et["ig"]) / 1e3, world)
+        e_map = max_over_ranks(sum(et["map"]) / 1e3, world)
+        e2e = {"value": istep.n_views * args.steps * world / e_ig, "unit": "views/s",
+               "fwd_bwd_iters_per_s": args.steps * world / e_map,
+               "h2d_bytes_per_step": mstep.h2d_bytes() + istep.h2d_bytes(),
+               "d2h_bytes_per_step": 4 + 4 * istep.n_views}
+
+    ws = work_stats(torch, gs, mstep)
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    # dominant kernel of the step: the back-to-front adjoint replay (gs_render_bwd);
+    # algorithmic FP32 work: 10 instr per evaluated (pixel, entry) + 38 per contributing one
+    t_bwd = stage_ms.get("gs_render_bwd", float("nan")) / 1e3
+    instr = 10.0 * ws["evaluated"] + 38.0 * ws["contributing"]
+    achieved = instr / t_bwd / 1e12
+    peak = sms * 128 * sm_max * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": "gs_render_bwd (k_render_bwd + k_proj_adjoint)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: %d SMs x 128 FP32 lanes x %.0f MHz (max SM clock)" % (sms, sm_max)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(istep.scene)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "views_per_step": istep.n_views, "gaussians_ig": istep.gm.n,
+                       "gaussians_map": mstep.frame.n, "keyframes": len(mstep.scene.cams),
+                       "l2": "flushed (256 MB write) before every timed part", "parallelism": "replicas" if world > 1
+                       else "single GPU", "ig_cuda_graph": bool(args.graph)},
+            "fwd_bwd": {"value": fwd_bwd, "unit": "iters/s", "ms": t_map_all / args.steps * 1e3},
+            "ig_ms": t_ig_all / args.steps * 1e3,
+            "stages_ms": stage_ms,
+            "work": ws,
+            "e2e": e2e,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": launches,
+            "gpu": props.name,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The oracle on the host cores, on the same workload: 2 candidates per step, scaled per pixel."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2409_18122_gb300 import scenes
+    sc = scenes.config3()
+    for _ in range(args.warmup):
+        O.info_gain(sc.gmap, [sc.cams[0]])
+    t, px = 0.0, 0
+    for _ in range(args.steps):
+        dt, p = oracle_sample(sc)
+        t += dt
+        px += p
+    value = px / t / mix_pixels_per_view(sc.cams)
+    sample = ("FP64 brute-force information gain of candidates 0 (80x60) and 1 (160x120) of the 256 over the "
+              "1M-Gaussian map per step, scaled to the 256-view mix by pixel count")
+    line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD}, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "views/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

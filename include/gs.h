@@ -187,14 +187,16 @@ gs_status gs_bin_sort(const gs_proj* proj, const gs_camera* cams, int32_t n_view
  *   unc   [sum_v P_v]    sum_i w_i u_i        (uncertainty channel)
  *   T     [sum_v P_v]    final transmittance prod_i (1 - alpha_i)
  *   last  [sum_v P_v]    1 + position (within the tile's range) of the last Gaussian added, 0 if none
- * Any of rgb/depth/unc may be NULL to skip writing it; T and last are
- * required when the images will be differentiated (gs_render_bwd). */
+ *   n_contrib [sum_v P_v] number of Gaussians added (work statistics)
+ * Any of rgb/depth/unc/n_contrib may be NULL to skip writing it; T and last
+ * are required when the images will be differentiated (gs_render_bwd). */
 typedef struct {
   float* rgb;
   float* depth;
   float* unc;
   float* T;
   int32_t* last;
+  int32_t* n_contrib;
 } gs_image;
 
 /* gs_render_fwd -- Sec. III front-to-back compositing.  For every pixel p and
@@ -279,6 +281,11 @@ const char* gs_status_str(gs_status s);
 
 /* Library version, "major.minor.patch" (static string, HOST). */
 const char* gs_version(void);
+
+/* Number of kernels this library has enqueued since it was loaded (HOST, all
+ * devices and threads).  Kernels replayed from a captured CUDA graph are not
+ * re-counted: a graph replay re-runs the kernels counted while capturing. */
+uint64_t gs_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -51,7 +51,8 @@ class gs_bins(ctypes.Structure):
 
 
 class gs_image(ctypes.Structure):
-    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("unc", c_void_p), ("T", c_void_p), ("last", c_void_p)]
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("unc", c_void_p), ("T", c_void_p), ("last", c_void_p),
+                ("n_contrib", c_void_p)]
 
 
 class gs_image_grad(ctypes.Structure):
@@ -82,6 +83,7 @@ PROTOTYPES = {
     "gs_read_status": (c_int32, [c_void_p, POINTER(c_uint32)]),
     "gs_status_str": (ctypes.c_char_p, [c_int32]),
     "gs_version": (ctypes.c_char_p, []),
+    "gs_kernel_launches": (ctypes.c_uint64, []),
 }
 
 _lib = None

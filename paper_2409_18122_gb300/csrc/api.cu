@@ -3,9 +3,15 @@
 // caller's stream.  Nothing here allocates, synchronises or prints.
 #include <stdint.h>
 
+#include <atomic>
+
 #include "gs_internal.h"
 
 namespace gs {
+
+static std::atomic<uint64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 int device_sm_count() {
   static int cached[64] = {0};
@@ -194,5 +200,7 @@ const char* gs_status_str(gs_status s) {
 }
 
 const char* gs_version(void) { return "0.1.0"; }
+
+uint64_t gs_kernel_launches(void) { return launch_count(); }
 
 }  // extern "C"

@@ -140,9 +140,11 @@ cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_vi
   const uint32_t* srec = in_a ? rv_a : rv_b;
   // 2. pair counts and offsets in depth order
   k_pair_counts<<<grid_for(rec_cap), kBlock, 0, st>>>(proj, srec, cnt);
+  note_launch();
   e = scan_exclusive(cnt, off, proj.count, rec_cap, &ctr[0], tmp, st);
   if (e != cudaSuccess) return e;
   k_pair_total<<<1, 1, 0, st>>>(&ctr[0], pair_cap, out.count, &ctr[1], proj.status);
+  note_launch();
   // 3. emission into whichever buffer makes the final pass land in `out`
   const int bits = bits_for(tile_cap);
   const int passes = sort_passes(0, bits);
@@ -150,13 +152,16 @@ cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_vi
   if (passes % 2 == 0) pb = SortBufs{out.tile, out.rec, pk_w, pv_w};
   else pb = SortBufs{pk_w, pv_w, out.tile, out.rec};
   k_emit<<<grid_for(rec_cap), kBlock, 0, st>>>(proj, cams, p.tile_w, srec, off, pair_cap, pb.keys_a, pb.vals_a);
+  note_launch();
   // 4. pairs by global tile id
   e = radix_sort(pb.keys_a, nullptr, pb.vals_a, pb, &ctr[1], pair_cap, 0, bits, tmp, st, &in_a);
   if (e != cudaSuccess) return e;
   // 5. ranges
   k_zero_u32<<<grid_for(2 * tile_cap), kBlock, 0, st>>>(out.ranges, 2 * tile_cap);
+  note_launch();
   k_ranges<<<grid_for(pair_cap), kBlock, 0, st>>>(out.tile, &ctr[1], pair_cap, tile_cap, proj.view_info, n_views,
                                                   out.ranges, proj.status);
+  note_launch();
   return cudaGetLastError();
 }
 

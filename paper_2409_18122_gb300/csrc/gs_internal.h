@@ -29,6 +29,10 @@ struct Carver {
 
 int device_sm_count();
 
+// Host-side count of kernel launches enqueued by this library (work accounting).
+void note_launch();
+uint64_t launch_count();
+
 // ------------------------------------------------------------------ scan
 // Exclusive prefix sum of n uint32 values into out[0..n]; out[n] = total.
 // n = min(*n_dev, n_cap) when n_dev != NULL, else n_cap.  Prefixes saturate at

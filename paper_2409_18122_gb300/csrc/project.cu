@@ -151,12 +151,20 @@ cudaError_t launch_project(const gs_map& map, const gs_camera* cams, int n_views
   uint32_t* counts = c.take<uint32_t>((size_t)map.n + 1);
   void* scan_tmp = c.take<char>(scan_temp_bytes(map.n));
   k_view_info<<<1, 1024, 0, st>>>(cams, n_views, p.tile_w, p.tile_h, out.view_info, out.status);
+  note_launch();
   const int64_t blocks = (map.n + kBlock - 1) / kBlock;
-  if (blocks > 0) k_project<false><<<(unsigned)blocks, kBlock, 0, st>>>(map, cams, n_views, p, out.view_info, counts, out);
+  if (blocks > 0) {
+    k_project<false><<<(unsigned)blocks, kBlock, 0, st>>>(map, cams, n_views, p, out.view_info, counts, out);
+    note_launch();
+  }
   cudaError_t e = scan_exclusive(counts, out.g_first, nullptr, map.n, nullptr, scan_tmp, st);
   if (e != cudaSuccess) return e;
-  if (blocks > 0) k_project<true><<<(unsigned)blocks, kBlock, 0, st>>>(map, cams, n_views, p, out.view_info, counts, out);
+  if (blocks > 0) {
+    k_project<true><<<(unsigned)blocks, kBlock, 0, st>>>(map, cams, n_views, p, out.view_info, counts, out);
+    note_launch();
+  }
   k_record_count<<<1, 1, 0, st>>>(out, map.n);
+  note_launch();
   return cudaGetLastError();
 }
 

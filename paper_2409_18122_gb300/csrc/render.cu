@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(1024) k_render_fwd(gs_map map, gs_proj proj, g
   const bool inside = px < ti.W && py < ti.H;
   const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
   float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, cd = 0.f, cu = 0.f;
-  int32_t last = 0;
+  int32_t last = 0, n_contrib = 0;
   bool done = !inside;
   const uint32_t beg = ti.beg, end = ti.end;
   for (uint32_t c0 = beg; c0 < end; c0 += B) {
@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(1024) k_render_fwd(gs_map map, gs_proj proj, g
       cu += w * k.w;
       T = Tn;
       last = (int32_t)(c0 - beg) + j + 1;
+      ++n_contrib;
     }
   }
   if (!inside) return;
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(1024) k_render_fwd(gs_map map, gs_proj proj, g
   if (img.unc) img.unc[o] = cu;
   if (img.T) img.T[o] = T;
   if (img.last) img.last[o] = last;
+  if (img.n_contrib) img.n_contrib[o] = n_contrib;
 }
 
 // Persistent U-only compositing: blocks take (view, tile) work items from a
@@ -173,6 +175,7 @@ cudaError_t launch_render_fwd(const gs_map& map, const gs_proj& proj, const gs_b
   }
   if (bins.tile_capacity > 0)
     k_render_fwd<<<(unsigned)bins.tile_capacity, B, smem, st>>>(map, proj, bins, cams, n_views, p, img);
+    note_launch();
   return cudaGetLastError();
 }
 
@@ -233,6 +236,7 @@ cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_vie
   e = launch_bin_sort(proj, cams, n_views, p, bins, inner, st);
   if (e != cudaSuccess) return e;
   k_zero_words<<<1, 32, 0, st>>>(work, 4);
+  note_launch();
   const int B = p.tile_w * p.tile_h;
   const size_t smem = 2 * sizeof(float4) * B;
   int per_sm = 0;
@@ -243,7 +247,9 @@ cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_vie
   if (grid > tile_cap) grid = tile_cap;
   if (grid < 1) grid = 1;
   k_ig_tiles<<<(unsigned)grid, B, smem, st>>>(proj, bins, cams, n_views, p, tile_sum, work);
+  note_launch();
   k_ig_views<<<n_views, 256, 0, st>>>(proj.view_info, cams, n_views, tile_sum, tile_cap, ig_out);
+  note_launch();
   return cudaGetLastError();
 }
 

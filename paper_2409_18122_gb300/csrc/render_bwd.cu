@@ -275,6 +275,7 @@ cudaError_t launch_render_bwd(const gs_map& map, const gs_proj& proj, const gs_b
   if (zb > 4096) zb = 4096;
   if (zb < 1) zb = 1;
   k_zero_g2d<<<(unsigned)zb, 256, 0, st>>>(g2d, proj.count, proj.capacity);
+  note_launch();
   const int B = p.tile_w * p.tile_h;
   const size_t smem = 3 * sizeof(float4) * B + sizeof(uint32_t) * B;
   static bool attr[64] = {false};
@@ -287,7 +288,11 @@ cudaError_t launch_render_bwd(const gs_map& map, const gs_proj& proj, const gs_b
   }
   if (bins.tile_capacity > 0)
     k_render_bwd<<<(unsigned)bins.tile_capacity, B, smem, st>>>(map, proj, bins, cams, n_views, p, fwd, g, g2d);
-  if (map.n > 0) k_proj_adjoint<<<(unsigned)((map.n + 255) / 256), 256, 0, st>>>(map, proj, cams, g2d, out);
+    note_launch();
+  if (map.n > 0) {
+    k_proj_adjoint<<<(unsigned)((map.n + 255) / 256), 256, 0, st>>>(map, proj, cams, g2d, out);
+    note_launch();
+  }
   return cudaGetLastError();
 }
 

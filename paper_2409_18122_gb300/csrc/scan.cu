@@ -148,8 +148,11 @@ cudaError_t scan_exclusive(const uint32_t* in, uint32_t* out, const uint32_t* n_
   const int g = (int)parts_for(n_cap);
   auto* partial = (unsigned long long*)temp;
   k_scan_reduce<<<g, kBlock, 0, st>>>(in, n_dev, n_cap, partial);
+  note_launch();
   k_scan_partials<<<1, 1024, 0, st>>>(partial, g, n_dev, n_cap, out, total_out);
+  note_launch();
   k_scan_down<<<g, kBlock, 0, st>>>(in, out, n_dev, n_cap, partial);
+  note_launch();
   return cudaGetLastError();
 }
 

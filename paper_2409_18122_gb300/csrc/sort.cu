@@ -231,8 +231,11 @@ cudaError_t radix_sort(const uint32_t* keys_in, const uint32_t* /*key_src*/, con
     uint32_t* kout = (p % 2 == 0) ? b.keys_b : b.keys_a;
     uint32_t* vout = (p % 2 == 0) ? b.vals_b : b.vals_a;
     k_upsweep<<<g, kBlock, 0, st>>>(kin, n_dev, n_cap, shift, hist);
+    note_launch();
     k_scan_hist<<<1, 1024, 0, st>>>(hist, g, digit_base);
+    note_launch();
     k_downsweep<<<g, kBlock, kDownSmem, st>>>(kin, vin, kout, vout, n_dev, n_cap, shift, hist, digit_base);
+    note_launch();
     kin = kout;
     vin = vout;
   }

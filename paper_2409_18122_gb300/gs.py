@@ -38,6 +38,44 @@ class RenderParams:
                            self.alpha_max, self.T_min)
 
 
+class StageTimer:
+    """Optional CUDA-event bracketing of every C-ABI call (for measurement only).
+
+    When `gs.TIMER` is a StageTimer, each entry point call records a start and
+    an end event on the stream it is launched on; `durations_ms(name)` returns
+    the per-call device times after a synchronise.
+    """
+
+    def __init__(self):
+        self.events = {}
+
+    def bracket(self, name, stream):
+        s = torch.cuda.current_stream() if stream is None else stream
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        self.events.setdefault(name, []).append((e0, e1))
+        return s, e0, e1
+
+    def durations_ms(self, name):
+        return [a.elapsed_time(b) for a, b in self.events.get(name, [])]
+
+    def clear(self):
+        self.events = {}
+
+
+TIMER: Optional[StageTimer] = None
+
+
+def _timed(name, stream, fn):
+    if TIMER is None:
+        return fn()
+    s, e0, e1 = TIMER.bracket(name, stream)
+    e0.record(s)
+    r = fn()
+    e1.record(s)
+    return r
+
+
 def _ptr(t: Optional[torch.Tensor]):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
@@ -156,31 +194,35 @@ class Frame:
         if gmap.n != self.n:
             raise ValueError("map has %d Gaussians, frame was built for %d" % (gmap.n, self.n))
         m = gmap.c()
-        L.check(L.lib().gs_project(ctypes.byref(m), _ptr(self.cams_dev), self.V, ctypes.byref(self.c_params),
-                                   ctypes.byref(self.c_proj), _ptr(self.ws), self.ws.numel(), _stream(stream)),
-                "gs_project")
+        _timed("gs_project", stream, lambda: L.check(
+            L.lib().gs_project(ctypes.byref(m), _ptr(self.cams_dev), self.V, ctypes.byref(self.c_params),
+                               ctypes.byref(self.c_proj), _ptr(self.ws), self.ws.numel(), _stream(stream)),
+            "gs_project"))
 
     def bin_sort(self, stream=None):
-        L.check(L.lib().gs_bin_sort(ctypes.byref(self.c_proj), _ptr(self.cams_dev), self.V,
-                                    ctypes.byref(self.c_params), ctypes.byref(self.c_bins), _ptr(self.ws),
-                                    self.ws.numel(), _stream(stream)), "gs_bin_sort")
+        _timed("gs_bin_sort", stream, lambda: L.check(
+            L.lib().gs_bin_sort(ctypes.byref(self.c_proj), _ptr(self.cams_dev), self.V, ctypes.byref(self.c_params),
+                                ctypes.byref(self.c_bins), _ptr(self.ws), self.ws.numel(), _stream(stream)),
+            "gs_bin_sort"))
 
-    def new_images(self, with_rgb=True, with_depth=True, with_unc=True):
+    def new_images(self, with_rgb=True, with_depth=True, with_unc=True, with_counts=False):
         d, P = self.device, self.n_pixels
         return dict(rgb=torch.empty(3 * P, dtype=torch.float32, device=d) if with_rgb else None,
                     depth=torch.empty(P, dtype=torch.float32, device=d) if with_depth else None,
                     unc=torch.empty(P, dtype=torch.float32, device=d) if with_unc else None,
                     T=torch.empty(P, dtype=torch.float32, device=d),
-                    last=torch.empty(P, dtype=torch.int32, device=d))
+                    last=torch.empty(P, dtype=torch.int32, device=d),
+                    n_contrib=torch.empty(P, dtype=torch.int32, device=d) if with_counts else None)
 
     def render_fwd(self, gmap: GaussianMapTensors, images=None, stream=None):
         img = self.new_images() if images is None else images
         c_img = L.gs_image(_ptr(img["rgb"]), _ptr(img["depth"]), _ptr(img["unc"]), _ptr(img["T"]),
-                           _ptr(img["last"]))
+                           _ptr(img["last"]), _ptr(img.get("n_contrib")))
         m = gmap.c()
-        L.check(L.lib().gs_render_fwd(ctypes.byref(m), ctypes.byref(self.c_proj), ctypes.byref(self.c_bins),
-                                      _ptr(self.cams_dev), self.V, ctypes.byref(self.c_params), ctypes.byref(c_img),
-                                      _stream(stream)), "gs_render_fwd")
+        _timed("gs_render_fwd", stream, lambda: L.check(
+            L.lib().gs_render_fwd(ctypes.byref(m), ctypes.byref(self.c_proj), ctypes.byref(self.c_bins),
+                                  _ptr(self.cams_dev), self.V, ctypes.byref(self.c_params), ctypes.byref(c_img),
+                                  _stream(stream)), "gs_render_fwd"))
         return img
 
     def render_bwd(self, gmap: GaussianMapTensors, images, d_rgb=None, d_depth=None, grads=None, stream=None):
@@ -189,14 +231,15 @@ class Frame:
             g = {k: torch.empty((self.n, 4), dtype=torch.float32, device=self.device) for k in
                  ("dmo", "dsu", "dq", "drgb")}
         c_img = L.gs_image(_ptr(images["rgb"]), _ptr(images["depth"]), _ptr(images["unc"]), _ptr(images["T"]),
-                           _ptr(images["last"]))
+                           _ptr(images["last"]), None)
         c_g = L.gs_image_grad(_ptr(d_rgb), _ptr(d_depth))
         c_out = L.gs_map_grad(_ptr(g["dmo"]), _ptr(g["dsu"]), _ptr(g["dq"]), _ptr(g["drgb"]))
         m = gmap.c()
-        L.check(L.lib().gs_render_bwd(ctypes.byref(m), ctypes.byref(self.c_proj), ctypes.byref(self.c_bins),
-                                      ctypes.byref(c_img), ctypes.byref(c_g), _ptr(self.cams_dev), self.V,
-                                      ctypes.byref(self.c_params), ctypes.byref(c_out), _ptr(self.ws),
-                                      self.ws.numel(), _stream(stream)), "gs_render_bwd")
+        _timed("gs_render_bwd", stream, lambda: L.check(
+            L.lib().gs_render_bwd(ctypes.byref(m), ctypes.byref(self.c_proj), ctypes.byref(self.c_bins),
+                                  ctypes.byref(c_img), ctypes.byref(c_g), _ptr(self.cams_dev), self.V,
+                                  ctypes.byref(self.c_params), ctypes.byref(c_out), _ptr(self.ws), self.ws.numel(),
+                                  _stream(stream)), "gs_render_bwd"))
         return g
 
     def forward(self, gmap: GaussianMapTensors, images=None, stream=None):
@@ -241,7 +284,7 @@ class Frame:
             d = {}
             if img.get("rgb") is not None:
                 d["rgb"] = img["rgb"][3 * p0:3 * (p0 + P)].view(3, c.height, c.width)
-            for k in ("depth", "unc", "T", "last"):
+            for k in ("depth", "unc", "T", "last", "n_contrib"):
                 if img.get(k) is not None:
                     d[k] = img[k][p0:p0 + P].view(c.height, c.width)
             out.append(d)
@@ -292,7 +335,7 @@ class InfoGain:
         _, _, tile_base, _ = tile_grid(self.cams, params)
         self.n_tiles = max(int(tile_base[-1]), 1)
         if pair_capacity is None:
-            pair_capacity = min(max(1 << 20, 4 * self.n * self.V), (1 << 31) - 1)
+            pair_capacity = min(max(1 << 20, 2 * self.n * self.V), (1 << 31) - 1)
         self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
         self.out = torch.zeros(self.V, dtype=torch.float32, device=self.device)
         self._alloc(int(pair_capacity))
@@ -307,10 +350,11 @@ class InfoGain:
     def __call__(self, gmap: GaussianMapTensors, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
         o = self.out if out is None else out
         m = gmap.c()
-        L.check(L.lib().gs_info_gain_batch(ctypes.byref(m), _ptr(self.cams_dev), self.V,
-                                           ctypes.byref(self.c_params), L.GS_IG_RENDER_MEAN, _ptr(o),
-                                           _ptr(self.status), self.pair_capacity, self.n_tiles, _ptr(self.ws),
-                                           self.ws.numel(), _stream(stream)), "gs_info_gain_batch")
+        _timed("gs_info_gain_batch", stream, lambda: L.check(
+            L.lib().gs_info_gain_batch(ctypes.byref(m), _ptr(self.cams_dev), self.V, ctypes.byref(self.c_params),
+                                       L.GS_IG_RENDER_MEAN, _ptr(o), _ptr(self.status), self.pair_capacity,
+                                       self.n_tiles, _ptr(self.ws), self.ws.numel(), _stream(stream)),
+            "gs_info_gain_batch"))
         return o
 
     def read_status(self) -> int:
