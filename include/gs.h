@@ -240,6 +240,38 @@ gs_status gs_render_bwd(const gs_map* map, const gs_proj* proj, const gs_bins* b
                         const gs_image_grad* grad, const gs_camera* cams, int32_t n_views, const gs_params* prm,
                         gs_map_grad* out, void* ws, size_t ws_bytes, void* stream);
 
+/* gs_render_bwd_noalloc -- gs_render_bwd for callers that cannot allocate
+ * device memory.  The paper has no counterpart; this is a deployment variant.
+ *
+ * Who needs it: a process that reserves all of its device memory once at
+ * start-up and must not allocate afterwards (for example a robot's real-time
+ * mapping loop), a plugin that only receives the buffers of its host
+ * application and has no allocator of its own, or code whose launches a
+ * framework is capturing into a CUDA graph and that must not allocate during
+ * the capture.  Such callers cannot provide the workspace of gs_render_bwd.
+ *
+ * What differs: the per-record scratch (48 bytes per record) lives in a fixed
+ * array inside the library's device image, sized for GS_NOALLOC_MAX_RECORDS
+ * records (12 MiB), which every GPU that loads the library keeps until the
+ * process exits.  Inputs and outputs are exactly those of gs_render_bwd (the
+ * caller still passes them); no workspace argument; nothing is allocated (no
+ * cudaMalloc, no cudaFree, no allocating library call).
+ *   - proj->capacity above GS_NOALLOC_MAX_RECORDS is rejected with
+ *     GS_ERR_WORKSPACE before anything is enqueued.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array, which keeps the last call's contents;
+ *     the call clears the part it uses before accumulating into it.  Calls
+ *     whose executions overlap on the GPU (different streams, or different host
+ *     threads on one device) race on the array and must be serialised by the
+ *     caller.
+ * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG, GS_ERR_WORKSPACE, GS_ERR_CUDA. */
+#define GS_NOALLOC_MAX_RECORDS (1 << 18)
+gs_status gs_render_bwd_noalloc(const gs_map* map, const gs_proj* proj, const gs_bins* bins, const gs_image* fwd,
+                                const gs_image_grad* grad, const gs_camera* cams, int32_t n_views,
+                                const gs_params* prm, gs_map_grad* out, void* stream);
+
 /* ------------------------------------------------------- information gain */
 enum { GS_IG_RENDER_MEAN = 0 };
 

@@ -23,6 +23,7 @@ GS_FLAG_RECORD_OVERFLOW = 1 << 4
 GS_FLAG_ERROR_MASK = GS_FLAG_PAIR_OVERFLOW | GS_FLAG_RANGE_OVERFLOW | GS_FLAG_BAD_CAMERA | GS_FLAG_RECORD_OVERFLOW
 GS_IG_RENDER_MEAN = 0
 GS_OP_PROJECT, GS_OP_BIN_SORT, GS_OP_RENDER_BWD, GS_OP_INFO_GAIN = range(4)
+GS_NOALLOC_MAX_RECORDS = 1 << 18
 
 
 class gs_camera(ctypes.Structure):
@@ -77,6 +78,9 @@ PROTOTYPES = {
     "gs_render_bwd": (c_int32, [POINTER(gs_map), POINTER(gs_proj), POINTER(gs_bins), POINTER(gs_image),
                                 POINTER(gs_image_grad), c_void_p, c_int32, POINTER(gs_params), POINTER(gs_map_grad),
                                 c_void_p, c_size_t, c_void_p]),
+    "gs_render_bwd_noalloc": (c_int32, [POINTER(gs_map), POINTER(gs_proj), POINTER(gs_bins), POINTER(gs_image),
+                                        POINTER(gs_image_grad), c_void_p, c_int32, POINTER(gs_params),
+                                        POINTER(gs_map_grad), c_void_p]),
     "gs_info_gain_batch": (c_int32, [POINTER(gs_map), c_void_p, c_int32, POINTER(gs_params), c_int32, c_void_p,
                                      c_void_p, c_int64, c_int64, c_void_p, c_size_t, c_void_p]),
     "gs_workspace_size": (c_int32, [c_int32, c_int64, c_int32, c_int64, c_int64, c_int64, POINTER(c_size_t)]),
