@@ -25,8 +25,9 @@
  *     word, which gs_read_status reads after the stream has been synchronised.
  *     Outputs of a call whose status carries GS_FLAG_PAIR_OVERFLOW or
  *     GS_FLAG_RANGE_OVERFLOW are incomplete and must be discarded.
- *   - Float4-typed arrays ([n][4] floats) must be 16-byte aligned; all other
- *     arrays 4-byte aligned; workspaces 256-byte aligned.
+ *   - Float4-typed arrays ([n][4] floats) must be 16-byte aligned, [n][2]
+ *     float and uint16 [n][4] arrays 8-byte aligned; all other arrays 4-byte
+ *     aligned; workspaces 256-byte aligned.
  *   - Rendering constants the paper leaves unstated are fields of gs_params.
  */
 #ifndef GS103_GS_H
@@ -90,7 +91,8 @@ typedef struct {
 } gs_map;
 
 /* Rendering constants (readings where the paper is silent).
- *   tile_w, tile_h  screen tile in pixels; tile_w * tile_h in {64,128,256,512,1024}, tile_w <= 64
+ *   tile_w, tile_h  screen tile in pixels: tile_w in {8, 16, 32, 64}, tile_h a multiple of 4,
+ *                   tile_w * tile_h in {64, 128, 256, 512, 1024} (one warp per 8x4 pixel block)
  *   eps2d           added to the diagonal of every 2D covariance (low-pass), px^2, >= 0
  *   near_plane      Gaussians with view depth <= near_plane are culled, > 0
  *   guard           centres with |t_x / t_z| > guard * (W/2) / f_x (same for y) are culled, > 0
@@ -105,9 +107,11 @@ typedef struct {
 
 /* ------------------------------------------------------------- projection */
 
-/* Projected records, one per visible (Gaussian, view), in ascending
- * (Gaussian id, view) order.  DEVICE buffers of `capacity` entries; capacity
- * >= n * n_views never overflows.
+/* Projected records, one per visible (Gaussian, view).  Order: Gaussians are
+ * taken in groups of 32 consecutive ids (group k = ids 32k .. 32k+31); records
+ * are ordered by (group, view, Gaussian id), so within one view they ascend in
+ * Gaussian id, and the records of one (group, view) are contiguous.  DEVICE
+ * buffers of `capacity` entries; capacity >= n * n_views never overflows.
  *   count      [1]        number of records written
  *   status     [1]        device status word (GS_FLAG_* bits), OR-ed by every call
  *   view_info  [V+1][2]   per view: (first global tile, first pixel); entry V holds the totals
@@ -116,7 +120,11 @@ typedef struct {
  *   conic_u    [cap][4]   (inverse 2D covariance a, b, c with q = a dx^2 + 2 b dx dy + c dy^2, u)
  *   rect       [cap][4]   uint16 tile rectangle (x0, y0, x1, y1), ends exclusive
  *   depth_key  [cap]      IEEE-754 bits of the float32 depth (the sort key)
- *   g_first    [n+1]      index of each Gaussian's first record; g_first[n] = count    */
+ *   ext        [cap][2]   support half-widths (sqrt(Q Sigma_2D,xx), sqrt(Q Sigma_2D,yy)) in pixels
+ *   grp_mask   [G*V]      bit i of entry (k, v) = Gaussian 32k+i is visible in view v (G = ceil(n/32))
+ *   grp_base   [G*V+1]    index of the first record of (group k, view v) at k*V + v; last entry = count
+ * The record of Gaussian g in view v is grp_base[k*V+v] + popcount(grp_mask[k*V+v] & ((1 << i) - 1))
+ * with k = g / 32, i = g % 32, if bit i is set. */
 typedef struct {
   int64_t capacity;
   uint32_t* count;
@@ -128,7 +136,9 @@ typedef struct {
   float* conic_u;
   uint16_t* rect;
   uint32_t* depth_key;
-  uint32_t* g_first;
+  float* ext;
+  uint32_t* grp_mask;
+  uint32_t* grp_base;
 } gs_proj;
 
 /* gs_project -- EWA projection of every Gaussian into every view (Sec. III
@@ -140,7 +150,7 @@ typedef struct {
  * mu_2D = (fx t_x/t_z + cx, fy t_y/t_z + cy); support box from
  * q <= Q = 2 ln(o / alpha_min): half-widths sqrt(Q Sigma_2D,xx), sqrt(Q Sigma_2D,yy),
  * clipped to the image and converted to tiles (cull if empty).
- * Records are written to `out` in (Gaussian, view) order.
+ * Records are written to `out` in (group of 32 Gaussians, view, Gaussian) order.
  * ws: DEVICE workspace of gs_workspace_size(GS_OP_PROJECT, ...) bytes.
  * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG (n < 0, n_views < 1,
  * n >= 2^32, bad params), GS_ERR_WORKSPACE, GS_ERR_CUDA; device flags

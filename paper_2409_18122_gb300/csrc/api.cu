@@ -31,7 +31,8 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 gs_status check_params(const gs_params* p) {
   if (!p) return GS_ERR_NULL;
   const int B = p->tile_w * p->tile_h;
-  if (p->tile_w < 1 || p->tile_h < 1 || p->tile_w > 64 || (B != 64 && B != 128 && B != 256 && B != 512 && B != 1024))
+  if ((p->tile_w != 8 && p->tile_w != 16 && p->tile_w != 32 && p->tile_w != 64) || p->tile_h < 4 ||
+      p->tile_h % 4 != 0 || (B != 64 && B != 128 && B != 256 && B != 512 && B != 1024))
     return GS_ERR_ARG;
   if (!(p->eps2d >= 0.f) || !(p->near_plane > 0.f) || !(p->guard > 0.f)) return GS_ERR_ARG;
   if (!(p->alpha_min >= 0.f && p->alpha_min < 1.f)) return GS_ERR_ARG;
@@ -59,12 +60,13 @@ gs_status check_views(const gs_camera* cams, int32_t n_views) {
 gs_status check_proj(const gs_proj* p) {
   if (!p) return GS_ERR_NULL;
   if (p->capacity < 0 || p->capacity >= ((int64_t)1 << 32) - 1) return GS_ERR_ARG;
-  if (!p->count || !p->status || !p->view_info || !p->g_first) return GS_ERR_NULL;
-  if (p->capacity > 0 && (!p->gid || !p->view || !p->xyod || !p->conic_u || !p->rect || !p->depth_key))
+  if (!p->count || !p->status || !p->view_info || !p->grp_mask || !p->grp_base) return GS_ERR_NULL;
+  if (p->capacity > 0 && (!p->gid || !p->view || !p->xyod || !p->conic_u || !p->rect || !p->depth_key || !p->ext))
     return GS_ERR_NULL;
-  if (!aligned(p->xyod, 16) || !aligned(p->conic_u, 16) || !aligned(p->rect, 8) || !aligned(p->gid, 4) ||
+  if (!aligned(p->xyod, 16) || !aligned(p->conic_u, 16) || !aligned(p->rect, 8) || !aligned(p->ext, 8) ||
+      !aligned(p->gid, 4) ||
       !aligned(p->view, 4) || !aligned(p->depth_key, 4) || !aligned(p->count, 4) || !aligned(p->status, 4) ||
-      !aligned(p->view_info, 4) || !aligned(p->g_first, 4))
+      !aligned(p->view_info, 4) || !aligned(p->grp_mask, 4) || !aligned(p->grp_base, 4))
     return GS_ERR_ALIGN;
   return GS_OK;
 }
@@ -72,7 +74,7 @@ gs_status check_proj(const gs_proj* p) {
 gs_status check_bins(const gs_bins* b) {
   if (!b) return GS_ERR_NULL;
   if (b->pair_capacity < 1 || b->pair_capacity >= ((int64_t)1 << 32) - 1) return GS_ERR_ARG;
-  if (b->tile_capacity < 1 || b->tile_capacity >= ((int64_t)1 << 31)) return GS_ERR_ARG;
+  if (b->tile_capacity < 1 || b->tile_capacity >= ((int64_t)1 << 27)) return GS_ERR_ARG;
   if (!b->count || !b->tile || !b->rec || !b->ranges) return GS_ERR_NULL;
   if (!aligned(b->count, 4) || !aligned(b->tile, 4) || !aligned(b->rec, 4) || !aligned(b->ranges, 8)) return GS_ERR_ALIGN;
   return GS_OK;
@@ -160,7 +162,7 @@ gs_status gs_info_gain_batch(const gs_map* map, const gs_camera* cams, int32_t n
   if (!ig_out || !status) return GS_ERR_NULL;
   if (!aligned(ig_out, 4) || !aligned(status, 4)) return GS_ERR_ALIGN;
   if (pair_capacity < 1 || pair_capacity >= ((int64_t)1 << 32) - 1) return GS_ERR_ARG;
-  if (tile_capacity < 1 || tile_capacity >= ((int64_t)1 << 31)) return GS_ERR_ARG;
+  if (tile_capacity < 1 || tile_capacity >= ((int64_t)1 << 27)) return GS_ERR_ARG;
   if (map->n * (int64_t)n_views >= ((int64_t)1 << 32) - 1) return GS_ERR_ARG;
   GS_TRY(check_ws(ws, ws_bytes, ig_ws_bytes(map->n, n_views, pair_capacity, tile_capacity)));
   return from_cuda(launch_info_gain(*map, cams, n_views, *prm, ig_out, status, pair_capacity, tile_capacity, ws,

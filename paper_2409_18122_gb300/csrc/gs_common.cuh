@@ -173,6 +173,7 @@ struct ViewProj {
   float mx, my;      // mu_2D
   float depth;       // t_z
   float ca, cb, cc;  // conic
+  float rx, ry;      // support half-widths in pixels
   int x0, y0, x1, y1;  // tile rect, ends exclusive
 };
 
@@ -225,6 +226,8 @@ __device__ __forceinline__ bool view_proj(float4 mo, const GaussPre& g, const Ca
   vp.y1 = (int)yhi / tile_h + 1;
   vp.mx = mux;
   vp.my = muy;
+  vp.rx = rx;
+  vp.ry = ry;
   vp.depth = tz;
   float idet = fdiv(1.0f, det);
   vp.ca = fmul(cc, idet);

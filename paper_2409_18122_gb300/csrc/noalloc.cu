@@ -59,8 +59,9 @@ extern "C" gs_status gs_render_bwd_noalloc(const gs_map* map, const gs_proj* pro
   if (proj->capacity < 0 || bins->pair_capacity < 1 || bins->tile_capacity < 1) return GS_ERR_ARG;
   if (proj->capacity > kMaxRecords) return GS_ERR_WORKSPACE;   // the fixed scratch is too small
   if (map->n > 0 && (!map->mo || !map->su || !map->q || !map->rgb)) return GS_ERR_NULL;
-  if (!proj->count || !proj->status || !proj->view_info || !proj->g_first || !proj->gid || !proj->view ||
-      !proj->xyod || !proj->conic_u || !bins->count || !bins->rec || !bins->ranges || !fwd->T || !fwd->last)
+  if (!proj->count || !proj->status || !proj->view_info || !proj->grp_mask || !proj->grp_base || !proj->gid ||
+      !proj->view ||
+      !proj->xyod || !proj->conic_u || !proj->ext || !bins->count || !bins->rec || !bins->ranges || !fwd->T || !fwd->last)
     return GS_ERR_NULL;
   if (map->n > 0 && (!out->dmo || !out->dsu || !out->dq || !out->drgb)) return GS_ERR_NULL;
   if (!aligned(map->mo, 16) || !aligned(map->su, 16) || !aligned(map->q, 16) || !aligned(map->rgb, 16) ||
@@ -68,8 +69,8 @@ extern "C" gs_status gs_render_bwd_noalloc(const gs_map* map, const gs_proj* pro
       !aligned(out->dq, 16) || !aligned(out->drgb, 16))
     return GS_ERR_ALIGN;
   const int B = prm->tile_w * prm->tile_h;
-  if (prm->tile_w < 1 || prm->tile_h < 1 || prm->tile_w > 64 ||
-      (B != 64 && B != 128 && B != 256 && B != 512 && B != 1024) || !(prm->alpha_max > 0.f && prm->alpha_max <= 1.f) ||
+  if ((prm->tile_w != 8 && prm->tile_w != 16 && prm->tile_w != 32 && prm->tile_w != 64) || prm->tile_h < 4 ||
+      prm->tile_h % 4 != 0 || (B != 64 && B != 128 && B != 256 && B != 512 && B != 1024) || !(prm->alpha_max > 0.f && prm->alpha_max <= 1.f) ||
       !(prm->alpha_min >= 0.f && prm->alpha_min < 1.f))
     return GS_ERR_ARG;
   void* scratch = nullptr;

@@ -6,9 +6,10 @@
 // Gaussian-major: one thread per Gaussian reads its 64 bytes of parameters once
 // (coalesced float4 SoA loads), computes the view-independent part (rotation,
 // 3D covariance, opacity, support bound) once, and loops over the cameras held
-// in shared memory.  Records are compacted in (Gaussian, view) order with two
-// passes (count, exclusive scan, write) so that the order is deterministic and
-// no block waits on another.
+// in shared memory.  Records are compacted in (group of 32 Gaussians, view,
+// Gaussian) order with two passes (count, exclusive scan, write), so the order is
+// deterministic, no block waits on another and every record store of a warp is
+// coalesced.
 #include "gs_common.cuh"
 #include "gs_internal.h"
 
@@ -82,13 +83,21 @@ __device__ __forceinline__ void stage_cams(const gs_camera* __restrict__ cams, c
   }
 }
 
+// One warp = one group of 32 consecutive Gaussians.  Count pass: per view, the
+// ballot of visible lanes is stored (grp_mask) and its popcount counted.  Write
+// pass: the visible lanes of a (group, view) write their records to consecutive
+// slots grp_base + rank, so every store instruction of the warp is contiguous.
 template <bool kWrite>
 __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera* __restrict__ cams, int n_views,
                                                      gs_params p, const uint32_t* __restrict__ view_info,
                                                      uint32_t* __restrict__ counts, gs_proj out) {
   __shared__ CamC s_cam[kMaxViewsPerChunk];
   const int64_t g = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t grp = g >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
   const bool active = g < map.n;
+  const bool grp_active = __any_sync(0xffffffffu, active);
   float4 mo = make_float4(0.f, 0.f, 0.f, 0.f), su = mo, q = mo;
   GaussPre pre;
   pre.valid = false;
@@ -100,21 +109,26 @@ __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera*
     if (!kWrite && !(finite4(mo) && isfinite(su.x) && isfinite(su.y) && isfinite(su.z) && finite4(q)))
       set_flag(out.status, GS_FLAG_NONFINITE);
   }
-  uint32_t n_vis = 0;
-  uint32_t dst = 0;
-  if (kWrite && active) dst = out.g_first[g];
   for (int v0 = 0; v0 < n_views; v0 += kMaxViewsPerChunk) {
     const int nv = min(kMaxViewsPerChunk, n_views - v0);
     __syncthreads();
     stage_cams(cams, view_info, v0, nv, p, s_cam);
     __syncthreads();
-    if (!active || !pre.valid) continue;
+    if (!grp_active) continue;
     for (int i = 0; i < nv; ++i) {
       const CamC& c = s_cam[i];
-      if (c.W <= 0) continue;
       ViewProj vp;
-      if (!view_proj(mo, pre, c, p.near_plane, p.eps2d, p.tile_w, p.tile_h, vp)) continue;
-      if (kWrite) {
+      const bool vis = active && pre.valid && c.W > 0 &&
+                       view_proj(mo, pre, c, p.near_plane, p.eps2d, p.tile_w, p.tile_h, vp);
+      const uint32_t m = __ballot_sync(0xffffffffu, vis);
+      const size_t slot = (size_t)grp * n_views + (v0 + i);
+      if (!kWrite) {
+        if (lane == 0) {
+          out.grp_mask[slot] = m;
+          counts[slot] = __popc(m);
+        }
+      } else if (vis) {
+        const uint32_t dst = out.grp_base[slot] + __popc(m & lt);
         if ((int64_t)dst < out.capacity) {
           out.gid[dst] = (uint32_t)g;
           out.view[dst] = (uint32_t)(v0 + i);
@@ -123,33 +137,32 @@ __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera*
           reinterpret_cast<ushort4*>(out.rect)[dst] =
               make_ushort4((unsigned short)vp.x0, (unsigned short)vp.y0, (unsigned short)vp.x1, (unsigned short)vp.y1);
           out.depth_key[dst] = __float_as_uint(vp.depth);
+          reinterpret_cast<float2*>(out.ext)[dst] = make_float2(vp.rx, vp.ry);
         }
-        ++dst;
-      } else {
-        ++n_vis;
       }
     }
   }
-  if (!kWrite && active) counts[g] = n_vis;
 }
 
-__global__ void k_record_count(const gs_proj out, int64_t n) {
-  const uint32_t total = out.g_first[n];
+__global__ void k_record_count(const gs_proj out, int64_t n_slots) {
+  const uint32_t total = out.grp_base[n_slots];
   *out.count = (int64_t)total > out.capacity ? (uint32_t)out.capacity : total;
   if ((int64_t)total > out.capacity) set_flag(out.status, GS_FLAG_RECORD_OVERFLOW);
 }
 
 }  // namespace
 
-size_t project_ws_bytes(int64_t n, int /*n_views*/) {
-  return align_up(sizeof(uint32_t) * (size_t)(n + 1), 256) + scan_temp_bytes(n);
+size_t project_ws_bytes(int64_t n, int n_views) {
+  const int64_t slots = ((n + 31) / 32) * (int64_t)n_views;
+  return align_up(sizeof(uint32_t) * (size_t)(slots + 1), 256) + scan_temp_bytes(slots);
 }
 
 cudaError_t launch_project(const gs_map& map, const gs_camera* cams, int n_views, const gs_params& p,
                            const gs_proj& out, void* ws, cudaStream_t st) {
+  const int64_t slots = ((map.n + 31) / 32) * (int64_t)n_views;
   Carver c(ws);
-  uint32_t* counts = c.take<uint32_t>((size_t)map.n + 1);
-  void* scan_tmp = c.take<char>(scan_temp_bytes(map.n));
+  uint32_t* counts = c.take<uint32_t>((size_t)slots + 1);
+  void* scan_tmp = c.take<char>(scan_temp_bytes(slots));
   k_view_info<<<1, 1024, 0, st>>>(cams, n_views, p.tile_w, p.tile_h, out.view_info, out.status);
   note_launch();
   const int64_t blocks = (map.n + kBlock - 1) / kBlock;
@@ -157,13 +170,13 @@ cudaError_t launch_project(const gs_map& map, const gs_camera* cams, int n_views
     k_project<false><<<(unsigned)blocks, kBlock, 0, st>>>(map, cams, n_views, p, out.view_info, counts, out);
     note_launch();
   }
-  cudaError_t e = scan_exclusive(counts, out.g_first, nullptr, map.n, nullptr, scan_tmp, st);
+  cudaError_t e = scan_exclusive(counts, out.grp_base, nullptr, slots, nullptr, scan_tmp, st);
   if (e != cudaSuccess) return e;
   if (blocks > 0) {
     k_project<true><<<(unsigned)blocks, kBlock, 0, st>>>(map, cams, n_views, p, out.view_info, counts, out);
     note_launch();
   }
-  k_record_count<<<1, 1, 0, st>>>(out, map.n);
+  k_record_count<<<1, 1, 0, st>>>(out, slots);
   note_launch();
   return cudaGetLastError();
 }

@@ -24,26 +24,30 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-__global__ void __launch_bounds__(1024) k_render_bwd(gs_map map, gs_proj proj, gs_bins bins,
-                                                      const gs_camera* __restrict__ cams, int n_views, gs_params p,
-                                                      gs_image fwd, gs_image_grad grad, float4* __restrict__ g2d) {
-  extern __shared__ float4 s_buf[];
-  const int B = blockDim.x;
-  float4* s_xyod = s_buf;
-  float4* s_con = s_buf + B;
-  float4* s_rgb = s_buf + 2 * B;
-  uint32_t* s_rec = reinterpret_cast<uint32_t*>(s_buf + 3 * B);
-  __shared__ TileInfo ti;
-  __shared__ int s_max_last;
-  const uint32_t tile = blockIdx.x;
-  if (threadIdx.x == 0) s_max_last = 0;
-  if (!tile_setup(proj, bins, cams, n_views, p, tile, ti)) return;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int px = ti.x0 + tid % p.tile_w, py = ti.y0 + tid / p.tile_w;
-  const bool inside = px < ti.W && py < ti.H;
-  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+constexpr int kBwdWarps = 2;   // warps (work items) per CTA
+
+__global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_proj proj, gs_bins bins,
+                                                                const gs_camera* __restrict__ cams, int n_views,
+                                                                gs_params p, gs_image fwd, gs_image_grad grad,
+                                                                float4* __restrict__ g2d, uint32_t n_items) {
+  __shared__ float4 s_stage[kBwdWarps][3][32];
+  __shared__ uint32_t s_rec[kBwdWarps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t item = blockIdx.x * kBwdWarps + warp;
+  if (item >= n_items) return;
+  const int wpt = warps_per_tile(p);
+  TileInfo ti;
+  if (!warp_tile_setup(proj, bins, cams, n_views, p, item / wpt, ti)) return;
+  WarpBlock wb;
+  warp_block(ti, p, (int)(item % wpt), wb);
+  float4* sx = s_stage[warp][0];
+  float4* sc = s_stage[warp][1];
+  float4* sr = s_stage[warp][2];
+  uint32_t* srec = s_rec[warp];
+  const bool inside = wb.px < ti.W && wb.py < ti.H;
+  const float pxc = (float)wb.px + 0.5f, pyc = (float)wb.py + 0.5f;
   const size_t P = (size_t)ti.W * ti.H;
-  const size_t pix = (size_t)py * ti.W + px;
+  const size_t pix = (size_t)wb.py * ti.W + wb.px;
   const size_t o = (size_t)ti.pix_base + pix;
   float T = 1.f, gr = 0.f, gg = 0.f, gb = 0.f, gd = 0.f;
   int last = 0;
@@ -57,30 +61,49 @@ __global__ void __launch_bounds__(1024) k_render_bwd(gs_map map, gs_proj proj, g
       gb = base[2 * P + pix];
     }
     if (grad.depth) gd = grad.depth[o];
-    atomicMax(&s_max_last, last);
   }
-  __syncthreads();
-  const int n_todo = s_max_last;
+  const int wlast = (int)__reduce_max_sync(0xffffffffu, (unsigned)last);
+  if (wlast == 0) return;
+  const uint32_t beg = ti.beg;
+  const float4* rgb = reinterpret_cast<const float4*>(map.rgb);
   float Sr = 0.f, Sg = 0.f, Sb = 0.f, Sd = 0.f;
-  for (int hi = n_todo; hi > 0; hi -= B) {
-    const int lo = hi - B > 0 ? hi - B : 0;
-    const int cnt = hi - lo;
-    __syncthreads();
-    if (tid < cnt) {
-      const uint32_t r = bins.rec[ti.beg + lo + tid];
-      s_rec[tid] = r;
-      s_xyod[tid] = __ldg(reinterpret_cast<const float4*>(proj.xyod) + r);
-      s_con[tid] = __ldg(reinterpret_cast<const float4*>(proj.conic_u) + r);
-      s_rgb[tid] = __ldg(reinterpret_cast<const float4*>(map.rgb) + proj.gid[r]);
+  // walk groups of 32 entries from the last one any lane used back to the first,
+  // loading the next (earlier) group while this one is processed
+  int g = ((wlast - 1) >> 5) << 5;
+  Entry nx;
+  float4 nrgb = make_float4(0.f, 0.f, 0.f, 0.f);
+  bool nv = g + lane < wlast;
+  if (nv) {
+    load_entry(proj, bins, beg + g + lane, nx);
+    nrgb = __ldg(rgb + __ldg(proj.gid + nx.rec));
+  }
+  for (; g >= 0; g -= 32) {
+    const Entry e = nx;
+    const float4 ergb = nrgb;
+    const bool ev = nv;
+    nv = g >= 32;
+    if (nv) {
+      load_entry(proj, bins, beg + g - 32 + lane, nx);
+      nrgb = __ldg(rgb + __ldg(proj.gid + nx.rec));
     }
-    __syncthreads();
-    for (int j = cnt - 1; j >= 0; --j) {
-      const int pos = lo + j;   // position in the tile's list
+    const bool ov = ev && box_overlaps(e.xyod, e.ext, wb);
+    uint32_t m = __ballot_sync(0xffffffffu, ov);
+    if (m == 0) continue;
+    if (ov) {
+      sx[lane] = e.xyod;
+      sc[lane] = e.con;
+      sr[lane] = ergb;
+      srec[lane] = e.rec;
+    }
+    __syncwarp();
+    while (m) {
+      const int b = 31 - __clz(m);
+      m ^= 1u << b;
+      const int pos = g + b;   // position in the tile's list
       bool contrib = inside && pos < last;
-      float a_ = 0.f, G = 0.f;
-      const float4 a = s_xyod[j];
-      const float4 k = s_con[j];
-      float dx = 0.f, dy = 0.f;
+      float a_ = 0.f, G = 0.f, dx = 0.f, dy = 0.f;
+      const float4 a = sx[b];
+      const float4 k = sc[b];
       if (contrib) {
         a_ = splat_alpha_dxy(a, k, pxc, pyc, p.alpha_max, dx, dy, G);
         if (a_ < p.alpha_min) contrib = false;
@@ -90,7 +113,7 @@ __global__ void __launch_bounds__(1024) k_render_bwd(gs_map map, gs_proj proj, g
 #pragma unroll
       for (int q = 0; q < 10; ++q) v[q] = 0.f;
       if (contrib) {
-        const float4 c = s_rgb[j];
+        const float4 c = sr[b];
         const float om = 1.f - a_;
         const float Ti = T / om;
         const float w = a_ * Ti;
@@ -118,12 +141,13 @@ __global__ void __launch_bounds__(1024) k_render_bwd(gs_map map, gs_proj proj, g
 #pragma unroll
       for (int q = 0; q < 10; ++q) v[q] = warp_sum(v[q]);
       if (lane == 0) {
-        float4* dst = g2d + 3 * (size_t)s_rec[j];
+        float4* dst = g2d + 3 * (size_t)srec[b];
         atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
         atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], 0.f));
         atomicAdd(dst + 2, make_float4(v[7], v[8], v[9], 0.f));
       }
     }
+    __syncwarp();
   }
 }
 
@@ -135,21 +159,23 @@ __global__ void k_zero_g2d(float4* __restrict__ g2d, const uint32_t* count, int6
     g2d[i] = z;
 }
 
-// Projection adjoint: one thread per Gaussian, summing over its records.
+// Projection adjoint: one thread per Gaussian, gathering its records (one per
+// view it is visible in, found through the group masks) without atomics.
 __global__ void __launch_bounds__(256) k_proj_adjoint(gs_map map, gs_proj proj, const gs_camera* __restrict__ cams,
-                                                      const float4* __restrict__ g2d, gs_map_grad out) {
+                                                      int n_views, const float4* __restrict__ g2d, gs_map_grad out) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= map.n) return;
-  int64_t nrec = (int64_t)*proj.count;
-  uint32_t r0 = proj.g_first[g], r1 = proj.g_first[g + 1];
-  if ((int64_t)r1 > nrec) r1 = (uint32_t)nrec;
+  const int64_t nrec = (int64_t)*proj.count;
+  const int64_t grp = g >> 5;
+  const uint32_t bit = 1u << (g & 31), lt = bit - 1u;
+  bool any = false;
+  for (int v = 0; v < n_views; ++v) any |= (proj.grp_mask[grp * n_views + v] & bit) != 0;
   float gmu[3] = {0.f, 0.f, 0.f}, go = 0.f, grgb[3] = {0.f, 0.f, 0.f};
   float M3[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
   const float4 mo = reinterpret_cast<const float4*>(map.mo)[g];
   const float4 su = reinterpret_cast<const float4*>(map.su)[g];
   const float4 qv = reinterpret_cast<const float4*>(map.q)[g];
   float Rq[9], s2[3], S3[3][3], qn[4], qnorm = 1.f;
-  const bool any = r0 < r1;
   if (any) {
     qnorm = sqrtf(qv.x * qv.x + qv.y * qv.y + qv.z * qv.z + qv.w * qv.w);
     const float w = qv.x / qnorm, x = qv.y / qnorm, y = qv.z / qnorm, z = qv.w / qnorm;
@@ -164,12 +190,16 @@ __global__ void __launch_bounds__(256) k_proj_adjoint(gs_map map, gs_proj proj, 
       for (int j = 0; j < 3; ++j)
         S3[i][j] = Rq[3 * i] * s2[0] * Rq[3 * j] + Rq[3 * i + 1] * s2[1] * Rq[3 * j + 1] + Rq[3 * i + 2] * s2[2] * Rq[3 * j + 2];
   }
-  for (uint32_t r = r0; r < r1; ++r) {
+  for (int v = 0; v < n_views && any; ++v) {
+    const uint32_t m = proj.grp_mask[grp * n_views + v];
+    if (!(m & bit)) continue;
+    const uint32_t r = proj.grp_base[grp * n_views + v] + __popc(m & lt);
+    if ((int64_t)r >= nrec) continue;
     const float4 A = g2d[3 * (size_t)r], Bv = g2d[3 * (size_t)r + 1], Cv = g2d[3 * (size_t)r + 2];
     grgb[0] += Cv.x; grgb[1] += Cv.y; grgb[2] += Cv.z;
     go += Bv.y;
     const float gmx = A.x, gmy = A.y, ga = A.z, gb = A.w, gc = Bv.x, gdep = Bv.z;
-    const gs_camera& cam = cams[proj.view[r]];
+    const gs_camera& cam = cams[v];
     const float* R = cam.R;
     const float dx = mo.x - cam.T[0], dy = mo.y - cam.T[1], dz = mo.z - cam.T[2];
     const float tx = R[0] * dx + R[3] * dy + R[6] * dz;
@@ -276,21 +306,14 @@ cudaError_t launch_render_bwd(const gs_map& map, const gs_proj& proj, const gs_b
   if (zb < 1) zb = 1;
   k_zero_g2d<<<(unsigned)zb, 256, 0, st>>>(g2d, proj.count, proj.capacity);
   note_launch();
-  const int B = p.tile_w * p.tile_h;
-  const size_t smem = 3 * sizeof(float4) * B + sizeof(uint32_t) * B;
-  static bool attr[64] = {false};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 64 && !attr[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_render_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    if (e != cudaSuccess) return e;
-    attr[dev] = true;
-  }
-  if (bins.tile_capacity > 0)
-    k_render_bwd<<<(unsigned)bins.tile_capacity, B, smem, st>>>(map, proj, bins, cams, n_views, p, fwd, g, g2d);
+  const int64_t items = bins.tile_capacity * (int64_t)((p.tile_w * p.tile_h) >> 5);
+  if (items > 0) {
+    k_render_bwd<<<(unsigned)((items + kBwdWarps - 1) / kBwdWarps), kBwdWarps * 32, 0, st>>>(
+        map, proj, bins, cams, n_views, p, fwd, g, g2d, (uint32_t)items);
     note_launch();
+  }
   if (map.n > 0) {
-    k_proj_adjoint<<<(unsigned)((map.n + 255) / 256), 256, 0, st>>>(map, proj, cams, g2d, out);
+    k_proj_adjoint<<<(unsigned)((map.n + 255) / 256), 256, 0, st>>>(map, proj, cams, n_views, g2d, out);
     note_launch();
   }
   return cudaGetLastError();

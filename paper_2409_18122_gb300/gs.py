@@ -173,7 +173,10 @@ class Frame:
         self.conic_u = torch.empty((rc, 4), dtype=torch.float32, device=d)
         self.rect = torch.empty((rc, 4), dtype=torch.int16, device=d)
         self.depth_key = _alloc_u32(rc, d)
-        self.g_first = _alloc_u32(self.n + 1, d)
+        self.ext = torch.empty((rc, 2), dtype=torch.float32, device=d)
+        self.n_slots = ((self.n + 31) // 32) * self.V
+        self.grp_mask = _alloc_u32(self.n_slots, d)
+        self.grp_base = _alloc_u32(self.n_slots + 1, d)
         self.pair_count = torch.zeros(1, dtype=torch.int32, device=d)
         self.pair_tile = _alloc_u32(pair_capacity, d)
         self.pair_rec = _alloc_u32(pair_capacity, d)
@@ -184,7 +187,7 @@ class Frame:
         self.ws = torch.empty(max(ws, 256), dtype=torch.uint8, device=d)
         self.c_proj = L.gs_proj(rc, _ptr(self.rec_count), _ptr(self.status), _ptr(self.view_info), _ptr(self.gid),
                                 _ptr(self.view), _ptr(self.xyod), _ptr(self.conic_u), _ptr(self.rect),
-                                _ptr(self.depth_key), _ptr(self.g_first))
+                                _ptr(self.depth_key), _ptr(self.ext), _ptr(self.grp_mask), _ptr(self.grp_base))
         self.c_bins = L.gs_bins(pair_capacity, max(self.n_tiles, 1), _ptr(self.pair_count), _ptr(self.pair_tile),
                                 _ptr(self.pair_rec), _ptr(self.ranges))
         self.c_params = self.params.c()

@@ -34,7 +34,9 @@ def gpu_records(frame):
         xyod=frame.xyod[:n].cpu().numpy(), conic_u=frame.conic_u[:n].cpu().numpy(),
         rect=frame.rect[:n].cpu().numpy().view(np.uint16).astype(np.int32),
         dkey=u32(frame.depth_key)[:n],
-        g_first=u32(frame.g_first)[:frame.n + 1],
+        ext=frame.ext[:n].cpu().numpy(),
+        grp_mask=u32(frame.grp_mask)[:frame.n_slots],
+        grp_base=u32(frame.grp_base)[:frame.n_slots + 1],
         view_info=u32(frame.view_info),
     )
 

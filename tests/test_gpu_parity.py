@@ -31,27 +31,45 @@ def run_forward(gmap, cams, params=gs.RenderParams(), pair_capacity=None):
 
 
 def check_projection(fr, gmap, cams, params):
+    """GPU records vs the oracle's: same set of visible (Gaussian, view), bit-exact integer fields,
+    FP32 values within rounding of the FP64 ones, and the documented record order and group masks."""
     rec = gpu_records(fr)
     pr = O.project(gmap, cams, oparams(params))
     ref = O.records_from_projection(pr)
+    V = len(cams)
     assert rec["n"] == len(ref["gid"])
-    np.testing.assert_array_equal(rec["gid"], ref["gid"])
-    np.testing.assert_array_equal(rec["view"], ref["view"])
-    np.testing.assert_array_equal(rec["dkey"], ref["dkey"])
-    np.testing.assert_array_equal(rec["rect"], ref["rect"])
+    # record order: (group of 32 Gaussians, view, Gaussian)
+    key = (rec["gid"].astype(np.int64) // 32) * V + rec["view"]
+    k2 = key * (1 << 32) + rec["gid"]
+    assert (np.diff(k2) > 0).all()
+    order = np.lexsort((rec["view"], rec["gid"]))          # -> (gid, view) order like the oracle's
     g, v = ref["gid"].astype(np.int64), ref["view"].astype(np.int64)
+    np.testing.assert_array_equal(rec["gid"][order], ref["gid"])
+    np.testing.assert_array_equal(rec["view"][order], ref["view"])
+    np.testing.assert_array_equal(rec["dkey"][order], ref["dkey"])
+    np.testing.assert_array_equal(rec["rect"][order], ref["rect"])
     W = max(c.width for c in cams)
-    np.testing.assert_allclose(rec["xyod"][:, :2], pr["mean2d"][v, g], rtol=0, atol=4e-6 * W)
-    np.testing.assert_allclose(rec["xyod"][:, 2], pr["opac"][v, g], rtol=2e-6)
-    np.testing.assert_allclose(rec["xyod"][:, 3], pr["depth"][v, g], rtol=2e-7)
+    np.testing.assert_allclose(rec["xyod"][order, :2], pr["mean2d"][v, g], rtol=0, atol=4e-6 * W)
+    np.testing.assert_allclose(rec["xyod"][order, 2], pr["opac"][v, g], rtol=2e-6)
+    np.testing.assert_allclose(rec["xyod"][order, 3], pr["depth"][v, g], rtol=2e-7)
     con = pr["conic"][v, g]
     scale = np.abs(con).max(axis=1, keepdims=True)
-    assert (np.abs(rec["conic_u"][:, :3] - con) <= 5e-4 * scale).all()
-    np.testing.assert_array_equal(rec["conic_u"][:, 3], gmap.su[g, 3])
-    # first record of every Gaussian
-    first = np.searchsorted(ref["gid"], np.arange(gmap.n + 1))
-    np.testing.assert_array_equal(rec["g_first"], first)
+    assert (np.abs(rec["conic_u"][order, :3] - con) <= 5e-4 * scale).all()
+    np.testing.assert_array_equal(rec["conic_u"][order, 3], gmap.su[g, 3])
+    # group masks and bases
+    n_grp = (gmap.n + 31) // 32
+    vis = np.zeros((n_grp * 32, V), bool)
+    vis[:gmap.n] = pr["vis"].T.astype(bool)
+    bits = (vis.reshape(n_grp, 32, V) * (1 << np.arange(32, dtype=np.uint64))[None, :, None]).sum(axis=1)
+    np.testing.assert_array_equal(rec["grp_mask"].reshape(n_grp, V), bits.astype(np.uint32))
+    counts = np.array([bin(int(x)).count("1") for x in rec["grp_mask"]])
+    np.testing.assert_array_equal(rec["grp_base"], np.concatenate([[0], np.cumsum(counts)]))
     return rec, ref
+
+
+def pairs_as_gid_view(bins_tile, bins_rec, rec):
+    return np.stack([bins_tile.astype(np.int64), rec["gid"][bins_rec].astype(np.int64),
+                     rec["view"][bins_rec].astype(np.int64)], 1)
 
 
 # --------------------------------------------------------------------------- projection
@@ -130,8 +148,15 @@ def test_bin_sort_pipeline_room_subset(tile):
     sub = sc.gmap.subset(np.arange(4096))
     p = gs.RenderParams(tile_w=tile[0], tile_h=tile[1])
     fr, _, _ = run_forward(sub, sc.cams, p)
-    rec, ref = check_projection(fr, sub, sc.cams, p)
-    _check_bins(fr, ref, sc.cams, p)
+    rec, ref_rec = check_projection(fr, sub, sc.cams, p)
+    ref = O.bin_sort(ref_rec, sc.cams, oparams(p))
+    b = gpu_bins(fr)
+    assert b["n"] == ref["n_pairs"]
+    np.testing.assert_array_equal(pairs_as_gid_view(b["tile"], b["rec"], rec),
+                                  pairs_as_gid_view((ref["keys"] >> np.uint64(32)), ref["vals"], ref_rec))
+    keys = (b["tile"].astype(np.uint64) << np.uint64(32)) | rec["dkey"][b["rec"]].astype(np.uint64)
+    np.testing.assert_array_equal(keys, ref["keys"])
+    np.testing.assert_array_equal(b["ranges"], ref["ranges"])
 
 
 # --------------------------------------------------------------------------- forward compositing
