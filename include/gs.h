@@ -91,8 +91,8 @@ typedef struct {
 } gs_map;
 
 /* Rendering constants (readings where the paper is silent).
- *   tile_w, tile_h  screen tile in pixels: tile_w in {8, 16, 32, 64}, tile_h a multiple of 4,
- *                   tile_w * tile_h in {64, 128, 256, 512, 1024} (one warp per 8x4 pixel block)
+ *   tile_w, tile_h  screen tile in pixels: tile_w in {8, 16, 32, 64}, tile_h a multiple of 8,
+ *                   tile_w * tile_h in {64, 128, 256, 512, 1024} (one warp per 8x8 pixel block)
  *   eps2d           added to the diagonal of every 2D covariance (low-pass), px^2, >= 0
  *   near_plane      Gaussians with view depth <= near_plane are culled, > 0
  *   guard           centres with |t_x / t_z| > guard * (W/2) / f_x (same for y) are culled, > 0

@@ -31,8 +31,8 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 gs_status check_params(const gs_params* p) {
   if (!p) return GS_ERR_NULL;
   const int B = p->tile_w * p->tile_h;
-  if ((p->tile_w != 8 && p->tile_w != 16 && p->tile_w != 32 && p->tile_w != 64) || p->tile_h < 4 ||
-      p->tile_h % 4 != 0 || (B != 64 && B != 128 && B != 256 && B != 512 && B != 1024))
+  if ((p->tile_w != 8 && p->tile_w != 16 && p->tile_w != 32 && p->tile_w != 64) || p->tile_h < 8 ||
+      p->tile_h % 8 != 0 || (B != 64 && B != 128 && B != 256 && B != 512 && B != 1024))
     return GS_ERR_ARG;
   if (!(p->eps2d >= 0.f) || !(p->near_plane > 0.f) || !(p->guard > 0.f)) return GS_ERR_ARG;
   if (!(p->alpha_min >= 0.f && p->alpha_min < 1.f)) return GS_ERR_ARG;

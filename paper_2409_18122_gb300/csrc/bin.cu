@@ -48,24 +48,60 @@ __global__ void k_pair_total(const uint32_t* __restrict__ total, int64_t pair_ca
   *n_clamped = (int64_t)t > pair_cap ? (uint32_t)pair_cap : t;
 }
 
-__global__ void k_emit(const gs_proj proj, const gs_camera* __restrict__ cams, int tile_w,
-                       const uint32_t* __restrict__ srec, const uint32_t* __restrict__ off, int64_t pair_cap,
-                       uint32_t* __restrict__ tile_key, uint32_t* __restrict__ tile_rec) {
+// One warp per 32 consecutive records (in depth order).  The warp scans their
+// tile counts, then writes the whole run of pairs with consecutive lanes on
+// consecutive slots; each lane finds the record that owns its pair with a
+// 5-step shuffle search over the running counts.  Writes are coalesced and
+// records with many tiles are spread over the warp.
+__global__ void __launch_bounds__(256) k_emit(const gs_proj proj, const gs_camera* __restrict__ cams, int tile_w,
+                                               const uint32_t* __restrict__ srec, const uint32_t* __restrict__ off,
+                                               int64_t pair_cap, uint32_t* __restrict__ tile_key,
+                                               uint32_t* __restrict__ tile_rec) {
   const int64_t n = clamp_count(proj.count, proj.capacity);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t r = srec[i];
-    const ushort4 rc = reinterpret_cast<const ushort4*>(proj.rect)[r];
-    const uint32_t v = proj.view[r];
-    const uint32_t tb = proj.view_info[2 * v];
-    const uint32_t tx = (uint32_t)((cams[v].width + tile_w - 1) / tile_w);
-    uint64_t k = off[i];
-    for (uint32_t y = rc.y; y < rc.w; ++y) {
-      const uint32_t row = tb + y * tx;
-      for (uint32_t x = rc.x; x < rc.z; ++x, ++k) {
-        if ((int64_t)k < pair_cap) {
-          tile_key[k] = row + x;
-          tile_rec[k] = r;
-        }
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i0 = warp0 * 32; i0 < n; i0 += n_warps * 32) {
+    const int64_t i = i0 + lane;
+    uint32_t r = 0, tile0 = 0, tx = 1, w = 1, cnt = 0;
+    if (i < n) {
+      r = srec[i];
+      const ushort4 rc = reinterpret_cast<const ushort4*>(proj.rect)[r];
+      const uint32_t v = proj.view[r];
+      tx = (uint32_t)((cams[v].width + tile_w - 1) / tile_w);
+      tile0 = proj.view_info[2 * v] + (uint32_t)rc.y * tx + rc.x;
+      w = (uint32_t)(rc.z - rc.x);
+      cnt = w * (uint32_t)(rc.w - rc.y);
+      if (w == 0) w = 1;
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t excl = incl - cnt;
+    const uint64_t base = __shfl_sync(0xffffffffu, lane == 0 ? off[i0] : 0u, 0);
+    for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+      const uint32_t k = k0 + lane;
+      int pos = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const uint32_t v = __shfl_sync(0xffffffffu, incl, pos + step - 1);
+        if (v <= k) pos += step;
+      }
+      const uint32_t o_tile0 = __shfl_sync(0xffffffffu, tile0, pos);
+      const uint32_t o_tx = __shfl_sync(0xffffffffu, tx, pos);
+      const uint32_t o_w = __shfl_sync(0xffffffffu, w, pos);
+      const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, pos);
+      const uint32_t o_r = __shfl_sync(0xffffffffu, r, pos);
+      const uint64_t slot = base + k;
+      if (k < total && slot < (uint64_t)pair_cap) {
+        const uint32_t j = k - o_excl;
+        const uint32_t y = j / o_w, x = j - y * o_w;
+        tile_key[slot] = o_tile0 + y * o_tx + x;
+        tile_rec[slot] = o_r;
       }
     }
   }

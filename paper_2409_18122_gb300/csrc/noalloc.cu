@@ -69,8 +69,8 @@ extern "C" gs_status gs_render_bwd_noalloc(const gs_map* map, const gs_proj* pro
       !aligned(out->dq, 16) || !aligned(out->drgb, 16))
     return GS_ERR_ALIGN;
   const int B = prm->tile_w * prm->tile_h;
-  if ((prm->tile_w != 8 && prm->tile_w != 16 && prm->tile_w != 32 && prm->tile_w != 64) || prm->tile_h < 4 ||
-      prm->tile_h % 4 != 0 || (B != 64 && B != 128 && B != 256 && B != 512 && B != 1024) || !(prm->alpha_max > 0.f && prm->alpha_max <= 1.f) ||
+  if ((prm->tile_w != 8 && prm->tile_w != 16 && prm->tile_w != 32 && prm->tile_w != 64) || prm->tile_h < 8 ||
+      prm->tile_h % 8 != 0 || (B != 64 && B != 128 && B != 256 && B != 512 && B != 1024) || !(prm->alpha_max > 0.f && prm->alpha_max <= 1.f) ||
       !(prm->alpha_min >= 0.f && prm->alpha_min < 1.f))
     return GS_ERR_ARG;
   void* scratch = nullptr;

@@ -20,6 +20,7 @@ namespace {
 
 constexpr int kFwdWarps = 2;   // warps (work items) per CTA: small CTAs free their slot as soon as both finish
 constexpr int kIgWarps = 8;    // warps per CTA of the persistent information-gain kernel
+constexpr int kPix = 1;        // pixels per lane of the forward and information-gain kernels
 
 __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_proj proj, gs_bins bins,
                                                                 const gs_camera* __restrict__ cams, int n_views,
@@ -28,39 +29,58 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t item = blockIdx.x * kFwdWarps + warp;
   if (item >= n_items) return;
-  const int wpt = warps_per_tile(p);
+  const int wpt = warps_per_tile<kPix>(p);
   TileInfo ti;
   if (!warp_tile_setup(proj, bins, cams, n_views, p, item / wpt, ti)) return;
   WarpBlock wb;
-  warp_block(ti, p, (int)(item % wpt), wb);
+  warp_block<kPix>(ti, p, (int)(item % wpt), wb);
   float4* sx = s_stage[warp][0];
   float4* sc = s_stage[warp][1];
   float4* sr = s_stage[warp][2];
-  const bool inside = wb.px < ti.W && wb.py < ti.H;
-  const float pxc = (float)wb.px + 0.5f, pyc = (float)wb.py + 0.5f;
-  float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, cd = 0.f, cu = 0.f;
-  int32_t last = 0, n_contrib = 0;
-  bool done = !inside;
+  const float pxc = (float)wb.px + 0.5f;
+  float pyc[kPix];
+  bool inside[kPix], done[kPix];
+  float T[kPix], cr[kPix], cg[kPix], cb[kPix], cd[kPix], cu[kPix];
+  int32_t last[kPix], n_contrib[kPix];
+#pragma unroll
+  for (int q = 0; q < kPix; ++q) {
+    pyc[q] = (float)(wb.py + 4 * q) + 0.5f;
+    inside[q] = wb.px < ti.W && wb.py + 4 * q < ti.H;
+    done[q] = !inside[q];
+    T[q] = 1.f;
+    cr[q] = cg[q] = cb[q] = cd[q] = cu[q] = 0.f;
+    last[q] = n_contrib[q] = 0;
+  }
   const uint32_t beg = ti.beg, n = ti.end - ti.beg;
   const float4* rgb = reinterpret_cast<const float4*>(map.rgb);
-  // software pipeline: the next group of 32 entries is loaded while this one is composited
-  Entry nx;
-  float4 nrgb = make_float4(0.f, 0.f, 0.f, 0.f);
-  bool nv = (uint32_t)lane < n;
-  if (nv) {
-    load_entry(proj, bins, beg + lane, nx);
-    nrgb = __ldg(rgb + __ldg(proj.gid + nx.rec));
+  // software pipeline over groups of 32 list entries: while group g is
+  // composited, the colours of group g+1, the records of group g+2 and the list
+  // indices of group g+3 are in flight
+  const uint32_t* rl = bins.rec + beg;
+  Entry e1, e2;
+  float4 c1 = make_float4(0.f, 0.f, 0.f, 0.f);
+  uint32_t gid2 = 0, r3 = 0;
+  if ((uint32_t)lane < n) {
+    load_entry(proj, bins, beg + lane, e1);
+    c1 = __ldg(rgb + __ldg(proj.gid + e1.rec));
   }
+  if (32u + lane < n) {
+    load_entry(proj, bins, beg + 32 + lane, e2);
+    gid2 = __ldg(proj.gid + e2.rec);
+  }
+  if (64u + lane < n) r3 = __ldg(rl + 64 + lane);
   for (uint32_t g = 0; g < n; g += 32) {
-    if (!__any_sync(0xffffffffu, !done)) break;
-    const Entry e = nx;
-    const float4 ergb = nrgb;
-    const bool ev = nv;
-    nv = g + 32 + lane < n;
-    if (nv) {
-      load_entry(proj, bins, beg + g + 32 + lane, nx);
-      nrgb = __ldg(rgb + __ldg(proj.gid + nx.rec));
+    if (!__any_sync(0xffffffffu, !all_done<kPix>(done))) break;
+    const Entry e = e1;
+    const float4 ergb = c1;
+    const bool ev = g + lane < n;
+    e1 = e2;
+    if (g + 32 + lane < n) c1 = __ldg(rgb + gid2);
+    if (g + 64 + lane < n) {
+      load_record(proj, r3, e2);
+      gid2 = __ldg(proj.gid + r3);
     }
+    if (g + 96 + lane < n) r3 = __ldg(rl + g + 96 + lane);
     const bool ov = ev && box_overlaps(e.xyod, e.ext, wb);
     uint32_t m = __ballot_sync(0xffffffffu, ov);
     if (m == 0) continue;
@@ -73,41 +93,48 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
     while (m) {
       const int b = __ffs(m) - 1;
       m &= m - 1;
-      if (done) continue;
+      if (all_done<kPix>(done)) continue;
       const float4 a = sx[b];
       const float4 k = sc[b];
-      const float alpha = splat_alpha(a, k, pxc, pyc, p.alpha_max);
-      if (alpha < p.alpha_min) continue;
-      const float Tn = T * (1.f - alpha);
-      if (Tn < p.T_min) { done = true; continue; }
-      const float w = alpha * T;
       const float4 c = sr[b];
-      cr += w * c.x;
-      cg += w * c.y;
-      cb += w * c.z;
-      cd += w * a.w;
-      cu += w * k.w;
-      T = Tn;
-      last = (int32_t)(g + b + 1);
-      ++n_contrib;
+#pragma unroll
+      for (int q = 0; q < kPix; ++q) {
+        if (done[q]) continue;
+        const float alpha = splat_alpha(a, k, pxc, pyc[q], p.alpha_max);
+        if (alpha < p.alpha_min) continue;
+        const float Tn = T[q] * (1.f - alpha);
+        if (Tn < p.T_min) { done[q] = true; continue; }
+        const float w = alpha * T[q];
+        cr[q] += w * c.x;
+        cg[q] += w * c.y;
+        cb[q] += w * c.z;
+        cd[q] += w * a.w;
+        cu[q] += w * k.w;
+        T[q] = Tn;
+        last[q] = (int32_t)(g + b + 1);
+        ++n_contrib[q];
+      }
     }
     __syncwarp();
   }
-  if (!inside) return;
   const size_t P = (size_t)ti.W * ti.H;
-  const size_t pix = (size_t)wb.py * ti.W + wb.px;
-  const size_t o = (size_t)ti.pix_base + pix;
-  if (img.rgb) {
-    float* base = img.rgb + 3 * (size_t)ti.pix_base;
-    base[pix] = cr;
-    base[P + pix] = cg;
-    base[2 * P + pix] = cb;
+#pragma unroll
+  for (int q = 0; q < kPix; ++q) {
+    if (!inside[q]) continue;
+    const size_t pix = (size_t)(wb.py + 4 * q) * ti.W + wb.px;
+    const size_t o = (size_t)ti.pix_base + pix;
+    if (img.rgb) {
+      float* base = img.rgb + 3 * (size_t)ti.pix_base;
+      base[pix] = cr[q];
+      base[P + pix] = cg[q];
+      base[2 * P + pix] = cb[q];
+    }
+    if (img.depth) img.depth[o] = cd[q];
+    if (img.unc) img.unc[o] = cu[q];
+    if (img.T) img.T[o] = T[q];
+    if (img.last) img.last[o] = last[q];
+    if (img.n_contrib) img.n_contrib[o] = n_contrib[q];
   }
-  if (img.depth) img.depth[o] = cd;
-  if (img.unc) img.unc[o] = cu;
-  if (img.T) img.T[o] = T;
-  if (img.last) img.last[o] = last;
-  if (img.n_contrib) img.n_contrib[o] = n_contrib;
 }
 
 // Persistent U-only compositing: every warp takes (tile, 8x4 block) work items
@@ -116,13 +143,14 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
 // accumulating, so the result does not depend on scheduling.
 __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bins bins,
                                                              const gs_camera* __restrict__ cams, int n_views,
-                                                             gs_params p, float* __restrict__ item_sum,
+                                                             gs_params p, const uint32_t* __restrict__ order,
+                                                             float* __restrict__ item_sum,
                                                              uint32_t* __restrict__ work) {
   __shared__ float4 s_stage[kIgWarps][2][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float4* sx = s_stage[warp][0];
   float4* sc = s_stage[warp][1];
-  const int wpt = warps_per_tile(p);
+  const int wpt = warps_per_tile<kPix>(p);
   const uint32_t total = proj.view_info[2 * n_views];
   const uint32_t n_tiles = (int64_t)total < bins.tile_capacity ? total : (uint32_t)bins.tile_capacity;
   const uint32_t n_items = n_tiles * (uint32_t)wpt;
@@ -131,27 +159,43 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
     if (lane == 0) item = atomicAdd(work, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= n_items) break;
+    // items are handed out longest tile list first; the slot keeps the tile's own index
+    const uint32_t tile = __ldg(order + item / wpt);
+    const uint32_t slot = tile * (uint32_t)wpt + item % wpt;
     TileInfo ti;
-    if (!warp_tile_setup(proj, bins, cams, n_views, p, item / wpt, ti)) {
-      if (lane == 0) item_sum[item] = 0.f;
+    if (!warp_tile_setup(proj, bins, cams, n_views, p, tile, ti)) {
+      if (lane == 0) item_sum[slot] = 0.f;
       continue;
     }
     WarpBlock wb;
-    warp_block(ti, p, (int)(item % wpt), wb);
-    const bool inside = wb.px < ti.W && wb.py < ti.H;
-    const float pxc = (float)wb.px + 0.5f, pyc = (float)wb.py + 0.5f;
-    float T = 1.f, cu = 0.f;
-    bool done = !inside;
+    warp_block<kPix>(ti, p, (int)(item % wpt), wb);
+    const float pxc = (float)wb.px + 0.5f;
+    float pyc[kPix], T[kPix], cu[kPix];
+    bool done[kPix];
+#pragma unroll
+    for (int q = 0; q < kPix; ++q) {
+      pyc[q] = (float)(wb.py + 4 * q) + 0.5f;
+      done[q] = !(wb.px < ti.W && wb.py + 4 * q < ti.H);
+      T[q] = 1.f;
+      cu[q] = 0.f;
+    }
     const uint32_t beg = ti.beg, n = ti.end - ti.beg;
-    Entry nx;
-    bool nv = (uint32_t)lane < n;
-    if (nv) load_entry(proj, bins, beg + lane, nx);
+    // three-stage software pipeline over groups of 32 list entries: while group g
+    // is composited, the records of groups g+1 and g+2 are in flight and the list
+    // indices of group g+3 are being fetched
+    Entry e1, e2;
+    uint32_t r3 = 0;
+    const uint32_t* rl = bins.rec + beg;
+    if ((uint32_t)lane < n) load_entry(proj, bins, beg + lane, e1);
+    if (32u + lane < n) load_entry(proj, bins, beg + 32 + lane, e2);
+    if (64u + lane < n) r3 = __ldg(rl + 64 + lane);
     for (uint32_t g = 0; g < n; g += 32) {
-      if (!__any_sync(0xffffffffu, !done)) break;
-      const Entry e = nx;
-      const bool ev = nv;
-      nv = g + 32 + lane < n;
-      if (nv) load_entry(proj, bins, beg + g + 32 + lane, nx);
+      if (!__any_sync(0xffffffffu, !all_done<kPix>(done))) break;
+      const Entry e = e1;
+      const bool ev = g + lane < n;
+      e1 = e2;
+      if (g + 64 + lane < n) load_record(proj, r3, e2);
+      if (g + 96 + lane < n) r3 = __ldg(rl + g + 96 + lane);
       const bool ov = ev && box_overlaps(e.xyod, e.ext, wb);
       uint32_t m = __ballot_sync(0xffffffffu, ov);
       if (m == 0) continue;
@@ -163,21 +207,28 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
       while (m) {
         const int b = __ffs(m) - 1;
         m &= m - 1;
-        if (done) continue;
+        if (all_done<kPix>(done)) continue;
         const float4 a = sx[b];
         const float4 k = sc[b];
-        const float alpha = splat_alpha(a, k, pxc, pyc, p.alpha_max);
-        if (alpha < p.alpha_min) continue;
-        const float Tn = T * (1.f - alpha);
-        if (Tn < p.T_min) { done = true; continue; }
-        cu += alpha * T * k.w;
-        T = Tn;
+#pragma unroll
+        for (int q = 0; q < kPix; ++q) {
+          if (done[q]) continue;
+          const float alpha = splat_alpha(a, k, pxc, pyc[q], p.alpha_max);
+          if (alpha < p.alpha_min) continue;
+          const float Tn = T[q] * (1.f - alpha);
+          if (Tn < p.T_min) { done[q] = true; continue; }
+          cu[q] += alpha * T[q] * k.w;
+          T[q] = Tn;
+        }
       }
       __syncwarp();
     }
+    float su = 0.f;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) cu += __shfl_down_sync(0xffffffffu, cu, d);
-    if (lane == 0) item_sum[item] = cu;
+    for (int q = 0; q < kPix; ++q) su += cu[q];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) su += __shfl_down_sync(0xffffffffu, su, d);
+    if (lane == 0) item_sum[slot] = su;
   }
 }
 
@@ -188,7 +239,7 @@ __global__ void __launch_bounds__(256) k_ig_views(const uint32_t* __restrict__ v
                                                    float* __restrict__ ig) {
   __shared__ float s_red[32];
   const int v = blockIdx.x;
-  const uint32_t wpt = (uint32_t)warps_per_tile(p);
+  const uint32_t wpt = (uint32_t)warps_per_tile<kPix>(p);
   uint32_t t1 = view_info[2 * v + 2];
   if ((int64_t)t1 > tile_cap) t1 = (uint32_t)tile_cap;
   const uint32_t i0 = view_info[2 * v] * wpt, i1 = t1 * wpt;
@@ -204,11 +255,22 @@ __global__ void k_zero_words(uint32_t* p, int n) {
   if (threadIdx.x < n) p[threadIdx.x] = 0u;
 }
 
+// Sort key of each tile for longest-first scheduling: 0xFFFF - min(list length, 0xFFFF).
+__global__ void k_tile_cost(const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ view_info, int n_views,
+                            int64_t tile_cap, uint32_t* __restrict__ key) {
+  uint32_t n = view_info[2 * n_views];
+  if ((int64_t)n > tile_cap) n = (uint32_t)tile_cap;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const uint32_t len = ranges[2 * (size_t)t + 1] - ranges[2 * (size_t)t];
+    key[t] = 0xFFFFu - (len < 0xFFFFu ? len : 0xFFFFu);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_render_fwd(const gs_map& map, const gs_proj& proj, const gs_bins& bins, const gs_camera* cams,
                               int n_views, const gs_params& p, const gs_image& img, cudaStream_t st) {
-  const int64_t items = bins.tile_capacity * (int64_t)((p.tile_w * p.tile_h) >> 5);
+  const int64_t items = bins.tile_capacity * (int64_t)((p.tile_w * p.tile_h) / (32 * kPix));
   if (items > 0) {
     k_render_fwd<<<(unsigned)((items + kFwdWarps - 1) / kFwdWarps), kFwdWarps * 32, 0, st>>>(
         map, proj, bins, cams, n_views, p, img, (uint32_t)items);
@@ -239,7 +301,8 @@ size_t ig_ws_bytes(int64_t n, int n_views, int64_t pair_cap, int64_t tile_cap) {
   c.take<float>(32 * tile_cap);                          // per work-item sums (<= 32 items per tile)
   c.take<uint32_t>(4);                                   // work counter
   size_t a = project_ws_bytes(n, n_views), b = bin_ws_bytes(rec_cap, pair_cap, tile_cap);
-  c.take<char>(a > b ? a : b);
+  const size_t o = 4 * align_up(sizeof(uint32_t) * (size_t)tile_cap, 256) + sort_temp_bytes(tile_cap);
+  c.take<char>(a > b ? (a > o ? a : o) : (b > o ? b : o));
   return align_up(c.off, 256);
 }
 
@@ -273,7 +336,8 @@ cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_vie
   float* item_sum = c.take<float>(32 * tile_cap);
   uint32_t* work = c.take<uint32_t>(4);
   size_t a = project_ws_bytes(map.n, n_views), b = bin_ws_bytes(rec_cap, pair_cap, tile_cap);
-  void* inner = c.take<char>(a > b ? a : b);
+  const size_t o = 4 * align_up(sizeof(uint32_t) * (size_t)tile_cap, 256) + sort_temp_bytes(tile_cap);
+  void* inner = c.take<char>(a > b ? (a > o ? a : o) : (b > o ? b : o));
 
   cudaError_t e = launch_project(map, cams, n_views, p, proj, inner, st);
   if (e != cudaSuccess) return e;
@@ -281,15 +345,33 @@ cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_vie
   if (e != cudaSuccess) return e;
   k_zero_words<<<1, 32, 0, st>>>(work, 4);
   note_launch();
+  // longest tile lists first (the inner workspace is free again once binning is done)
+  Carver oc(inner);
+  uint32_t* ok_a = oc.take<uint32_t>(tile_cap);
+  uint32_t* ov_a = oc.take<uint32_t>(tile_cap);
+  uint32_t* ok_b = oc.take<uint32_t>(tile_cap);
+  uint32_t* ov_b = oc.take<uint32_t>(tile_cap);
+  void* otmp = oc.take<char>(sort_temp_bytes(tile_cap));
+  {
+    int64_t gb = (tile_cap + 255) / 256;
+    if (gb > 4096) gb = 4096;
+    k_tile_cost<<<(unsigned)gb, 256, 0, st>>>(bins.ranges, proj.view_info, n_views, tile_cap, ok_a);
+    note_launch();
+  }
+  bool in_a = false;
+  e = radix_sort(ok_a, nullptr, nullptr, SortBufs{ok_a, ov_a, ok_b, ov_b}, proj.view_info + 2 * n_views, tile_cap, 0,
+                 16, otmp, st, &in_a);
+  if (e != cudaSuccess) return e;
+  const uint32_t* order = in_a ? ov_a : ov_b;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ig_items, kIgWarps * 32, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  const int64_t items = tile_cap * (int64_t)((p.tile_w * p.tile_h) >> 5);
+  const int64_t items = tile_cap * (int64_t)((p.tile_w * p.tile_h) / (32 * kPix));
   int64_t grid = (int64_t)device_sm_count() * per_sm;
   if (grid * kIgWarps > items) grid = (items + kIgWarps - 1) / kIgWarps;
   if (grid < 1) grid = 1;
-  k_ig_items<<<(unsigned)grid, kIgWarps * 32, 0, st>>>(proj, bins, cams, n_views, p, item_sum, work);
+  k_ig_items<<<(unsigned)grid, kIgWarps * 32, 0, st>>>(proj, bins, cams, n_views, p, order, item_sum, work);
   note_launch();
   k_ig_views<<<n_views, 256, 0, st>>>(proj.view_info, cams, n_views, p, item_sum, tile_cap, ig_out);
   note_launch();

@@ -25,6 +25,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 constexpr int kBwdWarps = 2;   // warps (work items) per CTA
+constexpr int kPix = 2;        // pixels per lane: one warp reduction per entry serves 64 pixels
 
 __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_proj proj, gs_bins bins,
                                                                 const gs_camera* __restrict__ cams, int n_views,
@@ -35,57 +36,79 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t item = blockIdx.x * kBwdWarps + warp;
   if (item >= n_items) return;
-  const int wpt = warps_per_tile(p);
+  const int wpt = warps_per_tile<kPix>(p);
   TileInfo ti;
   if (!warp_tile_setup(proj, bins, cams, n_views, p, item / wpt, ti)) return;
   WarpBlock wb;
-  warp_block(ti, p, (int)(item % wpt), wb);
+  warp_block<kPix>(ti, p, (int)(item % wpt), wb);
   float4* sx = s_stage[warp][0];
   float4* sc = s_stage[warp][1];
   float4* sr = s_stage[warp][2];
   uint32_t* srec = s_rec[warp];
-  const bool inside = wb.px < ti.W && wb.py < ti.H;
-  const float pxc = (float)wb.px + 0.5f, pyc = (float)wb.py + 0.5f;
+  const float pxc = (float)wb.px + 0.5f;
   const size_t P = (size_t)ti.W * ti.H;
-  const size_t pix = (size_t)wb.py * ti.W + wb.px;
-  const size_t o = (size_t)ti.pix_base + pix;
-  float T = 1.f, gr = 0.f, gg = 0.f, gb = 0.f, gd = 0.f;
-  int last = 0;
-  if (inside) {
-    T = fwd.T[o];
-    last = fwd.last[o];
-    if (grad.rgb) {
-      const float* base = grad.rgb + 3 * (size_t)ti.pix_base;
-      gr = base[pix];
-      gg = base[P + pix];
-      gb = base[2 * P + pix];
+  float pyc[kPix], T[kPix], gr[kPix], gg[kPix], gb[kPix], gd[kPix];
+  float Sr[kPix], Sg[kPix], Sb[kPix], Sd[kPix];
+  bool inside[kPix];
+  int last[kPix];
+#pragma unroll
+  for (int q = 0; q < kPix; ++q) {
+    const int py = wb.py + 4 * q;
+    pyc[q] = (float)py + 0.5f;
+    inside[q] = wb.px < ti.W && py < ti.H;
+    T[q] = 1.f;
+    gr[q] = gg[q] = gb[q] = gd[q] = 0.f;
+    Sr[q] = Sg[q] = Sb[q] = Sd[q] = 0.f;
+    last[q] = 0;
+    if (inside[q]) {
+      const size_t pix = (size_t)py * ti.W + wb.px;
+      const size_t o = (size_t)ti.pix_base + pix;
+      T[q] = fwd.T[o];
+      last[q] = fwd.last[o];
+      if (grad.rgb) {
+        const float* base = grad.rgb + 3 * (size_t)ti.pix_base;
+        gr[q] = base[pix];
+        gg[q] = base[P + pix];
+        gb[q] = base[2 * P + pix];
+      }
+      if (grad.depth) gd[q] = grad.depth[o];
     }
-    if (grad.depth) gd = grad.depth[o];
   }
-  const int wlast = (int)__reduce_max_sync(0xffffffffu, (unsigned)last);
+  int my_last = 0;
+#pragma unroll
+  for (int q = 0; q < kPix; ++q) my_last = max(my_last, last[q]);
+  const int wlast = (int)__reduce_max_sync(0xffffffffu, (unsigned)my_last);
   if (wlast == 0) return;
   const uint32_t beg = ti.beg;
   const float4* rgb = reinterpret_cast<const float4*>(map.rgb);
-  float Sr = 0.f, Sg = 0.f, Sb = 0.f, Sd = 0.f;
-  // walk groups of 32 entries from the last one any lane used back to the first,
-  // loading the next (earlier) group while this one is processed
+  // walk groups of 32 entries from the last one any lane used back to the first;
+  // while group g is processed, the colours of the previous group, the records
+  // of the one before and the list indices of the one before that are in flight
+  const uint32_t* rl = bins.rec + beg;
   int g = ((wlast - 1) >> 5) << 5;
-  Entry nx;
-  float4 nrgb = make_float4(0.f, 0.f, 0.f, 0.f);
-  bool nv = g + lane < wlast;
-  if (nv) {
-    load_entry(proj, bins, beg + g + lane, nx);
-    nrgb = __ldg(rgb + __ldg(proj.gid + nx.rec));
+  Entry e1, e2;
+  float4 c1 = make_float4(0.f, 0.f, 0.f, 0.f);
+  uint32_t gid2 = 0, r3 = 0;
+  if (g + lane < wlast) {
+    load_entry(proj, bins, beg + g + lane, e1);
+    c1 = __ldg(rgb + __ldg(proj.gid + e1.rec));
   }
+  if (g >= 32) {
+    load_entry(proj, bins, beg + g - 32 + lane, e2);
+    gid2 = __ldg(proj.gid + e2.rec);
+  }
+  if (g >= 64) r3 = __ldg(rl + g - 64 + lane);
   for (; g >= 0; g -= 32) {
-    const Entry e = nx;
-    const float4 ergb = nrgb;
-    const bool ev = nv;
-    nv = g >= 32;
-    if (nv) {
-      load_entry(proj, bins, beg + g - 32 + lane, nx);
-      nrgb = __ldg(rgb + __ldg(proj.gid + nx.rec));
+    const Entry e = e1;
+    const float4 ergb = c1;
+    const bool ev = g + lane < wlast;
+    e1 = e2;
+    if (g >= 32) c1 = __ldg(rgb + gid2);
+    if (g >= 64) {
+      load_record(proj, r3, e2);
+      gid2 = __ldg(proj.gid + r3);
     }
+    if (g >= 96) r3 = __ldg(rl + g - 96 + lane);
     const bool ov = ev && box_overlaps(e.xyod, e.ext, wb);
     uint32_t m = __ballot_sync(0xffffffffu, ov);
     if (m == 0) continue;
@@ -100,46 +123,56 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
       const int b = 31 - __clz(m);
       m ^= 1u << b;
       const int pos = g + b;   // position in the tile's list
-      bool contrib = inside && pos < last;
-      float a_ = 0.f, G = 0.f, dx = 0.f, dy = 0.f;
       const float4 a = sx[b];
       const float4 k = sc[b];
-      if (contrib) {
-        a_ = splat_alpha_dxy(a, k, pxc, pyc, p.alpha_max, dx, dy, G);
-        if (a_ < p.alpha_min) contrib = false;
+      bool contrib[kPix];
+      float al[kPix], G[kPix], dx[kPix], dy[kPix];
+#pragma unroll
+      for (int q = 0; q < kPix; ++q) {
+        contrib[q] = inside[q] && pos < last[q];
+        al[q] = G[q] = dx[q] = dy[q] = 0.f;
+        if (contrib[q]) {
+          al[q] = splat_alpha_dxy(a, k, pxc, pyc[q], p.alpha_max, dx[q], dy[q], G[q]);
+          if (al[q] < p.alpha_min) contrib[q] = false;
+        }
       }
-      if (!__any_sync(0xffffffffu, contrib)) continue;
+      bool any_c = false;
+#pragma unroll
+      for (int q = 0; q < kPix; ++q) any_c = any_c || contrib[q];
+      if (!__any_sync(0xffffffffu, any_c)) continue;
       float v[10];
 #pragma unroll
-      for (int q = 0; q < 10; ++q) v[q] = 0.f;
-      if (contrib) {
-        const float4 c = sr[b];
-        const float om = 1.f - a_;
-        const float Ti = T / om;
-        const float w = a_ * Ti;
-        const float dalpha = (gr * c.x + gg * c.y + gb * c.z + gd * a.w) * Ti -
-                             (gr * Sr + gg * Sg + gb * Sb + gd * Sd) / om;
-        Sr += w * c.x;
-        Sg += w * c.y;
-        Sb += w * c.z;
-        Sd += w * a.w;
-        T = Ti;
-        v[7] = gr * w;
-        v[8] = gg * w;
-        v[9] = gb * w;
-        v[6] = gd * w;
-        if (__fmul_rn(a.z, G) < p.alpha_max) {   // not clamped
-          v[5] = dalpha * G;                       // dL/do
-          const float dq = -0.5f * a_ * dalpha;    // dL/dq
-          v[0] = dq * 2.f * (k.x * dx + k.y * dy); // dL/dmu_x (dx = mu_x - p_x)
-          v[1] = dq * 2.f * (k.y * dx + k.z * dy); // dL/dmu_y
-          v[2] = dq * dx * dx;                     // dL/da
-          v[3] = dq * 2.f * dx * dy;               // dL/db
-          v[4] = dq * dy * dy;                     // dL/dc
+      for (int i = 0; i < 10; ++i) v[i] = 0.f;
+      const float4 c = sr[b];
+#pragma unroll
+      for (int q = 0; q < kPix; ++q) {
+        if (!contrib[q]) continue;
+        const float om = 1.f - al[q];
+        const float Ti = T[q] / om;
+        const float w = al[q] * Ti;
+        const float dalpha = (gr[q] * c.x + gg[q] * c.y + gb[q] * c.z + gd[q] * a.w) * Ti -
+                             (gr[q] * Sr[q] + gg[q] * Sg[q] + gb[q] * Sb[q] + gd[q] * Sd[q]) / om;
+        Sr[q] += w * c.x;
+        Sg[q] += w * c.y;
+        Sb[q] += w * c.z;
+        Sd[q] += w * a.w;
+        T[q] = Ti;
+        v[7] += gr[q] * w;
+        v[8] += gg[q] * w;
+        v[9] += gb[q] * w;
+        v[6] += gd[q] * w;
+        if (__fmul_rn(a.z, G[q]) < p.alpha_max) {   // not clamped
+          v[5] += dalpha * G[q];                       // dL/do
+          const float dq = -0.5f * al[q] * dalpha;     // dL/dq
+          v[0] += dq * 2.f * (k.x * dx[q] + k.y * dy[q]); // dL/dmu_x (dx = mu_x - p_x)
+          v[1] += dq * 2.f * (k.y * dx[q] + k.z * dy[q]); // dL/dmu_y
+          v[2] += dq * dx[q] * dx[q];                  // dL/da
+          v[3] += dq * 2.f * dx[q] * dy[q];            // dL/db
+          v[4] += dq * dy[q] * dy[q];                  // dL/dc
         }
       }
 #pragma unroll
-      for (int q = 0; q < 10; ++q) v[q] = warp_sum(v[q]);
+      for (int i = 0; i < 10; ++i) v[i] = warp_sum(v[i]);
       if (lane == 0) {
         float4* dst = g2d + 3 * (size_t)srec[b];
         atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
@@ -306,7 +339,7 @@ cudaError_t launch_render_bwd(const gs_map& map, const gs_proj& proj, const gs_b
   if (zb < 1) zb = 1;
   k_zero_g2d<<<(unsigned)zb, 256, 0, st>>>(g2d, proj.count, proj.capacity);
   note_launch();
-  const int64_t items = bins.tile_capacity * (int64_t)((p.tile_w * p.tile_h) >> 5);
+  const int64_t items = bins.tile_capacity * (int64_t)((p.tile_w * p.tile_h) / (32 * kPix));
   if (items > 0) {
     k_render_bwd<<<(unsigned)((items + kBwdWarps - 1) / kBwdWarps), kBwdWarps * 32, 0, st>>>(
         map, proj, bins, cams, n_views, p, fwd, g, g2d, (uint32_t)items);

@@ -69,17 +69,21 @@ __device__ __forceinline__ float splat_alpha(const float4& xyod, const float4& c
   return splat_alpha_dxy(xyod, con, pxc, pyc, alpha_max, dx, dy, G);
 }
 
-// Work item of the compositing kernels: one warp renders one 8x4 pixel block of
-// one screen tile.  Block b of a tile covers columns 8 (b mod (tile_w/8)) .. +7
-// and rows 4 (b div (tile_w/8)) .. +3; lane l owns pixel (l mod 8, l div 8).
-// Warps never wait for each other: each walks its tile's list on its own and
-// stops as soon as all 32 of its pixels are saturated.
+// Work item of the compositing kernels: one warp renders one 8 x (4 KP) pixel
+// block of one screen tile, KP pixels per lane (KP = 1 for the forward and
+// information-gain kernels, 2 for the backward kernel, whose per-entry warp
+// reduction is then shared by 64 pixels).  Block b of a tile covers columns
+// 8 (b mod (tile_w/8)) .. +7 and rows 4 KP (b div (tile_w/8)) .. +4 KP - 1;
+// lane l owns pixels (l mod 8, l div 8 + 4 q), q < KP.  Warps never wait for
+// each other: each walks its tile's list on its own and stops as soon as all of
+// its pixels are saturated.
 struct WarpBlock {
-  int px, py;                   // this lane's pixel
+  int px, py;                   // this lane's first pixel; the others are (px, py + 4 q)
   float bx0, bx1, by0, by1;     // pixel-centre bounds of the warp's block
 };
 
-__device__ __forceinline__ int warps_per_tile(const gs_params& p) { return (p.tile_w * p.tile_h) >> 5; }
+template <int KP>
+__device__ __forceinline__ int warps_per_tile(const gs_params& p) { return (p.tile_w * p.tile_h) / (32 * KP); }
 
 // Tile of `tile`, computed by lane 0 and broadcast; returns false (warp-uniform) if the tile does not exist.
 __device__ __forceinline__ bool warp_tile_setup(const gs_proj& proj, const gs_bins& bins, const gs_camera* cams,
@@ -122,16 +126,25 @@ __device__ __forceinline__ bool warp_tile_setup(const gs_proj& proj, const gs_bi
   return ti.valid;
 }
 
+template <int KP>
 __device__ __forceinline__ void warp_block(const TileInfo& ti, const gs_params& p, int blk, WarpBlock& wb) {
   const int lane = threadIdx.x & 31;
   const int wpr = p.tile_w >> 3;
-  const int wx = (blk % wpr) * 8, wy = (blk / wpr) * 4;
+  const int wx = (blk % wpr) * 8, wy = (blk / wpr) * 4 * KP;
   wb.px = ti.x0 + wx + (lane & 7);
   wb.py = ti.y0 + wy + (lane >> 3);
   wb.bx0 = (float)(ti.x0 + wx) + 0.5f;
   wb.bx1 = wb.bx0 + 7.f;
   wb.by0 = (float)(ti.y0 + wy) + 0.5f;
-  wb.by1 = wb.by0 + 3.f;
+  wb.by1 = wb.by0 + (float)(4 * KP - 1);
+}
+
+template <int KP>
+__device__ __forceinline__ bool all_done(const bool* done) {
+  bool r = true;
+#pragma unroll
+  for (int q = 0; q < KP; ++q) r = r && done[q];
+  return r;
 }
 
 // Can the support box of an entry (mean +/- half-widths) contain a pixel centre of the block?
@@ -152,6 +165,14 @@ __device__ __forceinline__ void load_entry(const gs_proj& proj, const gs_bins& b
   e.xyod = __ldg(reinterpret_cast<const float4*>(proj.xyod) + e.rec);
   e.con = __ldg(reinterpret_cast<const float4*>(proj.conic_u) + e.rec);
   e.ext = __ldg(reinterpret_cast<const float2*>(proj.ext) + e.rec);
+}
+
+// Record part of an entry whose record index is already known.
+__device__ __forceinline__ void load_record(const gs_proj& proj, uint32_t rec, Entry& e) {
+  e.rec = rec;
+  e.xyod = __ldg(reinterpret_cast<const float4*>(proj.xyod) + rec);
+  e.con = __ldg(reinterpret_cast<const float4*>(proj.conic_u) + rec);
+  e.ext = __ldg(reinterpret_cast<const float2*>(proj.ext) + rec);
 }
 
 // Fixed-tree block sum (deterministic for a fixed block size); result valid in thread 0.

@@ -15,10 +15,10 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
-constexpr int kItems = 16;
-constexpr int kTile = kBlock * kItems;   // 4096 keys per tile
+constexpr int kItems = 8;
+constexpr int kTile = kBlock * kItems;   // 2048 keys per tile
 constexpr int kRadix = 256;
-constexpr int kMaxParts = 1024;
+constexpr int kMaxParts = 2048;
 
 inline int64_t parts_for(int64_t n_cap) {
   int64_t g = (n_cap + kTile - 1) / kTile;
@@ -63,44 +63,65 @@ __global__ void __launch_bounds__(kBlock) k_upsweep(const uint32_t* __restrict__
 }
 
 // (2) hist[part][digit] -> exclusive prefix over parts per digit (in place);
-// digit_base[digit] = exclusive prefix of the digit totals.
+// digit_base[digit] = exclusive prefix of the digit totals.  32 warps; warp w
+// owns a contiguous range of parts, lane l owns digits l, l+32, ..., l+224, so
+// every load is coalesced and independent of the previous one.
 __global__ void __launch_bounds__(1024) k_scan_hist(uint32_t* __restrict__ hist, int g, uint32_t* digit_base) {
-  // 4 groups of 256 threads; group k handles parts [k*gs, (k+1)*gs)
-  __shared__ uint32_t group_tot[4][kRadix];
-  __shared__ uint32_t warp_tot[kWarps];
-  const int d = threadIdx.x & (kRadix - 1);
-  const int grp = threadIdx.x >> 8;
-  const int gsz = (g + 3) / 4;
-  const int p0 = grp * gsz;
-  int p1 = p0 + gsz;
+  __shared__ uint32_t wtot[32][kRadix];   // per-warp digit totals, then per-warp offsets
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int per = (g + 31) / 32;
+  const int p0 = warp * per;
+  int p1 = p0 + per;
   if (p1 > g) p1 = g;
-  uint32_t run = 0;
-  for (int p = p0; p < p1; ++p) {
-    uint32_t c = hist[(size_t)p * kRadix + d];
-    hist[(size_t)p * kRadix + d] = run;
-    run += c;
-  }
-  group_tot[grp][d] = run;
-  __syncthreads();
-  uint32_t add = 0;
-  for (int k = 0; k < grp; ++k) add += group_tot[k][d];
-  if (add)
-    for (int p = p0; p < p1; ++p) hist[(size_t)p * kRadix + d] += add;
-  if (grp == 0) {
-    uint32_t tot = group_tot[0][d] + group_tot[1][d] + group_tot[2][d] + group_tot[3][d];
-    // exclusive scan of tot over the 256 digits (threads 0..255)
-    const int lane = d & 31, w = d >> 5;
-    uint32_t x = tot;
+  uint32_t run[8];
 #pragma unroll
-    for (int s = 1; s < 32; s <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, s);
-      if (lane >= s) x += y;
+  for (int k = 0; k < 8; ++k) run[k] = 0;
+  for (int p = p0; p < p1; ++p) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) run[k] += hist[(size_t)p * kRadix + lane + 32 * k];
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) wtot[warp][lane + 32 * k] = run[k];
+  __syncthreads();
+  // per digit: exclusive scan over the 32 warps (thread d < 256), digit totals, then digit bases
+  __shared__ uint32_t dtot[kRadix];
+  if (threadIdx.x < kRadix) {
+    const int d = threadIdx.x;
+    uint32_t acc = 0;
+    for (int w = 0; w < 32; ++w) {
+      const uint32_t c = wtot[w][d];
+      wtot[w][d] = acc;
+      acc += c;
     }
-    if (lane == 31) warp_tot[w] = x;
-    asm volatile("bar.sync 1, 256;");
-    uint32_t before = 0;
-    for (int k = 0; k < w; ++k) before += warp_tot[k];
-    digit_base[d] = before + x - tot;
+    dtot[d] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    // exclusive scan of the 256 digit totals by one warp (8 per lane)
+    uint32_t v[8], s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { v[k] = dtot[lane * 8 + k]; s += v[k]; }
+    uint32_t x = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
+    }
+    uint32_t ex = x - s;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { digit_base[lane * 8 + k] = ex; ex += v[k]; }
+  }
+  // second sweep: each part's per-digit exclusive prefix
+#pragma unroll
+  for (int k = 0; k < 8; ++k) run[k] = wtot[warp][lane + 32 * k];
+  for (int p = p0; p < p1; ++p) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const size_t i = (size_t)p * kRadix + lane + 32 * k;
+      const uint32_t c = hist[i];
+      hist[i] = run[k];
+      run[k] += c;
+    }
   }
 }
 
@@ -126,29 +147,50 @@ __global__ void __launch_bounds__(kBlock) k_downsweep(const uint32_t* __restrict
   int64_t beg, end;
   part_range(count_of(n_dev, n_cap), beg, end);
 
-  for (int64_t t0 = beg; t0 < end; t0 += kTile) {
-    const int tile_n = (int)((end - t0) < kTile ? (end - t0) : kTile);
-    for (int i = tid; i < kWarps * (kRadix + 1); i += kBlock) whist[i] = 0;
-    __syncthreads();
-    uint32_t key[kItems], val[kItems];
-    uint16_t rank[kItems];
+  // the keys/values of the next tile are loaded while the current one is ranked and scattered
+  uint32_t nkey[kItems], nval[kItems];
+  auto load_tile = [&](int64_t t0) {
+    const int tn = (int)((end - t0) < kTile ? (end - t0) : kTile);
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
       const int li = warp * (kTile / kWarps) + i * 32 + lane;
-      const bool ok = li < tile_n;
-      key[i] = ok ? keys_in[t0 + li] : 0u;
-      val[i] = ok ? (vals_in ? vals_in[t0 + li] : (uint32_t)(t0 + li)) : 0u;
+      const bool ok = li < tn;
+      nkey[i] = ok ? keys_in[t0 + li] : 0u;
+      nval[i] = ok ? (vals_in ? vals_in[t0 + li] : (uint32_t)(t0 + li)) : 0u;
     }
+  };
+  if (beg < end) load_tile(beg);
+  for (int64_t t0 = beg; t0 < end; t0 += kTile) {
+    const int tile_n = (int)((end - t0) < kTile ? (end - t0) : kTile);
+    uint32_t key[kItems], val[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      key[i] = nkey[i];
+      val[i] = nval[i];
+    }
+    if (t0 + kTile < end) load_tile(t0 + kTile);
+    for (int i = tid; i < kWarps * (kRadix + 1); i += kBlock) whist[i] = 0;
+    __syncthreads();
+    uint16_t rank[kItems];
     uint32_t* wh = whist + warp * (kRadix + 1);
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
       const int li = warp * (kTile / kWarps) + i * 32 + lane;
-      const uint32_t d = li < tile_n ? ((key[i] >> shift) & 0xffu) : (uint32_t)kRadix;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const bool ok = li < tile_n;
+      const uint32_t d = ok ? ((key[i] >> shift) & 0xffu) : (uint32_t)kRadix;
+      // lanes holding the same digit: intersect the 8 digit-bit ballots (and validity)
+      uint32_t peers = __ballot_sync(0xffffffffu, ok);
+      if (!ok) peers = ~peers;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t bb = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bb : ~bb;
+      }
       const uint32_t before = wh[d];
       rank[i] = (uint16_t)(before + __popc(peers & lt_mask));
       __syncwarp();
-      if ((peers & lt_mask) == 0 && d < (uint32_t)kRadix) wh[d] = before + __popc(peers);
+      if ((peers & lt_mask) == 0 && ok) wh[d] = before + __popc(peers);
       __syncwarp();
     }
     __syncthreads();
@@ -165,9 +207,9 @@ __global__ void __launch_bounds__(kBlock) k_downsweep(const uint32_t* __restrict
       // exclusive scan of tile totals over digits
       uint32_t x = run;
 #pragma unroll
-      for (int s = 1; s < 32; s <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, s);
-        if (lane >= s) x += y;
+      for (int s2 = 1; s2 < 32; s2 <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, s2);
+        if (lane >= s2) x += y;
       }
       if (lane == 31) wsum[warp] = x;
       __syncthreads();

@@ -102,7 +102,7 @@ def test_host_side_argument_errors(lib):
     neg = L.gs_map(fake, fake, fake, fake, -1)
     assert lib.gs_project(P(neg), fake, 1, P(prm), P(proj), fake, 1 << 20, None) == L.GS_ERR_ARG
     # bad parameters
-    for bad in (_params(tile_w=10), _params(tile_w=128, tile_h=2), _params(tile_w=16, tile_h=6), _params(tile_w=4, tile_h=16), _params(near_plane=0.0), _params(alpha_max=0.0),
+    for bad in (_params(tile_w=10), _params(tile_w=128, tile_h=2), _params(tile_w=16, tile_h=6), _params(tile_w=4, tile_h=16), _params(tile_w=16, tile_h=4), _params(near_plane=0.0), _params(alpha_max=0.0),
                 _params(alpha_min=1.0), _params(eps2d=-1.0), _params(T_min=1.0), _params(guard=float("nan"))):
         assert lib.gs_project(P(m), fake, 1, P(bad), P(proj), fake, 1 << 20, None) == L.GS_ERR_ARG
     # misaligned map pointer
