@@ -56,7 +56,7 @@ enum {
 enum {
   GS_FLAG_PAIR_OVERFLOW = 1u << 0,   /* more (tile, Gaussian) pairs than gs_bins.pair_capacity */
   GS_FLAG_RANGE_OVERFLOW = 1u << 1,  /* more tiles over all views than gs_bins.tile_capacity   */
-  GS_FLAG_BAD_CAMERA = 1u << 2,      /* a camera has width*height <= 0 or non-positive focal   */
+  GS_FLAG_BAD_CAMERA = 1u << 2,      /* a camera has width*height <= 0, a non-positive focal length or an invalid tile size */
   GS_FLAG_NONFINITE = 1u << 3,       /* informational: Gaussians with non-finite parameters were culled */
   GS_FLAG_RECORD_OVERFLOW = 1u << 4  /* more visible (Gaussian, view) records than capacity    */
 };
@@ -67,12 +67,16 @@ enum {
 /* Pinhole camera (Sec. III: intrinsics K, pose R_k, T_k in the world frame).
  * R is camera-to-world, row-major; world-to-camera is t = R^T (mu - T).
  * Axes: x right, y down, z forward.  Pixel (u, v) samples (u + 0.5, v + 0.5).
- * 72 bytes; arrays of cameras are DEVICE arrays. */
+ * tile_w, tile_h: this view's screen tile (same rules as gs_params.tile_w/h);
+ * 0, 0 selects gs_params.tile_w, tile_h.  Low-resolution views render faster
+ * with smaller tiles (shorter per-tile lists).
+ * 80 bytes; arrays of cameras are DEVICE arrays. */
 typedef struct {
   float fx, fy, cx, cy;
   int32_t width, height;
   float R[9];
   float T[3];
+  int32_t tile_w, tile_h;
 } gs_camera;
 
 /* Gaussian map (Sec. III: colour c, position mu, size, opacity; anisotropic
@@ -114,13 +118,17 @@ typedef struct {
  * buffers of `capacity` entries; capacity >= n * n_views never overflows.
  *   count      [1]        number of records written
  *   status     [1]        device status word (GS_FLAG_* bits), OR-ed by every call
- *   view_info  [V+1][2]   per view: (first global tile, first pixel); entry V holds the totals
+ *   view_info  [V+1][4]   per view: (first global tile, first pixel, first warp item,
+ *                         tile_w | tile_h << 8 | tiles_x << 16); entry V holds the totals.
+ *                         A warp item is one 8x4 pixel block of a tile: view v has
+ *                         tiles(v) * tile_w * tile_h / 32 of them.
  *   gid, view  [cap]      Gaussian index and view index of the record
- *   xyod       [cap][4]   (mu_2D x, mu_2D y, opacity, depth t_z)
- *   conic_u    [cap][4]   (inverse 2D covariance a, b, c with q = a dx^2 + 2 b dx dy + c dy^2, u)
+ *   mean_ext   [cap][4]   (mu_2D x, mu_2D y, support half-widths sqrt(Q Sigma_2D,xx), sqrt(Q Sigma_2D,yy))
+ *   conic_o    [cap][4]   (inverse 2D covariance a, b, c with q = a dx^2 + 2 b dx dy + c dy^2, opacity)
+ *   color_d    [cap][4]   (r, g, b, depth t_z)
+ *   unc        [cap]      uncertainty u of the Gaussian
  *   rect       [cap][4]   uint16 tile rectangle (x0, y0, x1, y1), ends exclusive
  *   depth_key  [cap]      IEEE-754 bits of the float32 depth (the sort key)
- *   ext        [cap][2]   support half-widths (sqrt(Q Sigma_2D,xx), sqrt(Q Sigma_2D,yy)) in pixels
  *   grp_mask   [G*V]      bit i of entry (k, v) = Gaussian 32k+i is visible in view v (G = ceil(n/32))
  *   grp_base   [G*V+1]    index of the first record of (group k, view v) at k*V + v; last entry = count
  * The record of Gaussian g in view v is grp_base[k*V+v] + popcount(grp_mask[k*V+v] & ((1 << i) - 1))
@@ -132,11 +140,12 @@ typedef struct {
   uint32_t* view_info;
   uint32_t* gid;
   uint32_t* view;
-  float* xyod;
-  float* conic_u;
+  float* mean_ext;
+  float* conic_o;
+  float* color_d;
+  float* unc;
   uint16_t* rect;
   uint32_t* depth_key;
-  float* ext;
   uint32_t* grp_mask;
   uint32_t* grp_base;
 } gs_proj;
@@ -166,7 +175,8 @@ gs_status gs_project(const gs_map* map, const gs_camera* cams, int32_t n_views, 
  *   rec     [pair_capacity]   record index of each pair
  *   ranges  [tile_capacity][2] per global tile: [start, end) into tile/rec
  * Global tile id of tile (x, y) of view v = view_info[v].first_tile + y * tiles_x(v) + x,
- * tiles_x(v) = ceil(W_v / tile_w), tiles_y(v) = ceil(H_v / tile_h). */
+ * tiles_x(v) = ceil(W_v / tile_w(v)), tiles_y(v) = ceil(H_v / tile_h(v)) with the
+ * view's tile size (its camera's, else gs_params'). */
 typedef struct {
   int64_t pair_capacity;
   int64_t tile_capacity;

@@ -51,7 +51,7 @@
 enum { P_TILE_W = 0, P_TILE_H, P_EPS2D, P_NEAR, P_GUARD, P_ALPHA_MIN, P_ALPHA_MAX, P_T_MIN, P_COUNT };
 
 /* camera block: 16 floats per view: fx fy cx cy R00..R22 (camera-to-world, row-major) Tx Ty Tz;
- * plus 2 ints per view: width height.                                        */
+ * plus 4 ints per view: width height tile_w tile_h (tile size of that view).  */
 #define CAMF 16
 
 int or_num_threads(void) {
@@ -191,7 +191,7 @@ static int dec_view(const float* mo, const dec_gauss* dg, const float* cam, cons
   const float* R = cam + 4;
   const float* T = cam + 13;
   int W = wh[0], H = wh[1];
-  int tw = (int)prm[P_TILE_W], th = (int)prm[P_TILE_H];
+  int tw = wh[2], th = wh[3];
   float near = (float)prm[P_NEAR], guard = (float)prm[P_GUARD], eps = (float)prm[P_EPS2D];
   if (W <= 0 || H <= 0) return 0;
   float dx = mo[0] - T[0], dy = mo[1] - T[1], dz = mo[2] - T[2];
@@ -313,7 +313,7 @@ void or_project(int64_t N, const float* mo32, const float* su32, const float* q3
       int64_t o = (int64_t)v * N + g;
       uint32_t key = 0;
       int r4[4] = {0, 0, 0, 0};
-      int ok = dec_view(mo32 + 4 * g, &dg, cam + CAMF * v, camwh + 2 * v, prm, &key, r4);
+      int ok = dec_view(mo32 + 4 * g, &dg, cam + CAMF * v, camwh + 4 * v, prm, &key, r4);
       vis[o] = (int8_t)ok;
       dkey[o] = key;
       for (int k = 0; k < 4; ++k) rect[4 * o + k] = r4[k];
@@ -394,7 +394,7 @@ void or_render(int64_t N, const float* mo32, const float* su32, const float* q32
   char* need = (char*)calloc((size_t)(V > 0 ? V : 1), 1);
   for (int64_t k = 0; k < K; ++k) need[pix[3 * k]] = 1;
   for (int v = 0; v < V; ++v)
-    if (need[v]) build_view_list(N, mo32, su32, q32, mo64, su64, q64, cam + CAMF * v, camwh + 2 * v, prm, &L[v]);
+    if (need[v]) build_view_list(N, mo32, su32, q32, mo64, su64, q64, cam + CAMF * v, camwh + 4 * v, prm, &L[v]);
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t k = 0; k < K; ++k) {
     int v = pix[3 * k];
@@ -471,7 +471,7 @@ void or_grad(int64_t N, const float* mo32, const float* su32, const float* q32,
     for (int64_t k = 0; k < K; ++k) any |= (pix[3 * k] == v);
     if (!any) continue;
     view_list L;
-    build_view_list(N, mo32, su32, q32, mo64, su64, q64, camf, camwh + 2 * v, prm, &L);
+    build_view_list(N, mo32, su32, q32, mo64, su64, q64, camf, camwh + 4 * v, prm, &L);
     double* Gv = G + (size_t)v * (size_t)N * 8;
 #pragma omp parallel
     {

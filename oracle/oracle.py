@@ -106,15 +106,21 @@ def smooth_params(**kw) -> Params:
     return p
 
 
-def _cams(cams):
+def view_tile(c, params: Params):
+    """Tile size of a view: the camera's own (attributes tile_w, tile_h, if non-zero) else the params'."""
+    tw, th = getattr(c, "tile_w", 0), getattr(c, "tile_h", 0)
+    return (tw, th) if tw and th else (params.tile_w, params.tile_h)
+
+
+def _cams(cams, params: Params):
     V = len(cams)
     cf = np.zeros((V, 16), np.float32)
-    wh = np.zeros((V, 2), np.int32)
+    wh = np.zeros((V, 4), np.int32)
     for v, c in enumerate(cams):
         cf[v, 0:4] = [c.fx, c.fy, c.cx, c.cy]
         cf[v, 4:13] = np.asarray(c.R, np.float32).reshape(9)
         cf[v, 13:16] = np.asarray(c.T, np.float32).reshape(3)
-        wh[v] = [c.width, c.height]
+        wh[v] = [c.width, c.height, *view_tile(c, params)]
     return cf, wh
 
 
@@ -133,7 +139,7 @@ def project(gmap, cams, params: Params = Params()):
     lib = _load()
     (mo, su, q, rgb), (mo64, su64, q64, _) = _map(gmap)
     N, V = mo.shape[0], len(cams)
-    cf, wh = _cams(cams)
+    cf, wh = _cams(cams, params)
     prm = params.block()
     out = dict(vis=np.zeros((V, N), np.int8), dkey=np.zeros((V, N), np.uint32), rect=np.zeros((V, N, 4), np.int32),
                mean2d=np.zeros((V, N, 2)), conic=np.zeros((V, N, 3)), cov2d=np.zeros((V, N, 3)),
@@ -166,7 +172,7 @@ def render(gmap, cams, params: Params = Params(), pixels=None, delta: float = 1e
     (mo, su, q, rgb), (mo64, su64, q64, rgb64) = _map(gmap, values)
     pix = all_pixels(cams) if pixels is None else np.ascontiguousarray(pixels, np.int32)
     K = pix.shape[0]
-    cf, wh = _cams(cams)
+    cf, wh = _cams(cams, params)
     prm = params.block()
     out = np.zeros((K, 5))
     T = np.zeros(K)
@@ -225,7 +231,7 @@ def grad_pixels(gmap, cams, pixels, gpix, params: Params = Params(), values=None
     lib = _load()
     (mo, su, q, rgb), (mo64, su64, q64, rgb64) = _map(gmap, values)
     N = mo.shape[0]
-    cf, wh = _cams(cams)
+    cf, wh = _cams(cams, params)
     prm = params.block()
     pix = np.ascontiguousarray(pixels, np.int32).reshape(-1, 3)
     gp = np.ascontiguousarray(gpix, np.float64).reshape(-1, 4)
@@ -240,9 +246,9 @@ def grad_pixels(gmap, cams, pixels, gpix, params: Params = Params(), values=None
 
 
 def tile_grid(cams, params: Params = Params()):
-    """tiles_x per view and global tile base offsets (length V+1)."""
-    tx = np.array([-(-c.width // params.tile_w) for c in cams], np.int32)
-    ty = np.array([-(-c.height // params.tile_h) for c in cams], np.int32)
+    """tiles_x per view and global tile base offsets (length V+1), with each view's tile size."""
+    tx = np.array([-(-c.width // view_tile(c, params)[0]) for c in cams], np.int32)
+    ty = np.array([-(-c.height // view_tile(c, params)[1]) for c in cams], np.int32)
     base = np.zeros(len(cams) + 1, np.int64)
     base[1:] = np.cumsum(tx.astype(np.int64) * ty)
     return tx, base

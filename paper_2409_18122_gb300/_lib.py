@@ -28,7 +28,8 @@ GS_NOALLOC_MAX_RECORDS = 1 << 18
 
 class gs_camera(ctypes.Structure):
     _fields_ = [("fx", c_float), ("fy", c_float), ("cx", c_float), ("cy", c_float),
-                ("width", c_int32), ("height", c_int32), ("R", c_float * 9), ("T", c_float * 3)]
+                ("width", c_int32), ("height", c_int32), ("R", c_float * 9), ("T", c_float * 3),
+                ("tile_w", c_int32), ("tile_h", c_int32)]
 
 
 class gs_map(ctypes.Structure):
@@ -42,9 +43,9 @@ class gs_params(ctypes.Structure):
 
 class gs_proj(ctypes.Structure):
     _fields_ = [("capacity", c_int64), ("count", c_void_p), ("status", c_void_p), ("view_info", c_void_p),
-                ("gid", c_void_p), ("view", c_void_p), ("xyod", c_void_p), ("conic_u", c_void_p),
-                ("rect", c_void_p), ("depth_key", c_void_p), ("ext", c_void_p), ("grp_mask", c_void_p),
-                ("grp_base", c_void_p)]
+                ("gid", c_void_p), ("view", c_void_p), ("mean_ext", c_void_p), ("conic_o", c_void_p),
+                ("color_d", c_void_p), ("unc", c_void_p), ("rect", c_void_p), ("depth_key", c_void_p),
+                ("grp_mask", c_void_p), ("grp_base", c_void_p)]
 
 
 class gs_bins(ctypes.Structure):
@@ -65,7 +66,7 @@ class gs_map_grad(ctypes.Structure):
     _fields_ = [("dmo", c_void_p), ("dsu", c_void_p), ("dq", c_void_p), ("drgb", c_void_p)]
 
 
-assert ctypes.sizeof(gs_camera) == 72
+assert ctypes.sizeof(gs_camera) == 80
 assert ctypes.sizeof(gs_params) == 32
 
 # name -> (restype, argtypes); the exported C ABI

@@ -68,8 +68,8 @@ __global__ void __launch_bounds__(256) k_emit(const gs_proj proj, const gs_camer
       r = srec[i];
       const ushort4 rc = reinterpret_cast<const ushort4*>(proj.rect)[r];
       const uint32_t v = proj.view[r];
-      tx = (uint32_t)((cams[v].width + tile_w - 1) / tile_w);
-      tile0 = proj.view_info[2 * v] + (uint32_t)rc.y * tx + rc.x;
+      tx = proj.view_info[kVI * v + 3] >> 16;
+      tile0 = proj.view_info[kVI * v] + (uint32_t)rc.y * tx + rc.x;
       w = (uint32_t)(rc.z - rc.x);
       cnt = w * (uint32_t)(rc.w - rc.y);
       if (w == 0) w = 1;
@@ -115,7 +115,7 @@ __global__ void k_ranges(const uint32_t* __restrict__ tile, const uint32_t* n_de
                          int64_t tile_cap, const uint32_t* __restrict__ view_info, int n_views,
                          uint32_t* __restrict__ ranges, uint32_t* status) {
   const int64_t n = clamp_count(n_dev, pair_cap);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && (int64_t)view_info[2 * n_views] > tile_cap)
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (int64_t)view_info[kVI * n_views] > tile_cap)
     set_flag(status, GS_FLAG_RANGE_OVERFLOW);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t t = tile[i];

@@ -22,11 +22,15 @@ namespace gs {
 // ---------------------------------------------------------------- constants
 constexpr int kMaxViewsPerChunk = 128;   // cameras staged in shared memory at a time
 
-// view_info layout: [V+1][2] = (first global tile, first pixel)
-struct ViewInfo {
-  uint32_t tile_base;
-  uint32_t pix_base;
-};
+// view_info layout: [V+1][4] = (first global tile, first pixel, first warp item,
+// tile_w | tile_h << 8 | tiles_x << 16); a warp item is an 8x4 pixel block of a tile.
+constexpr int kVI = 4;
+
+__host__ __device__ __forceinline__ bool valid_tile(int tw, int th) {
+  const int b = tw * th;
+  return (tw == 8 || tw == 16 || tw == 32 || tw == 64) && th >= 8 && th % 8 == 0 &&
+         (b == 64 || b == 128 || b == 256 || b == 512 || b == 1024);
+}
 
 // Per-view constants derived from a gs_camera, staged in shared memory.
 struct CamC {
@@ -35,6 +39,7 @@ struct CamC {
   float T[3];
   float gx, gy;          // guard-band slopes guard * (W/2) / fx, guard * (H/2) / fy
   int W, H;
+  int tw, th;            // this view's tile size
   int tiles_x, tiles_y;
   uint32_t tile_base;
   uint32_t pix_base;
@@ -179,7 +184,8 @@ struct ViewProj {
 
 // Returns true if the Gaussian is visible in the view and fills `vp`.
 __device__ __forceinline__ bool view_proj(float4 mo, const GaussPre& g, const CamC& c, float near_plane,
-                                          float eps2d, int tile_w, int tile_h, ViewProj& vp) {
+                                          float eps2d, ViewProj& vp) {
+  const int tile_w = c.tw, tile_h = c.th;
   if (!g.valid) return false;
   const float* R = c.R;
   float dx = fsub(mo.x, c.T[0]), dy = fsub(mo.y, c.T[1]), dz = fsub(mo.z, c.T[2]);
@@ -236,9 +242,19 @@ __device__ __forceinline__ bool view_proj(float4 mo, const GaussPre& g, const Ca
   return true;
 }
 
+// Tile size of a view: the camera's own if set, else the default.
+__device__ __forceinline__ void view_tile(const gs_camera& g, int def_w, int def_h, int& tw, int& th) {
+  tw = (g.tile_w > 0 && g.tile_h > 0) ? g.tile_w : def_w;
+  th = (g.tile_w > 0 && g.tile_h > 0) ? g.tile_h : def_h;
+}
+
 // Camera -> per-view constants (guard slopes computed with the same operations
 // on every device so the cull decision is reproducible).
-__device__ __forceinline__ void load_cam(const gs_camera& g, float guard, int tile_w, int tile_h, CamC& c) {
+__device__ __forceinline__ void load_cam(const gs_camera& g, float guard, int def_tw, int def_th, CamC& c) {
+  int tile_w, tile_h;
+  view_tile(g, def_tw, def_th, tile_w, tile_h);
+  c.tw = tile_w;
+  c.th = tile_h;
   c.fx = g.fx; c.fy = g.fy; c.cx = g.cx; c.cy = g.cy;
 #pragma unroll
   for (int i = 0; i < 9; ++i) c.R[i] = g.R[i];
@@ -257,12 +273,12 @@ __device__ __forceinline__ void set_flag(uint32_t* status, uint32_t f) {
   if (status) atomicOr(status, f);
 }
 
-__device__ __forceinline__ int find_view(const uint32_t* view_info, int n_views, uint32_t tile) {
-  // largest v with tile_base[v] <= tile
+// Largest v with view_info[v].field <= key (field 0: first tile, 2: first warp item).
+__device__ __forceinline__ int find_view(const uint32_t* view_info, int n_views, uint32_t key, int field) {
   int lo = 0, hi = n_views - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    if (view_info[2 * mid] <= tile) lo = mid; else hi = mid - 1;
+    if (view_info[kVI * mid + field] <= key) lo = mid; else hi = mid - 1;
   }
   return lo;
 }

@@ -18,52 +18,77 @@ namespace {
 
 constexpr int kBlock = 256;
 
-// Per-view table: tile and pixel offsets (prefix sums over views), camera checks.
-__global__ void __launch_bounds__(1024) k_view_info(const gs_camera* __restrict__ cams, int n_views, int tile_w,
-                                                    int tile_h, uint32_t* __restrict__ view_info,
+__device__ __forceinline__ bool camera_ok(const gs_camera& c, int tw, int th) {
+  return c.width > 0 && c.height > 0 && c.fx > 0.f && c.fy > 0.f && isfinite(c.fx) && isfinite(c.fy) &&
+         valid_tile(tw, th);
+}
+
+// Per-view table: tile, pixel and warp-item offsets (prefix sums over views), tile
+// sizes, camera checks.
+__global__ void __launch_bounds__(1024) k_view_info(const gs_camera* __restrict__ cams, int n_views, int def_tw,
+                                                    int def_th, uint32_t* __restrict__ view_info,
                                                     uint32_t* status) {
-  __shared__ unsigned long long s_tiles[32], s_pix[32];
+  __shared__ unsigned long long s_sum[3][32];
   const int per = (n_views + blockDim.x - 1) / blockDim.x;
   const int v0 = threadIdx.x * per;
   int v1 = v0 + per;
   if (v1 > n_views) v1 = n_views;
-  unsigned long long t = 0, p = 0;
+  unsigned long long acc[3] = {0, 0, 0};   // tiles, pixels, warp items
   bool bad = false;
   for (int v = v0; v < v1; ++v) {
     const gs_camera& c = cams[v];
-    const bool ok = c.width > 0 && c.height > 0 && c.fx > 0.f && c.fy > 0.f && isfinite(c.fx) && isfinite(c.fy);
-    if (!ok) { bad = true; continue; }
-    t += (unsigned long long)((c.width + tile_w - 1) / tile_w) * (unsigned long long)((c.height + tile_h - 1) / tile_h);
-    p += (unsigned long long)c.width * (unsigned long long)c.height;
+    int tw, th;
+    view_tile(c, def_tw, def_th, tw, th);
+    if (!camera_ok(c, tw, th)) { bad = true; continue; }
+    const unsigned long long t = (unsigned long long)((c.width + tw - 1) / tw) * ((c.height + th - 1) / th);
+    acc[0] += t;
+    acc[1] += (unsigned long long)c.width * (unsigned long long)c.height;
+    acc[2] += t * (unsigned long long)(tw * th / 32);
   }
   if (bad) set_flag(status, GS_FLAG_BAD_CAMERA);
-  // block exclusive scan of (t, p)
+  // block exclusive scan of the three sums
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long xt = t, xp = p;
+  unsigned long long x[3] = {acc[0], acc[1], acc[2]};
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    unsigned long long yt = __shfl_up_sync(0xffffffffu, xt, d), yp = __shfl_up_sync(0xffffffffu, xp, d);
-    if (lane >= d) { xt += yt; xp += yp; }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x[k], d);
+      if (lane >= d) x[k] += y;
+    }
   }
-  if (lane == 31) { s_tiles[warp] = xt; s_pix[warp] = xp; }
+  if (lane == 31)
+    for (int k = 0; k < 3; ++k) s_sum[k][warp] = x[k];
   __syncthreads();
-  unsigned long long bt = 0, bp = 0;
-  for (int w = 0; w < warp; ++w) { bt += s_tiles[w]; bp += s_pix[w]; }
-  unsigned long long et = bt + xt - t, ep = bp + xp - p;
+  unsigned long long e[3];
+  for (int k = 0; k < 3; ++k) {
+    unsigned long long b = 0;
+    for (int w = 0; w < warp; ++w) b += s_sum[k][w];
+    e[k] = b + x[k] - acc[k];
+  }
   for (int v = v0; v < v1; ++v) {
     const gs_camera& c = cams[v];
-    view_info[2 * v] = (uint32_t)et;
-    view_info[2 * v + 1] = (uint32_t)ep;
-    const bool ok = c.width > 0 && c.height > 0 && c.fx > 0.f && c.fy > 0.f && isfinite(c.fx) && isfinite(c.fy);
+    int tw, th;
+    view_tile(c, def_tw, def_th, tw, th);
+    const bool ok = camera_ok(c, tw, th);
+    const uint32_t tx = ok ? (uint32_t)((c.width + tw - 1) / tw) : 0u;
+    view_info[kVI * v + 0] = (uint32_t)e[0];
+    view_info[kVI * v + 1] = (uint32_t)e[1];
+    view_info[kVI * v + 2] = (uint32_t)e[2];
+    view_info[kVI * v + 3] = ok ? ((uint32_t)tw | ((uint32_t)th << 8) | (tx << 16)) : 0u;
     if (ok) {
-      et += (unsigned long long)((c.width + tile_w - 1) / tile_w) * (unsigned long long)((c.height + tile_h - 1) / tile_h);
-      ep += (unsigned long long)c.width * (unsigned long long)c.height;
+      const unsigned long long t = (unsigned long long)tx * ((c.height + th - 1) / th);
+      e[0] += t;
+      e[1] += (unsigned long long)c.width * (unsigned long long)c.height;
+      e[2] += t * (unsigned long long)(tw * th / 32);
     }
   }
   if (threadIdx.x == blockDim.x - 1) {
-    if (et > 0xFFFFFFFFull || ep > 0xFFFFFFFFull) set_flag(status, GS_FLAG_RANGE_OVERFLOW);
-    view_info[2 * n_views] = (uint32_t)et;
-    view_info[2 * n_views + 1] = (uint32_t)ep;
+    if (e[0] > 0xFFFFFFFFull || e[1] > 0xFFFFFFFFull || e[2] > 0xFFFFFFFFull) set_flag(status, GS_FLAG_RANGE_OVERFLOW);
+    view_info[kVI * n_views + 0] = (uint32_t)e[0];
+    view_info[kVI * n_views + 1] = (uint32_t)e[1];
+    view_info[kVI * n_views + 2] = (uint32_t)e[2];
+    view_info[kVI * n_views + 3] = 0u;
   }
 }
 
@@ -73,12 +98,12 @@ __device__ __forceinline__ void stage_cams(const gs_camera* __restrict__ cams, c
     const gs_camera g = cams[v0 + i];
     CamC c;
     load_cam(g, p.guard, p.tile_w, p.tile_h, c);
-    if (!(g.width > 0 && g.height > 0 && g.fx > 0.f && g.fy > 0.f && isfinite(g.fx) && isfinite(g.fy))) {
+    if (!camera_ok(g, c.tw, c.th)) {
       c.W = 0;  // marks the view unusable
       c.H = 0;
     }
-    c.tile_base = view_info[2 * (v0 + i)];
-    c.pix_base = view_info[2 * (v0 + i) + 1];
+    c.tile_base = view_info[kVI * (v0 + i)];
+    c.pix_base = view_info[kVI * (v0 + i) + 1];
     s_cam[i] = c;
   }
 }
@@ -98,13 +123,14 @@ __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera*
   const uint32_t lt = (1u << lane) - 1u;
   const bool active = g < map.n;
   const bool grp_active = __any_sync(0xffffffffu, active);
-  float4 mo = make_float4(0.f, 0.f, 0.f, 0.f), su = mo, q = mo;
+  float4 mo = make_float4(0.f, 0.f, 0.f, 0.f), su = mo, q = mo, col = mo;
   GaussPre pre;
   pre.valid = false;
   if (active) {
     mo = __ldg(reinterpret_cast<const float4*>(map.mo) + g);
     su = __ldg(reinterpret_cast<const float4*>(map.su) + g);
     q = __ldg(reinterpret_cast<const float4*>(map.q) + g);
+    if (kWrite && out.color_d) col = __ldg(reinterpret_cast<const float4*>(map.rgb) + g);
     pre = gauss_pre(mo, su, q, p.alpha_min);
     if (!kWrite && !(finite4(mo) && isfinite(su.x) && isfinite(su.y) && isfinite(su.z) && finite4(q)))
       set_flag(out.status, GS_FLAG_NONFINITE);
@@ -119,7 +145,7 @@ __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera*
       const CamC& c = s_cam[i];
       ViewProj vp;
       const bool vis = active && pre.valid && c.W > 0 &&
-                       view_proj(mo, pre, c, p.near_plane, p.eps2d, p.tile_w, p.tile_h, vp);
+                       view_proj(mo, pre, c, p.near_plane, p.eps2d, vp);
       const uint32_t m = __ballot_sync(0xffffffffu, vis);
       const size_t slot = (size_t)grp * n_views + (v0 + i);
       if (!kWrite) {
@@ -132,12 +158,13 @@ __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera*
         if ((int64_t)dst < out.capacity) {
           out.gid[dst] = (uint32_t)g;
           out.view[dst] = (uint32_t)(v0 + i);
-          reinterpret_cast<float4*>(out.xyod)[dst] = make_float4(vp.mx, vp.my, pre.o, vp.depth);
-          reinterpret_cast<float4*>(out.conic_u)[dst] = make_float4(vp.ca, vp.cb, vp.cc, su.w);
+          reinterpret_cast<float4*>(out.mean_ext)[dst] = make_float4(vp.mx, vp.my, vp.rx, vp.ry);
+          reinterpret_cast<float4*>(out.conic_o)[dst] = make_float4(vp.ca, vp.cb, vp.cc, pre.o);
+          if (out.color_d) reinterpret_cast<float4*>(out.color_d)[dst] = make_float4(col.x, col.y, col.z, vp.depth);
+          out.unc[dst] = su.w;
           reinterpret_cast<ushort4*>(out.rect)[dst] =
               make_ushort4((unsigned short)vp.x0, (unsigned short)vp.y0, (unsigned short)vp.x1, (unsigned short)vp.y1);
           out.depth_key[dst] = __float_as_uint(vp.depth);
-          reinterpret_cast<float2*>(out.ext)[dst] = make_float2(vp.rx, vp.ry);
         }
       }
     }

@@ -22,21 +22,28 @@ constexpr int kFwdWarps = 2;   // warps (work items) per CTA: small CTAs free th
 constexpr int kIgWarps = 8;    // warps per CTA of the persistent information-gain kernel
 constexpr int kPix = 1;        // pixels per lane of the forward and information-gain kernels
 
+// The list walk of all compositing kernels is a four-stage software pipeline
+// over groups of 32 entries (one per lane).  While group g is composited, the
+// alpha/colour data of group g+32 is fetched -- only for entries whose support
+// box touches the warp's pixel block, decided from their means fetched one
+// iteration earlier -- the means of group g+64 are fetched, and the list
+// indices of group g+96.  Every fetch is issued one iteration before it is
+// used and none depends on a value loaded in the same iteration.
+
 __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_proj proj, gs_bins bins,
                                                                 const gs_camera* __restrict__ cams, int n_views,
                                                                 gs_params p, gs_image img, uint32_t n_items) {
-  __shared__ float4 s_stage[kFwdWarps][3][32];
+  __shared__ float4 s_stage[kFwdWarps][3][32];   // (mu_x, mu_y, u, -), (a, b, c, o), (r, g, b, depth)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t item = blockIdx.x * kFwdWarps + warp;
   if (item >= n_items) return;
-  const int wpt = warps_per_tile<kPix>(p);
   TileInfo ti;
-  if (!warp_tile_setup(proj, bins, cams, n_views, p, item / wpt, ti)) return;
+  if (!warp_item_setup<kPix>(proj, bins, cams, n_views, item, ti)) return;
   WarpBlock wb;
-  warp_block<kPix>(ti, p, (int)(item % wpt), wb);
-  float4* sx = s_stage[warp][0];
+  warp_block<kPix>(ti, wb);
+  float4* sm = s_stage[warp][0];
   float4* sc = s_stage[warp][1];
-  float4* sr = s_stage[warp][2];
+  float4* sk = s_stage[warp][2];
   const float pxc = (float)wb.px + 0.5f;
   float pyc[kPix];
   bool inside[kPix], done[kPix];
@@ -51,71 +58,79 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
     cr[q] = cg[q] = cb[q] = cd[q] = cu[q] = 0.f;
     last[q] = n_contrib[q] = 0;
   }
-  const uint32_t beg = ti.beg, n = ti.end - ti.beg;
-  const float4* rgb = reinterpret_cast<const float4*>(map.rgb);
-  // software pipeline over groups of 32 list entries: while group g is
-  // composited, the colours of group g+1, the records of group g+2 and the list
-  // indices of group g+3 are in flight
-  const uint32_t* rl = bins.rec + beg;
-  Entry e1, e2;
-  float4 c1 = make_float4(0.f, 0.f, 0.f, 0.f);
-  uint32_t gid2 = 0, r3 = 0;
-  if ((uint32_t)lane < n) {
-    load_entry(proj, bins, beg + lane, e1);
-    c1 = __ldg(rgb + __ldg(proj.gid + e1.rec));
+  const uint32_t n = ti.end - ti.beg;
+  const uint32_t* rl = bins.rec + ti.beg;
+  const float4* ME = reinterpret_cast<const float4*>(proj.mean_ext);
+  const float4* CO = reinterpret_cast<const float4*>(proj.conic_o);
+  const float4* CD = reinterpret_cast<const float4*>(proj.color_d);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  uint32_t rA = 0, rB = 0, rC = 0;
+  if ((uint32_t)lane < n) rA = __ldg(rl + lane);
+  if (32u + lane < n) rB = __ldg(rl + 32 + lane);
+  if (64u + lane < n) rC = __ldg(rl + 64 + lane);
+  float4 mA = z4, mB = z4;
+  if ((uint32_t)lane < n) mA = __ldg(ME + rA);
+  if (32u + lane < n) mB = __ldg(ME + rB);
+  bool ovA = (uint32_t)lane < n && box_overlaps(mA, wb);
+  float4 cA = z4, kA = z4;
+  float uA = 0.f;
+  if (ovA) {
+    cA = __ldg(CO + rA);
+    kA = __ldg(CD + rA);
+    uA = __ldg(proj.unc + rA);
   }
-  if (32u + lane < n) {
-    load_entry(proj, bins, beg + 32 + lane, e2);
-    gid2 = __ldg(proj.gid + e2.rec);
-  }
-  if (64u + lane < n) r3 = __ldg(rl + 64 + lane);
   for (uint32_t g = 0; g < n; g += 32) {
     if (!__any_sync(0xffffffffu, !all_done<kPix>(done))) break;
-    const Entry e = e1;
-    const float4 ergb = c1;
-    const bool ev = g + lane < n;
-    e1 = e2;
-    if (g + 32 + lane < n) c1 = __ldg(rgb + gid2);
-    if (g + 64 + lane < n) {
-      load_record(proj, r3, e2);
-      gid2 = __ldg(proj.gid + r3);
+    const bool ovB = g + 32 + lane < n && box_overlaps(mB, wb);
+    float4 cB = z4, kB = z4;
+    float uB = 0.f;
+    if (ovB) {
+      cB = __ldg(CO + rB);
+      kB = __ldg(CD + rB);
+      uB = __ldg(proj.unc + rB);
     }
-    if (g + 96 + lane < n) r3 = __ldg(rl + g + 96 + lane);
-    const bool ov = ev && box_overlaps(e.xyod, e.ext, wb);
-    uint32_t m = __ballot_sync(0xffffffffu, ov);
-    if (m == 0) continue;
-    if (ov) {
-      sx[lane] = e.xyod;
-      sc[lane] = e.con;
-      sr[lane] = ergb;
-    }
-    __syncwarp();
-    while (m) {
-      const int b = __ffs(m) - 1;
-      m &= m - 1;
-      if (all_done<kPix>(done)) continue;
-      const float4 a = sx[b];
-      const float4 k = sc[b];
-      const float4 c = sr[b];
-#pragma unroll
-      for (int q = 0; q < kPix; ++q) {
-        if (done[q]) continue;
-        const float alpha = splat_alpha(a, k, pxc, pyc[q], p.alpha_max);
-        if (alpha < p.alpha_min) continue;
-        const float Tn = T[q] * (1.f - alpha);
-        if (Tn < p.T_min) { done[q] = true; continue; }
-        const float w = alpha * T[q];
-        cr[q] += w * c.x;
-        cg[q] += w * c.y;
-        cb[q] += w * c.z;
-        cd[q] += w * a.w;
-        cu[q] += w * k.w;
-        T[q] = Tn;
-        last[q] = (int32_t)(g + b + 1);
-        ++n_contrib[q];
+    float4 mC = z4;
+    if (g + 64 + lane < n) mC = __ldg(ME + rC);
+    uint32_t rD = 0;
+    if (g + 96 + lane < n) rD = __ldg(rl + g + 96 + lane);
+    uint32_t m = __ballot_sync(0xffffffffu, ovA);
+    if (m) {
+      if (ovA) {
+        sm[lane] = make_float4(mA.x, mA.y, uA, 0.f);
+        sc[lane] = cA;
+        sk[lane] = kA;
       }
+      __syncwarp();
+      while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        if (all_done<kPix>(done)) continue;
+        const float4 mu = sm[b];
+        const float4 co = sc[b];
+        const float4 c = sk[b];
+#pragma unroll
+        for (int q = 0; q < kPix; ++q) {
+          if (done[q]) continue;
+          const float alpha = splat_alpha(mu.x, mu.y, co, pxc, pyc[q], p.alpha_max);
+          if (alpha < p.alpha_min) continue;
+          const float Tn = T[q] * (1.f - alpha);
+          if (Tn < p.T_min) { done[q] = true; continue; }
+          const float w = alpha * T[q];
+          cr[q] += w * c.x;
+          cg[q] += w * c.y;
+          cb[q] += w * c.z;
+          cd[q] += w * c.w;
+          cu[q] += w * mu.z;
+          T[q] = Tn;
+          last[q] = (int32_t)(g + b + 1);
+          ++n_contrib[q];
+        }
+      }
+      __syncwarp();
     }
-    __syncwarp();
+    mA = mB; ovA = ovB; cA = cB; kA = kB; uA = uB;
+    rB = rC; mB = mC;
+    rC = rD;
   }
   const size_t P = (size_t)ti.W * ti.H;
 #pragma unroll
@@ -137,38 +152,38 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
   }
 }
 
-// Persistent U-only compositing: every warp takes (tile, 8x4 block) work items
-// from a device counter until the batch is exhausted and writes the sum of U
-// over its 32 pixels to the item's own slot (fixed shuffle tree), never
-// accumulating, so the result does not depend on scheduling.
+// Persistent U-only compositing: every warp takes (tile, pixel block) work items
+// from a device counter, longest tile list first, until the batch is exhausted,
+// and writes the sum of U over its pixels to the item's own slot (fixed shuffle
+// tree), never accumulating, so the result does not depend on scheduling.
 __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bins bins,
                                                              const gs_camera* __restrict__ cams, int n_views,
                                                              gs_params p, const uint32_t* __restrict__ order,
-                                                             float* __restrict__ item_sum,
+                                                             float* __restrict__ item_sum, int64_t item_cap,
                                                              uint32_t* __restrict__ work) {
-  __shared__ float4 s_stage[kIgWarps][2][32];
+  __shared__ float4 s_stage[kIgWarps][2][32];   // (mu_x, mu_y, u, -), (a, b, c, o)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4* sx = s_stage[warp][0];
+  float4* sm = s_stage[warp][0];
   float4* sc = s_stage[warp][1];
-  const int wpt = warps_per_tile<kPix>(p);
-  const uint32_t total = proj.view_info[2 * n_views];
-  const uint32_t n_tiles = (int64_t)total < bins.tile_capacity ? total : (uint32_t)bins.tile_capacity;
-  const uint32_t n_items = n_tiles * (uint32_t)wpt;
+  uint32_t n_items = proj.view_info[kVI * n_views + 2] / kPix;
+  if ((int64_t)n_items > item_cap) n_items = (uint32_t)item_cap;
+  const float4* ME = reinterpret_cast<const float4*>(proj.mean_ext);
+  const float4* CO = reinterpret_cast<const float4*>(proj.conic_o);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   for (;;) {
     uint32_t item = 0;
     if (lane == 0) item = atomicAdd(work, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= n_items) break;
-    // items are handed out longest tile list first; the slot keeps the tile's own index
-    const uint32_t tile = __ldg(order + item / wpt);
-    const uint32_t slot = tile * (uint32_t)wpt + item % wpt;
+    // items are handed out longest tile list first; each writes its own slot
+    const uint32_t slot = __ldg(order + item);
     TileInfo ti;
-    if (!warp_tile_setup(proj, bins, cams, n_views, p, tile, ti)) {
+    if (!warp_item_setup<kPix>(proj, bins, cams, n_views, slot, ti)) {
       if (lane == 0) item_sum[slot] = 0.f;
       continue;
     }
     WarpBlock wb;
-    warp_block<kPix>(ti, p, (int)(item % wpt), wb);
+    warp_block<kPix>(ti, wb);
     const float pxc = (float)wb.px + 0.5f;
     float pyc[kPix], T[kPix], cu[kPix];
     bool done[kPix];
@@ -179,49 +194,64 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
       T[q] = 1.f;
       cu[q] = 0.f;
     }
-    const uint32_t beg = ti.beg, n = ti.end - ti.beg;
-    // three-stage software pipeline over groups of 32 list entries: while group g
-    // is composited, the records of groups g+1 and g+2 are in flight and the list
-    // indices of group g+3 are being fetched
-    Entry e1, e2;
-    uint32_t r3 = 0;
-    const uint32_t* rl = bins.rec + beg;
-    if ((uint32_t)lane < n) load_entry(proj, bins, beg + lane, e1);
-    if (32u + lane < n) load_entry(proj, bins, beg + 32 + lane, e2);
-    if (64u + lane < n) r3 = __ldg(rl + 64 + lane);
+    const uint32_t n = ti.end - ti.beg;
+    const uint32_t* rl = bins.rec + ti.beg;
+    uint32_t rA = 0, rB = 0, rC = 0;
+    if ((uint32_t)lane < n) rA = __ldg(rl + lane);
+    if (32u + lane < n) rB = __ldg(rl + 32 + lane);
+    if (64u + lane < n) rC = __ldg(rl + 64 + lane);
+    float4 mA = z4, mB = z4;
+    if ((uint32_t)lane < n) mA = __ldg(ME + rA);
+    if (32u + lane < n) mB = __ldg(ME + rB);
+    bool ovA = (uint32_t)lane < n && box_overlaps(mA, wb);
+    float4 cA = z4;
+    float uA = 0.f;
+    if (ovA) {
+      cA = __ldg(CO + rA);
+      uA = __ldg(proj.unc + rA);
+    }
     for (uint32_t g = 0; g < n; g += 32) {
       if (!__any_sync(0xffffffffu, !all_done<kPix>(done))) break;
-      const Entry e = e1;
-      const bool ev = g + lane < n;
-      e1 = e2;
-      if (g + 64 + lane < n) load_record(proj, r3, e2);
-      if (g + 96 + lane < n) r3 = __ldg(rl + g + 96 + lane);
-      const bool ov = ev && box_overlaps(e.xyod, e.ext, wb);
-      uint32_t m = __ballot_sync(0xffffffffu, ov);
-      if (m == 0) continue;
-      if (ov) {
-        sx[lane] = e.xyod;
-        sc[lane] = e.con;
+      const bool ovB = g + 32 + lane < n && box_overlaps(mB, wb);
+      float4 cB = z4;
+      float uB = 0.f;
+      if (ovB) {
+        cB = __ldg(CO + rB);
+        uB = __ldg(proj.unc + rB);
       }
-      __syncwarp();
-      while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        if (all_done<kPix>(done)) continue;
-        const float4 a = sx[b];
-        const float4 k = sc[b];
-#pragma unroll
-        for (int q = 0; q < kPix; ++q) {
-          if (done[q]) continue;
-          const float alpha = splat_alpha(a, k, pxc, pyc[q], p.alpha_max);
-          if (alpha < p.alpha_min) continue;
-          const float Tn = T[q] * (1.f - alpha);
-          if (Tn < p.T_min) { done[q] = true; continue; }
-          cu[q] += alpha * T[q] * k.w;
-          T[q] = Tn;
+      float4 mC = z4;
+      if (g + 64 + lane < n) mC = __ldg(ME + rC);
+      uint32_t rD = 0;
+      if (g + 96 + lane < n) rD = __ldg(rl + g + 96 + lane);
+      uint32_t m = __ballot_sync(0xffffffffu, ovA);
+      if (m) {
+        if (ovA) {
+          sm[lane] = make_float4(mA.x, mA.y, uA, 0.f);
+          sc[lane] = cA;
         }
+        __syncwarp();
+        while (m) {
+          const int b = __ffs(m) - 1;
+          m &= m - 1;
+          if (all_done<kPix>(done)) continue;
+          const float4 mu = sm[b];
+          const float4 co = sc[b];
+#pragma unroll
+          for (int q = 0; q < kPix; ++q) {
+            if (done[q]) continue;
+            const float alpha = splat_alpha(mu.x, mu.y, co, pxc, pyc[q], p.alpha_max);
+            if (alpha < p.alpha_min) continue;
+            const float Tn = T[q] * (1.f - alpha);
+            if (Tn < p.T_min) { done[q] = true; continue; }
+            cu[q] += alpha * T[q] * mu.z;
+            T[q] = Tn;
+          }
+        }
+        __syncwarp();
       }
-      __syncwarp();
+      mA = mB; ovA = ovB; cA = cB; uA = uB;
+      rB = rC; mB = mC;
+      rC = rD;
     }
     float su = 0.f;
 #pragma unroll
@@ -232,17 +262,16 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
   }
 }
 
-// IG_v = (1 / P_v) * sum over the items of the view's tiles, in a fixed order.
+// IG_v = (1 / P_v) * sum over the view's warp items, in a fixed order.
 __global__ void __launch_bounds__(256) k_ig_views(const uint32_t* __restrict__ view_info,
-                                                   const gs_camera* __restrict__ cams, int n_views, gs_params p,
-                                                   const float* __restrict__ item_sum, int64_t tile_cap,
+                                                   const gs_camera* __restrict__ cams, int n_views,
+                                                   const float* __restrict__ item_sum, int64_t item_cap,
                                                    float* __restrict__ ig) {
   __shared__ float s_red[32];
   const int v = blockIdx.x;
-  const uint32_t wpt = (uint32_t)warps_per_tile<kPix>(p);
-  uint32_t t1 = view_info[2 * v + 2];
-  if ((int64_t)t1 > tile_cap) t1 = (uint32_t)tile_cap;
-  const uint32_t i0 = view_info[2 * v] * wpt, i1 = t1 * wpt;
+  const uint32_t i0 = view_info[kVI * v + 2] / kPix;
+  uint32_t i1 = view_info[kVI * (v + 1) + 2] / kPix;
+  if ((int64_t)i1 > item_cap) i1 = (uint32_t)item_cap;
   const int W = cams[v].width, H = cams[v].height;
   float s = 0.f;
   // fixed assignment of items to threads and a fixed reduction tree: deterministic
@@ -255,14 +284,22 @@ __global__ void k_zero_words(uint32_t* p, int n) {
   if (threadIdx.x < n) p[threadIdx.x] = 0u;
 }
 
-// Sort key of each tile for longest-first scheduling: 0xFFFF - min(list length, 0xFFFF).
-__global__ void k_tile_cost(const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ view_info, int n_views,
-                            int64_t tile_cap, uint32_t* __restrict__ key) {
-  uint32_t n = view_info[2 * n_views];
-  if ((int64_t)n > tile_cap) n = (uint32_t)tile_cap;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    const uint32_t len = ranges[2 * (size_t)t + 1] - ranges[2 * (size_t)t];
-    key[t] = 0xFFFFu - (len < 0xFFFFu ? len : 0xFFFFu);
+// Sort key of each warp item for longest-first scheduling:
+// 0xFFFF - min(length of its tile's list, 0xFFFF).
+__global__ void k_item_cost(const gs_proj proj, const gs_bins bins, int n_views, int64_t item_cap,
+                            uint32_t* __restrict__ key) {
+  uint32_t n = proj.view_info[kVI * n_views + 2] / kPix;
+  if ((int64_t)n > item_cap) n = (uint32_t)item_cap;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int v = find_view(proj.view_info, n_views, i * kPix, 2);
+    const uint32_t code = proj.view_info[kVI * v + 3];
+    const uint32_t wpt = ((code & 0xffu) * ((code >> 8) & 0xffu)) / (32 * kPix);
+    uint32_t len = 0;
+    if (wpt) {
+      const uint32_t tile = proj.view_info[kVI * v] + (i - proj.view_info[kVI * v + 2] / kPix) / wpt;
+      if ((int64_t)tile < bins.tile_capacity) len = bins.ranges[2 * (size_t)tile + 1] - bins.ranges[2 * (size_t)tile];
+    }
+    key[i] = 0xFFFFu - (len < 0xFFFFu ? len : 0xFFFFu);
   }
 }
 
@@ -270,7 +307,7 @@ __global__ void k_tile_cost(const uint32_t* __restrict__ ranges, const uint32_t*
 
 cudaError_t launch_render_fwd(const gs_map& map, const gs_proj& proj, const gs_bins& bins, const gs_camera* cams,
                               int n_views, const gs_params& p, const gs_image& img, cudaStream_t st) {
-  const int64_t items = bins.tile_capacity * (int64_t)((p.tile_w * p.tile_h) / (32 * kPix));
+  const int64_t items = bins.tile_capacity * (32 / kPix);   // upper bound: at most 32 items per tile
   if (items > 0) {
     k_render_fwd<<<(unsigned)((items + kFwdWarps - 1) / kFwdWarps), kFwdWarps * 32, 0, st>>>(
         map, proj, bins, cams, n_views, p, img, (uint32_t)items);
@@ -283,14 +320,14 @@ size_t ig_ws_bytes(int64_t n, int n_views, int64_t pair_cap, int64_t tile_cap) {
   const int64_t rec_cap = n * (int64_t)n_views;
   Carver c(nullptr);
   c.take<uint32_t>(1);                                   // record count
-  c.take<uint32_t>(2 * (size_t)(n_views + 1));           // view info
+  c.take<uint32_t>(kVI * (size_t)(n_views + 1));         // view info
   c.take<uint32_t>(rec_cap);                             // gid
   c.take<uint32_t>(rec_cap);                             // view
-  c.take<float4>(rec_cap);                               // xyod
-  c.take<float4>(rec_cap);                               // conic_u
+  c.take<float4>(rec_cap);                               // mean_ext
+  c.take<float4>(rec_cap);                               // conic_o
+  c.take<float>(rec_cap);                                // unc
   c.take<ushort4>(rec_cap);                              // rect
   c.take<uint32_t>(rec_cap);                             // depth key
-  c.take<float2>(rec_cap);                               // ext
   const int64_t slots = ((n + 31) / 32) * (int64_t)n_views;
   c.take<uint32_t>(slots);                               // grp_mask
   c.take<uint32_t>(slots + 1);                           // grp_base
@@ -301,7 +338,7 @@ size_t ig_ws_bytes(int64_t n, int n_views, int64_t pair_cap, int64_t tile_cap) {
   c.take<float>(32 * tile_cap);                          // per work-item sums (<= 32 items per tile)
   c.take<uint32_t>(4);                                   // work counter
   size_t a = project_ws_bytes(n, n_views), b = bin_ws_bytes(rec_cap, pair_cap, tile_cap);
-  const size_t o = 4 * align_up(sizeof(uint32_t) * (size_t)tile_cap, 256) + sort_temp_bytes(tile_cap);
+  const size_t o = 4 * align_up(sizeof(uint32_t) * (size_t)(32 * tile_cap), 256) + sort_temp_bytes(32 * tile_cap);
   c.take<char>(a > b ? (a > o ? a : o) : (b > o ? b : o));
   return align_up(c.off, 256);
 }
@@ -315,14 +352,15 @@ cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_vie
   proj.capacity = rec_cap;
   proj.count = c.take<uint32_t>(1);
   proj.status = status;
-  proj.view_info = c.take<uint32_t>(2 * (size_t)(n_views + 1));
+  proj.view_info = c.take<uint32_t>(kVI * (size_t)(n_views + 1));
   proj.gid = c.take<uint32_t>(rec_cap);
   proj.view = c.take<uint32_t>(rec_cap);
-  proj.xyod = (float*)c.take<float4>(rec_cap);
-  proj.conic_u = (float*)c.take<float4>(rec_cap);
+  proj.mean_ext = (float*)c.take<float4>(rec_cap);
+  proj.conic_o = (float*)c.take<float4>(rec_cap);
+  proj.unc = c.take<float>(rec_cap);
+  proj.color_d = nullptr;   // not needed to score views: the projection skips the colours
   proj.rect = (uint16_t*)c.take<ushort4>(rec_cap);
   proj.depth_key = c.take<uint32_t>(rec_cap);
-  proj.ext = (float*)c.take<float2>(rec_cap);
   const int64_t slots = ((map.n + 31) / 32) * (int64_t)n_views;
   proj.grp_mask = c.take<uint32_t>(slots);
   proj.grp_base = c.take<uint32_t>(slots + 1);
@@ -336,7 +374,7 @@ cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_vie
   float* item_sum = c.take<float>(32 * tile_cap);
   uint32_t* work = c.take<uint32_t>(4);
   size_t a = project_ws_bytes(map.n, n_views), b = bin_ws_bytes(rec_cap, pair_cap, tile_cap);
-  const size_t o = 4 * align_up(sizeof(uint32_t) * (size_t)tile_cap, 256) + sort_temp_bytes(tile_cap);
+  const size_t o = 4 * align_up(sizeof(uint32_t) * (size_t)(32 * tile_cap), 256) + sort_temp_bytes(32 * tile_cap);
   void* inner = c.take<char>(a > b ? (a > o ? a : o) : (b > o ? b : o));
 
   cudaError_t e = launch_project(map, cams, n_views, p, proj, inner, st);
@@ -346,34 +384,35 @@ cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_vie
   k_zero_words<<<1, 32, 0, st>>>(work, 4);
   note_launch();
   // longest tile lists first (the inner workspace is free again once binning is done)
+  const int64_t item_cap = 32 * tile_cap;
   Carver oc(inner);
-  uint32_t* ok_a = oc.take<uint32_t>(tile_cap);
-  uint32_t* ov_a = oc.take<uint32_t>(tile_cap);
-  uint32_t* ok_b = oc.take<uint32_t>(tile_cap);
-  uint32_t* ov_b = oc.take<uint32_t>(tile_cap);
-  void* otmp = oc.take<char>(sort_temp_bytes(tile_cap));
+  uint32_t* ok_a = oc.take<uint32_t>(item_cap);
+  uint32_t* ov_a = oc.take<uint32_t>(item_cap);
+  uint32_t* ok_b = oc.take<uint32_t>(item_cap);
+  uint32_t* ov_b = oc.take<uint32_t>(item_cap);
+  void* otmp = oc.take<char>(sort_temp_bytes(item_cap));
   {
-    int64_t gb = (tile_cap + 255) / 256;
+    int64_t gb = (item_cap + 255) / 256;
     if (gb > 4096) gb = 4096;
-    k_tile_cost<<<(unsigned)gb, 256, 0, st>>>(bins.ranges, proj.view_info, n_views, tile_cap, ok_a);
+    k_item_cost<<<(unsigned)gb, 256, 0, st>>>(proj, bins, n_views, item_cap, ok_a);
     note_launch();
   }
   bool in_a = false;
-  e = radix_sort(ok_a, nullptr, nullptr, SortBufs{ok_a, ov_a, ok_b, ov_b}, proj.view_info + 2 * n_views, tile_cap, 0,
-                 16, otmp, st, &in_a);
+  e = radix_sort(ok_a, nullptr, nullptr, SortBufs{ok_a, ov_a, ok_b, ov_b}, proj.view_info + kVI * n_views + 2,
+                 item_cap, 0, 16, otmp, st, &in_a);
   if (e != cudaSuccess) return e;
   const uint32_t* order = in_a ? ov_a : ov_b;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ig_items, kIgWarps * 32, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  const int64_t items = tile_cap * (int64_t)((p.tile_w * p.tile_h) / (32 * kPix));
   int64_t grid = (int64_t)device_sm_count() * per_sm;
-  if (grid * kIgWarps > items) grid = (items + kIgWarps - 1) / kIgWarps;
+  if (grid * kIgWarps > item_cap) grid = (item_cap + kIgWarps - 1) / kIgWarps;
   if (grid < 1) grid = 1;
-  k_ig_items<<<(unsigned)grid, kIgWarps * 32, 0, st>>>(proj, bins, cams, n_views, p, order, item_sum, work);
+  k_ig_items<<<(unsigned)grid, kIgWarps * 32, 0, st>>>(proj, bins, cams, n_views, p, order, item_sum, item_cap,
+                                                       work);
   note_launch();
-  k_ig_views<<<n_views, 256, 0, st>>>(proj.view_info, cams, n_views, p, item_sum, tile_cap, ig_out);
+  k_ig_views<<<n_views, 256, 0, st>>>(proj.view_info, cams, n_views, item_sum, item_cap, ig_out);
   note_launch();
   return cudaGetLastError();
 }

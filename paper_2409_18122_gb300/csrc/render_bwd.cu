@@ -36,11 +36,10 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t item = blockIdx.x * kBwdWarps + warp;
   if (item >= n_items) return;
-  const int wpt = warps_per_tile<kPix>(p);
   TileInfo ti;
-  if (!warp_tile_setup(proj, bins, cams, n_views, p, item / wpt, ti)) return;
+  if (!warp_item_setup<kPix>(proj, bins, cams, n_views, item, ti)) return;
   WarpBlock wb;
-  warp_block<kPix>(ti, p, (int)(item % wpt), wb);
+  warp_block<kPix>(ti, wb);
   float4* sx = s_stage[warp][0];
   float4* sc = s_stage[warp][1];
   float4* sr = s_stage[warp][2];
@@ -79,108 +78,115 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
   for (int q = 0; q < kPix; ++q) my_last = max(my_last, last[q]);
   const int wlast = (int)__reduce_max_sync(0xffffffffu, (unsigned)my_last);
   if (wlast == 0) return;
-  const uint32_t beg = ti.beg;
-  const float4* rgb = reinterpret_cast<const float4*>(map.rgb);
-  // walk groups of 32 entries from the last one any lane used back to the first;
-  // while group g is processed, the colours of the previous group, the records
-  // of the one before and the list indices of the one before that are in flight
-  const uint32_t* rl = bins.rec + beg;
+  // groups of 32 entries are walked from the last one any lane used back to the
+  // first, with the same four-stage pipeline as the forward kernel (alpha and
+  // colour data of the next group, means of the one after, list indices of the
+  // one after that)
+  const uint32_t* rl = bins.rec + ti.beg;
+  const float4* ME = reinterpret_cast<const float4*>(proj.mean_ext);
+  const float4* CO = reinterpret_cast<const float4*>(proj.conic_o);
+  const float4* CD = reinterpret_cast<const float4*>(proj.color_d);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   int g = ((wlast - 1) >> 5) << 5;
-  Entry e1, e2;
-  float4 c1 = make_float4(0.f, 0.f, 0.f, 0.f);
-  uint32_t gid2 = 0, r3 = 0;
-  if (g + lane < wlast) {
-    load_entry(proj, bins, beg + g + lane, e1);
-    c1 = __ldg(rgb + __ldg(proj.gid + e1.rec));
+  uint32_t rA = 0, rB = 0, rC = 0;
+  if (g + lane < wlast) rA = __ldg(rl + g + lane);
+  if (g >= 32) rB = __ldg(rl + g - 32 + lane);
+  if (g >= 64) rC = __ldg(rl + g - 64 + lane);
+  float4 mA = z4, mB = z4;
+  if (g + lane < wlast) mA = __ldg(ME + rA);
+  if (g >= 32) mB = __ldg(ME + rB);
+  bool ovA = g + lane < wlast && box_overlaps(mA, wb);
+  float4 cA = z4, kA = z4;
+  if (ovA) {
+    cA = __ldg(CO + rA);
+    kA = __ldg(CD + rA);
   }
-  if (g >= 32) {
-    load_entry(proj, bins, beg + g - 32 + lane, e2);
-    gid2 = __ldg(proj.gid + e2.rec);
-  }
-  if (g >= 64) r3 = __ldg(rl + g - 64 + lane);
   for (; g >= 0; g -= 32) {
-    const Entry e = e1;
-    const float4 ergb = c1;
-    const bool ev = g + lane < wlast;
-    e1 = e2;
-    if (g >= 32) c1 = __ldg(rgb + gid2);
-    if (g >= 64) {
-      load_record(proj, r3, e2);
-      gid2 = __ldg(proj.gid + r3);
+    const bool ovB = g >= 32 && box_overlaps(mB, wb);
+    float4 cB = z4, kB = z4;
+    if (ovB) {
+      cB = __ldg(CO + rB);
+      kB = __ldg(CD + rB);
     }
-    if (g >= 96) r3 = __ldg(rl + g - 96 + lane);
-    const bool ov = ev && box_overlaps(e.xyod, e.ext, wb);
-    uint32_t m = __ballot_sync(0xffffffffu, ov);
-    if (m == 0) continue;
-    if (ov) {
-      sx[lane] = e.xyod;
-      sc[lane] = e.con;
-      sr[lane] = ergb;
-      srec[lane] = e.rec;
-    }
-    __syncwarp();
-    while (m) {
-      const int b = 31 - __clz(m);
-      m ^= 1u << b;
-      const int pos = g + b;   // position in the tile's list
-      const float4 a = sx[b];
-      const float4 k = sc[b];
-      bool contrib[kPix];
-      float al[kPix], G[kPix], dx[kPix], dy[kPix];
+    float4 mC = z4;
+    if (g >= 64) mC = __ldg(ME + rC);
+    uint32_t rD = 0;
+    if (g >= 96) rD = __ldg(rl + g - 96 + lane);
+    uint32_t m = __ballot_sync(0xffffffffu, ovA);
+    if (m) {
+      if (ovA) {
+        sx[lane] = make_float4(mA.x, mA.y, 0.f, 0.f);
+        sc[lane] = cA;
+        sr[lane] = kA;
+        srec[lane] = rA;
+      }
+      __syncwarp();
+      while (m) {
+        const int b = 31 - __clz(m);
+        m ^= 1u << b;
+        const int pos = g + b;   // position in the tile's list
+        const float4 mu = sx[b];
+        const float4 k = sc[b];
+        bool contrib[kPix];
+        float al[kPix], G[kPix], dx[kPix], dy[kPix];
 #pragma unroll
-      for (int q = 0; q < kPix; ++q) {
-        contrib[q] = inside[q] && pos < last[q];
-        al[q] = G[q] = dx[q] = dy[q] = 0.f;
-        if (contrib[q]) {
-          al[q] = splat_alpha_dxy(a, k, pxc, pyc[q], p.alpha_max, dx[q], dy[q], G[q]);
-          if (al[q] < p.alpha_min) contrib[q] = false;
+        for (int q = 0; q < kPix; ++q) {
+          contrib[q] = inside[q] && pos < last[q];
+          al[q] = G[q] = dx[q] = dy[q] = 0.f;
+          if (contrib[q]) {
+            al[q] = splat_alpha_dxy(mu.x, mu.y, k, pxc, pyc[q], p.alpha_max, dx[q], dy[q], G[q]);
+            if (al[q] < p.alpha_min) contrib[q] = false;
+          }
+        }
+        bool any_c = false;
+#pragma unroll
+        for (int q = 0; q < kPix; ++q) any_c = any_c || contrib[q];
+        if (!__any_sync(0xffffffffu, any_c)) continue;
+        float v[10];
+#pragma unroll
+        for (int i = 0; i < 10; ++i) v[i] = 0.f;
+        const float4 c = sr[b];
+#pragma unroll
+        for (int q = 0; q < kPix; ++q) {
+          if (!contrib[q]) continue;
+          const float om = 1.f - al[q];
+          const float Ti = T[q] / om;
+          const float w = al[q] * Ti;
+          const float dalpha = (gr[q] * c.x + gg[q] * c.y + gb[q] * c.z + gd[q] * c.w) * Ti -
+                               (gr[q] * Sr[q] + gg[q] * Sg[q] + gb[q] * Sb[q] + gd[q] * Sd[q]) / om;
+          Sr[q] += w * c.x;
+          Sg[q] += w * c.y;
+          Sb[q] += w * c.z;
+          Sd[q] += w * c.w;
+          T[q] = Ti;
+          v[7] += gr[q] * w;
+          v[8] += gg[q] * w;
+          v[9] += gb[q] * w;
+          v[6] += gd[q] * w;
+          if (__fmul_rn(k.w, G[q]) < p.alpha_max) {     // not clamped
+            v[5] += dalpha * G[q];                           // dL/do
+            const float dq = -0.5f * al[q] * dalpha;         // dL/dq
+            v[0] += dq * 2.f * (k.x * dx[q] + k.y * dy[q]);  // dL/dmu_x (dx = mu_x - p_x)
+            v[1] += dq * 2.f * (k.y * dx[q] + k.z * dy[q]);  // dL/dmu_y
+            v[2] += dq * dx[q] * dx[q];                      // dL/da
+            v[3] += dq * 2.f * dx[q] * dy[q];                // dL/db
+            v[4] += dq * dy[q] * dy[q];                      // dL/dc
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 10; ++i) v[i] = warp_sum(v[i]);
+        if (lane == 0) {
+          float4* dst = g2d + 3 * (size_t)srec[b];
+          atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
+          atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], 0.f));
+          atomicAdd(dst + 2, make_float4(v[7], v[8], v[9], 0.f));
         }
       }
-      bool any_c = false;
-#pragma unroll
-      for (int q = 0; q < kPix; ++q) any_c = any_c || contrib[q];
-      if (!__any_sync(0xffffffffu, any_c)) continue;
-      float v[10];
-#pragma unroll
-      for (int i = 0; i < 10; ++i) v[i] = 0.f;
-      const float4 c = sr[b];
-#pragma unroll
-      for (int q = 0; q < kPix; ++q) {
-        if (!contrib[q]) continue;
-        const float om = 1.f - al[q];
-        const float Ti = T[q] / om;
-        const float w = al[q] * Ti;
-        const float dalpha = (gr[q] * c.x + gg[q] * c.y + gb[q] * c.z + gd[q] * a.w) * Ti -
-                             (gr[q] * Sr[q] + gg[q] * Sg[q] + gb[q] * Sb[q] + gd[q] * Sd[q]) / om;
-        Sr[q] += w * c.x;
-        Sg[q] += w * c.y;
-        Sb[q] += w * c.z;
-        Sd[q] += w * a.w;
-        T[q] = Ti;
-        v[7] += gr[q] * w;
-        v[8] += gg[q] * w;
-        v[9] += gb[q] * w;
-        v[6] += gd[q] * w;
-        if (__fmul_rn(a.z, G[q]) < p.alpha_max) {   // not clamped
-          v[5] += dalpha * G[q];                       // dL/do
-          const float dq = -0.5f * al[q] * dalpha;     // dL/dq
-          v[0] += dq * 2.f * (k.x * dx[q] + k.y * dy[q]); // dL/dmu_x (dx = mu_x - p_x)
-          v[1] += dq * 2.f * (k.y * dx[q] + k.z * dy[q]); // dL/dmu_y
-          v[2] += dq * dx[q] * dx[q];                  // dL/da
-          v[3] += dq * 2.f * dx[q] * dy[q];            // dL/db
-          v[4] += dq * dy[q] * dy[q];                  // dL/dc
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 10; ++i) v[i] = warp_sum(v[i]);
-      if (lane == 0) {
-        float4* dst = g2d + 3 * (size_t)srec[b];
-        atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
-        atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], 0.f));
-        atomicAdd(dst + 2, make_float4(v[7], v[8], v[9], 0.f));
-      }
+      __syncwarp();
     }
-    __syncwarp();
+    mA = mB; ovA = ovB; cA = cB; kA = kB; rA = rB;
+    rB = rC; mB = mC;
+    rC = rD;
   }
 }
 
@@ -238,7 +244,7 @@ __global__ void __launch_bounds__(256) k_proj_adjoint(gs_map map, gs_proj proj, 
     const float tx = R[0] * dx + R[3] * dy + R[6] * dz;
     const float ty = R[1] * dx + R[4] * dy + R[7] * dz;
     const float tz = R[2] * dx + R[5] * dy + R[8] * dz;
-    const float4 con = reinterpret_cast<const float4*>(proj.conic_u)[r];
+    const float4 con = reinterpret_cast<const float4*>(proj.conic_o)[r];
     // dL/dSigma2D = -C G_C C (symmetric-matrix gradients)
     const float C00 = con.x, C01 = con.y, C11 = con.z;
     const float G00 = ga, G01 = 0.5f * gb, G11 = gc;
@@ -339,7 +345,7 @@ cudaError_t launch_render_bwd(const gs_map& map, const gs_proj& proj, const gs_b
   if (zb < 1) zb = 1;
   k_zero_g2d<<<(unsigned)zb, 256, 0, st>>>(g2d, proj.count, proj.capacity);
   note_launch();
-  const int64_t items = bins.tile_capacity * (int64_t)((p.tile_w * p.tile_h) / (32 * kPix));
+  const int64_t items = bins.tile_capacity * (32 / kPix);   // upper bound: at most 32 / kPix items per tile
   if (items > 0) {
     k_render_bwd<<<(unsigned)((items + kBwdWarps - 1) / kBwdWarps), kBwdWarps * 32, 0, st>>>(
         map, proj, bins, cams, n_views, p, fwd, g, g2d, (uint32_t)items);

@@ -9,64 +9,36 @@ namespace gs {
 
 struct TileInfo {
   bool valid;
-  int view;
   int W, H;
   int x0, y0;          // pixel origin of the tile
+  int tw;              // tile width of the view
+  int blk;             // pixel block of the tile handled by the warp
+  uint32_t tile;       // global tile id
   uint32_t pix_base;   // first pixel of the view in the concatenated images
   uint32_t beg, end;   // range in the sorted pair list
 };
 
-// Called by every thread of the block; returns whether the tile exists.
-__device__ __forceinline__ bool tile_setup(const gs_proj& proj, const gs_bins& bins, const gs_camera* cams,
-                                           int n_views, const gs_params& p, uint32_t tile, TileInfo& ti) {
-  if (threadIdx.x == 0) {
-    const uint32_t total = proj.view_info[2 * n_views];
-    ti.valid = tile < total && (int64_t)tile < bins.tile_capacity;
-    if (ti.valid) {
-      const int v = find_view(proj.view_info, n_views, tile);
-      const uint32_t local = tile - proj.view_info[2 * v];
-      const int W = cams[v].width, H = cams[v].height;
-      const uint32_t tx = (uint32_t)((W + p.tile_w - 1) / p.tile_w);
-      ti.view = v;
-      ti.W = W;
-      ti.H = H;
-      ti.x0 = (int)(local % tx) * p.tile_w;
-      ti.y0 = (int)(local / tx) * p.tile_h;
-      ti.pix_base = proj.view_info[2 * v + 1];
-      uint32_t n_pairs = *bins.count;
-      if ((int64_t)n_pairs > bins.pair_capacity) n_pairs = (uint32_t)bins.pair_capacity;
-      uint32_t b = bins.ranges[2 * (size_t)tile], e = bins.ranges[2 * (size_t)tile + 1];
-      if (e > n_pairs) e = n_pairs;
-      if (b > e) b = e;
-      ti.beg = b;
-      ti.end = e;
-    }
-  }
-  __syncthreads();
-  return ti.valid;
-}
-
 // alpha = min(alpha_max, o exp(-q/2)), q = a dx^2 + 2 b dx dy + c dy^2 with
-// (dx, dy) = mu_2D - pixel centre.  xyod = (mu_x, mu_y, o, depth), con = (a, b, c, u).
-// Written with explicit round-to-nearest intrinsics so that the forward,
-// backward and information-gain kernels compute bit-identical alphas (and so
-// take identical skip and stop decisions) whatever the compiler contracts.
-// Also returns (dx, dy) and G = exp(-q/2).
-__device__ __forceinline__ float splat_alpha_dxy(const float4& xyod, const float4& con, float pxc, float pyc,
+// (dx, dy) = mu_2D - pixel centre and co = (a, b, c, o).  Written with explicit
+// round-to-nearest intrinsics so that the forward, backward and
+// information-gain kernels compute bit-identical alphas (and so take identical
+// skip and stop decisions) whatever the compiler contracts.  Also returns
+// (dx, dy) and G = exp(-q/2).
+__device__ __forceinline__ float splat_alpha_dxy(float mx, float my, const float4& co, float pxc, float pyc,
                                                  float alpha_max, float& dx, float& dy, float& G) {
-  dx = __fsub_rn(xyod.x, pxc);
-  dy = __fsub_rn(xyod.y, pyc);
-  float q = __fmul_rn(__fmul_rn(con.z, dy), dy);
-  q = __fmaf_rn(__fmul_rn(con.x, dx), dx, q);
-  q = __fmaf_rn(__fmul_rn(__fadd_rn(con.y, con.y), dx), dy, q);
+  dx = __fsub_rn(mx, pxc);
+  dy = __fsub_rn(my, pyc);
+  float q = __fmul_rn(__fmul_rn(co.z, dy), dy);
+  q = __fmaf_rn(__fmul_rn(co.x, dx), dx, q);
+  q = __fmaf_rn(__fmul_rn(__fadd_rn(co.y, co.y), dx), dy, q);
   G = __expf(__fmul_rn(-0.5f, q));
-  return fminf(alpha_max, __fmul_rn(xyod.z, G));
+  return fminf(alpha_max, __fmul_rn(co.w, G));
 }
 
-__device__ __forceinline__ float splat_alpha(const float4& xyod, const float4& con, float pxc, float pyc,
+__device__ __forceinline__ float splat_alpha(float mx, float my, const float4& co, float pxc, float pyc,
                                              float alpha_max) {
   float dx, dy, G;
-  return splat_alpha_dxy(xyod, con, pxc, pyc, alpha_max, dx, dy, G);
+  return splat_alpha_dxy(mx, my, co, pxc, pyc, alpha_max, dx, dy, G);
 }
 
 // Work item of the compositing kernels: one warp renders one 8 x (4 KP) pixel
@@ -82,40 +54,55 @@ struct WarpBlock {
   float bx0, bx1, by0, by1;     // pixel-centre bounds of the warp's block
 };
 
+// Decodes warp item `item` (numbered view by view, tile by tile, block by block,
+// with tile_w * tile_h / (32 KP) items per tile) into its tile and block; lane 0
+// computes and broadcasts.  Returns false (warp-uniform) if the item does not exist.
 template <int KP>
-__device__ __forceinline__ int warps_per_tile(const gs_params& p) { return (p.tile_w * p.tile_h) / (32 * KP); }
-
-// Tile of `tile`, computed by lane 0 and broadcast; returns false (warp-uniform) if the tile does not exist.
-__device__ __forceinline__ bool warp_tile_setup(const gs_proj& proj, const gs_bins& bins, const gs_camera* cams,
-                                                int n_views, const gs_params& p, uint32_t tile, TileInfo& ti) {
+__device__ __forceinline__ bool warp_item_setup(const gs_proj& proj, const gs_bins& bins, const gs_camera* cams,
+                                                int n_views, uint32_t item, TileInfo& ti) {
   const int lane = threadIdx.x & 31;
-  int f[7] = {0, 0, 0, 0, 0, 0, 0};
+  int f[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  uint32_t pix_base = 0;
   if (lane == 0) {
-    const uint32_t total = proj.view_info[2 * n_views];
-    const bool valid = tile < total && (int64_t)tile < bins.tile_capacity;
-    if (valid) {
-      const int v = find_view(proj.view_info, n_views, tile);
-      const uint32_t local = tile - proj.view_info[2 * v];
-      const int W = cams[v].width, H = cams[v].height;
-      const uint32_t tx = (uint32_t)((W + p.tile_w - 1) / p.tile_w);
-      uint32_t n_pairs = *bins.count;
-      if ((int64_t)n_pairs > bins.pair_capacity) n_pairs = (uint32_t)bins.pair_capacity;
-      uint32_t b = bins.ranges[2 * (size_t)tile], e = bins.ranges[2 * (size_t)tile + 1];
-      if (e > n_pairs) e = n_pairs;
-      if (b > e) b = e;
-      f[0] = 1;
-      f[1] = W;
-      f[2] = H;
-      f[3] = (int)(local % tx) * p.tile_w;
-      f[4] = (int)(local / tx) * p.tile_h;
-      f[5] = (int)b;
-      f[6] = (int)e;
-      ti.pix_base = proj.view_info[2 * v + 1];
+    const uint32_t total = proj.view_info[kVI * n_views + 2] / KP;
+    if (item < total) {
+      // largest v with first_item(v) / KP <= item
+      int lo = 0, hi = n_views - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (proj.view_info[kVI * mid + 2] / KP <= item) lo = mid; else hi = mid - 1;
+      }
+      const int v = lo;
+      const uint32_t code = proj.view_info[kVI * v + 3];
+      const int tw = (int)(code & 0xffu), th = (int)((code >> 8) & 0xffu);
+      const uint32_t tx = code >> 16;
+      const uint32_t wpt = (uint32_t)(tw * th / (32 * KP));
+      const uint32_t local = item - proj.view_info[kVI * v + 2] / KP;
+      const uint32_t lt = wpt ? local / wpt : 0u;
+      const uint32_t tile = proj.view_info[kVI * v] + lt;
+      if (code != 0u && wpt != 0u && (int64_t)tile < bins.tile_capacity) {
+        uint32_t n_pairs = *bins.count;
+        if ((int64_t)n_pairs > bins.pair_capacity) n_pairs = (uint32_t)bins.pair_capacity;
+        uint32_t b = bins.ranges[2 * (size_t)tile], e = bins.ranges[2 * (size_t)tile + 1];
+        if (e > n_pairs) e = n_pairs;
+        if (b > e) b = e;
+        f[0] = 1;
+        f[1] = cams[v].width;
+        f[2] = cams[v].height;
+        f[3] = (int)(lt % tx) * tw;
+        f[4] = (int)(lt / tx) * th;
+        f[5] = (int)b;
+        f[6] = (int)e;
+        f[7] = tw;
+        f[8] = (int)(local % wpt);
+        f[9] = (int)tile;
+        pix_base = proj.view_info[kVI * v + 1];
+      }
     }
   }
 #pragma unroll
-  for (int i = 0; i < 7; ++i) f[i] = __shfl_sync(0xffffffffu, f[i], 0);
-  ti.pix_base = __shfl_sync(0xffffffffu, ti.pix_base, 0);
+  for (int i = 0; i < 10; ++i) f[i] = __shfl_sync(0xffffffffu, f[i], 0);
+  ti.pix_base = __shfl_sync(0xffffffffu, pix_base, 0);
   ti.valid = f[0] != 0;
   ti.W = f[1];
   ti.H = f[2];
@@ -123,13 +110,17 @@ __device__ __forceinline__ bool warp_tile_setup(const gs_proj& proj, const gs_bi
   ti.y0 = f[4];
   ti.beg = (uint32_t)f[5];
   ti.end = (uint32_t)f[6];
+  ti.tw = f[7];
+  ti.blk = f[8];
+  ti.tile = (uint32_t)f[9];
   return ti.valid;
 }
 
 template <int KP>
-__device__ __forceinline__ void warp_block(const TileInfo& ti, const gs_params& p, int blk, WarpBlock& wb) {
+__device__ __forceinline__ void warp_block(const TileInfo& ti, WarpBlock& wb) {
   const int lane = threadIdx.x & 31;
-  const int wpr = p.tile_w >> 3;
+  const int wpr = ti.tw >> 3;
+  const int blk = ti.blk;
   const int wx = (blk % wpr) * 8, wy = (blk / wpr) * 4 * KP;
   wb.px = ti.x0 + wx + (lane & 7);
   wb.py = ti.y0 + wy + (lane >> 3);
@@ -147,32 +138,10 @@ __device__ __forceinline__ bool all_done(const bool* done) {
   return r;
 }
 
-// Can the support box of an entry (mean +/- half-widths) contain a pixel centre of the block?
-__device__ __forceinline__ bool box_overlaps(const float4& xyod, const float2& ext, const WarpBlock& wb) {
-  return (xyod.x - ext.x <= wb.bx1) && (xyod.x + ext.x >= wb.bx0) && (xyod.y - ext.y <= wb.by1) &&
-         (xyod.y + ext.y >= wb.by0);
-}
-
-// One list entry as a lane holds it.
-struct Entry {
-  float4 xyod, con;
-  float2 ext;
-  uint32_t rec;
-};
-
-__device__ __forceinline__ void load_entry(const gs_proj& proj, const gs_bins& bins, uint32_t idx, Entry& e) {
-  e.rec = __ldg(bins.rec + idx);
-  e.xyod = __ldg(reinterpret_cast<const float4*>(proj.xyod) + e.rec);
-  e.con = __ldg(reinterpret_cast<const float4*>(proj.conic_u) + e.rec);
-  e.ext = __ldg(reinterpret_cast<const float2*>(proj.ext) + e.rec);
-}
-
-// Record part of an entry whose record index is already known.
-__device__ __forceinline__ void load_record(const gs_proj& proj, uint32_t rec, Entry& e) {
-  e.rec = rec;
-  e.xyod = __ldg(reinterpret_cast<const float4*>(proj.xyod) + rec);
-  e.con = __ldg(reinterpret_cast<const float4*>(proj.conic_u) + rec);
-  e.ext = __ldg(reinterpret_cast<const float2*>(proj.ext) + rec);
+// Can the support box of an entry, me = (mu_x, mu_y, half-width x, half-width y),
+// contain a pixel centre of the warp's block?
+__device__ __forceinline__ bool box_overlaps(const float4& me, const WarpBlock& wb) {
+  return (me.x - me.z <= wb.bx1) && (me.x + me.z >= wb.bx0) && (me.y - me.w <= wb.by1) && (me.y + me.w >= wb.by0);
 }
 
 // Fixed-tree block sum (deterministic for a fixed block size); result valid in thread 0.

@@ -17,8 +17,9 @@ import torch
 from . import _lib as L
 
 CAMERA_DTYPE = np.dtype([("fx", "<f4"), ("fy", "<f4"), ("cx", "<f4"), ("cy", "<f4"), ("width", "<i4"),
-                         ("height", "<i4"), ("R", "<f4", (9,)), ("T", "<f4", (3,))])
-assert CAMERA_DTYPE.itemsize == 72
+                         ("height", "<i4"), ("R", "<f4", (9,)), ("T", "<f4", (3,)), ("tile_w", "<i4"),
+                         ("tile_h", "<i4")])
+assert CAMERA_DTYPE.itemsize == 80
 
 
 @dataclass
@@ -90,7 +91,7 @@ def pack_cameras(cams) -> np.ndarray:
     a = np.zeros(len(cams), CAMERA_DTYPE)
     for i, c in enumerate(cams):
         a[i] = (c.fx, c.fy, c.cx, c.cy, c.width, c.height, np.asarray(c.R, np.float32).reshape(9),
-                np.asarray(c.T, np.float32).reshape(3))
+                np.asarray(c.T, np.float32).reshape(3), getattr(c, "tile_w", 0), getattr(c, "tile_h", 0))
     return a
 
 
@@ -98,9 +99,16 @@ def cameras_to_device(cams, device="cuda") -> torch.Tensor:
     return torch.from_numpy(pack_cameras(cams).view(np.uint8).copy()).to(device)
 
 
+def view_tile(c, params: RenderParams):
+    """Tile size of a view: the camera's own (tile_w, tile_h, if non-zero) else the params'."""
+    tw, th = getattr(c, "tile_w", 0), getattr(c, "tile_h", 0)
+    return (tw, th) if tw and th else (params.tile_w, params.tile_h)
+
+
 def tile_grid(cams, params: RenderParams):
-    tx = np.array([-(-c.width // params.tile_w) for c in cams], np.int64)
-    ty = np.array([-(-c.height // params.tile_h) for c in cams], np.int64)
+    """Per view: tiles_x, tiles_y; and the tile and pixel offsets of the views (length V+1)."""
+    tx = np.array([-(-c.width // view_tile(c, params)[0]) for c in cams], np.int64)
+    ty = np.array([-(-c.height // view_tile(c, params)[1]) for c in cams], np.int64)
     tiles = tx * ty
     pix = np.array([c.width * c.height for c in cams], np.int64)
     tile_base = np.concatenate([[0], np.cumsum(tiles)])
@@ -166,14 +174,15 @@ class Frame:
         self.pair_capacity = pair_capacity
         self.status = torch.zeros(1, dtype=torch.int32, device=d)
         self.rec_count = torch.zeros(1, dtype=torch.int32, device=d)
-        self.view_info = torch.zeros(2 * (self.V + 1), dtype=torch.int32, device=d)
+        self.view_info = torch.zeros(4 * (self.V + 1), dtype=torch.int32, device=d)
         self.gid = _alloc_u32(rc, d)
         self.view = _alloc_u32(rc, d)
-        self.xyod = torch.empty((rc, 4), dtype=torch.float32, device=d)
-        self.conic_u = torch.empty((rc, 4), dtype=torch.float32, device=d)
+        self.mean_ext = torch.empty((rc, 4), dtype=torch.float32, device=d)
+        self.conic_o = torch.empty((rc, 4), dtype=torch.float32, device=d)
+        self.color_d = torch.empty((rc, 4), dtype=torch.float32, device=d)
+        self.unc = torch.empty(rc, dtype=torch.float32, device=d)
         self.rect = torch.empty((rc, 4), dtype=torch.int16, device=d)
         self.depth_key = _alloc_u32(rc, d)
-        self.ext = torch.empty((rc, 2), dtype=torch.float32, device=d)
         self.n_slots = ((self.n + 31) // 32) * self.V
         self.grp_mask = _alloc_u32(self.n_slots, d)
         self.grp_base = _alloc_u32(self.n_slots + 1, d)
@@ -186,11 +195,15 @@ class Frame:
                  L.workspace_size(L.GS_OP_RENDER_BWD, self.n, self.V, rc))
         self.ws = torch.empty(max(ws, 256), dtype=torch.uint8, device=d)
         self.c_proj = L.gs_proj(rc, _ptr(self.rec_count), _ptr(self.status), _ptr(self.view_info), _ptr(self.gid),
-                                _ptr(self.view), _ptr(self.xyod), _ptr(self.conic_u), _ptr(self.rect),
-                                _ptr(self.depth_key), _ptr(self.ext), _ptr(self.grp_mask), _ptr(self.grp_base))
+                                _ptr(self.view), _ptr(self.mean_ext), _ptr(self.conic_o), _ptr(self.color_d),
+                                _ptr(self.unc), _ptr(self.rect), _ptr(self.depth_key), _ptr(self.grp_mask),
+                                _ptr(self.grp_base))
         self.c_bins = L.gs_bins(pair_capacity, max(self.n_tiles, 1), _ptr(self.pair_count), _ptr(self.pair_tile),
                                 _ptr(self.pair_rec), _ptr(self.ranges))
         self.c_params = self.params.c()
+
+    def view_tile(self, v: int):
+        return view_tile(self.cams[v], self.params)
 
     # -------------------------------------------------------------- stages
     def project(self, gmap: GaussianMapTensors, stream=None):
@@ -373,3 +386,55 @@ class InfoGain:
             self._alloc(min(2 * self.pair_capacity, (1 << 32) - 2))
             return True
         return False
+
+
+# ---------------------------------------------------------------------- tile autotuner
+TILE_CANDIDATES = ((16, 16), (16, 8), (8, 8), (32, 8))
+
+
+def autotune_tiles(gmap: GaussianMapTensors, cams: Sequence, params: RenderParams = RenderParams(),
+                   candidates=TILE_CANDIDATES, reps: int = 3, pair_capacity: Optional[int] = None):
+    """Pick a screen tile per resolution class by timing the batched information-gain pass.
+
+    For every distinct (width, height) among `cams`, the views of that class are
+    scored with each candidate tile size (CUDA events, best of `reps` after one
+    warm-up) and the fastest is kept.  Returns ({(W, H): (tile_w, tile_h)},
+    {(W, H): {tile: ms}}).  Use `with_tiles` to apply the choice to a camera list.
+    """
+    classes = {}
+    for c in cams:
+        classes.setdefault((c.width, c.height), []).append(c)
+    choice, timings = {}, {}
+    for res, group in classes.items():
+        timings[res] = {}
+        for tw, th in candidates:
+            if not (tw <= 64 and th % 8 == 0 and tw * th in (64, 128, 256, 512, 1024)):
+                continue
+            tc = [type(c)(c.fx, c.fy, c.cx, c.cy, c.width, c.height, c.R, c.T, tw, th) for c in group]
+            ig = InfoGain(gmap.n, tc, params, pair_capacity=pair_capacity)
+            ig(gmap)
+            torch.cuda.synchronize()
+            while ig.grow_if_needed():
+                ig(gmap)
+                torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ig(gmap)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            timings[res][(tw, th)] = best
+            del ig
+        choice[res] = min(timings[res], key=timings[res].get)
+    return choice, timings
+
+
+def with_tiles(cams: Sequence, choice) -> list:
+    """Cameras with their tile size set from an autotune_tiles choice ({(W, H): (tile_w, tile_h)})."""
+    out = []
+    for c in cams:
+        tw, th = choice.get((c.width, c.height), (0, 0))
+        out.append(type(c)(c.fx, c.fy, c.cx, c.cy, c.width, c.height, c.R, c.T, tw, th))
+    return out

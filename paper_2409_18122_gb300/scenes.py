@@ -39,6 +39,8 @@ class Camera:
     height: int
     R: np.ndarray = field(default_factory=lambda: np.eye(3, dtype=np.float32))
     T: np.ndarray = field(default_factory=lambda: np.zeros(3, dtype=np.float32))
+    tile_w: int = 0        # this view's screen tile; 0 = the renderer's default
+    tile_h: int = 0
 
     def __post_init__(self):
         self.R = np.asarray(self.R, dtype=np.float32).reshape(3, 3)
@@ -57,7 +59,13 @@ class Camera:
         Pixel (u, v) of the crop samples the same ray as pixel (u+x0, v+y0) of
         the full image, so a crop renders exactly that window.
         """
-        return Camera(self.fx, self.fy, self.cx - x0, self.cy - y0, w, h, self.R.copy(), self.T.copy())
+        return Camera(self.fx, self.fy, self.cx - x0, self.cy - y0, w, h, self.R.copy(), self.T.copy(),
+                      self.tile_w, self.tile_h)
+
+    def with_tile(self, tile_w: int, tile_h: int) -> "Camera":
+        """The same camera rendered with its own screen tile size."""
+        return Camera(self.fx, self.fy, self.cx, self.cy, self.width, self.height, self.R.copy(), self.T.copy(),
+                      tile_w, tile_h)
 
 
 @dataclass

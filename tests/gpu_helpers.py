@@ -31,10 +31,10 @@ def gpu_records(frame):
     return dict(
         n=n,
         gid=u32(frame.gid)[:n], view=u32(frame.view)[:n],
-        xyod=frame.xyod[:n].cpu().numpy(), conic_u=frame.conic_u[:n].cpu().numpy(),
+        mean_ext=frame.mean_ext[:n].cpu().numpy(), conic_o=frame.conic_o[:n].cpu().numpy(),
+        color_d=frame.color_d[:n].cpu().numpy(), unc=frame.unc[:n].cpu().numpy(),
         rect=frame.rect[:n].cpu().numpy().view(np.uint16).astype(np.int32),
         dkey=u32(frame.depth_key)[:n],
-        ext=frame.ext[:n].cpu().numpy(),
         grp_mask=u32(frame.grp_mask)[:frame.n_slots],
         grp_base=u32(frame.grp_base)[:frame.n_slots + 1],
         view_info=u32(frame.view_info),
@@ -70,8 +70,9 @@ def last_gid(frame, img_host_list):
     for v, (cam, h) in enumerate(zip(frame.cams, img_host_list)):
         H, W = cam.height, cam.width
         ys, xs = np.mgrid[0:H, 0:W]
-        tx = xs // frame.params.tile_w
-        ty = ys // frame.params.tile_h
+        tw, th = frame.view_tile(v)
+        tx = xs // tw
+        ty = ys // th
         tile = frame.tile_base[v] + ty * frame.tiles_x[v] + tx
         beg = b["ranges"][tile, 0]
         last = h["last"].astype(np.int64)

@@ -49,13 +49,18 @@ def check_projection(fr, gmap, cams, params):
     np.testing.assert_array_equal(rec["dkey"][order], ref["dkey"])
     np.testing.assert_array_equal(rec["rect"][order], ref["rect"])
     W = max(c.width for c in cams)
-    np.testing.assert_allclose(rec["xyod"][order, :2], pr["mean2d"][v, g], rtol=0, atol=4e-6 * W)
-    np.testing.assert_allclose(rec["xyod"][order, 2], pr["opac"][v, g], rtol=2e-6)
-    np.testing.assert_allclose(rec["xyod"][order, 3], pr["depth"][v, g], rtol=2e-7)
+    np.testing.assert_allclose(rec["mean_ext"][order, :2], pr["mean2d"][v, g], rtol=0, atol=4e-6 * W)
+    np.testing.assert_allclose(rec["conic_o"][order, 3], pr["opac"][v, g], rtol=2e-6)
+    np.testing.assert_allclose(rec["color_d"][order, 3], pr["depth"][v, g], rtol=2e-7)
+    np.testing.assert_array_equal(rec["color_d"][order, :3], gmap.rgb[g, :3])
     con = pr["conic"][v, g]
     scale = np.abs(con).max(axis=1, keepdims=True)
-    assert (np.abs(rec["conic_u"][order, :3] - con) <= 5e-4 * scale).all()
-    np.testing.assert_array_equal(rec["conic_u"][order, 3], gmap.su[g, 3])
+    assert (np.abs(rec["conic_o"][order, :3] - con) <= 5e-4 * scale).all()
+    np.testing.assert_array_equal(rec["unc"][order], gmap.su[g, 3])
+    # support half-widths: sqrt(2 ln(o / alpha_min) Sigma_2D,xx), Sigma_2D,yy likewise (FP64 reference)
+    Q = 2 * np.log(pr["opac"][v, g] / float(np.float32(params.alpha_min)))
+    ext_ref = np.sqrt(Q[:, None] * pr["cov2d"][v, g][:, [0, 2]])
+    np.testing.assert_allclose(rec["mean_ext"][order, 2:], ext_ref, rtol=1e-4, atol=1e-4)
     # group masks and bases
     n_grp = (gmap.n + 31) // 32
     vis = np.zeros((n_grp * 32, V), bool)
@@ -93,8 +98,15 @@ def _bin_only(rec, cams, params=gs.RenderParams(), pair_capacity=None):
     n = int(rec["gid"].max()) + 1 if R else 1
     fr = gs.Frame(n, cams, params, pair_capacity=pair_capacity)
     dev = fr.device
-    tb = np.stack([fr.tile_base, fr.pix_base], 1).astype(np.uint32).reshape(-1)
-    fr.view_info.copy_(torch.from_numpy(tb.view(np.int32)).to(dev))
+    tiles = np.diff(fr.tile_base)
+    codes = []
+    items = [0]
+    for v in range(len(cams)):
+        tw, th = fr.view_tile(v)
+        codes.append(tw | (th << 8) | (int(fr.tiles_x[v]) << 16))
+        items.append(items[-1] + int(tiles[v]) * tw * th // 32)
+    vi = np.stack([fr.tile_base, fr.pix_base, np.array(items), np.array(codes + [0])], 1).astype(np.uint32)
+    fr.view_info.copy_(torch.from_numpy(vi.reshape(-1).view(np.int32)).to(dev))
     fr.rec_count.fill_(R)
     if R:
         fr.gid[:R].copy_(torch.from_numpy(rec["gid"].view(np.int32)).to(dev))
@@ -195,6 +207,26 @@ def test_render_room_crop_ragged_tiles():
     gpu = images_host(fr, img)[0]
     ref = O.render_images(sub, cams)[0]
     compare_image(gpu, ref, "room crop", check_last=last_gid(fr, [gpu])[0])
+
+
+def test_per_view_tile_sizes_match_oracle():
+    """Views with their own tile sizes (8x8, 16x16, 32x8) in one batch: bit-exact binning, images within tolerance."""
+    sc = scenes.config2(n=30_000, n_views=3)
+    cams = [sc.cams[0].crop(100, 80, 120, 88).with_tile(8, 8), sc.cams[1].crop(0, 0, 96, 72),
+            sc.cams[2].crop(300, 200, 128, 64).with_tile(32, 8)]
+    p = gs.RenderParams()
+    fr, gm, img = run_forward(sc.gmap, cams, p)
+    rec, ref_rec = check_projection(fr, sc.gmap, cams, p)
+    ref = O.bin_sort(ref_rec, cams, oparams(p))
+    b = gpu_bins(fr)
+    np.testing.assert_array_equal(pairs_as_gid_view(b["tile"], b["rec"], rec),
+                                  pairs_as_gid_view((ref["keys"] >> np.uint64(32)), ref["vals"], ref_rec))
+    np.testing.assert_array_equal(b["ranges"], ref["ranges"])
+    gpu = images_host(fr, img)
+    refi = O.render_images(sc.gmap, cams, oparams(p))
+    lg = last_gid(fr, gpu)
+    for v in range(len(cams)):
+        compare_image(gpu[v], refi[v], "view %d" % v, check_last=lg[v])
 
 
 def test_tile_shape_invariance_bitwise():
@@ -367,6 +399,17 @@ def test_info_gain_batch_vs_oracle_and_single_view():
     for v in range(len(cams)):
         one = gs.InfoGain(gm.n, [cams[v]])(gm).cpu().numpy()
         assert one[0] == np.float32(ig[v]), (v, one[0], ig[v])
+
+
+def test_info_gain_per_view_tiles_vs_oracle():
+    gmap, cams = _ig_scene()
+    cams = [c.with_tile(8, 8) if c.width <= 80 else (c.with_tile(16, 8) if c.width <= 160 else c) for c in cams]
+    gm = gs.GaussianMapTensors.from_numpy(gmap)
+    ig = gs.InfoGain(gm.n, cams)(gm).cpu().numpy().astype(np.float64)
+    ref, imgs = O.info_gain(gmap, cams)
+    for v in range(len(cams)):
+        tol = IG_RTOL * abs(ref[v]) + 1e-7 + imgs[v]["knife"].mean() * 4e-3
+        assert abs(ig[v] - ref[v]) <= tol, (v, ig[v], ref[v])
 
 
 def test_info_gain_uniform_uncertainty_is_mean_coverage():
