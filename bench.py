@@ -44,7 +44,7 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
@@ -55,7 +55,7 @@ def parse():
 
 # ----------------------------------------------------------------------------- helpers
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms while running."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -70,7 +70,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
             self.proc = None
@@ -181,59 +181,112 @@ class MapStep:
 
 
 class IGStep:
-    """The batched information-gain pass over 256 candidate views of a 1M-Gaussian map."""
+    """The batched information-gain pass over 256 candidate views of a 1M-Gaussian map.
 
-    def __init__(self, gs, scenes, graph: bool):
+    project -> bin_sort -> composite (the three stages of gs_info_gain_batch) on
+    colour-free records, captured in one CUDA graph; the tile size of each
+    resolution class is picked by the autotuner at set-up.  Events recorded inside
+    the graph bracket the compositing kernel (the step's dominant kernel).
+    """
+
+    def __init__(self, gs, scenes, graph: bool, tune: bool = True):
         import torch
         self.torch = torch
         self.gs = gs
         sc = scenes.config3()
         self.scene = sc
         self.gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
-        self.ig = gs.InfoGain(self.gm.n, sc.cams)
+        cams = sc.cams
+        self.tile_choice = {}
+        if tune:
+            self.tile_choice, self.tile_timings = gs.autotune_tiles(self.gm, cams, pair_capacity=400_000_000)
+            cams = gs.with_tiles(cams, self.tile_choice)
+            torch.cuda.empty_cache()
+        self.cams = cams
+        self.frame = gs.Frame(self.gm.n, cams, pair_capacity=300_000_000, with_color=False)
         while True:
-            self.ig.status.zero_()
-            self.ig(self.gm)
+            self.frame.reset_status()
+            self.frame.project(self.gm)
+            self.frame.bin_sort()
             torch.cuda.synchronize()
-            if not self.ig.grow_if_needed():
+            if not self.frame.grow_if_needed():
                 break
-        assert not (self.ig.read_status() & gs.L.GS_FLAG_ERROR_MASK)
-        self.out = torch.zeros(len(sc.cams), dtype=torch.float32, device="cuda")
+        self.frame.check_status()
+        self.out = torch.zeros(len(cams), dtype=torch.float32, device="cuda")
+        self.frame.info_gain(self.out)
+        torch.cuda.synchronize()
         self.host = [t.cpu().pin_memory() for t in (self.gm.mo, self.gm.su, self.gm.q, self.gm.rgb)]
-        self.host_cams = self.ig.cams_dev.cpu().pin_memory()
-        self.out_host = torch.zeros(len(sc.cams), dtype=torch.float32).pin_memory()
+        self.host_cams = self.frame.cams_dev.cpu().pin_memory()
+        self.out_host = torch.zeros(len(cams), dtype=torch.float32).pin_memory()
         self.graph = None
         self.kernels_per_replay = 0
-        if graph:
+        try:
+            self.ev = (torch.cuda.Event(enable_timing=True, external=True),
+                       torch.cuda.Event(enable_timing=True, external=True))
+        except TypeError:
+            self.ev = None
+        if graph and self.ev is not None:
             s = torch.cuda.Stream()
             s.wait_stream(torch.cuda.current_stream())
             with torch.cuda.stream(s):
-                self.ig(self.gm, self.out)
+                self._run()
             torch.cuda.current_stream().wait_stream(s)
             torch.cuda.synchronize()
             g = torch.cuda.CUDAGraph()
             k0 = gs.L.lib().gs_kernel_launches()
             with torch.cuda.graph(g):
-                self.ig(self.gm, self.out)
+                self._run()
             self.kernels_per_replay = int(gs.L.lib().gs_kernel_launches() - k0)
             self.graph = g
+        if self.ev is None:
+            self.ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+    def _run(self):
+        self.frame.project(self.gm)
+        self.frame.bin_sort()
+        self.ev[0].record()
+        self.frame.info_gain(self.out)
+        self.ev[1].record()
 
     @property
     def n_views(self):
-        return len(self.scene.cams)
+        return len(self.cams)
 
     def __call__(self):
         if self.graph is not None:
             self.graph.replay()
         else:
-            self.ig(self.gm, self.out)
+            self._run()
         return self.out
+
+    def composite_ms(self, reps: int, flush):
+        """Device time of the compositing stage, from the events around it (mean of `reps` passes)."""
+        t = []
+        for _ in range(reps):
+            flush()
+            self()
+            self.torch.cuda.synchronize()
+            t.append(self.ev[0].elapsed_time(self.ev[1]))
+        return statistics.mean(t)
+
+    def contributing(self):
+        """Contributing (pixel, Gaussian) evaluations of one pass, counted with the forward kernel."""
+        torch, gs = self.torch, self.gs
+        fr = gs.Frame(self.gm.n, self.cams, pair_capacity=self.frame.pair_capacity)
+        img = fr.new_images(with_rgb=False, with_depth=False, with_unc=False, with_counts=True)
+        fr.forward(self.gm, img)
+        torch.cuda.synchronize()
+        c = int(img["n_contrib"].to(torch.int64).sum().item())
+        e = int(img["last"].to(torch.int64).sum().item())
+        del fr, img
+        torch.cuda.empty_cache()
+        return c, e
 
     def e2e(self):
         with self.torch.no_grad():
             for d, h in zip((self.gm.mo, self.gm.su, self.gm.q, self.gm.rgb), self.host):
                 d.copy_(h, non_blocking=True)
-            self.ig.cams_dev.copy_(self.host_cams, non_blocking=True)
+            self.frame.cams_dev.copy_(self.host_cams, non_blocking=True)
         self()
         self.out_host.copy_(self.out, non_blocking=True)
 
@@ -363,15 +416,23 @@ def run_ours(args):
     except (OSError, ValueError):
         pass
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # dominant kernel of the step: the back-to-front adjoint replay (gs_render_bwd);
-    # algorithmic FP32 work: 10 instr per evaluated (pixel, entry) + 38 per contributing one
-    t_bwd = stage_ms.get("gs_render_bwd", float("nan")) / 1e3
-    instr = 10.0 * ws["evaluated"] + 38.0 * ws["contributing"]
-    achieved = instr / t_bwd / 1e12
     peak = sms * 128 * sm_max * 1e6 / 1e12
-    roofline = {"bound": "alu", "kernel": "gs_render_bwd (k_render_bwd + k_proj_adjoint)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "derived: %d SMs x 128 FP32 lanes x %.0f MHz (max SM clock)" % (sms, sm_max)}
+    peak_src = "derived: %d SMs x 128 FP32 lanes x %.0f MHz (max SM clock); no FP32 peak is measured" % (sms, sm_max)
+    # dominant kernel of the step: the information-gain compositing (gs_info_gain_composite);
+    # algorithmic FP32 work = 16 instr per contributing (pixel, Gaussian) evaluation
+    # (alpha: 2 sub, 5 mul/fma, exp, mul, min, compare; accumulate: sub, mul, compare, 2 fma)
+    t_comp = istep.composite_ms(max(3, args.steps), flush) / 1e3
+    ig_contrib, ig_walked = istep.contributing()
+    achieved = 16.0 * ig_contrib / t_comp / 1e12
+    roofline = {"bound": "alu", "kernel": "k_ig_items (gs_info_gain_composite)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                "launch_ms": t_comp * 1e3, "contributing_evals": ig_contrib}
+    # the mapping step's backward kernel, for reference: 10 per evaluated + 38 per contributing evaluation
+    t_bwd = stage_ms.get("gs_render_bwd", float("nan")) / 1e3
+    bwd_ach = (10.0 * ws["evaluated"] + 38.0 * ws["contributing"]) / t_bwd / 1e12
+    rooflines = [roofline, {"bound": "alu", "kernel": "gs_render_bwd (k_render_bwd + k_proj_adjoint)",
+                            "achieved": bwd_ach, "peak": peak, "unit": "TFLOP/s", "frac": bwd_ach / peak,
+                            "launch_ms": t_bwd * 1e3}]
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -385,13 +446,15 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "views_per_step": istep.n_views, "gaussians_ig": istep.gm.n,
                        "gaussians_map": mstep.frame.n, "keyframes": len(mstep.scene.cams),
                        "l2": "flushed (256 MB write) before every timed part", "parallelism": "replicas" if world > 1
-                       else "single GPU", "ig_cuda_graph": bool(args.graph)},
+                       else "single GPU", "ig_cuda_graph": istep.graph is not None,
+                       "ig_tiles": {"%dx%d" % k: "%dx%d" % v for k, v in istep.tile_choice.items()}},
             "fwd_bwd": {"value": fwd_bwd, "unit": "iters/s", "ms": t_map_all / args.steps * 1e3},
             "ig_ms": t_ig_all / args.steps * 1e3,
             "stages_ms": stage_ms,
             "work": ws,
             "e2e": e2e,
             "roofline": roofline,
+            "rooflines": rooflines,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": launches,

@@ -125,7 +125,9 @@ typedef struct {
  *   gid, view  [cap]      Gaussian index and view index of the record
  *   mean_ext   [cap][4]   (mu_2D x, mu_2D y, support half-widths sqrt(Q Sigma_2D,xx), sqrt(Q Sigma_2D,yy))
  *   conic_o    [cap][4]   (inverse 2D covariance a, b, c with q = a dx^2 + 2 b dx dy + c dy^2, opacity)
- *   color_d    [cap][4]   (r, g, b, depth t_z)
+ *   color_d    [cap][4]   (r, g, b, depth t_z); may be NULL for records that are only used to
+ *                         score information gain (gs_project then skips the colours;
+ *                         gs_render_fwd / gs_render_bwd require it)
  *   unc        [cap]      uncertainty u of the Gaussian
  *   rect       [cap][4]   uint16 tile rectangle (x0, y0, x1, y1), ends exclusive
  *   depth_key  [cap]      IEEE-754 bits of the float32 depth (the sort key)
@@ -311,14 +313,28 @@ gs_status gs_info_gain_batch(const gs_map* map, const gs_camera* cams, int32_t n
                              int32_t mode, float* ig_out, uint32_t* status, int64_t pair_capacity,
                              int64_t tile_capacity, void* ws, size_t ws_bytes, void* stream);
 
+/* gs_info_gain_composite -- the compositing stage of gs_info_gain_batch on
+ * records and bins already produced by gs_project and gs_bin_sort for the
+ * candidate views: U-only front-to-back compositing (same alpha / skip / stop
+ * rules as gs_render_fwd) by a persistent kernel that takes warp items (8x4
+ * pixel blocks of tiles) longest tile list first from a device queue, one slot
+ * per item, then a fixed-order per-view reduction IG_v = (1/P_v) sum_p U(p).
+ * Exposed so that one projection and binning can be reused, and so the
+ * compositing kernel can be timed on its own.  ig_out: DEVICE float[n_views].
+ * ws: DEVICE workspace of gs_workspace_size(GS_OP_IG_COMPOSITE, ...) bytes.
+ * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG, GS_ERR_WORKSPACE, GS_ERR_CUDA. */
+gs_status gs_info_gain_composite(const gs_proj* proj, const gs_bins* bins, const gs_camera* cams, int32_t n_views,
+                                 const gs_params* prm, int32_t mode, float* ig_out, void* ws, size_t ws_bytes,
+                                 void* stream);
+
 /* ------------------------------------------------------------- utilities */
-enum { GS_OP_PROJECT = 0, GS_OP_BIN_SORT = 1, GS_OP_RENDER_BWD = 2, GS_OP_INFO_GAIN = 3 };
+enum { GS_OP_PROJECT = 0, GS_OP_BIN_SORT = 1, GS_OP_RENDER_BWD = 2, GS_OP_INFO_GAIN = 3, GS_OP_IG_COMPOSITE = 4 };
 
 /* gs_workspace_size -- HOST.  Bytes of workspace `op` needs:
  *   n, n_views      map size and number of views
  *   rec_capacity    record capacity of the gs_proj in use (GS_OP_INFO_GAIN: ignored, n * n_views)
  *   pair_capacity   pair capacity of the gs_bins in use
- *   tile_capacity   tile capacity of the gs_bins in use
+ *   tile_capacity   tile capacity of the gs_bins in use (GS_OP_IG_COMPOSITE: only this is used)
  * Writes the byte count to *bytes (HOST).  Errors: GS_ERR_NULL, GS_ERR_ARG, GS_ERR_CUDA. */
 gs_status gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t rec_capacity, int64_t pair_capacity,
                             int64_t tile_capacity, size_t* bytes);

@@ -22,7 +22,7 @@ GS_FLAG_NONFINITE = 1 << 3
 GS_FLAG_RECORD_OVERFLOW = 1 << 4
 GS_FLAG_ERROR_MASK = GS_FLAG_PAIR_OVERFLOW | GS_FLAG_RANGE_OVERFLOW | GS_FLAG_BAD_CAMERA | GS_FLAG_RECORD_OVERFLOW
 GS_IG_RENDER_MEAN = 0
-GS_OP_PROJECT, GS_OP_BIN_SORT, GS_OP_RENDER_BWD, GS_OP_INFO_GAIN = range(4)
+GS_OP_PROJECT, GS_OP_BIN_SORT, GS_OP_RENDER_BWD, GS_OP_INFO_GAIN, GS_OP_IG_COMPOSITE = range(5)
 GS_NOALLOC_MAX_RECORDS = 1 << 18
 
 
@@ -85,6 +85,8 @@ PROTOTYPES = {
                                         POINTER(gs_map_grad), c_void_p]),
     "gs_info_gain_batch": (c_int32, [POINTER(gs_map), c_void_p, c_int32, POINTER(gs_params), c_int32, c_void_p,
                                      c_void_p, c_int64, c_int64, c_void_p, c_size_t, c_void_p]),
+    "gs_info_gain_composite": (c_int32, [POINTER(gs_proj), POINTER(gs_bins), c_void_p, c_int32, POINTER(gs_params),
+                                         c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
     "gs_workspace_size": (c_int32, [c_int32, c_int64, c_int32, c_int64, c_int64, c_int64, POINTER(c_size_t)]),
     "gs_read_status": (c_int32, [c_void_p, POINTER(c_uint32)]),
     "gs_status_str": (ctypes.c_char_p, [c_int32]),

@@ -61,8 +61,8 @@ gs_status check_proj(const gs_proj* p) {
   if (!p) return GS_ERR_NULL;
   if (p->capacity < 0 || p->capacity >= ((int64_t)1 << 32) - 1) return GS_ERR_ARG;
   if (!p->count || !p->status || !p->view_info || !p->grp_mask || !p->grp_base) return GS_ERR_NULL;
-  if (p->capacity > 0 && (!p->gid || !p->view || !p->mean_ext || !p->conic_o || !p->color_d || !p->unc ||
-                          !p->rect || !p->depth_key))
+  if (p->capacity > 0 && (!p->gid || !p->view || !p->mean_ext || !p->conic_o || !p->unc || !p->rect ||
+                          !p->depth_key))
     return GS_ERR_NULL;
   if (!aligned(p->mean_ext, 16) || !aligned(p->conic_o, 16) || !aligned(p->color_d, 16) || !aligned(p->unc, 4) ||
       !aligned(p->rect, 8) || !aligned(p->gid, 4) ||
@@ -132,6 +132,7 @@ gs_status gs_render_fwd(const gs_map* map, const gs_proj* proj, const gs_bins* b
   GS_TRY(check_views(cams, n_views));
   GS_TRY(check_params(prm));
   if (!out) return GS_ERR_NULL;
+  if (proj->capacity > 0 && !proj->color_d) return GS_ERR_NULL;   // colours are needed to render
   return from_cuda(launch_render_fwd(*map, *proj, *bins, cams, n_views, *prm, *out, (cudaStream_t)stream));
 }
 
@@ -145,6 +146,7 @@ gs_status gs_render_bwd(const gs_map* map, const gs_proj* proj, const gs_bins* b
   GS_TRY(check_params(prm));
   if (!fwd || !grad || !out) return GS_ERR_NULL;
   if (!fwd->T || !fwd->last) return GS_ERR_NULL;
+  if (proj->capacity > 0 && !proj->color_d) return GS_ERR_NULL;
   if (map->n > 0 && (!out->dmo || !out->dsu || !out->dq || !out->drgb)) return GS_ERR_NULL;
   if (!aligned(out->dmo, 16) || !aligned(out->dsu, 16) || !aligned(out->dq, 16) || !aligned(out->drgb, 16))
     return GS_ERR_ALIGN;
@@ -170,6 +172,20 @@ gs_status gs_info_gain_batch(const gs_map* map, const gs_camera* cams, int32_t n
                                     (cudaStream_t)stream));
 }
 
+gs_status gs_info_gain_composite(const gs_proj* proj, const gs_bins* bins, const gs_camera* cams, int32_t n_views,
+                                 const gs_params* prm, int32_t mode, float* ig_out, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  GS_TRY(check_proj(proj));
+  GS_TRY(check_bins(bins));
+  GS_TRY(check_views(cams, n_views));
+  GS_TRY(check_params(prm));
+  if (mode != GS_IG_RENDER_MEAN) return GS_ERR_ARG;
+  if (!ig_out) return GS_ERR_NULL;
+  if (!aligned(ig_out, 4)) return GS_ERR_ALIGN;
+  GS_TRY(check_ws(ws, ws_bytes, ig_composite_ws_bytes(bins->tile_capacity)));
+  return from_cuda(launch_ig_composite(*proj, *bins, cams, n_views, *prm, ig_out, ws, (cudaStream_t)stream));
+}
+
 gs_status gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t rec_capacity, int64_t pair_capacity,
                             int64_t tile_capacity, size_t* bytes) {
   if (!bytes) return GS_ERR_NULL;
@@ -179,6 +195,7 @@ gs_status gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t rec_
     case GS_OP_BIN_SORT: *bytes = bin_ws_bytes(rec_capacity, pair_capacity, tile_capacity); return GS_OK;
     case GS_OP_RENDER_BWD: *bytes = bwd_ws_bytes(rec_capacity); return GS_OK;
     case GS_OP_INFO_GAIN: *bytes = ig_ws_bytes(n, n_views, pair_capacity, tile_capacity); return GS_OK;
+    case GS_OP_IG_COMPOSITE: *bytes = ig_composite_ws_bytes(tile_capacity); return GS_OK;
     default: return GS_ERR_ARG;
   }
 }

@@ -76,6 +76,10 @@ cudaError_t launch_render_bwd(const gs_map& map, const gs_proj& proj, const gs_b
                               const gs_image_grad& g, const gs_camera* cams, int n_views, const gs_params& p,
                               const gs_map_grad& out, void* ws, cudaStream_t st);
 
+size_t ig_composite_ws_bytes(int64_t tile_cap);
+cudaError_t launch_ig_composite(const gs_proj& proj, const gs_bins& bins, const gs_camera* cams, int n_views,
+                                const gs_params& p, float* ig_out, void* ws, cudaStream_t st);
+
 size_t ig_ws_bytes(int64_t n, int n_views, int64_t pair_cap, int64_t tile_cap);
 cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_views, const gs_params& p,
                              float* ig_out, uint32_t* status, int64_t pair_cap, int64_t tile_cap, void* ws,

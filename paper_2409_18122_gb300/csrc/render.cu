@@ -335,12 +335,63 @@ size_t ig_ws_bytes(int64_t n, int n_views, int64_t pair_cap, int64_t tile_cap) {
   c.take<uint32_t>(pair_cap);                            // tile
   c.take<uint32_t>(pair_cap);                            // rec
   c.take<uint32_t>(2 * tile_cap);                        // ranges
-  c.take<float>(32 * tile_cap);                          // per work-item sums (<= 32 items per tile)
-  c.take<uint32_t>(4);                                   // work counter
   size_t a = project_ws_bytes(n, n_views), b = bin_ws_bytes(rec_cap, pair_cap, tile_cap);
-  const size_t o = 4 * align_up(sizeof(uint32_t) * (size_t)(32 * tile_cap), 256) + sort_temp_bytes(32 * tile_cap);
+  const size_t o = ig_composite_ws_bytes(tile_cap);
   c.take<char>(a > b ? (a > o ? a : o) : (b > o ? b : o));
   return align_up(c.off, 256);
+}
+
+size_t ig_composite_ws_bytes(int64_t tile_cap) {
+  const int64_t item_cap = 32 * tile_cap;
+  Carver c(nullptr);
+  c.take<float>(item_cap);       // per-item sums
+  c.take<uint32_t>(4);           // work counter
+  c.take<uint32_t>(item_cap);    // order keys / values, ping-pong
+  c.take<uint32_t>(item_cap);
+  c.take<uint32_t>(item_cap);
+  c.take<uint32_t>(item_cap);
+  c.take<char>(sort_temp_bytes(item_cap));
+  return align_up(c.off, 256);
+}
+
+cudaError_t launch_ig_composite(const gs_proj& proj, const gs_bins& bins, const gs_camera* cams, int n_views,
+                                const gs_params& p, float* ig_out, void* ws, cudaStream_t st) {
+  const int64_t item_cap = 32 * bins.tile_capacity;
+  Carver c(ws);
+  float* item_sum = c.take<float>(item_cap);
+  uint32_t* work = c.take<uint32_t>(4);
+  uint32_t* ok_a = c.take<uint32_t>(item_cap);
+  uint32_t* ov_a = c.take<uint32_t>(item_cap);
+  uint32_t* ok_b = c.take<uint32_t>(item_cap);
+  uint32_t* ov_b = c.take<uint32_t>(item_cap);
+  void* otmp = c.take<char>(sort_temp_bytes(item_cap));
+  k_zero_words<<<1, 32, 0, st>>>(work, 4);
+  note_launch();
+  // longest tile lists first
+  {
+    int64_t gb = (item_cap + 255) / 256;
+    if (gb > 4096) gb = 4096;
+    k_item_cost<<<(unsigned)gb, 256, 0, st>>>(proj, bins, n_views, item_cap, ok_a);
+    note_launch();
+  }
+  bool in_a = false;
+  cudaError_t e = radix_sort(ok_a, nullptr, nullptr, SortBufs{ok_a, ov_a, ok_b, ov_b},
+                             proj.view_info + kVI * n_views + 2, item_cap, 0, 16, otmp, st, &in_a);
+  if (e != cudaSuccess) return e;
+  const uint32_t* order = in_a ? ov_a : ov_b;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ig_items, kIgWarps * 32, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)device_sm_count() * per_sm;
+  if (grid * kIgWarps > item_cap) grid = (item_cap + kIgWarps - 1) / kIgWarps;
+  if (grid < 1) grid = 1;
+  k_ig_items<<<(unsigned)grid, kIgWarps * 32, 0, st>>>(proj, bins, cams, n_views, p, order, item_sum, item_cap,
+                                                       work);
+  note_launch();
+  k_ig_views<<<n_views, 256, 0, st>>>(proj.view_info, cams, n_views, item_sum, item_cap, ig_out);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_views, const gs_params& p,
@@ -371,50 +422,16 @@ cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_vie
   bins.tile = c.take<uint32_t>(pair_cap);
   bins.rec = c.take<uint32_t>(pair_cap);
   bins.ranges = c.take<uint32_t>(2 * tile_cap);
-  float* item_sum = c.take<float>(32 * tile_cap);
-  uint32_t* work = c.take<uint32_t>(4);
   size_t a = project_ws_bytes(map.n, n_views), b = bin_ws_bytes(rec_cap, pair_cap, tile_cap);
-  const size_t o = 4 * align_up(sizeof(uint32_t) * (size_t)(32 * tile_cap), 256) + sort_temp_bytes(32 * tile_cap);
+  const size_t o = ig_composite_ws_bytes(tile_cap);
   void* inner = c.take<char>(a > b ? (a > o ? a : o) : (b > o ? b : o));
 
   cudaError_t e = launch_project(map, cams, n_views, p, proj, inner, st);
   if (e != cudaSuccess) return e;
   e = launch_bin_sort(proj, cams, n_views, p, bins, inner, st);
   if (e != cudaSuccess) return e;
-  k_zero_words<<<1, 32, 0, st>>>(work, 4);
-  note_launch();
-  // longest tile lists first (the inner workspace is free again once binning is done)
-  const int64_t item_cap = 32 * tile_cap;
-  Carver oc(inner);
-  uint32_t* ok_a = oc.take<uint32_t>(item_cap);
-  uint32_t* ov_a = oc.take<uint32_t>(item_cap);
-  uint32_t* ok_b = oc.take<uint32_t>(item_cap);
-  uint32_t* ov_b = oc.take<uint32_t>(item_cap);
-  void* otmp = oc.take<char>(sort_temp_bytes(item_cap));
-  {
-    int64_t gb = (item_cap + 255) / 256;
-    if (gb > 4096) gb = 4096;
-    k_item_cost<<<(unsigned)gb, 256, 0, st>>>(proj, bins, n_views, item_cap, ok_a);
-    note_launch();
-  }
-  bool in_a = false;
-  e = radix_sort(ok_a, nullptr, nullptr, SortBufs{ok_a, ov_a, ok_b, ov_b}, proj.view_info + kVI * n_views + 2,
-                 item_cap, 0, 16, otmp, st, &in_a);
-  if (e != cudaSuccess) return e;
-  const uint32_t* order = in_a ? ov_a : ov_b;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ig_items, kIgWarps * 32, 0);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)device_sm_count() * per_sm;
-  if (grid * kIgWarps > item_cap) grid = (item_cap + kIgWarps - 1) / kIgWarps;
-  if (grid < 1) grid = 1;
-  k_ig_items<<<(unsigned)grid, kIgWarps * 32, 0, st>>>(proj, bins, cams, n_views, p, order, item_sum, item_cap,
-                                                       work);
-  note_launch();
-  k_ig_views<<<n_views, 256, 0, st>>>(proj.view_info, cams, n_views, item_sum, item_cap, ig_out);
-  note_launch();
-  return cudaGetLastError();
+  // the inner workspace is free again once binning is done
+  return launch_ig_composite(proj, bins, cams, n_views, p, ig_out, inner, st);
 }
 
 }  // namespace gs

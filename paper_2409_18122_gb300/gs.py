@@ -154,9 +154,10 @@ class Frame:
     """
 
     def __init__(self, n: int, cams: Sequence, params: RenderParams = RenderParams(),
-                 pair_capacity: Optional[int] = None, device="cuda"):
+                 pair_capacity: Optional[int] = None, device="cuda", with_color: bool = True):
         self.device = torch.device(device)
         self.params = params
+        self.with_color = with_color
         self.cams = list(cams)
         self.V = len(self.cams)
         self.n = int(n)
@@ -171,6 +172,9 @@ class Frame:
 
     def _alloc(self, pair_capacity: int):
         d, rc = self.device, self.rec_capacity
+        for name in ("pair_tile", "pair_rec", "ws", "mean_ext", "conic_o", "color_d", "gid", "view", "rect"):
+            if hasattr(self, name):
+                setattr(self, name, None)   # release before reallocating
         self.pair_capacity = pair_capacity
         self.status = torch.zeros(1, dtype=torch.int32, device=d)
         self.rec_count = torch.zeros(1, dtype=torch.int32, device=d)
@@ -179,7 +183,7 @@ class Frame:
         self.view = _alloc_u32(rc, d)
         self.mean_ext = torch.empty((rc, 4), dtype=torch.float32, device=d)
         self.conic_o = torch.empty((rc, 4), dtype=torch.float32, device=d)
-        self.color_d = torch.empty((rc, 4), dtype=torch.float32, device=d)
+        self.color_d = torch.empty((rc, 4), dtype=torch.float32, device=d) if self.with_color else None
         self.unc = torch.empty(rc, dtype=torch.float32, device=d)
         self.rect = torch.empty((rc, 4), dtype=torch.int16, device=d)
         self.depth_key = _alloc_u32(rc, d)
@@ -257,6 +261,20 @@ class Frame:
                                   ctypes.byref(self.c_params), ctypes.byref(c_out), _ptr(self.ws), self.ws.numel(),
                                   _stream(stream)), "gs_render_bwd"))
         return g
+
+    def info_gain(self, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """Per-view mean of the composited uncertainty of the projected and binned views
+        (gs_info_gain_composite; call project and bin_sort first)."""
+        o = torch.zeros(self.V, dtype=torch.float32, device=self.device) if out is None else out
+        if not hasattr(self, "ig_ws"):
+            self.ig_ws = torch.empty(L.workspace_size(L.GS_OP_IG_COMPOSITE, self.n, self.V, 0, 0,
+                                                      max(self.n_tiles, 1)), dtype=torch.uint8, device=self.device)
+        _timed("gs_info_gain_composite", stream, lambda: L.check(
+            L.lib().gs_info_gain_composite(ctypes.byref(self.c_proj), ctypes.byref(self.c_bins), _ptr(self.cams_dev),
+                                           self.V, ctypes.byref(self.c_params), L.GS_IG_RENDER_MEAN, _ptr(o),
+                                           _ptr(self.ig_ws), self.ig_ws.numel(), _stream(stream)),
+            "gs_info_gain_composite"))
+        return o
 
     def forward(self, gmap: GaussianMapTensors, images=None, stream=None):
         """project -> bin_sort -> render_fwd."""
