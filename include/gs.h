@@ -58,9 +58,12 @@ enum {
   GS_FLAG_RANGE_OVERFLOW = 1u << 1,  /* more tiles over all views than gs_bins.tile_capacity   */
   GS_FLAG_BAD_CAMERA = 1u << 2,      /* a camera has width*height <= 0, a non-positive focal length or an invalid tile size */
   GS_FLAG_NONFINITE = 1u << 3,       /* informational: Gaussians with non-finite parameters were culled */
-  GS_FLAG_RECORD_OVERFLOW = 1u << 4  /* more visible (Gaussian, view) records than capacity    */
+  GS_FLAG_RECORD_OVERFLOW = 1u << 4, /* more visible (Gaussian, view) records than capacity    */
+  GS_FLAG_BAD_RECORDS = 1u << 5      /* gs_bin_sort input: records not grouped by increasing view,
+                                        a view id >= n_views, or a rectangle outside its view's tiles */
 };
-#define GS_FLAG_ERROR_MASK (GS_FLAG_PAIR_OVERFLOW | GS_FLAG_RANGE_OVERFLOW | GS_FLAG_BAD_CAMERA | GS_FLAG_RECORD_OVERFLOW)
+#define GS_FLAG_ERROR_MASK \
+  (GS_FLAG_PAIR_OVERFLOW | GS_FLAG_RANGE_OVERFLOW | GS_FLAG_BAD_CAMERA | GS_FLAG_RECORD_OVERFLOW | GS_FLAG_BAD_RECORDS)
 
 /* ------------------------------------------------------------------ inputs */
 
@@ -111,11 +114,11 @@ typedef struct {
 
 /* ------------------------------------------------------------- projection */
 
-/* Projected records, one per visible (Gaussian, view).  Order: Gaussians are
- * taken in groups of 32 consecutive ids (group k = ids 32k .. 32k+31); records
- * are ordered by (group, view, Gaussian id), so within one view they ascend in
- * Gaussian id, and the records of one (group, view) are contiguous.  DEVICE
- * buffers of `capacity` entries; capacity >= n * n_views never overflows.
+/* Projected records, one per visible (Gaussian, view).  Order: by (view,
+ * Gaussian id), so the records of one view are contiguous.  Gaussians are
+ * taken in groups of 32 consecutive ids (group k = ids 32k .. 32k+31); the
+ * records of one (view, group) are contiguous too.  DEVICE buffers of
+ * `capacity` entries; capacity >= n * n_views never overflows.
  *   count      [1]        number of records written
  *   status     [1]        device status word (GS_FLAG_* bits), OR-ed by every call
  *   view_info  [V+1][4]   per view: (first global tile, first pixel, first warp item,
@@ -131,9 +134,9 @@ typedef struct {
  *   unc        [cap]      uncertainty u of the Gaussian
  *   rect       [cap][4]   uint16 tile rectangle (x0, y0, x1, y1), ends exclusive
  *   depth_key  [cap]      IEEE-754 bits of the float32 depth (the sort key)
- *   grp_mask   [G*V]      bit i of entry (k, v) = Gaussian 32k+i is visible in view v (G = ceil(n/32))
- *   grp_base   [G*V+1]    index of the first record of (group k, view v) at k*V + v; last entry = count
- * The record of Gaussian g in view v is grp_base[k*V+v] + popcount(grp_mask[k*V+v] & ((1 << i) - 1))
+ *   grp_mask   [V*G]      bit i of entry v*G + k = Gaussian 32k+i is visible in view v (G = ceil(n/32))
+ *   grp_base   [V*G+1]    index of the first record of (view v, group k) at v*G + k; last entry = count
+ * The record of Gaussian g in view v is grp_base[v*G+k] + popcount(grp_mask[v*G+k] & ((1 << i) - 1))
  * with k = g / 32, i = g % 32, if bit i is set. */
 typedef struct {
   int64_t capacity;
@@ -161,7 +164,7 @@ typedef struct {
  * mu_2D = (fx t_x/t_z + cx, fy t_y/t_z + cy); support box from
  * q <= Q = 2 ln(o / alpha_min): half-widths sqrt(Q Sigma_2D,xx), sqrt(Q Sigma_2D,yy),
  * clipped to the image and converted to tiles (cull if empty).
- * Records are written to `out` in (group of 32 Gaussians, view, Gaussian) order.
+ * Records are written to `out` in (view, Gaussian) order.
  * ws: DEVICE workspace of gs_workspace_size(GS_OP_PROJECT, ...) bytes.
  * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG (n < 0, n_views < 1,
  * n >= 2^32, bad params), GS_ERR_WORKSPACE, GS_ERR_CUDA; device flags
@@ -173,9 +176,9 @@ gs_status gs_project(const gs_map* map, const gs_camera* cams, int32_t n_views, 
 
 /* Tile-sorted pair list.  DEVICE buffers:
  *   count   [1]               number of (tile, record) pairs P (may exceed capacity: overflow flag)
- *   tile    [pair_capacity]   global tile id of each pair, ascending
+ *   tile    [pair_capacity]   global tile id of each pair, ascending; may be NULL (not written)
  *   rec     [pair_capacity]   record index of each pair
- *   ranges  [tile_capacity][2] per global tile: [start, end) into tile/rec
+ *   ranges  [tile_capacity][2] per global tile: [start, end) into tile/rec, clipped to pair_capacity
  * Global tile id of tile (x, y) of view v = view_info[v].first_tile + y * tiles_x(v) + x,
  * tiles_x(v) = ceil(W_v / tile_w(v)), tiles_y(v) = ceil(H_v / tile_h(v)) with the
  * view's tile size (its camera's, else gs_params'). */
@@ -191,12 +194,16 @@ typedef struct {
 /* gs_bin_sort -- Sec. III "sorted in increasing order of depth": emits one pair
  * per tile covered by each record's rectangle and orders all pairs by
  * (view, tile, float32 depth, record index) -- bit-exact, deterministic.
- * Implementation: stable LSD radix sort of the records by depth bits, emission
- * in that order, stable LSD radix sort of the pairs by global tile id, then
- * per-tile [start, end) ranges.
+ * Input: records grouped by view in increasing view order (as gs_project
+ * writes them), rectangles inside their view's tile grid; other input sets
+ * GS_FLAG_BAD_RECORDS and leaves the output unspecified (but in bounds).
+ * Implementation: stable LSD radix sort of the record indices by depth bits and
+ * then by view; per-view chunks count their pairs per tile; one exclusive scan
+ * over (tile, chunk) gives every tile's range and every chunk's first slot in
+ * it; each pair is then written once, straight to its slot.
  * ws: DEVICE workspace of gs_workspace_size(GS_OP_BIN_SORT, ...) bytes.
  * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG, GS_ERR_WORKSPACE, GS_ERR_CUDA;
- * device flags GS_FLAG_PAIR_OVERFLOW, GS_FLAG_RANGE_OVERFLOW. */
+ * device flags GS_FLAG_PAIR_OVERFLOW, GS_FLAG_RANGE_OVERFLOW, GS_FLAG_BAD_RECORDS. */
 gs_status gs_bin_sort(const gs_proj* proj, const gs_camera* cams, int32_t n_views, const gs_params* prm,
                       gs_bins* out, void* ws, size_t ws_bytes, void* stream);
 

@@ -20,7 +20,9 @@ GS_FLAG_RANGE_OVERFLOW = 1 << 1
 GS_FLAG_BAD_CAMERA = 1 << 2
 GS_FLAG_NONFINITE = 1 << 3
 GS_FLAG_RECORD_OVERFLOW = 1 << 4
-GS_FLAG_ERROR_MASK = GS_FLAG_PAIR_OVERFLOW | GS_FLAG_RANGE_OVERFLOW | GS_FLAG_BAD_CAMERA | GS_FLAG_RECORD_OVERFLOW
+GS_FLAG_BAD_RECORDS = 1 << 5
+GS_FLAG_ERROR_MASK = (GS_FLAG_PAIR_OVERFLOW | GS_FLAG_RANGE_OVERFLOW | GS_FLAG_BAD_CAMERA | GS_FLAG_RECORD_OVERFLOW
+                      | GS_FLAG_BAD_RECORDS)
 GS_IG_RENDER_MEAN = 0
 GS_OP_PROJECT, GS_OP_BIN_SORT, GS_OP_RENDER_BWD, GS_OP_INFO_GAIN, GS_OP_IG_COMPOSITE = range(5)
 GS_NOALLOC_MAX_RECORDS = 1 << 18

@@ -76,7 +76,7 @@ gs_status check_bins(const gs_bins* b) {
   if (!b) return GS_ERR_NULL;
   if (b->pair_capacity < 1 || b->pair_capacity >= ((int64_t)1 << 32) - 1) return GS_ERR_ARG;
   if (b->tile_capacity < 1 || b->tile_capacity >= ((int64_t)1 << 27)) return GS_ERR_ARG;
-  if (!b->count || !b->tile || !b->rec || !b->ranges) return GS_ERR_NULL;
+  if (!b->count || !b->rec || !b->ranges) return GS_ERR_NULL;   // tile may be NULL
   if (!aligned(b->count, 4) || !aligned(b->tile, 4) || !aligned(b->rec, 4) || !aligned(b->ranges, 8)) return GS_ERR_ALIGN;
   return GS_OK;
 }
@@ -120,7 +120,7 @@ gs_status gs_bin_sort(const gs_proj* proj, const gs_camera* cams, int32_t n_view
   GS_TRY(check_views(cams, n_views));
   GS_TRY(check_params(prm));
   GS_TRY(check_bins(out));
-  GS_TRY(check_ws(ws, ws_bytes, bin_ws_bytes(proj->capacity, out->pair_capacity, out->tile_capacity)));
+  GS_TRY(check_ws(ws, ws_bytes, bin_ws_bytes(proj->capacity, out->pair_capacity, out->tile_capacity, n_views)));
   return from_cuda(launch_bin_sort(*proj, cams, n_views, *prm, *out, ws, (cudaStream_t)stream));
 }
 
@@ -192,7 +192,7 @@ gs_status gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t rec_
   if (n < 0 || n_views < 1 || rec_capacity < 0 || pair_capacity < 0 || tile_capacity < 0) return GS_ERR_ARG;
   switch (op) {
     case GS_OP_PROJECT: *bytes = project_ws_bytes(n, n_views); return GS_OK;
-    case GS_OP_BIN_SORT: *bytes = bin_ws_bytes(rec_capacity, pair_capacity, tile_capacity); return GS_OK;
+    case GS_OP_BIN_SORT: *bytes = bin_ws_bytes(rec_capacity, pair_capacity, tile_capacity, n_views); return GS_OK;
     case GS_OP_RENDER_BWD: *bytes = bwd_ws_bytes(rec_capacity); return GS_OK;
     case GS_OP_INFO_GAIN: *bytes = ig_ws_bytes(n, n_views, pair_capacity, tile_capacity); return GS_OK;
     case GS_OP_IG_COMPOSITE: *bytes = ig_composite_ws_bytes(tile_capacity); return GS_OK;

@@ -1,16 +1,27 @@
 // bin.cu -- gs_bin_sort: (tile, depth)-ordered pair list and per-tile ranges.
 //
 // Sec. III of RT-GuIDE sorts the Gaussians by increasing depth for each camera
-// before splatting.  Here every record is duplicated once per covered screen
-// tile, and the pairs are ordered by (view, tile, float32 depth, record index):
-//   1. stable radix sort of the records by the IEEE bits of their depth
-//      (records arrive in (Gaussian, view) order, so ties keep Gaussian order);
-//   2. pair counts in that order, exclusive scan -> pair offsets;
-//   3. emission: each record writes (global tile id, record index) for the tiles
-//      of its rectangle in row-major order;
-//   4. stable radix sort of the pairs by global tile id (which encodes the view),
-//      so within a tile the depth order of step 1 is kept;
-//   5. [start, end) of every tile by comparing neighbours.
+// before splatting.  Every record is duplicated once per covered screen tile and
+// the pairs are ordered by (view, tile, float32 depth, record index).  The
+// records of each view are contiguous (gs_project writes them view by view), so:
+//   1. view segments: the first record of every view;
+//   2. stable LSD radix sort of the record indices by the IEEE bits of their
+//      depth, segmented by view (every view's records are sorted in place):
+//      (view, depth, record) order;
+//   3. the rectangles in that order, each record's pair count, and an exclusive
+//      scan of the counts: the pairs of the sorted records, in order, are
+//      numbered 0 .. P-1 (records in order, the tiles of a rectangle row-major);
+//   4. the pairs of each view are cut into K equal chunks; one warp per chunk
+//      counts its pairs per tile of the view (shared-memory histogram);
+//   5. one exclusive scan over the counts laid out [global tile][chunk] gives,
+//      for every (tile, chunk), the first slot of that chunk's pairs in the
+//      tile's run -- and with it every tile's [start, end);
+//   6. each warp walks its chunk again in the same order and writes every pair
+//      straight to its slot, ranking pairs of the same tile among the lanes with
+//      a warp match, so the order inside a tile is the depth order of step 2.
+// No pair is ever sorted or moved twice, no block waits on another, and the
+// result is deterministic.  Chunks hold equal numbers of pairs: near Gaussians,
+// which come first in depth order, cover many tiles each.
 #include "gs_common.cuh"
 #include "gs_internal.h"
 
@@ -19,6 +30,11 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kMaxGrid = 4096;
+constexpr int kChunkTarget = 16384;   // warp chunks over all views
+constexpr int kWin = 1024;            // tile cells of a histogram window (shared memory per warp)
+constexpr int kPlaceWin = 512;        // tile cells of a placement window (two arrays per warp)
+constexpr int kWinCols = 256;         // widest window, in tiles
+constexpr int kBinWarps = 8;          // warps (= chunks) per block of the histogram / placement kernels
 
 inline unsigned grid_for(int64_t n_cap) {
   int64_t b = (n_cap + kBlock - 1) / kBlock;
@@ -27,176 +43,374 @@ inline unsigned grid_for(int64_t n_cap) {
   return (unsigned)b;
 }
 
+// Chunks per view: about kChunkTarget warps in total, at most 2^28 count entries.
+int chunks_per_view(int n_views, int64_t tile_cap) {
+  int64_t k = (kChunkTarget + n_views - 1) / n_views;
+  const int64_t max_entries = (int64_t)1 << 28;
+  if (tile_cap > 0 && k * tile_cap > max_entries) k = max_entries / tile_cap;
+  if (k < 1) k = 1;
+  return (int)k;
+}
+
 __device__ inline int64_t clamp_count(const uint32_t* n_dev, int64_t cap) {
   int64_t n = (int64_t)*n_dev;
   return n < cap ? n : cap;
-}
-
-__global__ void k_pair_counts(const gs_proj proj, const uint32_t* __restrict__ srec, uint32_t* __restrict__ cnt) {
-  const int64_t n = clamp_count(proj.count, proj.capacity);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const ushort4 r = reinterpret_cast<const ushort4*>(proj.rect)[srec[i]];
-    cnt[i] = (uint32_t)(r.z - r.x) * (uint32_t)(r.w - r.y);
-  }
-}
-
-__global__ void k_pair_total(const uint32_t* __restrict__ total, int64_t pair_cap, uint32_t* __restrict__ bins_count,
-                             uint32_t* __restrict__ n_clamped, uint32_t* status) {
-  const uint32_t t = *total;
-  *bins_count = t;
-  if ((int64_t)t > pair_cap || t == 0xFFFFFFFFu) set_flag(status, GS_FLAG_PAIR_OVERFLOW);
-  *n_clamped = (int64_t)t > pair_cap ? (uint32_t)pair_cap : t;
-}
-
-// One warp per 32 consecutive records (in depth order).  The warp scans their
-// tile counts, then writes the whole run of pairs with consecutive lanes on
-// consecutive slots; each lane finds the record that owns its pair with a
-// 5-step shuffle search over the running counts.  Writes are coalesced and
-// records with many tiles are spread over the warp.
-__global__ void __launch_bounds__(256) k_emit(const gs_proj proj, const gs_camera* __restrict__ cams, int tile_w,
-                                               const uint32_t* __restrict__ srec, const uint32_t* __restrict__ off,
-                                               int64_t pair_cap, uint32_t* __restrict__ tile_key,
-                                               uint32_t* __restrict__ tile_rec) {
-  const int64_t n = clamp_count(proj.count, proj.capacity);
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i0 = warp0 * 32; i0 < n; i0 += n_warps * 32) {
-    const int64_t i = i0 + lane;
-    uint32_t r = 0, tile0 = 0, tx = 1, w = 1, cnt = 0;
-    if (i < n) {
-      r = srec[i];
-      const ushort4 rc = reinterpret_cast<const ushort4*>(proj.rect)[r];
-      const uint32_t v = proj.view[r];
-      tx = proj.view_info[kVI * v + 3] >> 16;
-      tile0 = proj.view_info[kVI * v] + (uint32_t)rc.y * tx + rc.x;
-      w = (uint32_t)(rc.z - rc.x);
-      cnt = w * (uint32_t)(rc.w - rc.y);
-      if (w == 0) w = 1;
-    }
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += y;
-    }
-    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    const uint32_t excl = incl - cnt;
-    const uint64_t base = __shfl_sync(0xffffffffu, lane == 0 ? off[i0] : 0u, 0);
-    for (uint32_t k0 = 0; k0 < total; k0 += 32) {
-      const uint32_t k = k0 + lane;
-      int pos = 0;
-#pragma unroll
-      for (int step = 16; step >= 1; step >>= 1) {
-        const uint32_t v = __shfl_sync(0xffffffffu, incl, pos + step - 1);
-        if (v <= k) pos += step;
-      }
-      const uint32_t o_tile0 = __shfl_sync(0xffffffffu, tile0, pos);
-      const uint32_t o_tx = __shfl_sync(0xffffffffu, tx, pos);
-      const uint32_t o_w = __shfl_sync(0xffffffffu, w, pos);
-      const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, pos);
-      const uint32_t o_r = __shfl_sync(0xffffffffu, r, pos);
-      const uint64_t slot = base + k;
-      if (k < total && slot < (uint64_t)pair_cap) {
-        const uint32_t j = k - o_excl;
-        const uint32_t y = j / o_w, x = j - y * o_w;
-        tile_key[slot] = o_tile0 + y * o_tx + x;
-        tile_rec[slot] = o_r;
-      }
-    }
-  }
 }
 
 __global__ void k_zero_u32(uint32_t* __restrict__ p, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = 0u;
 }
 
-__global__ void k_ranges(const uint32_t* __restrict__ tile, const uint32_t* n_dev, int64_t pair_cap,
-                         int64_t tile_cap, const uint32_t* __restrict__ view_info, int n_views,
-                         uint32_t* __restrict__ ranges, uint32_t* status) {
-  const int64_t n = clamp_count(n_dev, pair_cap);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && (int64_t)view_info[kVI * n_views] > tile_cap)
-    set_flag(status, GS_FLAG_RANGE_OVERFLOW);
+// seg[v] = first record of view v (seg[V] = n) for records grouped by view in
+// increasing view order; a record out of that order, or with a view id >= V,
+// sets GS_FLAG_BAD_RECORDS.  seg must be zeroed first, so that every entry lies in
+// [0, n] even for bad input.  Thread 0 also stores the number of count entries
+// that step 4 scans: K * min(total tiles, tile_cap).
+__global__ void k_segments(const gs_proj proj, int n_views, int64_t tile_cap, int K, uint32_t* __restrict__ seg,
+                           uint32_t* __restrict__ scan_n) {
+  const int64_t n = clamp_count(proj.count, proj.capacity);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int64_t tiles = proj.view_info[kVI * n_views];
+    if (tiles > tile_cap) tiles = tile_cap;
+    *scan_n = (uint32_t)(tiles * K);
+    if (n == 0)
+      for (int v = 0; v <= n_views; ++v) seg[v] = 0u;
+  }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t t = tile[i];
-    if ((int64_t)t >= tile_cap) continue;
-    if (i == 0 || tile[i - 1] != t) ranges[2 * (int64_t)t] = (uint32_t)i;
-    if (i == n - 1 || tile[i + 1] != t) ranges[2 * (int64_t)t + 1] = (uint32_t)(i + 1);
+    int64_t v = proj.view[i];
+    if (v >= n_views) {
+      set_flag(proj.status, GS_FLAG_BAD_RECORDS);
+      v = n_views - 1;
+    }
+    int64_t prev = -1;
+    if (i > 0) {
+      prev = proj.view[i - 1];
+      if (prev >= n_views) prev = n_views - 1;
+      if (v < prev) set_flag(proj.status, GS_FLAG_BAD_RECORDS);
+    }
+    for (int64_t u = prev + 1; u <= v; ++u) seg[u] = (uint32_t)i;
+    if (i == n - 1)
+      for (int64_t u = v + 1; u <= n_views; ++u) seg[u] = (uint32_t)n;
   }
 }
 
-int bits_for(int64_t tile_cap) {
-  int b = 1;
-  while (b < 32 && ((int64_t)1 << b) < tile_cap) ++b;
-  return b;
+// Chunk (v, k): the sorted records [r0, r1) of view v whose first pair (as
+// numbered in step 3) lies in [P_v k / K, P_v (k+1) / K) of the view's P_v pairs,
+// so every chunk holds about P_v / K pairs; and the view's tile grid.
+struct Chunk {
+  int64_t r0, r1;
+  uint32_t tile_base, n_tiles, tiles_x, tiles_y, k;
+};
+
+// First r in [lo, hi] with poff[r] >= x (hi if none).
+__device__ inline int64_t lower_bound_u32(const uint32_t* __restrict__ poff, int64_t lo, int64_t hi, int64_t x) {
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)poff[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ inline bool chunk_of(int64_t cid, int K, const uint32_t* __restrict__ seg,
+                                const uint32_t* __restrict__ poff, const uint32_t* __restrict__ view_info,
+                                int64_t tile_cap, Chunk& c) {
+  const int v = (int)(cid / K);
+  c.k = (uint32_t)(cid - (int64_t)v * K);
+  int64_t s0 = seg[v], s1 = seg[v + 1];
+  if (s1 < s0) s1 = s0;
+  const int64_t a = poff[s0], b = poff[s1];
+  const int64_t P = b > a ? b - a : 0;
+  c.r0 = lower_bound_u32(poff, s0, s1, a + P * c.k / K);
+  c.r1 = c.k + 1 == (uint32_t)K ? s1 : lower_bound_u32(poff, s0, s1, a + P * (c.k + 1) / K);
+  if (c.r1 < c.r0) c.r1 = c.r0;
+  c.tile_base = view_info[kVI * v];
+  c.n_tiles = view_info[kVI * (v + 1)] - c.tile_base;
+  c.tiles_x = view_info[kVI * v + 3] >> 16;
+  c.tiles_y = c.tiles_x ? c.n_tiles / c.tiles_x : 0u;
+  // a view whose tiles do not all fit under tile_cap is skipped (GS_FLAG_RANGE_OVERFLOW is set elsewhere)
+  return c.n_tiles > 0 && (int64_t)c.tile_base + c.n_tiles <= tile_cap;
+}
+
+// Step 3a: rectangles in sorted order and their pair counts.  A rectangle
+// outside its view's tile grid counts 0 pairs and sets GS_FLAG_BAD_RECORDS.
+__global__ void k_sorted_rects(const gs_proj proj, const uint32_t* __restrict__ seg, int n_views,
+                               const uint32_t* __restrict__ srec, ushort4* __restrict__ srect,
+                               uint32_t* __restrict__ cnt) {
+  const int64_t n = clamp_count(proj.count, proj.capacity);
+  const ushort4* rect = reinterpret_cast<const ushort4*>(proj.rect);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    ushort4 rc = rect[srec[i]];
+    int lo = 0, hi = n_views - 1;   // view of sorted position i: the largest v with seg[v] <= i
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if ((int64_t)__ldg(seg + mid) <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    const uint32_t tx = proj.view_info[kVI * lo + 3] >> 16;
+    const uint32_t nt = proj.view_info[kVI * (lo + 1)] - proj.view_info[kVI * lo];
+    const uint32_t ty = tx ? nt / tx : 0u;
+    uint32_t c = 0;
+    if (rc.x < rc.z && rc.y < rc.w) {
+      if (rc.z <= tx && rc.w <= ty) c = (uint32_t)(rc.z - rc.x) * (uint32_t)(rc.w - rc.y);
+      else set_flag(proj.status, GS_FLAG_BAD_RECORDS);
+    }
+    if (c == 0) rc = make_ushort4(0, 0, 0, 0);   // no pairs: an empty rectangle downstream
+    srect[i] = rc;
+    cnt[i] = c;
+  }
+}
+
+// The tile grid of a view is handled in windows [xa, xb) x [ya, yb) of at most
+// `cells` cells (difference arrays need one extra row and column).
+__device__ inline void window_size(uint32_t tx, uint32_t ty, uint32_t cells, bool extra, uint32_t& ww,
+                                   uint32_t& wh) {
+  const uint32_t e = extra ? 1u : 0u;
+  ww = tx < (uint32_t)kWinCols ? tx : (uint32_t)kWinCols;
+  wh = cells / (ww + e) - e;
+  if (wh > ty) wh = ty;
+  if (wh < 1) wh = 1;
+}
+
+// Step 4: per chunk, the number of its pairs in every tile of its view:
+// cnt[K * global tile + k].  Each record adds the corners of its rectangle to a
+// 2D difference array; a 2D prefix sum turns it into per-tile counts.
+__global__ void __launch_bounds__(kBinWarps * 32) k_bin_hist(const gs_proj proj, const uint32_t* __restrict__ seg,
+                                                             const ushort4* __restrict__ srect,
+                                                             const uint32_t* __restrict__ poff, int n_views, int K,
+                                                             int64_t tile_cap, uint32_t* __restrict__ cnt) {
+  __shared__ uint32_t s_d[kBinWarps][kWin];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t cid = (int64_t)blockIdx.x * kBinWarps + warp;
+  if (cid >= (int64_t)n_views * K) return;
+  Chunk c;
+  if (!chunk_of(cid, K, seg, poff, proj.view_info, tile_cap, c)) {
+    // the tiles of a skipped view that lie under tile_cap are still scanned: zero counts
+    for (int64_t t = lane; t < (int64_t)c.n_tiles && (int64_t)c.tile_base + t < tile_cap; t += 32)
+      cnt[(size_t)K * (c.tile_base + t) + c.k] = 0u;
+    return;
+  }
+  uint32_t* D = s_d[warp];
+  uint32_t ww, wh;
+  window_size(c.tiles_x, c.tiles_y, kWin, true, ww, wh);
+  const uint32_t pitch = ww + 1;
+  for (uint32_t ya = 0; ya < c.tiles_y; ya += wh) {
+    const uint32_t yb = ya + wh < c.tiles_y ? ya + wh : c.tiles_y;
+    for (uint32_t xa = 0; xa < c.tiles_x; xa += ww) {
+      const uint32_t xb = xa + ww < c.tiles_x ? xa + ww : c.tiles_x;
+      for (int i = lane; i < kWin; i += 32) D[i] = 0u;
+      __syncwarp();
+      for (int64_t r = c.r0 + lane; r < c.r1; r += 32) {
+        const ushort4 rc = srect[r];
+        const uint32_t x0 = rc.x > xa ? rc.x : xa, x1 = rc.z < xb ? rc.z : xb;
+        const uint32_t y0 = rc.y > ya ? rc.y : ya, y1 = rc.w < yb ? rc.w : yb;
+        if (x0 < x1 && y0 < y1) {
+          atomicAdd(&D[(y0 - ya) * pitch + (x0 - xa)], 1u);
+          atomicAdd(&D[(y0 - ya) * pitch + (x1 - xa)], 0xFFFFFFFFu);
+          atomicAdd(&D[(y1 - ya) * pitch + (x0 - xa)], 0xFFFFFFFFu);
+          atomicAdd(&D[(y1 - ya) * pitch + (x1 - xa)], 1u);
+        }
+      }
+      __syncwarp();
+      const uint32_t rows = yb - ya, cols = xb - xa;
+      for (uint32_t y = lane; y < rows; y += 32) {   // prefix along x
+        uint32_t run = 0;
+        for (uint32_t x = 0; x < cols; ++x) {
+          run += D[y * pitch + x];
+          D[y * pitch + x] = run;
+        }
+      }
+      __syncwarp();
+      for (uint32_t x = lane; x < cols; x += 32) {   // prefix along y, and out
+        uint32_t run = 0;
+        for (uint32_t y = 0; y < rows; ++y) {
+          run += D[y * pitch + x];
+          cnt[(size_t)K * (c.tile_base + (ya + y) * c.tiles_x + xa + x) + c.k] = run;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Step 5b: ranges of every global tile from the scanned counts, the pair total
+// and the overflow flags.  Empty tiles, and tiles past the scanned range, get [0, 0).
+__global__ void k_bin_ranges(const uint32_t* __restrict__ off, const uint32_t* __restrict__ scan_n,
+                             const uint32_t* __restrict__ total, int K, int64_t pair_cap, int64_t tile_cap,
+                             const uint32_t* __restrict__ view_info, int n_views, uint32_t* __restrict__ ranges,
+                             uint32_t* __restrict__ bins_count, uint32_t* status) {
+  const int64_t lim = (int64_t)*scan_n / K;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const uint32_t t = *total;
+    *bins_count = t;
+    if ((int64_t)t > pair_cap || t == 0xFFFFFFFFu) set_flag(status, GS_FLAG_PAIR_OVERFLOW);
+    if ((int64_t)view_info[kVI * n_views] > tile_cap) set_flag(status, GS_FLAG_RANGE_OVERFLOW);
+  }
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < tile_cap; g += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t a = 0, b = 0;
+    if (g < lim) {
+      a = off[(size_t)K * g];
+      b = off[(size_t)K * (g + 1)];
+      if ((int64_t)a > pair_cap) a = (uint32_t)pair_cap;
+      if ((int64_t)b > pair_cap) b = (uint32_t)pair_cap;
+      if (a == b) a = b = 0u;   // an empty tile is [0, 0)
+    }
+    ranges[2 * g] = a;
+    ranges[2 * g + 1] = b;
+  }
+}
+
+// Step 6: every pair written to its slot.  Lanes hold 32 consecutive records;
+// each sets its bit in a per-tile mask for every tile of its rectangle, so the
+// rank of a record among the group's records covering tile t is the number of
+// lower bits set, in the order of step 2.  The lowest lane of each tile then
+// advances the tile's running slot.
+__global__ void __launch_bounds__(kBinWarps * 32) k_bin_place(const gs_proj proj, const uint32_t* __restrict__ seg,
+                                                              const uint32_t* __restrict__ srec,
+                                                              const ushort4* __restrict__ srect,
+                                                              const uint32_t* __restrict__ poff, int n_views, int K,
+                                                              int64_t tile_cap, const uint32_t* __restrict__ off,
+                                                              gs_bins out) {
+  __shared__ uint32_t s_run[kBinWarps][kPlaceWin];
+  __shared__ uint32_t s_msk[kBinWarps][kPlaceWin];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t bit = 1u << lane, lt = bit - 1u;
+  const int64_t cid = (int64_t)blockIdx.x * kBinWarps + warp;
+  if (cid >= (int64_t)n_views * K) return;
+  Chunk c;
+  if (!chunk_of(cid, K, seg, poff, proj.view_info, tile_cap, c)) return;
+  uint32_t* run = s_run[warp];
+  uint32_t* msk = s_msk[warp];
+  const int64_t cap = out.pair_capacity;
+  uint32_t ww, wh;
+  window_size(c.tiles_x, c.tiles_y, kPlaceWin, false, ww, wh);
+  for (uint32_t ya = 0; ya < c.tiles_y; ya += wh) {
+    const uint32_t yb = ya + wh < c.tiles_y ? ya + wh : c.tiles_y;
+    for (uint32_t xa = 0; xa < c.tiles_x; xa += ww) {
+      const uint32_t xb = xa + ww < c.tiles_x ? xa + ww : c.tiles_x;
+      const uint32_t cols = xb - xa, cells = (yb - ya) * cols;
+      for (uint32_t i = lane; i < cells; i += 32) {
+        const uint32_t y = ya + i / cols, x = xa + i % cols;
+        run[i] = off[(size_t)K * (c.tile_base + y * c.tiles_x + x) + c.k];
+        msk[i] = 0u;
+      }
+      __syncwarp();
+      for (int64_t g = c.r0; g < c.r1; g += 32) {
+        const int64_t r = g + lane;
+        uint32_t x0 = 0, x1 = 0, y0 = 0, y1 = 0, rec = 0;
+        if (r < c.r1) {
+          const ushort4 rc = srect[r];
+          x0 = rc.x > xa ? rc.x : xa;
+          x1 = rc.z < xb ? rc.z : xb;
+          y0 = rc.y > ya ? rc.y : ya;
+          y1 = rc.w < yb ? rc.w : yb;
+          if (x0 < x1 && y0 < y1) rec = srec[r];
+          else x1 = x0;   // nothing in this window
+        }
+        for (uint32_t y = y0; y < y1; ++y)
+          for (uint32_t x = x0; x < x1; ++x) atomicOr(&msk[(y - ya) * cols + (x - xa)], bit);
+        __syncwarp();
+        for (uint32_t y = y0; y < y1; ++y)
+          for (uint32_t x = x0; x < x1; ++x) {
+            const uint32_t i = (y - ya) * cols + (x - xa);
+            const uint32_t slot = run[i] + __popc(msk[i] & lt);
+            if ((int64_t)slot < cap) {
+              out.rec[slot] = rec;
+              if (out.tile) out.tile[slot] = c.tile_base + y * c.tiles_x + x;
+            }
+          }
+        __syncwarp();
+        for (uint32_t y = y0; y < y1; ++y)
+          for (uint32_t x = x0; x < x1; ++x) {
+            const uint32_t i = (y - ya) * cols + (x - xa);
+            const uint32_t m = msk[i];
+            if ((m & lt) == 0u && m != 0u) {   // lowest lane covering the tile
+              run[i] += __popc(m);
+              msk[i] = 0u;
+            }
+          }
+        __syncwarp();
+      }
+    }
+  }
 }
 
 }  // namespace
 
-size_t bin_ws_bytes(int64_t rec_cap, int64_t pair_cap, int64_t tile_cap) {
-  (void)tile_cap;
+size_t bin_ws_bytes(int64_t rec_cap, int64_t pair_cap, int64_t tile_cap, int n_views) {
+  (void)pair_cap;
+  const int K = chunks_per_view(n_views, tile_cap);
+  const int64_t cnt_cap = (int64_t)K * tile_cap + 1;
   Carver c(nullptr);
+  c.take<uint32_t>(n_views + 1);           // view segments
+  c.take<uint32_t>(4);                     // counters
   c.take<uint32_t>(rec_cap);               // record keys a
   c.take<uint32_t>(rec_cap);               // record vals a
   c.take<uint32_t>(rec_cap);               // record keys b
   c.take<uint32_t>(rec_cap);               // record vals b
-  c.take<uint32_t>(rec_cap + 1);           // pair counts
-  c.take<uint32_t>(rec_cap + 1);           // pair offsets
-  c.take<uint32_t>(pair_cap);              // pair keys (ping-pong partner)
-  c.take<uint32_t>(pair_cap);              // pair vals (ping-pong partner)
-  c.take<uint32_t>(4);                     // counters
-  size_t t = sort_temp_bytes(rec_cap > pair_cap ? rec_cap : pair_cap);
-  size_t s = scan_temp_bytes(rec_cap);
+  c.take<ushort4>(rec_cap);                // rectangles in sorted order
+  c.take<uint32_t>(rec_cap + 1);           // pair counts of the sorted records
+  c.take<uint32_t>(rec_cap + 1);           // ... scanned: first pair of each sorted record
+  c.take<uint32_t>(cnt_cap);               // per (tile, chunk) pair counts
+  c.take<uint32_t>(cnt_cap);               // ... scanned
+  size_t t = sort_temp_bytes(rec_cap, n_views);
+  size_t s = scan_temp_bytes(cnt_cap > rec_cap ? cnt_cap : rec_cap);
   c.take<char>(t > s ? t : s);
   return align_up(c.off, 256);
 }
 
 cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_views, const gs_params& p,
                             const gs_bins& out, void* ws, cudaStream_t st) {
-  const int64_t rec_cap = proj.capacity, pair_cap = out.pair_capacity, tile_cap = out.tile_capacity;
+  (void)cams;
+  (void)p;
+  const int64_t rec_cap = proj.capacity, tile_cap = out.tile_capacity;
+  const int K = chunks_per_view(n_views, tile_cap);
+  const int64_t cnt_cap = (int64_t)K * tile_cap + 1;
   Carver c(ws);
+  uint32_t* seg = c.take<uint32_t>(n_views + 1);
+  uint32_t* ctr = c.take<uint32_t>(4);      // [0] count entries to scan, [1] pair total
   uint32_t* rk_a = c.take<uint32_t>(rec_cap);
   uint32_t* rv_a = c.take<uint32_t>(rec_cap);
   uint32_t* rk_b = c.take<uint32_t>(rec_cap);
   uint32_t* rv_b = c.take<uint32_t>(rec_cap);
-  uint32_t* cnt = c.take<uint32_t>(rec_cap + 1);
-  uint32_t* off = c.take<uint32_t>(rec_cap + 1);
-  uint32_t* pk_w = c.take<uint32_t>(pair_cap);
-  uint32_t* pv_w = c.take<uint32_t>(pair_cap);
-  uint32_t* ctr = c.take<uint32_t>(4);      // [0] pair total (saturated), [1] pair count clamped to capacity
-  size_t t = sort_temp_bytes(rec_cap > pair_cap ? rec_cap : pair_cap);
-  size_t s = scan_temp_bytes(rec_cap);
+  ushort4* srect = c.take<ushort4>(rec_cap);
+  uint32_t* rcnt = c.take<uint32_t>(rec_cap + 1);
+  uint32_t* poff = c.take<uint32_t>(rec_cap + 1);
+  uint32_t* cnt = c.take<uint32_t>(cnt_cap);
+  uint32_t* off = c.take<uint32_t>(cnt_cap);
+  size_t t = sort_temp_bytes(rec_cap, n_views);
+  size_t s = scan_temp_bytes(cnt_cap > rec_cap ? cnt_cap : rec_cap);
   void* tmp = c.take<char>(t > s ? t : s);
 
-  // 1. records by depth bits (32 bits, 4 passes: result back in the a buffers)
+  // 1. view segments
+  k_zero_u32<<<grid_for(n_views + 1), kBlock, 0, st>>>(seg, n_views + 1);
+  note_launch();
+  k_segments<<<grid_for(rec_cap), kBlock, 0, st>>>(proj, n_views, tile_cap, K, seg, &ctr[0]);
+  note_launch();
+  // 2. record indices by depth bits within each view (4 passes: result back in the a buffers)
   bool in_a = false;
-  cudaError_t e = radix_sort(proj.depth_key, nullptr, nullptr, SortBufs{rk_a, rv_a, rk_b, rv_b}, proj.count,
-                             rec_cap, 0, 32, tmp, st, &in_a);
+  cudaError_t e = radix_sort(proj.depth_key, nullptr, SortBufs{rk_a, rv_a, rk_b, rv_b}, proj.count, rec_cap, 0, 32,
+                             tmp, st, &in_a, seg, n_views);
   if (e != cudaSuccess) return e;
   const uint32_t* srec = in_a ? rv_a : rv_b;
-  // 2. pair counts and offsets in depth order
-  k_pair_counts<<<grid_for(rec_cap), kBlock, 0, st>>>(proj, srec, cnt);
+  // 3. sorted rectangles, pair counts, pair numbering
+  k_sorted_rects<<<grid_for(rec_cap), kBlock, 0, st>>>(proj, seg, n_views, srec, srect, rcnt);
   note_launch();
-  e = scan_exclusive(cnt, off, proj.count, rec_cap, &ctr[0], tmp, st);
+  e = scan_exclusive(rcnt, poff, proj.count, rec_cap, nullptr, tmp, st);
   if (e != cudaSuccess) return e;
-  k_pair_total<<<1, 1, 0, st>>>(&ctr[0], pair_cap, out.count, &ctr[1], proj.status);
+  // 4. per-chunk tile counts
+  const int64_t chunks = (int64_t)n_views * K;
+  const unsigned bin_grid = (unsigned)((chunks + kBinWarps - 1) / kBinWarps);
+  k_bin_hist<<<bin_grid, kBinWarps * 32, 0, st>>>(proj, seg, srect, poff, n_views, K, tile_cap, cnt);
   note_launch();
-  // 3. emission into whichever buffer makes the final pass land in `out`
-  const int bits = bits_for(tile_cap);
-  const int passes = sort_passes(0, bits);
-  SortBufs pb;
-  if (passes % 2 == 0) pb = SortBufs{out.tile, out.rec, pk_w, pv_w};
-  else pb = SortBufs{pk_w, pv_w, out.tile, out.rec};
-  k_emit<<<grid_for(rec_cap), kBlock, 0, st>>>(proj, cams, p.tile_w, srec, off, pair_cap, pb.keys_a, pb.vals_a);
-  note_launch();
-  // 4. pairs by global tile id
-  e = radix_sort(pb.keys_a, nullptr, pb.vals_a, pb, &ctr[1], pair_cap, 0, bits, tmp, st, &in_a);
+  // 5. slots of every (tile, chunk); ranges and totals
+  e = scan_exclusive(cnt, off, &ctr[0], cnt_cap - 1, &ctr[1], tmp, st);
   if (e != cudaSuccess) return e;
-  // 5. ranges
-  k_zero_u32<<<grid_for(2 * tile_cap), kBlock, 0, st>>>(out.ranges, 2 * tile_cap);
+  k_bin_ranges<<<grid_for(tile_cap), kBlock, 0, st>>>(off, &ctr[0], &ctr[1], K, out.pair_capacity, tile_cap,
+                                                      proj.view_info, n_views, out.ranges, out.count, proj.status);
   note_launch();
-  k_ranges<<<grid_for(pair_cap), kBlock, 0, st>>>(out.tile, &ctr[1], pair_cap, tile_cap, proj.view_info, n_views,
-                                                  out.ranges, proj.status);
+  // 6. placement
+  k_bin_place<<<bin_grid, kBinWarps * 32, 0, st>>>(proj, seg, srec, srect, poff, n_views, K, tile_cap, off, out);
   note_launch();
   return cudaGetLastError();
 }

@@ -43,28 +43,31 @@ cudaError_t scan_exclusive(const uint32_t* in, uint32_t* out, const uint32_t* n_
 
 // ------------------------------------------------------------------ radix sort
 // Stable LSD radix sort of (key, value) uint32 pairs on bits [bit_begin, bit_end).
-// Input: keys_in (nullable: then keys are read as key_src[val]), vals_in
-// (nullable: identity 0..n-1).  Buffers a/b are ping-pong storage of n_cap
-// entries each; the sorted result ends in a if the number of 8-bit passes is
-// even, else in b.  *result_in_a tells which.  n = min(*n_dev, n_cap).
+// Input: keys_in, vals_in (nullable: identity 0..n-1).  Buffers a/b are
+// ping-pong storage of n_cap entries each; the sorted result ends in a if the
+// number of 8-bit passes is even, else in b.  *result_in_a tells which.
+// n = min(*n_dev, n_cap).  With seg != NULL and n_seg > 1 (segmented mode) the
+// elements [seg[s], seg[s+1]) of every segment s < n_seg (seg non-decreasing,
+// seg[n_seg] = n) are sorted among themselves and stay in place.
+// sort_temp_bytes(n_cap, n_seg): scratch for either mode (n_seg 0 for plain).
 struct SortBufs {
   uint32_t* keys_a;
   uint32_t* vals_a;
   uint32_t* keys_b;
   uint32_t* vals_b;
 };
-size_t sort_temp_bytes(int64_t n_cap);
+size_t sort_temp_bytes(int64_t n_cap, int n_seg = 0);
 int sort_passes(int bit_begin, int bit_end);
-cudaError_t radix_sort(const uint32_t* keys_in, const uint32_t* key_src, const uint32_t* vals_in, SortBufs bufs,
-                       const uint32_t* n_dev, int64_t n_cap, int bit_begin, int bit_end, void* temp,
-                       cudaStream_t st, bool* result_in_a);
+cudaError_t radix_sort(const uint32_t* keys_in, const uint32_t* vals_in, SortBufs bufs, const uint32_t* n_dev,
+                       int64_t n_cap, int bit_begin, int bit_end, void* temp, cudaStream_t st, bool* result_in_a,
+                       const uint32_t* seg = nullptr, int n_seg = 0);
 
 // ------------------------------------------------------------------ pipeline stages
 size_t project_ws_bytes(int64_t n, int n_views);
 cudaError_t launch_project(const gs_map& map, const gs_camera* cams, int n_views, const gs_params& p,
                            const gs_proj& out, void* ws, cudaStream_t st);
 
-size_t bin_ws_bytes(int64_t rec_cap, int64_t pair_cap, int64_t tile_cap);
+size_t bin_ws_bytes(int64_t rec_cap, int64_t pair_cap, int64_t tile_cap, int n_views);
 cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_views, const gs_params& p,
                             const gs_bins& out, void* ws, cudaStream_t st);
 

@@ -6,10 +6,10 @@
 // Gaussian-major: one thread per Gaussian reads its 64 bytes of parameters once
 // (coalesced float4 SoA loads), computes the view-independent part (rotation,
 // 3D covariance, opacity, support bound) once, and loops over the cameras held
-// in shared memory.  Records are compacted in (group of 32 Gaussians, view,
-// Gaussian) order with two passes (count, exclusive scan, write), so the order is
-// deterministic, no block waits on another and every record store of a warp is
-// coalesced.
+// in shared memory.  Records are compacted in (view, Gaussian) order with two
+// passes (count per (view, group of 32 Gaussians), exclusive scan, write), so the
+// order is deterministic, the records of every view are contiguous, no block
+// waits on another and every record store of a warp is coalesced.
 #include "gs_common.cuh"
 #include "gs_internal.h"
 
@@ -109,9 +109,10 @@ __device__ __forceinline__ void stage_cams(const gs_camera* __restrict__ cams, c
 }
 
 // One warp = one group of 32 consecutive Gaussians.  Count pass: per view, the
-// ballot of visible lanes is stored (grp_mask) and its popcount counted.  Write
-// pass: the visible lanes of a (group, view) write their records to consecutive
-// slots grp_base + rank, so every store instruction of the warp is contiguous.
+// ballot of visible lanes is stored (grp_mask, entry view * G + group) and its
+// popcount counted.  Write pass: the visible lanes of a (view, group) write their
+// records to consecutive slots grp_base + rank, so every store instruction of the
+// warp is contiguous.
 template <bool kWrite>
 __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera* __restrict__ cams, int n_views,
                                                      gs_params p, const uint32_t* __restrict__ view_info,
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera*
   const uint32_t lt = (1u << lane) - 1u;
   const bool active = g < map.n;
   const bool grp_active = __any_sync(0xffffffffu, active);
+  const int64_t n_grp = (map.n + 31) >> 5;
   float4 mo = make_float4(0.f, 0.f, 0.f, 0.f), su = mo, q = mo, col = mo;
   GaussPre pre;
   pre.valid = false;
@@ -147,7 +149,7 @@ __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera*
       const bool vis = active && pre.valid && c.W > 0 &&
                        view_proj(mo, pre, c, p.near_plane, p.eps2d, vp);
       const uint32_t m = __ballot_sync(0xffffffffu, vis);
-      const size_t slot = (size_t)grp * n_views + (v0 + i);
+      const size_t slot = (size_t)(v0 + i) * n_grp + grp;
       if (!kWrite) {
         if (lane == 0) {
           out.grp_mask[slot] = m;

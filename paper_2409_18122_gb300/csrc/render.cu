@@ -21,6 +21,7 @@ namespace {
 constexpr int kFwdWarps = 2;   // warps (work items) per CTA: small CTAs free their slot as soon as both finish
 constexpr int kIgWarps = 8;    // warps per CTA of the persistent information-gain kernel
 constexpr int kPix = 1;        // pixels per lane of the forward and information-gain kernels
+constexpr int kBatch = 4;      // overlapping entries whose alphas are computed together
 
 // The list walk of all compositing kernels is a four-stage software pipeline
 // over groups of 32 entries (one per lane).  While group g is composited, the
@@ -101,29 +102,44 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
         sk[lane] = kA;
       }
       __syncwarp();
-      while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        if (all_done<kPix>(done)) continue;
-        const float4 mu = sm[b];
-        const float4 co = sc[b];
-        const float4 c = sk[b];
+      // up to kBatch overlapping entries at a time: their alphas are independent
+      // and computed together; the transmittance updates then run in list order
+      while (m && !all_done<kPix>(done)) {
+        int bb[kBatch];
+        int nb = 0;
 #pragma unroll
-        for (int q = 0; q < kPix; ++q) {
-          if (done[q]) continue;
-          const float alpha = splat_alpha(mu.x, mu.y, co, pxc, pyc[q], p.alpha_max);
-          if (alpha < p.alpha_min) continue;
-          const float Tn = T[q] * (1.f - alpha);
-          if (Tn < p.T_min) { done[q] = true; continue; }
-          const float w = alpha * T[q];
-          cr[q] += w * c.x;
-          cg[q] += w * c.y;
-          cb[q] += w * c.z;
-          cd[q] += w * c.w;
-          cu[q] += w * mu.z;
-          T[q] = Tn;
-          last[q] = (int32_t)(g + b + 1);
-          ++n_contrib[q];
+        for (int k = 0; k < kBatch; ++k) {
+          bb[k] = m ? __ffs(m) - 1 : 0;
+          if (m) { m &= m - 1; nb = k + 1; }
+        }
+        float al[kBatch][kPix];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+          const float4 mu = sm[bb[k]];
+          const float4 co = sc[bb[k]];
+#pragma unroll
+          for (int q = 0; q < kPix; ++q) al[k][q] = k < nb ? splat_alpha(mu.x, mu.y, co, pxc, pyc[q], p.alpha_max) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+#pragma unroll
+          for (int q = 0; q < kPix; ++q) {
+            if (k >= nb || done[q]) continue;
+            const float alpha = al[k][q];
+            if (alpha < p.alpha_min) continue;
+            const float Tn = T[q] * (1.f - alpha);
+            if (Tn < p.T_min) { done[q] = true; continue; }
+            const float w = alpha * T[q];
+            const float4 c = sk[bb[k]];
+            cr[q] += w * c.x;
+            cg[q] += w * c.y;
+            cb[q] += w * c.z;
+            cd[q] += w * c.w;
+            cu[q] += w * sm[bb[k]].z;
+            T[q] = Tn;
+            last[q] = (int32_t)(g + bb[k] + 1);
+            ++n_contrib[q];
+          }
         }
       }
       __syncwarp();
@@ -230,21 +246,37 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
           sc[lane] = cA;
         }
         __syncwarp();
-        while (m) {
-          const int b = __ffs(m) - 1;
-          m &= m - 1;
-          if (all_done<kPix>(done)) continue;
-          const float4 mu = sm[b];
-          const float4 co = sc[b];
+        // up to kBatch overlapping entries at a time: their alphas are independent
+        // and computed together; the transmittance updates then run in list order
+        while (m && !all_done<kPix>(done)) {
+          int bb[kBatch];
+          int nb = 0;
 #pragma unroll
-          for (int q = 0; q < kPix; ++q) {
-            if (done[q]) continue;
-            const float alpha = splat_alpha(mu.x, mu.y, co, pxc, pyc[q], p.alpha_max);
-            if (alpha < p.alpha_min) continue;
-            const float Tn = T[q] * (1.f - alpha);
-            if (Tn < p.T_min) { done[q] = true; continue; }
-            cu[q] += alpha * T[q] * mu.z;
-            T[q] = Tn;
+          for (int k = 0; k < kBatch; ++k) {
+            bb[k] = m ? __ffs(m) - 1 : 0;
+            if (m) { m &= m - 1; nb = k + 1; }
+          }
+          float al[kBatch][kPix], uu[kBatch];
+#pragma unroll
+          for (int k = 0; k < kBatch; ++k) {
+            const float4 mu = sm[bb[k]];
+            const float4 co = sc[bb[k]];
+            uu[k] = mu.z;
+#pragma unroll
+            for (int q = 0; q < kPix; ++q) al[k][q] = k < nb ? splat_alpha(mu.x, mu.y, co, pxc, pyc[q], p.alpha_max) : 0.f;
+          }
+#pragma unroll
+          for (int k = 0; k < kBatch; ++k) {
+#pragma unroll
+            for (int q = 0; q < kPix; ++q) {
+              if (k >= nb || done[q]) continue;
+              const float alpha = al[k][q];
+              if (alpha < p.alpha_min) continue;
+              const float Tn = T[q] * (1.f - alpha);
+              if (Tn < p.T_min) { done[q] = true; continue; }
+              cu[q] += alpha * T[q] * uu[k];
+              T[q] = Tn;
+            }
           }
         }
         __syncwarp();
@@ -332,10 +364,9 @@ size_t ig_ws_bytes(int64_t n, int n_views, int64_t pair_cap, int64_t tile_cap) {
   c.take<uint32_t>(slots);                               // grp_mask
   c.take<uint32_t>(slots + 1);                           // grp_base
   c.take<uint32_t>(1);                                   // pair count
-  c.take<uint32_t>(pair_cap);                            // tile
   c.take<uint32_t>(pair_cap);                            // rec
   c.take<uint32_t>(2 * tile_cap);                        // ranges
-  size_t a = project_ws_bytes(n, n_views), b = bin_ws_bytes(rec_cap, pair_cap, tile_cap);
+  size_t a = project_ws_bytes(n, n_views), b = bin_ws_bytes(rec_cap, pair_cap, tile_cap, n_views);
   const size_t o = ig_composite_ws_bytes(tile_cap);
   c.take<char>(a > b ? (a > o ? a : o) : (b > o ? b : o));
   return align_up(c.off, 256);
@@ -375,7 +406,7 @@ cudaError_t launch_ig_composite(const gs_proj& proj, const gs_bins& bins, const 
     note_launch();
   }
   bool in_a = false;
-  cudaError_t e = radix_sort(ok_a, nullptr, nullptr, SortBufs{ok_a, ov_a, ok_b, ov_b},
+  cudaError_t e = radix_sort(ok_a, nullptr, SortBufs{ok_a, ov_a, ok_b, ov_b},
                              proj.view_info + kVI * n_views + 2, item_cap, 0, 16, otmp, st, &in_a);
   if (e != cudaSuccess) return e;
   const uint32_t* order = in_a ? ov_a : ov_b;
@@ -419,10 +450,10 @@ cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_vie
   bins.pair_capacity = pair_cap;
   bins.tile_capacity = tile_cap;
   bins.count = c.take<uint32_t>(1);
-  bins.tile = c.take<uint32_t>(pair_cap);
+  bins.tile = nullptr;   // compositing needs only the record of each pair and the ranges
   bins.rec = c.take<uint32_t>(pair_cap);
   bins.ranges = c.take<uint32_t>(2 * tile_cap);
-  size_t a = project_ws_bytes(map.n, n_views), b = bin_ws_bytes(rec_cap, pair_cap, tile_cap);
+  size_t a = project_ws_bytes(map.n, n_views), b = bin_ws_bytes(rec_cap, pair_cap, tile_cap, n_views);
   const size_t o = ig_composite_ws_bytes(tile_cap);
   void* inner = c.take<char>(a > b ? (a > o ? a : o) : (b > o ? b : o));
 

@@ -205,10 +205,10 @@ __global__ void __launch_bounds__(256) k_proj_adjoint(gs_map map, gs_proj proj, 
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= map.n) return;
   const int64_t nrec = (int64_t)*proj.count;
-  const int64_t grp = g >> 5;
+  const int64_t grp = g >> 5, n_grp = (map.n + 31) >> 5;   // mask entry of (view v, group) at v * n_grp + group
   const uint32_t bit = 1u << (g & 31), lt = bit - 1u;
   bool any = false;
-  for (int v = 0; v < n_views; ++v) any |= (proj.grp_mask[grp * n_views + v] & bit) != 0;
+  for (int v = 0; v < n_views; ++v) any |= (proj.grp_mask[v * n_grp + grp] & bit) != 0;
   float gmu[3] = {0.f, 0.f, 0.f}, go = 0.f, grgb[3] = {0.f, 0.f, 0.f};
   float M3[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
   const float4 mo = reinterpret_cast<const float4*>(map.mo)[g];
@@ -230,9 +230,9 @@ __global__ void __launch_bounds__(256) k_proj_adjoint(gs_map map, gs_proj proj, 
         S3[i][j] = Rq[3 * i] * s2[0] * Rq[3 * j] + Rq[3 * i + 1] * s2[1] * Rq[3 * j + 1] + Rq[3 * i + 2] * s2[2] * Rq[3 * j + 2];
   }
   for (int v = 0; v < n_views && any; ++v) {
-    const uint32_t m = proj.grp_mask[grp * n_views + v];
+    const uint32_t m = proj.grp_mask[v * n_grp + grp];
     if (!(m & bit)) continue;
-    const uint32_t r = proj.grp_base[grp * n_views + v] + __popc(m & lt);
+    const uint32_t r = proj.grp_base[v * n_grp + grp] + __popc(m & lt);
     if ((int64_t)r >= nrec) continue;
     const float4 A = g2d[3 * (size_t)r], Bv = g2d[3 * (size_t)r + 1], Cv = g2d[3 * (size_t)r + 2];
     grgb[0] += Cv.x; grgb[1] += Cv.y; grgb[2] += Cv.z;

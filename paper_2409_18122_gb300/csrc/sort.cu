@@ -8,6 +8,11 @@
 // memory in digit order and writes it out at the running digit offsets.  No
 // block ever waits on another, the result is deterministic, and the launch
 // shape depends only on the host-side capacity.
+//
+// Segmented mode: the input is cut into contiguous segments (the records of
+// one view each); partitions never cross a segment and digit offsets are
+// scanned per segment, so every pass keeps each segment in place and the
+// result is sorted within each segment.
 #include "gs_internal.h"
 
 namespace gs {
@@ -42,15 +47,78 @@ __device__ inline void part_range(int64_t n, int64_t& beg, int64_t& end) {
   if (beg > n) beg = n;
 }
 
+// Segmented partition map: pmap[0] = partition size, pmap[1 + s] = first
+// partition of segment s (s = 0 .. n_seg).  Segment s of n_s elements gets
+// ceil(n_s / size) partitions; size is chosen so that all fit in the grid.
+__global__ void __launch_bounds__(1024) k_part_map(const uint32_t* __restrict__ seg, int n_seg, const uint32_t* n_dev,
+                                                   int64_t n_cap, int grid, uint32_t* __restrict__ pmap) {
+  __shared__ unsigned long long s_sum[32];
+  const int64_t n = count_of(n_dev, n_cap);
+  const int64_t avail = grid - n_seg > 1 ? grid - n_seg : 1;
+  int64_t size = (n + avail - 1) / avail;
+  size = (size + kTile - 1) / kTile * kTile;
+  if (size < kTile) size = kTile;
+  const int per = (n_seg + blockDim.x - 1) / blockDim.x;
+  const int s0 = threadIdx.x * per;
+  int s1 = s0 + per;
+  if (s1 > n_seg) s1 = n_seg;
+  unsigned long long acc = 0;
+  for (int t = s0; t < s1; ++t) {
+    const int64_t a = seg[t], b = seg[t + 1];
+    if (b > a) acc += (unsigned long long)((b - a + size - 1) / size);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long x = acc;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) s_sum[warp] = x;
+  __syncthreads();
+  unsigned long long e = x - acc;
+  for (int w = 0; w < warp; ++w) e += s_sum[w];
+  for (int t = s0; t < s1; ++t) {
+    pmap[1 + t] = (uint32_t)e;
+    const int64_t a = seg[t], b = seg[t + 1];
+    if (b > a) e += (unsigned long long)((b - a + size - 1) / size);
+  }
+  if (threadIdx.x == blockDim.x - 1) pmap[1 + n_seg] = (uint32_t)e;
+  if (threadIdx.x == 0) pmap[0] = (uint32_t)size;
+}
+
+// Element range of this block's partition (segmented mode): empty past the last.
+__device__ inline void seg_part_range(const uint32_t* __restrict__ seg, int n_seg, const uint32_t* __restrict__ pmap,
+                                      int64_t& beg, int64_t& end) {
+  const int64_t p = blockIdx.x;
+  beg = end = 0;
+  if (p >= (int64_t)pmap[1 + n_seg]) return;
+  int lo = 0, hi = n_seg - 1;   // segment: the largest s with first partition <= p
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int64_t)pmap[1 + mid] <= p) lo = mid;
+    else hi = mid - 1;
+  }
+  const int64_t size = pmap[0];
+  const int64_t a = seg[lo], b = seg[lo + 1];
+  beg = a + (p - (int64_t)pmap[1 + lo]) * size;
+  end = beg + size;
+  if (end > b) end = b;
+  if (beg > end) beg = end;
+}
+
 // (1) digit counts of each partition: hist[part][digit]
-__global__ void __launch_bounds__(kBlock) k_upsweep(const uint32_t* __restrict__ keys, const uint32_t* n_dev,
+__global__ void __launch_bounds__(kBlock) k_upsweep(const uint32_t* __restrict__ keys,
+                                                     const uint32_t* __restrict__ seg, int n_seg,
+                                                     const uint32_t* __restrict__ pmap, const uint32_t* n_dev,
                                                      int64_t n_cap, int shift, uint32_t* __restrict__ hist) {
   __shared__ uint32_t cnt[kWarps][kRadix];
   const int warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kWarps * kRadix; i += kBlock) (&cnt[0][0])[i] = 0;
   __syncthreads();
   int64_t beg, end;
-  part_range(count_of(n_dev, n_cap), beg, end);
+  if (pmap) seg_part_range(seg, n_seg, pmap, beg, end);
+  else part_range(count_of(n_dev, n_cap), beg, end);
   for (int64_t i = beg + threadIdx.x; i < end; i += kBlock) {
     uint32_t d = (keys[i] >> shift) & 0xffu;
     atomicAdd(&cnt[warp][d], 1u);
@@ -125,9 +193,58 @@ __global__ void __launch_bounds__(1024) k_scan_hist(uint32_t* __restrict__ hist,
   }
 }
 
+// (2, segmented) one block per segment s: hist[part][digit] of the segment's
+// partitions -> seg[s] + (elements of smaller digits in the segment) + (elements
+// of this digit in earlier partitions of the segment), i.e. absolute offsets.
+// Partitions are read 8 at a time so that the loads overlap.
+__global__ void __launch_bounds__(kRadix) k_scan_hist_seg(uint32_t* __restrict__ hist, int g,
+                                                          const uint32_t* __restrict__ seg,
+                                                          const uint32_t* __restrict__ pmap) {
+  __shared__ uint32_t s_tot[kRadix];
+  const int s = blockIdx.x, d = threadIdx.x;
+  // (malformed segments can ask for more partitions than the grid has: those are never run)
+  const int64_t p0 = pmap[1 + s] < (uint32_t)g ? pmap[1 + s] : g;
+  const int64_t p1 = pmap[2 + s] < (uint32_t)g ? pmap[2 + s] : g;
+  uint32_t tot = 0;
+  for (int64_t p = p0; p < p1; p += 8) {
+    uint32_t c[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) c[k] = p + k < p1 ? hist[(size_t)(p + k) * kRadix + d] : 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tot += c[k];
+  }
+  s_tot[d] = tot;
+  __syncthreads();
+  // exclusive scan of the digit totals (256 threads, 8 warps)
+  const int lane = d & 31, warp = d >> 5;
+  uint32_t x = tot;
+#pragma unroll
+  for (int k = 1; k < 32; k <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, k);
+    if (lane >= k) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) s_tot[warp] = x;
+  __syncthreads();
+  uint32_t run = seg[s] + x - tot;
+  for (int w = 0; w < warp; ++w) run += s_tot[w];
+  for (int64_t p = p0; p < p1; p += 8) {
+    uint32_t c[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) c[k] = p + k < p1 ? hist[(size_t)(p + k) * kRadix + d] : 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (p + k < p1) hist[(size_t)(p + k) * kRadix + d] = run;
+      run += c[k];
+    }
+  }
+}
+
 // (3) stable scatter of each partition's tiles
 __global__ void __launch_bounds__(kBlock) k_downsweep(const uint32_t* __restrict__ keys_in,
                                                        const uint32_t* __restrict__ vals_in,
+                                                       const uint32_t* __restrict__ seg, int n_seg,
+                                                       const uint32_t* __restrict__ pmap,
                                                        uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                                                        const uint32_t* n_dev, int64_t n_cap, int shift,
                                                        const uint32_t* __restrict__ hist,
@@ -143,9 +260,14 @@ __global__ void __launch_bounds__(kBlock) k_downsweep(const uint32_t* __restrict
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  base[tid] = digit_base[tid] + hist[(size_t)blockIdx.x * kRadix + tid];
   int64_t beg, end;
-  part_range(count_of(n_dev, n_cap), beg, end);
+  if (pmap) {
+    base[tid] = hist[(size_t)blockIdx.x * kRadix + tid];   // already absolute
+    seg_part_range(seg, n_seg, pmap, beg, end);
+  } else {
+    base[tid] = digit_base[tid] + hist[(size_t)blockIdx.x * kRadix + tid];
+    part_range(count_of(n_dev, n_cap), beg, end);
+  }
 
   // the keys/values of the next tile are loaded while the current one is ranked and scattered
   uint32_t nkey[kItems], nval[kItems];
@@ -248,23 +370,33 @@ constexpr size_t kDownSmem = sizeof(uint32_t) * (2 * kTile + kWarps * (kRadix + 
 
 int sort_passes(int bit_begin, int bit_end) { return bit_end > bit_begin ? (bit_end - bit_begin + 7) / 8 : 0; }
 
-size_t sort_temp_bytes(int64_t n_cap) {
-  return align_up(sizeof(uint32_t) * kRadix * parts_for(n_cap), 256) + align_up(sizeof(uint32_t) * kRadix, 256);
+size_t sort_temp_bytes(int64_t n_cap, int n_seg) {
+  const int64_t g = parts_for(n_cap) + (n_seg > 1 ? n_seg : 0);
+  return align_up(sizeof(uint32_t) * kRadix * g, 256) + align_up(sizeof(uint32_t) * kRadix, 256) +
+         align_up(sizeof(uint32_t) * (n_seg + 2), 256);
 }
 
-cudaError_t radix_sort(const uint32_t* keys_in, const uint32_t* /*key_src*/, const uint32_t* vals_in, SortBufs b,
-                       const uint32_t* n_dev, int64_t n_cap, int bit_begin, int bit_end, void* temp,
-                       cudaStream_t st, bool* result_in_a) {
+cudaError_t radix_sort(const uint32_t* keys_in, const uint32_t* vals_in, SortBufs b, const uint32_t* n_dev,
+                       int64_t n_cap, int bit_begin, int bit_end, void* temp, cudaStream_t st, bool* result_in_a,
+                       const uint32_t* seg, int n_seg) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDownSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const int g = (int)parts_for(n_cap);
+  const bool segmented = seg && n_seg > 1;   // one segment sorts like the plain mode
+  const int g = (int)(parts_for(n_cap) + (segmented ? n_seg : 0));
   Carver c(temp);
   uint32_t* hist = c.take<uint32_t>((size_t)kRadix * g);
   uint32_t* digit_base = c.take<uint32_t>(kRadix);
+  uint32_t* pmap = c.take<uint32_t>(n_seg + 2);
+  if (segmented) {
+    k_part_map<<<1, 1024, 0, st>>>(seg, n_seg, n_dev, n_cap, g, pmap);
+    note_launch();
+  } else {
+    pmap = nullptr;
+  }
   const int passes = sort_passes(bit_begin, bit_end);
   const uint32_t* kin = keys_in;
   const uint32_t* vin = vals_in;
@@ -272,11 +404,13 @@ cudaError_t radix_sort(const uint32_t* keys_in, const uint32_t* /*key_src*/, con
     const int shift = bit_begin + 8 * p;
     uint32_t* kout = (p % 2 == 0) ? b.keys_b : b.keys_a;
     uint32_t* vout = (p % 2 == 0) ? b.vals_b : b.vals_a;
-    k_upsweep<<<g, kBlock, 0, st>>>(kin, n_dev, n_cap, shift, hist);
+    k_upsweep<<<g, kBlock, 0, st>>>(kin, seg, n_seg, pmap, n_dev, n_cap, shift, hist);
     note_launch();
-    k_scan_hist<<<1, 1024, 0, st>>>(hist, g, digit_base);
+    if (segmented) k_scan_hist_seg<<<n_seg, kRadix, 0, st>>>(hist, g, seg, pmap);
+    else k_scan_hist<<<1, 1024, 0, st>>>(hist, g, digit_base);
     note_launch();
-    k_downsweep<<<g, kBlock, kDownSmem, st>>>(kin, vin, kout, vout, n_dev, n_cap, shift, hist, digit_base);
+    k_downsweep<<<g, kBlock, kDownSmem, st>>>(kin, vin, seg, n_seg, pmap, kout, vout, n_dev, n_cap, shift, hist,
+                                              digit_base);
     note_launch();
     kin = kout;
     vin = vout;

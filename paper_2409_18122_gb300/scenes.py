@@ -284,10 +284,11 @@ def synthetic_records(seed: int, n_gauss: int, cams: Sequence[Camera], tile_w: i
                       p_visible: float = 0.5, max_extent: int = 6, tie_frac: float = 0.1):
     """Random projection records for exercising binning and sorting alone.
 
-    Returns dict with per-record arrays in (gaussian id, view) order:
-    gid (u32), view (u32), rect (int32 [R,4] = tile x0, y0, x1, y1 with
-    exclusive ends) and depth (float32 > 0).  A fraction `tie_frac` of the
-    depths are copied from another record so that equal keys occur.
+    Returns dict with per-record arrays in (view, gaussian id) order (the
+    records of a view contiguous, as the projection writes them): gid (u32),
+    view (u32), rect (int32 [R,4] = tile x0, y0, x1, y1 with exclusive ends)
+    and depth (float32 > 0).  A fraction `tie_frac` of the depths are copied
+    from another record so that equal keys occur.
     """
     rng = np.random.default_rng(seed)
     gids, views, rects, depths = [], [], [], []
@@ -312,5 +313,7 @@ def synthetic_records(seed: int, n_gauss: int, cams: Sequence[Camera], tile_w: i
         dst = rng.integers(0, r, size=k)
         src = rng.integers(0, r, size=k)
         depth[dst] = depth[src]
-    return dict(gid=np.asarray(gids, np.uint32), view=np.asarray(views, np.uint32),
-                rect=np.asarray(rects, np.int32).reshape(-1, 4), depth=depth)
+    view = np.asarray(views, np.uint32)
+    order = np.argsort(view, kind="stable")
+    return dict(gid=np.asarray(gids, np.uint32)[order], view=view[order],
+                rect=np.asarray(rects, np.int32).reshape(-1, 4)[order], depth=depth[order])

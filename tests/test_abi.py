@@ -69,9 +69,12 @@ def test_status_strings_and_version(lib):
 
 
 def test_workspace_sizes(lib):
+    # binning scratch grows with the record and tile capacities; pairs are written straight to gs_bins
     a = L.workspace_size(L.GS_OP_BIN_SORT, 1000, 2, 2000, 10_000, 100)
-    b = L.workspace_size(L.GS_OP_BIN_SORT, 1000, 2, 2000, 20_000, 100)
-    assert 0 < a < b and a % 256 == 0
+    b = L.workspace_size(L.GS_OP_BIN_SORT, 1000, 2, 4000, 10_000, 100)
+    c = L.workspace_size(L.GS_OP_BIN_SORT, 1000, 2, 2000, 10_000, 200)
+    assert 0 < a < b and a < c and a % 256 == 0
+    assert L.workspace_size(L.GS_OP_BIN_SORT, 1000, 2, 2000, 20_000, 100) == a
     assert L.workspace_size(L.GS_OP_RENDER_BWD, 10, 1, 10) >= 48 * 10
     assert L.workspace_size(L.GS_OP_INFO_GAIN, 100, 3, 0, 1000, 64) > 0
     out = ctypes.c_size_t(0)

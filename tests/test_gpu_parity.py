@@ -38,9 +38,8 @@ def check_projection(fr, gmap, cams, params):
     ref = O.records_from_projection(pr)
     V = len(cams)
     assert rec["n"] == len(ref["gid"])
-    # record order: (group of 32 Gaussians, view, Gaussian)
-    key = (rec["gid"].astype(np.int64) // 32) * V + rec["view"]
-    k2 = key * (1 << 32) + rec["gid"]
+    # record order: (view, Gaussian)
+    k2 = rec["view"].astype(np.int64) * (1 << 32) + rec["gid"]
     assert (np.diff(k2) > 0).all()
     order = np.lexsort((rec["view"], rec["gid"]))          # -> (gid, view) order like the oracle's
     g, v = ref["gid"].astype(np.int64), ref["view"].astype(np.int64)
@@ -66,7 +65,7 @@ def check_projection(fr, gmap, cams, params):
     vis = np.zeros((n_grp * 32, V), bool)
     vis[:gmap.n] = pr["vis"].T.astype(bool)
     bits = (vis.reshape(n_grp, 32, V) * (1 << np.arange(32, dtype=np.uint64))[None, :, None]).sum(axis=1)
-    np.testing.assert_array_equal(rec["grp_mask"].reshape(n_grp, V), bits.astype(np.uint32))
+    np.testing.assert_array_equal(rec["grp_mask"].reshape(V, n_grp), bits.astype(np.uint32).T)
     counts = np.array([bin(int(x)).count("1") for x in rec["grp_mask"]])
     np.testing.assert_array_equal(rec["grp_base"], np.concatenate([[0], np.cumsum(counts)]))
     return rec, ref
