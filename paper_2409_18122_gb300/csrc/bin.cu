@@ -260,11 +260,23 @@ __global__ void k_bin_ranges(const uint32_t* __restrict__ off, const uint32_t* _
   }
 }
 
-// Step 6: every pair written to its slot.  Lanes hold 32 consecutive records;
-// each sets its bit in a per-tile mask for every tile of its rectangle, so the
-// rank of a record among the group's records covering tile t is the number of
-// lower bits set, in the order of step 2.  The lowest lane of each tile then
-// advances the tile's running slot.
+// q = floor(j / w) for 1 <= w and j < 2^16: a float estimate (relative error a
+// few ulp, so off by at most one) corrected to the exact quotient.
+__device__ __forceinline__ uint32_t div_small(uint32_t j, uint32_t w) {
+  uint32_t q = __float2uint_rz(__fdividef((float)j, (float)w));
+  if (q * w > j) --q;
+  if ((q + 1u) * w <= j) ++q;
+  return q;
+}
+
+// Step 6: every pair written to its slot.  A warp takes its chunk's records 32
+// at a time (a group); their pairs inside the current window are enumerated 32
+// at a time (record order, each rectangle row-major), one pair per lane.  The
+// pair of group record o at window cell i sets bit o of msk[i], so its rank
+// among the group's records covering the cell is the number of lower bits set
+// (pairs of lower records come in the same or an earlier round).  After the
+// group, every cell's running slot advances by its count of bits.
+template <bool kTileIds>
 __global__ void __launch_bounds__(kBinWarps * 32) k_bin_place(const gs_proj proj, const uint32_t* __restrict__ seg,
                                                               const uint32_t* __restrict__ srec,
                                                               const ushort4* __restrict__ srect,
@@ -274,14 +286,13 @@ __global__ void __launch_bounds__(kBinWarps * 32) k_bin_place(const gs_proj proj
   __shared__ uint32_t s_run[kBinWarps][kPlaceWin];
   __shared__ uint32_t s_msk[kBinWarps][kPlaceWin];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t bit = 1u << lane, lt = bit - 1u;
   const int64_t cid = (int64_t)blockIdx.x * kBinWarps + warp;
   if (cid >= (int64_t)n_views * K) return;
   Chunk c;
   if (!chunk_of(cid, K, seg, poff, proj.view_info, tile_cap, c)) return;
   uint32_t* run = s_run[warp];
   uint32_t* msk = s_msk[warp];
-  const int64_t cap = out.pair_capacity;
+  const uint32_t cap = out.pair_capacity < 0xFFFFFFFFll ? (uint32_t)out.pair_capacity : 0xFFFFFFFFu;
   uint32_t ww, wh;
   window_size(c.tiles_x, c.tiles_y, kPlaceWin, false, ww, wh);
   for (uint32_t ya = 0; ya < c.tiles_y; ya += wh) {
@@ -296,39 +307,68 @@ __global__ void __launch_bounds__(kBinWarps * 32) k_bin_place(const gs_proj proj
       }
       __syncwarp();
       for (int64_t g = c.r0; g < c.r1; g += 32) {
+        // this lane's record, clipped to the window (window-relative corner)
         const int64_t r = g + lane;
-        uint32_t x0 = 0, x1 = 0, y0 = 0, y1 = 0, rec = 0;
+        uint32_t x0 = 0, y0 = 0, w = 1, cnt = 0, rec = 0;
         if (r < c.r1) {
           const ushort4 rc = srect[r];
-          x0 = rc.x > xa ? rc.x : xa;
-          x1 = rc.z < xb ? rc.z : xb;
-          y0 = rc.y > ya ? rc.y : ya;
-          y1 = rc.w < yb ? rc.w : yb;
-          if (x0 < x1 && y0 < y1) rec = srec[r];
-          else x1 = x0;   // nothing in this window
+          const uint32_t cx0 = rc.x > xa ? rc.x : xa, cx1 = rc.z < xb ? rc.z : xb;
+          const uint32_t cy0 = rc.y > ya ? rc.y : ya, cy1 = rc.w < yb ? rc.w : yb;
+          if (cx0 < cx1 && cy0 < cy1) {
+            x0 = cx0 - xa;
+            y0 = cy0 - ya;
+            w = cx1 - cx0;
+            cnt = w * (cy1 - cy0);
+            rec = srec[r];
+          }
         }
-        for (uint32_t y = y0; y < y1; ++y)
-          for (uint32_t x = x0; x < x1; ++x) atomicOr(&msk[(y - ya) * cols + (x - xa)], bit);
-        __syncwarp();
-        for (uint32_t y = y0; y < y1; ++y)
-          for (uint32_t x = x0; x < x1; ++x) {
-            const uint32_t i = (y - ya) * cols + (x - xa);
-            const uint32_t slot = run[i] + __popc(msk[i] & lt);
-            if ((int64_t)slot < cap) {
-              out.rec[slot] = rec;
-              if (out.tile) out.tile[slot] = c.tile_base + y * c.tiles_x + x;
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += v;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total == 0u) continue;
+        const uint32_t excl = incl - cnt;
+        for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+          const uint32_t k = k0 + lane;
+          int o = 0;   // owner: the first group record whose inclusive count exceeds k
+#pragma unroll
+          for (int step = 16; step >= 1; step >>= 1) {
+            const uint32_t v = __shfl_sync(0xffffffffu, incl, o + step - 1);
+            if (v <= k) o += step;
+          }
+          const uint32_t o_x0 = __shfl_sync(0xffffffffu, x0, o);
+          const uint32_t o_y0 = __shfl_sync(0xffffffffu, y0, o);
+          const uint32_t o_w = __shfl_sync(0xffffffffu, w, o);
+          const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, o);
+          const uint32_t o_rec = __shfl_sync(0xffffffffu, rec, o);
+          const bool valid = k < total;
+          uint32_t i = 0;
+          if (valid) {
+            const uint32_t j = k - o_excl;
+            const uint32_t y = div_small(j, o_w);
+            i = (o_y0 + y) * cols + o_x0 + (j - y * o_w);
+            atomicOr(&msk[i], 1u << o);
+          }
+          __syncwarp();
+          if (valid) {
+            const uint32_t slot = run[i] + __popc(msk[i] & ((1u << o) - 1u));
+            if (slot < cap) {
+              out.rec[slot] = o_rec;
+              if (kTileIds) out.tile[slot] = c.tile_base + (ya + i / cols) * c.tiles_x + xa + i % cols;
             }
           }
+        }
         __syncwarp();
-        for (uint32_t y = y0; y < y1; ++y)
-          for (uint32_t x = x0; x < x1; ++x) {
-            const uint32_t i = (y - ya) * cols + (x - xa);
-            const uint32_t m = msk[i];
-            if ((m & lt) == 0u && m != 0u) {   // lowest lane covering the tile
-              run[i] += __popc(m);
-              msk[i] = 0u;
-            }
+        for (uint32_t i = lane; i < cells; i += 32) {
+          const uint32_t m = msk[i];
+          if (m) {
+            run[i] += __popc(m);
+            msk[i] = 0u;
           }
+        }
         __syncwarp();
       }
     }
@@ -410,7 +450,11 @@ cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_vi
                                                       proj.view_info, n_views, out.ranges, out.count, proj.status);
   note_launch();
   // 6. placement
-  k_bin_place<<<bin_grid, kBinWarps * 32, 0, st>>>(proj, seg, srec, srect, poff, n_views, K, tile_cap, off, out);
+  if (out.tile)
+    k_bin_place<true><<<bin_grid, kBinWarps * 32, 0, st>>>(proj, seg, srec, srect, poff, n_views, K, tile_cap, off, out);
+  else
+    k_bin_place<false><<<bin_grid, kBinWarps * 32, 0, st>>>(proj, seg, srec, srect, poff, n_views, K, tile_cap, off,
+                                                           out);
   note_launch();
   return cudaGetLastError();
 }

@@ -143,19 +143,26 @@ __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera*
     stage_cams(cams, view_info, v0, nv, p, s_cam);
     __syncthreads();
     if (!grp_active) continue;
+    uint32_t m_ahead = 0;   // write pass: the visibility masks of the next 32 views, one per lane
     for (int i = 0; i < nv; ++i) {
       const CamC& c = s_cam[i];
-      ViewProj vp;
-      const bool vis = active && pre.valid && c.W > 0 &&
-                       view_proj(mo, pre, c, p.near_plane, p.eps2d, vp);
-      const uint32_t m = __ballot_sync(0xffffffffu, vis);
       const size_t slot = (size_t)(v0 + i) * n_grp + grp;
+      ViewProj vp;
       if (!kWrite) {
+        const bool vis = active && pre.valid && c.W > 0 && view_proj(mo, pre, c, p.near_plane, p.eps2d, vp);
+        const uint32_t m = __ballot_sync(0xffffffffu, vis);
         if (lane == 0) {
           out.grp_mask[slot] = m;
           counts[slot] = __popc(m);
         }
-      } else if (vis) {
+        continue;
+      }
+      // write pass: only the (Gaussian, view) pairs the count pass found visible are projected again
+      if ((i & 31) == 0)
+        m_ahead = i + lane < nv ? out.grp_mask[(size_t)(v0 + i + lane) * n_grp + grp] : 0u;
+      const uint32_t m = __shfl_sync(0xffffffffu, m_ahead, i & 31);
+      if (!(m & (1u << lane))) continue;
+      if (view_proj(mo, pre, c, p.near_plane, p.eps2d, vp)) {
         const uint32_t dst = out.grp_base[slot] + __popc(m & lt);
         if ((int64_t)dst < out.capacity) {
           out.gid[dst] = (uint32_t)g;
