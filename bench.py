@@ -50,7 +50,25 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graph", type=int, default=1, help="capture the information-gain pass in a CUDA graph")
+    # options for profiling runs (defaults give the benchmark)
+    ap.add_argument("--part", choices=["both", "ig", "map"], default="both", help="which part of the step to run")
+    ap.add_argument("--ig-tiles", default="auto",
+                    help="'auto' (autotuner) or fixed tiles per resolution, e.g. 80x60=8x8,160x120=16x16")
+    ap.add_argument("--ig-views", type=int, default=0, help="score only the first N candidates (0: all 256)")
     return ap.parse_args()
+
+
+def parse_tiles(spec: str):
+    """'80x60=8x8,160x120=16x16' -> {(80, 60): (8, 8), (160, 120): (16, 16)}; 'auto' -> None."""
+    if spec == "auto":
+        return None
+    out = {}
+    for item in spec.split(","):
+        res, tile = item.split("=")
+        w, h = (int(x) for x in res.split("x"))
+        tw, th = (int(x) for x in tile.split("x"))
+        out[(w, h)] = (tw, th)
+    return out
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -140,7 +158,7 @@ class MapStep:
         sc = scenes.config2()
         self.scene = sc
         gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
-        self.frame = gs.Frame(gm.n, sc.cams)
+        self.frame = gs.Frame(gm.n, sc.cams, with_pair_tiles=False)
         tgt = gs.GaussianMapTensors.from_numpy(scenes.perturbed(sc.gmap, seed=2002))
         while True:
             self.frame.reset_status()
@@ -189,21 +207,22 @@ class IGStep:
     the graph bracket the compositing kernel (the step's dominant kernel).
     """
 
-    def __init__(self, gs, scenes, graph: bool, tune: bool = True):
+    def __init__(self, gs, scenes, graph: bool, tiles=None, n_views: int = 0):
         import torch
         self.torch = torch
         self.gs = gs
         sc = scenes.config3()
         self.scene = sc
         self.gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
-        cams = sc.cams
-        self.tile_choice = {}
-        if tune:
+        cams = sc.cams[:n_views] if n_views > 0 else sc.cams
+        if tiles is None:
             self.tile_choice, self.tile_timings = gs.autotune_tiles(self.gm, cams, pair_capacity=400_000_000)
-            cams = gs.with_tiles(cams, self.tile_choice)
             torch.cuda.empty_cache()
+        else:
+            self.tile_choice = dict(tiles)
+        cams = gs.with_tiles(cams, self.tile_choice)
         self.cams = cams
-        self.frame = gs.Frame(self.gm.n, cams, pair_capacity=300_000_000, with_color=False)
+        self.frame = gs.Frame(self.gm.n, cams, pair_capacity=300_000_000, with_color=False, with_pair_tiles=False)
         while True:
             self.frame.reset_status()
             self.frame.project(self.gm)
@@ -358,11 +377,12 @@ def run_ours(args):
 
     rank, world, local = dist_setup()
     torch.backends.cuda.matmul.allow_tf32 = False
-    mstep = MapStep(gs, scenes)
-    istep = IGStep(gs, scenes, graph=bool(args.graph))
+    mstep = MapStep(gs, scenes) if args.part in ("both", "map") else None
+    istep = (IGStep(gs, scenes, graph=bool(args.graph), tiles=parse_tiles(args.ig_tiles), n_views=args.ig_views)
+             if args.part in ("both", "ig") else None)
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     flush = lambda: flush_buf.fill_(1.0)
-    parts = [("map", mstep), ("ig", istep)]
+    parts = [(n, f) for n, f in (("map", mstep), ("ig", istep)) if f is not None]
 
     for _ in range(args.warmup):
         for _, fn in parts:
@@ -378,23 +398,22 @@ def run_ours(args):
     k0 = gs.L.lib().gs_kernel_launches()
     times = timed_loop(torch, args.steps, parts, flush)
     torch.cuda.synchronize()
-    launches = int(gs.L.lib().gs_kernel_launches() - k0) + args.steps * istep.kernels_per_replay
+    launches = int(gs.L.lib().gs_kernel_launches() - k0) + (args.steps * istep.kernels_per_replay if istep else 0)
     barrier(world)
     clocks = sampler.stop()
     stage_ms = {k: statistics.mean(gs.TIMER.durations_ms(k)) for k in list(gs.TIMER.events)}
     gs.TIMER = None
 
-    t_map = sum(times["map"]) / 1e3
-    t_ig = sum(times["ig"]) / 1e3
+    t_map = sum(times.get("map", [0.0])) / 1e3
+    t_ig = sum(times.get("ig", [0.0])) / 1e3
     t_map_all = max_over_ranks(t_map, world)
     t_ig_all = max_over_ranks(t_ig, world)
-    views = istep.n_views * args.steps * world
-    value = views / t_ig_all
-    fwd_bwd = args.steps * world / t_map_all
+    value = istep.n_views * args.steps * world / t_ig_all if istep else None
+    fwd_bwd = args.steps * world / t_map_all if mstep else None
     ms_per_step = (max_over_ranks(t_map + t_ig, world) / args.steps) * 1e3
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and mstep is not None and istep is not None:
         for _ in range(2):
             mstep.e2e()
             istep.e2e()
@@ -406,6 +425,15 @@ def run_ours(args):
                "fwd_bwd_iters_per_s": args.steps * world / e_map,
                "h2d_bytes_per_step": mstep.h2d_bytes() + istep.h2d_bytes(),
                "d2h_bytes_per_step": 4 + 4 * istep.n_views}
+
+    if istep is None or mstep is None:
+        # a profiling run of one part: a short line, no roofline bookkeeping
+        if rank == 0:
+            print(json.dumps({"part": args.part, "steps": args.steps, "ms_per_step": ms_per_step,
+                              "value": value, "fwd_bwd": fwd_bwd, "stages_ms": stage_ms, "clocks": clocks,
+                              "ig_tiles": ({"%dx%d" % k: "%dx%d" % v for k, v in istep.tile_choice.items()}
+                                           if istep else None)}))
+        return
 
     ws = work_stats(torch, gs, mstep)
     props = torch.cuda.get_device_properties(0)

@@ -25,9 +25,10 @@
  *     word, which gs_read_status reads after the stream has been synchronised.
  *     Outputs of a call whose status carries GS_FLAG_PAIR_OVERFLOW or
  *     GS_FLAG_RANGE_OVERFLOW are incomplete and must be discarded.
- *   - Float4-typed arrays ([n][4] floats) must be 16-byte aligned, [n][2]
- *     float and uint16 [n][4] arrays 8-byte aligned; all other arrays 4-byte
- *     aligned; workspaces 256-byte aligned.
+ *   - gs_proj.splat ([n][8] floats) must be 32-byte aligned, other float4-typed
+ *     arrays ([n][4] floats) 16-byte aligned, [n][2] float and uint16 [n][4]
+ *     arrays 8-byte aligned; all other arrays 4-byte aligned; workspaces
+ *     256-byte aligned.
  *   - Rendering constants the paper leaves unstated are fields of gs_params.
  */
 #ifndef GS103_GS_H
@@ -126,12 +127,17 @@ typedef struct {
  *                         A warp item is one 8x4 pixel block of a tile: view v has
  *                         tiles(v) * tile_w * tile_h / 32 of them.
  *   gid, view  [cap]      Gaussian index and view index of the record
- *   mean_ext   [cap][4]   (mu_2D x, mu_2D y, support half-widths sqrt(Q Sigma_2D,xx), sqrt(Q Sigma_2D,yy))
- *   conic_o    [cap][4]   (inverse 2D covariance a, b, c with q = a dx^2 + 2 b dx dy + c dy^2, opacity)
+ *   splat      [cap][8]   32 bytes per record, everything compositing reads:
+ *                         (mu_2D x, mu_2D y, ext, u, a, b, c, o) -- u the uncertainty of the
+ *                         Gaussian, (a, b, c) the inverse 2D covariance with
+ *                         q = a dx^2 + 2 b dx dy + c dy^2, o the opacity, and ext the
+ *                         support half-widths sqrt(Q Sigma_2D,xx) (low 16 bits) and
+ *                         sqrt(Q Sigma_2D,yy) (high 16 bits) as IEEE half floats rounded
+ *                         up (a conservative bound used only to skip Gaussians that
+ *                         cannot reach a pixel block).  32-byte aligned.
  *   color_d    [cap][4]   (r, g, b, depth t_z); may be NULL for records that are only used to
  *                         score information gain (gs_project then skips the colours;
  *                         gs_render_fwd / gs_render_bwd require it)
- *   unc        [cap]      uncertainty u of the Gaussian
  *   rect       [cap][4]   uint16 tile rectangle (x0, y0, x1, y1), ends exclusive
  *   depth_key  [cap]      IEEE-754 bits of the float32 depth (the sort key)
  *   grp_mask   [V*G]      bit i of entry v*G + k = Gaussian 32k+i is visible in view v (G = ceil(n/32))
@@ -145,10 +151,8 @@ typedef struct {
   uint32_t* view_info;
   uint32_t* gid;
   uint32_t* view;
-  float* mean_ext;
-  float* conic_o;
+  float* splat;
   float* color_d;
-  float* unc;
   uint16_t* rect;
   uint32_t* depth_key;
   uint32_t* grp_mask;

@@ -45,9 +45,8 @@ class gs_params(ctypes.Structure):
 
 class gs_proj(ctypes.Structure):
     _fields_ = [("capacity", c_int64), ("count", c_void_p), ("status", c_void_p), ("view_info", c_void_p),
-                ("gid", c_void_p), ("view", c_void_p), ("mean_ext", c_void_p), ("conic_o", c_void_p),
-                ("color_d", c_void_p), ("unc", c_void_p), ("rect", c_void_p), ("depth_key", c_void_p),
-                ("grp_mask", c_void_p), ("grp_base", c_void_p)]
+                ("gid", c_void_p), ("view", c_void_p), ("splat", c_void_p), ("color_d", c_void_p),
+                ("rect", c_void_p), ("depth_key", c_void_p), ("grp_mask", c_void_p), ("grp_base", c_void_p)]
 
 
 class gs_bins(ctypes.Structure):

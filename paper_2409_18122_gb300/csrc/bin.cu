@@ -345,11 +345,13 @@ __global__ void __launch_bounds__(kBinWarps * 32) k_bin_place(const gs_proj proj
           const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, o);
           const uint32_t o_rec = __shfl_sync(0xffffffffu, rec, o);
           const bool valid = k < total;
-          uint32_t i = 0;
+          uint32_t i = 0, cy = 0, cx = 0;   // window cell, its row and column
           if (valid) {
             const uint32_t j = k - o_excl;
             const uint32_t y = div_small(j, o_w);
-            i = (o_y0 + y) * cols + o_x0 + (j - y * o_w);
+            cy = o_y0 + y;
+            cx = o_x0 + (j - y * o_w);
+            i = cy * cols + cx;
             atomicOr(&msk[i], 1u << o);
           }
           __syncwarp();
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(kBinWarps * 32) k_bin_place(const gs_proj proj
             const uint32_t slot = run[i] + __popc(msk[i] & ((1u << o) - 1u));
             if (slot < cap) {
               out.rec[slot] = o_rec;
-              if (kTileIds) out.tile[slot] = c.tile_base + (ya + i / cols) * c.tiles_x + xa + i % cols;
+              if (kTileIds) out.tile[slot] = c.tile_base + (ya + cy) * c.tiles_x + xa + cx;
             }
           }
         }

@@ -12,6 +12,7 @@
 // IEEE-754 implementation that performs the same operations.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -171,6 +172,21 @@ __device__ __forceinline__ GaussPre gauss_pre(float4 mo, float4 su, float4 q, fl
   }
   g.valid = true;
   return g;
+}
+
+// Support half-widths (rx, ry) of a record as two IEEE half floats rounded up, in
+// the bits of one float (rx in the low 16 bits): a conservative bound, used only to
+// skip Gaussians that cannot reach a pixel block.
+__device__ __forceinline__ float pack_ext(float rx, float ry) {
+  const uint32_t lo = __half_as_ushort(__float2half_ru(rx));
+  const uint32_t hi = __half_as_ushort(__float2half_ru(ry));
+  return __uint_as_float(lo | (hi << 16));
+}
+
+__device__ __forceinline__ void unpack_ext(float e, float& rx, float& ry) {
+  const uint32_t b = __float_as_uint(e);
+  rx = __half2float(__ushort_as_half((unsigned short)(b & 0xffffu)));
+  ry = __half2float(__ushort_as_half((unsigned short)(b >> 16)));
 }
 
 // ---------------------------------------------------------------- per view

@@ -60,11 +60,12 @@ extern "C" gs_status gs_render_bwd_noalloc(const gs_map* map, const gs_proj* pro
   if (proj->capacity > kMaxRecords) return GS_ERR_WORKSPACE;   // the fixed scratch is too small
   if (map->n > 0 && (!map->mo || !map->su || !map->q || !map->rgb)) return GS_ERR_NULL;
   if (!proj->count || !proj->status || !proj->view_info || !proj->grp_mask || !proj->grp_base || !proj->gid ||
-      !proj->view || !proj->mean_ext || !proj->conic_o || !proj->color_d || !proj->unc || !bins->count || !bins->rec || !bins->ranges || !fwd->T || !fwd->last)
+      !proj->view || !proj->splat || !proj->color_d || !bins->count || !bins->rec || !bins->ranges || !fwd->T ||
+      !fwd->last)
     return GS_ERR_NULL;
   if (map->n > 0 && (!out->dmo || !out->dsu || !out->dq || !out->drgb)) return GS_ERR_NULL;
   if (!aligned(map->mo, 16) || !aligned(map->su, 16) || !aligned(map->q, 16) || !aligned(map->rgb, 16) ||
-      !aligned(proj->mean_ext, 16) || !aligned(proj->conic_o, 16) || !aligned(proj->color_d, 16) ||
+      !aligned(proj->splat, 32) || !aligned(proj->color_d, 16) ||
       !aligned(out->dmo, 16) || !aligned(out->dsu, 16) ||
       !aligned(out->dq, 16) || !aligned(out->drgb, 16))
     return GS_ERR_ALIGN;

@@ -167,10 +167,10 @@ __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera*
         if ((int64_t)dst < out.capacity) {
           out.gid[dst] = (uint32_t)g;
           out.view[dst] = (uint32_t)(v0 + i);
-          reinterpret_cast<float4*>(out.mean_ext)[dst] = make_float4(vp.mx, vp.my, vp.rx, vp.ry);
-          reinterpret_cast<float4*>(out.conic_o)[dst] = make_float4(vp.ca, vp.cb, vp.cc, pre.o);
+          float4* sp = reinterpret_cast<float4*>(out.splat) + 2 * (size_t)dst;
+          sp[0] = make_float4(vp.mx, vp.my, pack_ext(vp.rx, vp.ry), su.w);
+          sp[1] = make_float4(vp.ca, vp.cb, vp.cc, pre.o);
           if (out.color_d) reinterpret_cast<float4*>(out.color_d)[dst] = make_float4(col.x, col.y, col.z, vp.depth);
-          out.unc[dst] = su.w;
           reinterpret_cast<ushort4*>(out.rect)[dst] =
               make_ushort4((unsigned short)vp.x0, (unsigned short)vp.y0, (unsigned short)vp.x1, (unsigned short)vp.y1);
           out.depth_key[dst] = __float_as_uint(vp.depth);

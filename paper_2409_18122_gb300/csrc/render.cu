@@ -61,8 +61,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
   }
   const uint32_t n = ti.end - ti.beg;
   const uint32_t* rl = bins.rec + ti.beg;
-  const float4* ME = reinterpret_cast<const float4*>(proj.mean_ext);
-  const float4* CO = reinterpret_cast<const float4*>(proj.conic_o);
+  const float4* SP = reinterpret_cast<const float4*>(proj.splat);
   const float4* CD = reinterpret_cast<const float4*>(proj.color_d);
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   uint32_t rA = 0, rB = 0, rC = 0;
@@ -70,34 +69,30 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
   if (32u + lane < n) rB = __ldg(rl + 32 + lane);
   if (64u + lane < n) rC = __ldg(rl + 64 + lane);
   float4 mA = z4, mB = z4;
-  if ((uint32_t)lane < n) mA = __ldg(ME + rA);
-  if (32u + lane < n) mB = __ldg(ME + rB);
+  if ((uint32_t)lane < n) mA = __ldg(SP + 2 * (size_t)rA);
+  if (32u + lane < n) mB = __ldg(SP + 2 * (size_t)rB);
   bool ovA = (uint32_t)lane < n && box_overlaps(mA, wb);
   float4 cA = z4, kA = z4;
-  float uA = 0.f;
   if (ovA) {
-    cA = __ldg(CO + rA);
+    cA = __ldg(SP + 2 * (size_t)rA + 1);
     kA = __ldg(CD + rA);
-    uA = __ldg(proj.unc + rA);
   }
   for (uint32_t g = 0; g < n; g += 32) {
     if (!__any_sync(0xffffffffu, !all_done<kPix>(done))) break;
     const bool ovB = g + 32 + lane < n && box_overlaps(mB, wb);
     float4 cB = z4, kB = z4;
-    float uB = 0.f;
     if (ovB) {
-      cB = __ldg(CO + rB);
+      cB = __ldg(SP + 2 * (size_t)rB + 1);
       kB = __ldg(CD + rB);
-      uB = __ldg(proj.unc + rB);
     }
     float4 mC = z4;
-    if (g + 64 + lane < n) mC = __ldg(ME + rC);
+    if (g + 64 + lane < n) mC = __ldg(SP + 2 * (size_t)rC);
     uint32_t rD = 0;
     if (g + 96 + lane < n) rD = __ldg(rl + g + 96 + lane);
     uint32_t m = __ballot_sync(0xffffffffu, ovA);
     if (m) {
       if (ovA) {
-        sm[lane] = make_float4(mA.x, mA.y, uA, 0.f);
+        sm[lane] = make_float4(mA.x, mA.y, mA.w, 0.f);
         sc[lane] = cA;
         sk[lane] = kA;
       }
@@ -144,7 +139,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
       }
       __syncwarp();
     }
-    mA = mB; ovA = ovB; cA = cB; kA = kB; uA = uB;
+    mA = mB; ovA = ovB; cA = cB; kA = kB;
     rB = rC; mB = mC;
     rC = rD;
   }
@@ -183,8 +178,7 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
   float4* sc = s_stage[warp][1];
   uint32_t n_items = proj.view_info[kVI * n_views + 2] / kPix;
   if ((int64_t)n_items > item_cap) n_items = (uint32_t)item_cap;
-  const float4* ME = reinterpret_cast<const float4*>(proj.mean_ext);
-  const float4* CO = reinterpret_cast<const float4*>(proj.conic_o);
+  const float4* SP = reinterpret_cast<const float4*>(proj.splat);
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   for (;;) {
     uint32_t item = 0;
@@ -217,32 +211,24 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
     if (32u + lane < n) rB = __ldg(rl + 32 + lane);
     if (64u + lane < n) rC = __ldg(rl + 64 + lane);
     float4 mA = z4, mB = z4;
-    if ((uint32_t)lane < n) mA = __ldg(ME + rA);
-    if (32u + lane < n) mB = __ldg(ME + rB);
+    if ((uint32_t)lane < n) mA = __ldg(SP + 2 * (size_t)rA);
+    if (32u + lane < n) mB = __ldg(SP + 2 * (size_t)rB);
     bool ovA = (uint32_t)lane < n && box_overlaps(mA, wb);
     float4 cA = z4;
-    float uA = 0.f;
-    if (ovA) {
-      cA = __ldg(CO + rA);
-      uA = __ldg(proj.unc + rA);
-    }
+    if (ovA) cA = __ldg(SP + 2 * (size_t)rA + 1);
     for (uint32_t g = 0; g < n; g += 32) {
       if (!__any_sync(0xffffffffu, !all_done<kPix>(done))) break;
       const bool ovB = g + 32 + lane < n && box_overlaps(mB, wb);
       float4 cB = z4;
-      float uB = 0.f;
-      if (ovB) {
-        cB = __ldg(CO + rB);
-        uB = __ldg(proj.unc + rB);
-      }
+      if (ovB) cB = __ldg(SP + 2 * (size_t)rB + 1);
       float4 mC = z4;
-      if (g + 64 + lane < n) mC = __ldg(ME + rC);
+      if (g + 64 + lane < n) mC = __ldg(SP + 2 * (size_t)rC);
       uint32_t rD = 0;
       if (g + 96 + lane < n) rD = __ldg(rl + g + 96 + lane);
       uint32_t m = __ballot_sync(0xffffffffu, ovA);
       if (m) {
         if (ovA) {
-          sm[lane] = make_float4(mA.x, mA.y, uA, 0.f);
+          sm[lane] = make_float4(mA.x, mA.y, mA.w, 0.f);
           sc[lane] = cA;
         }
         __syncwarp();
@@ -281,7 +267,7 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
         }
         __syncwarp();
       }
-      mA = mB; ovA = ovB; cA = cB; uA = uB;
+      mA = mB; ovA = ovB; cA = cB;
       rB = rC; mB = mC;
       rC = rD;
     }
@@ -355,9 +341,7 @@ size_t ig_ws_bytes(int64_t n, int n_views, int64_t pair_cap, int64_t tile_cap) {
   c.take<uint32_t>(kVI * (size_t)(n_views + 1));         // view info
   c.take<uint32_t>(rec_cap);                             // gid
   c.take<uint32_t>(rec_cap);                             // view
-  c.take<float4>(rec_cap);                               // mean_ext
-  c.take<float4>(rec_cap);                               // conic_o
-  c.take<float>(rec_cap);                                // unc
+  c.take<float4>(2 * (size_t)rec_cap);                   // splat
   c.take<ushort4>(rec_cap);                              // rect
   c.take<uint32_t>(rec_cap);                             // depth key
   const int64_t slots = ((n + 31) / 32) * (int64_t)n_views;
@@ -437,9 +421,7 @@ cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_vie
   proj.view_info = c.take<uint32_t>(kVI * (size_t)(n_views + 1));
   proj.gid = c.take<uint32_t>(rec_cap);
   proj.view = c.take<uint32_t>(rec_cap);
-  proj.mean_ext = (float*)c.take<float4>(rec_cap);
-  proj.conic_o = (float*)c.take<float4>(rec_cap);
-  proj.unc = c.take<float>(rec_cap);
+  proj.splat = (float*)c.take<float4>(2 * (size_t)rec_cap);
   proj.color_d = nullptr;   // not needed to score views: the projection skips the colours
   proj.rect = (uint16_t*)c.take<ushort4>(rec_cap);
   proj.depth_key = c.take<uint32_t>(rec_cap);

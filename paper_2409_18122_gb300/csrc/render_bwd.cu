@@ -83,8 +83,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
   // colour data of the next group, means of the one after, list indices of the
   // one after that)
   const uint32_t* rl = bins.rec + ti.beg;
-  const float4* ME = reinterpret_cast<const float4*>(proj.mean_ext);
-  const float4* CO = reinterpret_cast<const float4*>(proj.conic_o);
+  const float4* SP = reinterpret_cast<const float4*>(proj.splat);
   const float4* CD = reinterpret_cast<const float4*>(proj.color_d);
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   int g = ((wlast - 1) >> 5) << 5;
@@ -93,23 +92,23 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
   if (g >= 32) rB = __ldg(rl + g - 32 + lane);
   if (g >= 64) rC = __ldg(rl + g - 64 + lane);
   float4 mA = z4, mB = z4;
-  if (g + lane < wlast) mA = __ldg(ME + rA);
-  if (g >= 32) mB = __ldg(ME + rB);
+  if (g + lane < wlast) mA = __ldg(SP + 2 * (size_t)rA);
+  if (g >= 32) mB = __ldg(SP + 2 * (size_t)rB);
   bool ovA = g + lane < wlast && box_overlaps(mA, wb);
   float4 cA = z4, kA = z4;
   if (ovA) {
-    cA = __ldg(CO + rA);
+    cA = __ldg(SP + 2 * (size_t)rA + 1);
     kA = __ldg(CD + rA);
   }
   for (; g >= 0; g -= 32) {
     const bool ovB = g >= 32 && box_overlaps(mB, wb);
     float4 cB = z4, kB = z4;
     if (ovB) {
-      cB = __ldg(CO + rB);
+      cB = __ldg(SP + 2 * (size_t)rB + 1);
       kB = __ldg(CD + rB);
     }
     float4 mC = z4;
-    if (g >= 64) mC = __ldg(ME + rC);
+    if (g >= 64) mC = __ldg(SP + 2 * (size_t)rC);
     uint32_t rD = 0;
     if (g >= 96) rD = __ldg(rl + g - 96 + lane);
     uint32_t m = __ballot_sync(0xffffffffu, ovA);
@@ -244,7 +243,7 @@ __global__ void __launch_bounds__(256) k_proj_adjoint(gs_map map, gs_proj proj, 
     const float tx = R[0] * dx + R[3] * dy + R[6] * dz;
     const float ty = R[1] * dx + R[4] * dy + R[7] * dz;
     const float tz = R[2] * dx + R[5] * dy + R[8] * dz;
-    const float4 con = reinterpret_cast<const float4*>(proj.conic_o)[r];
+    const float4 con = reinterpret_cast<const float4*>(proj.splat)[2 * (size_t)r + 1];
     // dL/dSigma2D = -C G_C C (symmetric-matrix gradients)
     const float C00 = con.x, C01 = con.y, C11 = con.z;
     const float G00 = ga, G01 = 0.5f * gb, G11 = gc;

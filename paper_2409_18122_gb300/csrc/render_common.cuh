@@ -138,10 +138,12 @@ __device__ __forceinline__ bool all_done(const bool* done) {
   return r;
 }
 
-// Can the support box of an entry, me = (mu_x, mu_y, half-width x, half-width y),
-// contain a pixel centre of the warp's block?
-__device__ __forceinline__ bool box_overlaps(const float4& me, const WarpBlock& wb) {
-  return (me.x - me.z <= wb.bx1) && (me.x + me.z >= wb.bx0) && (me.y - me.w <= wb.by1) && (me.y + me.w >= wb.by0);
+// Can the support box of an entry contain a pixel centre of the warp's block?
+// s0 = first half of its splat record (mu_x, mu_y, packed half-widths, u).
+__device__ __forceinline__ bool box_overlaps(const float4& s0, const WarpBlock& wb) {
+  float rx, ry;
+  unpack_ext(s0.z, rx, ry);
+  return (s0.x - rx <= wb.bx1) && (s0.x + rx >= wb.bx0) && (s0.y - ry <= wb.by1) && (s0.y + ry >= wb.by0);
 }
 
 // Fixed-tree block sum (deterministic for a fixed block size); result valid in thread 0.

@@ -150,14 +150,18 @@ class Frame:
     """Device buffers for projecting, binning and rendering one map into a fixed camera set.
 
     pair_capacity bounds the number of (tile, Gaussian) pairs; exceeding it sets
-    GS_FLAG_PAIR_OVERFLOW (see `check_status` / `grow_if_needed`).
+    GS_FLAG_PAIR_OVERFLOW (see `check_status` / `grow_if_needed`).  with_color=False
+    leaves out the per-record colours (scoring only); with_pair_tiles=False leaves
+    out the global tile id of every pair (compositing needs only the ranges).
     """
 
     def __init__(self, n: int, cams: Sequence, params: RenderParams = RenderParams(),
-                 pair_capacity: Optional[int] = None, device="cuda", with_color: bool = True):
+                 pair_capacity: Optional[int] = None, device="cuda", with_color: bool = True,
+                 with_pair_tiles: bool = True):
         self.device = torch.device(device)
         self.params = params
         self.with_color = with_color
+        self.with_pair_tiles = with_pair_tiles
         self.cams = list(cams)
         self.V = len(self.cams)
         self.n = int(n)
@@ -172,7 +176,7 @@ class Frame:
 
     def _alloc(self, pair_capacity: int):
         d, rc = self.device, self.rec_capacity
-        for name in ("pair_tile", "pair_rec", "ws", "mean_ext", "conic_o", "color_d", "gid", "view", "rect"):
+        for name in ("pair_tile", "pair_rec", "ws", "splat", "color_d", "gid", "view", "rect"):
             if hasattr(self, name):
                 setattr(self, name, None)   # release before reallocating
         self.pair_capacity = pair_capacity
@@ -181,17 +185,15 @@ class Frame:
         self.view_info = torch.zeros(4 * (self.V + 1), dtype=torch.int32, device=d)
         self.gid = _alloc_u32(rc, d)
         self.view = _alloc_u32(rc, d)
-        self.mean_ext = torch.empty((rc, 4), dtype=torch.float32, device=d)
-        self.conic_o = torch.empty((rc, 4), dtype=torch.float32, device=d)
+        self.splat = torch.empty((rc, 8), dtype=torch.float32, device=d)
         self.color_d = torch.empty((rc, 4), dtype=torch.float32, device=d) if self.with_color else None
-        self.unc = torch.empty(rc, dtype=torch.float32, device=d)
         self.rect = torch.empty((rc, 4), dtype=torch.int16, device=d)
         self.depth_key = _alloc_u32(rc, d)
         self.n_slots = ((self.n + 31) // 32) * self.V
         self.grp_mask = _alloc_u32(self.n_slots, d)
         self.grp_base = _alloc_u32(self.n_slots + 1, d)
         self.pair_count = torch.zeros(1, dtype=torch.int32, device=d)
-        self.pair_tile = _alloc_u32(pair_capacity, d)
+        self.pair_tile = _alloc_u32(pair_capacity, d) if self.with_pair_tiles else None
         self.pair_rec = _alloc_u32(pair_capacity, d)
         self.ranges = torch.zeros((max(self.n_tiles, 1), 2), dtype=torch.int32, device=d)
         ws = max(L.workspace_size(L.GS_OP_PROJECT, self.n, self.V),
@@ -199,9 +201,8 @@ class Frame:
                  L.workspace_size(L.GS_OP_RENDER_BWD, self.n, self.V, rc))
         self.ws = torch.empty(max(ws, 256), dtype=torch.uint8, device=d)
         self.c_proj = L.gs_proj(rc, _ptr(self.rec_count), _ptr(self.status), _ptr(self.view_info), _ptr(self.gid),
-                                _ptr(self.view), _ptr(self.mean_ext), _ptr(self.conic_o), _ptr(self.color_d),
-                                _ptr(self.unc), _ptr(self.rect), _ptr(self.depth_key), _ptr(self.grp_mask),
-                                _ptr(self.grp_base))
+                                _ptr(self.view), _ptr(self.splat), _ptr(self.color_d), _ptr(self.rect),
+                                _ptr(self.depth_key), _ptr(self.grp_mask), _ptr(self.grp_base))
         self.c_bins = L.gs_bins(pair_capacity, max(self.n_tiles, 1), _ptr(self.pair_count), _ptr(self.pair_tile),
                                 _ptr(self.pair_rec), _ptr(self.ranges))
         self.c_params = self.params.c()

@@ -26,13 +26,22 @@ def u32(t: torch.Tensor) -> np.ndarray:
     return t.cpu().numpy().view(np.uint32)
 
 
+def unpack_ext(bits: np.ndarray) -> np.ndarray:
+    """[n] uint32 of packed half-widths -> [n, 2] float64 (rx from the low 16 bits, ry from the high)."""
+    lo = (bits & 0xFFFF).astype(np.uint16).view(np.float16).astype(np.float64)
+    hi = (bits >> 16).astype(np.uint16).view(np.float16).astype(np.float64)
+    return np.stack([lo, hi], 1)
+
+
 def gpu_records(frame):
     n = int(u32(frame.rec_count)[0])
+    sp = frame.splat[:n].cpu().numpy()
+    ext = unpack_ext(sp[:, 2].copy().view(np.uint32))
     return dict(
         n=n,
         gid=u32(frame.gid)[:n], view=u32(frame.view)[:n],
-        mean_ext=frame.mean_ext[:n].cpu().numpy(), conic_o=frame.conic_o[:n].cpu().numpy(),
-        color_d=frame.color_d[:n].cpu().numpy(), unc=frame.unc[:n].cpu().numpy(),
+        mean_ext=np.concatenate([sp[:, :2].astype(np.float64), ext], 1), conic_o=sp[:, 4:8],
+        color_d=frame.color_d[:n].cpu().numpy(), unc=sp[:, 3],
         rect=frame.rect[:n].cpu().numpy().view(np.uint16).astype(np.int32),
         dkey=u32(frame.depth_key)[:n],
         grp_mask=u32(frame.grp_mask)[:frame.n_slots],
