@@ -40,6 +40,24 @@ WORKLOAD = ("ig: 1,000,000 room Gaussians, 256 candidates (80x60/160x120/320x240
             "map: 500,000 room Gaussians, 4 keyframes 640x480, fwd+bwd+Adam")
 L2_FLUSH_BYTES = 256 << 20
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size k_ig_items launch,
+# from a one-pass ncu capture of
+#   python bench.py --part ig --ig-tiles 80x60=8x8,160x120=16x16,320x240=16x16 --steps 1 --warmup 1
+#          --no-e2e --no-cpu-baseline --graph 0
+# It holds while the tiles match and the sources that shape the kernel and its lists are unchanged.
+IG_TRAFFIC = {"bytes": 8.245e9, "tiles": {"80x60": "8x8", "160x120": "16x16", "320x240": "16x16"},
+              "sources_sha1": "f254fede5f16e4273523d9d07f5eef3a634f7a78"}
+IG_TRAFFIC_SOURCES = ("render.cu", "render_common.cuh", "gs_common.cuh", "bin.cu", "project.cu")
+
+
+def ig_sources_sha1() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for name in IG_TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2409_18122_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -55,6 +73,7 @@ def parse():
     ap.add_argument("--ig-tiles", default="auto",
                     help="'auto' (autotuner) or fixed tiles per resolution, e.g. 80x60=8x8,160x120=16x16")
     ap.add_argument("--ig-views", type=int, default=0, help="score only the first N candidates (0: all 256)")
+    ap.add_argument("--no-unbatched", action="store_true", help="skip the one-view-per-call comparison")
     return ap.parse_args()
 
 
@@ -313,6 +332,36 @@ class IGStep:
         return sum(h.numel() * h.element_size() for h in self.host) + self.host_cams.numel()
 
 
+class Unbatched:
+    """The same candidates scored one view at a time (gs_info_gain_batch with one camera per call)."""
+
+    def __init__(self, gs, istep):
+        import torch
+        self.torch = torch
+        self.istep = istep
+        self.cams_all = istep.frame.cams_dev.view(len(istep.cams), -1)   # the batch's 80-byte camera records
+        self.per_class = {}
+        for v, c in enumerate(istep.cams):
+            key = (c.width, c.height, c.tile_w, c.tile_h)
+            if key not in self.per_class:
+                self.per_class[key] = gs.InfoGain(istep.gm.n, [c], pair_capacity=1 << 24)
+        self.keys = [(c.width, c.height, c.tile_w, c.tile_h) for c in istep.cams]
+        self.out = torch.zeros(len(istep.cams), dtype=torch.float32, device="cuda")
+        self()
+        torch.cuda.synchronize()
+        for ig in self.per_class.values():
+            while ig.grow_if_needed():
+                self()
+                torch.cuda.synchronize()
+
+    def __call__(self):
+        for v, key in enumerate(self.keys):
+            ig = self.per_class[key]
+            ig.cams_dev.view(1, -1).copy_(self.cams_all[v:v + 1], non_blocking=True)
+            ig(self.istep.gm, out=self.out[v:v + 1])
+        return self.out
+
+
 # ----------------------------------------------------------------------------- timing loops
 def timed_loop(torch, steps, parts, flush):
     """Per part: list of per-step device milliseconds (events on the current stream)."""
@@ -452,15 +501,36 @@ def run_ours(args):
     t_comp = istep.composite_ms(max(3, args.steps), flush) / 1e3
     ig_contrib, ig_walked = istep.contributing()
     achieved = 16.0 * ig_contrib / t_comp / 1e12
+    tiles_now = {"%dx%d" % k: "%dx%d" % v for k, v in istep.tile_choice.items()}
+    traffic = (IG_TRAFFIC["bytes"] if IG_TRAFFIC["sources_sha1"] == ig_sources_sha1() and
+               tiles_now == IG_TRAFFIC["tiles"] else None)
     roofline = {"bound": "alu", "kernel": "k_ig_items (gs_info_gain_composite)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-                "launch_ms": t_comp * 1e3, "contributing_evals": ig_contrib}
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                "launch_ms": t_comp * 1e3, "contributing_evals": ig_contrib,
+                "traffic_note": "bytes per launch from ncu at full size with tiles %s; null when the tiles or the "
+                                "kernel sources differ" % IG_TRAFFIC["tiles"],
+                "dram_gbs_at_traffic": (traffic / t_comp / 1e9 if traffic else None)}
     # the mapping step's backward kernel, for reference: 10 per evaluated + 38 per contributing evaluation
     t_bwd = stage_ms.get("gs_render_bwd", float("nan")) / 1e3
     bwd_ach = (10.0 * ws["evaluated"] + 38.0 * ws["contributing"]) / t_bwd / 1e12
     rooflines = [roofline, {"bound": "alu", "kernel": "gs_render_bwd (k_render_bwd + k_proj_adjoint)",
                             "achieved": bwd_ach, "peak": peak, "unit": "TFLOP/s", "frac": bwd_ach / peak,
                             "launch_ms": t_bwd * 1e3}]
+
+    # the batched pass against the same candidates one view per call, at identical outputs
+    unbatched = None
+    if not args.no_unbatched:
+        unb = Unbatched(gs, istep)
+        ref = istep().clone()
+        got = unb().clone()
+        torch.cuda.synchronize()
+        t_unb = statistics.mean(timed_loop(torch, 3, [("u", unb)], flush)["u"]) / 1e3
+        unbatched = {"value": istep.n_views / t_unb, "unit": "views/s", "ms": t_unb * 1e3,
+                     "batch_speedup": value * t_unb / istep.n_views,
+                     "identical_outputs": bool(torch.equal(ref, got)),
+                     "max_abs_diff": float((ref - got).abs().max().item())}
+        del unb
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -478,6 +548,7 @@ def run_ours(args):
                        "ig_tiles": {"%dx%d" % k: "%dx%d" % v for k, v in istep.tile_choice.items()}},
             "fwd_bwd": {"value": fwd_bwd, "unit": "iters/s", "ms": t_map_all / args.steps * 1e3},
             "ig_ms": t_ig_all / args.steps * 1e3,
+            "ig_unbatched": unbatched,
             "stages_ms": stage_ms,
             "work": ws,
             "e2e": e2e,

@@ -403,6 +403,26 @@ def test_info_gain_batch_vs_oracle_and_single_view():
         assert one[0] == np.float32(ig[v]), (v, one[0], ig[v])
 
 
+def test_info_gain_composite_entry_matches_batch():
+    """gs_info_gain_composite on records from gs_project + gs_bin_sort (scoring-only records, no
+    pair tile ids): the same scalars, bit for bit, as gs_info_gain_batch, and within tolerance of
+    the oracle."""
+    gmap, cams = _ig_scene()
+    cams = [c.with_tile(8, 8) if c.width <= 80 else c for c in cams]
+    gm = gs.GaussianMapTensors.from_numpy(gmap)
+    batch = gs.InfoGain(gm.n, cams)(gm).cpu().numpy()
+    fr = gs.Frame(gm.n, cams, with_color=False, with_pair_tiles=False)
+    fr.project(gm)
+    fr.bin_sort()
+    comp = fr.info_gain().cpu().numpy()
+    fr.check_status()
+    np.testing.assert_array_equal(comp, batch)
+    ref, imgs = O.info_gain(gmap, cams)
+    for v in range(len(cams)):
+        tol = IG_RTOL * abs(ref[v]) + 1e-7 + imgs[v]["knife"].mean() * 4e-3
+        assert abs(float(comp[v]) - ref[v]) <= tol, (v, comp[v], ref[v])
+
+
 def test_info_gain_per_view_tiles_vs_oracle():
     gmap, cams = _ig_scene()
     cams = [c.with_tile(8, 8) if c.width <= 80 else (c.with_tile(16, 8) if c.width <= 160 else c) for c in cams]
