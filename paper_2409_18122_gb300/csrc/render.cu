@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
                                                                 gs_params p, gs_image img, uint32_t n_items) {
   __shared__ float4 s_stage[kFwdWarps][3][32];   // (mu_x, mu_y, u, -), (a, b, c, o), (r, g, b, depth)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
   const uint32_t item = blockIdx.x * kFwdWarps + warp;
   if (item >= n_items) return;
   TileInfo ti;
@@ -89,50 +90,51 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
     if (g + 64 + lane < n) mC = __ldg(SP + 2 * (size_t)rC);
     uint32_t rD = 0;
     if (g + 96 + lane < n) rD = __ldg(rl + g + 96 + lane);
-    uint32_t m = __ballot_sync(0xffffffffu, ovA);
+    const uint32_t m = __ballot_sync(0xffffffffu, ovA);
     if (m) {
+      // the overlapping entries, compacted in list order: (mu, u, o), (scaled conic,
+      // position in the group), colour
+      const int n_ov = __popc(m);
       if (ovA) {
-        sm[lane] = make_float4(mA.x, mA.y, mA.w, 0.f);
-        sc[lane] = cA;
-        sk[lane] = kA;
+        const int s = __popc(m & lt);
+        const float3 k2 = scaled_conic(cA);
+        sm[s] = make_float4(mA.x, mA.y, mA.w, cA.w);
+        sc[s] = make_float4(k2.x, k2.y, k2.z, __int_as_float(lane));
+        sk[s] = kA;
       }
       __syncwarp();
-      // up to kBatch overlapping entries at a time: their alphas are independent
-      // and computed together; the transmittance updates then run in list order
-      while (m && !all_done<kPix>(done)) {
-        int bb[kBatch];
-        int nb = 0;
-#pragma unroll
-        for (int k = 0; k < kBatch; ++k) {
-          bb[k] = m ? __ffs(m) - 1 : 0;
-          if (m) { m &= m - 1; nb = k + 1; }
-        }
+      // kBatch entries at a time: their alphas are independent and computed
+      // together; the transmittance updates then run in list order
+      for (int i0 = 0; i0 < n_ov && !all_done<kPix>(done); i0 += kBatch) {
         float al[kBatch][kPix];
 #pragma unroll
         for (int k = 0; k < kBatch; ++k) {
-          const float4 mu = sm[bb[k]];
-          const float4 co = sc[bb[k]];
+          const int i = i0 + k < n_ov ? i0 + k : n_ov - 1;
+          const float4 mu = sm[i];
+          const float4 kk = sc[i];
 #pragma unroll
-          for (int q = 0; q < kPix; ++q) al[k][q] = k < nb ? splat_alpha(mu.x, mu.y, co, pxc, pyc[q], p.alpha_max) : 0.f;
+          for (int q = 0; q < kPix; ++q)
+            al[k][q] = splat_alpha2(mu.x, mu.y, make_float3(kk.x, kk.y, kk.z), mu.w, pxc, pyc[q], p.alpha_max);
         }
 #pragma unroll
         for (int k = 0; k < kBatch; ++k) {
+          const int i = i0 + k;
 #pragma unroll
           for (int q = 0; q < kPix; ++q) {
-            if (k >= nb || done[q]) continue;
+            if (i >= n_ov || done[q]) continue;
             const float alpha = al[k][q];
             if (alpha < p.alpha_min) continue;
             const float Tn = T[q] * (1.f - alpha);
             if (Tn < p.T_min) { done[q] = true; continue; }
             const float w = alpha * T[q];
-            const float4 c = sk[bb[k]];
+            const float4 c = sk[i];
             cr[q] += w * c.x;
             cg[q] += w * c.y;
             cb[q] += w * c.z;
             cd[q] += w * c.w;
-            cu[q] += w * sm[bb[k]].z;
+            cu[q] += w * sm[i].z;
             T[q] = Tn;
-            last[q] = (int32_t)(g + bb[k] + 1);
+            last[q] = (int32_t)(g + __float_as_int(sc[i].w) + 1);
             ++n_contrib[q];
           }
         }
@@ -174,6 +176,7 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
                                                              uint32_t* __restrict__ work) {
   __shared__ float4 s_stage[kIgWarps][2][32];   // (mu_x, mu_y, u, -), (a, b, c, o)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
   float4* sm = s_stage[warp][0];
   float4* sc = s_stage[warp][1];
   uint32_t n_items = proj.view_info[kVI * n_views + 2] / kPix;
@@ -225,37 +228,36 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
       if (g + 64 + lane < n) mC = __ldg(SP + 2 * (size_t)rC);
       uint32_t rD = 0;
       if (g + 96 + lane < n) rD = __ldg(rl + g + 96 + lane);
-      uint32_t m = __ballot_sync(0xffffffffu, ovA);
+      const uint32_t m = __ballot_sync(0xffffffffu, ovA);
       if (m) {
+        // the overlapping entries, compacted in list order: (mu, u, o), scaled conic
+        const int n_ov = __popc(m);
         if (ovA) {
-          sm[lane] = make_float4(mA.x, mA.y, mA.w, 0.f);
-          sc[lane] = cA;
+          const int s = __popc(m & lt);
+          const float3 k2 = scaled_conic(cA);
+          sm[s] = make_float4(mA.x, mA.y, mA.w, cA.w);
+          sc[s] = make_float4(k2.x, k2.y, k2.z, 0.f);
         }
         __syncwarp();
-        // up to kBatch overlapping entries at a time: their alphas are independent
-        // and computed together; the transmittance updates then run in list order
-        while (m && !all_done<kPix>(done)) {
-          int bb[kBatch];
-          int nb = 0;
-#pragma unroll
-          for (int k = 0; k < kBatch; ++k) {
-            bb[k] = m ? __ffs(m) - 1 : 0;
-            if (m) { m &= m - 1; nb = k + 1; }
-          }
+        // kBatch entries at a time: their alphas are independent and computed
+        // together; the transmittance updates then run in list order
+        for (int i0 = 0; i0 < n_ov && !all_done<kPix>(done); i0 += kBatch) {
           float al[kBatch][kPix], uu[kBatch];
 #pragma unroll
           for (int k = 0; k < kBatch; ++k) {
-            const float4 mu = sm[bb[k]];
-            const float4 co = sc[bb[k]];
+            const int i = i0 + k < n_ov ? i0 + k : n_ov - 1;
+            const float4 mu = sm[i];
+            const float4 kk = sc[i];
             uu[k] = mu.z;
 #pragma unroll
-            for (int q = 0; q < kPix; ++q) al[k][q] = k < nb ? splat_alpha(mu.x, mu.y, co, pxc, pyc[q], p.alpha_max) : 0.f;
+            for (int q = 0; q < kPix; ++q)
+              al[k][q] = splat_alpha2(mu.x, mu.y, make_float3(kk.x, kk.y, kk.z), mu.w, pxc, pyc[q], p.alpha_max);
           }
 #pragma unroll
           for (int k = 0; k < kBatch; ++k) {
 #pragma unroll
             for (int q = 0; q < kPix; ++q) {
-              if (k >= nb || done[q]) continue;
+              if (i0 + k >= n_ov || done[q]) continue;
               const float alpha = al[k][q];
               if (alpha < p.alpha_min) continue;
               const float Tn = T[q] * (1.f - alpha);

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
           contrib[q] = inside[q] && pos < last[q];
           al[q] = G[q] = dx[q] = dy[q] = 0.f;
           if (contrib[q]) {
-            al[q] = splat_alpha_dxy(mu.x, mu.y, k, pxc, pyc[q], p.alpha_max, dx[q], dy[q], G[q]);
+            al[q] = splat_alpha2(mu.x, mu.y, scaled_conic(k), k.w, pxc, pyc[q], p.alpha_max, dx[q], dy[q], G[q]);
             if (al[q] < p.alpha_min) contrib[q] = false;
           }
         }

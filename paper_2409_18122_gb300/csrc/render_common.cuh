@@ -19,26 +19,40 @@ struct TileInfo {
 };
 
 // alpha = min(alpha_max, o exp(-q/2)), q = a dx^2 + 2 b dx dy + c dy^2 with
-// (dx, dy) = mu_2D - pixel centre and co = (a, b, c, o).  Written with explicit
-// round-to-nearest intrinsics so that the forward, backward and
+// (dx, dy) = mu_2D - pixel centre and conic (a, b, c).  exp(-q/2) is evaluated
+// as 2^p with p = -q/2 log2(e): the conic is scaled once per Gaussian (per warp
+// staging, not per pixel) to k = (-a/2, -b, -c/2) log2(e), so that
+// p = (k.x dx + k.y dy) dx + k.z dy^2 and G = 2^p is one ex2 instruction.  Written
+// with explicit round-to-nearest intrinsics so that the forward, backward and
 // information-gain kernels compute bit-identical alphas (and so take identical
-// skip and stop decisions) whatever the compiler contracts.  Also returns
-// (dx, dy) and G = exp(-q/2).
-__device__ __forceinline__ float splat_alpha_dxy(float mx, float my, const float4& co, float pxc, float pyc,
-                                                 float alpha_max, float& dx, float& dy, float& G) {
-  dx = __fsub_rn(mx, pxc);
-  dy = __fsub_rn(my, pyc);
-  float q = __fmul_rn(__fmul_rn(co.z, dy), dy);
-  q = __fmaf_rn(__fmul_rn(co.x, dx), dx, q);
-  q = __fmaf_rn(__fmul_rn(__fadd_rn(co.y, co.y), dx), dy, q);
-  G = __expf(__fmul_rn(-0.5f, q));
-  return fminf(alpha_max, __fmul_rn(co.w, G));
+// skip and stop decisions) whatever the compiler contracts.
+constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ __forceinline__ float3 scaled_conic(const float4& co) {
+  return make_float3(__fmul_rn(co.x, -0.5f * kLog2e), __fmul_rn(co.y, -kLog2e), __fmul_rn(co.z, -0.5f * kLog2e));
 }
 
-__device__ __forceinline__ float splat_alpha(float mx, float my, const float4& co, float pxc, float pyc,
-                                             float alpha_max) {
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Also returns (dx, dy) and G = exp(-q/2).
+__device__ __forceinline__ float splat_alpha2(float mx, float my, const float3& k, float o, float pxc, float pyc,
+                                              float alpha_max, float& dx, float& dy, float& G) {
+  dx = __fsub_rn(mx, pxc);
+  dy = __fsub_rn(my, pyc);
+  const float t = __fmaf_rn(k.x, dx, __fmul_rn(k.y, dy));
+  const float pw = __fmaf_rn(t, dx, __fmul_rn(__fmul_rn(k.z, dy), dy));
+  G = ex2_approx(pw);
+  return fminf(alpha_max, __fmul_rn(o, G));
+}
+
+__device__ __forceinline__ float splat_alpha2(float mx, float my, const float3& k, float o, float pxc, float pyc,
+                                              float alpha_max) {
   float dx, dy, G;
-  return splat_alpha_dxy(mx, my, co, pxc, pyc, alpha_max, dx, dy, G);
+  return splat_alpha2(mx, my, k, o, pxc, pyc, alpha_max, dx, dy, G);
 }
 
 // Work item of the compositing kernels: one warp renders one 8 x (4 KP) pixel
