@@ -21,7 +21,8 @@ namespace {
 constexpr int kFwdWarps = 2;   // warps (work items) per CTA: small CTAs free their slot as soon as both finish
 constexpr int kIgWarps = 8;    // warps per CTA of the persistent information-gain kernel
 constexpr int kPix = 1;        // pixels per lane of the forward and information-gain kernels
-constexpr int kBatch = 4;      // overlapping entries whose alphas are computed together
+constexpr int kFwdBatch = 4;   // overlapping entries whose alphas are computed together (forward)
+constexpr int kIgBatch = 8;    // ... and in the information-gain kernel
 
 // The list walk of all compositing kernels is a four-stage software pipeline
 // over groups of 32 entries (one per lane).  While group g is composited, the
@@ -103,12 +104,12 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
         sk[s] = kA;
       }
       __syncwarp();
-      // kBatch entries at a time: their alphas are independent and computed
+      // kFwdBatch entries at a time: their alphas are independent and computed
       // together; the transmittance updates then run in list order
-      for (int i0 = 0; i0 < n_ov && !all_done<kPix>(done); i0 += kBatch) {
-        float al[kBatch][kPix];
+      for (int i0 = 0; i0 < n_ov && !all_done<kPix>(done); i0 += kFwdBatch) {
+        float al[kFwdBatch][kPix];
 #pragma unroll
-        for (int k = 0; k < kBatch; ++k) {
+        for (int k = 0; k < kFwdBatch; ++k) {
           const int i = i0 + k < n_ov ? i0 + k : n_ov - 1;
           const float4 mu = sm[i];
           const float4 kk = sc[i];
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
             al[k][q] = splat_alpha2(mu.x, mu.y, make_float3(kk.x, kk.y, kk.z), mu.w, pxc, pyc[q], p.alpha_max);
         }
 #pragma unroll
-        for (int k = 0; k < kBatch; ++k) {
+        for (int k = 0; k < kFwdBatch; ++k) {
           const int i = i0 + k;
 #pragma unroll
           for (int q = 0; q < kPix; ++q) {
@@ -239,12 +240,12 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
           sc[s] = make_float4(k2.x, k2.y, k2.z, 0.f);
         }
         __syncwarp();
-        // kBatch entries at a time: their alphas are independent and computed
+        // kIgBatch entries at a time: their alphas are independent and computed
         // together; the transmittance updates then run in list order
-        for (int i0 = 0; i0 < n_ov && !all_done<kPix>(done); i0 += kBatch) {
-          float al[kBatch][kPix], uu[kBatch];
+        for (int i0 = 0; i0 < n_ov && !all_done<kPix>(done); i0 += kIgBatch) {
+          float al[kIgBatch][kPix], uu[kIgBatch];
 #pragma unroll
-          for (int k = 0; k < kBatch; ++k) {
+          for (int k = 0; k < kIgBatch; ++k) {
             const int i = i0 + k < n_ov ? i0 + k : n_ov - 1;
             const float4 mu = sm[i];
             const float4 kk = sc[i];
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
               al[k][q] = splat_alpha2(mu.x, mu.y, make_float3(kk.x, kk.y, kk.z), mu.w, pxc, pyc[q], p.alpha_max);
           }
 #pragma unroll
-          for (int k = 0; k < kBatch; ++k) {
+          for (int k = 0; k < kIgBatch; ++k) {
 #pragma unroll
             for (int q = 0; q < kPix; ++q) {
               if (i0 + k >= n_ov || done[q]) continue;

@@ -18,10 +18,23 @@
 namespace gs {
 namespace {
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Warp reduce-scatter of 16 values: on return, lanes 2j and 2j+1 hold the sum over
+// the warp of v[j].  Each halving step keeps half of the values and adds the
+// partner lane's copy of the same half: 8 + 4 + 2 + 1 + 1 = 16 shuffles for all
+// sixteen sums (a separate butterfly per value would take 80).
+__device__ __forceinline__ float warp_sum16(float (&v)[16]) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-  return v;
+  for (int n = 8, d = 16; n >= 1; n >>= 1, d >>= 1) {
+    const bool hi = (lane & d) != 0;   // this lane keeps the upper half of its n pairs
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      const float keep = hi ? v[i + n] : v[i];
+      const float send = hi ? v[i] : v[i + n];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, d);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 constexpr int kBwdWarps = 2;   // warps (work items) per CTA
@@ -141,9 +154,9 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
 #pragma unroll
         for (int q = 0; q < kPix; ++q) any_c = any_c || contrib[q];
         if (!__any_sync(0xffffffffu, any_c)) continue;
-        float v[10];
+        float v[16];
 #pragma unroll
-        for (int i = 0; i < 10; ++i) v[i] = 0.f;
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
         const float4 c = sr[b];
 #pragma unroll
         for (int q = 0; q < kPix; ++q) {
@@ -173,12 +186,12 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
           }
         }
 #pragma unroll
-        for (int i = 0; i < 10; ++i) v[i] = warp_sum(v[i]);
-        if (lane == 0) {
-          float4* dst = g2d + 3 * (size_t)srec[b];
-          atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
-          atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], 0.f));
-          atomicAdd(dst + 2, make_float4(v[7], v[8], v[9], 0.f));
+        const float tot = warp_sum16(v);   // sum of v[lane / 2]
+        const int j = lane >> 1;
+        if ((lane & 1) == 0 && j < 10) {
+          // per-record gradient slots: (v0, v1, v2, v3), (v4, v5, v6, -), (v7, v8, v9, -)
+          float* dst = reinterpret_cast<float*>(g2d + 3 * (size_t)srec[b]);
+          atomicAdd(dst + (j < 7 ? j : j + 1), tot);
         }
       }
       __syncwarp();
