@@ -43,10 +43,11 @@ inline unsigned grid_for(int64_t n_cap) {
   return (unsigned)b;
 }
 
-// Chunks per view: about kChunkTarget warps in total, at most 2^28 count entries.
+// Chunks per view: about kChunkTarget warps in total, at most 2^22 count entries
+// (the per-(tile, chunk) table is written, scanned and read once per call).
 int chunks_per_view(int n_views, int64_t tile_cap) {
   int64_t k = (kChunkTarget + n_views - 1) / n_views;
-  const int64_t max_entries = (int64_t)1 << 28;
+  const int64_t max_entries = (int64_t)1 << 22;
   if (tile_cap > 0 && k * tile_cap > max_entries) k = max_entries / tile_cap;
   if (k < 1) k = 1;
   return (int)k;
@@ -271,11 +272,11 @@ __device__ __forceinline__ uint32_t div_small(uint32_t j, uint32_t w) {
 
 // Step 6: every pair written to its slot.  A warp takes its chunk's records 32
 // at a time (a group); their pairs inside the current window are enumerated 32
-// at a time (record order, each rectangle row-major), one pair per lane.  The
-// pair of group record o at window cell i sets bit o of msk[i], so its rank
-// among the group's records covering the cell is the number of lower bits set
-// (pairs of lower records come in the same or an earlier round).  After the
-// group, every cell's running slot advances by its count of bits.
+// at a time (a round; record order, each rectangle row-major), one pair per lane.
+// The lanes of a round holding pairs of the same window cell belong to different
+// records, in lane order: each sets its lane bit in msk[cell], takes the running
+// slot plus the number of lower bits, and the lowest of them advances the running
+// slot and clears the mask for the next round.
 template <bool kTileIds>
 __global__ void __launch_bounds__(kBinWarps * 32) k_bin_place(const gs_proj proj, const uint32_t* __restrict__ seg,
                                                               const uint32_t* __restrict__ srec,
@@ -286,6 +287,7 @@ __global__ void __launch_bounds__(kBinWarps * 32) k_bin_place(const gs_proj proj
   __shared__ uint32_t s_run[kBinWarps][kPlaceWin];
   __shared__ uint32_t s_msk[kBinWarps][kPlaceWin];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lanebit = 1u << lane, lt = lanebit - 1u;
   const int64_t cid = (int64_t)blockIdx.x * kBinWarps + warp;
   if (cid >= (int64_t)n_views * K) return;
   Chunk c;
@@ -352,26 +354,25 @@ __global__ void __launch_bounds__(kBinWarps * 32) k_bin_place(const gs_proj proj
             cy = o_y0 + y;
             cx = o_x0 + (j - y * o_w);
             i = cy * cols + cx;
-            atomicOr(&msk[i], 1u << o);
+            atomicOr(&msk[i], lanebit);
           }
           __syncwarp();
+          uint32_t mm = 0;
           if (valid) {
-            const uint32_t slot = run[i] + __popc(msk[i] & ((1u << o) - 1u));
+            mm = msk[i];
+            const uint32_t slot = run[i] + __popc(mm & lt);
             if (slot < cap) {
               out.rec[slot] = o_rec;
               if (kTileIds) out.tile[slot] = c.tile_base + (ya + cy) * c.tiles_x + xa + cx;
             }
           }
-        }
-        __syncwarp();
-        for (uint32_t i = lane; i < cells; i += 32) {
-          const uint32_t m = msk[i];
-          if (m) {
-            run[i] += __popc(m);
+          __syncwarp();
+          if (valid && (mm & lt) == 0u) {   // lowest lane of the cell in this round
+            run[i] += __popc(mm);
             msk[i] = 0u;
           }
+          __syncwarp();
         }
-        __syncwarp();
       }
     }
   }

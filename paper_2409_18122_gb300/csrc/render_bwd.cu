@@ -185,7 +185,6 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
             v[4] += dq * dy[q] * dy[q];                      // dL/dc
           }
         }
-#pragma unroll
         const float tot = warp_sum16(v);   // sum of v[lane / 2]
         const int j = lane >> 1;
         if ((lane & 1) == 0 && j < 10) {

@@ -408,7 +408,7 @@ class InfoGain:
 
 
 # ---------------------------------------------------------------------- tile autotuner
-TILE_CANDIDATES = ((16, 16), (16, 8), (8, 8), (32, 8))
+TILE_CANDIDATES = ((16, 16), (16, 8), (8, 8), (32, 8), (32, 16), (32, 32))
 
 
 def autotune_tiles(gmap: GaussianMapTensors, cams: Sequence, params: RenderParams = RenderParams(),
