@@ -8,9 +8,10 @@
 //   2. stable LSD radix sort of the record indices by the IEEE bits of their
 //      depth, segmented by view (every view's records are sorted in place):
 //      (view, depth, record) order;
-//   3. the rectangles in that order, each record's pair count, and an exclusive
-//      scan of the counts: the pairs of the sorted records, in order, are
-//      numbered 0 .. P-1 (records in order, the tiles of a rectangle row-major);
+//   3. the rectangles in that order and each record's pair count (written by the
+//      last sort pass), and an exclusive scan of the counts: the pairs of the
+//      sorted records, in order, are numbered 0 .. P-1 (records in order, the
+//      tiles of a rectangle row-major);
 //   4. the pairs of each view are cut into K equal chunks; one warp per chunk
 //      counts its pairs per tile of the view (shared-memory histogram);
 //   5. one exclusive scan over the counts laid out [global tile][chunk] gives,
@@ -131,35 +132,6 @@ __device__ inline bool chunk_of(int64_t cid, int K, const uint32_t* __restrict__
   c.tiles_y = c.tiles_x ? c.n_tiles / c.tiles_x : 0u;
   // a view whose tiles do not all fit under tile_cap is skipped (GS_FLAG_RANGE_OVERFLOW is set elsewhere)
   return c.n_tiles > 0 && (int64_t)c.tile_base + c.n_tiles <= tile_cap;
-}
-
-// Step 3a: rectangles in sorted order and their pair counts.  A rectangle
-// outside its view's tile grid counts 0 pairs and sets GS_FLAG_BAD_RECORDS.
-__global__ void k_sorted_rects(const gs_proj proj, const uint32_t* __restrict__ seg, int n_views,
-                               const uint32_t* __restrict__ srec, ushort4* __restrict__ srect,
-                               uint32_t* __restrict__ cnt) {
-  const int64_t n = clamp_count(proj.count, proj.capacity);
-  const ushort4* rect = reinterpret_cast<const ushort4*>(proj.rect);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    ushort4 rc = rect[srec[i]];
-    int lo = 0, hi = n_views - 1;   // view of sorted position i: the largest v with seg[v] <= i
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if ((int64_t)__ldg(seg + mid) <= i) lo = mid;
-      else hi = mid - 1;
-    }
-    const uint32_t tx = proj.view_info[kVI * lo + 3] >> 16;
-    const uint32_t nt = proj.view_info[kVI * (lo + 1)] - proj.view_info[kVI * lo];
-    const uint32_t ty = tx ? nt / tx : 0u;
-    uint32_t c = 0;
-    if (rc.x < rc.z && rc.y < rc.w) {
-      if (rc.z <= tx && rc.w <= ty) c = (uint32_t)(rc.z - rc.x) * (uint32_t)(rc.w - rc.y);
-      else set_flag(proj.status, GS_FLAG_BAD_RECORDS);
-    }
-    if (c == 0) rc = make_ushort4(0, 0, 0, 0);   // no pairs: an empty rectangle downstream
-    srect[i] = rc;
-    cnt[i] = c;
-  }
 }
 
 // The tile grid of a view is handled in windows [xa, xb) x [ya, yb) of at most
@@ -431,14 +403,14 @@ cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_vi
   k_segments<<<grid_for(rec_cap), kBlock, 0, st>>>(proj, n_views, tile_cap, K, seg, &ctr[0]);
   note_launch();
   // 2. record indices by depth bits within each view (4 passes: result back in the a buffers)
+  // (the last pass also writes the rectangles in sorted order and their pair counts)
   bool in_a = false;
+  const SortRectEpilogue epi{reinterpret_cast<const ushort4*>(proj.rect), proj.view_info, srect, rcnt, proj.status};
   cudaError_t e = radix_sort(proj.depth_key, nullptr, SortBufs{rk_a, rv_a, rk_b, rv_b}, proj.count, rec_cap, 0, 32,
-                             tmp, st, &in_a, seg, n_views);
+                             tmp, st, &in_a, seg, n_views, &epi);
   if (e != cudaSuccess) return e;
   const uint32_t* srec = in_a ? rv_a : rv_b;
-  // 3. sorted rectangles, pair counts, pair numbering
-  k_sorted_rects<<<grid_for(rec_cap), kBlock, 0, st>>>(proj, seg, n_views, srec, srect, rcnt);
-  note_launch();
+  // 3. pair numbering
   e = scan_exclusive(rcnt, poff, proj.count, rec_cap, nullptr, tmp, st);
   if (e != cudaSuccess) return e;
   // 4. per-chunk tile counts

@@ -57,10 +57,23 @@ struct SortBufs {
   uint32_t* vals_b;
 };
 size_t sort_temp_bytes(int64_t n_cap, int n_seg = 0);
+// Optional work of the last pass of a sort whose segments are the views of a
+// binning batch and whose values are record indices: for the element r written
+// to position i, out_rect[i] = rect[r] and out_cnt[i] = its number of tiles (0,
+// with an empty out_rect[i], for an empty rectangle or one outside its view's
+// tile grid -- the latter also sets GS_FLAG_BAD_RECORDS).  The sorted keys are
+// then not written.
+struct SortRectEpilogue {
+  const ushort4* rect;
+  const uint32_t* view_info;
+  ushort4* out_rect;
+  uint32_t* out_cnt;
+  uint32_t* status;
+};
 int sort_passes(int bit_begin, int bit_end);
 cudaError_t radix_sort(const uint32_t* keys_in, const uint32_t* vals_in, SortBufs bufs, const uint32_t* n_dev,
                        int64_t n_cap, int bit_begin, int bit_end, void* temp, cudaStream_t st, bool* result_in_a,
-                       const uint32_t* seg = nullptr, int n_seg = 0);
+                       const uint32_t* seg = nullptr, int n_seg = 0, const SortRectEpilogue* epi = nullptr);
 
 // ------------------------------------------------------------------ pipeline stages
 size_t project_ws_bytes(int64_t n, int n_views);

@@ -88,11 +88,12 @@ __global__ void __launch_bounds__(1024) k_part_map(const uint32_t* __restrict__ 
 }
 
 // Element range of this block's partition (segmented mode): empty past the last.
-__device__ inline void seg_part_range(const uint32_t* __restrict__ seg, int n_seg, const uint32_t* __restrict__ pmap,
-                                      int64_t& beg, int64_t& end) {
+// Returns the partition's segment.
+__device__ inline int seg_part_range(const uint32_t* __restrict__ seg, int n_seg, const uint32_t* __restrict__ pmap,
+                                     int64_t& beg, int64_t& end) {
   const int64_t p = blockIdx.x;
   beg = end = 0;
-  if (p >= (int64_t)pmap[1 + n_seg]) return;
+  if (p >= (int64_t)pmap[1 + n_seg]) return 0;
   int lo = 0, hi = n_seg - 1;   // segment: the largest s with first partition <= p
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -105,6 +106,7 @@ __device__ inline void seg_part_range(const uint32_t* __restrict__ seg, int n_se
   end = beg + size;
   if (end > b) end = b;
   if (beg > end) beg = end;
+  return lo;
 }
 
 // (1) digit counts of each partition: hist[part][digit]
@@ -240,7 +242,9 @@ __global__ void __launch_bounds__(kRadix) k_scan_hist_seg(uint32_t* __restrict__
   }
 }
 
-// (3) stable scatter of each partition's tiles
+// (3) stable scatter of each partition's tiles (kEpi: the last pass of a binning
+// sort, see SortRectEpilogue)
+template <bool kEpi>
 __global__ void __launch_bounds__(kBlock) k_downsweep(const uint32_t* __restrict__ keys_in,
                                                        const uint32_t* __restrict__ vals_in,
                                                        const uint32_t* __restrict__ seg, int n_seg,
@@ -248,7 +252,8 @@ __global__ void __launch_bounds__(kBlock) k_downsweep(const uint32_t* __restrict
                                                        uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                                                        const uint32_t* n_dev, int64_t n_cap, int shift,
                                                        const uint32_t* __restrict__ hist,
-                                                       const uint32_t* __restrict__ digit_base) {
+                                                       const uint32_t* __restrict__ digit_base,
+                                                       const SortRectEpilogue epi) {
   extern __shared__ uint32_t smem[];
   uint32_t* s_keys = smem;                              // kTile
   uint32_t* s_vals = s_keys + kTile;                    // kTile
@@ -261,14 +266,21 @@ __global__ void __launch_bounds__(kBlock) k_downsweep(const uint32_t* __restrict
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   int64_t beg, end;
+  int segment = 0;
   if (pmap) {
     base[tid] = hist[(size_t)blockIdx.x * kRadix + tid];   // already absolute
-    seg_part_range(seg, n_seg, pmap, beg, end);
+    segment = seg_part_range(seg, n_seg, pmap, beg, end);
   } else {
     base[tid] = digit_base[tid] + hist[(size_t)blockIdx.x * kRadix + tid];
     part_range(count_of(n_dev, n_cap), beg, end);
   }
 
+  uint32_t tiles_x = 0, tiles_y = 0;   // epilogue: the tile grid of this partition's view
+  if (kEpi) {
+    tiles_x = epi.view_info[4 * segment + 3] >> 16;
+    const uint32_t nt = epi.view_info[4 * (segment + 1)] - epi.view_info[4 * segment];
+    tiles_y = tiles_x ? nt / tiles_x : 0u;
+  }
   // the keys/values of the next tile are loaded while the current one is ranked and scattered
   uint32_t nkey[kItems], nval[kItems];
   auto load_tile = [&](int64_t t0) {
@@ -351,12 +363,28 @@ __global__ void __launch_bounds__(kBlock) k_downsweep(const uint32_t* __restrict
       }
     }
     __syncthreads();
-    for (int j = tid; j < tile_n; j += kBlock) {
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+      const int j = tid + it * kBlock;
+      if (j >= tile_n) break;
       const uint32_t k = s_keys[j];
       const uint32_t d = (k >> shift) & 0xffu;
       const uint32_t g = base[d] + (uint32_t)j - t_start[d];
-      keys_out[g] = k;
-      vals_out[g] = s_vals[j];
+      const uint32_t v = s_vals[j];
+      vals_out[g] = v;
+      if (!kEpi) {
+        keys_out[g] = k;
+      } else {
+        ushort4 rc = epi.rect[v];
+        uint32_t c = 0;
+        if (rc.x < rc.z && rc.y < rc.w) {
+          if (rc.z <= tiles_x && rc.w <= tiles_y) c = (uint32_t)(rc.z - rc.x) * (uint32_t)(rc.w - rc.y);
+          else atomicOr(epi.status, (uint32_t)GS_FLAG_BAD_RECORDS);
+        }
+        if (c == 0) rc = make_ushort4(0, 0, 0, 0);
+        epi.out_rect[g] = rc;
+        epi.out_cnt[g] = c;
+      }
     }
     __syncthreads();
     base[tid] += t_cnt[tid];
@@ -378,13 +406,17 @@ size_t sort_temp_bytes(int64_t n_cap, int n_seg) {
 
 cudaError_t radix_sort(const uint32_t* keys_in, const uint32_t* vals_in, SortBufs b, const uint32_t* n_dev,
                        int64_t n_cap, int bit_begin, int bit_end, void* temp, cudaStream_t st, bool* result_in_a,
-                       const uint32_t* seg, int n_seg) {
+                       const uint32_t* seg, int n_seg, const SortRectEpilogue* epi) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDownSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_downsweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kDownSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_downsweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDownSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  const SortRectEpilogue no_epi{nullptr, nullptr, nullptr, nullptr, nullptr};
   const bool segmented = seg && n_seg > 1;   // one segment sorts like the plain mode
   const int g = (int)(parts_for(n_cap) + (segmented ? n_seg : 0));
   Carver c(temp);
@@ -409,8 +441,12 @@ cudaError_t radix_sort(const uint32_t* keys_in, const uint32_t* vals_in, SortBuf
     if (segmented) k_scan_hist_seg<<<n_seg, kRadix, 0, st>>>(hist, g, seg, pmap);
     else k_scan_hist<<<1, 1024, 0, st>>>(hist, g, digit_base);
     note_launch();
-    k_downsweep<<<g, kBlock, kDownSmem, st>>>(kin, vin, seg, n_seg, pmap, kout, vout, n_dev, n_cap, shift, hist,
-                                              digit_base);
+    if (epi && p == passes - 1)
+      k_downsweep<true><<<g, kBlock, kDownSmem, st>>>(kin, vin, seg, n_seg, pmap, kout, vout, n_dev, n_cap, shift,
+                                                      hist, digit_base, *epi);
+    else
+      k_downsweep<false><<<g, kBlock, kDownSmem, st>>>(kin, vin, seg, n_seg, pmap, kout, vout, n_dev, n_cap, shift,
+                                                       hist, digit_base, no_epi);
     note_launch();
     kin = kout;
     vin = vout;
