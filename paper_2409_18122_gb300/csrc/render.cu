@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
   float4* sc = s_stage[warp][1];
   float4* sk = s_stage[warp][2];
   const float pxc = (float)wb.px + 0.5f;
+  const float ln_amin = __logf(p.alpha_min);
   float pyc[kPix];
   bool inside[kPix], done[kPix];
   float T[kPix], cr[kPix], cg[kPix], cb[kPix], cd[kPix], cu[kPix];
@@ -91,6 +92,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
     if (g + 64 + lane < n) mC = __ldg(SP + 2 * (size_t)rC);
     uint32_t rD = 0;
     if (g + 96 + lane < n) rD = __ldg(rl + g + 96 + lane);
+    ovA = ovA && ellipse_reaches(mA, cA, wb, ln_amin);
     const uint32_t m = __ballot_sync(0xffffffffu, ovA);
     if (m) {
       // the overlapping entries, compacted in list order: (mu, u, o), (scaled conic,
@@ -199,6 +201,7 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
     WarpBlock wb;
     warp_block<kPix>(ti, wb);
     const float pxc = (float)wb.px + 0.5f;
+    const float ln_amin = __logf(p.alpha_min);
     float pyc[kPix], T[kPix], cu[kPix];
     bool done[kPix];
 #pragma unroll
@@ -229,6 +232,7 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
       if (g + 64 + lane < n) mC = __ldg(SP + 2 * (size_t)rC);
       uint32_t rD = 0;
       if (g + 96 + lane < n) rD = __ldg(rl + g + 96 + lane);
+      ovA = ovA && ellipse_reaches(mA, cA, wb, ln_amin);
       const uint32_t m = __ballot_sync(0xffffffffu, ovA);
       if (m) {
         // the overlapping entries, compacted in list order: (mu, u, o), scaled conic

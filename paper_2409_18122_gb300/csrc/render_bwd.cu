@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
   float4* sr = s_stage[warp][2];
   uint32_t* srec = s_rec[warp];
   const float pxc = (float)wb.px + 0.5f;
+  const float ln_amin = __logf(p.alpha_min);
   const size_t P = (size_t)ti.W * ti.H;
   float pyc[kPix], T[kPix], gr[kPix], gg[kPix], gb[kPix], gd[kPix];
   float Sr[kPix], Sg[kPix], Sb[kPix], Sd[kPix];
@@ -124,6 +125,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
     if (g >= 64) mC = __ldg(SP + 2 * (size_t)rC);
     uint32_t rD = 0;
     if (g >= 96) rD = __ldg(rl + g - 96 + lane);
+    ovA = ovA && ellipse_reaches(mA, cA, wb, ln_amin);
     uint32_t m = __ballot_sync(0xffffffffu, ovA);
     if (m) {
       if (ovA) {

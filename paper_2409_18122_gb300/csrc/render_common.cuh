@@ -160,6 +160,24 @@ __device__ __forceinline__ bool box_overlaps(const float4& s0, const WarpBlock& 
   return (s0.x - rx <= wb.bx1) && (s0.x + rx >= wb.bx0) && (s0.y - ry <= wb.by1) && (s0.y + ry >= wb.by0);
 }
 
+// Second, tighter cull for entries that passed box_overlaps (co = second half of the
+// splat record: a, b, c, o).  The support ellipse is q <= Q = 2 ln(o / alpha_min);
+// for any pixel centre p of the block, sqrt(q(p - mu)) >= sqrt(q(c - mu)) - r with c
+// the block centre and r = max over the block's corner offsets e of sqrt(q(e)) =
+// sqrt(a hx^2 + 2 |b| hx hy + c hy^2) (triangle inequality in the norm sqrt(q)).  So a
+// Gaussian with sqrt(q(c - mu)) > sqrt(Q) + r reaches no pixel of the block.  The
+// margin keeps the test conservative under FP32 rounding.  ln_amin = ln(alpha_min).
+__device__ __forceinline__ bool ellipse_reaches(const float4& s0, const float4& co, const WarpBlock& wb,
+                                                float ln_amin) {
+  const float hx = 0.5f * (wb.bx1 - wb.bx0), hy = 0.5f * (wb.by1 - wb.by0);
+  const float dx = s0.x - (wb.bx0 + hx), dy = s0.y - (wb.by0 + hy);
+  const float q = co.x * dx * dx + 2.f * co.y * dx * dy + co.z * dy * dy;
+  const float r2 = co.x * hx * hx + 2.f * fabsf(co.y) * hx * hy + co.z * hy * hy;
+  const float Q = 2.f * (__logf(co.w) - ln_amin);
+  const float reach = sqrtf(fmaxf(Q, 0.f)) + sqrtf(fmaxf(r2, 0.f));
+  return sqrtf(fmaxf(q, 0.f)) <= reach * 1.0001f + 1e-3f;
+}
+
 // Fixed-tree block sum (deterministic for a fixed block size); result valid in thread 0.
 __device__ __forceinline__ float block_sum_fixed(float v, float* s_red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
