@@ -33,14 +33,18 @@ __host__ __device__ __forceinline__ bool valid_tile(int tw, int th) {
          (b == 64 || b == 128 || b == 256 || b == 512 || b == 1024);
 }
 
-// Per-view constants derived from a gs_camera, staged in shared memory.
-struct CamC {
-  float fx, fy, cx, cy;
+// Per-view constants derived from a gs_camera, staged in shared memory.  The
+// first 64 bytes (rotation, centre, guard slopes, focal lengths) are what the
+// cull of every (Gaussian, view) pair reads, as four 16-byte loads.
+struct __align__(16) CamC {
   float R[9];
   float T[3];
   float gx, gy;          // guard-band slopes guard * (W/2) / fx, guard * (H/2) / fy
+  float fx, fy;
+  float cx, cy;
   int W, H;
-  int tw, th;            // this view's tile size
+  int tw, th;            // this view's tile size (powers of two)
+  int sx, sy;            // log2 of tw, th
   int tiles_x, tiles_y;
   uint32_t tile_base;
   uint32_t pix_base;
@@ -201,20 +205,22 @@ struct ViewProj {
 // Returns true if the Gaussian is visible in the view and fills `vp`.
 __device__ __forceinline__ bool view_proj(float4 mo, const GaussPre& g, const CamC& c, float near_plane,
                                           float eps2d, ViewProj& vp) {
-  const int tile_w = c.tw, tile_h = c.th;
   if (!g.valid) return false;
-  const float* R = c.R;
-  float dx = fsub(mo.x, c.T[0]), dy = fsub(mo.y, c.T[1]), dz = fsub(mo.z, c.T[2]);
+  const float4* c4 = reinterpret_cast<const float4*>(&c);
+  const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2], q3 = c4[3];
+  const float R[9] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x};
+  float dx = fsub(mo.x, q2.y), dy = fsub(mo.y, q2.z), dz = fsub(mo.z, q2.w);
   float tx = ffma(R[6], dz, ffma(R[3], dy, fmul(R[0], dx)));
   float ty = ffma(R[7], dz, ffma(R[4], dy, fmul(R[1], dx)));
   float tz = ffma(R[8], dz, ffma(R[5], dy, fmul(R[2], dx)));
   if (!(tz > near_plane)) return false;
-  if (fabsf(tx) > fmul(c.gx, tz)) return false;
-  if (fabsf(ty) > fmul(c.gy, tz)) return false;
+  if (fabsf(tx) > fmul(q3.x, tz)) return false;
+  if (fabsf(ty) > fmul(q3.y, tz)) return false;
+  const float fx = q3.z, fy = q3.w;
   float iz = fdiv(1.0f, tz);
   float u = fmul(tx, iz), v = fmul(ty, iz);
-  float mux = ffma(c.fx, u, c.cx), muy = ffma(c.fy, v, c.cy);
-  float j00 = fmul(c.fx, iz), j11 = fmul(c.fy, iz);
+  float mux = ffma(fx, u, c.cx), muy = ffma(fy, v, c.cy);
+  float j00 = fmul(fx, iz), j11 = fmul(fy, iz);
   float j02 = -fmul(j00, u), j12 = -fmul(j11, v);
   float T0[3], T1[3];
 #pragma unroll
@@ -242,10 +248,11 @@ __device__ __forceinline__ bool view_proj(float4 mo, const GaussPre& g, const Ca
   xhi = fminf(xhi, (float)(c.W - 1));
   yhi = fminf(yhi, (float)(c.H - 1));
   if (!(xlo <= xhi) || !(ylo <= yhi)) return false;
-  vp.x0 = (int)xlo / tile_w;
-  vp.y0 = (int)ylo / tile_h;
-  vp.x1 = (int)xhi / tile_w + 1;
-  vp.y1 = (int)yhi / tile_h + 1;
+  // pixel -> tile: the coordinates are >= 0 and tile sizes are powers of two
+  vp.x0 = (int)xlo >> c.sx;
+  vp.y0 = (int)ylo >> c.sy;
+  vp.x1 = ((int)xhi >> c.sx) + 1;
+  vp.y1 = ((int)yhi >> c.sy) + 1;
   vp.mx = mux;
   vp.my = muy;
   vp.rx = rx;
@@ -271,6 +278,8 @@ __device__ __forceinline__ void load_cam(const gs_camera& g, float guard, int de
   view_tile(g, def_tw, def_th, tile_w, tile_h);
   c.tw = tile_w;
   c.th = tile_h;
+  c.sx = __ffs(tile_w) - 1;
+  c.sy = __ffs(tile_h) - 1;
   c.fx = g.fx; c.fy = g.fy; c.cx = g.cx; c.cy = g.cy;
 #pragma unroll
   for (int i = 0; i < 9; ++i) c.R[i] = g.R[i];
