@@ -157,13 +157,20 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank: float, seconds_per_rank: float, world: int) -> float:
+    """Whole-job rate of N replicas: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / max_over_ranks(seconds_per_rank, world)
 
 
 # ----------------------------------------------------------------------------- workloads
@@ -457,8 +464,8 @@ def run_ours(args):
     t_ig = sum(times.get("ig", [0.0])) / 1e3
     t_map_all = max_over_ranks(t_map, world)
     t_ig_all = max_over_ranks(t_ig, world)
-    value = istep.n_views * args.steps * world / t_ig_all if istep else None
-    fwd_bwd = args.steps * world / t_map_all if mstep else None
+    value = job_throughput(istep.n_views * args.steps, t_ig, world) if istep else None
+    fwd_bwd = job_throughput(args.steps, t_map, world) if mstep else None
     ms_per_step = (max_over_ranks(t_map + t_ig, world) / args.steps) * 1e3
 
     e2e = None
