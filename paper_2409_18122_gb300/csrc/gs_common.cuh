@@ -203,6 +203,18 @@ struct ViewProj {
 };
 
 // Returns true if the Gaussian is visible in the view and fills `vp`.
+// The first culls of view_proj (near plane, guard band), with the same operations:
+// view_proj can only accept a pair this accepts.
+__device__ __forceinline__ bool frustum_ok(float4 mo, const CamC& c, float near_plane) {
+  const float4* c4 = reinterpret_cast<const float4*>(&c);
+  const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2], q3 = c4[3];
+  const float dx = fsub(mo.x, q2.y), dy = fsub(mo.y, q2.z), dz = fsub(mo.z, q2.w);
+  const float tx = ffma(q1.z, dz, ffma(q0.w, dy, fmul(q0.x, dx)));
+  const float ty = ffma(q1.w, dz, ffma(q1.x, dy, fmul(q0.y, dx)));
+  const float tz = ffma(q2.x, dz, ffma(q1.y, dy, fmul(q0.z, dx)));
+  return tz > near_plane && !(fabsf(tx) > fmul(q3.x, tz)) && !(fabsf(ty) > fmul(q3.y, tz));
+}
+
 __device__ __forceinline__ bool view_proj(float4 mo, const GaussPre& g, const CamC& c, float near_plane,
                                           float eps2d, ViewProj& vp) {
   if (!g.valid) return false;

@@ -17,6 +17,7 @@ namespace gs {
 namespace {
 
 constexpr int kBlock = 256;
+constexpr int kWarps = kBlock / 32;
 
 __device__ __forceinline__ bool camera_ok(const gs_camera& c, int tw, int th) {
   return c.width > 0 && c.height > 0 && c.fx > 0.f && c.fy > 0.f && isfinite(c.fx) && isfinite(c.fy) &&
@@ -108,20 +109,28 @@ __device__ __forceinline__ void stage_cams(const gs_camera* __restrict__ cams, c
   }
 }
 
-// One warp = one group of 32 consecutive Gaussians.  Count pass: per view, the
-// ballot of visible lanes is stored (grp_mask, entry view * G + group) and its
-// popcount counted.  Write pass: the visible lanes of a (view, group) write their
-// records to consecutive slots grp_base + rank, so every store instruction of the
-// warp is contiguous.
+// One warp = one group of 32 consecutive Gaussians.  For every view the lanes
+// test their Gaussian cheaply (near plane, guard band: frustum_ok; in the write
+// pass, the count pass's visibility bit) and queue the (view, lane) pairs that
+// pass in shared memory; whenever 32 are queued, each lane takes one and runs the
+// full projection, so the expensive EWA path runs with every lane busy whatever
+// the fraction of Gaussians a view sees.  Count pass: the visible lanes of each
+// (view, group) become a ballot mask (grp_mask, entry view * G + group) and its
+// popcount.  Write pass: every visible pair writes its record to
+// grp_base[(view, group)] + (visible lanes below it), i.e. in (view, Gaussian) order.
 template <bool kWrite>
 __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera* __restrict__ cams, int n_views,
                                                      gs_params p, const uint32_t* __restrict__ view_info,
                                                      uint32_t* __restrict__ counts, gs_proj out) {
   __shared__ CamC s_cam[kMaxViewsPerChunk];
+  __shared__ float4 s_g[kWarps][4][32];                  // per lane: mo, (S0..S3), (S4, S5, Q, o), (rgb, u)
+  __shared__ uint32_t s_q[kWarps][64];                   // queued (view in chunk << 5 | lane)
+  __shared__ uint32_t s_mask[kWarps][kMaxViewsPerChunk];   // per view of the chunk: visible lanes
+  __shared__ uint32_t s_base[kWarps][kMaxViewsPerChunk];   // write pass: first record of (view, group)
   const int64_t g = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  const int64_t grp = g >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
+  const int64_t grp = g >> 5;
   const bool active = g < map.n;
   const bool grp_active = __any_sync(0xffffffffu, active);
   const int64_t n_grp = (map.n + 31) >> 5;
@@ -137,46 +146,88 @@ __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera*
     if (!kWrite && !(finite4(mo) && isfinite(su.x) && isfinite(su.y) && isfinite(su.z) && finite4(q)))
       set_flag(out.status, GS_FLAG_NONFINITE);
   }
-  for (int v0 = 0; v0 < n_views; v0 += kMaxViewsPerChunk) {
-    const int nv = min(kMaxViewsPerChunk, n_views - v0);
-    __syncthreads();
-    stage_cams(cams, view_info, v0, nv, p, s_cam);
-    __syncthreads();
-    if (!grp_active) continue;
-    uint32_t m_ahead = 0;   // write pass: the visibility masks of the next 32 views, one per lane
-    for (int i = 0; i < nv; ++i) {
-      const CamC& c = s_cam[i];
-      const size_t slot = (size_t)(v0 + i) * n_grp + grp;
+  s_g[warp][0][lane] = mo;
+  s_g[warp][1][lane] = make_float4(pre.S[0], pre.S[1], pre.S[2], pre.S[3]);
+  s_g[warp][2][lane] = make_float4(pre.S[4], pre.S[5], pre.Q, pre.o);
+  s_g[warp][3][lane] = make_float4(col.x, col.y, col.z, su.w);
+  const bool usable = active && pre.valid;
+  uint32_t* queue = s_q[warp];
+  uint32_t* vmask = s_mask[warp];
+
+  // full projection of up to 32 queued pairs, one per lane
+  auto drain = [&](int v0, int count) {
+    if (lane < count) {
+      const uint32_t e = queue[lane];
+      const int gl = e & 31, vi = e >> 5;
+      const float4 gmo = s_g[warp][0][gl], s0 = s_g[warp][1][gl], s1 = s_g[warp][2][gl];
+      GaussPre gp;
+      gp.valid = true;
+      gp.S[0] = s0.x; gp.S[1] = s0.y; gp.S[2] = s0.z; gp.S[3] = s0.w; gp.S[4] = s1.x; gp.S[5] = s1.y;
+      gp.Q = s1.z;
+      gp.o = s1.w;
       ViewProj vp;
+      const bool vis = view_proj(gmo, gp, s_cam[vi], p.near_plane, p.eps2d, vp);
       if (!kWrite) {
-        const bool vis = active && pre.valid && c.W > 0 && view_proj(mo, pre, c, p.near_plane, p.eps2d, vp);
-        const uint32_t m = __ballot_sync(0xffffffffu, vis);
-        if (lane == 0) {
-          out.grp_mask[slot] = m;
-          counts[slot] = __popc(m);
-        }
-        continue;
-      }
-      // write pass: only the (Gaussian, view) pairs the count pass found visible are projected again
-      if ((i & 31) == 0)
-        m_ahead = i + lane < nv ? out.grp_mask[(size_t)(v0 + i + lane) * n_grp + grp] : 0u;
-      const uint32_t m = __shfl_sync(0xffffffffu, m_ahead, i & 31);
-      if (!(m & (1u << lane))) continue;
-      if (view_proj(mo, pre, c, p.near_plane, p.eps2d, vp)) {
-        const uint32_t dst = out.grp_base[slot] + __popc(m & lt);
+        if (vis) atomicOr(&vmask[vi], 1u << gl);
+      } else if (vis) {
+        const uint32_t dst = s_base[warp][vi] + __popc(vmask[vi] & ((1u << gl) - 1u));
         if ((int64_t)dst < out.capacity) {
-          out.gid[dst] = (uint32_t)g;
-          out.view[dst] = (uint32_t)(v0 + i);
+          const float4 cu = s_g[warp][3][gl];
+          out.gid[dst] = (uint32_t)((grp << 5) + gl);
+          out.view[dst] = (uint32_t)(v0 + vi);
           float4* sp = reinterpret_cast<float4*>(out.splat) + 2 * (size_t)dst;
-          sp[0] = make_float4(vp.mx, vp.my, pack_ext(vp.rx, vp.ry), su.w);
-          sp[1] = make_float4(vp.ca, vp.cb, vp.cc, pre.o);
-          if (out.color_d) reinterpret_cast<float4*>(out.color_d)[dst] = make_float4(col.x, col.y, col.z, vp.depth);
+          sp[0] = make_float4(vp.mx, vp.my, pack_ext(vp.rx, vp.ry), cu.w);
+          sp[1] = make_float4(vp.ca, vp.cb, vp.cc, gp.o);
+          if (out.color_d) reinterpret_cast<float4*>(out.color_d)[dst] = make_float4(cu.x, cu.y, cu.z, vp.depth);
           reinterpret_cast<ushort4*>(out.rect)[dst] =
               make_ushort4((unsigned short)vp.x0, (unsigned short)vp.y0, (unsigned short)vp.x1, (unsigned short)vp.y1);
           out.depth_key[dst] = __float_as_uint(vp.depth);
         }
       }
     }
+    __syncwarp();
+  };
+
+  for (int v0 = 0; v0 < n_views; v0 += kMaxViewsPerChunk) {
+    const int nv = min(kMaxViewsPerChunk, n_views - v0);
+    __syncthreads();
+    stage_cams(cams, view_info, v0, nv, p, s_cam);
+    __syncthreads();
+    if (!grp_active) continue;
+    for (int i = lane; i < nv; i += 32) {
+      const size_t slot = (size_t)(v0 + i) * n_grp + grp;
+      vmask[i] = kWrite ? out.grp_mask[slot] : 0u;
+      if (kWrite) s_base[warp][i] = out.grp_base[slot];
+    }
+    __syncwarp();
+    int qn = 0;   // queued pairs (warp-uniform)
+    for (int i = 0; i < nv; ++i) {
+      bool take;
+      if (kWrite) take = (vmask[i] >> lane) & 1u;
+      else take = usable && s_cam[i].W > 0 && frustum_ok(mo, s_cam[i], p.near_plane);
+      const uint32_t m = __ballot_sync(0xffffffffu, take);
+      if (take) queue[qn + __popc(m & lt)] = ((uint32_t)i << 5) | (uint32_t)lane;
+      qn += __popc(m);
+      __syncwarp();
+      if (qn >= 32) {
+        drain(v0, 32);
+        const uint32_t rest = lane + 32 < qn ? queue[lane + 32] : 0u;
+        __syncwarp();
+        if (lane + 32 < qn) queue[lane] = rest;
+        qn -= 32;
+        __syncwarp();
+      }
+    }
+    drain(v0, qn);
+    if (!kWrite) {
+      for (int i = lane; i < nv; i += 32) {
+        const size_t slot = (size_t)(v0 + i) * n_grp + grp;
+        const uint32_t m = vmask[i];
+        out.grp_mask[slot] = m;
+        counts[slot] = __popc(m);
+      }
+    }
+    __syncwarp();
   }
 }
 
