@@ -400,6 +400,54 @@ def work_stats(torch, gs, mstep):
                 pixels=fr.n_pixels, tiles=fr.n_tiles)
 
 
+def pipeline_roofline(istep, contributing, t_pass, hbm_gbs, issue_tps):
+    """Roofline of the whole information-gain pass: per stage the larger of algorithmic
+    bytes / HBM bandwidth and algorithmic FP32 instructions / issue peak, summed, over
+    the measured pass time.  Units: (Gaussian, view) pairs and visible records for the
+    projection (~25 instructions per culled pair, ~110 per visible one; 64 B read per
+    Gaussian, 52 B written per scoring record), (tile, record) pairs for binning (44 B
+    per pair: emit, one permutation, ranges), contributing (pixel, Gaussian) evaluations
+    for compositing (~12 instructions each)."""
+    fr = istep.frame
+    n, v = istep.gm.n, istep.n_views
+    recs = int(fr.rec_count.item())
+    pairs = int(fr.pair_count.item()) & 0xFFFFFFFF
+    st = {
+        "project": (64.0 * n + 52.0 * recs, 25.0 * n * v + 110.0 * recs),
+        "bin_sort": (44.0 * pairs, 0.0),
+        "composite": (0.0, 12.0 * contributing),
+    }
+    out = {}
+    total = 0.0
+    for k, (b, ins) in st.items():
+        t = max(b / (hbm_gbs * 1e9), ins / (issue_tps * 1e12))
+        out[k + "_roof_ms"] = t * 1e3
+        total += t
+    out.update(records=recs, pairs=pairs, pair_views=n * v, contributing=contributing,
+               roof_ms=total * 1e3, measured_ms=t_pass * 1e3, frac=total / t_pass)
+    return out
+
+
+def cfg0_latency_us(torch, gs, scenes, reps=30):
+    """Device time of one forward render of config 0 (project, bin, composite)."""
+    sc = scenes.config0()
+    gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
+    fr = gs.Frame(gm.n, sc.cams)
+    img = fr.new_images()
+    for _ in range(3):
+        fr.forward(gm, img)
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fr.forward(gm, img)
+        e1.record()
+        torch.cuda.synchronize()
+        t.append(e0.elapsed_time(e1) * 1e3)
+    return statistics.median(t)
+
+
 def mix_pixels_per_view(cams):
     return sum(c.width * c.height for c in cams) / len(cams)
 
@@ -507,6 +555,9 @@ def run_ours(args):
     # (alpha: 2 sub, 5 mul/fma, exp, mul, min, compare; accumulate: sub, mul, compare, 2 fma)
     t_comp = istep.composite_ms(max(3, args.steps), flush) / 1e3
     ig_contrib, ig_walked = istep.contributing()
+    hbm = float(peaks.get("hbm_gbs", 6673.5))
+    pipe = pipeline_roofline(istep, ig_contrib, t_ig_all / args.steps, hbm, peak)
+    lat0 = cfg0_latency_us(torch, gs, scenes)
     achieved = 16.0 * ig_contrib / t_comp / 1e12
     tiles_now = {"%dx%d" % k: "%dx%d" % v for k, v in istep.tile_choice.items()}
     traffic = (IG_TRAFFIC["bytes"] if IG_TRAFFIC["sources_sha1"] == ig_sources_sha1() and
@@ -558,6 +609,8 @@ def run_ours(args):
             "ig_unbatched": unbatched,
             "stages_ms": stage_ms,
             "work": ws,
+            "ig_pipeline_roofline": pipe,
+            "cfg0_forward_latency_us": lat0,
             "e2e": e2e,
             "roofline": roofline,
             "rooflines": rooflines,

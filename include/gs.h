@@ -318,11 +318,14 @@ enum { GS_IG_RENDER_MEAN = 0 };
  * fixed-order per-view reduction.  Same alpha / skip / stop rules as
  * gs_render_fwd.  ig_out: DEVICE float[n_views].
  * status: DEVICE uint32[1] status word (OR-ed).
- * pair_capacity / tile_capacity: capacities used inside ws (see gs_workspace_size).
+ * record_capacity / pair_capacity / tile_capacity: capacities used inside ws (see
+ * gs_workspace_size, whose rec_capacity is record_capacity); record_capacity 0
+ * means n * n_views, which never overflows.  More visible (Gaussian, view)
+ * records than record_capacity set GS_FLAG_RECORD_OVERFLOW.
  * Errors: as gs_project and gs_bin_sort. */
 gs_status gs_info_gain_batch(const gs_map* map, const gs_camera* cams, int32_t n_views, const gs_params* prm,
-                             int32_t mode, float* ig_out, uint32_t* status, int64_t pair_capacity,
-                             int64_t tile_capacity, void* ws, size_t ws_bytes, void* stream);
+                             int32_t mode, float* ig_out, uint32_t* status, int64_t record_capacity,
+                             int64_t pair_capacity, int64_t tile_capacity, void* ws, size_t ws_bytes, void* stream);
 
 /* gs_info_gain_composite -- the compositing stage of gs_info_gain_batch on
  * records and bins already produced by gs_project and gs_bin_sort for the

@@ -85,7 +85,7 @@ PROTOTYPES = {
                                         POINTER(gs_image_grad), c_void_p, c_int32, POINTER(gs_params),
                                         POINTER(gs_map_grad), c_void_p]),
     "gs_info_gain_batch": (c_int32, [POINTER(gs_map), c_void_p, c_int32, POINTER(gs_params), c_int32, c_void_p,
-                                     c_void_p, c_int64, c_int64, c_void_p, c_size_t, c_void_p]),
+                                     c_void_p, c_int64, c_int64, c_int64, c_void_p, c_size_t, c_void_p]),
     "gs_info_gain_composite": (c_int32, [POINTER(gs_proj), POINTER(gs_bins), c_void_p, c_int32, POINTER(gs_params),
                                          c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
     "gs_workspace_size": (c_int32, [c_int32, c_int64, c_int32, c_int64, c_int64, c_int64, POINTER(c_size_t)]),

@@ -153,8 +153,8 @@ gs_status gs_render_bwd(const gs_map* map, const gs_proj* proj, const gs_bins* b
 }
 
 gs_status gs_info_gain_batch(const gs_map* map, const gs_camera* cams, int32_t n_views, const gs_params* prm,
-                             int32_t mode, float* ig_out, uint32_t* status, int64_t pair_capacity,
-                             int64_t tile_capacity, void* ws, size_t ws_bytes, void* stream) {
+                             int32_t mode, float* ig_out, uint32_t* status, int64_t record_capacity,
+                             int64_t pair_capacity, int64_t tile_capacity, void* ws, size_t ws_bytes, void* stream) {
   GS_TRY(check_map(map));
   GS_TRY(check_views(cams, n_views));
   GS_TRY(check_params(prm));
@@ -163,10 +163,12 @@ gs_status gs_info_gain_batch(const gs_map* map, const gs_camera* cams, int32_t n
   if (!aligned(ig_out, 4) || !aligned(status, 4)) return GS_ERR_ALIGN;
   if (pair_capacity < 1 || pair_capacity >= ((int64_t)1 << 32) - 1) return GS_ERR_ARG;
   if (tile_capacity < 1 || tile_capacity >= ((int64_t)1 << 27)) return GS_ERR_ARG;
-  if (map->n * (int64_t)n_views >= ((int64_t)1 << 32) - 1) return GS_ERR_ARG;
-  GS_TRY(check_ws(ws, ws_bytes, ig_ws_bytes(map->n, n_views, pair_capacity, tile_capacity)));
-  return from_cuda(launch_info_gain(*map, cams, n_views, *prm, ig_out, status, pair_capacity, tile_capacity, ws,
-                                    (cudaStream_t)stream));
+  if (record_capacity < 0) return GS_ERR_ARG;
+  const int64_t rec_cap = record_capacity > 0 ? record_capacity : map->n * (int64_t)n_views;
+  if (rec_cap >= ((int64_t)1 << 32) - 1) return GS_ERR_ARG;
+  GS_TRY(check_ws(ws, ws_bytes, ig_ws_bytes(map->n, n_views, rec_cap, pair_capacity, tile_capacity)));
+  return from_cuda(launch_info_gain(*map, cams, n_views, *prm, ig_out, status, rec_cap, pair_capacity,
+                                    tile_capacity, ws, (cudaStream_t)stream));
 }
 
 gs_status gs_info_gain_composite(const gs_proj* proj, const gs_bins* bins, const gs_camera* cams, int32_t n_views,
@@ -191,7 +193,7 @@ gs_status gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t rec_
     case GS_OP_PROJECT: *bytes = project_ws_bytes(n, n_views); return GS_OK;
     case GS_OP_BIN_SORT: *bytes = bin_ws_bytes(rec_capacity, pair_capacity, tile_capacity, n_views); return GS_OK;
     case GS_OP_RENDER_BWD: *bytes = bwd_ws_bytes(rec_capacity); return GS_OK;
-    case GS_OP_INFO_GAIN: *bytes = ig_ws_bytes(n, n_views, pair_capacity, tile_capacity); return GS_OK;
+    case GS_OP_INFO_GAIN: *bytes = ig_ws_bytes(n, n_views, rec_capacity, pair_capacity, tile_capacity); return GS_OK;
     case GS_OP_IG_COMPOSITE: *bytes = ig_composite_ws_bytes(tile_capacity); return GS_OK;
     default: return GS_ERR_ARG;
   }

@@ -96,9 +96,10 @@ size_t ig_composite_ws_bytes(int64_t tile_cap);
 cudaError_t launch_ig_composite(const gs_proj& proj, const gs_bins& bins, const gs_camera* cams, int n_views,
                                 const gs_params& p, float* ig_out, void* ws, cudaStream_t st);
 
-size_t ig_ws_bytes(int64_t n, int n_views, int64_t pair_cap, int64_t tile_cap);
+// rec_cap: record capacity of the batch (n * n_views when 0).
+size_t ig_ws_bytes(int64_t n, int n_views, int64_t rec_cap, int64_t pair_cap, int64_t tile_cap);
 cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_views, const gs_params& p,
-                             float* ig_out, uint32_t* status, int64_t pair_cap, int64_t tile_cap, void* ws,
-                             cudaStream_t st);
+                             float* ig_out, uint32_t* status, int64_t rec_cap, int64_t pair_cap, int64_t tile_cap,
+                             void* ws, cudaStream_t st);
 
 }  // namespace gs

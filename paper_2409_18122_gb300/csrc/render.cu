@@ -341,8 +341,8 @@ cudaError_t launch_render_fwd(const gs_map& map, const gs_proj& proj, const gs_b
   return cudaGetLastError();
 }
 
-size_t ig_ws_bytes(int64_t n, int n_views, int64_t pair_cap, int64_t tile_cap) {
-  const int64_t rec_cap = n * (int64_t)n_views;
+size_t ig_ws_bytes(int64_t n, int n_views, int64_t rec_cap, int64_t pair_cap, int64_t tile_cap) {
+  if (rec_cap <= 0) rec_cap = n * (int64_t)n_views;
   Carver c(nullptr);
   c.take<uint32_t>(1);                                   // record count
   c.take<uint32_t>(kVI * (size_t)(n_views + 1));         // view info
@@ -417,9 +417,9 @@ cudaError_t launch_ig_composite(const gs_proj& proj, const gs_bins& bins, const 
 }
 
 cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_views, const gs_params& p,
-                             float* ig_out, uint32_t* status, int64_t pair_cap, int64_t tile_cap, void* ws,
-                             cudaStream_t st) {
-  const int64_t rec_cap = map.n * (int64_t)n_views;
+                             float* ig_out, uint32_t* status, int64_t rec_cap, int64_t pair_cap, int64_t tile_cap,
+                             void* ws, cudaStream_t st) {
+  if (rec_cap <= 0) rec_cap = map.n * (int64_t)n_views;
   Carver c(ws);
   gs_proj proj;
   proj.capacity = rec_cap;

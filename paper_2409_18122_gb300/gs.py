@@ -157,7 +157,7 @@ class Frame:
 
     def __init__(self, n: int, cams: Sequence, params: RenderParams = RenderParams(),
                  pair_capacity: Optional[int] = None, device="cuda", with_color: bool = True,
-                 with_pair_tiles: bool = True):
+                 with_pair_tiles: bool = True, record_capacity: Optional[int] = None):
         self.device = torch.device(device)
         self.params = params
         self.with_color = with_color
@@ -169,7 +169,8 @@ class Frame:
         self.tiles_x, self.tiles_y, self.tile_base, self.pix_base = tile_grid(self.cams, params)
         self.n_tiles = int(self.tile_base[-1])
         self.n_pixels = int(self.pix_base[-1])
-        self.rec_capacity = max(self.n * self.V, 1)
+        # records: at most n * V; a smaller capacity (large batches) grows on overflow
+        self.rec_capacity = max(int(record_capacity) if record_capacity else self.n * self.V, 1)
         if pair_capacity is None:
             pair_capacity = min(max(1 << 20, 8 * self.n * self.V), (1 << 31) - 1)
         self._alloc(int(pair_capacity))
@@ -300,8 +301,15 @@ class Frame:
         return f
 
     def grow_if_needed(self, margin: float = 1.25) -> bool:
-        """After a synchronised forward: if pairs overflowed, reallocate with room for them (returns True)."""
+        """After a synchronised forward: if records or pairs overflowed, reallocate with room for
+        them (returns True; run the forward again)."""
         f = self.read_status()
+        if f & L.GS_FLAG_RECORD_OVERFLOW:
+            need = int(self.grp_base[self.n_slots].item()) & 0xFFFFFFFF
+            self.rec_capacity = max(min(int(need * margin) + 1024, self.n * self.V), 1)
+            self.status.zero_()
+            self._alloc(self.pair_capacity)
+            return True
         if f & L.GS_FLAG_PAIR_OVERFLOW:
             need = int(self.pair_count.item()) & 0xFFFFFFFF
             if need == 0xFFFFFFFF:
@@ -359,7 +367,7 @@ class InfoGain:
     """Batched information gain over a fixed candidate set (gs_info_gain_batch)."""
 
     def __init__(self, n: int, cams: Sequence, params: RenderParams = RenderParams(),
-                 pair_capacity: Optional[int] = None, device="cuda"):
+                 pair_capacity: Optional[int] = None, device="cuda", record_capacity: Optional[int] = None):
         self.device = torch.device(device)
         self.params = params
         self.c_params = params.c()
@@ -371,13 +379,15 @@ class InfoGain:
         self.n_tiles = max(int(tile_base[-1]), 1)
         if pair_capacity is None:
             pair_capacity = min(max(1 << 20, 2 * self.n * self.V), (1 << 31) - 1)
+        # records: at most n * V; a smaller capacity (large batches) grows on overflow
+        self.record_capacity = int(record_capacity) if record_capacity else self.n * self.V
         self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
         self.out = torch.zeros(self.V, dtype=torch.float32, device=self.device)
         self._alloc(int(pair_capacity))
 
     def _alloc(self, pair_capacity):
         self.pair_capacity = pair_capacity
-        ws = L.workspace_size(L.GS_OP_INFO_GAIN, self.n, self.V, 0, pair_capacity, self.n_tiles)
+        ws = L.workspace_size(L.GS_OP_INFO_GAIN, self.n, self.V, self.record_capacity, pair_capacity, self.n_tiles)
         self.ws = None
         torch.cuda.empty_cache()
         self.ws = torch.empty(ws, dtype=torch.uint8, device=self.device)
@@ -387,8 +397,9 @@ class InfoGain:
         m = gmap.c()
         _timed("gs_info_gain_batch", stream, lambda: L.check(
             L.lib().gs_info_gain_batch(ctypes.byref(m), _ptr(self.cams_dev), self.V, ctypes.byref(self.c_params),
-                                       L.GS_IG_RENDER_MEAN, _ptr(o), _ptr(self.status), self.pair_capacity,
-                                       self.n_tiles, _ptr(self.ws), self.ws.numel(), _stream(stream)),
+                                       L.GS_IG_RENDER_MEAN, _ptr(o), _ptr(self.status), self.record_capacity,
+                                       self.pair_capacity, self.n_tiles, _ptr(self.ws), self.ws.numel(),
+                                       _stream(stream)),
             "gs_info_gain_batch"))
         return o
 
@@ -398,11 +409,16 @@ class InfoGain:
         return int(flags.value)
 
     def grow_if_needed(self) -> bool:
-        """After a synchronised call: if pairs overflowed, double the capacity (returns True)."""
+        """After a synchronised call: if records or pairs overflowed, double that capacity (returns True)."""
         f = self.read_status()
-        if f & L.GS_FLAG_PAIR_OVERFLOW:
+        if f & (L.GS_FLAG_PAIR_OVERFLOW | L.GS_FLAG_RECORD_OVERFLOW):
             self.status.zero_()
-            self._alloc(min(2 * self.pair_capacity, (1 << 32) - 2))
+            if f & L.GS_FLAG_RECORD_OVERFLOW:
+                self.record_capacity = min(2 * self.record_capacity, self.n * self.V, (1 << 32) - 2)
+            pc = self.pair_capacity
+            if f & L.GS_FLAG_PAIR_OVERFLOW:
+                pc = min(2 * self.pair_capacity, (1 << 32) - 2)
+            self._alloc(pc)
             return True
         return False
 

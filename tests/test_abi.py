@@ -118,8 +118,9 @@ def test_host_side_argument_errors(lib):
     bins = L.gs_bins(0, 10, fake, fake, fake, fake)
     assert lib.gs_bin_sort(P(proj), fake, 1, P(prm), P(bins), fake, 1 << 30, None) == L.GS_ERR_ARG
     # info gain: unknown mode, null output
-    assert lib.gs_info_gain_batch(P(m), fake, 1, P(prm), 7, fake, fake, 100, 10, fake, 1 << 30, None) == L.GS_ERR_ARG
-    assert lib.gs_info_gain_batch(P(m), fake, 1, P(prm), 0, None, fake, 100, 10, fake, 1 << 30, None) == L.GS_ERR_NULL
+    assert lib.gs_info_gain_batch(P(m), fake, 1, P(prm), 7, fake, fake, 0, 100, 10, fake, 1 << 30, None) == L.GS_ERR_ARG
+    assert lib.gs_info_gain_batch(P(m), fake, 1, P(prm), 0, None, fake, 0, 100, 10, fake, 1 << 30, None) == L.GS_ERR_NULL
+    assert lib.gs_info_gain_batch(P(m), fake, 1, P(prm), 0, fake, fake, -1, 100, 10, fake, 1 << 30, None) == L.GS_ERR_ARG
     # read_status: null
     f = ctypes.c_uint32(0)
     assert lib.gs_read_status(None, P(f)) == L.GS_ERR_NULL

@@ -267,6 +267,66 @@ def test_render_full_size_config1_sampled_pixels():
     compare_image(g, ref, "cfg1 sampled", check_last=lg)
 
 
+def _sampled(gpu_views, pix, fr):
+    out = dict(rgb=[], depth=[], unc=[], T=[])
+    lg_all = last_gid(fr, gpu_views)
+    lg = []
+    for v, u, y in pix:
+        g = gpu_views[v]
+        out["rgb"].append(g["rgb"][y, u])
+        for k in ("depth", "unc", "T"):
+            out[k].append(g[k][y, u])
+        lg.append(lg_all[v][y, u])
+    return {k: np.asarray(x) for k, x in out.items()}, np.asarray(lg)
+
+
+def test_config4_large_map_keyframes_and_candidate_batch():
+    """3M Gaussians on a 40x40 m map.  Two 1280x720 keyframes rendered in one batch: 300
+    sampled pixels each vs the oracle.  All 1,024 candidates (160x120 / 320x240) in one
+    information-gain batch: two of them equal the mean of their own forward-rendered
+    uncertainty channel, whose sampled pixels match the oracle."""
+    sc, cands = scenes.config4()
+    gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
+    cams = sc.cams[:2]
+    fr = gs.Frame(gm.n, cams)
+    img = fr.forward(gm)
+    torch.cuda.synchronize()
+    while fr.grow_if_needed():
+        img = fr.forward(gm)
+        torch.cuda.synchronize()
+    fr.check_status()
+    gpu = images_host(fr, img)
+    rng = np.random.default_rng(44)
+    pix = np.concatenate([np.stack([np.full(300, v), rng.integers(0, 1280, 300), rng.integers(0, 720, 300)], 1)
+                          for v in range(2)])
+    ref = O.render(sc.gmap, cams, pixels=pix)
+    g, lg = _sampled(gpu, pix, fr)
+    compare_image(g, ref, "cfg4 keyframes", check_last=lg)
+
+    ig_op = gs.InfoGain(gm.n, cands, record_capacity=400_000_000)
+    ig = ig_op(gm)
+    torch.cuda.synchronize()
+    while ig_op.grow_if_needed():
+        ig = ig_op(gm)
+        torch.cuda.synchronize()
+    assert not (ig_op.read_status() & gs.L.GS_FLAG_ERROR_MASK)
+    ig = ig.cpu().numpy()
+    assert np.isfinite(ig).all() and (ig >= 0).all()
+    for v in (0, 1):
+        cam = cands[v]
+        frv = gs.Frame(gm.n, [cam])
+        iv = frv.forward(gm)
+        torch.cuda.synchronize()
+        frv.check_status()
+        hv = images_host(frv, iv)
+        U = hv[0]["unc"].astype(np.float64)
+        assert abs(ig[v] - U.mean()) <= 1e-5 * max(U.mean(), 1e-3), (v, ig[v], U.mean())
+        pv = np.stack([np.zeros(200, int), rng.integers(0, cam.width, 200), rng.integers(0, cam.height, 200)], 1)
+        rv = O.render(sc.gmap, [cam], pixels=pv)
+        gv, lgv = _sampled(hv, pv, frv)
+        compare_image(gv, rv, "cfg4 candidate %d" % v, check_last=lgv)
+
+
 # --------------------------------------------------------------------------- gradients
 def _fd_slice():
     """Config-2 style slice: 1,000 room Gaussians near keyframe 0, 64x48 at f = 52.5."""
