@@ -16,6 +16,14 @@ Functions and the passages they follow (RT-GuIDE, arXiv 2409.18122):
                mean of the composited uncertainty channel.
   bin_sort     Sec. III "sorted in increasing order of depth": pairs (tile, Gaussian)
                ordered by (view, tile, depth, record index).
+  uncertainty_update   Sec. IV-A: u = |mu_k - mu_{k-1}| (or its square), unchanged
+               means keep their u.
+  uncertainty_thresholds  Sec. IV-B (implementation details): G_H / G_L thresholds at
+               half a standard deviation above / below the mean of u.
+  visibility / view_utility  Sec. IV-B, Eq. view_util: xi = |visible G_H| - lambda
+               |visible G_L| (or the sum of u of the visible Gaussians); visible =
+               in the field of view and within the perception range.
+  region_uncertainty   Sec. IV-B high-level planner: mean u of cuboid regions.
 """
 from __future__ import annotations
 
@@ -286,3 +294,93 @@ def ex32(x: float) -> np.float32:
 
 def lg32(x: float) -> np.float32:
     return np.float32(_load().lg32(float(x)))
+
+
+# ------------------------------------------------------------------ render-free utility
+def uncertainty_update(mo_prev: np.ndarray, mo_cur: np.ndarray, u_prev: np.ndarray, squared: bool = False):
+    """Sec. IV-A: u_i = |mu_cur,i - mu_prev,i| in FP64 (squared for the ablation), for the
+    Gaussians whose mean changed; the others keep u_prev (the paper's bookkeeping)."""
+    d = mo_cur[:, :3].astype(np.float64) - mo_prev[:, :3].astype(np.float64)
+    moved = (mo_cur[:, :3] != mo_prev[:, :3]).any(axis=1)
+    d2 = (d * d).sum(axis=1)
+    u = np.array(u_prev, np.float64, copy=True)
+    u[moved] = d2[moved] if squared else np.sqrt(d2[moved])
+    return u
+
+
+def uncertainty_thresholds(mo: np.ndarray, u: np.ndarray, ground_z: float = -np.inf):
+    """Mean and population standard deviation of u over the Gaussians with mu_z >= ground_z
+    (exactly rounded FP64 sums), and the thresholds mean + sigma/2 (high) and mean - sigma/2
+    (low).  Returns (mean, sigma, t_high, t_low, count)."""
+    import math
+    keep = mo[:, 2] >= np.float32(ground_z)
+    x = u[keep].astype(np.float64)
+    m = len(x)
+    if m == 0:
+        return 0.0, 0.0, 0.0, 0.0, 0
+    mean = math.fsum(x) / m
+    sigma = math.sqrt(math.fsum((x - mean) ** 2) / m)
+    return mean, sigma, mean + 0.5 * sigma, mean - 0.5 * sigma, m
+
+
+def visibility(mo: np.ndarray, cam, near_plane: float = 0.2, range_m: float = 5.0) -> np.ndarray:
+    """v(x, g) of every mean for one camera, decided in FP32: t = R^T (mu - T) with each
+    product and sum rounded to float32 in the order (R0 dx + R3 dy) + R6 dz (t_y, t_z
+    likewise), pixel (fx t_x / t_z + cx, fy t_y / t_z + cy); visible iff
+    near < t_z <= range and the pixel lies in [0, W) x [0, H)."""
+    f = np.float32
+    R = np.asarray(cam.R, np.float32).reshape(3, 3)
+    T = np.asarray(cam.T, np.float32).reshape(3)
+    dx = mo[:, 0].astype(f) - T[0]
+    dy = mo[:, 1].astype(f) - T[1]
+    dz = mo[:, 2].astype(f) - T[2]
+    # t_j = sum_i R[i][j] d_i  (t = R^T d); R row-major: R[i][j] = R_flat[3 i + j]
+    tx = (R[0, 0] * dx + R[1, 0] * dy) + R[2, 0] * dz
+    ty = (R[0, 1] * dx + R[1, 1] * dy) + R[2, 1] * dz
+    tz = (R[0, 2] * dx + R[1, 2] * dy) + R[2, 2] * dz
+    with np.errstate(divide="ignore", invalid="ignore"):
+        px = (f(cam.fx) * tx) / tz + f(cam.cx)
+        py = (f(cam.fy) * ty) / tz + f(cam.cy)
+    ok = (tz > f(near_plane)) & (tz <= f(range_m))
+    return ok & (px >= 0) & (px < f(cam.width)) & (py >= 0) & (py < f(cam.height))
+
+
+def view_utility(mo: np.ndarray, u: np.ndarray, cams, near_plane: float = 0.2, range_m: float = 5.0,
+                 lam: float = 1.0, ground_z: float = -np.inf, mode: str = "xi", thresholds=None):
+    """Eq. view_util per camera: xi = |visible G_H| - lam |visible G_L| (mode "xi", also
+    returning the counts [V, 2]) or the FP64 sum of u over the visible Gaussians (mode
+    "sum").  G_H = {u > t_high}, G_L = {u < t_low} from uncertainty_thresholds unless given."""
+    keep = mo[:, 2] >= np.float32(ground_z)
+    if thresholds is None:
+        thresholds = uncertainty_thresholds(mo, u, ground_z)
+    t_hi, t_lo = thresholds[2], thresholds[3]
+    u64 = u.astype(np.float64)
+    hi = keep & (u64 > t_hi)
+    lo = keep & (u64 < t_lo)
+    xi = np.zeros(len(cams))
+    counts = np.zeros((len(cams), 2), np.int64)
+    for v, cam in enumerate(cams):
+        vis = visibility(mo, cam, near_plane, range_m)
+        if mode == "sum":
+            xi[v] = u64[vis & keep].sum()
+        else:
+            counts[v] = ((vis & hi).sum(), (vis & lo).sum())
+            xi[v] = counts[v, 0] - lam * counts[v, 1]
+    return xi, counts
+
+
+def region_uncertainty(mo: np.ndarray, u: np.ndarray, origin, size: float, dims):
+    """Mean u per cuboid region: region index (iz dims[1] + iy) dims[0] + ix with
+    i = floor((mu - origin) / size) computed in float32 (the kernel's precision);
+    Gaussians outside the grid are left out.  Returns (mean [R], count [R])."""
+    f = np.float32
+    idx = np.floor((mo[:, :3].astype(f) - np.asarray(origin, f)) / f(size))
+    dims = np.asarray(dims, np.int64)
+    inside = ((idx >= 0) & (idx < dims[None, :].astype(f))).all(axis=1)
+    ii = idx[inside].astype(np.int64)
+    r = (ii[:, 2] * dims[1] + ii[:, 1]) * dims[0] + ii[:, 0]
+    R = int(dims.prod())
+    cnt = np.bincount(r, minlength=R)
+    tot = np.bincount(r, weights=u[inside].astype(np.float64), minlength=R)
+    mean = np.where(cnt > 0, tot / np.maximum(cnt, 1), 0.0)
+    return mean, cnt

@@ -387,3 +387,94 @@ def test_gradient_opacity_single_gaussian():
     assert o * G > 1 / 255
     gr = O.grad(g, [CAM], [d])
     np.testing.assert_allclose(gr["dmo"][0, 3], G * float(np.float32(col)) * o * (1 - o), rtol=1e-12)
+
+
+# ------------------------------------------------------------ render-free view utility (Sec. IV-A/B)
+def _mo(xyz):
+    a = np.zeros((len(xyz), 4), np.float32)
+    a[:, :3] = np.asarray(xyz, np.float32)
+    return a
+
+
+def test_uncertainty_update_closed_form_and_bookkeeping():
+    prev = _mo([[0, 0, 0], [1, 1, 1], [2, 0, 0]])
+    cur = _mo([[3, 4, 0], [1, 1, 1], [2, 0, 0.5]])
+    u0 = np.array([7.0, 7.0, 7.0])
+    np.testing.assert_allclose(O.uncertainty_update(prev, cur, u0), [5.0, 7.0, 0.5])
+    np.testing.assert_allclose(O.uncertainty_update(prev, cur, u0, squared=True), [25.0, 7.0, 0.25])
+
+
+def test_uncertainty_thresholds_hand_values():
+    """u = 0, 1, ..., 9: mean 4.5, population variance 8.25; G_H = {6..9}, G_L = {0..3}."""
+    u = np.arange(10.0)
+    mo = _mo([[0, 0, 1]] * 10)
+    mean, sigma, t_hi, t_lo, m = O.uncertainty_thresholds(mo, u)
+    assert (mean, m) == (4.5, 10)
+    assert sigma == pytest.approx(math.sqrt(8.25), rel=1e-15)
+    assert sum(u > t_hi) == 4 and sum(u < t_lo) == 4 and u[u > t_hi].min() == 6 and u[u < t_lo].max() == 3
+    # ground-plane removal: the five lowest Gaussians are left out
+    mo2 = mo.copy()
+    mo2[:5, 2] = -1.0
+    mean2, sigma2, _, _, m2 = O.uncertainty_thresholds(mo2, u, ground_z=0.0)
+    assert (mean2, m2) == (7.0, 5) and sigma2 == pytest.approx(math.sqrt(2.0), rel=1e-15)
+
+
+def test_visibility_pinhole_edges_and_range():
+    cam = Camera(100.0, 100.0, 50.0, 40.0, 100, 80)           # camera at the origin looking along +z
+    # u = 100 x / z + 50: x = -1.5 at z = 3 gives u = 0 (inside), x = 1.5 gives u = 100 (outside);
+    # v = 100 y / z + 40 with y = -+1.25, z = 3.125 gives exactly 0 (inside) and 80 (outside)
+    pts = [[0, 0, 3], [0, 0, 6], [0, 0, -1], [-1.5, 0, 3], [1.5, 0, 3], [1.4999, 0, 3], [0, 1.25, 3.125],
+           [0, -1.25, 3.125], [0, 0, 5.0], [0, 0, 0.2]]
+    vis = O.visibility(_mo(pts), cam, near_plane=0.2, range_m=5.0)
+    np.testing.assert_array_equal(vis, [1, 0, 0, 1, 0, 1, 0, 1, 1, 0])
+
+
+def test_visibility_fp32_decisions_match_fp64_projection_away_from_edges():
+    """The float32 decision sequence against an independent FP64 pinhole projection, on
+    random points that are not within 1e-3 of an image edge or a depth limit."""
+    rng = np.random.default_rng(3)
+    cam = Camera(200.0, 210.0, 80.0, 60.0, 160, 120, Rotation.from_euler("xyz", [0.2, -0.5, 0.3]).as_matrix(),
+                 [0.3, -0.2, 0.5])
+    R = np.asarray(cam.R, np.float64)
+    # points around the frustum: camera coordinates with |t_x|, |t_y| up to 0.7 t_z, t_z in (0.1, 6)
+    tz = rng.uniform(0.1, 6.0, 20000)
+    tc = np.stack([rng.uniform(-0.7, 0.7, 20000) * tz, rng.uniform(-0.7, 0.7, 20000) * tz, tz], 1)
+    p = tc @ R.T + np.asarray(cam.T, np.float64)
+    t = (p - np.asarray(cam.T, np.float64)) @ R          # t = R^T (p - T)
+    px = cam.fx * t[:, 0] / t[:, 2] + cam.cx
+    py = cam.fy * t[:, 1] / t[:, 2] + cam.cy
+    ref = (t[:, 2] > 0.2) & (t[:, 2] <= 5.0) & (px >= 0) & (px < cam.width) & (py >= 0) & (py < cam.height)
+    clear = (np.abs(t[:, 2] - 0.2) > 1e-3) & (np.abs(t[:, 2] - 5.0) > 1e-3) & (np.abs(px) > 1e-3) & \
+            (np.abs(px - cam.width) > 1e-3) & (np.abs(py) > 1e-3) & (np.abs(py - cam.height) > 1e-3)
+    got = O.visibility(_mo(p), cam, 0.2, 5.0)
+    assert ref[clear].sum() > 2000 and (~ref[clear]).sum() > 2000
+    np.testing.assert_array_equal(got[clear], ref[clear])
+
+
+def test_view_utility_hand_counts():
+    """Ten visible Gaussians with u = 0..9 and five more behind the camera: xi = 4 - lambda * 4
+    (G_H = {6..9}, G_L = {0..3}, thresholds from all fifteen), and the sum mode adds u of the
+    visible ones."""
+    cam = Camera(100.0, 100.0, 50.0, 40.0, 100, 80)
+    vis_pts = [[0.1 * i - 0.5, 0, 3] for i in range(10)]
+    hid_pts = [[0, 0, -2]] * 5
+    mo = _mo(vis_pts + hid_pts)
+    u = np.concatenate([np.arange(10.0), np.array([0.0, 9.0, 4.5, 4.5, 4.5])])
+    st = O.uncertainty_thresholds(mo, u)
+    assert sum(u > st[2]) == 5 and sum(u < st[3]) == 5       # the hidden 9 and 0 join G_H and G_L
+    xi, counts = O.view_utility(mo, u, [cam], lam=1.0)
+    np.testing.assert_array_equal(counts, [[4, 4]])
+    assert xi[0] == 0.0
+    xi2, _ = O.view_utility(mo, u, [cam], lam=0.5)
+    assert xi2[0] == 2.0
+    xs, _ = O.view_utility(mo, u, [cam], mode="sum")
+    assert xs[0] == 45.0
+
+
+def test_region_uncertainty_hand_means():
+    mo = _mo([[0.5, 0.5, 0.5], [1.0, 2.0, 0.1], [3.0, 0.1, 0.1], [2.6, 2.6, 0.2], [-0.1, 0, 0], [9, 9, 9]])
+    u = np.array([1.0, 3.0, 5.0, 7.0, 100.0, 100.0])
+    mean, cnt = O.region_uncertainty(mo, u, origin=(0, 0, 0), size=2.5, dims=(2, 2, 1))
+    # region (0,0): first two; (1,0): the third; (1,1): the fourth; the last two lie outside
+    np.testing.assert_array_equal(cnt, [2, 1, 0, 1])
+    np.testing.assert_allclose(mean, [2.0, 5.0, 0.0, 7.0])
