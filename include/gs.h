@@ -341,14 +341,93 @@ gs_status gs_info_gain_composite(const gs_proj* proj, const gs_bins* bins, const
                                  const gs_params* prm, int32_t mode, float* ig_out, void* ws, size_t ws_bytes,
                                  void* stream);
 
+/* --------------------------------------------- render-free view utility (Sec. IV-A/B)
+ * The paper scores candidate poses without rendering: per Gaussian, the magnitude
+ * of the change of its mean between map updates is its uncertainty u; Gaussians
+ * with u above mean(u) + sigma(u)/2 form G_H, below mean(u) - sigma(u)/2 form G_L;
+ * a pose's utility is xi = |visible G_H| - lambda |visible G_L| (Eq. view_util).
+ * v(x, g) = 1 iff g's mean lies in front of the camera with near < t_z <= range
+ * (the sensor's perception range) and projects inside the image; no occlusion
+ * test.  The map's u channel is gs_map.su[i].w. */
+enum { GS_U_ABS = 0, GS_U_SQ = 1 };        /* u = |mu_k - mu_{k-1}|, or its square (ablation) */
+enum { GS_XI = 0, GS_XI_SUM = 1 };         /* Eq. view_util, or sum of u over visible Gaussians (ablation) */
+
+/* Parameters of the view utility.  near_plane > 0, range > near_plane; lambda:
+ * lambda_xi (1 in the paper); Gaussians with mu_z < ground_z are left out of the
+ * thresholds and of xi (ground-plane removal; -INFINITY keeps every Gaussian). */
+typedef struct {
+  float near_plane, range, lambda, ground_z;
+} gs_utility_params;
+
+/* Cuboid regions: region (ix, iy, iz), 0 <= i < dims, holds the means with
+ * floor((mu - origin) / size) = (ix, iy, iz); region index (iz dims[1] + iy) dims[0] + ix. */
+typedef struct {
+  float origin[3];
+  float size;
+  int32_t dims[3];
+} gs_region_grid;
+
+/* gs_uncertainty_update -- Sec. IV-A: for every Gaussian whose mean changed
+ * between mo_prev and mo_cur (DEVICE float[n][4], means in the first three), set
+ * su[i][3] = |mu_cur - mu_prev| (GS_U_ABS) or its square (GS_U_SQ); Gaussians whose
+ * mean did not change keep their previous value (the paper's bookkeeping).  Each
+ * difference, product and sum is rounded separately (IEEE FP32, no fused
+ * multiply-add), the root correctly rounded.  su: DEVICE float[n][4].
+ * Errors: GS_ERR_NULL, GS_ERR_ALIGN (16-byte arrays), GS_ERR_ARG, GS_ERR_CUDA. */
+gs_status gs_uncertainty_update(const float* mo_prev, const float* mo_cur, float* su, int64_t n, int32_t mode,
+                                void* stream);
+
+/* gs_uncertainty_thresholds -- mean and population standard deviation of u over the
+ * Gaussians with mu_z >= ground_z (FP64, two passes, fixed summation order), into
+ * DEVICE double stats[5] = (mean, sigma, mean + sigma/2, mean - sigma/2, count).
+ * ws: DEVICE workspace of gs_workspace_size(GS_OP_THRESHOLDS, ...) bytes.
+ * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG, GS_ERR_WORKSPACE, GS_ERR_CUDA. */
+gs_status gs_uncertainty_thresholds(const gs_map* map, float ground_z, double* stats, void* ws, size_t ws_bytes,
+                                    void* stream);
+
+/* gs_view_utility_batch -- Eq. view_util for n_views poses in one batch:
+ * GS_XI: xi_v = |{g in G_H: v(x_v, g)}| - lambda |{g in G_L: v(x_v, g)}| with
+ * G_H = {u > stats[2]}, G_L = {u < stats[3]} (stats from gs_uncertainty_thresholds);
+ * GS_XI_SUM: xi_v = sum of u over the visible Gaussians (FP32, fixed order).
+ * Visibility is decided in FP32: t = R^T (mu - T) with every product and sum
+ * rounded separately in the order (R0 dx + R3 dy) + R6 dz (likewise for t_y, t_z),
+ * pixel = (fx t_x / t_z + cx, fy t_y / t_z + cy) with correctly rounded division,
+ * visible iff near < t_z <= range, 0 <= px < W and 0 <= py < H.
+ * xi_out: DEVICE float[n_views]; counts_out: DEVICE uint32[n_views][2] (visible
+ * |G_H|, |G_L|) or NULL.  Deterministic.  ws: gs_workspace_size(GS_OP_VIEW_UTILITY).
+ * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG, GS_ERR_WORKSPACE, GS_ERR_CUDA. */
+gs_status gs_view_utility_batch(const gs_map* map, const gs_camera* cams, int32_t n_views,
+                                const gs_utility_params* prm, int32_t mode, const double* stats, float* xi_out,
+                                uint32_t* counts_out, void* ws, size_t ws_bytes, void* stream);
+
+/* gs_region_uncertainty -- Sec. IV-B high-level planner: mean uncertainty of each
+ * cuboid region, Omega_o = (1/M_o) sum over the region's Gaussians of u (0 if M_o = 0).
+ * omega_out: DEVICE float[R], count_out: DEVICE uint32[R] (M_o) or NULL,
+ * R = dims[0] dims[1] dims[2].  Sums in FP64 (atomic, so the last bits of a sum
+ * may depend on the order).  ws: gs_workspace_size(GS_OP_REGIONS, ...) with R as
+ * rec_capacity.  Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG, GS_ERR_WORKSPACE, GS_ERR_CUDA. */
+gs_status gs_region_uncertainty(const gs_map* map, const gs_region_grid* grid, float* omega_out, uint32_t* count_out,
+                                void* ws, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------- utilities */
-enum { GS_OP_PROJECT = 0, GS_OP_BIN_SORT = 1, GS_OP_RENDER_BWD = 2, GS_OP_INFO_GAIN = 3, GS_OP_IG_COMPOSITE = 4 };
+enum {
+  GS_OP_PROJECT = 0,
+  GS_OP_BIN_SORT = 1,
+  GS_OP_RENDER_BWD = 2,
+  GS_OP_INFO_GAIN = 3,
+  GS_OP_IG_COMPOSITE = 4,
+  GS_OP_THRESHOLDS = 5,
+  GS_OP_VIEW_UTILITY = 6,
+  GS_OP_REGIONS = 7
+};
 
 /* gs_workspace_size -- HOST.  Bytes of workspace `op` needs:
  *   n, n_views      map size and number of views
- *   rec_capacity    record capacity of the gs_proj in use (GS_OP_INFO_GAIN: ignored, n * n_views)
+ *   rec_capacity    record capacity of the gs_proj in use (GS_OP_INFO_GAIN: the record_capacity
+ *                   argument, 0 for n * n_views; GS_OP_REGIONS: the number of regions)
  *   pair_capacity   pair capacity of the gs_bins in use
  *   tile_capacity   tile capacity of the gs_bins in use (GS_OP_IG_COMPOSITE: only this is used)
+ * GS_OP_THRESHOLDS needs nothing else; GS_OP_VIEW_UTILITY only n_views.
  * Writes the byte count to *bytes (HOST).  Errors: GS_ERR_NULL, GS_ERR_ARG, GS_ERR_CUDA. */
 gs_status gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t rec_capacity, int64_t pair_capacity,
                             int64_t tile_capacity, size_t* bytes);

@@ -24,7 +24,10 @@ GS_FLAG_BAD_RECORDS = 1 << 5
 GS_FLAG_ERROR_MASK = (GS_FLAG_PAIR_OVERFLOW | GS_FLAG_RANGE_OVERFLOW | GS_FLAG_BAD_CAMERA | GS_FLAG_RECORD_OVERFLOW
                       | GS_FLAG_BAD_RECORDS)
 GS_IG_RENDER_MEAN = 0
-GS_OP_PROJECT, GS_OP_BIN_SORT, GS_OP_RENDER_BWD, GS_OP_INFO_GAIN, GS_OP_IG_COMPOSITE = range(5)
+(GS_OP_PROJECT, GS_OP_BIN_SORT, GS_OP_RENDER_BWD, GS_OP_INFO_GAIN, GS_OP_IG_COMPOSITE, GS_OP_THRESHOLDS,
+ GS_OP_VIEW_UTILITY, GS_OP_REGIONS) = range(8)
+GS_U_ABS, GS_U_SQ = 0, 1
+GS_XI, GS_XI_SUM = 0, 1
 GS_NOALLOC_MAX_RECORDS = 1 << 18
 
 
@@ -54,6 +57,14 @@ class gs_bins(ctypes.Structure):
                 ("rec", c_void_p), ("ranges", c_void_p)]
 
 
+class gs_utility_params(ctypes.Structure):
+    _fields_ = [("near_plane", c_float), ("range", c_float), ("lambda", c_float), ("ground_z", c_float)]
+
+
+class gs_region_grid(ctypes.Structure):
+    _fields_ = [("origin", c_float * 3), ("size", c_float), ("dims", c_int32 * 3)]
+
+
 class gs_image(ctypes.Structure):
     _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("unc", c_void_p), ("T", c_void_p), ("last", c_void_p),
                 ("n_contrib", c_void_p)]
@@ -72,6 +83,12 @@ assert ctypes.sizeof(gs_params) == 32
 
 # name -> (restype, argtypes); the exported C ABI
 PROTOTYPES = {
+    "gs_uncertainty_update": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p]),
+    "gs_uncertainty_thresholds": (c_int32, [POINTER(gs_map), c_float, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "gs_view_utility_batch": (c_int32, [POINTER(gs_map), c_void_p, c_int32, POINTER(gs_utility_params), c_int32,
+                                        c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "gs_region_uncertainty": (c_int32, [POINTER(gs_map), POINTER(gs_region_grid), c_void_p, c_void_p, c_void_p,
+                                        c_size_t, c_void_p]),
     "gs_project": (c_int32, [POINTER(gs_map), c_void_p, c_int32, POINTER(gs_params), POINTER(gs_proj), c_void_p,
                              c_size_t, c_void_p]),
     "gs_bin_sort": (c_int32, [POINTER(gs_proj), c_void_p, c_int32, POINTER(gs_params), POINTER(gs_bins), c_void_p,

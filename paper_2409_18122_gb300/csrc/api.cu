@@ -185,6 +185,53 @@ gs_status gs_info_gain_composite(const gs_proj* proj, const gs_bins* bins, const
   return from_cuda(launch_ig_composite(*proj, *bins, cams, n_views, *prm, ig_out, ws, (cudaStream_t)stream));
 }
 
+gs_status gs_uncertainty_update(const float* mo_prev, const float* mo_cur, float* su, int64_t n, int32_t mode,
+                                void* stream) {
+  if (n < 0 || (mode != GS_U_ABS && mode != GS_U_SQ)) return GS_ERR_ARG;
+  if (n > 0 && (!mo_prev || !mo_cur || !su)) return GS_ERR_NULL;
+  if (!aligned(mo_prev, 16) || !aligned(mo_cur, 16) || !aligned(su, 16)) return GS_ERR_ALIGN;
+  return from_cuda(launch_uncertainty_update(mo_prev, mo_cur, su, n, mode == GS_U_SQ, (cudaStream_t)stream));
+}
+
+gs_status gs_uncertainty_thresholds(const gs_map* map, float ground_z, double* stats, void* ws, size_t ws_bytes,
+                                    void* stream) {
+  GS_TRY(check_map(map));
+  if (!stats) return GS_ERR_NULL;
+  if (!aligned(stats, 8)) return GS_ERR_ALIGN;
+  if (ground_z != ground_z) return GS_ERR_ARG;
+  GS_TRY(check_ws(ws, ws_bytes, thresholds_ws_bytes()));
+  return from_cuda(launch_uncertainty_thresholds(map->mo, map->su, map->n, ground_z, stats, ws, (cudaStream_t)stream));
+}
+
+gs_status gs_view_utility_batch(const gs_map* map, const gs_camera* cams, int32_t n_views,
+                                const gs_utility_params* prm, int32_t mode, const double* stats, float* xi_out,
+                                uint32_t* counts_out, void* ws, size_t ws_bytes, void* stream) {
+  GS_TRY(check_map(map));
+  GS_TRY(check_views(cams, n_views));
+  if (!prm || !xi_out) return GS_ERR_NULL;
+  if (mode != GS_XI && mode != GS_XI_SUM) return GS_ERR_ARG;
+  if (mode == GS_XI && !stats) return GS_ERR_NULL;
+  if (!(prm->near_plane > 0.f) || !(prm->range > prm->near_plane) || !(prm->lambda == prm->lambda) ||
+      prm->ground_z != prm->ground_z)
+    return GS_ERR_ARG;
+  if (!aligned(xi_out, 4) || !aligned(counts_out, 4) || !aligned(stats, 8)) return GS_ERR_ALIGN;
+  GS_TRY(check_ws(ws, ws_bytes, utility_ws_bytes(n_views)));
+  return from_cuda(launch_view_utility(map->mo, map->su, map->n, cams, n_views, *prm, mode, stats, xi_out, counts_out,
+                                       ws, (cudaStream_t)stream));
+}
+
+gs_status gs_region_uncertainty(const gs_map* map, const gs_region_grid* grid, float* omega_out, uint32_t* count_out,
+                                void* ws, size_t ws_bytes, void* stream) {
+  GS_TRY(check_map(map));
+  if (!grid || !omega_out) return GS_ERR_NULL;
+  if (!(grid->size > 0.f) || grid->dims[0] < 1 || grid->dims[1] < 1 || grid->dims[2] < 1) return GS_ERR_ARG;
+  const int64_t nr = (int64_t)grid->dims[0] * grid->dims[1] * grid->dims[2];
+  if (nr > ((int64_t)1 << 30)) return GS_ERR_ARG;
+  if (!aligned(omega_out, 4) || !aligned(count_out, 4)) return GS_ERR_ALIGN;
+  GS_TRY(check_ws(ws, ws_bytes, regions_ws_bytes(nr)));
+  return from_cuda(launch_regions(map->mo, map->su, map->n, *grid, omega_out, count_out, ws, (cudaStream_t)stream));
+}
+
 gs_status gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t rec_capacity, int64_t pair_capacity,
                             int64_t tile_capacity, size_t* bytes) {
   if (!bytes) return GS_ERR_NULL;
@@ -195,6 +242,9 @@ gs_status gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t rec_
     case GS_OP_RENDER_BWD: *bytes = bwd_ws_bytes(rec_capacity); return GS_OK;
     case GS_OP_INFO_GAIN: *bytes = ig_ws_bytes(n, n_views, rec_capacity, pair_capacity, tile_capacity); return GS_OK;
     case GS_OP_IG_COMPOSITE: *bytes = ig_composite_ws_bytes(tile_capacity); return GS_OK;
+    case GS_OP_THRESHOLDS: *bytes = thresholds_ws_bytes(); return GS_OK;
+    case GS_OP_VIEW_UTILITY: *bytes = utility_ws_bytes(n_views); return GS_OK;
+    case GS_OP_REGIONS: *bytes = regions_ws_bytes(rec_capacity); return GS_OK;
     default: return GS_ERR_ARG;
   }
 }

@@ -102,4 +102,18 @@ cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_vie
                              float* ig_out, uint32_t* status, int64_t rec_cap, int64_t pair_cap, int64_t tile_cap,
                              void* ws, cudaStream_t st);
 
+// render-free view utility (utility.cu)
+cudaError_t launch_uncertainty_update(const float* mo_prev, const float* mo_cur, float* su, int64_t n, int squared,
+                                      cudaStream_t st);
+size_t thresholds_ws_bytes();
+cudaError_t launch_uncertainty_thresholds(const float* mo, const float* su, int64_t n, float ground_z, double* stats,
+                                          void* ws, cudaStream_t st);
+size_t utility_ws_bytes(int n_views);
+cudaError_t launch_view_utility(const float* mo, const float* su, int64_t n, const gs_camera* cams, int n_views,
+                                const gs_utility_params& prm, int mode, const double* stats, float* xi,
+                                uint32_t* counts, void* ws, cudaStream_t st);
+size_t regions_ws_bytes(int64_t n_regions);
+cudaError_t launch_regions(const float* mo, const float* su, int64_t n, const gs_region_grid& grid, float* omega,
+                           uint32_t* count_out, void* ws, cudaStream_t st);
+
 }  // namespace gs

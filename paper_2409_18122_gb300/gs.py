@@ -423,6 +423,75 @@ class InfoGain:
         return False
 
 
+# ------------------------------------------------------- render-free view utility (Sec. IV-A/B)
+def uncertainty_update(mo_prev: torch.Tensor, mo_cur: torch.Tensor, su: torch.Tensor, squared: bool = False,
+                       stream=None):
+    """u = |mu_cur - mu_prev| (or its square) into su[:, 3] for Gaussians whose mean moved
+    (gs_uncertainty_update); the others keep their u."""
+    for t in (mo_prev, mo_cur, su):
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.dim() != 2 or t.shape[1] != 4:
+            raise ValueError("expected contiguous float32 CUDA tensors of shape [N, 4]")
+    L.check(L.lib().gs_uncertainty_update(_ptr(mo_prev), _ptr(mo_cur), _ptr(su), int(su.shape[0]),
+                                          L.GS_U_SQ if squared else L.GS_U_ABS, _stream(stream)),
+            "gs_uncertainty_update")
+
+
+class ViewUtility:
+    """Render-free utility xi of candidate poses (Eq. view_util; gs_view_utility_batch).
+
+    thresholds(): mean and sigma of u, high / low thresholds mean +- sigma / 2 (device double[5]);
+    __call__: xi per view (mode GS_XI: visible |G_H| - lambda |G_L|; GS_XI_SUM: sum of u over
+    the visible Gaussians) and, for GS_XI, the visible counts [V, 2]."""
+
+    def __init__(self, cams: Sequence, near_plane: float = 0.2, range_m: float = 5.0, lam: float = 1.0,
+                 ground_z: float = float("-inf"), device="cuda"):
+        self.device = torch.device(device)
+        self.cams = list(cams)
+        self.V = len(self.cams)
+        self.cams_dev = cameras_to_device(self.cams, self.device)
+        self.prm = L.gs_utility_params(near_plane, range_m, lam, ground_z)
+        self.stats = torch.zeros(5, dtype=torch.float64, device=self.device)
+        self.xi = torch.zeros(self.V, dtype=torch.float32, device=self.device)
+        self.counts = torch.zeros((self.V, 2), dtype=torch.int32, device=self.device)
+        self.ws_t = torch.empty(max(L.workspace_size(L.GS_OP_THRESHOLDS, 0, 1), 256), dtype=torch.uint8,
+                                device=self.device)
+        self.ws_u = torch.empty(max(L.workspace_size(L.GS_OP_VIEW_UTILITY, 0, self.V), 256), dtype=torch.uint8,
+                                device=self.device)
+
+    def thresholds(self, gmap: GaussianMapTensors, stream=None) -> torch.Tensor:
+        m = gmap.c()
+        _timed("gs_uncertainty_thresholds", stream, lambda: L.check(
+            L.lib().gs_uncertainty_thresholds(ctypes.byref(m), self.prm.ground_z, _ptr(self.stats), _ptr(self.ws_t),
+                                              self.ws_t.numel(), _stream(stream)), "gs_uncertainty_thresholds"))
+        return self.stats
+
+    def __call__(self, gmap: GaussianMapTensors, mode: int = 0, stats: Optional[torch.Tensor] = None,
+                 stream=None):
+        m = gmap.c()
+        st = self.stats if stats is None else stats
+        cnt = self.counts if mode == L.GS_XI else None
+        _timed("gs_view_utility_batch", stream, lambda: L.check(
+            L.lib().gs_view_utility_batch(ctypes.byref(m), _ptr(self.cams_dev), self.V, ctypes.byref(self.prm), mode,
+                                          _ptr(st), _ptr(self.xi), _ptr(cnt), _ptr(self.ws_u), self.ws_u.numel(),
+                                          _stream(stream)), "gs_view_utility_batch"))
+        return self.xi
+
+
+def region_uncertainty(gmap: GaussianMapTensors, origin, size: float, dims, stream=None):
+    """Mean u of every cuboid region (gs_region_uncertainty): (omega [R], count [R]),
+    region index (iz * dims[1] + iy) * dims[0] + ix."""
+    grid = L.gs_region_grid((ctypes.c_float * 3)(*origin), float(size), (ctypes.c_int32 * 3)(*dims))
+    R = int(dims[0]) * int(dims[1]) * int(dims[2])
+    dev = gmap.mo.device
+    omega = torch.zeros(R, dtype=torch.float32, device=dev)
+    count = torch.zeros(R, dtype=torch.int32, device=dev)
+    ws = torch.empty(max(L.workspace_size(L.GS_OP_REGIONS, gmap.n, 1, R), 256), dtype=torch.uint8, device=dev)
+    m = gmap.c()
+    L.check(L.lib().gs_region_uncertainty(ctypes.byref(m), ctypes.byref(grid), _ptr(omega), _ptr(count), _ptr(ws),
+                                          ws.numel(), _stream(stream)), "gs_region_uncertainty")
+    return omega, count
+
+
 # ---------------------------------------------------------------------- tile autotuner
 TILE_CANDIDATES = ((16, 16), (16, 8), (8, 8), (32, 8), (32, 16), (32, 32))
 

@@ -44,6 +44,7 @@ def test_struct_layouts_match_header(tmp_path):
     structs = {
         "gs_camera": L.gs_camera, "gs_map": L.gs_map, "gs_params": L.gs_params, "gs_proj": L.gs_proj,
         "gs_bins": L.gs_bins, "gs_image": L.gs_image, "gs_image_grad": L.gs_image_grad, "gs_map_grad": L.gs_map_grad,
+        "gs_utility_params": L.gs_utility_params, "gs_region_grid": L.gs_region_grid,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gs.h"', "int main(void) {"]
     for s, cls in structs.items():
