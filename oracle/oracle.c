@@ -94,6 +94,11 @@ float ex32(float x) {
   return p * scale;
 }
 
+/* ex32 of every element (the collision check's radii). */
+void or_ex32v(int64_t n, const float* x, float* y) {
+  for (int64_t i = 0; i < n; ++i) y[i] = ex32(x[i]);
+}
+
 /* ln y for finite y > 0 (normal): y = m 2^e with m in [sqrt(1/2), sqrt(2)),
  * ln m = 2 atanh(s), s = (m-1)/(m+1), by the odd series 2(s + s^3/3 + ... + s^13/13);
  * ln y = e ln2 + ln m with the same two-part ln 2. */

@@ -24,6 +24,9 @@ Functions and the passages they follow (RT-GuIDE, arXiv 2409.18122):
                |visible G_L| (or the sum of u of the visible Gaussians); visible =
                in the field of view and within the perception range.
   region_uncertainty   Sec. IV-B high-level planner: mean u of cuboid regions.
+  trajectory_utility   Eq. traj_utility: sum of xi over a trajectory's states, best one.
+  collision_check      Sec. IV-B collision checking: distance of each test point to every
+               Gaussian against r_robot + lambda_g r (principal axis as the radius).
 """
 from __future__ import annotations
 
@@ -62,6 +65,8 @@ def _load():
         lib.or_num_threads.restype = I
         lib.ex32.argtypes = [ctypes.c_float]
         lib.ex32.restype = ctypes.c_float
+        lib.or_ex32v.argtypes = [I64, P, P]
+        lib.or_ex32v.restype = None
         lib.lg32.argtypes = [ctypes.c_float]
         lib.lg32.restype = ctypes.c_float
         lib.or_project.argtypes = [I64, P, P, P, P, P, P, I, P, P, P, P, P, P, P, P, P, P, P]
@@ -384,3 +389,44 @@ def region_uncertainty(mo: np.ndarray, u: np.ndarray, origin, size: float, dims)
     tot = np.bincount(r, weights=u[inside].astype(np.float64), minlength=R)
     mean = np.where(cnt > 0, tot / np.maximum(cnt, 1), 0.0)
     return mean, cnt
+
+
+def trajectory_utility(mo: np.ndarray, u: np.ndarray, cams, n_traj: int, n_states: int, **kw):
+    """Eq. traj_utility: per trajectory the sum over its states (cams[t * n_states + l]) of
+    view_utility, and the first trajectory with the largest sum."""
+    xi, _ = view_utility(mo, u, cams, **kw)
+    s = xi.reshape(n_traj, n_states).sum(axis=1)
+    return s, int(np.argmax(s))
+
+
+def ex32v(x: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float32)
+    y = np.empty_like(x)
+    _load().or_ex32v(x.size, _p(x), _p(y))
+    return y
+
+
+def collision_check(mo: np.ndarray, su: np.ndarray, points: np.ndarray, r_robot: float, lambda_g: float = 3.0,
+                    ground_z: float = -np.inf):
+    """Sec. IV-B collision checking: for every test point, the smallest |p - mu_i| - gamma_i
+    (FP64) over the Gaussians with mu_z >= ground_z, gamma_i = r_robot + lambda_g r_i with
+    r_i = exp(largest log-scale), and whether some |p - mu_i|^2 < gamma_i^2 -- decided in
+    float32 like the kernel: d = p - mu, |d|^2 = (dx dx + dy dy) + dz dz, gamma = r_robot +
+    lambda_g r, r from ex32.  Returns (margin [M], collides [M])."""
+    f = np.float32
+    keep = mo[:, 2] >= f(ground_z)
+    mu = mo[keep, :3].astype(f)
+    r = ex32v(su[keep, :3].max(axis=1))
+    gam = f(r_robot) + f(lambda_g) * r
+    gam2 = gam * gam
+    gam64 = gam.astype(np.float64)
+    margin = np.full(len(points), np.inf)
+    hit = np.zeros(len(points), bool)
+    for k, p in enumerate(np.asarray(points, f)[:, :3]):
+        d = p[None, :] - mu
+        d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+        hit[k] = bool((d2 < gam2).any())
+        if len(mu):
+            exact = np.sqrt(((p.astype(np.float64)[None, :] - mu.astype(np.float64)) ** 2).sum(axis=1))
+            margin[k] = (exact - gam64).min()
+    return margin, hit

@@ -478,3 +478,36 @@ def test_region_uncertainty_hand_means():
     # region (0,0): first two; (1,0): the third; (1,1): the fourth; the last two lie outside
     np.testing.assert_array_equal(cnt, [2, 1, 0, 1])
     np.testing.assert_allclose(mean, [2.0, 5.0, 0.0, 7.0])
+
+
+def test_trajectory_utility_hand_sums_and_first_argmax():
+    """Three trajectories of two states; state utilities known by construction: a pose that
+    sees the two highest-u Gaussians, one that sees the two lowest, one that sees nothing."""
+    mo = _mo([[0, 0, 3], [0.1, 0, 3], [0, 0, -3], [0.1, 0, -3], [5, 5, 5], [5, 5, 6]])
+    u = np.array([9.0, 8.0, 0.0, 1.0, 4.0, 5.0])      # mean 4.5, sigma ~3.3: G_H = {9, 8}, G_L = {0, 1}
+    see_hi = Camera(100.0, 100.0, 50.0, 40.0, 100, 80)
+    see_lo = Camera(100.0, 100.0, 50.0, 40.0, 100, 80, Rotation.from_euler("y", np.pi).as_matrix(), [0, 0, 0])
+    blind = Camera(100.0, 100.0, 50.0, 40.0, 100, 80, np.eye(3), [0, 0, 50])
+    cams = [see_hi, blind, see_lo, see_lo, see_hi, see_lo]      # xi: 2, 0 | -2, -2 | 2, -2
+    s, best = O.trajectory_utility(mo, u, cams, 3, 2)
+    np.testing.assert_array_equal(s, [2.0, -4.0, 0.0])
+    assert best == 0
+    s2, best2 = O.trajectory_utility(mo, u, [see_hi, see_hi, blind, blind, see_hi, see_hi], 3, 2)
+    assert list(s2) == [4.0, 0.0, 4.0] and best2 == 0             # ties: the first
+
+
+def test_collision_check_closed_form():
+    """One Gaussian at the origin with principal axis 0.2 m: gamma = 0.3 + 3 * 0.2 = 0.9 m."""
+    mo = _mo([[0, 0, 0], [10, 0, 0]])
+    su = np.zeros((2, 4), np.float32)
+    su[0, :3] = np.log([0.1, 0.2, 0.05])
+    su[1, :3] = np.log([0.01, 0.01, 0.01])
+    pts = np.zeros((4, 4), np.float32)
+    pts[:, 0] = [0.5, 1.0, 9.95, 5.0]
+    margin, hit = O.collision_check(mo, su, pts, r_robot=0.3, lambda_g=3.0)
+    r0 = float(O.ex32(np.log(np.float32(0.2))))
+    g0, g1 = 0.3 + 3 * r0, 0.3 + 3 * float(O.ex32(np.log(np.float32(0.01))))
+    np.testing.assert_allclose(margin, [0.5 - g0, 1.0 - g0, 0.05 - g1, min(5.0 - g0, 5.0 - g1)], rtol=1e-6)
+    np.testing.assert_array_equal(hit, [True, False, True, False])
+    m2, h2 = O.collision_check(mo, su, pts, 0.3, 3.0, ground_z=5.0)     # every Gaussian removed
+    assert np.isinf(m2).all() and not h2.any()
