@@ -400,6 +400,30 @@ gs_status gs_view_utility_batch(const gs_map* map, const gs_camera* cams, int32_
                                 const gs_utility_params* prm, int32_t mode, const double* stats, float* xi_out,
                                 uint32_t* counts_out, void* ws, size_t ws_bytes, void* stream);
 
+/* gs_trajectory_utility -- Eq. traj_utility: n_traj trajectories of n_states states
+ * each (cams[t * n_states + l] is state l of trajectory t); traj_out[t] = sum over l of
+ * xi (as gs_view_utility_batch, summed in FP64 in state order), best_out[0] = the first t
+ * with the largest sum.  traj_out: DEVICE float[n_traj]; best_out: DEVICE int32[1].
+ * ws: gs_workspace_size(GS_OP_TRAJECTORY, ...) with n_views = n_traj * n_states.
+ * Errors: as gs_view_utility_batch. */
+gs_status gs_trajectory_utility(const gs_map* map, const gs_camera* cams, int32_t n_traj, int32_t n_states,
+                                const gs_utility_params* prm, int32_t mode, const double* stats, float* traj_out,
+                                int32_t* best_out, void* ws, size_t ws_bytes, void* stream);
+
+/* gs_collision_check -- Sec. IV-B collision checking with all Gaussians: for every
+ * test point p_k (DEVICE float[n_points][4], position in the first three),
+ * margin_out[k] = min over the Gaussians with mu_z >= ground_z of |p_k - mu_i| - gamma_i,
+ * gamma_i = r_robot + lambda_g r_i, r_i = exp(largest log-scale) (the principal axis
+ * as the radius); +INFINITY if there is no Gaussian.  collides_out[k] = 1 iff some
+ * Gaussian has |p_k - mu_i|^2 < gamma_i^2, decided in FP32 with separately rounded
+ * operations: d = p - mu, |d|^2 = (dx dx + dy dy) + dz dz, gamma = r_robot + lambda_g r,
+ * gamma^2 = gamma gamma, r from the library's FP32 exp (Cody-Waite).  Deterministic.
+ * margin_out: DEVICE float[n_points]; collides_out: DEVICE uint32[n_points].
+ * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG, GS_ERR_CUDA. */
+gs_status gs_collision_check(const gs_map* map, const float* points, int32_t n_points, float r_robot,
+                             float lambda_g, float ground_z, float* margin_out, uint32_t* collides_out,
+                             void* stream);
+
 /* gs_region_uncertainty -- Sec. IV-B high-level planner: mean uncertainty of each
  * cuboid region, Omega_o = (1/M_o) sum over the region's Gaussians of u (0 if M_o = 0).
  * omega_out: DEVICE float[R], count_out: DEVICE uint32[R] (M_o) or NULL,
@@ -418,7 +442,8 @@ enum {
   GS_OP_IG_COMPOSITE = 4,
   GS_OP_THRESHOLDS = 5,
   GS_OP_VIEW_UTILITY = 6,
-  GS_OP_REGIONS = 7
+  GS_OP_REGIONS = 7,
+  GS_OP_TRAJECTORY = 8
 };
 
 /* gs_workspace_size -- HOST.  Bytes of workspace `op` needs:
@@ -427,7 +452,8 @@ enum {
  *                   argument, 0 for n * n_views; GS_OP_REGIONS: the number of regions)
  *   pair_capacity   pair capacity of the gs_bins in use
  *   tile_capacity   tile capacity of the gs_bins in use (GS_OP_IG_COMPOSITE: only this is used)
- * GS_OP_THRESHOLDS needs nothing else; GS_OP_VIEW_UTILITY only n_views.
+ * GS_OP_THRESHOLDS needs nothing else; GS_OP_VIEW_UTILITY and GS_OP_TRAJECTORY only n_views
+ * (for GS_OP_TRAJECTORY: the total number of states).
  * Writes the byte count to *bytes (HOST).  Errors: GS_ERR_NULL, GS_ERR_ARG, GS_ERR_CUDA. */
 gs_status gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t rec_capacity, int64_t pair_capacity,
                             int64_t tile_capacity, size_t* bytes);

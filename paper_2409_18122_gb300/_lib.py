@@ -25,7 +25,7 @@ GS_FLAG_ERROR_MASK = (GS_FLAG_PAIR_OVERFLOW | GS_FLAG_RANGE_OVERFLOW | GS_FLAG_B
                       | GS_FLAG_BAD_RECORDS)
 GS_IG_RENDER_MEAN = 0
 (GS_OP_PROJECT, GS_OP_BIN_SORT, GS_OP_RENDER_BWD, GS_OP_INFO_GAIN, GS_OP_IG_COMPOSITE, GS_OP_THRESHOLDS,
- GS_OP_VIEW_UTILITY, GS_OP_REGIONS) = range(8)
+ GS_OP_VIEW_UTILITY, GS_OP_REGIONS, GS_OP_TRAJECTORY) = range(9)
 GS_U_ABS, GS_U_SQ = 0, 1
 GS_XI, GS_XI_SUM = 0, 1
 GS_NOALLOC_MAX_RECORDS = 1 << 18
@@ -89,6 +89,10 @@ PROTOTYPES = {
                                         c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "gs_region_uncertainty": (c_int32, [POINTER(gs_map), POINTER(gs_region_grid), c_void_p, c_void_p, c_void_p,
                                         c_size_t, c_void_p]),
+    "gs_trajectory_utility": (c_int32, [POINTER(gs_map), c_void_p, c_int32, c_int32, POINTER(gs_utility_params),
+                                        c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "gs_collision_check": (c_int32, [POINTER(gs_map), c_void_p, c_int32, c_float, c_float, c_float, c_void_p,
+                                     c_void_p, c_void_p]),
     "gs_project": (c_int32, [POINTER(gs_map), c_void_p, c_int32, POINTER(gs_params), POINTER(gs_proj), c_void_p,
                              c_size_t, c_void_p]),
     "gs_bin_sort": (c_int32, [POINTER(gs_proj), c_void_p, c_int32, POINTER(gs_params), POINTER(gs_bins), c_void_p,

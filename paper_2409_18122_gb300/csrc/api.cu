@@ -220,6 +220,35 @@ gs_status gs_view_utility_batch(const gs_map* map, const gs_camera* cams, int32_
                                        ws, (cudaStream_t)stream));
 }
 
+gs_status gs_trajectory_utility(const gs_map* map, const gs_camera* cams, int32_t n_traj, int32_t n_states,
+                                const gs_utility_params* prm, int32_t mode, const double* stats, float* traj_out,
+                                int32_t* best_out, void* ws, size_t ws_bytes, void* stream) {
+  GS_TRY(check_map(map));
+  if (n_traj < 1 || n_states < 1 || (int64_t)n_traj * n_states > (1 << 20)) return GS_ERR_ARG;
+  GS_TRY(check_views(cams, n_traj * n_states));
+  if (!prm || !traj_out || !best_out) return GS_ERR_NULL;
+  if (mode != GS_XI && mode != GS_XI_SUM) return GS_ERR_ARG;
+  if (mode == GS_XI && !stats) return GS_ERR_NULL;
+  if (!(prm->near_plane > 0.f) || !(prm->range > prm->near_plane) || !(prm->lambda == prm->lambda) ||
+      prm->ground_z != prm->ground_z)
+    return GS_ERR_ARG;
+  if (!aligned(traj_out, 4) || !aligned(best_out, 4) || !aligned(stats, 8)) return GS_ERR_ALIGN;
+  GS_TRY(check_ws(ws, ws_bytes, trajectory_ws_bytes(n_traj * n_states)));
+  return from_cuda(launch_trajectory_utility(map->mo, map->su, map->n, cams, n_traj, n_states, *prm, mode, stats,
+                                             traj_out, best_out, ws, (cudaStream_t)stream));
+}
+
+gs_status gs_collision_check(const gs_map* map, const float* points, int32_t n_points, float r_robot,
+                             float lambda_g, float ground_z, float* margin_out, uint32_t* collides_out,
+                             void* stream) {
+  GS_TRY(check_map(map));
+  if (n_points < 0 || !(r_robot >= 0.f) || !(lambda_g >= 0.f) || ground_z != ground_z) return GS_ERR_ARG;
+  if (n_points > 0 && (!points || !margin_out || !collides_out)) return GS_ERR_NULL;
+  if (!aligned(points, 16) || !aligned(margin_out, 4) || !aligned(collides_out, 4)) return GS_ERR_ALIGN;
+  return from_cuda(launch_collision_check(map->mo, map->su, map->n, points, n_points, r_robot, lambda_g, ground_z,
+                                          margin_out, collides_out, (cudaStream_t)stream));
+}
+
 gs_status gs_region_uncertainty(const gs_map* map, const gs_region_grid* grid, float* omega_out, uint32_t* count_out,
                                 void* ws, size_t ws_bytes, void* stream) {
   GS_TRY(check_map(map));
@@ -245,6 +274,7 @@ gs_status gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t rec_
     case GS_OP_THRESHOLDS: *bytes = thresholds_ws_bytes(); return GS_OK;
     case GS_OP_VIEW_UTILITY: *bytes = utility_ws_bytes(n_views); return GS_OK;
     case GS_OP_REGIONS: *bytes = regions_ws_bytes(rec_capacity); return GS_OK;
+    case GS_OP_TRAJECTORY: *bytes = trajectory_ws_bytes(n_views); return GS_OK;
     default: return GS_ERR_ARG;
   }
 }

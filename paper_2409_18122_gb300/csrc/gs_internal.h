@@ -112,6 +112,13 @@ size_t utility_ws_bytes(int n_views);
 cudaError_t launch_view_utility(const float* mo, const float* su, int64_t n, const gs_camera* cams, int n_views,
                                 const gs_utility_params& prm, int mode, const double* stats, float* xi,
                                 uint32_t* counts, void* ws, cudaStream_t st);
+size_t trajectory_ws_bytes(int n_states_total);
+cudaError_t launch_trajectory_utility(const float* mo, const float* su, int64_t n, const gs_camera* cams, int n_traj,
+                                      int n_states, const gs_utility_params& prm, int mode, const double* stats,
+                                      float* traj_out, int32_t* best_out, void* ws, cudaStream_t st);
+cudaError_t launch_collision_check(const float* mo, const float* su, int64_t n, const float* pts, int n_pts,
+                                   float r_robot, float lambda_g, float ground_z, float* margin_out,
+                                   uint32_t* collides_out, cudaStream_t st);
 size_t regions_ws_bytes(int64_t n_regions);
 cudaError_t launch_regions(const float* mo, const float* su, int64_t n, const gs_region_grid& grid, float* omega,
                            uint32_t* count_out, void* ws, cudaStream_t st);

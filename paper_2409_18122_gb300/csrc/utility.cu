@@ -249,6 +249,111 @@ __global__ void k_region_mean(const double* __restrict__ sum, const uint32_t* __
     omega[r] = count[r] ? (float)(sum[r] / (double)count[r]) : 0.f;
 }
 
+// Trajectory information (Eq. traj_utility): per trajectory the sum over its states
+// of xi (states l = 0..L in order, FP64), and the first trajectory with the largest sum.
+__global__ void k_traj_sum(const float* __restrict__ xi, int n_traj, int n_states, float* __restrict__ out,
+                           int32_t* __restrict__ best) {
+  __shared__ double s_best[256];
+  __shared__ int s_idx[256];
+  double bv = -INFINITY;
+  int bi = 0x7fffffff;
+  for (int t = threadIdx.x; t < n_traj; t += blockDim.x) {
+    double acc = 0.0;
+    for (int l = 0; l < n_states; ++l) acc += (double)xi[(size_t)t * n_states + l];
+    out[t] = (float)acc;
+    if (acc > bv) { bv = acc; bi = t; }
+  }
+  s_best[threadIdx.x] = bv;
+  s_idx[threadIdx.x] = bi;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = -INFINITY;
+    int i = 0x7fffffff;
+    for (int k = 0; k < (int)blockDim.x; ++k)
+      if (s_best[k] > v || (s_best[k] == v && s_idx[k] < i)) { v = s_best[k]; i = s_idx[k]; }
+    *best = n_traj > 0 ? i : -1;
+  }
+}
+
+// Collision check (Sec. IV-B): ordered integer key of a float, so that unsigned
+// minimum = float minimum.
+__device__ __forceinline__ uint32_t fkey(float f) {
+  const uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+constexpr int kColChunk = 4096;   // Gaussians per block of the collision kernel
+constexpr int kColTile = 256;     // Gaussians staged in shared memory at a time
+
+// Per block: a chunk of Gaussians against every test point (one point per thread,
+// the Gaussians broadcast from shared memory).  Each thread keeps its point's
+// smallest margin |p - mu| - gamma (a square root only when the pair can beat it)
+// and whether some Gaussian has |p - mu|^2 < gamma^2 (separately rounded FP32).
+__global__ void __launch_bounds__(kBlock) k_collision(const float4* __restrict__ mo, const float4* __restrict__ su,
+                                                      int64_t n, const float4* __restrict__ pts, int n_pts,
+                                                      float r_robot, float lambda_g, float ground_z,
+                                                      uint32_t* __restrict__ margin_key, uint32_t* __restrict__ hit) {
+  __shared__ float4 s_g[kColTile];   // (mu, gamma)
+  const int64_t g0 = (int64_t)blockIdx.x * kColChunk;
+  int64_t g1 = g0 + kColChunk;
+  if (g1 > n) g1 = n;
+  for (int p0 = 0; p0 < n_pts; p0 += kBlock) {
+    const int pi = p0 + threadIdx.x;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pi < n_pts) p = pts[pi];
+    float best = INFINITY;
+    bool col = false;
+    for (int64_t t0 = g0; t0 < g1; t0 += kColTile) {
+      __syncthreads();
+      const int64_t gi = t0 + threadIdx.x;
+      float4 e = make_float4(0.f, 0.f, 0.f, -1.f);   // gamma < 0: no Gaussian
+      if (gi < g1) {
+        const float4 m = mo[gi];
+        if (m.z >= ground_z) {
+          const float4 s = su[gi];
+          const float r = ex32(fmaxf(fmaxf(s.x, s.y), s.z));   // principal axis
+          e = make_float4(m.x, m.y, m.z, __fadd_rn(r_robot, __fmul_rn(lambda_g, r)));
+        }
+      }
+      s_g[threadIdx.x] = e;
+      __syncthreads();
+      const int cnt = (int)(g1 - t0 < kColTile ? g1 - t0 : kColTile);
+      if (pi < n_pts) {
+        for (int k = 0; k < cnt; ++k) {
+          const float4 g = s_g[k];
+          if (!(g.w >= 0.f)) continue;
+          const float dx = __fsub_rn(p.x, g.x), dy = __fsub_rn(p.y, g.y), dz = __fsub_rn(p.z, g.z);
+          const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+          col |= d2 < __fmul_rn(g.w, g.w);
+          const float lim = g.w + best;   // a smaller margin needs |p - mu| < gamma + best
+          if (lim > 0.f && d2 < lim * lim) best = fminf(best, sqrtf(d2) - g.w);
+        }
+      }
+    }
+    if (pi < n_pts) {
+      if (best < INFINITY) atomicMin(&margin_key[pi], fkey(best));
+      if (col) atomicOr(&hit[pi], 1u);
+    }
+  }
+}
+
+__global__ void k_collision_init(uint32_t* __restrict__ margin_key, uint32_t* __restrict__ hit, int n_pts) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pts; i += gridDim.x * blockDim.x) {
+    margin_key[i] = fkey(INFINITY);
+    hit[i] = 0u;
+  }
+}
+
+__global__ void k_collision_finish(uint32_t* __restrict__ margin, int n_pts) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pts; i += gridDim.x * blockDim.x) {
+    const uint32_t k = margin[i];
+    reinterpret_cast<float*>(margin)[i] = fkey_inv(k);
+  }
+}
+
 __global__ void k_zero_bytes(uint8_t* p, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = 0;
 }
@@ -354,6 +459,44 @@ cudaError_t launch_regions(const float* mo, const float* su, int64_t n, const gs
   int64_t g2 = (nr + 255) / 256;
   if (g2 > 4096) g2 = 4096;
   k_region_mean<<<(unsigned)(g2 < 1 ? 1 : g2), 256, 0, st>>>(sum, cnt, nr, omega);
+  note_launch();
+  return cudaGetLastError();
+}
+
+size_t trajectory_ws_bytes(int n_states_total) {
+  return utility_ws_bytes(n_states_total) + align_up(sizeof(float) * (size_t)n_states_total, 256);
+}
+
+cudaError_t launch_trajectory_utility(const float* mo, const float* su, int64_t n, const gs_camera* cams, int n_traj,
+                                      int n_states, const gs_utility_params& prm, int mode, const double* stats,
+                                      float* traj_out, int32_t* best_out, void* ws, cudaStream_t st) {
+  const int total = n_traj * n_states;
+  Carver c(ws);
+  void* uws = c.take<char>(utility_ws_bytes(total));
+  float* xi = c.take<float>((size_t)total);
+  cudaError_t e = launch_view_utility(mo, su, n, cams, total, prm, mode, stats, xi, nullptr, uws, st);
+  if (e != cudaSuccess) return e;
+  k_traj_sum<<<1, 256, 0, st>>>(xi, n_traj, n_states, traj_out, best_out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collision_check(const float* mo, const float* su, int64_t n, const float* pts, int n_pts,
+                                   float r_robot, float lambda_g, float ground_z, float* margin_out,
+                                   uint32_t* collides_out, cudaStream_t st) {
+  uint32_t* key = reinterpret_cast<uint32_t*>(margin_out);
+  const int ib = (n_pts + 255) / 256;
+  k_collision_init<<<ib < 1 ? 1 : ib, 256, 0, st>>>(key, collides_out, n_pts);
+  note_launch();
+  if (n > 0 && n_pts > 0) {
+    const int64_t blocks = (n + kColChunk - 1) / kColChunk;
+    k_collision<<<(unsigned)blocks, kBlock, 0, st>>>(reinterpret_cast<const float4*>(mo),
+                                                     reinterpret_cast<const float4*>(su), n,
+                                                     reinterpret_cast<const float4*>(pts), n_pts, r_robot, lambda_g,
+                                                     ground_z, key, collides_out);
+    note_launch();
+  }
+  k_collision_finish<<<ib < 1 ? 1 : ib, 256, 0, st>>>(key, n_pts);
   note_launch();
   return cudaGetLastError();
 }

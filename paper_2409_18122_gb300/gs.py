@@ -477,6 +477,41 @@ class ViewUtility:
         return self.xi
 
 
+def trajectory_utility(vu: "ViewUtility", gmap: GaussianMapTensors, n_traj: int, n_states: int, mode: int = 0,
+                       stream=None):
+    """Eq. traj_utility over the poses of `vu` (state l of trajectory t at index t * n_states + l):
+    (per-trajectory sum of xi [n_traj], index of the best trajectory).  For GS_XI the
+    thresholds of vu (vu.thresholds) are used."""
+    if n_traj * n_states != vu.V:
+        raise ValueError("the ViewUtility must hold n_traj * n_states poses")
+    out = torch.zeros(n_traj, dtype=torch.float32, device=vu.device)
+    best = torch.zeros(1, dtype=torch.int32, device=vu.device)
+    ws = torch.empty(max(L.workspace_size(L.GS_OP_TRAJECTORY, gmap.n, vu.V), 256), dtype=torch.uint8,
+                     device=vu.device)
+    m = gmap.c()
+    L.check(L.lib().gs_trajectory_utility(ctypes.byref(m), _ptr(vu.cams_dev), n_traj, n_states, ctypes.byref(vu.prm),
+                                          mode, _ptr(vu.stats), _ptr(out), _ptr(best), _ptr(ws), ws.numel(),
+                                          _stream(stream)), "gs_trajectory_utility")
+    return out, best
+
+
+def collision_check(gmap: GaussianMapTensors, points: torch.Tensor, r_robot: float, lambda_g: float = 3.0,
+                    ground_z: float = float("-inf"), stream=None):
+    """Smallest margin |p - mu| - (r_robot + lambda_g r) of every test point over all Gaussians
+    and whether it collides (gs_collision_check).  points: CUDA float32 [M, 4] (xyz, -)."""
+    if points.dtype != torch.float32 or not points.is_cuda or points.dim() != 2 or points.shape[1] != 4:
+        raise ValueError("points must be a CUDA float32 tensor of shape [M, 4]")
+    pts = points.contiguous()
+    M = int(pts.shape[0])
+    margin = torch.empty(max(M, 1), dtype=torch.float32, device=pts.device)
+    hit = torch.empty(max(M, 1), dtype=torch.int32, device=pts.device)
+    m = gmap.c()
+    L.check(L.lib().gs_collision_check(ctypes.byref(m), _ptr(pts), M, float(r_robot), float(lambda_g),
+                                       float(ground_z), _ptr(margin), _ptr(hit), _stream(stream)),
+            "gs_collision_check")
+    return margin[:M], hit[:M]
+
+
 def region_uncertainty(gmap: GaussianMapTensors, origin, size: float, dims, stream=None):
     """Mean u of every cuboid region (gs_region_uncertainty): (omega [R], count [R]),
     region index (iz * dims[1] + iy) * dims[0] + ix."""

@@ -127,3 +127,38 @@ def test_region_uncertainty_vs_oracle():
     ref, ref_cnt = O.region_uncertainty(gmap.mo, gmap.su[:, 3], (0.0, 0.0, 0.0), 2.5, (4, 4, 2))
     np.testing.assert_array_equal(count.cpu().numpy(), ref_cnt)
     np.testing.assert_allclose(omega.cpu().numpy(), ref, rtol=1e-6, atol=0)
+
+
+def test_trajectory_utility_vs_oracle():
+    gmap, _ = _scene(n=30_000, seed=12)
+    rng = np.random.default_rng(12)
+    n_traj, n_states = 6, 4
+    cams = []
+    for t in range(n_traj):
+        x, y = rng.uniform(2, 8, 2)
+        yaw = rng.uniform(0, 2 * np.pi)
+        for l in range(n_states):   # a short straight path with a slight turn
+            cams.append(scenes.yaw_camera(x + 0.3 * l * np.cos(yaw), y + 0.3 * l * np.sin(yaw), 1.5,
+                                          yaw + 0.1 * l, 160, 120, 131.25))
+    gm = gs.GaussianMapTensors.from_numpy(gmap)
+    vu = gs.ViewUtility(cams)
+    st = _thr_gpu(gm, vu)
+    s, best = gs.trajectory_utility(vu, gm, n_traj, n_states)
+    ref, ref_best = O.trajectory_utility(gmap.mo, gmap.su[:, 3], cams, n_traj, n_states,
+                                         thresholds=tuple(float(x) for x in st))
+    np.testing.assert_array_equal(s.cpu().numpy(), ref.astype(np.float32))
+    assert int(best.item()) == ref_best
+
+
+def test_collision_check_vs_oracle():
+    gmap, _ = _scene(n=50_000, seed=13)
+    rng = np.random.default_rng(13)
+    pts = np.zeros((129, 4), np.float32)
+    pts[:, :3] = rng.uniform([0, 0, 0.2], [10, 10, 2.5], (129, 3))
+    gm = gs.GaussianMapTensors.from_numpy(gmap)
+    for r_robot, lam, gz in ((0.25, 3.0, float("-inf")), (0.05, 1.0, 0.3)):
+        margin, hit = gs.collision_check(gm, torch.from_numpy(pts).cuda(), r_robot, lam, gz)
+        ref_m, ref_h = O.collision_check(gmap.mo, gmap.su, pts, r_robot, lam, gz)
+        np.testing.assert_array_equal(hit.cpu().numpy().astype(bool), ref_h)
+        np.testing.assert_allclose(margin.cpu().numpy(), ref_m, rtol=1e-5, atol=2e-6)
+        assert 0 < ref_h.sum() < len(pts)
