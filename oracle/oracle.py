@@ -27,6 +27,9 @@ Functions and the passages they follow (RT-GuIDE, arXiv 2409.18122):
   trajectory_utility   Eq. traj_utility: sum of xi over a trajectory's states, best one.
   collision_check      Sec. IV-B collision checking: distance of each test point to every
                Gaussian against r_robot + lambda_g r (principal axis as the radius).
+  ssim_map / mapping_loss  Eq. 3: L1 depth + lambda_1 L1 colour + lambda_2 (1 - SSIM), SSIM with
+               the 11 x 11 Gaussian window (sigma 1.5, zero outside the image; the paper
+               does not state the window), and the gradient with respect to the images.
 """
 from __future__ import annotations
 
@@ -430,3 +433,71 @@ def collision_check(mo: np.ndarray, su: np.ndarray, points: np.ndarray, r_robot:
             exact = np.sqrt(((p.astype(np.float64)[None, :] - mu.astype(np.float64)) ** 2).sum(axis=1))
             margin[k] = (exact - gam64).min()
     return margin, hit
+
+
+# ------------------------------------------------------------------ mapping loss (Eq. 3)
+SSIM_C1, SSIM_C2 = 0.01 ** 2, 0.03 ** 2
+
+
+def ssim_window(size: int = 11, sigma: float = 1.5) -> np.ndarray:
+    """Normalised 1D Gaussian window; the 2D window is its outer product."""
+    k = np.arange(size, dtype=np.float64) - (size - 1) / 2
+    g = np.exp(-k * k / (2 * sigma * sigma))
+    return g / g.sum()
+
+
+def blur(img: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """Same-size correlation of a 2D image with the window outer(g, g), zero outside the image."""
+    from scipy.signal import correlate2d
+    return correlate2d(img, np.outer(g, g), mode="same", boundary="fill", fillvalue=0.0)
+
+
+def ssim_map(x: np.ndarray, y: np.ndarray, g=None):
+    """Per-pixel SSIM of two single-channel images (FP64):
+    ((2 mu_x mu_y + C1)(2 s_xy + C2)) / ((mu_x^2 + mu_y^2 + C1)(s_x^2 + s_y^2 + C2)) with the
+    windowed means mu = G*x, variances G*x^2 - mu^2 and covariance G*(xy) - mu_x mu_y."""
+    g = ssim_window() if g is None else g
+    mx, my = blur(x, g), blur(y, g)
+    sxx = blur(x * x, g) - mx * mx
+    syy = blur(y * y, g) - my * my
+    sxy = blur(x * y, g) - mx * my
+    return ((2 * mx * my + SSIM_C1) * (2 * sxy + SSIM_C2)) / ((mx * mx + my * my + SSIM_C1) * (sxx + syy + SSIM_C2))
+
+
+def mapping_loss(rgb, depth, rgb_ref, depth_ref, w_d: float = 1.0, w_c: float = 0.4, w_s: float = 0.1):
+    """Eq. 3 for one view (rgb [3,H,W], depth [H,W]):
+    L = (1/N_p) sum_p (w_d |d - d_ref| + w_c |c - c_ref|_1) + w_s (1 - SSIM(c, c_ref)),
+    SSIM = mean over the three channels and all pixels of ssim_map.  Returns (L, dL/drgb,
+    dL/ddepth) in FP64; sign(0) = 0 for the L1 terms.  The SSIM gradient follows the moments:
+    with m1 = G*x, m2 = G*x^2, m12 = G*(x y), dS/dx = G*(dS/dm1) + 2 x G*(dS/dm2) + y G*(dS/dm12)
+    (the window is symmetric, so the adjoint of the zero-padded correlation is itself)."""
+    g = ssim_window()
+    rgb = np.asarray(rgb, np.float64)
+    rgb_ref = np.asarray(rgb_ref, np.float64)
+    depth = np.asarray(depth, np.float64)
+    depth_ref = np.asarray(depth_ref, np.float64)
+    N = depth.shape[0] * depth.shape[1]
+    dd = depth - depth_ref
+    dc = rgb - rgb_ref
+    loss = (w_d * np.abs(dd).sum() + w_c * np.abs(dc).sum()) / N
+    g_depth = w_d * np.sign(dd) / N
+    g_rgb = w_c * np.sign(dc) / N
+    s_tot = 0.0
+    for ch in range(3):
+        x, y = rgb[ch], rgb_ref[ch]
+        m1, my = blur(x, g), blur(y, g)
+        m2, m12 = blur(x * x, g), blur(x * y, g)
+        syy = blur(y * y, g) - my * my
+        A1 = 2 * m1 * my + SSIM_C1
+        A2 = 2 * (m12 - m1 * my) + SSIM_C2
+        B1 = m1 * m1 + my * my + SSIM_C1
+        B2 = m2 - m1 * m1 + syy + SSIM_C2
+        S = A1 * A2 / (B1 * B2)
+        s_tot += S.sum()
+        dm1 = 2 * my * (A2 - A1) / (B1 * B2) - 2 * m1 * S * (1 / B1 - 1 / B2)
+        dm2 = -S / B2
+        dm12 = 2 * A1 / (B1 * B2)
+        dS = blur(dm1, g) + 2 * x * blur(dm2, g) + y * blur(dm12, g)
+        g_rgb[ch] -= w_s * dS / (3 * N)
+    loss += w_s * (1 - s_tot / (3 * N))
+    return loss, g_rgb, g_depth

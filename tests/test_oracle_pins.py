@@ -511,3 +511,95 @@ def test_collision_check_closed_form():
     np.testing.assert_array_equal(hit, [True, False, True, False])
     m2, h2 = O.collision_check(mo, su, pts, 0.3, 3.0, ground_z=5.0)     # every Gaussian removed
     assert np.isinf(m2).all() and not h2.any()
+
+
+# ------------------------------------------------------------------ mapping loss (Eq. 3)
+def _ssim_brute(x, y, r=5, sigma=1.5):
+    """SSIM map by explicit window sums (zero outside the image), straight from the definition."""
+    H, W = x.shape
+    w = {(i, j): math.exp(-(i * i + j * j) / (2 * sigma * sigma)) for i in range(-r, r + 1) for j in range(-r, r + 1)}
+    tot = sum(w.values())
+    out = np.zeros_like(x)
+    for py in range(H):
+        for px in range(W):
+            m = [0.0] * 5
+            for (i, j), wt in w.items():
+                yy, xx = py + i, px + j
+                if 0 <= yy < H and 0 <= xx < W:
+                    a, b = x[yy, xx], y[yy, xx]
+                    for k, v in enumerate((a, b, a * a, b * b, a * b)):
+                        m[k] += wt / tot * v
+            mx, my = m[0], m[1]
+            sx, sy, sxy = m[2] - mx * mx, m[3] - my * my, m[4] - mx * my
+            c1, c2 = 0.01 ** 2, 0.03 ** 2
+            out[py, px] = (2 * mx * my + c1) * (2 * sxy + c2) / ((mx * mx + my * my + c1) * (sx + sy + c2))
+    return out
+
+
+def test_ssim_map_brute_force_tiny():
+    rng = np.random.default_rng(31)
+    x, y = rng.uniform(0, 1, (7, 9)), rng.uniform(0, 1, (7, 9))
+    np.testing.assert_allclose(O.ssim_map(x, y), _ssim_brute(x, y), rtol=1e-12, atol=1e-14)
+
+
+def test_ssim_moments_match_scipy_gaussian_filter():
+    """The windowed moments equal scipy's Gaussian filter truncated at radius 5, zero outside."""
+    from scipy.ndimage import gaussian_filter
+    rng = np.random.default_rng(32)
+    x, y = rng.uniform(0, 1, (20, 27)), rng.uniform(0, 1, (20, 27))
+    f = lambda a: gaussian_filter(a, 1.5, mode="constant", cval=0.0, truncate=5 / 1.5)
+    mx, my = f(x), f(y)
+    ref = ((2 * mx * my + 1e-4) * (2 * (f(x * y) - mx * my) + 9e-4)) / \
+        ((mx * mx + my * my + 1e-4) * (f(x * x) - mx * mx + f(y * y) - my * my + 9e-4))
+    np.testing.assert_allclose(O.ssim_map(x, y), ref, rtol=1e-12, atol=1e-14)
+
+
+def test_ssim_constant_images_interior_closed_form():
+    """Constant images a, b: away from the border sigma = 0 and S = (2ab + C1) / (a^2 + b^2 + C1)."""
+    a, b = 0.7, 0.3
+    s = O.ssim_map(np.full((16, 16), a), np.full((16, 16), b))
+    np.testing.assert_allclose(s[5:-5, 5:-5], (2 * a * b + 1e-4) / (a * a + b * b + 1e-4), rtol=1e-13)
+
+
+def test_mapping_loss_identical_images():
+    """x = y: L1 terms vanish, SSIM = 1 exactly (loss 0) and, SSIM being maximal there, its gradient is 0."""
+    rng = np.random.default_rng(33)
+    x = rng.uniform(0, 1, (3, 12, 15))
+    d = rng.uniform(1, 3, (12, 15))
+    L, gr, gd = O.mapping_loss(x, d, x, d)
+    assert abs(L) < 1e-14
+    assert np.abs(gr).max() < 1e-12 and np.abs(gd).max() == 0.0
+
+
+def test_mapping_loss_l1_weights_reduce_to_plain_means():
+    """w = (0.1, 1/3, 0) is mean |rgb - ref| over all elements + 0.1 mean |d - ref|."""
+    rng = np.random.default_rng(34)
+    x, y = rng.uniform(0, 1, (3, 10, 11)), rng.uniform(0, 1, (3, 10, 11))
+    d, dr = rng.uniform(1, 3, (10, 11)), rng.uniform(1, 3, (10, 11))
+    L, gr, gd = O.mapping_loss(x, d, y, dr, w_d=0.1, w_c=1 / 3, w_s=0.0)
+    assert L == pytest.approx(np.abs(x - y).mean() + 0.1 * np.abs(d - dr).mean(), rel=1e-14)
+    np.testing.assert_allclose(gr, np.sign(x - y) / x.size, rtol=1e-14)
+    np.testing.assert_allclose(gd, 0.1 * np.sign(d - dr) / d.size, rtol=1e-14)
+
+
+def test_mapping_loss_gradient_central_differences():
+    """dL/d(rgb, depth) of Eq. 3 against FP64 central differences (the L1 kinks are avoided: |x - y| >= 0.02)."""
+    rng = np.random.default_rng(35)
+    y = rng.uniform(0.1, 0.9, (3, 9, 13))
+    x = y + rng.choice([-1, 1], y.shape) * rng.uniform(0.02, 0.2, y.shape)
+    dr = rng.uniform(1, 3, (9, 13))
+    d = dr + rng.choice([-1, 1], dr.shape) * rng.uniform(0.02, 0.2, dr.shape)
+    L, gr, gd = O.mapping_loss(x, d, y, dr)
+    h = 1e-6
+    for idx in [(0, 0, 0), (1, 4, 6), (2, 8, 12), (0, 3, 11), (2, 0, 7)]:
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += h
+        xm[idx] -= h
+        fd = (O.mapping_loss(xp, d, y, dr)[0] - O.mapping_loss(xm, d, y, dr)[0]) / (2 * h)
+        assert gr[idx] == pytest.approx(fd, rel=1e-6, abs=1e-10)
+    for idx in [(0, 0), (5, 7)]:
+        dp, dm = d.copy(), d.copy()
+        dp[idx] += h
+        dm[idx] -= h
+        fd = (O.mapping_loss(x, dp, y, dr)[0] - O.mapping_loss(x, dm, y, dr)[0]) / (2 * h)
+        assert gd[idx] == pytest.approx(fd, rel=1e-6)
