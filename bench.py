@@ -175,9 +175,11 @@ def job_throughput(units_per_rank: float, seconds_per_rank: float, world: int) -
 
 # ----------------------------------------------------------------------------- workloads
 class MapStep:
-    """One mapping iteration on the 500k-Gaussian, 4-keyframe map."""
+    """One mapping iteration on the 500k-Gaussian, 4-keyframe map: render, the loss and its
+    image gradient (gs_image_loss; by default mean L1 over RGB + 0.1 x mean L1 depth, or the
+    paper's Eq. 3 weights with SSIM), gs_render_bwd, Adam."""
 
-    def __init__(self, gs, scenes):
+    def __init__(self, gs, scenes, weights=None):
         import torch
         self.torch = torch
         self.gs = gs
@@ -200,15 +202,16 @@ class MapStep:
         self.host_tgt = [self.tgt_rgb.cpu().pin_memory(), self.tgt_depth.cpu().pin_memory()]
         self.opt = torch.optim.Adam(self.params, lr=1e-4, fused=True)
         self.loss_host = torch.zeros(1, dtype=torch.float32).pin_memory()
+        self.loss_fn = gs.ImageLoss.for_cameras(sc.cams, gs.L1_WEIGHTS if weights is None else weights)
 
     def __call__(self):
         gs, torch = self.gs, self.torch
         self.opt.zero_grad(set_to_none=True)
         rgb, depth, _ = gs.render(*self.params, self.frame)
-        loss = (rgb - self.tgt_rgb).abs().mean() + 0.1 * (depth - self.tgt_depth).abs().mean()
-        loss.backward()
+        loss, d_rgb, d_depth = self.loss_fn(rgb.detach(), depth.detach(), self.tgt_rgb, self.tgt_depth)
+        torch.autograd.backward((rgb, depth), (d_rgb, d_depth))
         self.opt.step()
-        return loss
+        return loss[:1]
 
     def e2e(self):
         """Host inputs -> device, step, loss -> host (all enqueued on the current stream)."""
@@ -448,6 +451,79 @@ def cfg0_latency_us(torch, gs, scenes, reps=30):
     return statistics.median(t)
 
 
+def render_free_xi(torch, gs, istep, flush, reps=10):
+    """The paper's render-free scoring (Eq. view_util) of the same candidates over the
+    same map: thresholds + batched xi, device time per pass."""
+    vu = gs.ViewUtility(istep.scene.cams)
+    for _ in range(3):
+        vu.thresholds(istep.gm)
+        vu(istep.gm, gs.L.GS_XI)
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(reps):
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        vu.thresholds(istep.gm)
+        vu(istep.gm, gs.L.GS_XI)
+        e1.record()
+        torch.cuda.synchronize()
+        t.append(e0.elapsed_time(e1))
+    ms = statistics.mean(t)
+    return {"value": vu.V / (ms / 1e3), "unit": "views/s", "ms": ms, "views": vu.V,
+            "paper_context": "0.013 s per planning step for RTGuIDE's render-free score on an RTX A4000 "
+                             "(number of candidate views per step not stated)"}
+
+
+def eq3_map_step(torch, gs, scenes, flush, steps=10):
+    """The mapping step with the paper's full loss (Eq. 3: depth L1 + 0.4 colour L1 + 0.1 (1 - SSIM))
+    on the same 500k-Gaussian, 4 x 640x480 workload; iterations/s and the loss kernels' share."""
+    m = MapStep(gs, scenes, weights=gs.EQ3_WEIGHTS)
+    for _ in range(3):
+        m()
+    torch.cuda.synchronize()
+    gs.TIMER = gs.StageTimer()
+    t = timed_loop(torch, steps, [("m", m)], flush)["m"]
+    loss_ms = statistics.mean(gs.TIMER.durations_ms("gs_image_loss"))
+    gs.TIMER = None
+    ms = statistics.mean(t)
+    out = {"value": 1e3 / ms, "unit": "iters/s", "ms": ms, "gs_image_loss_ms": loss_ms,
+           "loss": float(m.loss_fn.loss[0].item()), "ssim": float(m.loss_fn.loss[3].item())}
+    del m
+    torch.cuda.empty_cache()
+    return out
+
+
+def collision_timing(torch, gs, scenes, reps=20):
+    """Collision check of 129 test points (one motion-primitive tree layer) against every
+    Gaussian of the 3M-Gaussian, 40x40 m map, r_robot 0.3 m, lambda_g 3 (Sec. IV-B)."""
+    import numpy as np
+    sc, _ = scenes.config4()
+    gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
+    rng = np.random.default_rng(129)
+    pts = np.zeros((129, 4), np.float32)
+    pts[:, :3] = rng.uniform([0.5, 0.5, 0.3], [39.5, 39.5, 1.0], (129, 3))
+    p = torch.from_numpy(pts).cuda()
+    for _ in range(3):
+        gs.collision_check(gm, p, 0.3, 3.0)
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gs.collision_check(gm, p, 0.3, 3.0)
+        e1.record()
+        torch.cuda.synchronize()
+        t.append(e0.elapsed_time(e1))
+    ms = statistics.median(t)
+    del gm
+    torch.cuda.empty_cache()
+    return {"ms": ms, "points": 129, "gaussians": sc.gmap.n,
+            "pair_tests_per_s": 129 * sc.gmap.n / (ms / 1e3),
+            "paper_context": "0.62 s for planning a 5 m trajectory with 129 collision points at 3e6 "
+                             "Gaussians (GPU collision checks, tree search included, hardware not stated)"}
+
+
 def mix_pixels_per_view(cams):
     return sum(c.width * c.height for c in cams) / len(cams)
 
@@ -558,6 +634,9 @@ def run_ours(args):
     hbm = float(peaks.get("hbm_gbs", 6673.5))
     pipe = pipeline_roofline(istep, ig_contrib, t_ig_all / args.steps, hbm, peak)
     lat0 = cfg0_latency_us(torch, gs, scenes)
+    xi_free = render_free_xi(torch, gs, istep, flush)
+    collide = collision_timing(torch, gs, scenes)
+    eq3 = eq3_map_step(torch, gs, scenes, flush)
     achieved = 16.0 * ig_contrib / t_comp / 1e12
     tiles_now = {"%dx%d" % k: "%dx%d" % v for k, v in istep.tile_choice.items()}
     traffic = (IG_TRAFFIC["bytes"] if IG_TRAFFIC["sources_sha1"] == ig_sources_sha1() and
@@ -611,6 +690,9 @@ def run_ours(args):
             "work": ws,
             "ig_pipeline_roofline": pipe,
             "cfg0_forward_latency_us": lat0,
+            "render_free_xi": xi_free,
+            "collision_check": collide,
+            "fwd_bwd_eq3_ssim": eq3,
             "e2e": e2e,
             "roofline": roofline,
             "rooflines": rooflines,

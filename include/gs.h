@@ -433,6 +433,41 @@ gs_status gs_collision_check(const gs_map* map, const float* points, int32_t n_p
 gs_status gs_region_uncertainty(const gs_map* map, const gs_region_grid* grid, float* omega_out, uint32_t* count_out,
                                 void* ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------ mapping loss (Eq. 3)
+ * The map is refined by minimising, over the keyframes, a photometric loss of
+ * the rendered colour and depth against the observations (Eq. 3):
+ *   L = (1/N_p) sum_p (w_d |d(p) - d_ref(p)| + w_c |c(p) - c_ref(p)|_1) + w_s (1 - SSIM(c, c_ref))
+ * with the paper's weights w_d = 1, w_c = lambda_1 = 0.4, w_s = lambda_2 = 0.1.  Readings where the
+ * paper is silent: N_p is the total pixel count of all views in the call; |.|_1 sums the
+ * three channels; SSIM is the mean over the three channels and all pixels of
+ *   S(p) = ((2 mu_x mu_y + C1)(2 s_xy + C2)) / ((mu_x^2 + mu_y^2 + C1)(s_x^2 + s_y^2 + C2)),
+ * C1 = 0.01^2, C2 = 0.03^2, with windowed moments mu = G*x, s_x^2 = G*(x^2) - mu_x^2,
+ * s_xy = G*(x y) - mu_x mu_y over an 11 x 11 Gaussian window (sigma 1.5, normalised),
+ * the image taken as zero outside its border; each view is its own image. */
+typedef struct {
+  float w_depth, w_rgb, w_ssim;
+} gs_loss_weights;
+
+/* gs_image_loss -- Eq. 3 for n_views rendered views against their references, and its
+ * gradient with respect to the rendered images (ready for gs_render_bwd).
+ *   sizes      HOST int32[n_views][2]: (width, height) of each view, > 0
+ *   rgb, rgb_ref      DEVICE float, the gs_image.rgb layout (views concatenated, planar per view)
+ *   depth, depth_ref  DEVICE float, the gs_image.depth layout; may be NULL iff w_depth = 0
+ *   loss_out   DEVICE float[4]: (L, mean |d - d_ref|, mean |c - c_ref|_1, SSIM), the sums in FP64
+ *              in a fixed order (deterministic)
+ *   d_rgb      DEVICE float, dL/d rgb (rgb layout) or NULL; d_depth: dL/d depth or NULL.
+ *              The L1 terms use sign(0) = 0.  Overwritten.
+ * w_depth, w_rgb, w_ssim >= 0 and finite.  ws: DEVICE workspace of
+ * gs_image_loss_workspace_size bytes (the same sizes).
+ * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG, GS_ERR_WORKSPACE, GS_ERR_CUDA. */
+gs_status gs_image_loss(const int32_t* sizes, int32_t n_views, const float* rgb, const float* depth,
+                        const float* rgb_ref, const float* depth_ref, const gs_loss_weights* w, float* loss_out,
+                        float* d_rgb, float* d_depth, void* ws, size_t ws_bytes, void* stream);
+
+/* gs_image_loss_workspace_size -- HOST.  Workspace bytes of gs_image_loss for these view
+ * sizes (HOST int32[n_views][2]) into *bytes.  Errors: GS_ERR_NULL, GS_ERR_ARG. */
+gs_status gs_image_loss_workspace_size(const int32_t* sizes, int32_t n_views, size_t* bytes);
+
 /* ------------------------------------------------------------- utilities */
 enum {
   GS_OP_PROJECT = 0,

@@ -501,3 +501,22 @@ def mapping_loss(rgb, depth, rgb_ref, depth_ref, w_d: float = 1.0, w_c: float = 
         g_rgb[ch] -= w_s * dS / (3 * N)
     loss += w_s * (1 - s_tot / (3 * N))
     return loss, g_rgb, g_depth
+
+
+def mapping_loss_views(rgbs, depths, rgb_refs, depth_refs, w_d: float = 1.0, w_c: float = 0.4, w_s: float = 0.1):
+    """Eq. 3 over several views with N_p = the total pixel count of all views (each view is its
+    own image for SSIM): L = sum_v (N_v / N_p) L_v, and each view's gradient scaled by N_v / N_p.
+    Returns (L, mean |d - d_ref|, mean |c - c_ref|_1, SSIM, [dL/drgb_v], [dL/ddepth_v])."""
+    n_v = [np.asarray(d).size for d in depths]
+    n_p = float(sum(n_v))
+    L, l1d, l1c, ss, g_rgb, g_depth = 0.0, 0.0, 0.0, 0.0, [], []
+    for x, d, y, dr, n in zip(rgbs, depths, rgb_refs, depth_refs, n_v):
+        Lv, gr, gd = mapping_loss(x, d, y, dr, w_d, w_c, w_s)
+        f = n / n_p
+        L += f * Lv
+        l1d += np.abs(np.asarray(d, np.float64) - np.asarray(dr, np.float64)).sum() / n_p
+        l1c += np.abs(np.asarray(x, np.float64) - np.asarray(y, np.float64)).sum() / n_p
+        ss += sum(ssim_map(np.asarray(x[c], np.float64), np.asarray(y[c], np.float64)).sum() for c in range(3)) / (3 * n_p)
+        g_rgb.append(f * gr)
+        g_depth.append(f * gd)
+    return L, l1d, l1c, ss, g_rgb, g_depth

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <cmath>
 
 #include "gs_internal.h"
 
@@ -259,6 +260,35 @@ gs_status gs_region_uncertainty(const gs_map* map, const gs_region_grid* grid, f
   if (!aligned(omega_out, 4) || !aligned(count_out, 4)) return GS_ERR_ALIGN;
   GS_TRY(check_ws(ws, ws_bytes, regions_ws_bytes(nr)));
   return from_cuda(launch_regions(map->mo, map->su, map->n, *grid, omega_out, count_out, ws, (cudaStream_t)stream));
+}
+
+gs_status gs_image_loss(const int32_t* sizes, int32_t n_views, const float* rgb, const float* depth,
+                        const float* rgb_ref, const float* depth_ref, const gs_loss_weights* w, float* loss_out,
+                        float* d_rgb, float* d_depth, void* ws, size_t ws_bytes, void* stream) {
+  if (!sizes || !w || !rgb || !rgb_ref || !loss_out) return GS_ERR_NULL;
+  if (n_views < 1) return GS_ERR_ARG;
+  const float wt[3] = {w->w_depth, w->w_rgb, w->w_ssim};
+  for (float x : wt)
+    if (!(x >= 0.f) || std::isinf(x)) return GS_ERR_ARG;
+  if (w->w_depth != 0.f && (!depth || !depth_ref)) return GS_ERR_NULL;
+  if ((depth == nullptr) != (depth_ref == nullptr)) return GS_ERR_NULL;
+  const size_t need = image_loss_ws_bytes(sizes, n_views);
+  if (need == 0) return GS_ERR_ARG;
+  if (!aligned(rgb, 4) || !aligned(rgb_ref, 4) || !aligned(depth, 4) || !aligned(depth_ref, 4) ||
+      !aligned(loss_out, 4) || !aligned(d_rgb, 4) || !aligned(d_depth, 4))
+    return GS_ERR_ALIGN;
+  GS_TRY(check_ws(ws, ws_bytes, need));
+  return from_cuda(launch_image_loss(sizes, n_views, rgb, depth, rgb_ref, depth_ref, *w, loss_out, d_rgb, d_depth, ws,
+                                     (cudaStream_t)stream));
+}
+
+gs_status gs_image_loss_workspace_size(const int32_t* sizes, int32_t n_views, size_t* bytes) {
+  if (!sizes || !bytes) return GS_ERR_NULL;
+  if (n_views < 1) return GS_ERR_ARG;
+  const size_t need = image_loss_ws_bytes(sizes, n_views);
+  if (need == 0) return GS_ERR_ARG;
+  *bytes = need;
+  return GS_OK;
 }
 
 gs_status gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t rec_capacity, int64_t pair_capacity,

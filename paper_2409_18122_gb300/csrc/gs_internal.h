@@ -120,6 +120,13 @@ cudaError_t launch_collision_check(const float* mo, const float* su, int64_t n, 
                                    float r_robot, float lambda_g, float ground_z, float* margin_out,
                                    uint32_t* collides_out, cudaStream_t st);
 size_t regions_ws_bytes(int64_t n_regions);
+
+// ------------------------------------------------------------------ mapping loss (Eq. 3)
+// 0 if the sizes are invalid.
+size_t image_loss_ws_bytes(const int32_t* sizes, int n_views);
+cudaError_t launch_image_loss(const int32_t* sizes, int n_views, const float* rgb, const float* depth,
+                              const float* rgb_ref, const float* depth_ref, const gs_loss_weights& w,
+                              float* loss_out, float* d_rgb, float* d_depth, void* ws, cudaStream_t st);
 cudaError_t launch_regions(const float* mo, const float* su, int64_t n, const gs_region_grid& grid, float* omega,
                            uint32_t* count_out, void* ws, cudaStream_t st);
 

@@ -527,6 +527,68 @@ def region_uncertainty(gmap: GaussianMapTensors, origin, size: float, dims, stre
     return omega, count
 
 
+# ---------------------------------------------------------------------- mapping loss (Eq. 3)
+EQ3_WEIGHTS = (1.0, 0.4, 0.1)          # (w_depth, w_rgb = lambda_1, w_ssim = lambda_2), Eq. 3
+L1_WEIGHTS = (0.1, 1.0 / 3.0, 0.0)     # mean L1 over RGB elements + 0.1 x mean L1 depth
+
+
+class ImageLoss:
+    """Eq. 3 over the views of a batch (gs_image_loss): loss and dL/d(rgb, depth) in one call.
+
+    sizes: [(width, height)] per view, in the gs_image layout order; weights: (w_depth,
+    w_rgb, w_ssim).  __call__ returns (loss4, d_rgb, d_depth), loss4 = device float[4]
+    (L, mean |d - d_ref|, mean |c - c_ref|_1, SSIM or NaN when w_ssim = 0); the gradient
+    buffers are reused by every call."""
+
+    def __init__(self, sizes, weights=EQ3_WEIGHTS, device="cuda"):
+        self.device = torch.device(device)
+        self.sizes = np.ascontiguousarray(np.asarray(sizes, dtype=np.int32).reshape(-1, 2))
+        self.V = len(self.sizes)
+        self.P = int((self.sizes[:, 0].astype(np.int64) * self.sizes[:, 1]).sum())
+        self.w = L.gs_loss_weights(*[float(x) for x in weights])
+        nb = ctypes.c_size_t(0)
+        L.check(L.lib().gs_image_loss_workspace_size(self.sizes.ctypes.data, self.V, ctypes.byref(nb)),
+                "gs_image_loss_workspace_size")
+        self.ws = torch.empty(max(int(nb.value), 256), dtype=torch.uint8, device=self.device)
+        self.loss = torch.zeros(4, dtype=torch.float32, device=self.device)
+        self.d_rgb = torch.zeros(3 * self.P, dtype=torch.float32, device=self.device)
+        self.d_depth = torch.zeros(self.P, dtype=torch.float32, device=self.device)
+
+    @staticmethod
+    def for_cameras(cams, weights=EQ3_WEIGHTS, device="cuda") -> "ImageLoss":
+        return ImageLoss([(c.width, c.height) for c in cams], weights, device)
+
+    def __call__(self, rgb, depth, rgb_ref, depth_ref, with_grad: bool = True, stream=None):
+        for t, n in ((rgb, 3 * self.P), (rgb_ref, 3 * self.P), (depth, self.P), (depth_ref, self.P)):
+            if t is not None and (t.numel() != n or t.dtype != torch.float32 or not t.is_contiguous()):
+                raise ValueError("images must be contiguous float32 tensors in the gs_image layout")
+        dr = self.d_rgb if with_grad else None
+        dd = self.d_depth if with_grad else None
+        _timed("gs_image_loss", stream, lambda: L.check(
+            L.lib().gs_image_loss(self.sizes.ctypes.data, self.V, _ptr(rgb), _ptr(depth), _ptr(rgb_ref),
+                                  _ptr(depth_ref), ctypes.byref(self.w), _ptr(self.loss), _ptr(dr), _ptr(dd),
+                                  _ptr(self.ws), self.ws.numel(), _stream(stream)), "gs_image_loss"))
+        return self.loss, dr, dd
+
+
+class _ImageLossFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rgb, depth, rgb_ref, depth_ref, fn: ImageLoss):
+        loss, d_rgb, d_depth = fn(rgb.detach(), depth.detach(), rgb_ref, depth_ref)
+        ctx.save_for_backward(d_rgb.clone(), d_depth.clone())
+        return loss[0].clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        d_rgb, d_depth = ctx.saved_tensors
+        return d_rgb * g, d_depth * g, None, None, None
+
+
+def image_loss(rgb, depth, rgb_ref, depth_ref, fn: ImageLoss):
+    """Differentiable Eq. 3 loss (scalar) of rendered images against references."""
+    return _ImageLossFn.apply(rgb, depth, rgb_ref, depth_ref, fn)
+
+
 # ---------------------------------------------------------------------- tile autotuner
 TILE_CANDIDATES = ((16, 16), (16, 8), (8, 8), (32, 8), (32, 16), (32, 32))
 

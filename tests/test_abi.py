@@ -45,6 +45,7 @@ def test_struct_layouts_match_header(tmp_path):
         "gs_camera": L.gs_camera, "gs_map": L.gs_map, "gs_params": L.gs_params, "gs_proj": L.gs_proj,
         "gs_bins": L.gs_bins, "gs_image": L.gs_image, "gs_image_grad": L.gs_image_grad, "gs_map_grad": L.gs_map_grad,
         "gs_utility_params": L.gs_utility_params, "gs_region_grid": L.gs_region_grid,
+        "gs_loss_weights": L.gs_loss_weights,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gs.h"', "int main(void) {"]
     for s, cls in structs.items():
@@ -122,6 +123,31 @@ def test_host_side_argument_errors(lib):
     assert lib.gs_info_gain_batch(P(m), fake, 1, P(prm), 7, fake, fake, 0, 100, 10, fake, 1 << 30, None) == L.GS_ERR_ARG
     assert lib.gs_info_gain_batch(P(m), fake, 1, P(prm), 0, None, fake, 0, 100, 10, fake, 1 << 30, None) == L.GS_ERR_NULL
     assert lib.gs_info_gain_batch(P(m), fake, 1, P(prm), 0, fake, fake, -1, 100, 10, fake, 1 << 30, None) == L.GS_ERR_ARG
+    # image loss: sizes, weights, depth pointers, workspace
+    sz = (ctypes.c_int32 * 4)(64, 48, 37, 29)
+    w = L.gs_loss_weights(1.0, 0.4, 0.1)
+    nb = ctypes.c_size_t(0)
+    assert lib.gs_image_loss_workspace_size(sz, 2, P(nb)) == L.GS_OK and nb.value % 256 == 0
+    need = nb.value
+    assert need >= 36 * (64 * 48 + 37 * 29)
+    assert lib.gs_image_loss_workspace_size(sz, 1, P(nb)) == L.GS_OK and nb.value < need
+    assert lib.gs_image_loss_workspace_size((ctypes.c_int32 * 2)(0, 5), 1, P(nb)) == L.GS_ERR_ARG
+    assert lib.gs_image_loss_workspace_size(None, 1, P(nb)) == L.GS_ERR_NULL
+    ok = (sz, 2, fake, fake, fake, fake, P(w), fake, fake, fake, fake, need, None)
+
+    def call(**kw):
+        a = list(ok)
+        for i, v in kw.items():
+            a[int(i[1:])] = v
+        return lib.gs_image_loss(*a)
+    assert call(a0=None) == L.GS_ERR_NULL and call(a2=None) == L.GS_ERR_NULL and call(a7=None) == L.GS_ERR_NULL
+    assert call(a1=0) == L.GS_ERR_ARG
+    assert call(a3=None, a5=None) == L.GS_ERR_NULL                   # w_depth != 0 needs depth
+    assert call(a3=None) == L.GS_ERR_NULL                            # depth and depth_ref together
+    for bad in ((-1.0, 0.4, 0.1), (1.0, float("nan"), 0.1), (1.0, 0.4, float("inf"))):
+        assert call(a6=P(L.gs_loss_weights(*bad))) == L.GS_ERR_ARG
+    assert call(a11=need - 256) == L.GS_ERR_WORKSPACE
+    assert call(a8=ctypes.c_void_p(0x10002)) == L.GS_ERR_ALIGN
     # read_status: null
     f = ctypes.c_uint32(0)
     assert lib.gs_read_status(None, P(f)) == L.GS_ERR_NULL

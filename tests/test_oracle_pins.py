@@ -603,3 +603,18 @@ def test_mapping_loss_gradient_central_differences():
         dm[idx] -= h
         fd = (O.mapping_loss(x, dp, y, dr)[0] - O.mapping_loss(x, dm, y, dr)[0]) / (2 * h)
         assert gd[idx] == pytest.approx(fd, rel=1e-6)
+
+
+def test_mapping_loss_views_normalisation():
+    """N_p over all views: one view reduces to mapping_loss; a view repeated twice has the same
+    loss with half the gradient per copy; the three reported terms recombine to L."""
+    rng = np.random.default_rng(36)
+    x, y = rng.uniform(0, 1, (3, 8, 10)), rng.uniform(0, 1, (3, 8, 10))
+    d, dr = rng.uniform(1, 3, (8, 10)), rng.uniform(1, 3, (8, 10))
+    L1v, gr1, gd1 = O.mapping_loss(x, d, y, dr)
+    L, l1d, l1c, ss, gr, gd = O.mapping_loss_views([x], [d], [y], [dr])
+    assert L == pytest.approx(L1v, rel=1e-15) and np.array_equal(gr[0], gr1)
+    L2, l1d2, l1c2, ss2, gr2, gd2 = O.mapping_loss_views([x, x], [d, d], [y, y], [dr, dr])
+    assert L2 == pytest.approx(L1v, rel=1e-14) and ss2 == pytest.approx(ss, rel=1e-14)
+    np.testing.assert_allclose(gr2[1], gr1 / 2, rtol=1e-15)
+    assert L == pytest.approx(l1d + 0.4 * l1c + 0.1 * (1 - ss), rel=1e-14)
