@@ -243,29 +243,28 @@ __device__ __forceinline__ uint32_t div_small(uint32_t j, uint32_t w) {
 }
 
 // Step 6: every pair written to its slot.  A warp takes its chunk's records 32
-// at a time (a group); their pairs inside the current window are enumerated 32
-// at a time (a round; record order, each rectangle row-major), one pair per lane.
+// at a time (a group; the next group's rectangles and record ids are loaded while
+// the current one is placed); their pairs inside the current window are enumerated
+// 32 at a time (a round; record order, each rectangle row-major), one pair per lane.
 // The lanes of a round holding pairs of the same window cell belong to different
-// records, in lane order: each sets its lane bit in msk[cell], takes the running
-// slot plus the number of lower bits, and the lowest of them advances the running
-// slot and clears the mask for the next round.
+// records, in lane order: a warp match on the cell gives each its rank among them,
+// its slot is the cell's running slot plus that rank, and the lowest of them
+// advances the running slot for the next round.
 template <bool kTileIds>
-__global__ void __launch_bounds__(kBinWarps * 32) k_bin_place(const gs_proj proj, const uint32_t* __restrict__ seg,
+__global__ void __launch_bounds__(kBinWarps * 32, 5) k_bin_place(const gs_proj proj, const uint32_t* __restrict__ seg,
                                                               const uint32_t* __restrict__ srec,
                                                               const ushort4* __restrict__ srect,
                                                               const uint32_t* __restrict__ poff, int n_views, int K,
                                                               int64_t tile_cap, const uint32_t* __restrict__ off,
                                                               gs_bins out) {
   __shared__ uint32_t s_run[kBinWarps][kPlaceWin];
-  __shared__ uint32_t s_msk[kBinWarps][kPlaceWin];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t lanebit = 1u << lane, lt = lanebit - 1u;
+  const uint32_t lt = (1u << lane) - 1u;
   const int64_t cid = (int64_t)blockIdx.x * kBinWarps + warp;
   if (cid >= (int64_t)n_views * K) return;
   Chunk c;
   if (!chunk_of(cid, K, seg, poff, proj.view_info, tile_cap, c)) return;
   uint32_t* run = s_run[warp];
-  uint32_t* msk = s_msk[warp];
   const uint32_t cap = out.pair_capacity < 0xFFFFFFFFll ? (uint32_t)out.pair_capacity : 0xFFFFFFFFu;
   uint32_t ww, wh;
   window_size(c.tiles_x, c.tiles_y, kPlaceWin, false, ww, wh);
@@ -277,15 +276,25 @@ __global__ void __launch_bounds__(kBinWarps * 32) k_bin_place(const gs_proj proj
       for (uint32_t i = lane; i < cells; i += 32) {
         const uint32_t y = ya + i / cols, x = xa + i % cols;
         run[i] = off[(size_t)K * (c.tile_base + y * c.tiles_x + x) + c.k];
-        msk[i] = 0u;
+      }
+      ushort4 rc_next = make_ushort4(0, 0, 0, 0);
+      uint32_t rec_next = 0;
+      if (c.r0 + lane < c.r1) {
+        rc_next = srect[c.r0 + lane];
+        rec_next = srec[c.r0 + lane];
       }
       __syncwarp();
       for (int64_t g = c.r0; g < c.r1; g += 32) {
+        const ushort4 rc = rc_next;
+        const uint32_t rec_g = rec_next;
+        const bool have = g + lane < c.r1;
+        if (g + 32 + lane < c.r1) {
+          rc_next = srect[g + 32 + lane];
+          rec_next = srec[g + 32 + lane];
+        }
         // this lane's record, clipped to the window (window-relative corner)
-        const int64_t r = g + lane;
         uint32_t x0 = 0, y0 = 0, w = 1, cnt = 0, rec = 0;
-        if (r < c.r1) {
-          const ushort4 rc = srect[r];
+        if (have) {
           const uint32_t cx0 = rc.x > xa ? rc.x : xa, cx1 = rc.z < xb ? rc.z : xb;
           const uint32_t cy0 = rc.y > ya ? rc.y : ya, cy1 = rc.w < yb ? rc.w : yb;
           if (cx0 < cx1 && cy0 < cy1) {
@@ -293,7 +302,7 @@ __global__ void __launch_bounds__(kBinWarps * 32) k_bin_place(const gs_proj proj
             y0 = cy0 - ya;
             w = cx1 - cx0;
             cnt = w * (cy1 - cy0);
-            rec = srec[r];
+            rec = rec_g;
           }
         }
         uint32_t incl = cnt;
@@ -319,30 +328,26 @@ __global__ void __launch_bounds__(kBinWarps * 32) k_bin_place(const gs_proj proj
           const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, o);
           const uint32_t o_rec = __shfl_sync(0xffffffffu, rec, o);
           const bool valid = k < total;
-          uint32_t i = 0, cy = 0, cx = 0;   // window cell, its row and column
+          uint32_t i = 0xFFFFFFFFu, cy = 0, cx = 0;   // window cell, its row and column
           if (valid) {
             const uint32_t j = k - o_excl;
             const uint32_t y = div_small(j, o_w);
             cy = o_y0 + y;
             cx = o_x0 + (j - y * o_w);
             i = cy * cols + cx;
-            atomicOr(&msk[i], lanebit);
           }
-          __syncwarp();
-          uint32_t mm = 0;
+          // lanes of the same cell (invalid lanes share the key 0xFFFFFFFF and do nothing)
+          const uint32_t peers = __match_any_sync(0xffffffffu, i);
+          const uint32_t below = peers & lt;
           if (valid) {
-            mm = msk[i];
-            const uint32_t slot = run[i] + __popc(mm & lt);
+            const uint32_t slot = run[i] + __popc(below);
             if (slot < cap) {
               out.rec[slot] = o_rec;
               if (kTileIds) out.tile[slot] = c.tile_base + (ya + cy) * c.tiles_x + xa + cx;
             }
           }
           __syncwarp();
-          if (valid && (mm & lt) == 0u) {   // lowest lane of the cell in this round
-            run[i] += __popc(mm);
-            msk[i] = 0u;
-          }
+          if (valid && below == 0u) run[i] += __popc(peers);   // lowest lane of the cell in this round
           __syncwarp();
         }
       }

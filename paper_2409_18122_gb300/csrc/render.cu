@@ -97,13 +97,19 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
     if (m) {
       // the overlapping entries, compacted in list order: (mu, u, o), (scaled conic,
       // position in the group), colour
+      // padded to whole batches with entries of opacity -1 (alpha < 0: always skipped)
       const int n_ov = __popc(m);
+      const int n_pad = (n_ov + kFwdBatch - 1) / kFwdBatch * kFwdBatch;
       if (ovA) {
         const int s = __popc(m & lt);
         const float3 k2 = scaled_conic(cA);
         sm[s] = make_float4(mA.x, mA.y, mA.w, cA.w);
         sc[s] = make_float4(k2.x, k2.y, k2.z, __int_as_float(lane));
         sk[s] = kA;
+      }
+      if (lane >= n_ov && lane < n_pad) {   // slots [n_ov, n_pad): disjoint from the staged ones
+        sm[lane] = make_float4(0.f, 0.f, 0.f, -1.f);
+        sc[lane] = z4;
       }
       __syncwarp();
       // kFwdBatch entries at a time: their alphas are independent and computed
@@ -112,7 +118,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
         float al[kFwdBatch][kPix];
 #pragma unroll
         for (int k = 0; k < kFwdBatch; ++k) {
-          const int i = i0 + k < n_ov ? i0 + k : n_ov - 1;
+          const int i = i0 + k;
           const float4 mu = sm[i];
           const float4 kk = sc[i];
 #pragma unroll
@@ -124,7 +130,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_pr
           const int i = i0 + k;
 #pragma unroll
           for (int q = 0; q < kPix; ++q) {
-            if (i >= n_ov || done[q]) continue;
+            if (done[q]) continue;
             const float alpha = al[k][q];
             if (alpha < p.alpha_min) continue;
             const float Tn = T[q] * (1.f - alpha);
@@ -202,13 +208,13 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
     warp_block<kPix>(ti, wb);
     const float pxc = (float)wb.px + 0.5f;
     const float ln_amin = __logf(p.alpha_min);
+    // T = 0 marks a saturated pixel (and one outside the image): the stop rule sets it,
+    // and a zero T adds nothing and stays zero, so no separate flag is kept
     float pyc[kPix], T[kPix], cu[kPix];
-    bool done[kPix];
 #pragma unroll
     for (int q = 0; q < kPix; ++q) {
       pyc[q] = (float)(wb.py + 4 * q) + 0.5f;
-      done[q] = !(wb.px < ti.W && wb.py + 4 * q < ti.H);
-      T[q] = 1.f;
+      T[q] = (wb.px < ti.W && wb.py + 4 * q < ti.H) ? 1.f : 0.f;
       cu[q] = 0.f;
     }
     const uint32_t n = ti.end - ti.beg;
@@ -224,7 +230,7 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
     float4 cA = z4;
     if (ovA) cA = __ldg(SP + 2 * (size_t)rA + 1);
     for (uint32_t g = 0; g < n; g += 32) {
-      if (!__any_sync(0xffffffffu, !all_done<kPix>(done))) break;
+      if (!__any_sync(0xffffffffu, live<kPix>(T))) break;
       const bool ovB = g + 32 + lane < n && box_overlaps(mB, wb);
       float4 cB = z4;
       if (ovB) cB = __ldg(SP + 2 * (size_t)rB + 1);
@@ -235,24 +241,29 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
       ovA = ovA && ellipse_reaches(mA, cA, wb, ln_amin);
       const uint32_t m = __ballot_sync(0xffffffffu, ovA);
       if (m) {
-        // the overlapping entries, compacted in list order: (mu, u, o), scaled conic
+        // the overlapping entries, compacted in list order: (mu, u, o), scaled conic;
+        // padded to whole batches with entries of opacity -1 (alpha < 0: always skipped)
         const int n_ov = __popc(m);
+        const int n_pad = (n_ov + kIgBatch - 1) / kIgBatch * kIgBatch;
         if (ovA) {
           const int s = __popc(m & lt);
           const float3 k2 = scaled_conic(cA);
           sm[s] = make_float4(mA.x, mA.y, mA.w, cA.w);
           sc[s] = make_float4(k2.x, k2.y, k2.z, 0.f);
         }
+        if (lane >= n_ov && lane < n_pad) {   // slots [n_ov, n_pad): disjoint from the staged ones
+          sm[lane] = make_float4(0.f, 0.f, 0.f, -1.f);
+          sc[lane] = z4;
+        }
         __syncwarp();
         // kIgBatch entries at a time: their alphas are independent and computed
         // together; the transmittance updates then run in list order
-        for (int i0 = 0; i0 < n_ov && !all_done<kPix>(done); i0 += kIgBatch) {
+        for (int i0 = 0; i0 < n_ov && live<kPix>(T); i0 += kIgBatch) {
           float al[kIgBatch][kPix], uu[kIgBatch];
 #pragma unroll
           for (int k = 0; k < kIgBatch; ++k) {
-            const int i = i0 + k < n_ov ? i0 + k : n_ov - 1;
-            const float4 mu = sm[i];
-            const float4 kk = sc[i];
+            const float4 mu = sm[i0 + k];
+            const float4 kk = sc[i0 + k];
             uu[k] = mu.z;
 #pragma unroll
             for (int q = 0; q < kPix; ++q)
@@ -262,11 +273,10 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
           for (int k = 0; k < kIgBatch; ++k) {
 #pragma unroll
             for (int q = 0; q < kPix; ++q) {
-              if (i0 + k >= n_ov || done[q]) continue;
               const float alpha = al[k][q];
               if (alpha < p.alpha_min) continue;
               const float Tn = T[q] * (1.f - alpha);
-              if (Tn < p.T_min) { done[q] = true; continue; }
+              if (Tn < p.T_min) { T[q] = 0.f; continue; }
               cu[q] += alpha * T[q] * uu[k];
               T[q] = Tn;
             }

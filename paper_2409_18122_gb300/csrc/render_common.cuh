@@ -152,6 +152,16 @@ __device__ __forceinline__ bool all_done(const bool* done) {
   return r;
 }
 
+// Some pixel of the lane is not saturated (the information-gain kernel keeps T = 0 for
+// saturated pixels and for pixels outside the image).
+template <int KP>
+__device__ __forceinline__ bool live(const float* T) {
+  bool r = false;
+#pragma unroll
+  for (int q = 0; q < KP; ++q) r = r || T[q] != 0.f;
+  return r;
+}
+
 // Can the support box of an entry contain a pixel centre of the warp's block?
 // s0 = first half of its splat record (mu_x, mu_y, packed half-widths, u).
 __device__ __forceinline__ bool box_overlaps(const float4& s0, const WarpBlock& wb) {
