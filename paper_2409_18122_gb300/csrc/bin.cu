@@ -31,7 +31,8 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kMaxGrid = 4096;
-constexpr int kChunkTarget = 16384;   // warp chunks over all views
+constexpr int kChunkTarget = 65536;   // warp chunks over all views
+constexpr int kPairsPerEntry = 4;     // pairs per (tile, chunk) count entry, at least
 constexpr int kWin = 1024;            // tile cells of a histogram window (shared memory per warp)
 constexpr int kPlaceWin = 512;        // tile cells of a placement window (two arrays per warp)
 constexpr int kWinCols = 256;         // widest window, in tiles
@@ -44,12 +45,18 @@ inline unsigned grid_for(int64_t n_cap) {
   return (unsigned)b;
 }
 
-// Chunks per view: about kChunkTarget warps in total, at most 2^22 count entries
-// (the per-(tile, chunk) table is written, scanned and read once per call).
-int chunks_per_view(int n_views, int64_t tile_cap) {
+// Chunks per view: about kChunkTarget warps in total, with at most pair_cap /
+// kPairsPerEntry and 2^24 count entries (the per-(tile, chunk) table is written,
+// scanned and read once per call, and each chunk walks every tile of its view, so the
+// table is kept small against the pairs: the pair capacity bounds their number).
+int chunks_per_view(int n_views, int64_t tile_cap, int64_t pair_cap) {
   int64_t k = (kChunkTarget + n_views - 1) / n_views;
-  const int64_t max_entries = (int64_t)1 << 22;
-  if (tile_cap > 0 && k * tile_cap > max_entries) k = max_entries / tile_cap;
+  if (tile_cap > 0) {
+    const int64_t by_table = ((int64_t)1 << 24) / tile_cap;
+    const int64_t by_pairs = pair_cap / kPairsPerEntry / tile_cap;
+    if (k > by_table) k = by_table;
+    if (k > by_pairs) k = by_pairs;
+  }
   if (k < 1) k = 1;
   return (int)k;
 }
@@ -233,38 +240,36 @@ __global__ void k_bin_ranges(const uint32_t* __restrict__ off, const uint32_t* _
   }
 }
 
-// q = floor(j / w) for 1 <= w and j < 2^16: a float estimate (relative error a
-// few ulp, so off by at most one) corrected to the exact quotient.
-__device__ __forceinline__ uint32_t div_small(uint32_t j, uint32_t w) {
-  uint32_t q = __float2uint_rz(__fdividef((float)j, (float)w));
-  if (q * w > j) --q;
-  if ((q + 1u) * w <= j) ++q;
-  return q;
-}
-
 // Step 6: every pair written to its slot.  A warp takes its chunk's records 32
 // at a time (a group; the next group's rectangles and record ids are loaded while
-// the current one is placed); their pairs inside the current window are enumerated
-// 32 at a time (a round; record order, each rectangle row-major), one pair per lane.
-// The lanes of a round holding pairs of the same window cell belong to different
-// records, in lane order: a warp match on the cell gives each its rank among them,
-// its slot is the cell's running slot plus that rank, and the lowest of them
-// advances the running slot for the next round.
+// the current one is placed).  The group's records that have pairs in the current
+// window are compacted, in order, into shared memory (corner, width, first pair,
+// record id and a reciprocal of the width), and their pairs are enumerated 32 at a
+// time (a round; record order, each rectangle row-major), one pair per lane.  The
+// record owning pair k is found from the records that start inside the round (one
+// warp OR of start bits and a population count), not by a search.  The lanes of a
+// round holding pairs of the same window cell belong to different records, in lane
+// order: a warp match on the cell gives each its rank among them, its slot is the
+// cell's running slot plus that rank, and the lowest of them advances the running
+// slot for the next round.
 template <bool kTileIds>
 __global__ void __launch_bounds__(kBinWarps * 32, 5) k_bin_place(const gs_proj proj, const uint32_t* __restrict__ seg,
-                                                              const uint32_t* __restrict__ srec,
-                                                              const ushort4* __restrict__ srect,
-                                                              const uint32_t* __restrict__ poff, int n_views, int K,
-                                                              int64_t tile_cap, const uint32_t* __restrict__ off,
-                                                              gs_bins out) {
+                                                                 const uint32_t* __restrict__ srec,
+                                                                 const ushort4* __restrict__ srect,
+                                                                 const uint32_t* __restrict__ poff, int n_views, int K,
+                                                                 int64_t tile_cap, const uint32_t* __restrict__ off,
+                                                                 gs_bins out) {
   __shared__ uint32_t s_run[kBinWarps][kPlaceWin];
+  __shared__ uint4 s_grp[kBinWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t le = (2u << lane) - 1u;   // lanes 0 .. lane (all 32 for lane 31)
   const int64_t cid = (int64_t)blockIdx.x * kBinWarps + warp;
   if (cid >= (int64_t)n_views * K) return;
   Chunk c;
   if (!chunk_of(cid, K, seg, poff, proj.view_info, tile_cap, c)) return;
   uint32_t* run = s_run[warp];
+  uint4* grp = s_grp[warp];
   const uint32_t cap = out.pair_capacity < 0xFFFFFFFFll ? (uint32_t)out.pair_capacity : 0xFFFFFFFFu;
   uint32_t ww, wh;
   window_size(c.tiles_x, c.tiles_y, kPlaceWin, false, ww, wh);
@@ -293,7 +298,7 @@ __global__ void __launch_bounds__(kBinWarps * 32, 5) k_bin_place(const gs_proj p
           rec_next = srec[g + 32 + lane];
         }
         // this lane's record, clipped to the window (window-relative corner)
-        uint32_t x0 = 0, y0 = 0, w = 1, cnt = 0, rec = 0;
+        uint32_t x0 = 0, y0 = 0, w = 1, cnt = 0;
         if (have) {
           const uint32_t cx0 = rc.x > xa ? rc.x : xa, cx1 = rc.z < xb ? rc.z : xb;
           const uint32_t cy0 = rc.y > ya ? rc.y : ya, cy1 = rc.w < yb ? rc.w : yb;
@@ -302,9 +307,10 @@ __global__ void __launch_bounds__(kBinWarps * 32, 5) k_bin_place(const gs_proj p
             y0 = cy0 - ya;
             w = cx1 - cx0;
             cnt = w * (cy1 - cy0);
-            rec = rec_g;
           }
         }
+        const uint32_t nz = __ballot_sync(0xffffffffu, cnt > 0u);
+        if (nz == 0u) continue;
         uint32_t incl = cnt;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -312,42 +318,46 @@ __global__ void __launch_bounds__(kBinWarps * 32, 5) k_bin_place(const gs_proj p
           if (lane >= d) incl += v;
         }
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        if (total == 0u) continue;
         const uint32_t excl = incl - cnt;
+        __syncwarp();   // the previous group's rounds are done with grp
+        if (cnt > 0u) {
+          // floor(j / w) = umulhi(j, ceil(2^32 / w)) exactly for j w < 2^32 (here j < 2^9, w <= 2^8)
+          const uint32_t magic = w > 1u ? 0xFFFFFFFFu / w + 1u : 0u;
+          grp[__popc(nz & lt)] = make_uint4(x0 | (y0 << 8) | (w << 17), excl, rec_g, magic);
+        }
+        __syncwarp();
+        uint32_t before = 0;   // records of the group whose first pair precedes this round
         for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+          const uint32_t d = excl - k0;   // < 32 iff this lane's record starts in the round
+          const uint32_t starts = __reduce_or_sync(0xffffffffu, (cnt > 0u && d < 32u) ? (1u << d) : 0u);
           const uint32_t k = k0 + lane;
-          int o = 0;   // owner: the first group record whose inclusive count exceeds k
-#pragma unroll
-          for (int step = 16; step >= 1; step >>= 1) {
-            const uint32_t v = __shfl_sync(0xffffffffu, incl, o + step - 1);
-            if (v <= k) o += step;
-          }
-          const uint32_t o_x0 = __shfl_sync(0xffffffffu, x0, o);
-          const uint32_t o_y0 = __shfl_sync(0xffffffffu, y0, o);
-          const uint32_t o_w = __shfl_sync(0xffffffffu, w, o);
-          const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, o);
-          const uint32_t o_rec = __shfl_sync(0xffffffffu, rec, o);
           const bool valid = k < total;
-          uint32_t i = 0xFFFFFFFFu, cy = 0, cx = 0;   // window cell, its row and column
+          uint32_t i = 0xFFFFFFFFu, cy = 0, cx = 0, o_rec = 0;   // window cell, its row and column
           if (valid) {
-            const uint32_t j = k - o_excl;
-            const uint32_t y = div_small(j, o_w);
-            cy = o_y0 + y;
-            cx = o_x0 + (j - y * o_w);
+            const uint4 e = grp[before + __popc(starts & le) - 1u];   // the owner of pair k
+            const uint32_t j = k - e.y;
+            const uint32_t ow = e.x >> 17;
+            const uint32_t y = ow > 1u ? __umulhi(j, e.w) : j;
+            cy = ((e.x >> 8) & 0x1FFu) + y;
+            cx = (e.x & 0xFFu) + (j - y * ow);
             i = cy * cols + cx;
+            o_rec = e.z;
           }
+          before += __popc(starts);
           // lanes of the same cell (invalid lanes share the key 0xFFFFFFFF and do nothing)
           const uint32_t peers = __match_any_sync(0xffffffffu, i);
           const uint32_t below = peers & lt;
+          uint32_t base = 0;
           if (valid) {
-            const uint32_t slot = run[i] + __popc(below);
+            base = run[i];
+            const uint32_t slot = base + __popc(below);
             if (slot < cap) {
               out.rec[slot] = o_rec;
               if (kTileIds) out.tile[slot] = c.tile_base + (ya + cy) * c.tiles_x + xa + cx;
             }
           }
           __syncwarp();
-          if (valid && below == 0u) run[i] += __popc(peers);   // lowest lane of the cell in this round
+          if (valid && below == 0u) run[i] = base + __popc(peers);   // lowest lane of the cell in this round
           __syncwarp();
         }
       }
@@ -358,8 +368,7 @@ __global__ void __launch_bounds__(kBinWarps * 32, 5) k_bin_place(const gs_proj p
 }  // namespace
 
 size_t bin_ws_bytes(int64_t rec_cap, int64_t pair_cap, int64_t tile_cap, int n_views) {
-  (void)pair_cap;
-  const int K = chunks_per_view(n_views, tile_cap);
+  const int K = chunks_per_view(n_views, tile_cap, pair_cap);
   const int64_t cnt_cap = (int64_t)K * tile_cap + 1;
   Carver c(nullptr);
   c.take<uint32_t>(n_views + 1);           // view segments
@@ -384,7 +393,7 @@ cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_vi
   (void)cams;
   (void)p;
   const int64_t rec_cap = proj.capacity, tile_cap = out.tile_capacity;
-  const int K = chunks_per_view(n_views, tile_cap);
+  const int K = chunks_per_view(n_views, tile_cap, out.pair_capacity);
   const int64_t cnt_cap = (int64_t)K * tile_cap + 1;
   Carver c(ws);
   uint32_t* seg = c.take<uint32_t>(n_views + 1);
