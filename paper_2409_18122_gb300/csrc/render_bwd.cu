@@ -8,9 +8,10 @@
 // The kernel replays each tile back to front starting from the saved final
 // transmittance and last index, recovering T_i = T_{i+1} / (1 - alpha_i), so no
 // per-pixel contributor list is stored.  Per-Gaussian screen-space gradients are
-// summed over the 32 pixels of a warp with shuffles and added with one float4
-// atomic per warp; a second kernel maps them through the projection per
-// Gaussian (records of one Gaussian are contiguous), without atomics.
+// summed over the 32 pixels of a warp with a shuffle reduce-scatter and added with
+// ten scalar atomics per (warp, entry), one from each lane holding a sum; a second
+// kernel maps them through the projection per Gaussian (records of one Gaussian
+// are contiguous), without atomics.
 #include "gs_common.cuh"
 #include "gs_internal.h"
 #include "render_common.cuh"
@@ -38,7 +39,7 @@ __device__ __forceinline__ float warp_sum16(float (&v)[16]) {
 }
 
 constexpr int kBwdWarps = 2;   // warps (work items) per CTA
-constexpr int kPix = 2;        // pixels per lane: one warp reduction per entry serves 64 pixels
+constexpr int kPix = 1;        // pixels per lane (8x4 blocks: finer culling beats sharing reductions)
 
 __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_proj proj, gs_bins bins,
                                                                 const gs_camera* __restrict__ cams, int n_views,

@@ -56,9 +56,8 @@ __device__ __forceinline__ float splat_alpha2(float mx, float my, const float3& 
 }
 
 // Work item of the compositing kernels: one warp renders one 8 x (4 KP) pixel
-// block of one screen tile, KP pixels per lane (KP = 1 for the forward and
-// information-gain kernels, 2 for the backward kernel, whose per-entry warp
-// reduction is then shared by 64 pixels).  Block b of a tile covers columns
+// block of one screen tile, KP pixels per lane (KP = 1 in every kernel: a larger
+// block per warp culls less finely, which costs more than it saves).  Block b of a tile covers columns
 // 8 (b mod (tile_w/8)) .. +7 and rows 4 KP (b div (tile_w/8)) .. +4 KP - 1;
 // lane l owns pixels (l mod 8, l div 8 + 4 q), q < KP.  Warps never wait for
 // each other: each walks its tile's list on its own and stops as soon as all of
