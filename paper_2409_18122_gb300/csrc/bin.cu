@@ -34,7 +34,7 @@ constexpr int kMaxGrid = 4096;
 constexpr int kChunkTarget = 65536;   // warp chunks over all views
 constexpr int kPairsPerEntry = 4;     // pairs per (tile, chunk) count entry, at least
 constexpr int kWin = 1024;            // tile cells of a histogram window (shared memory per warp)
-constexpr int kPlaceWin = 512;        // tile cells of a placement window (two arrays per warp)
+constexpr int kPlaceWin = 512;        // tile cells of a placement window (running slots per warp)
 constexpr int kWinCols = 256;         // widest window, in tiles
 constexpr int kBinWarps = 8;          // warps (= chunks) per block of the histogram / placement kernels
 

@@ -32,7 +32,7 @@ constexpr int kIgBatch = 8;    // ... and in the information-gain kernel
 // indices of group g+96.  Every fetch is issued one iteration before it is
 // used and none depends on a value loaded in the same iteration.
 
-__global__ void __launch_bounds__(kFwdWarps * 32) k_render_fwd(gs_map map, gs_proj proj, gs_bins bins,
+__global__ void __launch_bounds__(kFwdWarps * 32, 12) k_render_fwd(gs_map map, gs_proj proj, gs_bins bins,
                                                                 const gs_camera* __restrict__ cams, int n_views,
                                                                 gs_params p, gs_image img, uint32_t n_items) {
   __shared__ float4 s_stage[kFwdWarps][3][32];   // (mu_x, mu_y, u, -), (a, b, c, o), (r, g, b, depth)
