@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cfg4", action="store_true", help="skip the 3M-Gaussian exploration-map loop")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graph", type=int, default=1, help="capture the information-gain pass in a CUDA graph")
     # options for profiling runs (defaults give the benchmark)
@@ -193,11 +194,11 @@ class MapStep:
     iteration (forward, loss, backward, fused capturable Adam) is captured once in a CUDA
     graph and replayed; eager() runs it op by op (used for the per-stage breakdown)."""
 
-    def __init__(self, gs, scenes, weights=None, graph=True):
+    def __init__(self, gs, scenes, weights=None, graph=True, scene=None, capturable=None):
         import torch
         self.torch = torch
         self.gs = gs
-        sc = scenes.config2()
+        sc = scenes.config2() if scene is None else scene
         self.scene = sc
         gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
         self.frame = gs.Frame(gm.n, sc.cams, with_pair_tiles=False)
@@ -214,7 +215,8 @@ class MapStep:
         self.params = [t.clone().requires_grad_(True) for t in (gm.mo, gm.su, gm.q, gm.rgb)]
         self.host = [t.detach().cpu().pin_memory() for t in self.params]
         self.host_tgt = [self.tgt_rgb.cpu().pin_memory(), self.tgt_depth.cpu().pin_memory()]
-        self.opt = torch.optim.Adam(self.params, lr=1e-4, fused=True, capturable=graph)
+        self.opt = torch.optim.Adam(self.params, lr=1e-4, fused=True,
+                                    capturable=graph if capturable is None else capturable)
         self.loss_host = torch.zeros(1, dtype=torch.float32).pin_memory()
         self.loss_fn = gs.ImageLoss.for_cameras(sc.cams, gs.L1_WEIGHTS if weights is None else weights)
         self.graph = None
@@ -273,14 +275,16 @@ class IGStep:
     the graph bracket the compositing kernel (the step's dominant kernel).
     """
 
-    def __init__(self, gs, scenes, graph: bool, tiles=None, n_views: int = 0):
+    def __init__(self, gs, scenes, graph: bool, tiles=None, n_views: int = 0, scene=None, cams=None,
+                 record_capacity=None, pair_capacity: int = 300_000_000):
         import torch
         self.torch = torch
         self.gs = gs
-        sc = scenes.config3()
+        sc = scenes.config3() if scene is None else scene
         self.scene = sc
         self.gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
-        cams = sc.cams[:n_views] if n_views > 0 else sc.cams
+        cams = sc.cams if cams is None else cams
+        cams = cams[:n_views] if n_views > 0 else cams
         if tiles is None:
             self.tile_choice, self.tile_timings = gs.autotune_tiles(self.gm, cams, pair_capacity=400_000_000)
             torch.cuda.empty_cache()
@@ -288,7 +292,8 @@ class IGStep:
             self.tile_choice = dict(tiles)
         cams = gs.with_tiles(cams, self.tile_choice)
         self.cams = cams
-        self.frame = gs.Frame(self.gm.n, cams, pair_capacity=300_000_000, with_color=False, with_pair_tiles=False)
+        self.frame = gs.Frame(self.gm.n, cams, pair_capacity=pair_capacity, with_color=False, with_pair_tiles=False,
+                              record_capacity=record_capacity)
         while True:
             self.frame.reset_status()
             self.frame.project(self.gm)
@@ -532,6 +537,59 @@ def eq3_map_step(torch, gs, scenes, flush, steps=10):
     return out
 
 
+def config4_loop(torch, gs, scenes, tiles, flush, steps=5):
+    """The large exploration map (3M Gaussians, 40x40 m): one mapping iteration over 8
+    keyframes at 1280x720 (loss as in the 500k step) and one information-gain pass over
+    1,024 candidates (160x120 / 320x240 halves, the tiles the autotuner picked for those
+    classes), captured together in one CUDA graph and replayed; events inside the graph
+    split the two parts."""
+    sc, cands = scenes.config4()
+    m = MapStep(gs, scenes, graph=False, scene=sc, capturable=True)
+    ig = IGStep(gs, scenes, graph=False, tiles=tiles, scene=sc, cams=cands, record_capacity=400_000_000,
+                pair_capacity=1_500_000_000)
+    try:
+        ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(3)]
+    except TypeError:
+        return {"unavailable": "events inside a captured graph need torch.cuda.Event(external=True)"}
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            m.eager()
+            ig._run()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ev[0].record()
+        m.eager()
+        ev[1].record()
+        ig._run()
+        ev[2].record()
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    t_map, t_ig = [], []
+    for _ in range(steps):
+        flush()
+        g.replay()
+        torch.cuda.synchronize()
+        t_map.append(ev[0].elapsed_time(ev[1]))
+        t_ig.append(ev[1].elapsed_time(ev[2]))
+    ms_map, ms_ig = statistics.mean(t_map), statistics.mean(t_ig)
+    fr = ig.frame
+    out = {"gaussians": sc.gmap.n, "keyframes": len(sc.cams), "keyframe_px": "1280x720",
+           "candidates": len(cands), "steps": steps, "ms_per_step": ms_map + ms_ig,
+           "fwd_bwd": {"value": 1e3 / ms_map, "unit": "iters/s", "ms": ms_map},
+           "ig": {"value": len(cands) / (ms_ig / 1e3), "unit": "views/s", "ms": ms_ig},
+           "ig_records": int(fr.rec_count.item()), "ig_pairs": int(fr.pair_count.item()) & 0xFFFFFFFF,
+           "map_pairs": int(m.frame.pair_count.item()) & 0xFFFFFFFF,
+           "ig_tiles": {"%dx%d" % k: "%dx%d" % v for k, v in ig.tile_choice.items()}}
+    del g, m, ig, fr
+    torch.cuda.empty_cache()
+    return out
+
+
 def collision_timing(torch, gs, scenes, reps=20):
     """Collision check of 129 test points (one motion-primitive tree layer) against every
     Gaussian of the 3M-Gaussian, 40x40 m map, r_robot 0.3 m, lambda_g 3 (Sec. IV-B)."""
@@ -680,6 +738,7 @@ def run_ours(args):
     xi_free = render_free_xi(torch, gs, istep, flush)
     collide = collision_timing(torch, gs, scenes)
     eq3 = eq3_map_step(torch, gs, scenes, flush)
+    cfg4 = None if args.no_cfg4 else config4_loop(torch, gs, scenes, istep.tile_choice, flush)
     achieved = 16.0 * ig_contrib / t_comp / 1e12
     tiles_now = {"%dx%d" % k: "%dx%d" % v for k, v in istep.tile_choice.items()}
     traffic_src = None
@@ -739,6 +798,7 @@ def run_ours(args):
             "render_free_xi": xi_free,
             "collision_check": collide,
             "fwd_bwd_eq3_ssim": eq3,
+            "config4_loop": cfg4,
             "e2e": e2e,
             "roofline": roofline,
             "rooflines": rooflines,
