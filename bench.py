@@ -474,7 +474,8 @@ def pipeline_roofline(istep, contributing, t_pass, hbm_gbs, issue_tps):
 
 
 def cfg0_latency_us(torch, gs, scenes, reps=30):
-    """Device time of one forward render of config 0 (project, bin, composite)."""
+    """Device time of one forward render of config 0 (project, bin, composite), launched
+    call by call and replayed from a CUDA graph (median microseconds)."""
     sc = scenes.config0()
     gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
     fr = gs.Frame(gm.n, sc.cams)
@@ -482,15 +483,31 @@ def cfg0_latency_us(torch, gs, scenes, reps=30):
     for _ in range(3):
         fr.forward(gm, img)
     torch.cuda.synchronize()
-    t = []
-    for _ in range(reps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
+
+    def median_us(fn):
+        t = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1) * 1e3)
+        return statistics.median(t)
+
+    eager = median_us(lambda: fr.forward(gm, img))
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
         fr.forward(gm, img)
-        e1.record()
-        torch.cuda.synchronize()
-        t.append(e0.elapsed_time(e1) * 1e3)
-    return statistics.median(t)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fr.forward(gm, img)
+    g.replay()
+    torch.cuda.synchronize()
+    return {"eager": eager, "graph": median_us(g.replay), "unit": "us"}
 
 
 def render_free_xi(torch, gs, istep, flush, reps=10):
