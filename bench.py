@@ -693,14 +693,18 @@ def run_ours(args):
                 + (args.steps * mstep.kernels_per_replay if mstep else 0))
     barrier(world)
     clocks = sampler.stop()
-    # per-stage breakdown of the mapping step (entry points of the C ABI), from eager
-    # iterations outside the timed region (the timed iterations replay one CUDA graph)
-    stage_ms = {}
-    if mstep is not None:
+    # per-stage breakdown (entry points of the C ABI) from eager iterations outside the
+    # timed region (the timed iterations replay CUDA graphs)
+    def stages(fn):
         gs.TIMER = gs.StageTimer()
-        timed_loop(torch, max(3, min(args.steps, 10)), [("map", mstep.eager)], flush)
-        stage_ms = {k: statistics.mean(gs.TIMER.durations_ms(k)) for k in list(gs.TIMER.events)}
+        timed_loop(torch, max(3, min(args.steps, 10)), [("part", fn)], flush)
+        out = {k: statistics.mean(gs.TIMER.durations_ms(k)) for k in list(gs.TIMER.events)}
         gs.TIMER = None
+        return out
+
+    map_stage_ms = stages(mstep.eager) if mstep is not None else {}
+    ig_stage_ms = stages(istep._run) if istep is not None else {}
+    stage_ms = map_stage_ms if mstep is not None else ig_stage_ms
 
     t_map = sum(times.get("map", [0.0])) / 1e3
     t_ig = sum(times.get("ig", [0.0])) / 1e3
@@ -809,6 +813,7 @@ def run_ours(args):
             "ig_ms": t_ig_all / args.steps * 1e3,
             "ig_unbatched": unbatched,
             "stages_ms": stage_ms,
+            "ig_stages_ms_eager": ig_stage_ms,
             "work": ws,
             "ig_pipeline_roofline": pipe,
             "cfg0_forward_latency_us": lat0,
