@@ -473,6 +473,54 @@ def pipeline_roofline(istep, contributing, t_pass, hbm_gbs, issue_tps):
     return out
 
 
+def stage_roofline(pipe, stage_ms, hbm_gbs, issue_tps):
+    """Per stage of the information-gain pass: achieved algorithmic rate over the stage's
+    eager event-timed duration, against the roofline that bounds it (units as in
+    pipeline_roofline: the projection and compositing by FP32 issue, the binning by HBM)."""
+    n_pairs, recs, contrib = pipe["pairs"], pipe["records"], pipe["contributing"]
+    n_pv = pipe["pair_views"]
+    rows = {
+        "gs_project": ("alu", 25.0 * n_pv + 110.0 * recs, issue_tps * 1e12, "T lane-instr/s"),
+        "gs_bin_sort": ("hbm", 44.0 * n_pairs, hbm_gbs * 1e9, "GB/s"),
+        "gs_info_gain_composite": ("alu", 12.0 * contrib, issue_tps * 1e12, "T lane-instr/s"),
+    }
+    out = {}
+    for k, (bound, work, peak, unit) in rows.items():
+        ms = stage_ms.get(k)
+        if not ms:
+            continue
+        rate = work / (ms / 1e3)
+        scale = 1e12 if bound == "alu" else 1e9
+        out[k] = {"bound": bound, "ms": ms, "achieved": rate / scale, "peak": peak / scale, "unit": unit,
+                  "frac": rate / peak}
+    return out
+
+
+def map_stage_roofline(ws, n, n_views, stage_ms, hbm_gbs, issue_tps):
+    """Per stage of the mapping step: projection (25 instructions per (Gaussian, view), 110 per
+    visible record), binning (44 B per pair), forward compositing (10 instructions per
+    evaluated, 6 more per contributing (pixel, Gaussian)), backward (10 per evaluated, 38 per
+    contributing, plus the projection adjoint), loss (mean L1: 12 B per pixel and channel of
+    colour and depth: two reads, one gradient write)."""
+    rows = {
+        "gs_project": ("alu", 25.0 * n * n_views + 110.0 * ws["records"]),
+        "gs_bin_sort": ("hbm", 44.0 * ws["pairs"]),
+        "gs_render_fwd": ("alu", 10.0 * ws["evaluated"] + 6.0 * ws["contributing"]),
+        "gs_render_bwd": ("alu", 10.0 * ws["evaluated"] + 38.0 * ws["contributing"]),
+        "gs_image_loss": ("hbm", 12.0 * 4 * ws["pixels"]),
+    }
+    out = {}
+    for k, (bound, work) in rows.items():
+        ms = stage_ms.get(k)
+        if not ms:
+            continue
+        rate = work / (ms / 1e3)
+        peak, scale, unit = (issue_tps * 1e12, 1e12, "T lane-instr/s") if bound == "alu" else (hbm_gbs * 1e9, 1e9, "GB/s")
+        out[k] = {"bound": bound, "ms": ms, "achieved": rate / scale, "peak": peak / scale, "unit": unit,
+                  "frac": rate / peak}
+    return out
+
+
 def cfg0_latency_us(torch, gs, scenes, reps=30):
     """Device time of one forward render of config 0 (project, bin, composite), launched
     call by call and replayed from a CUDA graph (median microseconds)."""
@@ -814,6 +862,9 @@ def run_ours(args):
             "ig_unbatched": unbatched,
             "stages_ms": stage_ms,
             "ig_stages_ms_eager": ig_stage_ms,
+            "ig_stage_roofline": stage_roofline(pipe, ig_stage_ms, hbm, peak),
+            "map_stage_roofline": map_stage_roofline(ws, mstep.frame.n, len(mstep.scene.cams), map_stage_ms, hbm,
+                                                     peak),
             "work": ws,
             "ig_pipeline_roofline": pipe,
             "cfg0_forward_latency_us": lat0,

@@ -12,7 +12,8 @@
 //           zero-padded correlation with a symmetric window is itself) and forms
 //           dS/dx = G*dm1 + 2 x G*dm2 + y G*dm12, then dL/dx with the L1 sign term.
 // A one-CTA kernel sums the partials in FP64 in a fixed order.  Without the SSIM term
-// (w_ssim = 0) pass 1 writes the L1 gradient itself and pass 2 is skipped.
+// (w_ssim = 0) the loss is elementwise: one flat kernel over the colour and one over the
+// depth array (contiguous chunks per block, fixed partial slots) replaces both passes.
 #include <math.h>
 
 #include "gs_internal.h"
@@ -154,14 +155,13 @@ __device__ __forceinline__ void block_partial(float v0, float v1, float v2, doub
   }
 }
 
-template <bool kSsim>
 __global__ void __launch_bounds__(kLossThreads) k_loss_fwd(const __grid_constant__ LossArgs a) {
   const int t = blockIdx.x, ch = blockIdx.y;
   const TileGeo g = tile_geo(a, t, ch);
   const int c = threadIdx.x & 31, r0 = 2 * (threadIdx.x >> 5);
   float s_sum = 0.f, l1c = 0.f, l1d = 0.f;
 
-  if constexpr (kSsim) {
+  {
     __shared__ float s_in[5][kInH][kInW];  // x, y, x^2, y^2, xy
     __shared__ float s_h[5][kInH][kLTW];
     for (int i = threadIdx.x; i < kInH * kInW; i += kLossThreads) {
@@ -199,16 +199,6 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_fwd(const __grid_constant
       }
       l1c += fabsf(s_in[0][r0 + q + kR][c + kR] - s_in[1][r0 + q + kR][c + kR]);
     }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int px = g.x0 + c, py = g.y0 + r0 + q;
-      if (px >= g.W || py >= g.H) continue;
-      const int64_t o = g.base + (int64_t)py * g.W + px;
-      const float dc = a.rgb[o] - a.rgb_ref[o];
-      l1c += fabsf(dc);
-      if (a.d_rgb) a.d_rgb[o] = a.w_c * sgnf(dc) * a.inv_n;
-    }
   }
 
   if (ch == 0 && (a.depth || a.d_depth)) {
@@ -245,6 +235,26 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_ssim_bwd(const __grid_con
     const float dS = fmaf(y, b[2][q], fmaf(2.f * x, b[1][q], b[0][q]));
     a.d_rgb[o] = a.w_c * sgnf(x - y) * a.inv_n - a.w_s * a.inv_3n * dS;
   }
+}
+
+// Loss without the SSIM term: elementwise over the flat arrays.  Block b takes the
+// contiguous elements [b chunk, (b + 1) chunk) and stores its sum of |x - y| in field
+// `field` of partial slot slot0 + b (other fields zero); g = w sign(x - y) / N_p if g.
+// x == NULL (no depth): differences are zero.
+__global__ void __launch_bounds__(kLossThreads) k_loss_l1(const float* __restrict__ x, const float* __restrict__ y,
+                                                          float* __restrict__ g, int64_t n, int64_t chunk, float w,
+                                                          float inv_n, int field, double* __restrict__ part,
+                                                          int64_t slot0) {
+  const int64_t b0 = (int64_t)blockIdx.x * chunk;
+  const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
+  float acc = 0.f;
+#pragma unroll 4
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += kLossThreads) {
+    const float d = x ? x[i] - y[i] : 0.f;
+    acc += fabsf(d);
+    if (g) g[i] = w * sgnf(d) * inv_n;
+  }
+  block_partial(0.f, field == 1 ? acc : 0.f, field == 2 ? acc : 0.f, part + 3 * (slot0 + blockIdx.x));
 }
 
 __global__ void __launch_bounds__(kLossThreads)
@@ -335,7 +345,22 @@ cudaError_t launch_image_loss(const int32_t* sizes, int n_views, const float* rg
   }
 
   int64_t pix = 0, slot = 0;
-  for (int v0 = 0; v0 < n_views; v0 += kLossViewsPerLaunch) {
+  if (!ssim) {
+    // elementwise: contiguous chunks of at least 4096 elements (at most P / 1024 + 2 partial
+    // slots, within the 3 x tiles the workspace holds), about 8 blocks per SM of 152
+    int64_t chunk = (3 * lay.P + 152 * 8 - 1) / (152 * 8);
+    chunk = (chunk + 4 * kLossThreads - 1) / (4 * kLossThreads) * (4 * kLossThreads);
+    if (chunk < 4096) chunk = 4096;
+    const int64_t nb_c = (3 * lay.P + chunk - 1) / chunk, nb_d = (lay.P + chunk - 1) / chunk;
+    k_loss_l1<<<(unsigned)nb_c, kLossThreads, 0, st>>>(rgb, rgb_ref, d_rgb, 3 * lay.P, chunk, w.w_rgb, a.inv_n, 1,
+                                                       part, 0);
+    note_launch();
+    k_loss_l1<<<(unsigned)nb_d, kLossThreads, 0, st>>>(depth, depth_ref, d_depth, lay.P, chunk, w.w_depth, a.inv_n,
+                                                       2, part, nb_c);
+    note_launch();
+    slot = nb_c + nb_d;
+  }
+  for (int v0 = 0; v0 < n_views && ssim; v0 += kLossViewsPerLaunch) {
     const int nv = n_views - v0 < kLossViewsPerLaunch ? n_views - v0 : kLossViewsPerLaunch;
     a.n_views = nv;
     a.part_base = (int32_t)slot;
@@ -351,12 +376,9 @@ cudaError_t launch_image_loss(const int32_t* sizes, int n_views, const float* rg
       tb += ((W + kLTW - 1) / kLTW) * ((H + kLTH - 1) / kLTH);
     }
     const dim3 grid((unsigned)tb, 3);
-    if (ssim)
-      k_loss_fwd<true><<<grid, kLossThreads, 0, st>>>(a);
-    else
-      k_loss_fwd<false><<<grid, kLossThreads, 0, st>>>(a);
+    k_loss_fwd<<<grid, kLossThreads, 0, st>>>(a);
     note_launch();
-    if (ssim && d_rgb) {
+    if (d_rgb) {
       k_loss_ssim_bwd<<<grid, kLossThreads, 0, st>>>(a);
       note_launch();
     }
