@@ -85,21 +85,37 @@ __global__ void k_segments(const gs_proj proj, int n_views, int64_t tile_cap, in
     if (n == 0)
       for (int v = 0; v <= n_views; ++v) seg[v] = 0u;
   }
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t v = proj.view[i];
-    if (v >= n_views) {
-      set_flag(proj.status, GS_FLAG_BAD_RECORDS);
-      v = n_views - 1;
+  // four records per thread and 16-byte load when the view array is 16-byte aligned
+  const bool vec = ((uintptr_t)proj.view & 15u) == 0;
+  const int64_t per = vec ? 4 : 1;
+  const int64_t groups = (n + per - 1) / per;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < groups; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = j * per;
+    uint32_t vv[4];
+    if (vec && i0 + 4 <= n) {
+      const uint4 q = reinterpret_cast<const uint4*>(proj.view)[j];
+      vv[0] = q.x; vv[1] = q.y; vv[2] = q.z; vv[3] = q.w;
+    } else {
+      for (int k = 0; k < 4; ++k) vv[k] = (k < per && i0 + k < n) ? proj.view[i0 + k] : 0u;
     }
     int64_t prev = -1;
-    if (i > 0) {
-      prev = proj.view[i - 1];
+    if (i0 > 0) {
+      prev = proj.view[i0 - 1];
       if (prev >= n_views) prev = n_views - 1;
-      if (v < prev) set_flag(proj.status, GS_FLAG_BAD_RECORDS);
     }
-    for (int64_t u = prev + 1; u <= v; ++u) seg[u] = (uint32_t)i;
-    if (i == n - 1)
-      for (int64_t u = v + 1; u <= n_views; ++u) seg[u] = (uint32_t)n;
+    for (int k = 0; k < per && i0 + k < n; ++k) {
+      const int64_t i = i0 + k;
+      int64_t v = vv[k];
+      if (v >= n_views) {
+        set_flag(proj.status, GS_FLAG_BAD_RECORDS);
+        v = n_views - 1;
+      }
+      if (v < prev) set_flag(proj.status, GS_FLAG_BAD_RECORDS);
+      for (int64_t u = prev + 1; u <= v; ++u) seg[u] = (uint32_t)i;
+      if (i == n - 1)
+        for (int64_t u = v + 1; u <= n_views; ++u) seg[u] = (uint32_t)n;
+      prev = v;
+    }
   }
 }
 

@@ -155,6 +155,25 @@ def test_bin_sort_empty_and_overflow():
     assert need == O.bin_sort(rec, cams)["n_pairs"] > 1000
 
 
+def test_bin_sort_flags_bad_records():
+    """Records grouped by increasing view pass; two records of different views swapped (out
+    of view order), or a view id >= V, set GS_FLAG_BAD_RECORDS (the kernels clamp the view
+    ids and clip the rectangles, so nothing is read or written out of bounds)."""
+    cams = [Camera(100, 100, 60, 40, 120, 80), Camera(100, 100, 60, 40, 120, 80)]
+    rec = scenes.synthetic_records(11, 3000, cams, max_extent=4)
+    rec["dkey"] = rec["depth"].view(np.uint32)
+    bad_flag = gs.L.GS_FLAG_BAD_RECORDS
+    assert not (_bin_only(rec, cams).read_status() & bad_flag)
+    i = int(np.argmax(rec["view"] == 1))   # first record of view 1
+    assert i > 0
+    swapped = {k: v.copy() for k, v in rec.items()}
+    swapped["view"][[i - 1, i]] = swapped["view"][[i, i - 1]]
+    assert _bin_only(swapped, cams).read_status() & bad_flag
+    beyond = {k: v.copy() for k, v in rec.items()}
+    beyond["view"][-1] = len(cams)
+    assert _bin_only(beyond, cams).read_status() & bad_flag
+
+
 @pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
 def test_bin_sort_pipeline_room_subset(tile):
     """Projection + binning on the first 4,096 Gaussians of the 200k-Gaussian room, bit-exact."""
