@@ -50,6 +50,8 @@ IG_TRAFFIC_SHA1 = "322ede6e36016f9caddf0da6504b0778f2e269e8"
 IG_TRAFFIC = [
     {"tiles": {"80x60": "8x8", "160x120": "16x16", "320x240": "16x16"}, "bytes": 5.834e9 + 4.09e6},
     {"tiles": {"80x60": "8x8", "160x120": "16x8", "320x240": "32x16"}, "bytes": 5.558e9 + 4.27e6},
+    {"tiles": {"80x60": "8x8", "160x120": "16x16", "320x240": "32x16"}, "bytes": 5.812e9 + 3.76e6},
+    {"tiles": {"80x60": "8x8", "160x120": "16x8", "320x240": "16x16"}, "bytes": 5.628e9 + 4.20e6},
 ]
 IG_TRAFFIC_HEADERS = ("render_common.cuh", "gs_common.cuh")
 
