@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
                                                                 const gs_camera* __restrict__ cams, int n_views,
                                                                 gs_params p, gs_image fwd, gs_image_grad grad,
                                                                 float4* __restrict__ g2d, uint32_t n_items) {
-  __shared__ float4 s_stage[kBwdWarps][3][32];
+  __shared__ float4 s_stage[kBwdWarps][4][32];   // (mu), (conic, o), (colour, depth), (scaled conic)
+  static_assert(kPix == 1, "the entry body below is written for one pixel per lane");
   __shared__ uint32_t s_rec[kBwdWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t item = blockIdx.x * kBwdWarps + warp;
@@ -57,6 +58,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
   float4* sx = s_stage[warp][0];
   float4* sc = s_stage[warp][1];
   float4* sr = s_stage[warp][2];
+  float4* sk = s_stage[warp][3];
   uint32_t* srec = s_rec[warp];
   const float pxc = (float)wb.px + 0.5f;
   const float ln_amin = __logf(p.alpha_min);
@@ -130,9 +132,11 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
     uint32_t m = __ballot_sync(0xffffffffu, ovA);
     if (m) {
       if (ovA) {
+        const float3 k2 = scaled_conic(cA);
         sx[lane] = make_float4(mA.x, mA.y, 0.f, 0.f);
         sc[lane] = cA;
         sr[lane] = kA;
+        sk[lane] = make_float4(k2.x, k2.y, k2.z, 0.f);
         srec[lane] = rA;
       }
       __syncwarp();
@@ -142,52 +146,42 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
         const int pos = g + b;   // position in the tile's list
         const float4 mu = sx[b];
         const float4 k = sc[b];
-        bool contrib[kPix];
-        float al[kPix], G[kPix], dx[kPix], dy[kPix];
-#pragma unroll
-        for (int q = 0; q < kPix; ++q) {
-          contrib[q] = inside[q] && pos < last[q];
-          al[q] = G[q] = dx[q] = dy[q] = 0.f;
-          if (contrib[q]) {
-            al[q] = splat_alpha2(mu.x, mu.y, scaled_conic(k), k.w, pxc, pyc[q], p.alpha_max, dx[q], dy[q], G[q]);
-            if (al[q] < p.alpha_min) contrib[q] = false;
-          }
-        }
-        bool any_c = false;
-#pragma unroll
-        for (int q = 0; q < kPix; ++q) any_c = any_c || contrib[q];
-        if (!__any_sync(0xffffffffu, any_c)) continue;
-        float v[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        const float4 ks = sk[b];
+        // the alpha of the forward pass (same staged scaled conic, same operations)
+        float dx = 0.f, dy = 0.f, G = 0.f, al = 0.f;
+        const bool live = inside[0] && pos < last[0];
+        if (live) al = splat_alpha2(mu.x, mu.y, make_float3(ks.x, ks.y, ks.z), k.w, pxc, pyc[0], p.alpha_max, dx, dy, G);
+        const bool contrib = live && !(al < p.alpha_min);
+        if (!__any_sync(0xffffffffu, contrib)) continue;
+        // A lane that does not contribute runs the same arithmetic with alpha = G = dx = dy = 0:
+        // its T and suffix sums stay exactly unchanged (T * 1, S + 0) and every term is zero.
+        if (!contrib) al = G = dx = dy = 0.f;
         const float4 c = sr[b];
+        const float inv = 1.f / (1.f - al);
+        const float Ti = T[0] * inv;
+        const float w = al * Ti;
+        const float dalpha = (gr[0] * c.x + gg[0] * c.y + gb[0] * c.z + gd[0] * c.w) * Ti -
+                             (gr[0] * Sr[0] + gg[0] * Sg[0] + gb[0] * Sb[0] + gd[0] * Sd[0]) * inv;
+        Sr[0] += w * c.x;
+        Sg[0] += w * c.y;
+        Sb[0] += w * c.z;
+        Sd[0] += w * c.w;
+        T[0] = Ti;
+        const bool free = __fmul_rn(k.w, G) < p.alpha_max;   // alpha not clamped
+        const float dq = free ? -0.5f * al * dalpha : 0.f;    // dL/dq
+        float v[16];
+        v[0] = dq * 2.f * (k.x * dx + k.y * dy);  // dL/dmu_x (dx = mu_x - p_x)
+        v[1] = dq * 2.f * (k.y * dx + k.z * dy);  // dL/dmu_y
+        v[2] = dq * dx * dx;                      // dL/da
+        v[3] = dq * 2.f * dx * dy;                // dL/db
+        v[4] = dq * dy * dy;                      // dL/dc
+        v[5] = free ? dalpha * G : 0.f;           // dL/do
+        v[6] = gd[0] * w;
+        v[7] = gr[0] * w;
+        v[8] = gg[0] * w;
+        v[9] = gb[0] * w;
 #pragma unroll
-        for (int q = 0; q < kPix; ++q) {
-          if (!contrib[q]) continue;
-          const float om = 1.f - al[q];
-          const float Ti = T[q] / om;
-          const float w = al[q] * Ti;
-          const float dalpha = (gr[q] * c.x + gg[q] * c.y + gb[q] * c.z + gd[q] * c.w) * Ti -
-                               (gr[q] * Sr[q] + gg[q] * Sg[q] + gb[q] * Sb[q] + gd[q] * Sd[q]) / om;
-          Sr[q] += w * c.x;
-          Sg[q] += w * c.y;
-          Sb[q] += w * c.z;
-          Sd[q] += w * c.w;
-          T[q] = Ti;
-          v[7] += gr[q] * w;
-          v[8] += gg[q] * w;
-          v[9] += gb[q] * w;
-          v[6] += gd[q] * w;
-          if (__fmul_rn(k.w, G[q]) < p.alpha_max) {     // not clamped
-            v[5] += dalpha * G[q];                           // dL/do
-            const float dq = -0.5f * al[q] * dalpha;         // dL/dq
-            v[0] += dq * 2.f * (k.x * dx[q] + k.y * dy[q]);  // dL/dmu_x (dx = mu_x - p_x)
-            v[1] += dq * 2.f * (k.y * dx[q] + k.z * dy[q]);  // dL/dmu_y
-            v[2] += dq * dx[q] * dx[q];                      // dL/da
-            v[3] += dq * 2.f * dx[q] * dy[q];                // dL/db
-            v[4] += dq * dy[q] * dy[q];                      // dL/dc
-          }
-        }
+        for (int i = 10; i < 16; ++i) v[i] = 0.f;
         const float tot = warp_sum16(v);   // sum of v[lane / 2]
         const int j = lane >> 1;
         if ((lane & 1) == 0 && j < 10) {
