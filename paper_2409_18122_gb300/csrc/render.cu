@@ -21,7 +21,7 @@ namespace {
 constexpr int kFwdWarps = 2;   // warps (work items) per CTA: small CTAs free their slot as soon as both finish
 constexpr int kIgWarps = 8;    // warps per CTA of the persistent information-gain kernel
 constexpr int kPix = 1;        // pixels per lane of the forward and information-gain kernels
-constexpr int kFwdBatch = 4;   // overlapping entries whose alphas are computed together (forward)
+constexpr int kFwdBatch = 2;   // overlapping entries whose alphas are computed together (forward)
 constexpr int kIgBatch = 8;    // ... and in the information-gain kernel
 
 // The list walk of all compositing kernels is a four-stage software pipeline

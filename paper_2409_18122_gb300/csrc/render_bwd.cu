@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
         // its T and suffix sums stay exactly unchanged (T * 1, S + 0) and every term is zero.
         if (!contrib) al = G = dx = dy = 0.f;
         const float4 c = sr[b];
-        const float inv = 1.f / (1.f - al);
+        const float inv = __fdividef(1.f, 1.f - al);   // 1 - alpha in [1 - alpha_max, 1]: approximate reciprocal
         const float Ti = T[0] * inv;
         const float w = al * Ti;
         const float dalpha = (gr[0] * c.x + gg[0] * c.y + gb[0] * c.z + gd[0] * c.w) * Ti -
