@@ -8,7 +8,7 @@
 // The kernel replays each tile back to front starting from the saved final
 // transmittance and last index, recovering T_i = T_{i+1} / (1 - alpha_i), so no
 // per-pixel contributor list is stored.  Per-Gaussian screen-space gradients are
-// summed over the 32 pixels of a warp with a shuffle reduce-scatter and added with
+// summed over the 32 pixels of a warp with a 12-shuffle reduce-scatter and added with
 // ten scalar atomics per (warp, entry), one from each lane holding a sum; a second
 // kernel maps them through the projection per Gaussian (records of one Gaussian
 // are contiguous), without atomics.
@@ -19,29 +19,45 @@
 namespace gs {
 namespace {
 
-// Warp reduce-scatter of 16 values: on return, lanes 2j and 2j+1 hold the sum over
-// the warp of v[j].  Each halving step keeps half of the values and adds the
-// partner lane's copy of the same half: 8 + 4 + 2 + 1 + 1 = 16 shuffles for all
-// sixteen sums (a separate butterfly per value would take 80).
-__device__ __forceinline__ float warp_sum16(float (&v)[16]) {
+// Warp reduce-scatter of the ten gradient terms of an entry.  Each halving step keeps
+// part of the values and adds the partner lane's copy of the same part: 5 values per
+// half-warp after the first step (pairs (i, i + 5)), then 3 (of 5 padded to 6), 2 (of
+// 3 padded to 4), 1, and a last exchange: 5 + 3 + 2 + 1 + 1 = 12 shuffles.  On return
+// lanes 2m and 2m + 1 hold the sum over the warp of v[j] with, for lane bits
+// (b4, b3, b2, b1), j = 5 b4 + s, s = 3 b3 + 2 b2 + b1, where s <= 2 (b3 = 0) or
+// s <= 4 (b3 = 1); other lanes hold padding.
+__device__ __forceinline__ float warp_sum10(const float (&v)[10]) {
   const int lane = threadIdx.x & 31;
+  float u[6], w[4], x[2];
+  {
+    const bool hi = (lane & 16) != 0;
 #pragma unroll
-  for (int n = 8, d = 16; n >= 1; n >>= 1, d >>= 1) {
-    const bool hi = (lane & d) != 0;   // this lane keeps the upper half of its n pairs
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-      const float keep = hi ? v[i + n] : v[i];
-      const float send = hi ? v[i] : v[i + n];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, d);
-    }
+    for (int i = 0; i < 5; ++i)
+      u[i] = (hi ? v[i + 5] : v[i]) + __shfl_xor_sync(0xffffffffu, hi ? v[i] : v[i + 5], 16);
+    u[5] = 0.f;
   }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+  {
+    const bool hi = (lane & 8) != 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      w[i] = (hi ? u[i + 3] : u[i]) + __shfl_xor_sync(0xffffffffu, hi ? u[i] : u[i + 3], 8);
+    w[3] = 0.f;
+  }
+  {
+    const bool hi = (lane & 4) != 0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+      x[i] = (hi ? w[i + 2] : w[i]) + __shfl_xor_sync(0xffffffffu, hi ? w[i] : w[i + 2], 4);
+  }
+  const bool hi = (lane & 2) != 0;
+  const float y = (hi ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, hi ? x[0] : x[1], 2);
+  return y + __shfl_xor_sync(0xffffffffu, y, 1);
 }
 
 constexpr int kBwdWarps = 2;   // warps (work items) per CTA
 constexpr int kPix = 1;        // pixels per lane (8x4 blocks: finer culling beats sharing reductions)
 
-__global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_proj proj, gs_bins bins,
+__global__ void __launch_bounds__(kBwdWarps * 32, 16) k_render_bwd(gs_map map, gs_proj proj, gs_bins bins,
                                                                 const gs_camera* __restrict__ cams, int n_views,
                                                                 gs_params p, gs_image fwd, gs_image_grad grad,
                                                                 float4* __restrict__ g2d, uint32_t n_items) {
@@ -169,7 +185,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
         T[0] = Ti;
         const bool free = __fmul_rn(k.w, G) < p.alpha_max;   // alpha not clamped
         const float dq = free ? -0.5f * al * dalpha : 0.f;    // dL/dq
-        float v[16];
+        float v[10];
         v[0] = dq * 2.f * (k.x * dx + k.y * dy);  // dL/dmu_x (dx = mu_x - p_x)
         v[1] = dq * 2.f * (k.y * dx + k.z * dy);  // dL/dmu_y
         v[2] = dq * dx * dx;                      // dL/da
@@ -180,11 +196,11 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
         v[7] = gr[0] * w;
         v[8] = gg[0] * w;
         v[9] = gb[0] * w;
-#pragma unroll
-        for (int i = 10; i < 16; ++i) v[i] = 0.f;
-        const float tot = warp_sum16(v);   // sum of v[lane / 2]
-        const int j = lane >> 1;
-        if ((lane & 1) == 0 && j < 10) {
+        const float tot = warp_sum10(v);
+        const int b3 = (lane >> 3) & 1;
+        const int sidx = 3 * b3 + 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
+        if ((lane & 1) == 0 && sidx <= (b3 ? 4 : 2)) {
+          const int j = 5 * ((lane >> 4) & 1) + sidx;   // the term this lane holds the sum of
           // per-record gradient slots: (v0, v1, v2, v3), (v4, v5, v6, -), (v7, v8, v9, -)
           float* dst = reinterpret_cast<float*>(g2d + 3 * (size_t)srec[b]);
           atomicAdd(dst + (j < 7 ? j : j + 1), tot);
