@@ -523,13 +523,22 @@ def map_stage_roofline(ws, n, n_views, stage_ms, hbm_gbs, issue_tps):
     return out
 
 
-def cfg0_latency_us(torch, gs, scenes, reps=30):
+def cfg0_latency_us(torch, gs, scenes, reps=30, scene=None):
     """Device time of one forward render of config 0 (project, bin, composite), launched
-    call by call and replayed from a CUDA graph (median microseconds)."""
-    sc = scenes.config0()
+    call by call and replayed from a CUDA graph (median microseconds); `scene` renders
+    another single-view config the same way."""
+    sc = scenes.config0() if scene is None else scene
     gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
     fr = gs.Frame(gm.n, sc.cams)
     img = fr.new_images()
+    while True:
+        fr.reset_status()
+        fr.forward(gm, img)
+        torch.cuda.synchronize()
+        if not fr.grow_if_needed():
+            break
+        img = fr.new_images()
+    fr.check_status()
     for _ in range(3):
         fr.forward(gm, img)
     torch.cuda.synchronize()
@@ -703,9 +712,16 @@ def oracle_sample(sc3):
 def cpu_baseline(sc3):
     """The FP64 oracle, as it stands, on the host cores (bounded sample, scaled per pixel)."""
     from oracle import oracle as O
+    import time
+    from paper_2409_18122_gb300 import scenes
     t, px = oracle_sample(sc3)
     value = px / t / mix_pixels_per_view(sc3.cams)
+    sc0 = scenes.config0()
+    t0 = time.perf_counter()
+    O.render_images(sc0.gmap, sc0.cams)
+    t_cfg0 = time.perf_counter() - t0
     return {"value": value, "unit": "views/s", "cores": O.num_threads(), "kind": "oracle",
+            "cfg0_full_render_s": t_cfg0,
             "sample": "FP64 brute-force information gain of candidates 0 (80x60) and 1 (160x120) over the full "
                       "1M-Gaussian map (%.1f s for %d pixels), scaled to the 256-view mix by pixel count "
                       "(%.0f pixels per view)" % (t, px, mix_pixels_per_view(sc3.cams))}
@@ -806,6 +822,7 @@ def run_ours(args):
     hbm = float(peaks.get("hbm_gbs", 6673.5))
     pipe = pipeline_roofline(istep, ig_contrib, t_ig_all / args.steps, hbm, peak)
     lat0 = cfg0_latency_us(torch, gs, scenes)
+    lat1 = cfg0_latency_us(torch, gs, scenes, reps=20, scene=scenes.config1())
     xi_free = render_free_xi(torch, gs, istep, flush)
     collide = collision_timing(torch, gs, scenes)
     eq3 = eq3_map_step(torch, gs, scenes, flush)
@@ -870,6 +887,7 @@ def run_ours(args):
             "work": ws,
             "ig_pipeline_roofline": pipe,
             "cfg0_forward_latency_us": lat0,
+            "cfg1_forward_latency_us": lat1,
             "render_free_xi": xi_free,
             "collision_check": collide,
             "fwd_bwd_eq3_ssim": eq3,
