@@ -57,11 +57,11 @@ __device__ __forceinline__ float warp_sum10(const float (&v)[10]) {
 constexpr int kBwdWarps = 2;   // warps (work items) per CTA
 constexpr int kPix = 1;        // pixels per lane (8x4 blocks: finer culling beats sharing reductions)
 
-__global__ void __launch_bounds__(kBwdWarps * 32, 16) k_render_bwd(gs_map map, gs_proj proj, gs_bins bins,
+__global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_proj proj, gs_bins bins,
                                                                 const gs_camera* __restrict__ cams, int n_views,
                                                                 gs_params p, gs_image fwd, gs_image_grad grad,
                                                                 float4* __restrict__ g2d, uint32_t n_items) {
-  __shared__ float4 s_stage[kBwdWarps][4][32];   // (mu), (conic, o), (colour, depth), (scaled conic)
+  __shared__ float4 s_stage[kBwdWarps][3][32];   // (mu), (colour, depth), (scaled conic, o)
   static_assert(kPix == 1, "the entry body below is written for one pixel per lane");
   __shared__ uint32_t s_rec[kBwdWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -72,9 +72,8 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 16) k_render_bwd(gs_map map, g
   WarpBlock wb;
   warp_block<kPix>(ti, wb);
   float4* sx = s_stage[warp][0];
-  float4* sc = s_stage[warp][1];
-  float4* sr = s_stage[warp][2];
-  float4* sk = s_stage[warp][3];
+  float4* sr = s_stage[warp][1];
+  float4* sk = s_stage[warp][2];
   uint32_t* srec = s_rec[warp];
   const float pxc = (float)wb.px + 0.5f;
   const float ln_amin = __logf(p.alpha_min);
@@ -150,9 +149,8 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 16) k_render_bwd(gs_map map, g
       if (ovA) {
         const float3 k2 = scaled_conic(cA);
         sx[lane] = make_float4(mA.x, mA.y, 0.f, 0.f);
-        sc[lane] = cA;
         sr[lane] = kA;
-        sk[lane] = make_float4(k2.x, k2.y, k2.z, 0.f);
+        sk[lane] = make_float4(k2.x, k2.y, k2.z, cA.w);
         srec[lane] = rA;
       }
       __syncwarp();
@@ -161,12 +159,11 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 16) k_render_bwd(gs_map map, g
         m ^= 1u << b;
         const int pos = g + b;   // position in the tile's list
         const float4 mu = sx[b];
-        const float4 k = sc[b];
         const float4 ks = sk[b];
         // the alpha of the forward pass (same staged scaled conic, same operations)
         float dx = 0.f, dy = 0.f, G = 0.f, al = 0.f;
         const bool live = inside[0] && pos < last[0];
-        if (live) al = splat_alpha2(mu.x, mu.y, make_float3(ks.x, ks.y, ks.z), k.w, pxc, pyc[0], p.alpha_max, dx, dy, G);
+        if (live) al = splat_alpha2(mu.x, mu.y, make_float3(ks.x, ks.y, ks.z), ks.w, pxc, pyc[0], p.alpha_max, dx, dy, G);
         const bool contrib = live && !(al < p.alpha_min);
         if (!__any_sync(0xffffffffu, contrib)) continue;
         // A lane that does not contribute runs the same arithmetic with alpha = G = dx = dy = 0:
@@ -183,14 +180,16 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 16) k_render_bwd(gs_map map, g
         Sb[0] += w * c.z;
         Sd[0] += w * c.w;
         T[0] = Ti;
-        const bool free = __fmul_rn(k.w, G) < p.alpha_max;   // alpha not clamped
+        const bool free = __fmul_rn(ks.w, G) < p.alpha_max;   // alpha not clamped
         const float dq = free ? -0.5f * al * dalpha : 0.f;    // dL/dq
+        // dL/dmu_2D = 2 (a P + b Q, b P + c Q) with P = sum dq dx, Q = sum dq dy (dx = mu_x - p_x):
+        // the conic is the record's, so P and Q are summed and k_proj_adjoint applies it
         float v[10];
-        v[0] = dq * 2.f * (k.x * dx + k.y * dy);  // dL/dmu_x (dx = mu_x - p_x)
-        v[1] = dq * 2.f * (k.y * dx + k.z * dy);  // dL/dmu_y
-        v[2] = dq * dx * dx;                      // dL/da
-        v[3] = dq * 2.f * dx * dy;                // dL/db
-        v[4] = dq * dy * dy;                      // dL/dc
+        v[0] = dq * dx;              // P
+        v[1] = dq * dy;              // Q
+        v[2] = v[0] * dx;            // dL/da
+        v[3] = 2.f * v[0] * dy;      // dL/db
+        v[4] = v[1] * dy;            // dL/dc
         v[5] = free ? dalpha * G : 0.f;           // dL/do
         v[6] = gd[0] * w;
         v[7] = gr[0] * w;
@@ -261,14 +260,16 @@ __global__ void __launch_bounds__(256) k_proj_adjoint(gs_map map, gs_proj proj, 
     const float4 A = g2d[3 * (size_t)r], Bv = g2d[3 * (size_t)r + 1], Cv = g2d[3 * (size_t)r + 2];
     grgb[0] += Cv.x; grgb[1] += Cv.y; grgb[2] += Cv.z;
     go += Bv.y;
-    const float gmx = A.x, gmy = A.y, ga = A.z, gb = A.w, gc = Bv.x, gdep = Bv.z;
+    const float4 con = reinterpret_cast<const float4*>(proj.splat)[2 * (size_t)r + 1];
+    // slots A.x, A.y hold P = sum dq dx, Q = sum dq dy: dL/dmu_2D = 2 (a P + b Q, b P + c Q)
+    const float gmx = 2.f * (con.x * A.x + con.y * A.y), gmy = 2.f * (con.y * A.x + con.z * A.y);
+    const float ga = A.z, gb = A.w, gc = Bv.x, gdep = Bv.z;
     const gs_camera& cam = cams[v];
     const float* R = cam.R;
     const float dx = mo.x - cam.T[0], dy = mo.y - cam.T[1], dz = mo.z - cam.T[2];
     const float tx = R[0] * dx + R[3] * dy + R[6] * dz;
     const float ty = R[1] * dx + R[4] * dy + R[7] * dz;
     const float tz = R[2] * dx + R[5] * dy + R[8] * dz;
-    const float4 con = reinterpret_cast<const float4*>(proj.splat)[2 * (size_t)r + 1];
     // dL/dSigma2D = -C G_C C (symmetric-matrix gradients)
     const float C00 = con.x, C01 = con.y, C11 = con.z;
     const float G00 = ga, G01 = 0.5f * gb, G11 = gc;
