@@ -161,44 +161,42 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_fwd(const __grid_constant
   const int c = threadIdx.x & 31, r0 = 2 * (threadIdx.x >> 5);
   float s_sum = 0.f, l1c = 0.f, l1d = 0.f;
 
-  {
-    __shared__ float s_in[5][kInH][kInW];  // x, y, x^2, y^2, xy
-    __shared__ float s_h[5][kInH][kLTW];
-    for (int i = threadIdx.x; i < kInH * kInW; i += kLossThreads) {
-      const int r = i / kInW, cc = i - r * kInW;
-      const int gx = g.x0 - kR + cc, gy = g.y0 - kR + r;
-      const bool in = gx >= 0 && gx < g.W && gy >= 0 && gy < g.H;
-      const int64_t o = g.base + (int64_t)gy * g.W + gx;
-      const float xv = in ? a.rgb[o] : 0.f, yv = in ? a.rgb_ref[o] : 0.f;
-      s_in[0][r][cc] = xv;
-      s_in[1][r][cc] = yv;
-      s_in[2][r][cc] = xv * xv;
-      s_in[3][r][cc] = yv * yv;
-      s_in[4][r][cc] = xv * yv;
-    }
-    __syncthreads();
-    float m[5][2];
-    blur_tile<5>(a, s_in, s_h, m);
+  __shared__ float s_in[5][kInH][kInW];  // x, y, x^2, y^2, xy
+  __shared__ float s_h[5][kInH][kLTW];
+  for (int i = threadIdx.x; i < kInH * kInW; i += kLossThreads) {
+    const int r = i / kInW, cc = i - r * kInW;
+    const int gx = g.x0 - kR + cc, gy = g.y0 - kR + r;
+    const bool in = gx >= 0 && gx < g.W && gy >= 0 && gy < g.H;
+    const int64_t o = g.base + (int64_t)gy * g.W + gx;
+    const float xv = in ? a.rgb[o] : 0.f, yv = in ? a.rgb_ref[o] : 0.f;
+    s_in[0][r][cc] = xv;
+    s_in[1][r][cc] = yv;
+    s_in[2][r][cc] = xv * xv;
+    s_in[3][r][cc] = yv * yv;
+    s_in[4][r][cc] = xv * yv;
+  }
+  __syncthreads();
+  float m[5][2];
+  blur_tile<5>(a, s_in, s_h, m);
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int px = g.x0 + c, py = g.y0 + r0 + q;
-      if (px >= g.W || py >= g.H) continue;
-      const int64_t o = g.base + (int64_t)py * g.W + px;
-      const float mx = m[0][q], my = m[1][q];
-      const float sxx = m[2][q] - mx * mx, syy = m[3][q] - my * my, sxy = m[4][q] - mx * my;
-      const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
-      const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
-      const float iD = __frcp_rn(B1 * B2);
-      const float S = A1 * A2 * iD;
-      s_sum += S;
-      if (a.d_rgb) {
-        // dS/dm1 = 2 my (A2 - A1) / D - 2 mx S (1/B1 - 1/B2);  dS/dm2 = -S / B2;  dS/dm12 = 2 A1 / D
-        a.dm[o] = 2.f * iD * (my * (A2 - A1) - mx * S * (B2 - B1));
-        a.dm[3 * a.P + o] = -S * B1 * iD;
-        a.dm[6 * a.P + o] = 2.f * A1 * iD;
-      }
-      l1c += fabsf(s_in[0][r0 + q + kR][c + kR] - s_in[1][r0 + q + kR][c + kR]);
+  for (int q = 0; q < 2; ++q) {
+    const int px = g.x0 + c, py = g.y0 + r0 + q;
+    if (px >= g.W || py >= g.H) continue;
+    const int64_t o = g.base + (int64_t)py * g.W + px;
+    const float mx = m[0][q], my = m[1][q];
+    const float sxx = m[2][q] - mx * mx, syy = m[3][q] - my * my, sxy = m[4][q] - mx * my;
+    const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
+    const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
+    const float iD = __frcp_rn(B1 * B2);
+    const float S = A1 * A2 * iD;
+    s_sum += S;
+    if (a.d_rgb) {
+      // dS/dm1 = 2 my (A2 - A1) / D - 2 mx S (1/B1 - 1/B2);  dS/dm2 = -S / B2;  dS/dm12 = 2 A1 / D
+      a.dm[o] = 2.f * iD * (my * (A2 - A1) - mx * S * (B2 - B1));
+      a.dm[3 * a.P + o] = -S * B1 * iD;
+      a.dm[6 * a.P + o] = 2.f * A1 * iD;
     }
+    l1c += fabsf(s_in[0][r0 + q + kR][c + kR] - s_in[1][r0 + q + kR][c + kR]);
   }
 
   if (ch == 0 && (a.depth || a.d_depth)) {
