@@ -30,10 +30,13 @@ Functions and the passages they follow (RT-GuIDE, arXiv 2409.18122):
   ssim_map / mapping_loss  Eq. 3: L1 depth + lambda_1 L1 colour + lambda_2 (1 - SSIM), SSIM with
                the 11 x 11 Gaussian window (sigma 1.5, zero outside the image; the paper
                does not state the window), and the gradient with respect to the images.
+  adam_step    the optimiser of the mapping iterations (Adam, as in the paper's mapping
+               module): one update with bias corrections.
 """
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from dataclasses import dataclass, asdict
@@ -520,3 +523,19 @@ def mapping_loss_views(rgbs, depths, rgb_refs, depth_refs, w_d: float = 1.0, w_c
         g_rgb.append(f * gr)
         g_depth.append(f * gd)
     return L, l1d, l1c, ss, g_rgb, g_depth
+
+
+# ------------------------------------------------------------------ optimiser of the mapping iterations
+def adam_step(p, g, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """One Adam update (Kingma and Ba), the optimiser of the mapping iterations (the map is
+    refined by gradient steps on the rendering loss, Eq. 2 / Sec. IV-A), in FP64:
+    m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2, and with the bias corrections
+    c1 = 1 - b1^t, c2 = 1 - b2^t: p <- p - (lr / c1) m / (sqrt(v) / sqrt(c2) + eps).
+    t is the number of this step (1 for the first).  Returns new (p, m, v)."""
+    p = np.asarray(p, np.float64)
+    g = np.asarray(g, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    c1, c2 = 1.0 - beta1 ** t, 1.0 - beta2 ** t
+    p = p - (lr / c1) * m / (np.sqrt(v) / math.sqrt(c2) + eps)
+    return p, m, v

@@ -618,3 +618,39 @@ def test_mapping_loss_views_normalisation():
     assert L2 == pytest.approx(L1v, rel=1e-14) and ss2 == pytest.approx(ss, rel=1e-14)
     np.testing.assert_allclose(gr2[1], gr1 / 2, rtol=1e-15)
     assert L == pytest.approx(l1d + 0.4 * l1c + 0.1 * (1 - ss), rel=1e-14)
+
+
+def test_adam_first_steps_by_hand():
+    """Adam from zero moments: the first step moves each parameter by lr g / (|g| + eps), i.e.
+    lr times the sign of g up to eps; the second step, with the bias corrections written out by
+    hand, and a zero gradient that leaves the parameter and the moments unchanged."""
+    p = np.array([1.0, -2.0, 0.5, 3.0])
+    g = np.array([0.3, -4.0, 0.0, 1e-3])
+    lr, b1, b2, eps = 0.01, 0.9, 0.999, 1e-8
+    p1, m1, v1 = O.adam_step(p, g, np.zeros(4), np.zeros(4), 1, lr, b1, b2, eps)
+    np.testing.assert_allclose(p1, p - lr * g / (np.abs(g) + eps), rtol=1e-12, atol=0)
+    assert p1[2] == p[2] and m1[2] == 0 and v1[2] == 0
+    g2 = np.array([-0.1, 2.0, 0.0, 1e-3])
+    p2, m2, v2 = O.adam_step(p1, g2, m1, v1, 2, lr, b1, b2, eps)
+    mm = 0.9 * 0.1 * g + 0.1 * g2
+    vv = 0.999 * 0.001 * g * g + 0.001 * g2 * g2
+    ref = p1 - lr / (1 - 0.81) * mm / (np.sqrt(vv) / np.sqrt(1 - 0.999 ** 2) + eps)
+    np.testing.assert_allclose(m2, mm, rtol=1e-14)
+    np.testing.assert_allclose(v2, vv, rtol=1e-14)
+    np.testing.assert_allclose(p2, ref, rtol=1e-13)
+
+
+def test_adam_matches_torch_cpu_adam():
+    """Five steps against PyTorch's own CPU Adam in FP64 (a library implementation)."""
+    import torch
+    rng = np.random.default_rng(41)
+    p0 = rng.normal(size=(64, 4))
+    grads = [rng.normal(size=(64, 4)) * s for s in (1.0, 0.1, 3.0, 0.0, 1e-3)]
+    tp = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=2e-3, betas=(0.9, 0.999), eps=1e-8)
+    p, m, v = p0.copy(), np.zeros_like(p0), np.zeros_like(p0)
+    for t, g in enumerate(grads, start=1):
+        tp.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+        p, m, v = O.adam_step(p, g, m, v, t, 2e-3)
+    np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-12, atol=1e-15)
