@@ -192,11 +192,11 @@ def job_throughput(units_per_rank: float, seconds_per_rank: float, world: int) -
 class MapStep:
     """One mapping iteration on the 500k-Gaussian, 4-keyframe map: render, the loss and its
     image gradient (gs_image_loss; by default mean L1 over RGB + 0.1 x mean L1 depth, or the
-    paper's Eq. 3 weights with SSIM), gs_render_bwd, Adam.  With graph=True the whole
-    iteration (forward, loss, backward, fused capturable Adam) is captured once in a CUDA
-    graph and replayed; eager() runs it op by op (used for the per-stage breakdown)."""
+    paper's Eq. 3 weights with SSIM), gs_render_bwd, Adam (gs_adam_step).  With graph=True
+    the whole iteration (forward, loss, backward, Adam) is captured once in a CUDA graph and
+    replayed; eager() runs it op by op (used for the per-stage breakdown)."""
 
-    def __init__(self, gs, scenes, weights=None, graph=True, scene=None, capturable=None):
+    def __init__(self, gs, scenes, weights=None, graph=True, scene=None):
         import torch
         self.torch = torch
         self.gs = gs
@@ -217,8 +217,7 @@ class MapStep:
         self.params = [t.clone().requires_grad_(True) for t in (gm.mo, gm.su, gm.q, gm.rgb)]
         self.host = [t.detach().cpu().pin_memory() for t in self.params]
         self.host_tgt = [self.tgt_rgb.cpu().pin_memory(), self.tgt_depth.cpu().pin_memory()]
-        self.opt = torch.optim.Adam(self.params, lr=1e-4, fused=True,
-                                    capturable=graph if capturable is None else capturable)
+        self.opt = gs.Adam(self.params, lr=1e-4)   # gs_adam_step: one kernel, device step count
         self.loss_host = torch.zeros(1, dtype=torch.float32).pin_memory()
         self.loss_fn = gs.ImageLoss.for_cameras(sc.cams, gs.L1_WEIGHTS if weights is None else weights)
         self.graph = None
@@ -503,13 +502,14 @@ def map_stage_roofline(ws, n, n_views, stage_ms, hbm_gbs, issue_tps):
     visible record), binning (44 B per pair), forward compositing (10 instructions per
     evaluated, 6 more per contributing (pixel, Gaussian)), backward (10 per evaluated, 38 per
     contributing, plus the projection adjoint), loss (mean L1: 12 B per pixel and channel of
-    colour and depth: two reads, one gradient write)."""
+    colour and depth: two reads, one gradient write), Adam (28 B per parameter)."""
     rows = {
         "gs_project": ("alu", 25.0 * n * n_views + 110.0 * ws["records"]),
         "gs_bin_sort": ("hbm", 44.0 * ws["pairs"]),
         "gs_render_fwd": ("alu", 10.0 * ws["evaluated"] + 6.0 * ws["contributing"]),
         "gs_render_bwd": ("alu", 10.0 * ws["evaluated"] + 38.0 * ws["contributing"]),
         "gs_image_loss": ("hbm", 12.0 * 4 * ws["pixels"]),
+        "gs_adam_step": ("hbm", 28.0 * 16 * n),   # p, g, m, v read, p, m, v written; 16 floats per Gaussian
     }
     out = {}
     for k, (bound, work) in rows.items():
@@ -620,7 +620,7 @@ def config4_loop(torch, gs, scenes, tiles, flush, steps=5):
     classes), captured together in one CUDA graph and replayed; events inside the graph
     split the two parts."""
     sc, cands = scenes.config4()
-    m = MapStep(gs, scenes, graph=False, scene=sc, capturable=True)
+    m = MapStep(gs, scenes, graph=False, scene=sc)
     ig = IGStep(gs, scenes, graph=False, tiles=tiles, scene=sc, cams=cands, record_capacity=400_000_000,
                 pair_capacity=1_500_000_000)
     try:

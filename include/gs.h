@@ -468,6 +468,30 @@ gs_status gs_image_loss(const int32_t* sizes, int32_t n_views, const float* rgb,
  * sizes (HOST int32[n_views][2]) into *bytes.  Errors: GS_ERR_NULL, GS_ERR_ARG. */
 gs_status gs_image_loss_workspace_size(const int32_t* sizes, int32_t n_views, size_t* bytes);
 
+/* ------------------------------------------------ optimiser of the mapping iterations
+ * The map is refined by gradient steps on the rendering loss (Eq. 2, Sec. IV-A); the
+ * mapping module uses Adam (Kingma and Ba). */
+typedef struct {
+  double lr, beta1, beta2, eps;   /* double, so that 1 - beta and beta^t keep their precision */
+} gs_adam_params;
+
+enum { GS_ADAM_MAX_TENSORS = 8 };
+
+/* gs_adam_step -- one Adam update of up to GS_ADAM_MAX_TENSORS tensors in place:
+ *   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+ *   p <- p - (lr / c1) m / (sqrt(v) / sqrt(c2) + eps),  c1 = 1 - b1^t, c2 = 1 - b2^t,
+ * with t = *step + 1; *step is incremented on the device after the update, so a captured
+ * graph replays successive steps.
+ *   params, grads, m, v  HOST arrays of n_tensors DEVICE float pointers, 16-byte aligned;
+ *                        grads[i] == NULL skips tensor i (no gradient)
+ *   sizes                HOST int64[n_tensors]: elements of each tensor, a multiple of 4
+ *   step                 DEVICE uint32[1]: steps completed so far (0 before the first)
+ * lr >= 0, 0 <= beta1, beta2 < 1, eps > 0, all finite.  Deterministic.
+ * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG, GS_ERR_CUDA. */
+gs_status gs_adam_step(float* const* params, const float* const* grads, float* const* m, float* const* v,
+                       const int64_t* sizes, int32_t n_tensors, const gs_adam_params* prm, uint32_t* step,
+                       void* stream);
+
 /* ------------------------------------------------------------- utilities */
 enum {
   GS_OP_PROJECT = 0,

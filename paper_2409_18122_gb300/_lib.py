@@ -69,6 +69,14 @@ class gs_loss_weights(ctypes.Structure):
     _fields_ = [("w_depth", c_float), ("w_rgb", c_float), ("w_ssim", c_float)]
 
 
+class gs_adam_params(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double)]
+
+
+GS_ADAM_MAX_TENSORS = 8
+
+
 class gs_image(ctypes.Structure):
     _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("unc", c_void_p), ("T", c_void_p), ("last", c_void_p),
                 ("n_contrib", c_void_p)]
@@ -100,6 +108,8 @@ PROTOTYPES = {
     "gs_image_loss": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, POINTER(gs_loss_weights),
                                 c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "gs_image_loss_workspace_size": (c_int32, [c_void_p, c_int32, POINTER(c_size_t)]),
+    "gs_adam_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, POINTER(gs_adam_params),
+                               c_void_p, c_void_p]),
     "gs_project": (c_int32, [POINTER(gs_map), c_void_p, c_int32, POINTER(gs_params), POINTER(gs_proj), c_void_p,
                              c_size_t, c_void_p]),
     "gs_bin_sort": (c_int32, [POINTER(gs_proj), c_void_p, c_int32, POINTER(gs_params), POINTER(gs_bins), c_void_p,

@@ -291,6 +291,24 @@ gs_status gs_image_loss_workspace_size(const int32_t* sizes, int32_t n_views, si
   return GS_OK;
 }
 
+gs_status gs_adam_step(float* const* params, const float* const* grads, float* const* m, float* const* v,
+                       const int64_t* sizes, int32_t n_tensors, const gs_adam_params* prm, uint32_t* step,
+                       void* stream) {
+  if (!params || !grads || !m || !v || !sizes || !prm || !step) return GS_ERR_NULL;
+  if (n_tensors < 1 || n_tensors > GS_ADAM_MAX_TENSORS) return GS_ERR_ARG;
+  if (!(prm->lr >= 0.0) || std::isinf(prm->lr) || !(prm->beta1 >= 0.0 && prm->beta1 < 1.0) ||
+      !(prm->beta2 >= 0.0 && prm->beta2 < 1.0) || !(prm->eps > 0.0) || std::isinf(prm->eps))
+    return GS_ERR_ARG;
+  if (!aligned(step, 4)) return GS_ERR_ALIGN;
+  for (int i = 0; i < n_tensors; ++i) {
+    if (sizes[i] < 0 || sizes[i] % 4 != 0) return GS_ERR_ARG;
+    if (sizes[i] > 0 && grads[i] && (!params[i] || !m[i] || !v[i])) return GS_ERR_NULL;
+    if (!aligned(params[i], 16) || !aligned(grads[i], 16) || !aligned(m[i], 16) || !aligned(v[i], 16))
+      return GS_ERR_ALIGN;
+  }
+  return from_cuda(launch_adam(params, grads, m, v, sizes, n_tensors, *prm, step, (cudaStream_t)stream));
+}
+
 gs_status gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t rec_capacity, int64_t pair_capacity,
                             int64_t tile_capacity, size_t* bytes) {
   if (!bytes) return GS_ERR_NULL;

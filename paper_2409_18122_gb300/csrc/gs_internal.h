@@ -121,6 +121,11 @@ cudaError_t launch_collision_check(const float* mo, const float* su, int64_t n, 
                                    uint32_t* collides_out, cudaStream_t st);
 size_t regions_ws_bytes(int64_t n_regions);
 
+// ------------------------------------------------------------------ Adam step
+cudaError_t launch_adam(float* const* params, const float* const* grads, float* const* m, float* const* v,
+                        const int64_t* sizes, int n_tensors, const gs_adam_params& prm, uint32_t* step,
+                        cudaStream_t st);
+
 // ------------------------------------------------------------------ mapping loss (Eq. 3)
 // 0 if the sizes are invalid.
 size_t image_loss_ws_bytes(const int32_t* sizes, int n_views);

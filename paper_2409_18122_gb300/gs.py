@@ -589,6 +589,42 @@ def image_loss(rgb, depth, rgb_ref, depth_ref, fn: ImageLoss):
     return _ImageLossFn.apply(rgb, depth, rgb_ref, depth_ref, fn)
 
 
+# ---------------------------------------------------------------------- optimiser (gs_adam_step)
+class Adam:
+    """Adam on float32 tensors in place (gs_adam_step): one kernel over all of them, with the
+    step count on the device so that the update can be captured in a CUDA graph.  The same
+    update as torch.optim.Adam (no weight decay, no amsgrad); tensors need a multiple of 4
+    elements and 16-byte alignment.  Gradients are read from each tensor's .grad."""
+
+    def __init__(self, params, lr: float = 1e-3, betas=(0.9, 0.999), eps: float = 1e-8):
+        self.params = list(params)
+        if not 1 <= len(self.params) <= L.GS_ADAM_MAX_TENSORS:
+            raise ValueError("between 1 and %d tensors" % L.GS_ADAM_MAX_TENSORS)
+        dev = self.params[0].device
+        with torch.no_grad():
+            self.m = [torch.zeros_like(p) for p in self.params]
+            self.v = [torch.zeros_like(p) for p in self.params]
+        self.step_count = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.prm = L.gs_adam_params(float(lr), float(betas[0]), float(betas[1]), float(eps))
+        n = len(self.params)
+        self._sizes = (ctypes.c_int64 * n)(*[p.numel() for p in self.params])
+
+    def zero_grad(self, set_to_none: bool = True):
+        for p in self.params:
+            if set_to_none:
+                p.grad = None
+            elif p.grad is not None:
+                p.grad.zero_()
+
+    def step(self, stream=None):
+        n = len(self.params)
+        arr = lambda ts: (ctypes.c_void_p * n)(*[_ptr(t) for t in ts])
+        grads = [p.grad for p in self.params]
+        _timed("gs_adam_step", stream, lambda: L.check(
+            L.lib().gs_adam_step(arr(self.params), arr(grads), arr(self.m), arr(self.v), self._sizes, n,
+                                 ctypes.byref(self.prm), _ptr(self.step_count), _stream(stream)), "gs_adam_step"))
+
+
 # ---------------------------------------------------------------------- tile autotuner
 TILE_CANDIDATES = ((16, 16), (16, 8), (8, 8), (32, 8), (32, 16), (32, 32))
 

@@ -45,7 +45,7 @@ def test_struct_layouts_match_header(tmp_path):
         "gs_camera": L.gs_camera, "gs_map": L.gs_map, "gs_params": L.gs_params, "gs_proj": L.gs_proj,
         "gs_bins": L.gs_bins, "gs_image": L.gs_image, "gs_image_grad": L.gs_image_grad, "gs_map_grad": L.gs_map_grad,
         "gs_utility_params": L.gs_utility_params, "gs_region_grid": L.gs_region_grid,
-        "gs_loss_weights": L.gs_loss_weights,
+        "gs_loss_weights": L.gs_loss_weights, "gs_adam_params": L.gs_adam_params,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gs.h"', "int main(void) {"]
     for s, cls in structs.items():
@@ -153,6 +153,20 @@ def test_host_side_argument_errors(lib):
         assert call(a6=P(L.gs_loss_weights(*bad))) == L.GS_ERR_ARG
     assert call(a11=need - 256) == L.GS_ERR_WORKSPACE
     assert call(a8=ctypes.c_void_p(0x10002)) == L.GS_ERR_ALIGN
+    # Adam step: tensor count, sizes, parameters, alignment
+    ptrs = (ctypes.c_void_p * 2)(fake, fake)
+    sizes = (ctypes.c_int64 * 2)(16, 8)
+    ap = L.gs_adam_params(1e-3, 0.9, 0.999, 1e-8)
+    assert lib.gs_adam_step(ptrs, ptrs, ptrs, ptrs, sizes, 0, P(ap), fake, None) == L.GS_ERR_ARG
+    assert lib.gs_adam_step(ptrs, ptrs, ptrs, ptrs, sizes, 9, P(ap), fake, None) == L.GS_ERR_ARG
+    assert lib.gs_adam_step(None, ptrs, ptrs, ptrs, sizes, 2, P(ap), fake, None) == L.GS_ERR_NULL
+    assert lib.gs_adam_step(ptrs, ptrs, ptrs, ptrs, sizes, 2, P(ap), None, None) == L.GS_ERR_NULL
+    assert lib.gs_adam_step(ptrs, ptrs, ptrs, ptrs, (ctypes.c_int64 * 2)(16, 6), 2, P(ap), fake, None) == L.GS_ERR_ARG
+    for bad in ((-1.0, 0.9, 0.999, 1e-8), (1e-3, 1.0, 0.999, 1e-8), (1e-3, 0.9, 0.999, 0.0),
+                (float("nan"), 0.9, 0.999, 1e-8)):
+        assert lib.gs_adam_step(ptrs, ptrs, ptrs, ptrs, sizes, 2, P(L.gs_adam_params(*bad)), fake, None) == L.GS_ERR_ARG
+    mis = (ctypes.c_void_p * 2)(fake, ctypes.c_void_p(0x10004))
+    assert lib.gs_adam_step(mis, ptrs, ptrs, ptrs, sizes, 2, P(ap), fake, None) == L.GS_ERR_ALIGN
     # read_status: null
     f = ctypes.c_uint32(0)
     assert lib.gs_read_status(None, P(f)) == L.GS_ERR_NULL
