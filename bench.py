@@ -294,7 +294,7 @@ class IGStep:
         cams = gs.with_tiles(cams, self.tile_choice)
         self.cams = cams
         self.frame = gs.Frame(self.gm.n, cams, pair_capacity=pair_capacity, with_color=False, with_pair_tiles=False,
-                              record_capacity=record_capacity)
+                              record_capacity=record_capacity, with_gid=False)
         while True:
             self.frame.reset_status()
             self.frame.project(self.gm)

@@ -126,7 +126,8 @@ typedef struct {
  *                         tile_w | tile_h << 8 | tiles_x << 16); entry V holds the totals.
  *                         A warp item is one 8x4 pixel block of a tile: view v has
  *                         tiles(v) * tile_w * tile_h / 32 of them.
- *   gid, view  [cap]      Gaussian index and view index of the record
+ *   gid, view  [cap]      Gaussian index and view index of the record (gid may be NULL: not
+ *                         written; the library itself never reads it)
  *   splat      [cap][8]   32 bytes per record, everything compositing reads:
  *                         (mu_2D x, mu_2D y, ext, u, a, b, c, o) -- u the uncertainty of the
  *                         Gaussian, (a, b, c) the inverse 2D covariance with

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera*
         const uint32_t dst = s_base[warp][vi] + __popc(vmask[vi] & ((1u << gl) - 1u));
         if ((int64_t)dst < out.capacity) {
           const float4 cu = s_g[warp][3][gl];
-          out.gid[dst] = (uint32_t)((grp << 5) + gl);
+          if (out.gid) out.gid[dst] = (uint32_t)((grp << 5) + gl);
           out.view[dst] = (uint32_t)(v0 + vi);
           float4* sp = reinterpret_cast<float4*>(out.splat) + 2 * (size_t)dst;
           sp[0] = make_float4(vp.mx, vp.my, pack_ext(vp.rx, vp.ry), cu.w);

@@ -356,7 +356,6 @@ size_t ig_ws_bytes(int64_t n, int n_views, int64_t rec_cap, int64_t pair_cap, in
   Carver c(nullptr);
   c.take<uint32_t>(1);                                   // record count
   c.take<uint32_t>(kVI * (size_t)(n_views + 1));         // view info
-  c.take<uint32_t>(rec_cap);                             // gid
   c.take<uint32_t>(rec_cap);                             // view
   c.take<float4>(2 * (size_t)rec_cap);                   // splat
   c.take<ushort4>(rec_cap);                              // rect
@@ -436,7 +435,7 @@ cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_vie
   proj.count = c.take<uint32_t>(1);
   proj.status = status;
   proj.view_info = c.take<uint32_t>(kVI * (size_t)(n_views + 1));
-  proj.gid = c.take<uint32_t>(rec_cap);
+  proj.gid = nullptr;   // Gaussian ids are not needed to score views
   proj.view = c.take<uint32_t>(rec_cap);
   proj.splat = (float*)c.take<float4>(2 * (size_t)rec_cap);
   proj.color_d = nullptr;   // not needed to score views: the projection skips the colours

@@ -11,6 +11,7 @@ namespace {
 
 constexpr int kBlock = 512;
 constexpr int kItems = 8;
+static_assert(kItems == 8, "the down-sweep moves each thread's items as two 16-byte vectors");
 constexpr int kTile = kBlock * kItems;
 constexpr int kMaxParts = 1024;
 
@@ -119,21 +120,37 @@ __global__ void __launch_bounds__(kBlock) k_scan_down(const uint32_t* __restrict
   int64_t end = beg + chunk;
   if (end > n) end = n;
   unsigned long long carry = partial[blockIdx.x];
+  // 16-byte loads and stores when both arrays allow them (i0 is a multiple of 8 elements)
+  const bool vec = (((uintptr_t)in | (uintptr_t)out) & 15u) == 0;
   for (int64_t t0 = beg; t0 < end; t0 += kTile) {
     uint32_t v[kItems];
     unsigned long long s = 0;
     const int64_t i0 = t0 + (int64_t)threadIdx.x * kItems;
+    const bool full = vec && i0 + kItems <= end;
+    if (full) {
+      const uint4 a = reinterpret_cast<const uint4*>(in + i0)[0], b = reinterpret_cast<const uint4*>(in + i0)[1];
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-      v[k] = (i0 + k < end) ? in[i0 + k] : 0u;
-      s += v[k];
+      for (int k = 0; k < kItems; ++k) v[k] = (i0 + k < end) ? in[i0 + k] : 0u;
     }
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) s += v[k];
     unsigned long long tot;
     unsigned long long ex = block_exclusive_scan(s, &tot) + carry;
+    uint32_t o[kItems];
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
-      if (i0 + k < end) out[i0 + k] = sat32(ex);
+      o[k] = sat32(ex);
       ex += v[k];
+    }
+    if (full) {
+      reinterpret_cast<uint4*>(out + i0)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+      reinterpret_cast<uint4*>(out + i0)[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kItems; ++k)
+        if (i0 + k < end) out[i0 + k] = o[k];
     }
     carry += tot;
   }
