@@ -363,19 +363,35 @@ __global__ void __launch_bounds__(kBlock) k_downsweep(const uint32_t* __restrict
       }
     }
     __syncthreads();
+    if (!kEpi) {
 #pragma unroll
-    for (int it = 0; it < kItems; ++it) {
-      const int j = tid + it * kBlock;
-      if (j >= tile_n) break;
-      const uint32_t k = s_keys[j];
-      const uint32_t d = (k >> shift) & 0xffu;
-      const uint32_t g = base[d] + (uint32_t)j - t_start[d];
-      const uint32_t v = s_vals[j];
-      vals_out[g] = v;
-      if (!kEpi) {
+      for (int it = 0; it < kItems; ++it) {
+        const int j = tid + it * kBlock;
+        if (j >= tile_n) break;
+        const uint32_t k = s_keys[j];
+        const uint32_t d = (k >> shift) & 0xffu;
+        const uint32_t g = base[d] + (uint32_t)j - t_start[d];
+        vals_out[g] = s_vals[j];
         keys_out[g] = k;
-      } else {
-        ushort4 rc = epi.rect[v];
+      }
+    } else {
+      // all of this thread's rectangle gathers first, so that they are in flight together
+      // (the stores below go to other arrays, but the compiler cannot know that)
+      ushort4 rcs[kItems];
+#pragma unroll
+      for (int it = 0; it < kItems; ++it) {
+        const int j = tid + it * kBlock;
+        rcs[it] = j < tile_n ? epi.rect[s_vals[j]] : make_ushort4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int it = 0; it < kItems; ++it) {
+        const int j = tid + it * kBlock;
+        if (j >= tile_n) break;
+        const uint32_t k = s_keys[j];
+        const uint32_t d = (k >> shift) & 0xffu;
+        const uint32_t g = base[d] + (uint32_t)j - t_start[d];
+        vals_out[g] = s_vals[j];
+        ushort4 rc = rcs[it];
         uint32_t c = 0;
         if (rc.x < rc.z && rc.y < rc.w) {
           if (rc.z <= tiles_x && rc.w <= tiles_y) c = (uint32_t)(rc.z - rc.x) * (uint32_t)(rc.w - rc.y);
