@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(kBinWarps * 32) k_bin_hist(const gs_proj proj,
       const uint32_t xb = xa + ww < c.tiles_x ? xa + ww : c.tiles_x;
       for (int i = lane; i < kWin; i += 32) D[i] = 0u;
       __syncwarp();
+#pragma unroll 4
       for (int64_t r = c.r0 + lane; r < c.r1; r += 32) {
         const ushort4 rc = srect[r];
         const uint32_t x0 = rc.x > xa ? rc.x : xa, x1 = rc.z < xb ? rc.z : xb;
@@ -294,6 +295,7 @@ __global__ void __launch_bounds__(kBinWarps * 32, 5) k_bin_place(const gs_proj p
     for (uint32_t xa = 0; xa < c.tiles_x; xa += ww) {
       const uint32_t xb = xa + ww < c.tiles_x ? xa + ww : c.tiles_x;
       const uint32_t cols = xb - xa, cells = (yb - ya) * cols;
+#pragma unroll 4
       for (uint32_t i = lane; i < cells; i += 32) {
         const uint32_t y = ya + i / cols, x = xa + i % cols;
         run[i] = off[(size_t)K * (c.tile_base + y * c.tiles_x + x) + c.k];
