@@ -451,7 +451,7 @@ def pipeline_roofline(istep, contributing, t_pass, hbm_gbs, issue_tps):
     bytes / HBM bandwidth and algorithmic FP32 instructions / issue peak, summed, over
     the measured pass time.  Units: (Gaussian, view) pairs and visible records for the
     projection (~25 instructions per culled pair, ~110 per visible one; 64 B read per
-    Gaussian, 52 B written per scoring record), (tile, record) pairs for binning (44 B
+    Gaussian, 48 B written per scoring record), (tile, record) pairs for binning (44 B
     per pair: emit, one permutation, ranges), contributing (pixel, Gaussian) evaluations
     for compositing (~12 instructions each)."""
     fr = istep.frame
@@ -459,7 +459,7 @@ def pipeline_roofline(istep, contributing, t_pass, hbm_gbs, issue_tps):
     recs = int(fr.rec_count.item())
     pairs = int(fr.pair_count.item()) & 0xFFFFFFFF
     st = {
-        "project": (64.0 * n + 52.0 * recs, 25.0 * n * v + 110.0 * recs),
+        "project": (64.0 * n + 48.0 * recs, 25.0 * n * v + 110.0 * recs),
         "bin_sort": (44.0 * pairs, 0.0),
         "composite": (0.0, 12.0 * contributing),
     }
