@@ -666,6 +666,9 @@ def config4_loop(torch, gs, scenes, tiles, flush, steps=5):
     return out
 
 
+COLLISION_POINTS = 129    # test points of one planning call (Fig. planning_time, Sec. V-B)
+
+
 def collision_timing(torch, gs, scenes, reps=20):
     """Collision check of 129 test points (one motion-primitive tree layer) against every
     Gaussian of the 3M-Gaussian, 40x40 m map, r_robot 0.3 m, lambda_g 3 (Sec. IV-B)."""
@@ -673,25 +676,25 @@ def collision_timing(torch, gs, scenes, reps=20):
     sc, _ = scenes.config4()
     gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
     rng = np.random.default_rng(129)
-    pts = np.zeros((129, 4), np.float32)
-    pts[:, :3] = rng.uniform([0.5, 0.5, 0.3], [39.5, 39.5, 1.0], (129, 3))
+    pts = np.zeros((COLLISION_POINTS, 4), np.float32)
+    pts[:, :3] = rng.uniform([0.5, 0.5, 0.3], [39.5, 39.5, 1.0], (COLLISION_POINTS, 3))
     p = torch.from_numpy(pts).cuda()
     for _ in range(3):
-        gs.collision_check(gm, p, 0.3, 3.0)
+        gs.collision_check(gm, p, 0.3, gs.LAMBDA_G)
     torch.cuda.synchronize()
     t = []
     for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        gs.collision_check(gm, p, 0.3, 3.0)
+        gs.collision_check(gm, p, 0.3, gs.LAMBDA_G)
         e1.record()
         torch.cuda.synchronize()
         t.append(e0.elapsed_time(e1))
     ms = statistics.median(t)
     del gm
     torch.cuda.empty_cache()
-    return {"ms": ms, "points": 129, "gaussians": sc.gmap.n,
-            "pair_tests_per_s": 129 * sc.gmap.n / (ms / 1e3),
+    return {"ms": ms, "points": COLLISION_POINTS, "gaussians": sc.gmap.n,
+            "pair_tests_per_s": COLLISION_POINTS * sc.gmap.n / (ms / 1e3),
             "paper_context": "0.62 s for planning a 5 m trajectory with 129 collision points at 3e6 "
                              "Gaussians (GPU collision checks, tree search included, hardware not stated)"}
 

@@ -426,6 +426,13 @@ class InfoGain:
 
 
 # ------------------------------------------------------- render-free view utility (Sec. IV-A/B)
+# Values of Sec. IV-C: Gaussian regions of 2.5 m, lambda_xi = 1 (Eq. view_util),
+# lambda_g = 3 (the collision test's radius scale, Sec. IV-B)
+REGION_SIZE_M = 2.5
+LAMBDA_XI = 1.0
+LAMBDA_G = 3.0
+
+
 def uncertainty_update(mo_prev: torch.Tensor, mo_cur: torch.Tensor, su: torch.Tensor, squared: bool = False,
                        stream=None):
     """u = |mu_cur - mu_prev| (or its square) into su[:, 3] for Gaussians whose mean moved
@@ -445,7 +452,7 @@ class ViewUtility:
     __call__: xi per view (mode GS_XI: visible |G_H| - lambda |G_L|; GS_XI_SUM: sum of u over
     the visible Gaussians) and, for GS_XI, the visible counts [V, 2]."""
 
-    def __init__(self, cams: Sequence, near_plane: float = 0.2, range_m: float = 5.0, lam: float = 1.0,
+    def __init__(self, cams: Sequence, near_plane: float = 0.2, range_m: float = 5.0, lam: float = LAMBDA_XI,
                  ground_z: float = float("-inf"), device="cuda"):
         self.device = torch.device(device)
         self.cams = list(cams)
@@ -497,7 +504,7 @@ def trajectory_utility(vu: "ViewUtility", gmap: GaussianMapTensors, n_traj: int,
     return out, best
 
 
-def collision_check(gmap: GaussianMapTensors, points: torch.Tensor, r_robot: float, lambda_g: float = 3.0,
+def collision_check(gmap: GaussianMapTensors, points: torch.Tensor, r_robot: float, lambda_g: float = LAMBDA_G,
                     ground_z: float = float("-inf"), stream=None):
     """Smallest margin |p - mu| - (r_robot + lambda_g r) of every test point over all Gaussians
     and whether it collides (gs_collision_check).  points: CUDA float32 [M, 4] (xyz, -)."""
@@ -516,7 +523,8 @@ def collision_check(gmap: GaussianMapTensors, points: torch.Tensor, r_robot: flo
 
 def region_uncertainty(gmap: GaussianMapTensors, origin, size: float, dims, stream=None):
     """Mean u of every cuboid region (gs_region_uncertainty): (omega [R], count [R]),
-    region index (iz * dims[1] + iy) * dims[0] + ix."""
+    region index (iz * dims[1] + iy) * dims[0] + ix.  The paper's regions have size
+    REGION_SIZE_M."""
     grid = L.gs_region_grid((ctypes.c_float * 3)(*origin), float(size), (ctypes.c_int32 * 3)(*dims))
     R = int(dims[0]) * int(dims[1]) * int(dims[2])
     dev = gmap.mo.device

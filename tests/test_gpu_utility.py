@@ -123,7 +123,7 @@ def test_view_utility_full_size_config3():
 def test_region_uncertainty_vs_oracle():
     gmap, _ = _scene(n=40_000, seed=7)
     gm = gs.GaussianMapTensors.from_numpy(gmap)
-    omega, count = gs.region_uncertainty(gm, (0.0, 0.0, 0.0), 2.5, (4, 4, 2))
+    omega, count = gs.region_uncertainty(gm, (0.0, 0.0, 0.0), gs.REGION_SIZE_M, (4, 4, 2))
     ref, ref_cnt = O.region_uncertainty(gmap.mo, gmap.su[:, 3], (0.0, 0.0, 0.0), 2.5, (4, 4, 2))
     np.testing.assert_array_equal(count.cpu().numpy(), ref_cnt)
     np.testing.assert_allclose(omega.cpu().numpy(), ref, rtol=1e-6, atol=0)
