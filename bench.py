@@ -474,6 +474,18 @@ def pipeline_roofline(istep, contributing, t_pass, hbm_gbs, issue_tps):
     return out
 
 
+def at_load_clock(rooflines, sms, load_mhz):
+    """Adds to each FP32-issue roofline the issue peak at the median SM clock sampled under
+    load (SMs x 128 lanes x MHz) and the fraction of it achieved; no-op without a sample."""
+    if not load_mhz:
+        return rooflines
+    for r in rooflines:
+        if r.get("bound") == "alu":
+            r["peak_at_load_clock"] = sms * 128 * float(load_mhz) * 1e6 / 1e12
+            r["frac_at_load_clock"] = r["achieved"] / r["peak_at_load_clock"]
+    return rooflines
+
+
 def stage_roofline(pipe, stage_ms, hbm_gbs, issue_tps):
     """Per stage of the information-gain pass: achieved algorithmic rate over the stage's
     eager event-timed duration, against the roofline that bounds it (units as in
@@ -848,6 +860,7 @@ def run_ours(args):
     rooflines = [roofline, {"bound": "alu", "kernel": "gs_render_bwd (k_render_bwd + k_proj_adjoint)",
                             "achieved": bwd_ach, "peak": peak, "unit": "TFLOP/s", "frac": bwd_ach / peak,
                             "launch_ms": t_bwd * 1e3}]
+    at_load_clock(rooflines, sms, (clocks or {}).get("sm_mhz"))
 
     # the batched pass against the same candidates one view per call, at identical outputs
     unbatched = None

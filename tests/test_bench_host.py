@@ -49,3 +49,12 @@ def test_mix_pixels_per_view(bench):
     cams = [SimpleNamespace(width=80, height=60), SimpleNamespace(width=160, height=120),
             SimpleNamespace(width=320, height=240)]
     assert bench.mix_pixels_per_view(cams) == pytest.approx((4800 + 19200 + 76800) / 3)
+
+
+def test_issue_peak_at_the_load_clock(bench):
+    r = [{"bound": "alu", "achieved": 4.0}, {"bound": "hbm", "achieved": 1000.0}]
+    bench.at_load_clock(r, 152, 2000.0)
+    assert r[0]["peak_at_load_clock"] == pytest.approx(152 * 128 * 2000e6 / 1e12)
+    assert r[0]["frac_at_load_clock"] == pytest.approx(4.0 / (152 * 128 * 2000e6 / 1e12))
+    assert "peak_at_load_clock" not in r[1]
+    assert bench.at_load_clock(r[1:], 152, None) == r[1:]
