@@ -79,6 +79,17 @@ gs_status check_bins(const gs_bins* b) {
   return GS_OK;
 }
 
+gs_status check_image(const gs_image* im) {
+  if (!aligned(im->rgb, 4) || !aligned(im->depth, 4) || !aligned(im->unc, 4) || !aligned(im->T, 4) ||
+      !aligned(im->last, 4) || !aligned(im->n_contrib, 4))
+    return GS_ERR_ALIGN;
+  return GS_OK;
+}
+
+gs_status check_image_grad(const gs_image_grad* g) {
+  return aligned(g->rgb, 4) && aligned(g->depth, 4) ? GS_OK : GS_ERR_ALIGN;
+}
+
 gs_status check_ws(void* ws, size_t have, size_t need) {
   if (need == 0) return GS_OK;
   if (!ws) return GS_ERR_NULL;
@@ -131,6 +142,7 @@ gs_status gs_render_fwd(const gs_map* map, const gs_proj* proj, const gs_bins* b
   GS_TRY(check_params(prm));
   if (!out) return GS_ERR_NULL;
   if (proj->capacity > 0 && !proj->color_d) return GS_ERR_NULL;   // colours are needed to render
+  GS_TRY(check_image(out));
   return from_cuda(launch_render_fwd(*map, *proj, *bins, cams, n_views, *prm, *out, (cudaStream_t)stream));
 }
 
@@ -148,6 +160,8 @@ gs_status gs_render_bwd(const gs_map* map, const gs_proj* proj, const gs_bins* b
   if (map->n > 0 && (!out->dmo || !out->dsu || !out->dq || !out->drgb)) return GS_ERR_NULL;
   if (!aligned(out->dmo, 16) || !aligned(out->dsu, 16) || !aligned(out->dq, 16) || !aligned(out->drgb, 16))
     return GS_ERR_ALIGN;
+  GS_TRY(check_image(fwd));
+  GS_TRY(check_image_grad(grad));
   GS_TRY(check_ws(ws, ws_bytes, bwd_ws_bytes(proj->capacity)));
   return from_cuda(
       launch_render_bwd(*map, *proj, *bins, *fwd, *grad, cams, n_views, *prm, *out, ws, (cudaStream_t)stream));

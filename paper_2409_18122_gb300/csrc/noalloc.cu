@@ -67,7 +67,8 @@ extern "C" gs_status gs_render_bwd_noalloc(const gs_map* map, const gs_proj* pro
   if (!aligned(map->mo, 16) || !aligned(map->su, 16) || !aligned(map->q, 16) || !aligned(map->rgb, 16) ||
       !aligned(proj->splat, 32) || !aligned(proj->color_d, 16) ||
       !aligned(out->dmo, 16) || !aligned(out->dsu, 16) ||
-      !aligned(out->dq, 16) || !aligned(out->drgb, 16))
+      !aligned(out->dq, 16) || !aligned(out->drgb, 16) || !aligned(fwd->T, 4) || !aligned(fwd->last, 4) ||
+      !aligned(grad->rgb, 4) || !aligned(grad->depth, 4))
     return GS_ERR_ALIGN;
   const int B = prm->tile_w * prm->tile_h;
   if ((prm->tile_w != 8 && prm->tile_w != 16 && prm->tile_w != 32 && prm->tile_w != 64) || prm->tile_h < 8 ||

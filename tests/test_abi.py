@@ -124,6 +124,19 @@ def test_host_side_argument_errors(lib):
     # bins capacity
     bins = L.gs_bins(0, 10, fake, fake, fake, fake)
     assert lib.gs_bin_sort(P(proj), fake, 1, P(prm), P(bins), fake, 1 << 30, None) == L.GS_ERR_ARG
+    # images: a misaligned output, saved image or image gradient is refused before any launch
+    bins = L.gs_bins(100, 10, fake, fake, fake, fake)
+    odd = ctypes.c_void_p(0x10002)
+    img_bad = L.gs_image(fake, odd, None, fake, fake, None)
+    assert lib.gs_render_fwd(P(m), P(proj), P(bins), fake, 1, P(prm), P(img_bad), None) == L.GS_ERR_ALIGN
+    img = L.gs_image(fake, fake, None, fake, fake, None)
+    out = L.gs_map_grad(fake, fake, fake, fake)
+    for fwd, grad in ((img_bad, L.gs_image_grad(fake, fake)), (img, L.gs_image_grad(odd, None)),
+                      (img, L.gs_image_grad(None, odd))):
+        assert lib.gs_render_bwd(P(m), P(proj), P(bins), P(fwd), P(grad), fake, 1, P(prm), P(out), fake, 1 << 30,
+                                 None) == L.GS_ERR_ALIGN
+    assert lib.gs_render_bwd_noalloc(P(m), P(proj), P(bins), P(img), P(L.gs_image_grad(odd, None)), fake, 1, P(prm),
+                                     P(out), None) == L.GS_ERR_ALIGN
     # info gain: unknown mode, null output
     assert lib.gs_info_gain_batch(P(m), fake, 1, P(prm), 7, fake, fake, 0, 100, 10, fake, 1 << 30, None) == L.GS_ERR_ARG
     assert lib.gs_info_gain_batch(P(m), fake, 1, P(prm), 0, None, fake, 0, 100, 10, fake, 1 << 30, None) == L.GS_ERR_NULL
