@@ -154,6 +154,6 @@ def test_autograd_function_backward():
     loss = gs.image_loss(x, d, _flat(rrefs), _flat(drefs), fn)
     (2.0 * loss).backward()
     L, _, _, _, gr, gd = O.mapping_loss_views(rgbs, deps, rrefs, drefs)
-    assert float(loss) == pytest.approx(L, rel=2e-5)
+    assert float(loss.detach()) == pytest.approx(L, rel=2e-5)
     _check_grad(x.grad.cpu().numpy() / 2, gr, _ssim_part(rgbs, rrefs, sizes, 0.1))
     np.testing.assert_allclose(d.grad.cpu().numpy() / 2, gd[0].reshape(-1), rtol=1e-6)

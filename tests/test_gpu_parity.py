@@ -12,7 +12,8 @@ from oracle import oracle as O
 from paper_2409_18122_gb300 import gs, scenes
 from paper_2409_18122_gb300.scenes import Camera
 
-from gpu_helpers import (IG_RTOL, compare_grads, compare_image, gpu_bins, gpu_records, images_host, last_gid)
+from gpu_helpers import (IG_RTOL, compare_grads, compare_image, gpu_bins, gpu_records, images_host, last_gid,
+                         u32)
 
 pytestmark = pytest.mark.gpu
 
@@ -537,3 +538,57 @@ def test_info_gain_full_size_config3_two_views():
         ref, imgs = O.info_gain(sc.gmap, [sc.cams[v]])
         tol = IG_RTOL * abs(ref[0]) + 1e-7 + imgs[0]["knife"].mean() * 4e-3
         assert abs(ig[v] - ref[0]) <= tol, (v, ig[v], ref[0])
+
+
+# --------------------------------------------------------------------------- degenerate inputs
+@pytest.mark.parametrize("case", ["empty", "behind"])
+def test_empty_and_fully_culled_maps(case):
+    """An empty map, or a map with every Gaussian behind the cameras: no records and no pairs,
+    the zero background with T = 1 and no contributor in every view, zero information gain (as
+    the oracle's), and, for the culled map, all-zero gradients."""
+    sc = scenes.config0()
+    if case == "empty":
+        z = np.zeros((0, 4), np.float32)
+        gmap = scenes.GaussianMap(z, z, z, z)
+    else:
+        gmap = sc.gmap.copy()
+        gmap.mo[:, 2] = -gmap.mo[:, 2]
+    cams = sc.cams + [Camera(50, 50, 20, 15, 40, 30)]
+    fr, gm, img = run_forward(gmap, cams)
+    assert int(u32(fr.rec_count)[0]) == 0 and gpu_bins(fr)["n"] == 0
+    for h in images_host(fr, img):
+        for k in ("rgb", "depth", "unc"):
+            assert (h[k] == 0).all(), k
+        assert (h["T"] == 1).all() and (h["last"] == 0).all()
+    ig_op = gs.InfoGain(gm.n, cams)
+    ig = ig_op(gm).cpu().numpy()
+    assert not (ig_op.read_status() & gs.L.GS_FLAG_ERROR_MASK)
+    np.testing.assert_array_equal(ig, O.info_gain(gmap, cams)[0].astype(np.float32))
+    assert (ig == 0).all()
+    if case == "behind":
+        d_rgb = torch.ones_like(img["rgb"])
+        d_dep = torch.ones_like(img["depth"])
+        g = fr.render_bwd(gm, img, d_rgb, d_dep)
+        torch.cuda.synchronize()
+        for k in ("dmo", "dsu", "dq", "drgb"):
+            assert float(g[k].abs().max()) == 0.0, k
+
+
+def test_views_smaller_than_a_warp_block():
+    """1x1, 3x2 and 9x5 views beside a full one: the lanes outside a view write nothing and add
+    nothing; images and information gain agree with the oracle."""
+    sc = scenes.config0()
+    cams = [Camera(100, 100, 0.5, 0.5, 1, 1), Camera(100, 100, 1.5, 1.0, 3, 2), sc.cams[0],
+            Camera(100, 100, 4.5, 2.5, 9, 5)]
+    fr, gm, img = run_forward(sc.gmap, cams)
+    gpu = images_host(fr, img)
+    ref = O.render_images(sc.gmap, cams)
+    lg = last_gid(fr, gpu)
+    for v in range(len(cams)):
+        assert gpu[v]["T"].shape == (cams[v].height, cams[v].width)
+        compare_image(gpu[v], ref[v], "view %d" % v, check_last=lg[v])
+    ig = gs.InfoGain(gm.n, cams)(gm).cpu().numpy().astype(np.float64)
+    ref_ig, imgs = O.info_gain(sc.gmap, cams)
+    for v in range(len(cams)):
+        tol = IG_RTOL * abs(ref_ig[v]) + 1e-7 + imgs[v]["knife"].mean() * 4e-3
+        assert abs(ig[v] - ref_ig[v]) <= tol, (v, ig[v], ref_ig[v])
