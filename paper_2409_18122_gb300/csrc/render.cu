@@ -133,9 +133,9 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 12) k_render_fwd(gs_map map, g
             if (done[q]) continue;
             const float alpha = al[k][q];
             if (alpha < p.alpha_min) continue;
-            const float Tn = T[q] * (1.f - alpha);
-            if (Tn < p.T_min) { done[q] = true; continue; }
             const float w = alpha * T[q];
+            const float Tn = T[q] - w;      // T (1 - alpha)
+            if (Tn < p.T_min) { done[q] = true; continue; }
             const float4 c = sk[i];
             cr[q] += w * c.x;
             cg[q] += w * c.y;
@@ -275,9 +275,10 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
             for (int q = 0; q < kPix; ++q) {
               const float alpha = al[k][q];
               if (alpha < p.alpha_min) continue;
-              const float Tn = T[q] * (1.f - alpha);
+              const float w = T[q] * alpha;   // T (1 - alpha) taken as T - w: one instruction less
+              const float Tn = T[q] - w;
               if (Tn < p.T_min) { T[q] = 0.f; continue; }
-              cu[q] += alpha * T[q] * uu[k];
+              cu[q] += w * uu[k];
               T[q] = Tn;
             }
           }
