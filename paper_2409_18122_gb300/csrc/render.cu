@@ -241,18 +241,18 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
       ovA = ovA && ellipse_reaches(mA, cA, wb, ln_amin);
       const uint32_t m = __ballot_sync(0xffffffffu, ovA);
       if (m) {
-        // the overlapping entries, compacted in list order: (mu, u, o), scaled conic;
-        // padded to whole batches with entries of opacity -1 (alpha < 0: always skipped)
+        // the overlapping entries, compacted in list order: (mu, u, log2 o), scaled conic;
+        // padded to whole batches with entries of log2 o = -inf (alpha = 0: adds nothing)
         const int n_ov = __popc(m);
         const int n_pad = (n_ov + kIgBatch - 1) / kIgBatch * kIgBatch;
         if (ovA) {
           const int s = __popc(m & lt);
           const float3 k2 = scaled_conic(cA);
-          sm[s] = make_float4(mA.x, mA.y, mA.w, cA.w);
+          sm[s] = make_float4(mA.x, mA.y, mA.w, __log2f(cA.w));
           sc[s] = make_float4(k2.x, k2.y, k2.z, 0.f);
         }
         if (lane >= n_ov && lane < n_pad) {   // slots [n_ov, n_pad): disjoint from the staged ones
-          sm[lane] = make_float4(0.f, 0.f, 0.f, -1.f);
+          sm[lane] = make_float4(0.f, 0.f, 0.f, -INFINITY);
           sc[lane] = z4;
         }
         __syncwarp();
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
             uu[k] = mu.z;
 #pragma unroll
             for (int q = 0; q < kPix; ++q)
-              al[k][q] = splat_alpha2(mu.x, mu.y, make_float3(kk.x, kk.y, kk.z), mu.w, pxc, pyc[q], p.alpha_max);
+              al[k][q] = splat_alpha_lo(mu.x, mu.y, make_float3(kk.x, kk.y, kk.z), mu.w, pxc, pyc[q], p.alpha_max);
           }
 #pragma unroll
           for (int k = 0; k < kIgBatch; ++k) {
