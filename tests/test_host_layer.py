@@ -1,0 +1,132 @@
+"""Host-side logic of the Python layer, on the CPU: camera records, the tile grid, tile
+choices, the per-view image views and the capacity growth after an overflow.  Buffers are
+allocated on the CPU device (the layer computes sizes and pointers only; no kernel runs)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2409_18122_gb300 import _lib as L
+from paper_2409_18122_gb300 import gs
+from paper_2409_18122_gb300.scenes import Camera
+
+
+def _cams():
+    return [Camera(100, 100, 60, 40, 120, 80), Camera(50, 50, 20, 15, 40, 30).with_tile(8, 8),
+            Camera(80, 80, 16.5, 9.5, 33, 19).with_tile(32, 8), Camera(10, 10, 0.5, 0.5, 1, 1)]
+
+
+def test_camera_records_match_the_c_struct():
+    """The numpy record the layer uploads has the offsets of gs_camera (checked against the
+    header by the ABI test) and carries each camera's own tile size."""
+    for name, _ in L.gs_camera._fields_:
+        assert gs.CAMERA_DTYPE.fields[name][1] == getattr(L.gs_camera, name).offset, name
+    assert gs.CAMERA_DTYPE.itemsize == L.ctypes.sizeof(L.gs_camera)
+    cams = _cams()
+    a = gs.pack_cameras(cams)
+    R = np.arange(9, dtype=np.float32).reshape(3, 3)
+    c = Camera(1.5, 2.5, 3.5, 4.5, 7, 9, R=R, T=np.array([1.0, -2.0, 3.0]))
+    b = gs.pack_cameras([c])[0]
+    assert (b["fx"], b["fy"], b["cx"], b["cy"], b["width"], b["height"]) == (1.5, 2.5, 3.5, 4.5, 7, 9)
+    np.testing.assert_array_equal(b["R"], R.reshape(9))
+    np.testing.assert_array_equal(b["T"], [1.0, -2.0, 3.0])
+    assert [(r["tile_w"], r["tile_h"]) for r in a] == [(0, 0), (8, 8), (32, 8), (0, 0)]
+    dev = gs.cameras_to_device(cams, "cpu")
+    assert dev.dtype == torch.uint8 and dev.numel() == 80 * len(cams)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 16)])
+def test_tile_grid_matches_the_oracle(tile):
+    """The layer's tile grid (used to size buffers and split images) equals the oracle's,
+    per-view tiles included, and its pixel offsets are the running sums of W x H."""
+    cams = _cams()
+    p = gs.RenderParams(tile_w=tile[0], tile_h=tile[1])
+    tx, ty, tile_base, pix_base = gs.tile_grid(cams, p)
+    otx, obase = O.tile_grid(cams, O.Params(tile_w=tile[0], tile_h=tile[1]))
+    np.testing.assert_array_equal(tx, otx)
+    np.testing.assert_array_equal(tile_base, obase)
+    np.testing.assert_array_equal(pix_base, np.concatenate([[0], np.cumsum([c.width * c.height for c in cams])]))
+    # the 8x8 view of 40x30 has 5 x 4 tiles, the 1x1 view one tile of the default size
+    assert (tx[1], ty[1]) == (5, 4) and (tx[3], ty[3]) == (1, 1)
+
+
+def test_with_tiles_applies_a_choice_per_resolution_class():
+    cams = [Camera(50, 50, 40, 30, 80, 60), Camera(90, 90, 80, 60, 160, 120), Camera(50, 50, 40, 30, 80, 60)]
+    out = gs.with_tiles(cams, {(80, 60): (8, 8), (160, 120): (16, 8)})
+    assert [(c.tile_w, c.tile_h) for c in out] == [(8, 8), (16, 8), (8, 8)]
+    assert [(c.width, c.height, c.fx) for c in out] == [(c.width, c.height, c.fx) for c in cams]
+    none = gs.with_tiles(cams, {})
+    assert all((c.tile_w, c.tile_h) == (0, 0) for c in none)     # 0 = the renderer's default
+
+
+def test_split_images_views_the_flat_buffers():
+    cams = _cams()
+    fr = gs.Frame(100, cams, device="cpu")
+    P = fr.n_pixels
+    img = {"rgb": torch.arange(3 * P, dtype=torch.float32), "T": torch.arange(P, dtype=torch.float32),
+           "last": torch.arange(P, dtype=torch.int32)}
+    parts = fr.split_images(img)
+    assert len(parts) == len(cams)
+    p0 = 0
+    for c, d in zip(cams, parts):
+        n = c.width * c.height
+        assert d["rgb"].shape == (3, c.height, c.width) and d["T"].shape == (c.height, c.width)
+        # planar per view: channel k of this view starts at 3 p0 + k n
+        for k in range(3):
+            assert float(d["rgb"][k, 0, 0]) == 3 * p0 + k * n
+        assert float(d["T"][-1, -1]) == p0 + n - 1 and int(d["last"][0, 0]) == p0
+        assert "depth" not in d
+        p0 += n
+    assert p0 == P
+
+
+def _frame_with_status(flags, monkeypatch, n=1000):
+    fr = gs.Frame(n, _cams(), device="cpu", record_capacity=64, pair_capacity=4096)
+    monkeypatch.setattr(fr, "read_status", lambda: flags)
+    return fr
+
+
+def test_record_overflow_grows_the_record_capacity(monkeypatch):
+    """After GS_FLAG_RECORD_OVERFLOW the record buffers are sized for the records the
+    projection counted (grp_base[V G], with a margin), never beyond N x V."""
+    fr = _frame_with_status(L.GS_FLAG_RECORD_OVERFLOW, monkeypatch)
+    fr.grp_base[fr.n_slots] = 500
+    assert fr.grow_if_needed()
+    assert fr.rec_capacity == int(500 * 1.25) + 1024
+    assert fr.splat.shape[0] == fr.rec_capacity and fr.c_proj.capacity == fr.rec_capacity
+    assert fr.pair_capacity == 4096
+    fr2 = _frame_with_status(L.GS_FLAG_RECORD_OVERFLOW, monkeypatch, n=100)
+    fr2.grp_base[fr2.n_slots] = 390
+    assert fr2.grow_if_needed() and fr2.rec_capacity == 100 * len(_cams())
+
+
+def test_pair_overflow_grows_the_pair_capacity(monkeypatch):
+    fr = _frame_with_status(L.GS_FLAG_PAIR_OVERFLOW, monkeypatch)
+    fr.pair_count[0] = 10_000
+    assert fr.grow_if_needed()
+    assert fr.pair_capacity == int(10_000 * 1.25) + 1024
+    assert fr.pair_rec.numel() == fr.pair_capacity and fr.c_bins.pair_capacity == fr.pair_capacity
+    # a saturated count (more pairs than 32 bits hold) doubles the capacity instead
+    fr = _frame_with_status(L.GS_FLAG_PAIR_OVERFLOW, monkeypatch)
+    fr.pair_count[0] = -1
+    assert fr.grow_if_needed() and fr.pair_capacity == int(2 * 4096 * 1.25) + 1024
+
+
+def test_no_overflow_keeps_the_buffers(monkeypatch):
+    fr = _frame_with_status(0, monkeypatch)
+    rec, pairs = fr.rec_capacity, fr.pair_capacity
+    assert not fr.grow_if_needed()
+    assert (fr.rec_capacity, fr.pair_capacity) == (rec, pairs)
+
+
+def test_workspace_covers_every_stage():
+    """The frame's workspace is at least what gs_workspace_size asks for each stage."""
+    cams = _cams()
+    fr = gs.Frame(5000, cams, device="cpu")
+    need = [L.workspace_size(L.GS_OP_PROJECT, fr.n, fr.V),
+            L.workspace_size(L.GS_OP_BIN_SORT, fr.n, fr.V, fr.rec_capacity, fr.pair_capacity, fr.n_tiles),
+            L.workspace_size(L.GS_OP_RENDER_BWD, fr.n, fr.V, fr.rec_capacity)]
+    assert fr.ws.numel() >= max(need)
+    ig = gs.InfoGain(5000, cams, device="cpu")
+    assert ig.ws.numel() >= L.workspace_size(L.GS_OP_INFO_GAIN, 5000, len(cams), ig.record_capacity,
+                                             ig.pair_capacity, ig.n_tiles)
