@@ -130,3 +130,18 @@ def test_workspace_covers_every_stage():
     ig = gs.InfoGain(5000, cams, device="cpu")
     assert ig.ws.numel() >= L.workspace_size(L.GS_OP_INFO_GAIN, 5000, len(cams), ig.record_capacity,
                                              ig.pair_capacity, ig.n_tiles)
+
+
+def test_info_gain_growth_doubles_the_overflowed_capacity(monkeypatch):
+    """The batched pass has no count to read back cheaply: an overflowed record or pair
+    capacity is doubled (records never beyond N x V) and the status word cleared."""
+    cams = _cams()
+    ig = gs.InfoGain(1000, cams, device="cpu", record_capacity=300, pair_capacity=5000)
+    ig.status[0] = 7
+    monkeypatch.setattr(ig, "read_status", lambda: L.GS_FLAG_RECORD_OVERFLOW | L.GS_FLAG_PAIR_OVERFLOW)
+    assert ig.grow_if_needed()
+    assert (ig.record_capacity, ig.pair_capacity) == (600, 10_000) and int(ig.status[0]) == 0
+    ig.record_capacity = 3000
+    assert ig.grow_if_needed() and ig.record_capacity == 1000 * len(cams)
+    monkeypatch.setattr(ig, "read_status", lambda: 0)
+    assert not ig.grow_if_needed()
