@@ -142,6 +142,23 @@ def make_map(mo, su, q, rgb) -> L.gs_map:
     return L.gs_map(_ptr(mo), _ptr(su), _ptr(q), _ptr(rgb), int(mo.shape[0]))
 
 
+def _require(t: Optional[torch.Tensor], what: str, numel: int, dtype=torch.float32):
+    """Host-side check before a tensor's pointer crosses the C ABI: the library reads and writes
+    device memory, so a host, non-contiguous, wrongly typed or too small tensor is refused here
+    (None passes: the entry points take NULL for optional buffers)."""
+    if t is None:
+        return
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()
+            and t.numel() >= numel):
+        raise ValueError("%s must be a contiguous %s CUDA tensor of at least %d elements" % (what, dtype, numel))
+
+
+def _require_images(img, P: int):
+    for k, n, dt in (("rgb", 3 * P, torch.float32), ("depth", P, torch.float32), ("unc", P, torch.float32),
+                     ("T", P, torch.float32), ("last", P, torch.int32), ("n_contrib", P, torch.int32)):
+        _require(img.get(k), "image " + k, n, dt)
+
+
 def _alloc_u32(n, device):
     return torch.empty(max(int(n), 1), dtype=torch.int32, device=device)
 
@@ -240,6 +257,7 @@ class Frame:
 
     def render_fwd(self, gmap: GaussianMapTensors, images=None, stream=None):
         img = self.new_images() if images is None else images
+        _require_images(img, self.n_pixels)
         c_img = L.gs_image(_ptr(img["rgb"]), _ptr(img["depth"]), _ptr(img["unc"]), _ptr(img["T"]),
                            _ptr(img["last"]), _ptr(img.get("n_contrib")))
         m = gmap.c()
@@ -254,6 +272,11 @@ class Frame:
         if g is None:
             g = {k: torch.empty((self.n, 4), dtype=torch.float32, device=self.device) for k in
                  ("dmo", "dsu", "dq", "drgb")}
+        _require_images(images, self.n_pixels)
+        _require(d_rgb, "d_rgb", 3 * self.n_pixels)
+        _require(d_depth, "d_depth", self.n_pixels)
+        for k in ("dmo", "dsu", "dq", "drgb"):
+            _require(g[k], "gradient " + k, 4 * self.n)
         c_img = L.gs_image(_ptr(images["rgb"]), _ptr(images["depth"]), _ptr(images["unc"]), _ptr(images["T"]),
                            _ptr(images["last"]), None)
         c_g = L.gs_image_grad(_ptr(d_rgb), _ptr(d_depth))
@@ -270,6 +293,7 @@ class Frame:
         """Per-view mean of the composited uncertainty of the projected and binned views
         (gs_info_gain_composite; call project and bin_sort first)."""
         o = torch.zeros(self.V, dtype=torch.float32, device=self.device) if out is None else out
+        _require(o, "out", self.V)
         if not hasattr(self, "ig_ws"):
             self.ig_ws = torch.empty(L.workspace_size(L.GS_OP_IG_COMPOSITE, self.n, self.V, 0, 0,
                                                       max(self.n_tiles, 1)), dtype=torch.uint8, device=self.device)
@@ -396,6 +420,7 @@ class InfoGain:
 
     def __call__(self, gmap: GaussianMapTensors, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
         o = self.out if out is None else out
+        _require(o, "out", self.V)
         m = gmap.c()
         _timed("gs_info_gain_batch", stream, lambda: L.check(
             L.lib().gs_info_gain_batch(ctypes.byref(m), _ptr(self.cams_dev), self.V, ctypes.byref(self.c_params),
@@ -570,8 +595,9 @@ class ImageLoss:
 
     def __call__(self, rgb, depth, rgb_ref, depth_ref, with_grad: bool = True, stream=None):
         for t, n in ((rgb, 3 * self.P), (rgb_ref, 3 * self.P), (depth, self.P), (depth_ref, self.P)):
-            if t is not None and (t.numel() != n or t.dtype != torch.float32 or not t.is_contiguous()):
-                raise ValueError("images must be contiguous float32 tensors in the gs_image layout")
+            if t is not None and (t.numel() != n or t.dtype != torch.float32 or not t.is_contiguous()
+                                  or not t.is_cuda):
+                raise ValueError("images must be contiguous float32 CUDA tensors in the gs_image layout")
         dr = self.d_rgb if with_grad else None
         dd = self.d_depth if with_grad else None
         _timed("gs_image_loss", stream, lambda: L.check(
@@ -610,6 +636,10 @@ class Adam:
         self.params = list(params)
         if not 1 <= len(self.params) <= L.GS_ADAM_MAX_TENSORS:
             raise ValueError("between 1 and %d tensors" % L.GS_ADAM_MAX_TENSORS)
+        for i, p in enumerate(self.params):
+            _require(p, "parameter %d" % i, p.numel())
+            if p.numel() % 4:
+                raise ValueError("parameter %d: the number of elements must be a multiple of 4" % i)
         dev = self.params[0].device
         with torch.no_grad():
             self.m = [torch.zeros_like(p) for p in self.params]
@@ -630,6 +660,8 @@ class Adam:
         n = len(self.params)
         arr = lambda ts: (ctypes.c_void_p * n)(*[_ptr(t) for t in ts])
         grads = [p.grad for p in self.params]
+        for i, (p, g) in enumerate(zip(self.params, grads)):
+            _require(g, "gradient %d" % i, p.numel())
         _timed("gs_adam_step", stream, lambda: L.check(
             L.lib().gs_adam_step(arr(self.params), arr(grads), arr(self.m), arr(self.v), self._sizes, n,
                                  ctypes.byref(self.prm), _ptr(self.step_count), _stream(stream)), "gs_adam_step"))

@@ -145,3 +145,36 @@ def test_info_gain_growth_doubles_the_overflowed_capacity(monkeypatch):
     assert ig.grow_if_needed() and ig.record_capacity == 1000 * len(cams)
     monkeypatch.setattr(ig, "read_status", lambda: 0)
     assert not ig.grow_if_needed()
+
+
+def test_host_tensors_are_refused_before_the_library():
+    """Every entry point of the layer checks, before a pointer crosses the C ABI, that the
+    tensors it passes are contiguous CUDA tensors of the right type and size (the kernels
+    would otherwise be handed host addresses)."""
+    cams = _cams()
+    fr = gs.Frame(100, cams, device="cpu")
+    P = fr.n_pixels
+    img = {"rgb": torch.zeros(3 * P), "depth": torch.zeros(P), "unc": None, "T": torch.ones(P),
+           "last": torch.zeros(P, dtype=torch.int32)}
+    with pytest.raises(ValueError, match="image"):
+        fr.render_fwd(None, img)
+    with pytest.raises(ValueError, match="image"):
+        fr.render_bwd(None, img, torch.zeros(3 * P), torch.zeros(P))
+    with pytest.raises(ValueError, match="out"):
+        fr.info_gain(torch.zeros(len(cams)))
+    ig = gs.InfoGain(100, cams, device="cpu")
+    with pytest.raises(ValueError, match="out"):
+        ig(None, out=torch.zeros(len(cams)))
+    with pytest.raises(ValueError, match="parameter 0"):
+        gs.Adam([torch.zeros(8, 4)])
+    loss = gs.ImageLoss([(c.width, c.height) for c in cams], device="cpu")
+    with pytest.raises(ValueError, match="CUDA"):
+        loss(torch.zeros(3 * P), torch.zeros(P), torch.zeros(3 * P), torch.zeros(P))
+
+
+def test_require_accepts_none_and_checks_type_and_size():
+    gs._require(None, "x", 10)
+    with pytest.raises(ValueError, match="at least 10"):
+        gs._require(torch.zeros(20), "x", 10)          # a host tensor, whatever its size
+    with pytest.raises(ValueError):
+        gs._require(np.zeros(20, np.float32), "x", 10)  # not a tensor at all
