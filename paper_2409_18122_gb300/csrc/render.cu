@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(256) k_ig_views(const uint32_t* __restrict__ v
   const int W = cams[v].width, H = cams[v].height;
   float s = 0.f;
   // fixed assignment of items to threads and a fixed reduction tree: deterministic
-  for (uint32_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += item_sum[i];
+  for (int64_t i = (int64_t)i0 + threadIdx.x; i < (int64_t)i1; i += blockDim.x) s += item_sum[i];
   s = block_sum_fixed(s, s_red);
   if (threadIdx.x == 0) ig[v] = (W > 0 && H > 0) ? s / ((float)W * (float)H) : 0.f;
 }
@@ -326,7 +326,10 @@ __global__ void k_item_cost(const gs_proj proj, const gs_bins bins, int n_views,
                             uint32_t* __restrict__ key) {
   uint32_t n = proj.view_info[kVI * n_views + 2] / kPix;
   if ((int64_t)n > item_cap) n = (uint32_t)item_cap;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  // 64-bit index: a 32-bit one could wrap past n when n is near 2^32 and never leave the loop
+  for (int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i64 < (int64_t)n;
+       i64 += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = (uint32_t)i64;
     const int v = find_view(proj.view_info, n_views, i * kPix, 2);
     const uint32_t code = proj.view_info[kVI * v + 3];
     const uint32_t wpt = ((code & 0xffu) * ((code >> 8) & 0xffu)) / (32 * kPix);

@@ -341,14 +341,14 @@ __global__ void __launch_bounds__(kBlock) k_collision(const float4* __restrict__
 }
 
 __global__ void k_collision_init(uint32_t* __restrict__ margin_key, uint32_t* __restrict__ hit, int n_pts) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pts; i += gridDim.x * blockDim.x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pts; i += (int64_t)gridDim.x * blockDim.x) {
     margin_key[i] = fkey(INFINITY);
     hit[i] = 0u;
   }
 }
 
 __global__ void k_collision_finish(uint32_t* __restrict__ margin, int n_pts) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pts; i += gridDim.x * blockDim.x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pts; i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t k = margin[i];
     reinterpret_cast<float*>(margin)[i] = fkey_inv(k);
   }
