@@ -190,3 +190,32 @@ def test_python_binding_raises_without_library(monkeypatch):
     monkeypatch.setattr(L, "_lib", None)
     with pytest.raises(L.GSError):
         L.lib()
+
+
+def test_plain_c_program_builds_links_and_calls(lib, tmp_path):
+    """The boundary is a C library: a C99 program (strict, warnings as errors) and the same
+    source as C++11 compile against include/gs.h alone, and the C program links against
+    libgs103.so and calls its host-side entry points without any Python or torch."""
+    src = tmp_path / "use_gs.c"
+    src.write_text("\n".join([
+        "#include <stdio.h>",
+        "#include \"gs.h\"",
+        "int main(void) {",
+        "  size_t b = 0;",
+        "  gs_status s = gs_workspace_size(GS_OP_PROJECT, 1000, 4, 0, 0, 0, &b);",
+        "  gs_status bad = gs_workspace_size(GS_OP_PROJECT, -1, 4, 0, 0, 0, &b);",
+        "  printf(\"%d %d %zu|%s|%s\\n\", (int)s, (int)bad, b, gs_status_str(bad), gs_version());",
+        "  return s == GS_OK && bad == GS_ERR_ARG && b > 0 ? 0 : 1;",
+        "}"]) + "\n")
+    inc = os.path.join(ROOT, "include")
+    libdir = os.path.dirname(L.LIB_PATH)
+    subprocess.check_call(["g++", "-std=c++11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, "-x", "c++",
+                           str(src), "-c", "-o", str(tmp_path / "use_gs_cxx.o")])
+    exe = tmp_path / "use_gs"
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, str(src),
+                           "-L", libdir, "-lgs103", "-Wl,-rpath," + libdir, "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stdout + out.stderr
+    codes, status, version = out.stdout.strip().split("|")
+    assert codes.split()[:2] == [str(L.GS_OK), str(L.GS_ERR_ARG)]
+    assert status.startswith("GS_ERR_ARG") and version
