@@ -378,7 +378,9 @@ typedef struct {
 gs_status gs_uncertainty_update(const float* mo_prev, const float* mo_cur, float* su, int64_t n, int32_t mode,
                                 void* stream);
 
-/* gs_uncertainty_thresholds -- mean and population standard deviation of u over the
+/* gs_uncertainty_thresholds -- Sec. IV-C: G_H and G_L are the Gaussians whose update
+ * magnitude u lies more than half a standard deviation above / below its mean (ground
+ * Gaussians left out, Sec. IV-C).  Mean and population standard deviation of u over the
  * Gaussians with mu_z >= ground_z (FP64, two passes, fixed summation order), into
  * DEVICE double stats[5] = (mean, sigma, mean + sigma/2, mean - sigma/2, count).
  * ws: DEVICE workspace of gs_workspace_size(GS_OP_THRESHOLDS, ...) bytes.

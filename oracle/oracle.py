@@ -18,7 +18,7 @@ Functions and the passages they follow (RT-GuIDE, arXiv 2409.18122):
                ordered by (view, tile, depth, record index).
   uncertainty_update   Sec. IV-A: u = |mu_k - mu_{k-1}| (or its square), unchanged
                means keep their u.
-  uncertainty_thresholds  Sec. IV-B (implementation details): G_H / G_L thresholds at
+  uncertainty_thresholds  Sec. IV-C (implementation details): G_H / G_L thresholds at
                half a standard deviation above / below the mean of u.
   visibility / view_utility  Sec. IV-B, Eq. view_util: xi = |visible G_H| - lambda
                |visible G_L| (or the sum of u of the visible Gaussians); visible =
