@@ -328,9 +328,9 @@ gs_status gs_info_gain_batch(const gs_map* map, const gs_camera* cams, int32_t n
                              int32_t mode, float* ig_out, uint32_t* status, int64_t record_capacity,
                              int64_t pair_capacity, int64_t tile_capacity, void* ws, size_t ws_bytes, void* stream);
 
-/* gs_info_gain_composite -- the compositing stage of gs_info_gain_batch on
- * records and bins already produced by gs_project and gs_bin_sort for the
- * candidate views: U-only front-to-back compositing (same alpha / skip / stop
+/* gs_info_gain_composite -- Eq. (nbv), Sec. IV-A: the compositing stage of
+ * gs_info_gain_batch on records and bins already produced by gs_project and
+ * gs_bin_sort for the candidate views: U-only front-to-back compositing (same alpha / skip / stop
  * rules as gs_render_fwd) by a persistent kernel that takes warp items (8x4
  * pixel blocks of tiles) longest tile list first from a device queue, one slot
  * per item, then a fixed-order per-view reduction IG_v = (1/P_v) sum_p U(p).
@@ -496,6 +496,9 @@ gs_status gs_adam_step(float* const* params, const float* const* grads, float* c
                        void* stream);
 
 /* ------------------------------------------------------------- utilities */
+/* The library's own bookkeeping (workspace sizes, the device status word, status
+ * strings, version, launch count): none of these computes a step of the method, so
+ * no passage of the paper applies to them. */
 enum {
   GS_OP_PROJECT = 0,
   GS_OP_BIN_SORT = 1,
