@@ -70,3 +70,39 @@ def test_collision_workload_point_count():
     spec.loader.exec_module(bench)
     assert bench.COLLISION_POINTS == int(PAPER["collision_points"])
 
+
+
+def _make_golden():
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(GOLDEN, "make_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _compare(got, ref, path="fixture"):
+    """Integers exactly; floats to 1e-12 relative (the oracle is FP64 with a fixed operation
+    order; libm may differ in the last bit between machines)."""
+    if isinstance(ref, dict):
+        assert set(got) == set(ref), path
+        for k in ref:
+            _compare(got[k], ref[k], path + "." + k)
+    elif isinstance(ref, list):
+        assert len(got) == len(ref), path
+        for i, (g, r) in enumerate(zip(got, ref)):
+            _compare(g, r, "%s[%d]" % (path, i))
+    elif isinstance(ref, int):
+        assert got == ref, path
+    else:
+        assert abs(got - ref) <= 1e-12 * abs(ref) + 1e-15, (path, got, ref)
+
+
+def test_oracle_reproduces_its_tiny_scene_fixture():
+    """Regression fixture (written by tests/golden/make_golden.py from the oracle alone):
+    pair keys, tile ranges and last contributors exactly, images, information gain and
+    gradients to FP64 rounding.  A deliberate change to the oracle regenerates it."""
+    import json
+    ref = json.load(open(os.path.join(GOLDEN, "oracle_tiny_scene.json")))
+    ref.pop("written_by")
+    got = json.loads(json.dumps(_make_golden().compute()))
+    _compare(got, ref)
+    assert ref["n_pairs"] == len(ref["keys"]) > 100
