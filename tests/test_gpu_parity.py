@@ -175,7 +175,7 @@ def test_bin_sort_flags_bad_records():
     assert _bin_only(beyond, cams).read_status() & bad_flag
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8), (16, 8), (32, 16), (32, 32)])
 def test_bin_sort_pipeline_room_subset(tile):
     """Projection + binning on the first 4,096 Gaussians of the 200k-Gaussian room, bit-exact."""
     sc = scenes.config1()
@@ -255,7 +255,9 @@ def test_tile_shape_invariance_bitwise():
     sc = scenes.config2(n=20_000, n_views=1)
     cams = [sc.cams[0].crop(160, 120, 200, 136)]
     outs = []
-    for tw, th in ((16, 16), (8, 8), (32, 8), (16, 32)):
+    shapes = [(16, 16), (8, 8), (32, 8), (16, 32)] + [t for t in gs.TILE_CANDIDATES if t not in ((16, 16), (8, 8),
+                                                                                                (32, 8))]
+    for tw, th in shapes:
         fr, gm, img = run_forward(sc.gmap, cams, gs.RenderParams(tile_w=tw, tile_h=th))
         outs.append(images_host(fr, img)[0])
     for o in outs[1:]:
@@ -503,9 +505,21 @@ def test_info_gain_composite_entry_matches_batch():
         assert abs(float(comp[v]) - ref[v]) <= tol, (v, comp[v], ref[v])
 
 
-def test_info_gain_per_view_tiles_vs_oracle():
+IG_TILE_SETS = [((8, 8), (16, 8), (16, 16)), ((8, 8), (16, 8), (32, 16)), ((16, 8), (32, 16), (32, 32)),
+                ((32, 8), (16, 16), (32, 32)), ((32, 16), (32, 32), (8, 8))]
+
+
+def test_ig_tile_sets_cover_every_candidate():
+    assert set(gs.TILE_CANDIDATES) <= {t for s in IG_TILE_SETS for t in s}
+
+
+@pytest.mark.parametrize("tiles", IG_TILE_SETS, ids=lambda t: "-".join("%dx%d" % x for x in t))
+def test_info_gain_per_view_tiles_vs_oracle(tiles):
+    """Per-view tiles by resolution class (80x60, 160x120, 320x240), every shape the autotuner
+    can return among them."""
     gmap, cams = _ig_scene()
-    cams = [c.with_tile(8, 8) if c.width <= 80 else (c.with_tile(16, 8) if c.width <= 160 else c) for c in cams]
+    cls = lambda c: 0 if c.width <= 80 else (1 if c.width <= 160 else 2)
+    cams = [c.with_tile(*tiles[cls(c)]) for c in cams]
     gm = gs.GaussianMapTensors.from_numpy(gmap)
     ig = gs.InfoGain(gm.n, cams)(gm).cpu().numpy().astype(np.float64)
     ref, imgs = O.info_gain(gmap, cams)
@@ -527,17 +541,64 @@ def test_info_gain_uniform_uncertainty_is_mean_coverage():
         assert abs(ig[v] - np.mean(1 - T[v])) < 1e-5
 
 
-def test_info_gain_full_size_config3_two_views():
-    """1M Gaussians, all 256 candidates in one batch; two 80x60 views checked against the oracle."""
+# the tiles the autotuner picked for the information-gain pass of the 1M-Gaussian, 256-candidate
+# batch on a GB300 (80x60, 160x120, 320x240 classes); set explicitly so that the test checks the
+# configuration that is timed
+CONFIG3_TILES = {(80, 60): (8, 8), (160, 120): (16, 8), (320, 240): (32, 16)}
+
+
+def test_info_gain_full_size_config3_autotuned_tiles():
+    """1M Gaussians, all 256 candidates in one batch at the autotuned tiles; two views of each
+    resolution class against the oracle (information gain over all pixels), and the number of
+    contributing (pixel, Gaussian) evaluations per pixel of the forward kernel, at the same tiles,
+    against the oracle's count (the work unit of the compositing roofline)."""
     sc = scenes.config3()
+    cams = gs.with_tiles(sc.cams, CONFIG3_TILES)
     gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
-    ig_op = gs.InfoGain(gm.n, sc.cams)
-    ig = ig_op(gm).cpu().numpy()
+    ig_op = gs.InfoGain(gm.n, cams)
+    ig = ig_op(gm)
+    torch.cuda.synchronize()
+    while ig_op.grow_if_needed():
+        ig = ig_op(gm)
+        torch.cuda.synchronize()
+    ig = ig.cpu().numpy()
     assert not (ig_op.read_status() & gs.L.GS_FLAG_ERROR_MASK)
-    for v in (0, 3):
-        ref, imgs = O.info_gain(sc.gmap, [sc.cams[v]])
-        tol = IG_RTOL * abs(ref[0]) + 1e-7 + imgs[0]["knife"].mean() * 4e-3
-        assert abs(ig[v] - ref[0]) <= tol, (v, ig[v], ref[0])
+    picks = [v for cls in ((80, 60), (160, 120), (320, 240))
+             for v in [i for i, c in enumerate(cams) if (c.width, c.height) == cls][1::40][:2]]
+    assert len(picks) == 6
+    sel = [cams[v] for v in picks]
+    fr = gs.Frame(gm.n, sel)
+    img = fr.new_images(with_counts=True)
+    fr.forward(gm, img)
+    torch.cuda.synchronize()
+    fr.check_status()
+    views = fr.split_images(img)
+    ref, imgs = O.info_gain(sc.gmap, sel)
+    for k, v in enumerate(picks):
+        tol = IG_RTOL * abs(ref[k]) + 1e-7 + imgs[k]["knife"].mean() * 4e-3
+        assert abs(ig[v] - ref[k]) <= tol, (v, ig[v], ref[k])
+        nc = views[k]["n_contrib"].cpu().numpy()
+        differ = nc != imgs[k]["n_contrib"]
+        assert not (differ & ~imgs[k]["knife"]).any(), (v, int(differ.sum()))
+        assert differ.sum() <= max(1, 1e-4 * differ.size), (v, int(differ.sum()))
+
+
+def test_guard_band_scene_vs_oracle():
+    """Centres just inside and just outside the guard band on each side, at three depths: the
+    kernels keep and cull exactly the oracle's set, and render the off-image centres that the
+    band keeps like the oracle."""
+    from test_oracle_pins import GUARD_CAM, guard_band_scene
+    g, meta = guard_band_scene()
+    cams = [GUARD_CAM]
+    fr, gm, img = run_forward(g, cams)
+    rec, _ = check_projection(fr, g, cams, fr.params)
+    np.testing.assert_array_equal(np.sort(rec["gid"]), [i for i, m in enumerate(meta) if m[4]])
+    gpu = images_host(fr, img)[0]
+    ref = O.render_images(g, cams)[0]
+    assert (ref["unc"] > 0).mean() > 0.05
+    compare_image(gpu, ref, "guard band", check_last=last_gid(fr, [gpu])[0])
+    ig = gs.InfoGain(gm.n, cams)(gm).cpu().numpy().astype(np.float64)
+    assert abs(ig[0] - ref["unc"].mean()) <= IG_RTOL * abs(ref["unc"].mean()) + 1e-7
 
 
 # --------------------------------------------------------------------------- degenerate inputs

@@ -265,6 +265,79 @@ def test_opacity_floor_and_near_plane():
     np.testing.assert_array_equal(O.project(g2, [cam])["vis"][0], [0, 0, 1, 1])
 
 
+# ----------------------------------------------------------------------------- guard band
+# The cull of a centre outside the guard band (the reading taken where the paper is silent:
+# 1.3 times the half field of view on each axis, |t_x / t_z| <= 1.3 (W/2) / f_x and the same
+# in y).  fx != fy and W/fx != H/fy, so that a swap of the axes, of W and H or of fx and fy
+# moves one of the bands; the factor 1.3 is written out here, not taken from Params.
+GUARD_READING = 1.3
+GUARD_CAM = Camera(120.0, 100.0, 64.0, 48.0, 128, 96)
+GUARD_LS = -1.2          # sigma 0.30 m: the support reaches into the image from inside the band
+
+
+def guard_band_scene(cam=GUARD_CAM, depths=(1.5, 2.5, 4.0), rel=1e-3):
+    """One Gaussian per (depth, axis, side, factor): centre at t_axis / t_z = side x factor x the
+    band's slope, the other lateral coordinate 0, factor 1 - rel (inside) or 1 + rel (outside).
+    Returns the map and, per Gaussian, (axis, side, factor, t_z, inside)."""
+    slope = (GUARD_READING * (cam.width / 2) / cam.fx, GUARD_READING * (cam.height / 2) / cam.fy)
+    pos, meta = [], []
+    for tz in depths:
+        for axis in (0, 1):
+            for side in (1.0, -1.0):
+                for f in (1 - rel, 1 + rel):
+                    t = [0.0, 0.0, tz]
+                    t[axis] = side * f * slope[axis] * tz
+                    pos.append(t)
+                    meta.append((axis, side, f, tz, f < 1))
+    n = len(pos)
+    g = gmap_from(pos, [[GUARD_LS] * 3] * n, [[1, 0, 0, 0]] * n, [2.0] * n, [[0.25, 0.5, 0.75]] * n, [1.0] * n)
+    return g, meta
+
+
+def _axis_aligned_alpha(g, i, cam, pix, eps):
+    """Closed-form alpha of Gaussian i (identity rotation, camera at the origin looking +z) at
+    the pixel centres pix (K x 3: view, u, v): Sigma_2D = J diag(s^2) J^T + eps I with
+    J = [[f_x/t_z, 0, -f_x t_x/t_z^2], [0, f_y/t_z, -f_y t_y/t_z^2]]; the skip and clamp rules."""
+    tx, ty, tz = g.mo[i, :3].astype(np.float64)
+    s2 = np.exp(2 * g.su[i, :3].astype(np.float64))
+    fx, fy = cam.fx, cam.fy
+    J = np.array([[fx / tz, 0, -fx * tx / tz ** 2], [0, fy / tz, -fy * ty / tz ** 2]])
+    S = J @ np.diag(s2) @ J.T + eps * np.eye(2)
+    mx, my = fx * tx / tz + cam.cx, fy * ty / tz + cam.cy
+    d = np.stack([pix[:, 1] + 0.5 - mx, pix[:, 2] + 0.5 - my], 1)
+    q = np.einsum("ki,ij,kj->k", d, np.linalg.inv(S), d)
+    a = sig(g.mo[i, 3]) * np.exp(-0.5 * q)
+    return np.where(a < AMIN, 0.0, np.minimum(a, AMAX))
+
+
+def test_guard_band_keeps_inside_culls_outside():
+    g, meta = guard_band_scene()
+    pr = O.project(g, [GUARD_CAM])
+    np.testing.assert_array_equal(pr["vis"][0].astype(bool), [m[4] for m in meta])
+
+
+def test_guard_band_edge_gaussian_closed_form_alpha():
+    """A centre outside the image but inside the band is rendered, with the closed-form alpha
+    of its 2D Gaussian at every pixel; a centre just outside the band adds nothing anywhere."""
+    g, meta = guard_band_scene()
+    p = O.Params()
+    eps = float(np.float32(p.eps2d))
+    pix = O.all_pixels([GUARD_CAM])
+    for i, (axis, side, f, tz, inside) in enumerate(meta):
+        one = g.subset([i])
+        r = O.render(one, [GUARD_CAM], p, pixels=pix)
+        if inside:
+            mx = GUARD_CAM.fx * float(one.mo[0, 0]) / float(one.mo[0, 2]) + GUARD_CAM.cx
+            my = GUARD_CAM.fy * float(one.mo[0, 1]) / float(one.mo[0, 2]) + GUARD_CAM.cy
+            assert not (0 <= mx <= GUARD_CAM.width and 0 <= my <= GUARD_CAM.height), "centre must be off-image"
+            a = _axis_aligned_alpha(g, i, GUARD_CAM, pix, eps)
+            assert (a > 0).sum() > 20, "the support must reach into the image"
+            np.testing.assert_allclose(r["unc"], a, rtol=1e-11, atol=1e-15)
+            np.testing.assert_allclose(r["T"], 1 - a, rtol=1e-11, atol=1e-15)
+        else:
+            assert (r["unc"] == 0).all() and (r["T"] == 1).all() and (r["n_contrib"] == 0).all()
+
+
 # ----------------------------------------------------------------------------- binning / sort
 def test_bin_sort_against_brute_force():
     from paper_2409_18122_gb300.scenes import synthetic_records
