@@ -24,6 +24,11 @@ __device__ __forceinline__ bool camera_ok(const gs_camera& c, int tw, int th) {
          valid_tile(tw, th);
 }
 
+// Pixels of a view in the image layout: W x H, a negative size counting as zero.
+__device__ __forceinline__ unsigned long long view_pixels(const gs_camera& c) {
+  return (unsigned long long)(c.width > 0 ? c.width : 0) * (unsigned long long)(c.height > 0 ? c.height : 0);
+}
+
 // Per-view table: tile, pixel and warp-item offsets (prefix sums over views), tile
 // sizes, camera checks.
 __global__ void __launch_bounds__(1024) k_view_info(const gs_camera* __restrict__ cams, int n_views, int def_tw,
@@ -34,16 +39,19 @@ __global__ void __launch_bounds__(1024) k_view_info(const gs_camera* __restrict_
   const int v0 = threadIdx.x * per;
   int v1 = v0 + per;
   if (v1 > n_views) v1 = n_views;
+  // every view keeps its W x H pixels in the image layout, so that the layout is the same
+  // whatever the device decides about a camera; an invalid camera gets no tiles and no warp
+  // items (its pixels are never written)
   unsigned long long acc[3] = {0, 0, 0};   // tiles, pixels, warp items
   bool bad = false;
   for (int v = v0; v < v1; ++v) {
     const gs_camera& c = cams[v];
     int tw, th;
     view_tile(c, def_tw, def_th, tw, th);
+    acc[1] += view_pixels(c);
     if (!camera_ok(c, tw, th)) { bad = true; continue; }
     const unsigned long long t = (unsigned long long)((c.width + tw - 1) / tw) * ((c.height + th - 1) / th);
     acc[0] += t;
-    acc[1] += (unsigned long long)c.width * (unsigned long long)c.height;
     acc[2] += t * (unsigned long long)(tw * th / 32);
   }
   if (bad) set_flag(status, GS_FLAG_BAD_CAMERA);
@@ -77,10 +85,10 @@ __global__ void __launch_bounds__(1024) k_view_info(const gs_camera* __restrict_
     view_info[kVI * v + 1] = (uint32_t)e[1];
     view_info[kVI * v + 2] = (uint32_t)e[2];
     view_info[kVI * v + 3] = ok ? ((uint32_t)tw | ((uint32_t)th << 8) | (tx << 16)) : 0u;
+    e[1] += view_pixels(c);
     if (ok) {
       const unsigned long long t = (unsigned long long)tx * ((c.height + th - 1) / th);
       e[0] += t;
-      e[1] += (unsigned long long)c.width * (unsigned long long)c.height;
       e[2] += t * (unsigned long long)(tw * th / 32);
     }
   }

@@ -105,12 +105,28 @@ def view_tile(c, params: RenderParams):
     return (tw, th) if tw and th else (params.tile_w, params.tile_h)
 
 
+def valid_tile(tw: int, th: int) -> bool:
+    """The tile sizes the kernels accept (include/gs.h gs_params)."""
+    return tw in (8, 16, 32, 64) and th >= 8 and th % 8 == 0 and tw * th in (64, 128, 256, 512, 1024)
+
+
+def camera_ok(c, params: RenderParams) -> bool:
+    """The library's camera check (a camera failing it sets GS_FLAG_BAD_CAMERA and gets no tiles):
+    a positive image size, positive finite focal lengths and a valid tile size."""
+    tw, th = view_tile(c, params)
+    fx, fy = float(np.float32(c.fx)), float(np.float32(c.fy))
+    return (c.width > 0 and c.height > 0 and fx > 0 and fy > 0 and np.isfinite(fx) and np.isfinite(fy)
+            and valid_tile(tw, th))
+
+
 def tile_grid(cams, params: RenderParams):
-    """Per view: tiles_x, tiles_y; and the tile and pixel offsets of the views (length V+1)."""
-    tx = np.array([-(-c.width // view_tile(c, params)[0]) for c in cams], np.int64)
-    ty = np.array([-(-c.height // view_tile(c, params)[1]) for c in cams], np.int64)
+    """Per view: tiles_x, tiles_y; and the tile and pixel offsets of the views (length V+1).
+    A view whose camera fails camera_ok has no tiles but keeps its W x H pixels."""
+    ok = [camera_ok(c, params) for c in cams]
+    tx = np.array([-(-c.width // view_tile(c, params)[0]) if k else 0 for c, k in zip(cams, ok)], np.int64)
+    ty = np.array([-(-c.height // view_tile(c, params)[1]) if k else 0 for c, k in zip(cams, ok)], np.int64)
     tiles = tx * ty
-    pix = np.array([c.width * c.height for c in cams], np.int64)
+    pix = np.array([max(c.width, 0) * max(c.height, 0) for c in cams], np.int64)
     tile_base = np.concatenate([[0], np.cumsum(tiles)])
     pix_base = np.concatenate([[0], np.cumsum(pix)])
     return tx, ty, tile_base, pix_base
@@ -190,6 +206,9 @@ class Frame:
         self.n_pixels = int(self.pix_base[-1])
         # records: at most n * V; a smaller capacity (large batches) grows on overflow
         self.rec_capacity = max(int(record_capacity) if record_capacity else self.n * self.V, 1)
+        # bumped by every projection and binning: the backward pass replays the records and tile
+        # lists of its own forward, so it refuses to run once they have been overwritten
+        self.generation = 0
         if pair_capacity is None:
             pair_capacity = min(max(1 << 20, 8 * self.n * self.V), (1 << 31) - 1)
         self._alloc(int(pair_capacity))
@@ -235,12 +254,14 @@ class Frame:
         if gmap.n != self.n:
             raise ValueError("map has %d Gaussians, frame was built for %d" % (gmap.n, self.n))
         m = gmap.c()
+        self.generation += 1
         _timed("gs_project", stream, lambda: L.check(
             L.lib().gs_project(ctypes.byref(m), _ptr(self.cams_dev), self.V, ctypes.byref(self.c_params),
                                ctypes.byref(self.c_proj), _ptr(self.ws), self.ws.numel(), _stream(stream)),
             "gs_project"))
 
     def bin_sort(self, stream=None):
+        self.generation += 1
         _timed("gs_bin_sort", stream, lambda: L.check(
             L.lib().gs_bin_sort(ctypes.byref(self.c_proj), _ptr(self.cams_dev), self.V, ctypes.byref(self.c_params),
                                 ctypes.byref(self.c_bins), _ptr(self.ws), self.ws.numel(), _stream(stream)),
@@ -335,12 +356,14 @@ class Frame:
             self.rec_capacity = max(min(int(need * margin) + 1024, self.n * self.V), 1)
             self.status.zero_()
             self._alloc(self.pair_capacity)
+            self.generation += 1
             return True
         if f & L.GS_FLAG_PAIR_OVERFLOW:
             need = int(self.pair_count.item()) & 0xFFFFFFFF
             if need == 0xFFFFFFFF:
                 need = 2 * self.pair_capacity
             self._alloc(min(int(need * margin) + 1024, (1 << 32) - 2))
+            self.generation += 1
             return True
         return False
 
@@ -360,18 +383,31 @@ class Frame:
         return out
 
 
+class StaleFrameError(RuntimeError):
+    """backward() of a render whose Frame has been projected or binned again since its forward."""
+
+
 class _RenderFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, mo, su, q, rgb, frame: Frame):
         gmap = GaussianMapTensors(mo, su, q, rgb)
         img = frame.forward(gmap)
         ctx.frame = frame
+        ctx.generation = frame.generation
         ctx.img = img
         ctx.save_for_backward(mo, su, q, rgb)
+        # the uncertainty channel has no adjoint (u_i is not a learned parameter, and the
+        # backward kernel replays colour and depth only): no gradient flows through it
+        ctx.mark_non_differentiable(img["unc"])
         return img["rgb"], img["depth"], img["unc"]
 
     @staticmethod
     def backward(ctx, g_rgb, g_depth, g_unc):
+        if ctx.frame.generation != ctx.generation:
+            raise StaleFrameError(
+                "the Frame was projected or binned again after this render's forward pass; its records and "
+                "tile lists no longer belong to this render.  Give each render that is differentiated together "
+                "its own Frame, or call backward before the next render through the same Frame.")
         mo, su, q, rgb = ctx.saved_tensors
         gmap = GaussianMapTensors(mo, su, q, rgb)
         g_rgb = None if g_rgb is None else g_rgb.contiguous()
@@ -384,7 +420,11 @@ def render(mo, su, q, rgb, frame: Frame):
     """Differentiable render of all views of `frame`: flat (rgb [3P], depth [P], unc [P]) tensors.
 
     Gradients flow to mo (means, opacity logit), su (log-scales; the uncertainty
-    column gets zero), q and rgb through gs_render_bwd.
+    column gets zero), q and rgb through gs_render_bwd, from the rgb and depth
+    outputs.  The uncertainty output is marked non-differentiable (the backward pass
+    has no adjoint for it).  The backward pass replays the frame's records and tile
+    lists: rendering through the same frame again before backward() makes that
+    backward() raise StaleFrameError instead of returning wrong gradients.
     """
     return _RenderFn.apply(mo, su, q, rgb, frame)
 
@@ -687,7 +727,7 @@ def autotune_tiles(gmap: GaussianMapTensors, cams: Sequence, params: RenderParam
     for res, group in classes.items():
         timings[res] = {}
         for tw, th in candidates:
-            if not (tw <= 64 and th % 8 == 0 and tw * th in (64, 128, 256, 512, 1024)):
+            if not valid_tile(tw, th):
                 continue
             tc = [type(c)(c.fx, c.fy, c.cx, c.cy, c.width, c.height, c.R, c.T, tw, th) for c in group]
             ig = InfoGain(gmap.n, tc, params, pair_capacity=pair_capacity)

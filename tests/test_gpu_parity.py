@@ -445,6 +445,35 @@ def test_autograd_function_matches_direct_adjoint():
         torch.testing.assert_close(p.grad, g[k], rtol=1e-5, atol=1e-9)
 
 
+def test_backward_refuses_a_frame_rendered_again():
+    """Keyframes rendered through one Frame one after the other, then one loss: the first render's
+    backward would replay the second's tile lists, so it raises; with a Frame per render both
+    gradients equal the direct adjoint of their own render."""
+    sc = scenes.config2(n=20_000, n_views=2)
+    gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
+    params = [t.clone().requires_grad_(True) for t in (gm.mo, gm.su, gm.q, gm.rgb)]
+    shared = gs.Frame(gm.n, [sc.cams[0]])
+    rgb_a, _, _ = gs.render(*params, shared)
+    shared.cams_dev.copy_(gs.cameras_to_device([sc.cams[1]]))
+    rgb_b, _, _ = gs.render(*params, shared)
+    with pytest.raises(gs.StaleFrameError):
+        (rgb_a.sum() + rgb_b.sum()).backward()
+    for p in params:
+        p.grad = None
+    frames = [gs.Frame(gm.n, [c]) for c in sc.cams]
+    outs = [gs.render(*params, f)[0] for f in frames]
+    sum(o.sum() for o in outs).backward()
+    total = {k: torch.zeros_like(t) for k, t in zip(("dmo", "dsu", "dq", "drgb"), params)}
+    for f, o in zip(frames, outs):
+        img = f.forward(gm)
+        g = f.render_bwd(gm, img, torch.ones_like(o), None)
+        for k in total:
+            total[k] += g[k]
+    torch.cuda.synchronize()
+    for p, k in zip(params, ("dmo", "dsu", "dq", "drgb")):
+        torch.testing.assert_close(p.grad, total[k], rtol=1e-5, atol=1e-7)
+
+
 def test_gradients_full_size_sparse_pixels():
     """Config-2 map (500k) and keyframe at 640x480, image gradient on 48 sampled pixels (elsewhere zero)."""
     sc = scenes.config2()

@@ -178,3 +178,47 @@ def test_require_accepts_none_and_checks_type_and_size():
         gs._require(torch.zeros(20), "x", 10)          # a host tensor, whatever its size
     with pytest.raises(ValueError):
         gs._require(np.zeros(20, np.float32), "x", 10)  # not a tensor at all
+
+
+class _FakeFrame:
+    """Stands in for gs.Frame on the CPU: forward() bumps the generation like project() and
+    bin_sort() do and returns images; render_bwd() returns gradients of ones."""
+
+    def __init__(self, n, P):
+        self.n, self.P, self.generation, self.bwd_calls = n, P, 0, 0
+
+    def forward(self, gmap):
+        self.generation += 2
+        z = torch.zeros(self.P)
+        return dict(rgb=torch.zeros(3 * self.P), depth=z.clone(), unc=z.clone(), T=z.clone(),
+                    last=torch.zeros(self.P, dtype=torch.int32))
+
+    def render_bwd(self, gmap, img, d_rgb, d_depth):
+        self.bwd_calls += 1
+        return {k: torch.ones(self.n, 4) for k in ("dmo", "dsu", "dq", "drgb")}
+
+
+def _params(n=5):
+    return [torch.zeros(n, 4, requires_grad=True) for _ in range(4)]
+
+
+def test_backward_after_a_second_render_through_the_frame_raises():
+    """Two renders through one frame, then backward of the first: the records and tile lists it
+    would replay belong to the second render, so it raises instead of returning wrong gradients."""
+    fr = _FakeFrame(5, 12)
+    p = _params()
+    rgb1, _, _ = gs.render(*p, fr)
+    rgb2, _, _ = gs.render(*p, fr)
+    with pytest.raises(gs.StaleFrameError):
+        rgb1.sum().backward()
+    assert fr.bwd_calls == 0
+    rgb2.sum().backward()            # the latest render is still differentiable
+    assert fr.bwd_calls == 1 and torch.equal(p[0].grad, torch.ones(5, 4))
+
+
+def test_uncertainty_output_is_not_differentiable():
+    fr = _FakeFrame(5, 12)
+    rgb, depth, unc = gs.render(*_params(), fr)
+    assert rgb.requires_grad and depth.requires_grad and not unc.requires_grad
+    with pytest.raises(RuntimeError):
+        unc.sum().backward()
