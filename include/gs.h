@@ -58,7 +58,9 @@ enum {
   GS_FLAG_PAIR_OVERFLOW = 1u << 0,   /* more (tile, Gaussian) pairs than gs_bins.pair_capacity */
   GS_FLAG_RANGE_OVERFLOW = 1u << 1,  /* more tiles over all views than gs_bins.tile_capacity   */
   GS_FLAG_BAD_CAMERA = 1u << 2,      /* a camera has width*height <= 0, a non-positive focal length or an invalid tile size */
-  GS_FLAG_NONFINITE = 1u << 3,       /* informational: Gaussians with non-finite parameters were culled */
+  GS_FLAG_NONFINITE = 1u << 3,       /* informational: Gaussians with a non-finite mean, opacity logit,
+                                        log-scale or quaternion entry were culled (colours and u are
+                                        not checked: they only scale a channel) */
   GS_FLAG_RECORD_OVERFLOW = 1u << 4, /* more visible (Gaussian, view) records than capacity    */
   GS_FLAG_BAD_RECORDS = 1u << 5      /* gs_bin_sort input: records not grouped by increasing view,
                                         a view id >= n_views, or a rectangle outside its view's tiles */
@@ -186,7 +188,8 @@ gs_status gs_project(const gs_map* map, const gs_camera* cams, int32_t n_views, 
  *   ranges  [tile_capacity][2] per global tile: [start, end) into tile/rec, clipped to pair_capacity
  * Global tile id of tile (x, y) of view v = view_info[v].first_tile + y * tiles_x(v) + x,
  * tiles_x(v) = ceil(W_v / tile_w(v)), tiles_y(v) = ceil(H_v / tile_h(v)) with the
- * view's tile size (its camera's, else gs_params'). */
+ * view's tile size (its camera's, else gs_params'); a view whose camera is invalid
+ * (GS_FLAG_BAD_CAMERA) has no tiles. */
 typedef struct {
   int64_t pair_capacity;
   int64_t tile_capacity;
@@ -215,7 +218,10 @@ gs_status gs_bin_sort(const gs_proj* proj, const gs_camera* cams, int32_t n_view
 /* ------------------------------------------------------------- compositing */
 
 /* Rendered images of all views, concatenated: view v starts at pixel
- * view_info[v].first_pixel (P_v = W_v H_v pixels, row-major).  DEVICE buffers:
+ * view_info[v].first_pixel = sum_{u<v} P_u (P_v = W_v H_v pixels, row-major; a
+ * negative width or height counts as 0).  A view whose camera is invalid
+ * (GS_FLAG_BAD_CAMERA) keeps its P_v pixels in this layout but has no tiles:
+ * its pixels are not written.  DEVICE buffers:
  *   rgb   [sum_v 3 P_v]  planar per view: channel c of view v at 3*first_pixel + c*P_v
  *   depth [sum_v P_v]    sum_i w_i t_z,i      (Sec. III, c_i replaced by d_i)
  *   unc   [sum_v P_v]    sum_i w_i u_i        (uncertainty channel)
@@ -290,8 +296,9 @@ gs_status gs_render_bwd(const gs_map* map, const gs_proj* proj, const gs_bins* b
  * process exits.  Inputs and outputs are exactly those of gs_render_bwd (the
  * caller still passes them); no workspace argument; nothing is allocated (no
  * cudaMalloc, no cudaFree, no allocating library call).
- *   - proj->capacity above GS_NOALLOC_MAX_RECORDS is rejected with
- *     GS_ERR_WORKSPACE before anything is enqueued.
+ *   - Every argument is checked exactly as gs_render_bwd checks it (same
+ *     codes); then proj->capacity above GS_NOALLOC_MAX_RECORDS is rejected
+ *     with GS_ERR_WORKSPACE.  Nothing is enqueued on an error.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
@@ -307,6 +314,12 @@ gs_status gs_render_bwd_noalloc(const gs_map* map, const gs_proj* proj, const gs
                                 const gs_params* prm, gs_map_grad* out, void* stream);
 
 /* ------------------------------------------------------- information gain */
+/* The `mode` argument of gs_info_gain_batch and gs_info_gain_composite selects
+ * the score; GS_IG_RENDER_MEAN is the only value accepted (any other returns
+ * GS_ERR_ARG).  The argument is kept for further rendered scores.  The paper's
+ * own render-free score (xi, Eq. view_util) has its own entry point,
+ * gs_view_utility_batch, because it reads the map directly and needs no
+ * records, bins or images. */
 enum { GS_IG_RENDER_MEAN = 0 };
 
 /* gs_info_gain_batch -- Eq. (nbv) with the Jacobian replaced by the per-pixel

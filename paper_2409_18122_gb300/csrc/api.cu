@@ -100,21 +100,42 @@ gs_status check_ws(void* ws, size_t have, size_t need) {
 
 gs_status from_cuda(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
 
-}  // namespace
-}  // namespace gs
-
-using namespace gs;
-
 #define GS_TRY(x)                   \
   do {                              \
     gs_status s__ = (x);            \
     if (s__ != GS_OK) return s__;   \
   } while (0)
 
+}  // namespace
+
+gs_status validate_render_bwd(const gs_map* map, const gs_proj* proj, const gs_bins* bins, const gs_image* fwd,
+                              const gs_image_grad* grad, const gs_camera* cams, int32_t n_views, const gs_params* prm,
+                              const gs_map_grad* out) {
+  GS_TRY(check_map(map));
+  GS_TRY(check_proj(proj));
+  GS_TRY(check_bins(bins));
+  GS_TRY(check_views(cams, n_views));
+  GS_TRY(check_params(prm));
+  if (!fwd || !grad || !out) return GS_ERR_NULL;
+  if (!fwd->T || !fwd->last) return GS_ERR_NULL;
+  if (proj->capacity > 0 && !proj->color_d) return GS_ERR_NULL;
+  if (map->n > 0 && (!out->dmo || !out->dsu || !out->dq || !out->drgb)) return GS_ERR_NULL;
+  if (!aligned(out->dmo, 16) || !aligned(out->dsu, 16) || !aligned(out->dq, 16) || !aligned(out->drgb, 16))
+    return GS_ERR_ALIGN;
+  GS_TRY(check_image(fwd));
+  GS_TRY(check_image_grad(grad));
+  return GS_OK;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
 extern "C" {
 
 gs_status gs_project(const gs_map* map, const gs_camera* cams, int32_t n_views, const gs_params* prm, gs_proj* out,
                      void* ws, size_t ws_bytes, void* stream) {
+  GS_TRACE("gs_project");
   GS_TRY(check_map(map));
   GS_TRY(check_views(cams, n_views));
   GS_TRY(check_params(prm));
@@ -125,6 +146,7 @@ gs_status gs_project(const gs_map* map, const gs_camera* cams, int32_t n_views, 
 
 gs_status gs_bin_sort(const gs_proj* proj, const gs_camera* cams, int32_t n_views, const gs_params* prm,
                       gs_bins* out, void* ws, size_t ws_bytes, void* stream) {
+  GS_TRACE("gs_bin_sort");
   GS_TRY(check_proj(proj));
   GS_TRY(check_views(cams, n_views));
   GS_TRY(check_params(prm));
@@ -135,6 +157,7 @@ gs_status gs_bin_sort(const gs_proj* proj, const gs_camera* cams, int32_t n_view
 
 gs_status gs_render_fwd(const gs_map* map, const gs_proj* proj, const gs_bins* bins, const gs_camera* cams,
                         int32_t n_views, const gs_params* prm, gs_image* out, void* stream) {
+  GS_TRACE("gs_render_fwd");
   GS_TRY(check_map(map));
   GS_TRY(check_proj(proj));
   GS_TRY(check_bins(bins));
@@ -149,19 +172,8 @@ gs_status gs_render_fwd(const gs_map* map, const gs_proj* proj, const gs_bins* b
 gs_status gs_render_bwd(const gs_map* map, const gs_proj* proj, const gs_bins* bins, const gs_image* fwd,
                         const gs_image_grad* grad, const gs_camera* cams, int32_t n_views, const gs_params* prm,
                         gs_map_grad* out, void* ws, size_t ws_bytes, void* stream) {
-  GS_TRY(check_map(map));
-  GS_TRY(check_proj(proj));
-  GS_TRY(check_bins(bins));
-  GS_TRY(check_views(cams, n_views));
-  GS_TRY(check_params(prm));
-  if (!fwd || !grad || !out) return GS_ERR_NULL;
-  if (!fwd->T || !fwd->last) return GS_ERR_NULL;
-  if (proj->capacity > 0 && !proj->color_d) return GS_ERR_NULL;
-  if (map->n > 0 && (!out->dmo || !out->dsu || !out->dq || !out->drgb)) return GS_ERR_NULL;
-  if (!aligned(out->dmo, 16) || !aligned(out->dsu, 16) || !aligned(out->dq, 16) || !aligned(out->drgb, 16))
-    return GS_ERR_ALIGN;
-  GS_TRY(check_image(fwd));
-  GS_TRY(check_image_grad(grad));
+  GS_TRACE("gs_render_bwd");
+  GS_TRY(validate_render_bwd(map, proj, bins, fwd, grad, cams, n_views, prm, out));
   GS_TRY(check_ws(ws, ws_bytes, bwd_ws_bytes(proj->capacity)));
   return from_cuda(
       launch_render_bwd(*map, *proj, *bins, *fwd, *grad, cams, n_views, *prm, *out, ws, (cudaStream_t)stream));
@@ -170,6 +182,7 @@ gs_status gs_render_bwd(const gs_map* map, const gs_proj* proj, const gs_bins* b
 gs_status gs_info_gain_batch(const gs_map* map, const gs_camera* cams, int32_t n_views, const gs_params* prm,
                              int32_t mode, float* ig_out, uint32_t* status, int64_t record_capacity,
                              int64_t pair_capacity, int64_t tile_capacity, void* ws, size_t ws_bytes, void* stream) {
+  GS_TRACE("gs_info_gain_batch");
   GS_TRY(check_map(map));
   GS_TRY(check_views(cams, n_views));
   GS_TRY(check_params(prm));
@@ -189,6 +202,7 @@ gs_status gs_info_gain_batch(const gs_map* map, const gs_camera* cams, int32_t n
 gs_status gs_info_gain_composite(const gs_proj* proj, const gs_bins* bins, const gs_camera* cams, int32_t n_views,
                                  const gs_params* prm, int32_t mode, float* ig_out, void* ws, size_t ws_bytes,
                                  void* stream) {
+  GS_TRACE("gs_info_gain_composite");
   GS_TRY(check_proj(proj));
   GS_TRY(check_bins(bins));
   GS_TRY(check_views(cams, n_views));
@@ -202,6 +216,7 @@ gs_status gs_info_gain_composite(const gs_proj* proj, const gs_bins* bins, const
 
 gs_status gs_uncertainty_update(const float* mo_prev, const float* mo_cur, float* su, int64_t n, int32_t mode,
                                 void* stream) {
+  GS_TRACE("gs_uncertainty_update");
   if (n < 0 || (mode != GS_U_ABS && mode != GS_U_SQ)) return GS_ERR_ARG;
   if (n > 0 && (!mo_prev || !mo_cur || !su)) return GS_ERR_NULL;
   if (!aligned(mo_prev, 16) || !aligned(mo_cur, 16) || !aligned(su, 16)) return GS_ERR_ALIGN;
@@ -210,6 +225,7 @@ gs_status gs_uncertainty_update(const float* mo_prev, const float* mo_cur, float
 
 gs_status gs_uncertainty_thresholds(const gs_map* map, float ground_z, double* stats, void* ws, size_t ws_bytes,
                                     void* stream) {
+  GS_TRACE("gs_uncertainty_thresholds");
   GS_TRY(check_map(map));
   if (!stats) return GS_ERR_NULL;
   if (!aligned(stats, 8)) return GS_ERR_ALIGN;
@@ -221,6 +237,7 @@ gs_status gs_uncertainty_thresholds(const gs_map* map, float ground_z, double* s
 gs_status gs_view_utility_batch(const gs_map* map, const gs_camera* cams, int32_t n_views,
                                 const gs_utility_params* prm, int32_t mode, const double* stats, float* xi_out,
                                 uint32_t* counts_out, void* ws, size_t ws_bytes, void* stream) {
+  GS_TRACE("gs_view_utility_batch");
   GS_TRY(check_map(map));
   GS_TRY(check_views(cams, n_views));
   if (!prm || !xi_out) return GS_ERR_NULL;
@@ -238,6 +255,7 @@ gs_status gs_view_utility_batch(const gs_map* map, const gs_camera* cams, int32_
 gs_status gs_trajectory_utility(const gs_map* map, const gs_camera* cams, int32_t n_traj, int32_t n_states,
                                 const gs_utility_params* prm, int32_t mode, const double* stats, float* traj_out,
                                 int32_t* best_out, void* ws, size_t ws_bytes, void* stream) {
+  GS_TRACE("gs_trajectory_utility");
   GS_TRY(check_map(map));
   if (n_traj < 1 || n_states < 1 || (int64_t)n_traj * n_states > (1 << 20)) return GS_ERR_ARG;
   GS_TRY(check_views(cams, n_traj * n_states));
@@ -256,6 +274,7 @@ gs_status gs_trajectory_utility(const gs_map* map, const gs_camera* cams, int32_
 gs_status gs_collision_check(const gs_map* map, const float* points, int32_t n_points, float r_robot,
                              float lambda_g, float ground_z, float* margin_out, uint32_t* collides_out,
                              void* stream) {
+  GS_TRACE("gs_collision_check");
   GS_TRY(check_map(map));
   if (n_points < 0 || !(r_robot >= 0.f) || !(lambda_g >= 0.f) || ground_z != ground_z) return GS_ERR_ARG;
   if (n_points > 0 && (!points || !margin_out || !collides_out)) return GS_ERR_NULL;
@@ -266,6 +285,7 @@ gs_status gs_collision_check(const gs_map* map, const float* points, int32_t n_p
 
 gs_status gs_region_uncertainty(const gs_map* map, const gs_region_grid* grid, float* omega_out, uint32_t* count_out,
                                 void* ws, size_t ws_bytes, void* stream) {
+  GS_TRACE("gs_region_uncertainty");
   GS_TRY(check_map(map));
   if (!grid || !omega_out) return GS_ERR_NULL;
   if (!(grid->size > 0.f) || grid->dims[0] < 1 || grid->dims[1] < 1 || grid->dims[2] < 1) return GS_ERR_ARG;
@@ -279,6 +299,7 @@ gs_status gs_region_uncertainty(const gs_map* map, const gs_region_grid* grid, f
 gs_status gs_image_loss(const int32_t* sizes, int32_t n_views, const float* rgb, const float* depth,
                         const float* rgb_ref, const float* depth_ref, const gs_loss_weights* w, float* loss_out,
                         float* d_rgb, float* d_depth, void* ws, size_t ws_bytes, void* stream) {
+  GS_TRACE("gs_image_loss");
   if (!sizes || !w || !rgb || !rgb_ref || !loss_out) return GS_ERR_NULL;
   if (n_views < 1) return GS_ERR_ARG;
   const float wt[3] = {w->w_depth, w->w_rgb, w->w_ssim};
@@ -308,6 +329,7 @@ gs_status gs_image_loss_workspace_size(const int32_t* sizes, int32_t n_views, si
 gs_status gs_adam_step(float* const* params, const float* const* grads, float* const* m, float* const* v,
                        const int64_t* sizes, int32_t n_tensors, const gs_adam_params* prm, uint32_t* step,
                        void* stream) {
+  GS_TRACE("gs_adam_step");
   if (!params || !grads || !m || !v || !sizes || !prm || !step) return GS_ERR_NULL;
   if (n_tensors < 1 || n_tensors > GS_ADAM_MAX_TENSORS) return GS_ERR_ARG;
   if (!(prm->lr >= 0.0) || std::isinf(prm->lr) || !(prm->beta1 >= 0.0 && prm->beta1 < 1.0) ||

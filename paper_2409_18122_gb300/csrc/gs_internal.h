@@ -6,9 +6,22 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gs.h"
 
 namespace gs {
+
+// NVTX range over one C-ABI call (host side: argument checks and the enqueue of its
+// kernels), named after the entry point, so that a profiler's timeline shows which call
+// launched which kernels.  With no tool attached a push or pop is one indirect call.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+#define GS_TRACE(name) ::gs::TraceRange gs_trace_range_(name)
 
 // ------------------------------------------------------------------ helpers
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -88,6 +101,11 @@ cudaError_t launch_render_fwd(const gs_map& map, const gs_proj& proj, const gs_b
                               int n_views, const gs_params& p, const gs_image& img, cudaStream_t st);
 
 size_t bwd_ws_bytes(int64_t rec_cap);
+// Every argument check of gs_render_bwd except the workspace's (api.cu); GS_OK if the
+// arguments are valid.  Shared by the workspace and the allocation-free entry points.
+gs_status validate_render_bwd(const gs_map* map, const gs_proj* proj, const gs_bins* bins, const gs_image* fwd,
+                              const gs_image_grad* grad, const gs_camera* cams, int32_t n_views, const gs_params* prm,
+                              const gs_map_grad* out);
 cudaError_t launch_render_bwd(const gs_map& map, const gs_proj& proj, const gs_bins& bins, const gs_image& fwd,
                               const gs_image_grad& g, const gs_camera* cams, int n_views, const gs_params& p,
                               const gs_map_grad& out, void* ws, cudaStream_t st);

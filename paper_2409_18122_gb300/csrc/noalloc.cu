@@ -45,8 +45,6 @@ gs_status scratch_address(void** out) {
   return GS_OK;
 }
 
-bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
-
 }  // namespace
 }  // namespace gs
 
@@ -54,27 +52,11 @@ extern "C" gs_status gs_render_bwd_noalloc(const gs_map* map, const gs_proj* pro
                                            const gs_image* fwd, const gs_image_grad* grad, const gs_camera* cams,
                                            int32_t n_views, const gs_params* prm, gs_map_grad* out, void* stream) {
   using namespace gs;
-  if (!map || !proj || !bins || !fwd || !grad || !cams || !prm || !out) return GS_ERR_NULL;
-  if (map->n < 0 || n_views < 1 || n_views > (1 << 20)) return GS_ERR_ARG;
-  if (proj->capacity < 0 || bins->pair_capacity < 1 || bins->tile_capacity < 1) return GS_ERR_ARG;
-  if (proj->capacity > kMaxRecords) return GS_ERR_WORKSPACE;   // the fixed scratch is too small
-  if (map->n > 0 && (!map->mo || !map->su || !map->q || !map->rgb)) return GS_ERR_NULL;
-  if (!proj->count || !proj->status || !proj->view_info || !proj->grp_mask || !proj->grp_base || !proj->gid ||
-      !proj->view || !proj->splat || !proj->color_d || !bins->count || !bins->rec || !bins->ranges || !fwd->T ||
-      !fwd->last)
-    return GS_ERR_NULL;
-  if (map->n > 0 && (!out->dmo || !out->dsu || !out->dq || !out->drgb)) return GS_ERR_NULL;
-  if (!aligned(map->mo, 16) || !aligned(map->su, 16) || !aligned(map->q, 16) || !aligned(map->rgb, 16) ||
-      !aligned(proj->splat, 32) || !aligned(proj->color_d, 16) ||
-      !aligned(out->dmo, 16) || !aligned(out->dsu, 16) ||
-      !aligned(out->dq, 16) || !aligned(out->drgb, 16) || !aligned(fwd->T, 4) || !aligned(fwd->last, 4) ||
-      !aligned(grad->rgb, 4) || !aligned(grad->depth, 4))
-    return GS_ERR_ALIGN;
-  const int B = prm->tile_w * prm->tile_h;
-  if ((prm->tile_w != 8 && prm->tile_w != 16 && prm->tile_w != 32 && prm->tile_w != 64) || prm->tile_h < 8 ||
-      prm->tile_h % 8 != 0 || (B != 64 && B != 128 && B != 256 && B != 512 && B != 1024) || !(prm->alpha_max > 0.f && prm->alpha_max <= 1.f) ||
-      !(prm->alpha_min >= 0.f && prm->alpha_min < 1.f))
-    return GS_ERR_ARG;
+  GS_TRACE("gs_render_bwd_noalloc");
+  // the same checks as gs_render_bwd, then the bound of the fixed scratch in place of a workspace
+  const gs_status v = validate_render_bwd(map, proj, bins, fwd, grad, cams, n_views, prm, out);
+  if (v != GS_OK) return v;
+  if (proj->capacity > kMaxRecords) return GS_ERR_WORKSPACE;
   void* scratch = nullptr;
   gs_status s = scratch_address(&scratch);
   if (s != GS_OK) return s;
