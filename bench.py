@@ -40,6 +40,7 @@ METRIC = "candidate views/sec (batched info-gain) and fwd+bwd iters/sec at 500k 
 WORKLOAD = ("ig: 1,000,000 room Gaussians, 256 candidates (80x60/160x120/320x240 thirds); "
             "map: 500,000 room Gaussians, 4 keyframes 640x480, fwd+bwd+Adam")
 L2_FLUSH_BYTES = 256 << 20
+IG_INSTR_PER_EVAL = 12.0    # FP32 lane-instructions per contributing evaluation of the U-only compositing
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size k_ig_items launch,
 # from one-pass ncu captures of
@@ -474,6 +475,12 @@ def pipeline_roofline(istep, contributing, t_pass, hbm_gbs, issue_tps):
     return out
 
 
+def compositing_rate(contributing, launch_s):
+    """Achieved rate of the information-gain compositing kernel in T lane-instructions/s:
+    IG_INSTR_PER_EVAL per contributing (pixel, Gaussian) evaluation over one launch's duration."""
+    return IG_INSTR_PER_EVAL * contributing / launch_s / 1e12
+
+
 def at_load_clock(rooflines, sms, load_mhz):
     """Adds to each FP32-issue roofline the issue peak at the median SM clock sampled under
     load (SMs x 128 lanes x MHz) and the fraction of it achieved; no-op without a sample."""
@@ -830,8 +837,12 @@ def run_ours(args):
     peak = sms * 128 * sm_max * 1e6 / 1e12
     peak_src = "derived: %d SMs x 128 FP32 lanes x %.0f MHz (max SM clock); no FP32 peak is measured" % (sms, sm_max)
     # dominant kernel of the step: the information-gain compositing (gs_info_gain_composite);
-    # algorithmic FP32 work = 16 instr per contributing (pixel, Gaussian) evaluation
-    # (alpha: 2 sub, 5 mul/fma, exp, mul, min, compare; accumulate: sub, mul, compare, 2 fma)
+    # algorithmic work = 12 FP32 lane-instructions per contributing (pixel, Gaussian) evaluation
+    # of the U-only compositing (the unit count of the scope's measurement plan): the pixel
+    # offset (2 sub), the quadratic form with the opacity in the exponent (3 fma/mul), ex2,
+    # the clamp, the skip test, w = alpha T, T - w, the stop test and the U accumulation;
+    # contributing evaluations are counted by the forward kernel at the same tiles (its
+    # per-pixel count equals the oracle's in the GPU parity tests)
     t_comp = istep.composite_ms(max(3, args.steps), flush) / 1e3
     ig_contrib, ig_walked = istep.contributing()
     hbm = float(peaks.get("hbm_gbs", 6673.5))
@@ -842,15 +853,16 @@ def run_ours(args):
     collide = collision_timing(torch, gs, scenes)
     eq3 = eq3_map_step(torch, gs, scenes, flush)
     cfg4 = None if args.no_cfg4 else config4_loop(torch, gs, scenes, istep.tile_choice, flush)
-    achieved = 16.0 * ig_contrib / t_comp / 1e12
+    achieved = compositing_rate(ig_contrib, t_comp)
     tiles_now = {"%dx%d" % k: "%dx%d" % v for k, v in istep.tile_choice.items()}
     traffic_src = None
     if IG_TRAFFIC_SHA1 == ig_sources_sha1():
         traffic_src = next((t for t in IG_TRAFFIC if t["tiles"] == tiles_now), None)
     traffic = traffic_src["bytes"] if traffic_src else None
     roofline = {"bound": "alu", "kernel": "k_ig_items (gs_info_gain_composite)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                "launch_ms": t_comp * 1e3, "contributing_evals": ig_contrib,
+                "peak": peak, "unit": "T lane-instr/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_source": peak_src, "launch_ms": t_comp * 1e3, "contributing_evals": ig_contrib,
+                "instr_per_eval": IG_INSTR_PER_EVAL, "list_entries_to_last_contributor": ig_walked,
                 "traffic_note": "dram read + write bytes per launch from a one-pass ncu capture at full size with "
                                 "the same tiles; null when no capture matches the tiles or the kernel sources",
                 "dram_gbs_at_traffic": (traffic / t_comp / 1e9 if traffic else None)}
@@ -858,7 +870,7 @@ def run_ours(args):
     t_bwd = stage_ms.get("gs_render_bwd", float("nan")) / 1e3
     bwd_ach = (10.0 * ws["evaluated"] + 38.0 * ws["contributing"]) / t_bwd / 1e12
     rooflines = [roofline, {"bound": "alu", "kernel": "gs_render_bwd (k_render_bwd + k_proj_adjoint)",
-                            "achieved": bwd_ach, "peak": peak, "unit": "TFLOP/s", "frac": bwd_ach / peak,
+                            "achieved": bwd_ach, "peak": peak, "unit": "T lane-instr/s", "frac": bwd_ach / peak,
                             "launch_ms": t_bwd * 1e3}]
     at_load_clock(rooflines, sms, (clocks or {}).get("sm_mhz"))
 

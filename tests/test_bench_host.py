@@ -58,3 +58,14 @@ def test_issue_peak_at_the_load_clock(bench):
     assert r[0]["frac_at_load_clock"] == pytest.approx(4.0 / (152 * 128 * 2000e6 / 1e12))
     assert "peak_at_load_clock" not in r[1]
     assert bench.at_load_clock(r[1:], 152, None) == r[1:]
+
+
+def test_headline_roofline_reproduces_from_its_fields(bench):
+    """frac = 12 x contributing evaluations / launch time / (SMs x 128 x clock): the line's
+    roofline can be recomputed from launch_ms, contributing_evals and the stated peak."""
+    assert bench.IG_INSTR_PER_EVAL == 12.0
+    contrib, launch_ms = 886_993_606, 3.106
+    ach = bench.compositing_rate(contrib, launch_ms / 1e3)
+    peak = 152 * 128 * 2070e6 / 1e12
+    assert ach == pytest.approx(12 * contrib / (launch_ms / 1e3) / 1e12)
+    assert ach / peak == pytest.approx(0.0851, abs=5e-4)
