@@ -470,8 +470,9 @@ def test_backward_refuses_a_frame_rendered_again():
         for k in total:
             total[k] += g[k]
     torch.cuda.synchronize()
-    for p, k in zip(params, ("dmo", "dsu", "dq", "drgb")):
-        torch.testing.assert_close(p.grad, total[k], rtol=1e-5, atol=1e-7)
+    # float atomics sum in a different order on every call: the gradient tolerance of the suite
+    got = {k: p.grad.cpu().numpy() for p, k in zip(params, ("dmo", "dsu", "dq", "drgb"))}
+    compare_grads(got, {k: v.cpu().numpy().astype(np.float64) for k, v in total.items()}, what="per-frame renders")
 
 
 def test_gradients_full_size_sparse_pixels():
