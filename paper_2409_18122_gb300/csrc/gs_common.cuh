@@ -215,6 +215,26 @@ __device__ __forceinline__ bool frustum_ok(float4 mo, const CamC& c, float near_
   return tz > near_plane && !(fabsf(tx) > fmul(q3.x, tz)) && !(fabsf(ty) > fmul(q3.y, tz));
 }
 
+// Group cull: false only if no centre within `rad` of (gc) can pass frustum_ok for the
+// view.  For a point p with |p - gc| <= rad and t = R^T (p - T): t_z <= t_z(gc) + rad, and
+// its signed distance to each side plane t_x = +-gx t_z (t_y = +-gy t_z) differs from the
+// centre's by at most rad.  `m` covers the rounding of frustum_ok's FP32 evaluation (a few
+// ulp of |p - T|) with a wide margin, so the cull never drops a pair frustum_ok accepts.
+__device__ __forceinline__ bool group_may_meet(const float* gc, float rad, const CamC& c, float near_plane) {
+  const float dx = gc[0] - c.T[0], dy = gc[1] - c.T[1], dz = gc[2] - c.T[2];
+  const float tx = c.R[0] * dx + c.R[3] * dy + c.R[6] * dz;
+  const float ty = c.R[1] * dx + c.R[4] * dy + c.R[7] * dz;
+  const float tz = c.R[2] * dx + c.R[5] * dy + c.R[8] * dz;
+  const float m = 1e-4f * (fabsf(dx) + fabsf(dy) + fabsf(dz) + rad) + 1e-4f;
+  const float r = rad + m;
+  if (tz + r <= near_plane) return false;
+  const float kx = r * sqrtf(1.f + c.gx * c.gx) * 1.0001f;
+  const float ky = r * sqrtf(1.f + c.gy * c.gy) * 1.0001f;
+  if (tx - c.gx * tz > kx || -tx - c.gx * tz > kx) return false;
+  if (ty - c.gy * tz > ky || -ty - c.gy * tz > ky) return false;
+  return true;
+}
+
 __device__ __forceinline__ bool view_proj(float4 mo, const GaussPre& g, const CamC& c, float near_plane,
                                           float eps2d, ViewProj& vp) {
   if (!g.valid) return false;

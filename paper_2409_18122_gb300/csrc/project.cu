@@ -161,6 +161,31 @@ __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera*
   const bool usable = active && pre.valid;
   uint32_t* queue = s_q[warp];
   uint32_t* vmask = s_mask[warp];
+  // count pass: a sphere holding the centres of the group's usable Gaussians, for the group
+  // cull of every view (group_may_meet); its radius carries a margin against rounding
+  float gc[3] = {0.f, 0.f, 0.f}, grad = 0.f;
+  const uint32_t use_mask = __ballot_sync(0xffffffffu, usable);
+  if (!kWrite && use_mask) {
+    float sx = usable ? mo.x : 0.f, sy = usable ? mo.y : 0.f, sz = usable ? mo.z : 0.f;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, d);
+      sy += __shfl_xor_sync(0xffffffffu, sy, d);
+      sz += __shfl_xor_sync(0xffffffffu, sz, d);
+    }
+    const float inv = 1.f / (float)__popc(use_mask);
+    gc[0] = sx * inv;
+    gc[1] = sy * inv;
+    gc[2] = sz * inv;
+    float r2 = 0.f;
+    if (usable) {
+      const float ex = mo.x - gc[0], ey = mo.y - gc[1], ez = mo.z - gc[2];
+      r2 = ex * ex + ey * ey + ez * ez;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, d));
+    grad = sqrtf(r2) * 1.001f + 1e-4f;
+  }
 
   // full projection of up to 32 queued pairs, one per lane
   auto drain = [&](int v0, int count) {
@@ -209,21 +234,36 @@ __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera*
     }
     __syncwarp();
     int qn = 0;   // queued pairs (warp-uniform)
-    for (int i = 0; i < nv; ++i) {
-      bool take;
-      if (kWrite) take = (vmask[i] >> lane) & 1u;
-      else take = usable && s_cam[i].W > 0 && frustum_ok(mo, s_cam[i], p.near_plane);
-      const uint32_t m = __ballot_sync(0xffffffffu, take);
-      if (take) queue[qn + __popc(m & lt)] = ((uint32_t)i << 5) | (uint32_t)lane;
-      qn += __popc(m);
-      __syncwarp();
-      if (qn >= 32) {
-        drain(v0, 32);
-        const uint32_t rest = lane + 32 < qn ? queue[lane + 32] : 0u;
+    // 32 views at a time, one per lane, are first tested for the whole group: in the count
+    // pass a view whose frustum the group's sphere cannot meet is skipped, in the write pass
+    // a view in which none of the group is visible; the lanes then test their own Gaussian
+    // against each remaining view in turn
+    for (int vb = 0; vb < nv; vb += 32) {
+      const int iv = vb + lane;
+      bool cand = false;
+      if (iv < nv) {
+        if (kWrite) cand = vmask[iv] != 0u;
+        else cand = use_mask != 0u && s_cam[iv].W > 0 && group_may_meet(gc, grad, s_cam[iv], p.near_plane);
+      }
+      uint32_t cm = __ballot_sync(0xffffffffu, cand);
+      while (cm) {
+        const int i = vb + __ffs(cm) - 1;
+        cm &= cm - 1u;
+        bool take;
+        if (kWrite) take = (vmask[i] >> lane) & 1u;
+        else take = usable && frustum_ok(mo, s_cam[i], p.near_plane);
+        const uint32_t m = __ballot_sync(0xffffffffu, take);
+        if (take) queue[qn + __popc(m & lt)] = ((uint32_t)i << 5) | (uint32_t)lane;
+        qn += __popc(m);
         __syncwarp();
-        if (lane + 32 < qn) queue[lane] = rest;
-        qn -= 32;
-        __syncwarp();
+        if (qn >= 32) {
+          drain(v0, 32);
+          const uint32_t rest = lane + 32 < qn ? queue[lane + 32] : 0u;
+          __syncwarp();
+          if (lane + 32 < qn) queue[lane] = rest;
+          qn -= 32;
+          __syncwarp();
+        }
       }
     }
     drain(v0, qn);
