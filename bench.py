@@ -90,6 +90,11 @@ def parse():
                     help="'auto' (autotuner) or fixed tiles per resolution, e.g. 80x60=8x8,160x120=16x16")
     ap.add_argument("--ig-views", type=int, default=0, help="score only the first N candidates (0: all 256)")
     ap.add_argument("--no-unbatched", action="store_true", help="skip the one-view-per-call comparison")
+    ap.add_argument("--ig-batch", type=int, default=None,
+                    help="chunk depth of the information-gain compositing (4, 8, 16; default: autotuned "
+                         "with --ig-tiles auto, else 8)")
+    ap.add_argument("--no-map-tune", action="store_true",
+                    help="mapping step at the default tile and depth instead of the autotuner's")
     return ap.parse_args()
 
 
@@ -197,14 +202,17 @@ class MapStep:
     the whole iteration (forward, loss, backward, Adam) is captured once in a CUDA graph and
     replayed; eager() runs it op by op (used for the per-stage breakdown)."""
 
-    def __init__(self, gs, scenes, weights=None, graph=True, scene=None):
+    def __init__(self, gs, scenes, weights=None, graph=True, scene=None, tune=True):
         import torch
         self.torch = torch
         self.gs = gs
         sc = scenes.config2() if scene is None else scene
         self.scene = sc
         gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
-        self.frame = gs.Frame(gm.n, sc.cams, with_pair_tiles=False)
+        # keyframe tile and forward chunk depth picked by the autotuner (timed fwd + bwd passes)
+        self.render_params, self.tune_timings = (gs.autotune_mapping(gm, sc.cams) if tune
+                                                 else (gs.RenderParams(), {}))
+        self.frame = gs.Frame(gm.n, sc.cams, self.render_params, with_pair_tiles=False)
         tgt = gs.GaussianMapTensors.from_numpy(scenes.perturbed(sc.gmap, seed=2002))
         while True:
             self.frame.reset_status()
@@ -278,7 +286,7 @@ class IGStep:
     """
 
     def __init__(self, gs, scenes, graph: bool, tiles=None, n_views: int = 0, scene=None, cams=None,
-                 record_capacity=None, pair_capacity: int = 300_000_000):
+                 record_capacity=None, pair_capacity: int = 300_000_000, batch=None):
         import torch
         self.torch = torch
         self.gs = gs
@@ -294,8 +302,14 @@ class IGStep:
             self.tile_choice = dict(tiles)
         cams = gs.with_tiles(cams, self.tile_choice)
         self.cams = cams
-        self.frame = gs.Frame(self.gm.n, cams, pair_capacity=pair_capacity, with_color=False, with_pair_tiles=False,
-                              record_capacity=record_capacity, with_gid=False)
+        # chunk depth of the compositing: autotuned with the tiles, or given
+        if batch is None and tiles is None:
+            batch, self.batch_timings = gs.autotune_ig_batch(self.gm, cams, pair_capacity=400_000_000)
+        else:
+            self.batch_timings = {}
+        self.params = gs.RenderParams(ig_batch=int(batch or 0))
+        self.frame = gs.Frame(self.gm.n, cams, self.params, pair_capacity=pair_capacity, with_color=False,
+                              with_pair_tiles=False, record_capacity=record_capacity, with_gid=False)
         while True:
             self.frame.reset_status()
             self.frame.project(self.gm)
@@ -632,7 +646,7 @@ def eq3_map_step(torch, gs, scenes, flush, steps=10):
     return out
 
 
-def config4_loop(torch, gs, scenes, tiles, flush, steps=5):
+def config4_loop(torch, gs, scenes, tiles, flush, steps=5, batch=None):
     """The large exploration map (3M Gaussians, 40x40 m): one mapping iteration over 8
     keyframes at 1280x720 (loss as in the 500k step) and one information-gain pass over
     1,024 candidates (160x120 / 320x240 halves, the tiles the autotuner picked for those
@@ -641,7 +655,7 @@ def config4_loop(torch, gs, scenes, tiles, flush, steps=5):
     sc, cands = scenes.config4()
     m = MapStep(gs, scenes, graph=False, scene=sc)
     ig = IGStep(gs, scenes, graph=False, tiles=tiles, scene=sc, cams=cands, record_capacity=400_000_000,
-                pair_capacity=1_500_000_000)
+                pair_capacity=1_500_000_000, batch=batch)
     try:
         ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(3)]
     except TypeError:
@@ -679,7 +693,9 @@ def config4_loop(torch, gs, scenes, tiles, flush, steps=5):
            "ig": {"value": len(cands) / (ms_ig / 1e3), "unit": "views/s", "ms": ms_ig},
            "ig_records": int(fr.rec_count.item()), "ig_pairs": int(fr.pair_count.item()) & 0xFFFFFFFF,
            "map_pairs": int(m.frame.pair_count.item()) & 0xFFFFFFFF,
-           "ig_tiles": {"%dx%d" % k: "%dx%d" % v for k, v in ig.tile_choice.items()}}
+           "ig_tiles": {"%dx%d" % k: "%dx%d" % v for k, v in ig.tile_choice.items()},
+           "ig_batch": ig.params.ig_batch, "map_tile": "%dx%d" % (m.render_params.tile_w, m.render_params.tile_h),
+           "map_fwd_batch": m.render_params.fwd_batch}
     del g, m, ig, fr
     torch.cuda.empty_cache()
     return out
@@ -758,9 +774,9 @@ def run_ours(args):
 
     rank, world, local = dist_setup()
     torch.backends.cuda.matmul.allow_tf32 = False
-    mstep = MapStep(gs, scenes) if args.part in ("both", "map") else None
-    istep = (IGStep(gs, scenes, graph=bool(args.graph), tiles=parse_tiles(args.ig_tiles), n_views=args.ig_views)
-             if args.part in ("both", "ig") else None)
+    mstep = MapStep(gs, scenes, tune=not args.no_map_tune) if args.part in ("both", "map") else None
+    istep = (IGStep(gs, scenes, graph=bool(args.graph), tiles=parse_tiles(args.ig_tiles), n_views=args.ig_views,
+                    batch=args.ig_batch) if args.part in ("both", "ig") else None)
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     flush = lambda: flush_buf.fill_(1.0)
     parts = [(n, f) for n, f in (("map", mstep), ("ig", istep)) if f is not None]
@@ -822,7 +838,14 @@ def run_ours(args):
             print(json.dumps({"part": args.part, "steps": args.steps, "ms_per_step": ms_per_step,
                               "value": value, "fwd_bwd": fwd_bwd, "stages_ms": stage_ms, "clocks": clocks,
                               "ig_tiles": ({"%dx%d" % k: "%dx%d" % v for k, v in istep.tile_choice.items()}
-                                           if istep else None)}))
+                                           if istep else None),
+                              "ig_batch": istep.params.ig_batch if istep else None,
+                              "ig_batch_ms": ({str(k): v for k, v in istep.batch_timings.items()} if istep else None),
+                              "map_params": ({"tile": "%dx%d" % (mstep.render_params.tile_w,
+                                                                         mstep.render_params.tile_h),
+                                              "fwd_batch": mstep.render_params.fwd_batch,
+                                              "timings_ms": {"%dx%d/%d" % k: v for k, v in mstep.tune_timings.items()}}
+                                             if mstep else None)}))
         return
 
     ws = work_stats(torch, gs, mstep)
@@ -852,7 +875,8 @@ def run_ours(args):
     xi_free = render_free_xi(torch, gs, istep, flush)
     collide = collision_timing(torch, gs, scenes)
     eq3 = eq3_map_step(torch, gs, scenes, flush)
-    cfg4 = None if args.no_cfg4 else config4_loop(torch, gs, scenes, istep.tile_choice, flush)
+    cfg4 = None if args.no_cfg4 else config4_loop(torch, gs, scenes, istep.tile_choice, flush,
+                                                  batch=istep.params.ig_batch)
     achieved = compositing_rate(ig_contrib, t_comp)
     tiles_now = {"%dx%d" % k: "%dx%d" % v for k, v in istep.tile_choice.items()}
     traffic_src = None
@@ -903,7 +927,12 @@ def run_ours(args):
                        "l2": "flushed (256 MB write) before every timed part", "parallelism": "replicas" if world > 1
                        else "single GPU", "ig_cuda_graph": istep.graph is not None,
                        "map_cuda_graph": mstep.graph is not None,
-                       "ig_tiles": {"%dx%d" % k: "%dx%d" % v for k, v in istep.tile_choice.items()}},
+                       "ig_tiles": {"%dx%d" % k: "%dx%d" % v for k, v in istep.tile_choice.items()},
+                       "ig_batch": istep.params.ig_batch,
+                       "map_tile": "%dx%d" % (mstep.render_params.tile_w, mstep.render_params.tile_h),
+                       "map_fwd_batch": mstep.render_params.fwd_batch},
+            "autotune": {"ig_batch_ms": {str(k): v for k, v in istep.batch_timings.items()},
+                         "map_ms": {"%dx%d/%d" % k: v for k, v in mstep.tune_timings.items()}},
             "fwd_bwd": {"value": fwd_bwd, "unit": "iters/s", "ms": t_map_all / args.steps * 1e3},
             "ig_ms": t_ig_all / args.steps * 1e3,
             "ig_unbatched": unbatched,

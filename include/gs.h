@@ -100,19 +100,26 @@ typedef struct {
   int64_t n;
 } gs_map;
 
-/* Rendering constants (readings where the paper is silent).
+/* Rendering constants (readings where the paper is silent) and two choices of the
+ * compositing loops that change speed, never results.
  *   tile_w, tile_h  screen tile in pixels: tile_w in {8, 16, 32, 64}, tile_h a multiple of 8,
- *                   tile_w * tile_h in {64, 128, 256, 512, 1024} (one warp per 8x8 pixel block)
+ *                   tile_w * tile_h in {64, 128, 256, 512, 1024} (one warp per 8x4 pixel block)
  *   eps2d           added to the diagonal of every 2D covariance (low-pass), px^2, >= 0
  *   near_plane      Gaussians with view depth <= near_plane are culled, > 0
  *   guard           centres with |t_x / t_z| > guard * (W/2) / f_x (same for y) are culled, > 0
  *   alpha_min       a Gaussian whose alpha at a pixel is below this is skipped, in [0, 1)
  *   alpha_max       alpha = min(alpha_max, o * exp(-q/2)), in (0, 1]
  *   T_min           compositing stops before adding a Gaussian that would take T below this, >= 0
- * Defaults: 16, 16, 0.3, 0.2, 1.3, 1/255, 0.99, 1e-4. */
+ *   ig_batch        chunk depth of the information-gain compositing: how many of a warp's
+ *                   staged list entries have their alphas evaluated together before the
+ *                   transmittance updates run through them in list order; 4, 8 or 16 (0: 8)
+ *   fwd_batch       the same for gs_render_fwd: 1, 2 or 4 (0: 2)
+ * The outputs are bit for bit the same for every ig_batch and fwd_batch.
+ * Defaults: 16, 16, 0.3, 0.2, 1.3, 1/255, 0.99, 1e-4, 0, 0. */
 typedef struct {
   int32_t tile_w, tile_h;
   float eps2d, near_plane, guard, alpha_min, alpha_max, T_min;
+  int32_t ig_batch, fwd_batch;
 } gs_params;
 
 /* ------------------------------------------------------------- projection */

@@ -43,7 +43,8 @@ class gs_map(ctypes.Structure):
 
 class gs_params(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("eps2d", c_float), ("near_plane", c_float),
-                ("guard", c_float), ("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float)]
+                ("guard", c_float), ("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float),
+                ("ig_batch", c_int32), ("fwd_batch", c_int32)]
 
 
 class gs_proj(ctypes.Structure):
@@ -91,7 +92,7 @@ class gs_map_grad(ctypes.Structure):
 
 
 assert ctypes.sizeof(gs_camera) == 80
-assert ctypes.sizeof(gs_params) == 32
+assert ctypes.sizeof(gs_params) == 40
 
 # name -> (restype, argtypes); the exported C ABI
 PROTOTYPES = {

@@ -39,6 +39,8 @@ gs_status check_params(const gs_params* p) {
   if (!(p->alpha_min >= 0.f && p->alpha_min < 1.f)) return GS_ERR_ARG;
   if (!(p->alpha_max > 0.f && p->alpha_max <= 1.f)) return GS_ERR_ARG;
   if (!(p->T_min >= 0.f && p->T_min < 1.f)) return GS_ERR_ARG;
+  if (p->ig_batch != 0 && p->ig_batch != 4 && p->ig_batch != 8 && p->ig_batch != 16) return GS_ERR_ARG;
+  if (p->fwd_batch != 0 && p->fwd_batch != 1 && p->fwd_batch != 2 && p->fwd_batch != 4) return GS_ERR_ARG;
   return GS_OK;
 }
 

@@ -21,8 +21,11 @@ namespace {
 constexpr int kFwdWarps = 2;   // warps (work items) per CTA: small CTAs free their slot as soon as both finish
 constexpr int kIgWarps = 8;    // warps per CTA of the persistent information-gain kernel
 constexpr int kPix = 1;        // pixels per lane of the forward and information-gain kernels
-constexpr int kFwdBatch = 2;   // overlapping entries whose alphas are computed together (forward)
-constexpr int kIgBatch = 8;    // ... and in the information-gain kernel
+// Chunk depth: overlapping entries whose alphas are computed together, a template argument
+// of both compositing kernels chosen per launch by gs_params (forward 1, 2 or 4, default 2;
+// information gain 4, 8 or 16, default 8)
+constexpr int kFwdBatchDefault = 2;
+constexpr int kIgBatchDefault = 8;
 
 // The list walk of all compositing kernels is a four-stage software pipeline
 // over groups of 32 entries (one per lane).  While group g is composited, the
@@ -32,6 +35,7 @@ constexpr int kIgBatch = 8;    // ... and in the information-gain kernel
 // indices of group g+96.  Every fetch is issued one iteration before it is
 // used and none depends on a value loaded in the same iteration.
 
+template <int kFwdBatch>
 __global__ void __launch_bounds__(kFwdWarps * 32, 12) k_render_fwd(gs_map map, gs_proj proj, gs_bins bins,
                                                                 const gs_camera* __restrict__ cams, int n_views,
                                                                 gs_params p, gs_image img, uint32_t n_items) {
@@ -178,6 +182,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 12) k_render_fwd(gs_map map, g
 // from a device counter, longest tile list first, until the batch is exhausted,
 // and writes the sum of U over its pixels to the item's own slot (fixed shuffle
 // tree), never accumulating, so the result does not depend on scheduling.
+template <int kIgBatch>
 __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bins bins,
                                                              const gs_camera* __restrict__ cams, int n_views,
                                                              gs_params p, const uint32_t* __restrict__ order,
@@ -342,14 +347,38 @@ __global__ void k_item_cost(const gs_proj proj, const gs_bins bins, int n_views,
   }
 }
 
+// The persistent compositing kernel at one chunk depth: one CTA per resident slot.
+template <int kB>
+cudaError_t launch_ig_items(const gs_proj& proj, const gs_bins& bins, const gs_camera* cams, int n_views,
+                            const gs_params& p, const uint32_t* order, float* item_sum, int64_t item_cap,
+                            uint32_t* work, cudaStream_t st) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ig_items<kB>, kIgWarps * 32, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)device_sm_count() * per_sm;
+  if (grid * kIgWarps > item_cap) grid = (item_cap + kIgWarps - 1) / kIgWarps;
+  if (grid < 1) grid = 1;
+  k_ig_items<kB><<<(unsigned)grid, kIgWarps * 32, 0, st>>>(proj, bins, cams, n_views, p, order, item_sum, item_cap,
+                                                           work);
+  note_launch();
+  return cudaSuccess;
+}
+
 }  // namespace
 
 cudaError_t launch_render_fwd(const gs_map& map, const gs_proj& proj, const gs_bins& bins, const gs_camera* cams,
                               int n_views, const gs_params& p, const gs_image& img, cudaStream_t st) {
   const int64_t items = bins.tile_capacity * (32 / kPix);   // upper bound: at most 32 items per tile
   if (items > 0) {
-    k_render_fwd<<<(unsigned)((items + kFwdWarps - 1) / kFwdWarps), kFwdWarps * 32, 0, st>>>(
-        map, proj, bins, cams, n_views, p, img, (uint32_t)items);
+    const unsigned grid = (unsigned)((items + kFwdWarps - 1) / kFwdWarps);
+    const int b = p.fwd_batch ? p.fwd_batch : kFwdBatchDefault;
+    if (b == 1)
+      k_render_fwd<1><<<grid, kFwdWarps * 32, 0, st>>>(map, proj, bins, cams, n_views, p, img, (uint32_t)items);
+    else if (b == 4)
+      k_render_fwd<4><<<grid, kFwdWarps * 32, 0, st>>>(map, proj, bins, cams, n_views, p, img, (uint32_t)items);
+    else
+      k_render_fwd<2><<<grid, kFwdWarps * 32, 0, st>>>(map, proj, bins, cams, n_views, p, img, (uint32_t)items);
     note_launch();
   }
   return cudaGetLastError();
@@ -414,16 +443,11 @@ cudaError_t launch_ig_composite(const gs_proj& proj, const gs_bins& bins, const 
                              proj.view_info + kVI * n_views + 2, item_cap, 0, 16, otmp, st, &in_a);
   if (e != cudaSuccess) return e;
   const uint32_t* order = in_a ? ov_a : ov_b;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ig_items, kIgWarps * 32, 0);
+  const int b = p.ig_batch ? p.ig_batch : kIgBatchDefault;
+  e = b == 4 ? launch_ig_items<4>(proj, bins, cams, n_views, p, order, item_sum, item_cap, work, st)
+    : b == 16 ? launch_ig_items<16>(proj, bins, cams, n_views, p, order, item_sum, item_cap, work, st)
+              : launch_ig_items<8>(proj, bins, cams, n_views, p, order, item_sum, item_cap, work, st);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)device_sm_count() * per_sm;
-  if (grid * kIgWarps > item_cap) grid = (item_cap + kIgWarps - 1) / kIgWarps;
-  if (grid < 1) grid = 1;
-  k_ig_items<<<(unsigned)grid, kIgWarps * 32, 0, st>>>(proj, bins, cams, n_views, p, order, item_sum, item_cap,
-                                                       work);
-  note_launch();
   k_ig_views<<<n_views, 256, 0, st>>>(proj.view_info, cams, n_views, item_sum, item_cap, ig_out);
   note_launch();
   return cudaGetLastError();

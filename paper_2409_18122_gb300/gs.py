@@ -33,10 +33,12 @@ class RenderParams:
     alpha_min: float = 1.0 / 255.0
     alpha_max: float = 0.99
     T_min: float = 1e-4
+    ig_batch: int = 0      # chunk depth of the information-gain compositing: 4, 8 or 16 (0: 8)
+    fwd_batch: int = 0     # chunk depth of the forward compositing: 1, 2 or 4 (0: 2)
 
     def c(self) -> L.gs_params:
         return L.gs_params(self.tile_w, self.tile_h, self.eps2d, self.near, self.guard, self.alpha_min,
-                           self.alpha_max, self.T_min)
+                           self.alpha_max, self.T_min, self.ig_batch, self.fwd_batch)
 
 
 class StageTimer:
@@ -748,6 +750,88 @@ def autotune_tiles(gmap: GaussianMapTensors, cams: Sequence, params: RenderParam
             del ig
         choice[res] = min(timings[res], key=timings[res].get)
     return choice, timings
+
+
+IG_BATCH_CANDIDATES = (4, 8, 16)     # RenderParams.ig_batch
+FWD_BATCH_CANDIDATES = (1, 2, 4)     # RenderParams.fwd_batch
+
+
+def _best_ms(fn, reps: int) -> float:
+    """Best device time of `fn` over `reps` calls (CUDA events on the current stream), after one warm-up."""
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def autotune_ig_batch(gmap: GaussianMapTensors, cams: Sequence, params: RenderParams = RenderParams(),
+                      candidates=IG_BATCH_CANDIDATES, reps: int = 3, pair_capacity: Optional[int] = None):
+    """Pick the chunk depth of the information-gain compositing (RenderParams.ig_batch) by timing
+    the batched pass over `cams` (with their own tiles, e.g. from autotune_tiles) at each
+    candidate; the scores are the same for every depth.  Returns (depth, {depth: ms})."""
+    from dataclasses import replace
+    timings = {}
+    for b in candidates:
+        ig = InfoGain(gmap.n, cams, replace(params, ig_batch=int(b)), pair_capacity=pair_capacity)
+        ig(gmap)
+        torch.cuda.synchronize()
+        while ig.grow_if_needed():
+            ig(gmap)
+            torch.cuda.synchronize()
+        timings[int(b)] = _best_ms(lambda: ig(gmap), reps)
+        del ig
+    torch.cuda.empty_cache()
+    return min(timings, key=timings.get), timings
+
+
+def autotune_mapping(gmap: GaussianMapTensors, cams: Sequence, params: RenderParams = RenderParams(),
+                     tiles=TILE_CANDIDATES, batches=FWD_BATCH_CANDIDATES, reps: int = 3):
+    """Pick the keyframes' tile (RenderParams.tile_w, tile_h) and the forward chunk depth
+    (RenderParams.fwd_batch) of a mapping step by timing one forward and backward pass of the
+    map through all `cams` (unit image gradients): the tile first at the default depth, then
+    the depth at that tile.  Returns (params, {(tile_w, tile_h, fwd_batch): ms})."""
+    from dataclasses import replace
+    timings = {}
+
+    def time_step(prm):
+        fr = Frame(gmap.n, cams, prm, with_pair_tiles=False)
+        img = fr.forward(gmap)
+        torch.cuda.synchronize()
+        while fr.grow_if_needed():
+            img = fr.forward(gmap)
+            torch.cuda.synchronize()
+        d_rgb, d_dep = torch.ones_like(img["rgb"]), torch.ones_like(img["depth"])
+        grads = {k: torch.empty((gmap.n, 4), dtype=torch.float32, device=fr.device) for k in ("dmo", "dsu", "dq", "drgb")}
+
+        def step():
+            fr.forward(gmap, img)
+            fr.render_bwd(gmap, img, d_rgb, d_dep, grads)
+
+        ms = _best_ms(step, reps)
+        del fr, img, grads
+        return ms
+
+    for tw, th in tiles:
+        if not valid_tile(tw, th):
+            continue
+        prm = replace(params, tile_w=int(tw), tile_h=int(th))
+        timings[(int(tw), int(th), prm.fwd_batch)] = time_step(prm)
+    tw, th, _ = min(timings, key=timings.get)
+    for b in batches:
+        prm = replace(params, tile_w=tw, tile_h=th, fwd_batch=int(b))
+        key = (tw, th, int(b))
+        if key not in timings:
+            timings[key] = time_step(prm)
+    best = min((k for k in timings if k[:2] == (tw, th)), key=timings.get)
+    torch.cuda.empty_cache()
+    return replace(params, tile_w=best[0], tile_h=best[1], fwd_batch=best[2]), timings
 
 
 def with_tiles(cams: Sequence, choice) -> list:

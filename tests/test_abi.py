@@ -91,7 +91,8 @@ def test_workspace_sizes(lib):
 
 
 def _params(**kw):
-    d = dict(tile_w=16, tile_h=16, eps2d=0.3, near_plane=0.2, guard=1.3, alpha_min=1 / 255, alpha_max=0.99, T_min=1e-4)
+    d = dict(tile_w=16, tile_h=16, eps2d=0.3, near_plane=0.2, guard=1.3, alpha_min=1 / 255, alpha_max=0.99, T_min=1e-4,
+             ig_batch=0, fwd_batch=0)
     d.update(kw)
     return L.gs_params(*d.values())
 
@@ -113,7 +114,8 @@ def test_host_side_argument_errors(lib):
     assert lib.gs_project(P(neg), fake, 1, P(prm), P(proj), fake, 1 << 20, None) == L.GS_ERR_ARG
     # bad parameters
     for bad in (_params(tile_w=10), _params(tile_w=128, tile_h=2), _params(tile_w=16, tile_h=6), _params(tile_w=4, tile_h=16), _params(tile_w=16, tile_h=4), _params(near_plane=0.0), _params(alpha_max=0.0),
-                _params(alpha_min=1.0), _params(eps2d=-1.0), _params(T_min=1.0), _params(guard=float("nan"))):
+                _params(alpha_min=1.0), _params(eps2d=-1.0), _params(T_min=1.0), _params(guard=float("nan")),
+                _params(ig_batch=3), _params(ig_batch=32), _params(fwd_batch=8), _params(fwd_batch=-1)):
         assert lib.gs_project(P(m), fake, 1, P(bad), P(proj), fake, 1 << 20, None) == L.GS_ERR_ARG
     # misaligned map pointer
     mis = L.gs_map(ctypes.c_void_p(0x10004), fake, fake, fake, 10)

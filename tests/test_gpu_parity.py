@@ -265,6 +265,46 @@ def test_tile_shape_invariance_bitwise():
             np.testing.assert_array_equal(o[k], outs[0][k])
 
 
+def test_chunk_depth_does_not_change_results():
+    """The compositing chunk depths the autotuner chooses from (gs_params ig_batch, fwd_batch)
+    change speed only: information gain and forward images are bit for bit the same."""
+    gmap, cams = _ig_scene()
+    gm = gs.GaussianMapTensors.from_numpy(gmap)
+    cams = gs.with_tiles(cams, CONFIG3_TILES)
+    igs = [gs.InfoGain(gm.n, cams, gs.RenderParams(ig_batch=b))(gm).cpu().numpy() for b in gs.IG_BATCH_CANDIDATES]
+    for o in igs[1:]:
+        np.testing.assert_array_equal(o, igs[0])
+    sc = scenes.config2(n=20_000, n_views=2)
+    outs = []
+    for b in gs.FWD_BATCH_CANDIDATES:
+        fr, _, img = run_forward(sc.gmap, sc.cams, gs.RenderParams(fwd_batch=b))
+        outs.append({k: v.cpu().numpy() for k, v in img.items() if v is not None})
+    for o in outs[1:]:
+        for k in ("rgb", "depth", "unc", "T", "last"):
+            np.testing.assert_array_equal(o[k], outs[0][k])
+
+
+def test_autotuners_pick_valid_choices():
+    """The tile / chunk-depth autotuners return choices from their candidate sets and timings
+    for each; rendering with the mapping autotuner's choice gives the oracle's images."""
+    gmap, cams = _ig_scene(8000, 2)
+    gm = gs.GaussianMapTensors.from_numpy(gmap)
+    tiles, tt = gs.autotune_tiles(gm, cams, reps=1)
+    assert all(t in gs.TILE_CANDIDATES for t in tiles.values()) and set(tiles) == {(c.width, c.height) for c in cams}
+    b, bt = gs.autotune_ig_batch(gm, gs.with_tiles(cams, tiles), reps=1)
+    assert b in gs.IG_BATCH_CANDIDATES and set(bt) == set(gs.IG_BATCH_CANDIDATES)
+    sc = scenes.config2(n=20_000, n_views=2)
+    gm2 = gs.GaussianMapTensors.from_numpy(sc.gmap)
+    prm, mt = gs.autotune_mapping(gm2, [c.crop(200, 150, 160, 120) for c in sc.cams], reps=1)
+    assert (prm.tile_w, prm.tile_h) in gs.TILE_CANDIDATES and prm.fwd_batch in gs.FWD_BATCH_CANDIDATES
+    assert (prm.tile_w, prm.tile_h, prm.fwd_batch) in mt
+    cams2 = [c.crop(200, 150, 160, 120) for c in sc.cams]
+    fr, _, img = run_forward(sc.gmap, cams2, prm)
+    ref = O.render_images(sc.gmap, cams2, oparams(prm))
+    for v, h in enumerate(images_host(fr, img)):
+        compare_image(h, ref[v], "view %d" % v)
+
+
 def test_input_permutation_invariance():
     """Distinct depths: permuting the Gaussians does not change the image (bitwise)."""
     sc = scenes.config0()
