@@ -719,7 +719,8 @@ def autotune_tiles(gmap: GaussianMapTensors, cams: Sequence, params: RenderParam
 
     For every distinct (width, height) among `cams`, the views of that class are
     scored with each candidate tile size (CUDA events, best of `reps` after one
-    warm-up) and the fastest is kept.  Returns ({(W, H): (tile_w, tile_h)},
+    warm-up, L2 flushed before each) and the fastest is kept, unless the default
+    tile of `params` is within TUNE_MARGIN of it.  Returns ({(W, H): (tile_w, tile_h)},
     {(W, H): {tile: ms}}).  Use `with_tiles` to apply the choice to a camera list.
     """
     classes = {}
@@ -738,17 +739,9 @@ def autotune_tiles(gmap: GaussianMapTensors, cams: Sequence, params: RenderParam
             while ig.grow_if_needed():
                 ig(gmap)
                 torch.cuda.synchronize()
-            best = float("inf")
-            for _ in range(reps):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                ig(gmap)
-                e1.record()
-                torch.cuda.synchronize()
-                best = min(best, e0.elapsed_time(e1))
-            timings[res][(tw, th)] = best
+            timings[res][(tw, th)] = _best_ms(lambda: ig(gmap), reps)
             del ig
-        choice[res] = min(timings[res], key=timings[res].get)
+        choice[res] = _pick(timings[res], (params.tile_w, params.tile_h))
     return choice, timings
 
 
@@ -756,23 +749,39 @@ IG_BATCH_CANDIDATES = (4, 8, 16)     # RenderParams.ig_batch
 FWD_BATCH_CANDIDATES = (1, 2, 4)     # RenderParams.fwd_batch
 
 
+L2_FLUSH_BYTES = 256 << 20     # more than the GPU's L2: written between timed calls of the autotuners
+TUNE_MARGIN = 0.01             # a candidate replaces the default only if it is faster by more than this
+
+
 def _best_ms(fn, reps: int) -> float:
-    """Best device time of `fn` over `reps` calls (CUDA events on the current stream), after one warm-up."""
+    """Best device time of `fn` over `reps` calls (CUDA events on the current stream), after one
+    warm-up, with the L2 cache flushed before every timed call (as the steps it tunes run)."""
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     fn()
     torch.cuda.synchronize()
     best = float("inf")
     for _ in range(reps):
+        flush.fill_(1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         fn()
         e1.record()
         torch.cuda.synchronize()
         best = min(best, e0.elapsed_time(e1))
+    del flush
+    return best
+
+
+def _pick(timings, default):
+    """The fastest key, unless the default (when timed) is within TUNE_MARGIN of it."""
+    best = min(timings, key=timings.get)
+    if default in timings and timings[default] <= timings[best] * (1.0 + TUNE_MARGIN):
+        return default
     return best
 
 
 def autotune_ig_batch(gmap: GaussianMapTensors, cams: Sequence, params: RenderParams = RenderParams(),
-                      candidates=IG_BATCH_CANDIDATES, reps: int = 3, pair_capacity: Optional[int] = None):
+                      candidates=IG_BATCH_CANDIDATES, reps: int = 5, pair_capacity: Optional[int] = None):
     """Pick the chunk depth of the information-gain compositing (RenderParams.ig_batch) by timing
     the batched pass over `cams` (with their own tiles, e.g. from autotune_tiles) at each
     candidate; the scores are the same for every depth.  Returns (depth, {depth: ms})."""
@@ -788,11 +797,11 @@ def autotune_ig_batch(gmap: GaussianMapTensors, cams: Sequence, params: RenderPa
         timings[int(b)] = _best_ms(lambda: ig(gmap), reps)
         del ig
     torch.cuda.empty_cache()
-    return min(timings, key=timings.get), timings
+    return _pick(timings, 8), timings
 
 
 def autotune_mapping(gmap: GaussianMapTensors, cams: Sequence, params: RenderParams = RenderParams(),
-                     tiles=TILE_CANDIDATES, batches=FWD_BATCH_CANDIDATES, reps: int = 3):
+                     tiles=TILE_CANDIDATES, batches=FWD_BATCH_CANDIDATES, reps: int = 5):
     """Pick the keyframes' tile (RenderParams.tile_w, tile_h) and the forward chunk depth
     (RenderParams.fwd_batch) of a mapping step by timing one forward and backward pass of the
     map through all `cams` (unit image gradients): the tile first at the default depth, then
@@ -818,18 +827,19 @@ def autotune_mapping(gmap: GaussianMapTensors, cams: Sequence, params: RenderPar
         del fr, img, grads
         return ms
 
+    d_batch = params.fwd_batch or 2
     for tw, th in tiles:
         if not valid_tile(tw, th):
             continue
-        prm = replace(params, tile_w=int(tw), tile_h=int(th))
-        timings[(int(tw), int(th), prm.fwd_batch)] = time_step(prm)
-    tw, th, _ = min(timings, key=timings.get)
+        prm = replace(params, tile_w=int(tw), tile_h=int(th), fwd_batch=d_batch)
+        timings[(int(tw), int(th), d_batch)] = time_step(prm)
+    tw, th, _ = _pick(timings, (params.tile_w, params.tile_h, d_batch))
     for b in batches:
         prm = replace(params, tile_w=tw, tile_h=th, fwd_batch=int(b))
         key = (tw, th, int(b))
         if key not in timings:
             timings[key] = time_step(prm)
-    best = min((k for k in timings if k[:2] == (tw, th)), key=timings.get)
+    best = _pick({k: v for k, v in timings.items() if k[:2] == (tw, th)}, (tw, th, d_batch))
     torch.cuda.empty_cache()
     return replace(params, tile_w=best[0], tile_h=best[1], fwd_batch=best[2]), timings
 
