@@ -132,11 +132,14 @@ typedef struct {
  *   count      [1]        number of records written
  *   status     [1]        device status word (GS_FLAG_* bits), OR-ed by every call
  *   view_info  [V+1][4]   per view: (first global tile, first pixel, first warp item,
- *                         tile_w | tile_h << 8 | tiles_x << 16); entry V holds the totals.
+ *                         tile_w | tile_h << 8 | tiles_x << 16); entry V holds the totals
+ *                         of the first three and, in its fourth field, G (below).
  *                         A warp item is one 8x4 pixel block of a tile: view v has
  *                         tiles(v) * tile_w * tile_h / 32 of them.
- *   gid, view  [cap]      Gaussian index and view index of the record (gid may be NULL: not
- *                         written; the library itself never reads it)
+ *   gid, view  [cap]      Gaussian index and view index of the record.  gid may be NULL (not
+ *                         written; the library itself never reads it).  view may be NULL
+ *                         (not written): gs_bin_sort then finds each view's records through
+ *                         grp_base and G, which holds only for records written by gs_project.
  *   splat      [cap][8]   32 bytes per record, everything compositing reads:
  *                         (mu_2D x, mu_2D y, ext, u, a, b, c, o) -- u the uncertainty of the
  *                         Gaussian, (a, b, c) the inverse 2D covariance with
@@ -212,6 +215,9 @@ typedef struct {
  * Input: records grouped by view in increasing view order (as gs_project
  * writes them), rectangles inside their view's tile grid; other input sets
  * GS_FLAG_BAD_RECORDS and leaves the output unspecified (but in bounds).
+ * Records without view ids (proj->view NULL) must be those gs_project wrote with
+ * this proj's view table, group masks and offsets: each view's first record is then
+ * read from grp_base (no check of the record order).
  * Implementation: stable LSD radix sort of the record indices by depth bits and
  * then by view; per-view chunks count their pairs per tile; one exclusive scan
  * over (tile, chunk) gives every tile's range and every chunk's first slot in

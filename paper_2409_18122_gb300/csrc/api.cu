@@ -64,7 +64,7 @@ gs_status check_proj(const gs_proj* p) {
   if (!p) return GS_ERR_NULL;
   if (p->capacity < 0 || p->capacity >= ((int64_t)1 << 32) - 1) return GS_ERR_ARG;
   if (!p->count || !p->status || !p->view_info || !p->grp_mask || !p->grp_base) return GS_ERR_NULL;
-  if (p->capacity > 0 && (!p->view || !p->splat || !p->rect || !p->depth_key)) return GS_ERR_NULL;
+  if (p->capacity > 0 && (!p->splat || !p->rect || !p->depth_key)) return GS_ERR_NULL;   // view may be NULL
   if (!aligned(p->splat, 32) || !aligned(p->color_d, 16) || !aligned(p->rect, 8) || !aligned(p->gid, 4) ||
       !aligned(p->view, 4) || !aligned(p->depth_key, 4) || !aligned(p->count, 4) || !aligned(p->status, 4) ||
       !aligned(p->view_info, 4) || !aligned(p->grp_mask, 4) || !aligned(p->grp_base, 4))

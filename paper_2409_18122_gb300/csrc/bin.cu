@@ -119,6 +119,26 @@ __global__ void k_segments(const gs_proj proj, int n_views, int64_t tile_cap, in
   }
 }
 
+// seg[v] from the projection's group offsets, for records written by gs_project without
+// per-record view ids: view v's records start at grp_base[v * G] (clipped to the record
+// count), G = the number of 32-Gaussian groups, which gs_project leaves in
+// view_info[V][3]; seg[V] = the record count.
+__global__ void k_segments_from_groups(const gs_proj proj, int n_views, int64_t tile_cap, int K,
+                                       uint32_t* __restrict__ seg, uint32_t* __restrict__ scan_n) {
+  const int64_t n = clamp_count(proj.count, proj.capacity);
+  const int64_t n_grp = proj.view_info[kVI * n_views + 3];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int64_t tiles = proj.view_info[kVI * n_views];
+    if (tiles > tile_cap) tiles = tile_cap;
+    *scan_n = (uint32_t)(tiles * K);
+  }
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n_views;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = v < n_views ? (int64_t)proj.grp_base[v * n_grp] : n;
+    seg[v] = (uint32_t)(b < n ? b : n);
+  }
+}
+
 // Chunk (v, k): the sorted records [r0, r1) of view v whose first pair (as
 // numbered in step 3) lies in [P_v k / K, P_v (k+1) / K) of the view's P_v pairs,
 // so every chunk holds about P_v / K pairs; and the view's tile grid.
@@ -429,11 +449,16 @@ cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_vi
   size_t s = scan_temp_bytes(cnt_cap > rec_cap ? cnt_cap : rec_cap);
   void* tmp = c.take<char>(t > s ? t : s);
 
-  // 1. view segments
-  k_zero_u32<<<grid_for(n_views + 1), kBlock, 0, st>>>(seg, n_views + 1);
-  note_launch();
-  k_segments<<<grid_for(rec_cap), kBlock, 0, st>>>(proj, n_views, tile_cap, K, seg, &ctr[0]);
-  note_launch();
+  // 1. view segments (from the records' view ids, or from the projection's group offsets)
+  if (!proj.view) {
+    k_segments_from_groups<<<grid_for(n_views + 1), kBlock, 0, st>>>(proj, n_views, tile_cap, K, seg, &ctr[0]);
+    note_launch();
+  } else {
+    k_zero_u32<<<grid_for(n_views + 1), kBlock, 0, st>>>(seg, n_views + 1);
+    note_launch();
+    k_segments<<<grid_for(rec_cap), kBlock, 0, st>>>(proj, n_views, tile_cap, K, seg, &ctr[0]);
+    note_launch();
+  }
   // 2. record indices by depth bits within each view (4 passes: result back in the a buffers)
   // (the last pass also writes the rectangles in sorted order and their pair counts)
   bool in_a = false;

@@ -94,6 +94,8 @@ cudaError_t launch_project(const gs_map& map, const gs_camera* cams, int n_views
                            const gs_proj& out, void* ws, cudaStream_t st);
 
 size_t bin_ws_bytes(int64_t rec_cap, int64_t pair_cap, int64_t tile_cap, int n_views);
+// proj.view == NULL: records written by launch_project without view ids; the view segments
+// come from proj.grp_base and the group count in view_info[V][3].
 cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_views, const gs_params& p,
                             const gs_bins& out, void* ws, cudaStream_t st);
 

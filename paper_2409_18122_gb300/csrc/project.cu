@@ -32,7 +32,7 @@ __device__ __forceinline__ unsigned long long view_pixels(const gs_camera& c) {
 // Per-view table: tile, pixel and warp-item offsets (prefix sums over views), tile
 // sizes, camera checks.
 __global__ void __launch_bounds__(1024) k_view_info(const gs_camera* __restrict__ cams, int n_views, int def_tw,
-                                                    int def_th, uint32_t* __restrict__ view_info,
+                                                    int def_th, uint32_t n_groups, uint32_t* __restrict__ view_info,
                                                     uint32_t* status) {
   __shared__ unsigned long long s_sum[3][32];
   const int per = (n_views + blockDim.x - 1) / blockDim.x;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(1024) k_view_info(const gs_camera* __restrict_
     view_info[kVI * n_views + 0] = (uint32_t)e[0];
     view_info[kVI * n_views + 1] = (uint32_t)e[1];
     view_info[kVI * n_views + 2] = (uint32_t)e[2];
-    view_info[kVI * n_views + 3] = 0u;
+    view_info[kVI * n_views + 3] = n_groups;   // groups of 32 Gaussians: the stride of grp_mask / grp_base
   }
 }
 
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera*
         if ((int64_t)dst < out.capacity) {
           const float4 cu = s_g[warp][3][gl];
           if (out.gid) out.gid[dst] = (uint32_t)((grp << 5) + gl);
-          out.view[dst] = (uint32_t)(v0 + vi);
+          if (out.view) out.view[dst] = (uint32_t)(v0 + vi);
           float4* sp = reinterpret_cast<float4*>(out.splat) + 2 * (size_t)dst;
           sp[0] = make_float4(vp.mx, vp.my, pack_ext(vp.rx, vp.ry), cu.w);
           sp[1] = make_float4(vp.ca, vp.cb, vp.cc, gp.o);
@@ -298,7 +298,8 @@ cudaError_t launch_project(const gs_map& map, const gs_camera* cams, int n_views
   Carver c(ws);
   uint32_t* counts = c.take<uint32_t>((size_t)slots + 1);
   void* scan_tmp = c.take<char>(scan_temp_bytes(slots));
-  k_view_info<<<1, 1024, 0, st>>>(cams, n_views, p.tile_w, p.tile_h, out.view_info, out.status);
+  k_view_info<<<1, 1024, 0, st>>>(cams, n_views, p.tile_w, p.tile_h, (uint32_t)((map.n + 31) / 32), out.view_info,
+                                  out.status);
   note_launch();
   const int64_t blocks = (map.n + kBlock - 1) / kBlock;
   if (blocks > 0) {

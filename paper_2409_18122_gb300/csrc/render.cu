@@ -389,8 +389,7 @@ size_t ig_ws_bytes(int64_t n, int n_views, int64_t rec_cap, int64_t pair_cap, in
   Carver c(nullptr);
   c.take<uint32_t>(1);                                   // record count
   c.take<uint32_t>(kVI * (size_t)(n_views + 1));         // view info
-  c.take<uint32_t>(rec_cap);                             // view
-  c.take<float4>(2 * (size_t)rec_cap);                   // splat
+  c.take<float4>(2 * (size_t)rec_cap);                   // splat (no view ids: segments from grp_base)
   c.take<ushort4>(rec_cap);                              // rect
   c.take<uint32_t>(rec_cap);                             // depth key
   const int64_t slots = ((n + 31) / 32) * (int64_t)n_views;
@@ -463,8 +462,8 @@ cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_vie
   proj.count = c.take<uint32_t>(1);
   proj.status = status;
   proj.view_info = c.take<uint32_t>(kVI * (size_t)(n_views + 1));
-  proj.gid = nullptr;   // Gaussian ids are not needed to score views
-  proj.view = c.take<uint32_t>(rec_cap);
+  proj.gid = nullptr;    // Gaussian ids are not needed to score views
+  proj.view = nullptr;   // nor view ids: binning finds each view's records through grp_base
   proj.splat = (float*)c.take<float4>(2 * (size_t)rec_cap);
   proj.color_d = nullptr;   // not needed to score views: the projection skips the colours
   proj.rect = (uint16_t*)c.take<ushort4>(rec_cap);

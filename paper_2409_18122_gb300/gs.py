@@ -188,16 +188,20 @@ class Frame:
     GS_FLAG_PAIR_OVERFLOW (see `check_status` / `grow_if_needed`).  with_color=False
     leaves out the per-record colours (scoring only); with_pair_tiles=False leaves
     out the global tile id of every pair (compositing needs only the ranges);
-    with_gid=False leaves out the Gaussian id of every record (the kernels never read it).
+    with_gid=False leaves out the Gaussian id of every record (the kernels never read it);
+    with_view=False leaves out the view id of every record (binning then finds each view's
+    records through the projection's group offsets).
     """
 
     def __init__(self, n: int, cams: Sequence, params: RenderParams = RenderParams(),
                  pair_capacity: Optional[int] = None, device="cuda", with_color: bool = True,
-                 with_pair_tiles: bool = True, record_capacity: Optional[int] = None, with_gid: bool = True):
+                 with_pair_tiles: bool = True, record_capacity: Optional[int] = None, with_gid: bool = True,
+                 with_view: bool = True):
         self.device = torch.device(device)
         self.params = params
         self.with_color = with_color
         self.with_gid = with_gid
+        self.with_view = with_view
         self.with_pair_tiles = with_pair_tiles
         self.cams = list(cams)
         self.V = len(self.cams)
@@ -225,7 +229,7 @@ class Frame:
         self.rec_count = torch.zeros(1, dtype=torch.int32, device=d)
         self.view_info = torch.zeros(4 * (self.V + 1), dtype=torch.int32, device=d)
         self.gid = _alloc_u32(rc, d) if self.with_gid else None
-        self.view = _alloc_u32(rc, d)
+        self.view = _alloc_u32(rc, d) if self.with_view else None
         self.splat = torch.empty((rc, 8), dtype=torch.float32, device=d)
         self.color_d = torch.empty((rc, 4), dtype=torch.float32, device=d) if self.with_color else None
         self.rect = torch.empty((rc, 4), dtype=torch.int16, device=d)

@@ -53,7 +53,8 @@ def gpu_records(frame):
 def gpu_bins(frame):
     n = int(u32(frame.pair_count)[0])
     m = min(n, frame.pair_capacity)
-    return dict(n=n, tile=u32(frame.pair_tile)[:m], rec=u32(frame.pair_rec)[:m],
+    return dict(n=n, tile=u32(frame.pair_tile)[:m] if frame.pair_tile is not None else None,
+                rec=u32(frame.pair_rec)[:m],
                 ranges=u32(frame.ranges)[:frame.n_tiles * 2].reshape(-1, 2).astype(np.int64))
 
 

@@ -569,6 +569,17 @@ def test_info_gain_composite_entry_matches_batch():
     comp = fr.info_gain().cpu().numpy()
     fr.check_status()
     np.testing.assert_array_equal(comp, batch)
+    # records without view ids: binning finds the views through the group offsets; the same
+    # tile lists and ranges, the same scores
+    fv = gs.Frame(gm.n, cams, with_color=False, with_view=False)
+    fv.project(gm)
+    fv.bin_sort()
+    comp_v = fv.info_gain().cpu().numpy()
+    fv.check_status()
+    np.testing.assert_array_equal(comp_v, batch)
+    ref_bins, v_bins = gpu_bins(fr), gpu_bins(fv)
+    np.testing.assert_array_equal(v_bins["rec"], ref_bins["rec"])
+    np.testing.assert_array_equal(v_bins["ranges"], ref_bins["ranges"])
     ref, imgs = O.info_gain(gmap, cams)
     for v in range(len(cams)):
         tol = IG_RTOL * abs(ref[v]) + 1e-7 + imgs[v]["knife"].mean() * 4e-3
