@@ -235,6 +235,9 @@ __device__ __forceinline__ bool group_may_meet(const float* gc, float rad, const
   return true;
 }
 
+// kFull = false: only the decision (the same operations up to the rectangle test; the
+// record's conic, mean and depth are not formed), for the projection's count pass.
+template <bool kFull = true>
 __device__ __forceinline__ bool view_proj(float4 mo, const GaussPre& g, const CamC& c, float near_plane,
                                           float eps2d, ViewProj& vp) {
   if (!g.valid) return false;
@@ -280,6 +283,7 @@ __device__ __forceinline__ bool view_proj(float4 mo, const GaussPre& g, const Ca
   xhi = fminf(xhi, (float)(c.W - 1));
   yhi = fminf(yhi, (float)(c.H - 1));
   if (!(xlo <= xhi) || !(ylo <= yhi)) return false;
+  if (!kFull) return true;
   // pixel -> tile: the coordinates are >= 0 and tile sizes are powers of two
   vp.x0 = (int)xlo >> c.sx;
   vp.y0 = (int)ylo >> c.sy;

@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kBlock) k_project(gs_map map, const gs_camera*
       gp.Q = s1.z;
       gp.o = s1.w;
       ViewProj vp;
-      const bool vis = view_proj(gmo, gp, s_cam[vi], p.near_plane, p.eps2d, vp);
+      const bool vis = view_proj<kWrite>(gmo, gp, s_cam[vi], p.near_plane, p.eps2d, vp);
       if (!kWrite) {
         if (vis) atomicOr(&vmask[vi], 1u << gl);
       } else if (vis) {
