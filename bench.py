@@ -599,7 +599,29 @@ def cfg0_latency_us(torch, gs, scenes, reps=30, scene=None):
         fr.forward(gm, img)
     g.replay()
     torch.cuda.synchronize()
-    return {"eager": eager, "graph": median_us(g.replay), "unit": "us"}
+    out = {"eager": eager, "graph": median_us(g.replay), "unit": "us"}
+    # the same render in one launch (gs_render_small), when the map is small enough for it
+    if gm.n <= gs.L.GS_SMALL_MAX_GAUSSIANS:
+        simg = {k: torch.empty_like(v) for k, v in img.items() if v is not None}
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        gs.render_small(gm, sc.cams, images=simg, status=st)
+        torch.cuda.synchronize()
+        ok = int(st.item()) & gs.L.GS_FLAG_ERROR_MASK == 0
+        same = ok and all(torch.equal(simg[k], img[k]) for k in simg)
+        out["one_launch"] = {"eager": median_us(lambda: gs.render_small(gm, sc.cams, images=simg, status=st)),
+                             "identical_to_tiled": bool(same), "unit": "us"}
+        cams_dev = gs.cameras_to_device(sc.cams)
+        with torch.cuda.stream(side):
+            gs.render_small(gm, cams_dev, images=simg, status=st)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g2 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g2):
+            gs.render_small(gm, cams_dev, images=simg, status=st)
+        g2.replay()
+        torch.cuda.synchronize()
+        out["one_launch"]["graph"] = median_us(g2.replay)
+    return out
 
 
 def render_free_xi(torch, gs, istep, flush, reps=10):

@@ -261,6 +261,30 @@ typedef struct {
 gs_status gs_render_fwd(const gs_map* map, const gs_proj* proj, const gs_bins* bins, const gs_camera* cams,
                         int32_t n_views, const gs_params* prm, gs_image* out, void* stream);
 
+/* gs_render_small -- the forward render of gs_render_fwd (Sec. III), from the map
+ * directly, in one kernel launch and without records, bins or workspace: for maps of
+ * up to a few thousand Gaussians, whose tiled render (gs_project + gs_bin_sort +
+ * gs_render_fwd, about 35 kernels) is bound by launch latency.  Every CTA takes screen
+ * tiles, projects the whole map for the tile's view with gs_project's decision
+ * arithmetic, sorts the Gaussians whose tile rectangle covers the tile by depth key
+ * (ties by Gaussian id) in shared memory and composites the tile; the outputs are bit
+ * for bit those of the tiled path with the same parameters (`last` indexes the tile's
+ * list of gs_bin_sort).  Cost grows with map size x tiles: use the tiled path for
+ * large maps.
+ *   map->n <= GS_SMALL_MAX_GAUSSIANS, n_views <= GS_SMALL_MAX_VIEWS, else GS_ERR_ARG.
+ *   A tile covered by more than GS_SMALL_MAX_LIST Gaussians sets GS_FLAG_PAIR_OVERFLOW
+ *   and its pixels are not written: render such a view with the tiled path.
+ *   status: DEVICE uint32[1] status word (OR-ed): also GS_FLAG_BAD_CAMERA (the view
+ *   keeps its pixels in the layout and they are not written), GS_FLAG_NONFINITE (checked
+ *   when the views have at least one tile) and GS_FLAG_RANGE_OVERFLOW (more than 2^20
+ *   tiles or 2^32 pixels over the views: the views past that bound are not written).
+ * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG, GS_ERR_CUDA. */
+#define GS_SMALL_MAX_GAUSSIANS (1 << 16)
+#define GS_SMALL_MAX_VIEWS 64
+#define GS_SMALL_MAX_LIST 2048
+gs_status gs_render_small(const gs_map* map, const gs_camera* cams, int32_t n_views, const gs_params* prm,
+                          gs_image* out, uint32_t* status, void* stream);
+
 /* Image-space gradient dL/d(rgb, depth), same layouts as gs_image.rgb / .depth.
  * Either may be NULL (treated as zero).  The uncertainty channel is not
  * differentiated: u_i is not a learned parameter. */

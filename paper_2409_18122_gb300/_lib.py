@@ -29,6 +29,9 @@ GS_IG_RENDER_MEAN = 0
 GS_U_ABS, GS_U_SQ = 0, 1
 GS_XI, GS_XI_SUM = 0, 1
 GS_NOALLOC_MAX_RECORDS = 1 << 18
+GS_SMALL_MAX_GAUSSIANS = 1 << 16
+GS_SMALL_MAX_VIEWS = 64
+GS_SMALL_MAX_LIST = 2048
 
 
 class gs_camera(ctypes.Structure):
@@ -117,6 +120,8 @@ PROTOTYPES = {
                               c_size_t, c_void_p]),
     "gs_render_fwd": (c_int32, [POINTER(gs_map), POINTER(gs_proj), POINTER(gs_bins), c_void_p, c_int32,
                                 POINTER(gs_params), POINTER(gs_image), c_void_p]),
+    "gs_render_small": (c_int32, [POINTER(gs_map), c_void_p, c_int32, POINTER(gs_params), POINTER(gs_image),
+                                  c_void_p, c_void_p]),
     "gs_render_bwd": (c_int32, [POINTER(gs_map), POINTER(gs_proj), POINTER(gs_bins), POINTER(gs_image),
                                 POINTER(gs_image_grad), c_void_p, c_int32, POINTER(gs_params), POINTER(gs_map_grad),
                                 c_void_p, c_size_t, c_void_p]),

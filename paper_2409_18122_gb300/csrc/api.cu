@@ -171,6 +171,19 @@ gs_status gs_render_fwd(const gs_map* map, const gs_proj* proj, const gs_bins* b
   return from_cuda(launch_render_fwd(*map, *proj, *bins, cams, n_views, *prm, *out, (cudaStream_t)stream));
 }
 
+gs_status gs_render_small(const gs_map* map, const gs_camera* cams, int32_t n_views, const gs_params* prm,
+                          gs_image* out, uint32_t* status, void* stream) {
+  GS_TRACE("gs_render_small");
+  GS_TRY(check_map(map));
+  GS_TRY(check_views(cams, n_views));
+  GS_TRY(check_params(prm));
+  if (map->n > GS_SMALL_MAX_GAUSSIANS || n_views > GS_SMALL_MAX_VIEWS) return GS_ERR_ARG;
+  if (!out || !status) return GS_ERR_NULL;
+  if (!aligned(status, 4)) return GS_ERR_ALIGN;
+  GS_TRY(check_image(out));
+  return from_cuda(launch_render_small(*map, cams, n_views, *prm, *out, status, (cudaStream_t)stream));
+}
+
 gs_status gs_render_bwd(const gs_map* map, const gs_proj* proj, const gs_bins* bins, const gs_image* fwd,
                         const gs_image_grad* grad, const gs_camera* cams, int32_t n_views, const gs_params* prm,
                         gs_map_grad* out, void* ws, size_t ws_bytes, void* stream) {

@@ -102,6 +102,10 @@ cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_vi
 cudaError_t launch_render_fwd(const gs_map& map, const gs_proj& proj, const gs_bins& bins, const gs_camera* cams,
                               int n_views, const gs_params& p, const gs_image& img, cudaStream_t st);
 
+// the one-launch forward render of a small map (small.cu)
+cudaError_t launch_render_small(const gs_map& map, const gs_camera* cams, int n_views, const gs_params& p,
+                                const gs_image& img, uint32_t* status, cudaStream_t st);
+
 size_t bwd_ws_bytes(int64_t rec_cap);
 // Every argument check of gs_render_bwd except the workspace's (api.cu); GS_OK if the
 // arguments are valid.  Shared by the workspace and the allocation-free entry points.

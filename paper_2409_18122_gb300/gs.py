@@ -389,6 +389,41 @@ class Frame:
         return out
 
 
+def render_small(gmap: GaussianMapTensors, cams, params: RenderParams = RenderParams(), images=None,
+                 status: Optional[torch.Tensor] = None, stream=None):
+    """Forward render of a small map in one launch (gs_render_small): the images of
+    Frame.forward bit for bit, without records, bins or workspace.  `cams`: camera objects,
+    or their gs_camera records already on the device (then pass `images`).  Returns (images,
+    status tensor); after a synchronise, `status & GS_FLAG_PAIR_OVERFLOW` means a tile held
+    more than GS_SMALL_MAX_LIST Gaussians and was not written (render with a Frame)."""
+    on_device = isinstance(cams, torch.Tensor)   # gs_camera records already on the device (uint8 [80 V])
+    n_views = cams.numel() // CAMERA_DTYPE.itemsize if on_device else len(cams)
+    if gmap.n > L.GS_SMALL_MAX_GAUSSIANS or n_views > L.GS_SMALL_MAX_VIEWS:
+        raise ValueError("render_small takes at most %d Gaussians and %d views" %
+                         (L.GS_SMALL_MAX_GAUSSIANS, L.GS_SMALL_MAX_VIEWS))
+    if images is None and on_device:
+        raise ValueError("pass the images when the cameras are already on the device")
+    dev = gmap.mo.device
+    cams_dev = cams if on_device else cameras_to_device(cams, dev)
+    if images is None:
+        P = int(tile_grid(cams, params)[3][-1])
+        images = dict(rgb=torch.empty(3 * P, dtype=torch.float32, device=dev),
+                      depth=torch.empty(P, dtype=torch.float32, device=dev),
+                      unc=torch.empty(P, dtype=torch.float32, device=dev),
+                      T=torch.empty(P, dtype=torch.float32, device=dev),
+                      last=torch.empty(P, dtype=torch.int32, device=dev), n_contrib=None)
+    st = torch.zeros(1, dtype=torch.int32, device=dev) if status is None else status
+    _require(st, "status", 1, torch.int32)
+    c_img = L.gs_image(_ptr(images.get("rgb")), _ptr(images.get("depth")), _ptr(images.get("unc")),
+                       _ptr(images.get("T")), _ptr(images.get("last")), _ptr(images.get("n_contrib")))
+    m = gmap.c()
+    prm = params.c()
+    _timed("gs_render_small", stream, lambda: L.check(
+        L.lib().gs_render_small(ctypes.byref(m), _ptr(cams_dev), n_views, ctypes.byref(prm), ctypes.byref(c_img),
+                                _ptr(st), _stream(stream)), "gs_render_small"))
+    return images, st
+
+
 class StaleFrameError(RuntimeError):
     """backward() of a render whose Frame has been projected or binned again since its forward."""
 

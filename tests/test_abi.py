@@ -131,6 +131,14 @@ def test_host_side_argument_errors(lib):
     odd = ctypes.c_void_p(0x10002)
     img_bad = L.gs_image(fake, odd, None, fake, fake, None)
     assert lib.gs_render_fwd(P(m), P(proj), P(bins), fake, 1, P(prm), P(img_bad), None) == L.GS_ERR_ALIGN
+    # the one-launch small render: size limits, a status word, aligned images
+    img_ok = L.gs_image(fake, fake, None, fake, fake, None)
+    big = L.gs_map(fake, fake, fake, fake, L.GS_SMALL_MAX_GAUSSIANS + 1)
+    assert lib.gs_render_small(P(big), fake, 1, P(prm), P(img_ok), fake, None) == L.GS_ERR_ARG
+    assert lib.gs_render_small(P(m), fake, L.GS_SMALL_MAX_VIEWS + 1, P(prm), P(img_ok), fake, None) == L.GS_ERR_ARG
+    assert lib.gs_render_small(P(m), fake, 1, P(prm), P(img_ok), None, None) == L.GS_ERR_NULL
+    assert lib.gs_render_small(P(m), fake, 1, P(prm), P(img_bad), fake, None) == L.GS_ERR_ALIGN
+    assert lib.gs_render_small(P(m), fake, 1, P(_params(tile_w=12)), P(img_ok), fake, None) == L.GS_ERR_ARG
     img = L.gs_image(fake, fake, None, fake, fake, None)
     out = L.gs_map_grad(fake, fake, fake, fake)
     for fwd, grad in ((img_bad, L.gs_image_grad(fake, fake)), (img, L.gs_image_grad(odd, None)),

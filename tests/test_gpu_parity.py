@@ -682,6 +682,78 @@ def test_guard_band_scene_vs_oracle():
     assert abs(ig[0] - ref["unc"].mean()) <= IG_RTOL * abs(ref["unc"].mean()) + 1e-7
 
 
+# --------------------------------------------------------------------------- one-launch small render
+def _small_vs_tiled(gmap, cams, params=gs.RenderParams()):
+    """gs_render_small and the tiled path (project, bin_sort, render_fwd) on the same inputs."""
+    gm = gs.GaussianMapTensors.from_numpy(gmap)
+    fr = gs.Frame(gm.n, cams, params)
+    ref = fr.new_images(with_counts=True)
+    fr.forward(gm, ref)
+    P = fr.n_pixels
+    img = dict(rgb=torch.full((3 * P,), -7.0, device="cuda"), depth=torch.full((P,), -7.0, device="cuda"),
+               unc=torch.full((P,), -7.0, device="cuda"), T=torch.full((P,), -7.0, device="cuda"),
+               last=torch.full((P,), -7, dtype=torch.int32, device="cuda"),
+               n_contrib=torch.full((P,), -7, dtype=torch.int32, device="cuda"))
+    img, st = gs.render_small(gm, cams, params, img)
+    torch.cuda.synchronize()
+    return fr, ref, img, int(st.item())
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8), (16, 32), (32, 32)])
+def test_small_render_equals_tiled_path_bitwise(tile):
+    """The one-launch render of config 0 gives the tiled path's images, T, last and
+    contributor counts bit for bit, at every tile shape."""
+    sc = scenes.config0()
+    fr, ref, img, st = _small_vs_tiled(sc.gmap, sc.cams, gs.RenderParams(tile_w=tile[0], tile_h=tile[1]))
+    assert st & gs.L.GS_FLAG_ERROR_MASK == 0
+    for k in ("rgb", "depth", "unc", "T", "last", "n_contrib"):
+        assert torch.equal(img[k], ref[k]), k
+
+
+def test_small_render_multiview_vs_oracle():
+    """Several views of one small map (ragged edges, per-view tiles, views smaller than a
+    pixel block) against the tiled path bit for bit and the oracle within tolerance."""
+    sc = scenes.config2(n=4_000, n_views=2)
+    cams = [sc.cams[0].crop(200, 160, 96, 64), sc.cams[1].crop(0, 0, 80, 60).with_tile(8, 8),
+            Camera(100, 100, 1.5, 1.0, 3, 2), scenes.yaw_camera(5, 5, 1.5, 0.3, 72, 40, 50.0).with_tile(32, 8)]
+    fr, ref, img, st = _small_vs_tiled(sc.gmap, cams)
+    assert st & gs.L.GS_FLAG_ERROR_MASK == 0
+    for k in ("rgb", "depth", "unc", "T", "last", "n_contrib"):
+        assert torch.equal(img[k], ref[k]), k
+    gpu = images_host(fr, img)
+    oref = O.render_images(sc.gmap, cams)
+    lg = last_gid(fr, gpu)
+    for v in range(len(cams)):
+        compare_image(gpu[v], oref[v], "view %d" % v, check_last=lg[v])
+
+
+def test_small_render_flags():
+    """A tile covered by more Gaussians than fit in shared memory is flagged and not written;
+    non-finite entries and an invalid camera raise their flags as in the tiled path."""
+    n = gs.L.GS_SMALL_MAX_LIST + 100
+    rng = np.random.default_rng(5)
+    mu = np.stack([rng.uniform(-0.05, 0.05, n), rng.uniform(-0.05, 0.05, n), rng.uniform(2, 3, n)], 1)
+    g = scenes.GaussianMap(np.c_[mu, np.full(n, 2.0)].astype(np.float32),
+                           np.c_[np.full((n, 3), -3.0), rng.uniform(size=n)].astype(np.float32),
+                           np.tile(np.float32([1, 0, 0, 0]), (n, 1)), np.c_[rng.uniform(size=(n, 3)),
+                                                                         np.zeros(n)].astype(np.float32))
+    cam = Camera(100, 100, 32, 32, 64, 64)
+    gm = gs.GaussianMapTensors.from_numpy(g)
+    img, st = gs.render_small(gm, [cam])
+    torch.cuda.synchronize()
+    assert int(st.item()) & gs.L.GS_FLAG_PAIR_OVERFLOW
+    sc = scenes.config0()
+    bad = sc.gmap.copy()
+    bad.mo[3, 0] = np.nan
+    cams = [sc.cams[0], Camera(-100.0, 100.0, 64.0, 48.0, 128, 96)]
+    fr, ref, img, st = _small_vs_tiled(bad, cams)
+    assert st & gs.L.GS_FLAG_NONFINITE and st & gs.L.GS_FLAG_BAD_CAMERA
+    P0 = cams[0].width * cams[0].height
+    for k in ("depth", "unc", "T", "last"):
+        assert torch.equal(img[k][:P0], ref[k][:P0]), k
+        assert (img[k][P0:] == -7).all(), k   # the invalid view's pixels are left alone
+
+
 # --------------------------------------------------------------------------- degenerate inputs
 @pytest.mark.parametrize("case", ["empty", "behind"])
 def test_empty_and_fully_culled_maps(case):
