@@ -201,7 +201,7 @@ class MapStep:
     the whole iteration (forward, loss, backward, Adam) is captured once in a CUDA graph and
     replayed; eager() runs it op by op (used for the per-stage breakdown)."""
 
-    def __init__(self, gs, scenes, weights=None, graph=True, scene=None, tune=True):
+    def __init__(self, gs, scenes, weights=None, graph=True, scene=None, tune=True, render_params=None):
         import torch
         self.torch = torch
         self.gs = gs
@@ -209,8 +209,11 @@ class MapStep:
         self.scene = sc
         gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
         # keyframe tile and forward chunk depth picked by the autotuner (timed fwd + bwd passes)
-        self.render_params, self.tune_timings = (gs.autotune_mapping(gm, sc.cams) if tune
-                                                 else (gs.RenderParams(), {}))
+        if render_params is not None:
+            self.render_params, self.tune_timings = render_params, {}
+        else:
+            self.render_params, self.tune_timings = (gs.autotune_mapping(gm, sc.cams) if tune
+                                                     else (gs.RenderParams(), {}))
         self.frame = gs.Frame(gm.n, sc.cams, self.render_params, with_pair_tiles=False)
         tgt = gs.GaussianMapTensors.from_numpy(scenes.perturbed(sc.gmap, seed=2002))
         while True:
@@ -261,13 +264,17 @@ class MapStep:
             return self.graph_loss
         return self.eager()
 
-    def e2e(self):
-        """Host inputs -> device, step, loss -> host (all enqueued on the current stream)."""
+    def upload(self):
+        """This step's inputs from pinned host memory (on the current stream)."""
         with self.torch.no_grad():
             for d, h in zip(self.params, self.host):
                 d.copy_(h, non_blocking=True)
             self.tgt_rgb.copy_(self.host_tgt[0], non_blocking=True)
             self.tgt_depth.copy_(self.host_tgt[1], non_blocking=True)
+
+    def e2e(self):
+        """Host inputs -> device, step, loss -> host (all enqueued on the current stream)."""
+        self.upload()
         loss = self()
         self.loss_host.copy_(loss.detach().reshape(1), non_blocking=True)
 
@@ -324,31 +331,42 @@ class IGStep:
         self.host = [t.cpu().pin_memory() for t in (self.gm.mo, self.gm.su, self.gm.q, self.gm.rgb)]
         self.host_cams = self.frame.cams_dev.cpu().pin_memory()
         self.out_host = torch.zeros(len(cams), dtype=torch.float32).pin_memory()
+        # a second device copy of the map: the end-to-end loop uploads the next step's map into
+        # one buffer while the current step runs from the other
+        self.gms = [self.gm, gs.GaussianMapTensors(*(t.clone() for t in (self.gm.mo, self.gm.su, self.gm.q,
+                                                                          self.gm.rgb)))]
         self.graph = None
+        self.graphs = []
         self.kernels_per_replay = 0
         try:
             self.ev = (torch.cuda.Event(enable_timing=True, external=True),
                        torch.cuda.Event(enable_timing=True, external=True))
+            # recorded after each buffer's projection, the last stage that reads the map
+            self.ev_proj = [torch.cuda.Event(external=True), torch.cuda.Event(external=True)]
         except TypeError:
             self.ev = None
         if graph and self.ev is not None:
-            s = torch.cuda.Stream()
-            s.wait_stream(torch.cuda.current_stream())
-            with torch.cuda.stream(s):
-                self._run()
-            torch.cuda.current_stream().wait_stream(s)
-            torch.cuda.synchronize()
-            g = torch.cuda.CUDAGraph()
-            k0 = gs.L.lib().gs_kernel_launches()
-            with torch.cuda.graph(g):
-                self._run()
-            self.kernels_per_replay = int(gs.L.lib().gs_kernel_launches() - k0)
-            self.graph = g
+            for b in (0, 1):
+                s = torch.cuda.Stream()
+                s.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.stream(s):
+                    self._run(b)
+                torch.cuda.current_stream().wait_stream(s)
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                k0 = gs.L.lib().gs_kernel_launches()
+                with torch.cuda.graph(g):
+                    self._run(b)
+                self.kernels_per_replay = int(gs.L.lib().gs_kernel_launches() - k0)
+                self.graphs.append(g)
+            self.graph = self.graphs[0]
         if self.ev is None:
             self.ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            self.ev_proj = [torch.cuda.Event(), torch.cuda.Event()]
 
-    def _run(self):
-        self.frame.project(self.gm)
+    def _run(self, b=0):
+        self.frame.project(self.gms[b])
+        self.ev_proj[b].record()
         self.frame.bin_sort()
         self.ev[0].record()
         self.frame.info_gain(self.out)
@@ -388,12 +406,26 @@ class IGStep:
         torch.cuda.empty_cache()
         return c, e
 
-    def e2e(self):
+    def upload_map(self, b):
+        """This step's map from pinned host memory into buffer b (on the current stream)."""
         with self.torch.no_grad():
-            for d, h in zip((self.gm.mo, self.gm.su, self.gm.q, self.gm.rgb), self.host):
+            g = self.gms[b]
+            for d, h in zip((g.mo, g.su, g.q, g.rgb), self.host):
                 d.copy_(h, non_blocking=True)
+
+    def run_buffer(self, b):
+        """One pass projecting the map in buffer b, its cameras uploaded first (current stream)."""
+        with self.torch.no_grad():
             self.frame.cams_dev.copy_(self.host_cams, non_blocking=True)
-        self()
+        if self.graphs:
+            self.graphs[b].replay()
+        else:
+            self._run(b)
+        return self.out
+
+    def e2e(self):
+        self.upload_map(0)
+        self.run_buffer(0)
         self.out_host.copy_(self.out, non_blocking=True)
 
     def h2d_bytes(self):
@@ -428,6 +460,67 @@ class Unbatched:
             ig.cams_dev.view(1, -1).copy_(self.cams_all[v:v + 1], non_blocking=True)
             ig(self.istep.gm, out=self.out[v:v + 1])
         return self.out
+
+
+# ----------------------------------------------------------------------------- end-to-end loops
+def pipelined_e2e_ms(torch, steps, upload, run, readback, last_reader, flush):
+    """Device time of `steps` end-to-end steps, each uploading its inputs from pinned host
+    memory into one of two input buffers (b = step mod 2), running from that buffer and
+    reading its result back to the host.  The uploads go on a copy stream: step k+1's upload
+    starts as soon as the last reader of its buffer (in step k-1) is done, so it overlaps
+    step k.  upload(b) / run(b) / readback(b) enqueue on the current stream; last_reader(b)
+    is an event recorded by run(b) after the last read of buffer b.  The L2 flush before
+    every step is not counted."""
+    main = torch.cuda.current_stream()
+    cs = torch.cuda.Stream()
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fl = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    start.record(main)
+    cs.wait_stream(main)
+    with torch.cuda.stream(cs):
+        upload(0)
+        copied[0].record(cs)
+    for k in range(steps):
+        b = k & 1
+        if k + 1 < steps:
+            nb = b ^ 1
+            with torch.cuda.stream(cs):
+                if k >= 1:
+                    cs.wait_event(last_reader(nb))
+                upload(nb)
+                copied[nb].record(cs)
+        fl[k][0].record(main)
+        flush()
+        fl[k][1].record(main)
+        main.wait_event(copied[b])
+        run(b)
+        readback(b)
+    end.record(main)
+    torch.cuda.synchronize()
+    return start.elapsed_time(end) - sum(a.elapsed_time(c) for a, c in fl)
+
+
+def map_e2e_ms(torch, pair, steps, flush):
+    """pipelined_e2e_ms for the mapping step: two MapSteps (their own parameters, targets,
+    frame and graph) take the steps in turn."""
+    done = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def run(b):
+        pair[b].last_loss = pair[b]()
+        done[b].record()
+
+    def readback(b):
+        pair[b].loss_host.copy_(pair[b].last_loss.detach().reshape(1), non_blocking=True)
+
+    return pipelined_e2e_ms(torch, steps, lambda b: pair[b].upload(), run, readback, lambda b: done[b], flush)
+
+
+def ig_e2e_ms(torch, istep, steps, flush):
+    """pipelined_e2e_ms for the information-gain pass: the two map buffers of one IGStep."""
+    return pipelined_e2e_ms(torch, steps, istep.upload_map, istep.run_buffer,
+                            lambda b: istep.out_host.copy_(istep.out, non_blocking=True),
+                            lambda b: istep.ev_proj[b], flush)
 
 
 # ----------------------------------------------------------------------------- timing loops
@@ -846,17 +939,21 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e and mstep is not None and istep is not None:
-        for _ in range(2):
-            mstep.e2e()
-            istep.e2e()
-        torch.cuda.synchronize()
-        et = timed_loop(torch, args.steps, [("map", mstep.e2e), ("ig", istep.e2e)], flush)
-        e_ig = max_over_ranks(sum(et["ig"]) / 1e3, world)
-        e_map = max_over_ranks(sum(et["map"]) / 1e3, world)
+        # end to end through the same public calls: every step uploads its inputs from pinned
+        # host memory and reads its result back; uploads overlap the previous step (two input
+        # buffers, a copy stream)
+        mstep_b = MapStep(gs, scenes, render_params=mstep.render_params)
+        pair = (mstep, mstep_b)
+        ig_e2e_ms(torch, istep, 2, flush)
+        map_e2e_ms(torch, pair, 2, flush)
+        e_ig = max_over_ranks(ig_e2e_ms(torch, istep, args.steps, flush) / 1e3, world)
+        e_map = max_over_ranks(map_e2e_ms(torch, pair, args.steps, flush) / 1e3, world)
+        del mstep_b, pair
         e2e = {"value": istep.n_views * args.steps * world / e_ig, "unit": "views/s",
                "fwd_bwd_iters_per_s": args.steps * world / e_map,
                "h2d_bytes_per_step": mstep.h2d_bytes() + istep.h2d_bytes(),
-               "d2h_bytes_per_step": 4 + 4 * istep.n_views}
+               "d2h_bytes_per_step": 4 + 4 * istep.n_views,
+               "pipelined": "each step's uploads overlap the previous step (double-buffered inputs, copy stream)"}
 
     if istep is None or mstep is None:
         # a profiling run of one part: a short line, no roofline bookkeeping

@@ -753,11 +753,11 @@ TILE_CANDIDATES = ((16, 16), (16, 8), (8, 8), (32, 8), (32, 16), (32, 32))
 
 
 def autotune_tiles(gmap: GaussianMapTensors, cams: Sequence, params: RenderParams = RenderParams(),
-                   candidates=TILE_CANDIDATES, reps: int = 3, pair_capacity: Optional[int] = None):
+                   candidates=TILE_CANDIDATES, reps: int = 5, pair_capacity: Optional[int] = None):
     """Pick a screen tile per resolution class by timing the batched information-gain pass.
 
     For every distinct (width, height) among `cams`, the views of that class are
-    scored with each candidate tile size (CUDA events, best of `reps` after one
+    scored with each candidate tile size (CUDA events, median of `reps` after one
     warm-up, L2 flushed before each) and the fastest is kept, unless the default
     tile of `params` is within TUNE_MARGIN of it.  Returns ({(W, H): (tile_w, tile_h)},
     {(W, H): {tile: ms}}).  Use `with_tiles` to apply the choice to a camera list.
@@ -789,16 +789,17 @@ FWD_BATCH_CANDIDATES = (1, 2, 4)     # RenderParams.fwd_batch
 
 
 L2_FLUSH_BYTES = 256 << 20     # more than the GPU's L2: written between timed calls of the autotuners
-TUNE_MARGIN = 0.01             # a candidate replaces the default only if it is faster by more than this
+TUNE_MARGIN = 0.03             # a candidate replaces the default only if it is faster by more than this
 
 
 def _best_ms(fn, reps: int) -> float:
-    """Best device time of `fn` over `reps` calls (CUDA events on the current stream), after one
-    warm-up, with the L2 cache flushed before every timed call (as the steps it tunes run)."""
+    """Median device time of `fn` over `reps` calls (CUDA events on the current stream), after
+    one warm-up, with the L2 cache flushed before every timed call (as the steps it tunes run).
+    The median, not the minimum: a single fast outlier must not decide a choice."""
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     fn()
     torch.cuda.synchronize()
-    best = float("inf")
+    t = []
     for _ in range(reps):
         flush.fill_(1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -806,9 +807,9 @@ def _best_ms(fn, reps: int) -> float:
         fn()
         e1.record()
         torch.cuda.synchronize()
-        best = min(best, e0.elapsed_time(e1))
+        t.append(e0.elapsed_time(e1))
     del flush
-    return best
+    return float(np.median(t))
 
 
 def _pick(timings, default):
@@ -820,7 +821,7 @@ def _pick(timings, default):
 
 
 def autotune_ig_batch(gmap: GaussianMapTensors, cams: Sequence, params: RenderParams = RenderParams(),
-                      candidates=IG_BATCH_CANDIDATES, reps: int = 5, pair_capacity: Optional[int] = None):
+                      candidates=IG_BATCH_CANDIDATES, reps: int = 7, pair_capacity: Optional[int] = None):
     """Pick the chunk depth of the information-gain compositing (RenderParams.ig_batch) by timing
     the batched pass over `cams` (with their own tiles, e.g. from autotune_tiles) at each
     candidate; the scores are the same for every depth.  Returns (depth, {depth: ms})."""
@@ -840,7 +841,7 @@ def autotune_ig_batch(gmap: GaussianMapTensors, cams: Sequence, params: RenderPa
 
 
 def autotune_mapping(gmap: GaussianMapTensors, cams: Sequence, params: RenderParams = RenderParams(),
-                     tiles=TILE_CANDIDATES, batches=FWD_BATCH_CANDIDATES, reps: int = 5):
+                     tiles=TILE_CANDIDATES, batches=FWD_BATCH_CANDIDATES, reps: int = 7):
     """Pick the keyframes' tile (RenderParams.tile_w, tile_h) and the forward chunk depth
     (RenderParams.fwd_batch) of a mapping step by timing one forward and backward pass of the
     map through all `cams` (unit image gradients): the tile first at the default depth, then
