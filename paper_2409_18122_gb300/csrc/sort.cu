@@ -23,7 +23,12 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kItems = 8;
 constexpr int kTile = kBlock * kItems;   // 2048 keys per tile
 constexpr int kRadix = 256;
-constexpr int kMaxParts = 2048;
+// Partitions of a large sort.  More, smaller partitions keep the blocks that run at the same
+// time on fewer segments, so the last pass of a binning sort, which gathers each record's
+// rectangle by record index within its view, finds them in L2: at 2,048 / 4,096 / 8,192 /
+// 16,384 / 32,768 partitions the binning of a 256-view batch took 3.80 / 3.56 / 3.52 / 3.61 /
+// 3.89 ms (per-partition histograms and scans grow with the count).
+constexpr int kMaxParts = 8192;
 
 inline int64_t parts_for(int64_t n_cap) {
   int64_t g = (n_cap + kTile - 1) / kTile;
