@@ -222,3 +222,36 @@ def test_uncertainty_output_is_not_differentiable():
     assert rgb.requires_grad and depth.requires_grad and not unc.requires_grad
     with pytest.raises(RuntimeError):
         unc.sum().backward()
+
+
+def test_autotuner_keeps_the_default_within_the_margin():
+    """A candidate replaces the default only if it is faster by more than TUNE_MARGIN."""
+    m = gs.TUNE_MARGIN
+    assert gs._pick({"d": 1.0, "a": 1.0 / (1 + m / 2)}, "d") == "d"
+    assert gs._pick({"d": 1.0, "a": 1.0 / (1 + 2 * m)}, "d") == "a"
+    assert gs._pick({"a": 2.0, "b": 1.0}, "missing") == "b"
+
+
+def test_tile_and_camera_checks_mirror_the_library():
+    """The Python layer's tile and camera checks, which size the buffers, accept exactly what
+    the library's do (include/gs.h gs_params, GS_FLAG_BAD_CAMERA)."""
+    ok = {(w, h) for w in (8, 16, 32, 64) for h in range(8, 129, 8) if w * h in (64, 128, 256, 512, 1024)}
+    for w in range(0, 70):
+        for h in range(0, 140):
+            assert gs.valid_tile(w, h) == ((w, h) in ok), (w, h)
+    p = gs.RenderParams()
+    assert gs.camera_ok(Camera(100, 100, 60, 40, 120, 80), p)
+    assert not gs.camera_ok(Camera(-100, 100, 60, 40, 120, 80), p)
+    assert not gs.camera_ok(Camera(100, 0, 60, 40, 120, 80), p)
+    assert not gs.camera_ok(Camera(100, 100, 60, 40, 0, 80), p)
+    assert not gs.camera_ok(Camera(100, 100, 60, 40, 120, 80).with_tile(12, 8), p)
+    assert not gs.camera_ok(Camera(float("inf"), 100, 60, 40, 120, 80), p)
+
+
+def test_invalid_cameras_keep_their_pixels_and_lose_their_tiles():
+    cams = [Camera(100, 100, 60, 40, 120, 80), Camera(-100, 100, 60, 40, 64, 48),
+            Camera(100, 100, 60, 40, 0, 48), Camera(50, 50, 20, 15, 40, 30).with_tile(12, 8)]
+    tx, ty, tile_base, pix_base = gs.tile_grid(cams, gs.RenderParams())
+    assert list(tx * ty) == [8 * 5, 0, 0, 0]
+    assert list(np.diff(pix_base)) == [120 * 80, 64 * 48, 0, 40 * 30]
+    assert tile_base[-1] == 40
