@@ -17,8 +17,9 @@
 namespace gs {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;   // a multiple of 256 (the sort's digits)
 constexpr int kWarps = kThreads / 32;
+static_assert(kThreads % 256 == 0, "one thread per digit in the sort's digit loops");
 constexpr int kList = GS_SMALL_MAX_LIST;   // Gaussians of one tile that fit in shared memory
 
 struct SmallSmem {
@@ -78,16 +79,17 @@ __device__ bool locate_tile(const gs_camera* cams, int n_views, const gs_params&
 }
 
 // Stable LSD radix sort of the n (key, idx) pairs in buffer 0 by the 32 key bits (four
-// 8-bit passes, the result back in buffer 0).  Items are ranked in chunks of 256 in list
-// order: within a chunk by warp (lower warps first) and lane (warp match), across chunks
-// by a running count per digit, so equal keys keep their order.
+// 8-bit passes, the result back in buffer 0).  Items are ranked in chunks of kThreads in
+// list order: within a chunk by warp (lower warps first) and lane (warp match), across
+// chunks by a running count per digit, so equal keys keep their order.  Threads 0..255 own
+// one digit each in the digit loops.
 __device__ void sort_list(SmallSmem& s, int n) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   for (int pass = 0; pass < 4; ++pass) {
     const int shift = 8 * pass, src = pass & 1, dst = src ^ 1;
     // digit totals -> first slot of every digit
-    s.run[tid] = 0u;
+    if (tid < 256) s.run[tid] = 0u;
     __syncthreads();
     for (int i = tid; i < n; i += kThreads) atomicAdd(&s.run[(s.key[src][i] >> shift) & 0xffu], 1u);
     __syncthreads();
@@ -106,7 +108,7 @@ __device__ void sort_list(SmallSmem& s, int n) {
       for (int k = 0; k < 8; ++k) { s.base[lane * 8 + k] = e; e += v[k]; }
     }
     __syncthreads();
-    s.run[tid] = 0u;
+    if (tid < 256) s.run[tid] = 0u;
     for (int c0 = 0; c0 < n; c0 += kThreads) {
       for (int i = lane; i < 256; i += 32) s.cnt[warp][i] = 0u;
       __syncthreads();
@@ -125,10 +127,12 @@ __device__ void sort_list(SmallSmem& s, int n) {
         s.idx[dst][pos] = s.idx[src][i];
       }
       __syncthreads();
-      uint32_t add = 0;
+      if (tid < 256) {
+        uint32_t add = 0;
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) add += s.cnt[w][tid];
-      s.run[tid] += add;
+        for (int w = 0; w < kWarps; ++w) add += s.cnt[w][tid];
+        s.run[tid] += add;
+      }
       __syncthreads();
     }
   }
