@@ -157,17 +157,35 @@ __device__ inline int64_t lower_bound_u32(const uint32_t* __restrict__ poff, int
   return lo;
 }
 
-__device__ inline bool chunk_of(int64_t cid, int K, const uint32_t* __restrict__ seg,
-                                const uint32_t* __restrict__ poff, const uint32_t* __restrict__ view_info,
-                                int64_t tile_cap, Chunk& c) {
+// First record of every chunk: bounds[v (K + 1) + k] = the first sorted record of view v whose
+// first pair lies at or past P_v k / K (bounds[v (K + 1) + K] = the view's end).  One thread
+// per bound, so the binary searches run side by side instead of at the start of every warp
+// of the histogram and placement kernels.
+__global__ void k_chunk_bounds(const uint32_t* __restrict__ seg, const uint32_t* __restrict__ poff, int n_views,
+                               int K, uint32_t* __restrict__ bounds) {
+  const int64_t nb = (int64_t)n_views * (K + 1);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
+    const int v = (int)(i / (K + 1));
+    const int k = (int)(i - (int64_t)v * (K + 1));
+    int64_t s0 = seg[v], s1 = seg[v + 1];
+    if (s1 < s0) s1 = s0;
+    int64_t r = s1;
+    if (k < K) {
+      const int64_t a = poff[s0], b = poff[s1];
+      const int64_t P = b > a ? b - a : 0;
+      r = lower_bound_u32(poff, s0, s1, a + P * k / K);
+    }
+    bounds[i] = (uint32_t)r;
+  }
+}
+
+__device__ inline bool chunk_of(int64_t cid, int K, const uint32_t* __restrict__ bounds,
+                                const uint32_t* __restrict__ view_info, int64_t tile_cap, Chunk& c) {
   const int v = (int)(cid / K);
   c.k = (uint32_t)(cid - (int64_t)v * K);
-  int64_t s0 = seg[v], s1 = seg[v + 1];
-  if (s1 < s0) s1 = s0;
-  const int64_t a = poff[s0], b = poff[s1];
-  const int64_t P = b > a ? b - a : 0;
-  c.r0 = lower_bound_u32(poff, s0, s1, a + P * c.k / K);
-  c.r1 = c.k + 1 == (uint32_t)K ? s1 : lower_bound_u32(poff, s0, s1, a + P * (c.k + 1) / K);
+  const uint32_t* b = bounds + (size_t)v * (K + 1) + c.k;
+  c.r0 = b[0];
+  c.r1 = b[1];
   if (c.r1 < c.r0) c.r1 = c.r0;
   c.tile_base = view_info[kVI * v];
   c.n_tiles = view_info[kVI * (v + 1)] - c.tile_base;
@@ -191,16 +209,15 @@ __device__ inline void window_size(uint32_t tx, uint32_t ty, uint32_t cells, boo
 // Step 4: per chunk, the number of its pairs in every tile of its view:
 // cnt[K * global tile + k].  Each record adds the corners of its rectangle to a
 // 2D difference array; a 2D prefix sum turns it into per-tile counts.
-__global__ void __launch_bounds__(kBinWarps * 32) k_bin_hist(const gs_proj proj, const uint32_t* __restrict__ seg,
-                                                             const ushort4* __restrict__ srect,
-                                                             const uint32_t* __restrict__ poff, int n_views, int K,
+__global__ void __launch_bounds__(kBinWarps * 32) k_bin_hist(const gs_proj proj, const uint32_t* __restrict__ bounds,
+                                                             const ushort4* __restrict__ srect, int n_views, int K,
                                                              int64_t tile_cap, uint32_t* __restrict__ cnt) {
   __shared__ uint32_t s_d[kBinWarps][kWin];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t cid = (int64_t)blockIdx.x * kBinWarps + warp;
   if (cid >= (int64_t)n_views * K) return;
   Chunk c;
-  if (!chunk_of(cid, K, seg, poff, proj.view_info, tile_cap, c)) {
+  if (!chunk_of(cid, K, bounds, proj.view_info, tile_cap, c)) {
     // the tiles of a skipped view that lie under tile_cap are still scanned: zero counts
     for (int64_t t = lane; t < (int64_t)c.n_tiles && (int64_t)c.tile_base + t < tile_cap; t += 32)
       cnt[(size_t)K * (c.tile_base + t) + c.k] = 0u;
@@ -290,10 +307,10 @@ __global__ void k_bin_ranges(const uint32_t* __restrict__ off, const uint32_t* _
 // cell's running slot plus that rank, and the lowest of them advances the running
 // slot for the next round.
 template <bool kTileIds>
-__global__ void __launch_bounds__(kBinWarps * 32, 5) k_bin_place(const gs_proj proj, const uint32_t* __restrict__ seg,
+__global__ void __launch_bounds__(kBinWarps * 32, 5) k_bin_place(const gs_proj proj,
+                                                                 const uint32_t* __restrict__ bounds,
                                                                  const uint32_t* __restrict__ srec,
-                                                                 const ushort4* __restrict__ srect,
-                                                                 const uint32_t* __restrict__ poff, int n_views, int K,
+                                                                 const ushort4* __restrict__ srect, int n_views, int K,
                                                                  int64_t tile_cap, const uint32_t* __restrict__ off,
                                                                  gs_bins out) {
   __shared__ uint32_t s_run[kBinWarps][kPlaceWin];
@@ -304,7 +321,7 @@ __global__ void __launch_bounds__(kBinWarps * 32, 5) k_bin_place(const gs_proj p
   const int64_t cid = (int64_t)blockIdx.x * kBinWarps + warp;
   if (cid >= (int64_t)n_views * K) return;
   Chunk c;
-  if (!chunk_of(cid, K, seg, poff, proj.view_info, tile_cap, c)) return;
+  if (!chunk_of(cid, K, bounds, proj.view_info, tile_cap, c)) return;
   uint32_t* run = s_run[warp];
   uint4* grp = s_grp[warp];
   const uint32_t cap = out.pair_capacity < 0xFFFFFFFFll ? (uint32_t)out.pair_capacity : 0xFFFFFFFFu;
@@ -364,13 +381,18 @@ __global__ void __launch_bounds__(kBinWarps * 32, 5) k_bin_place(const gs_proj p
           grp[__popc(nz & lt)] = make_uint4(x0 | (y0 << 8) | (w << 17), excl, rec_g, magic);
         }
         __syncwarp();
-        uint32_t before = 0;   // records of the group whose first pair precedes this round
-        for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+        // The rounds are software-pipelined: the cell, record and same-cell lanes of round
+        // k0 + 32 (which read only the group table) are found while round k0 reads and
+        // advances the running slots, so the two dependency chains overlap.
+        uint32_t before = 0;   // records of the group whose first pair precedes the next round
+        auto cell_of = [&](uint32_t k0, bool& valid, uint32_t& i, uint32_t& peers, uint32_t& o_rec, uint32_t& cx,
+                           uint32_t& cy) {
           const uint32_t d = excl - k0;   // < 32 iff this lane's record starts in the round
           const uint32_t starts = __reduce_or_sync(0xffffffffu, (cnt > 0u && d < 32u) ? (1u << d) : 0u);
           const uint32_t k = k0 + lane;
-          const bool valid = k < total;
-          uint32_t i = 0xFFFFFFFFu, cy = 0, cx = 0, o_rec = 0;   // window cell, its row and column
+          valid = k < total;
+          i = 0xFFFFFFFFu;   // invalid lanes share this key and do nothing
+          cy = cx = o_rec = 0;
           if (valid) {
             const uint4 e = grp[before + __popc(starts & le) - 1u];   // the owner of pair k
             const uint32_t j = k - e.y;
@@ -382,21 +404,34 @@ __global__ void __launch_bounds__(kBinWarps * 32, 5) k_bin_place(const gs_proj p
             o_rec = e.z;
           }
           before += __popc(starts);
-          // lanes of the same cell (invalid lanes share the key 0xFFFFFFFF and do nothing)
-          const uint32_t peers = __match_any_sync(0xffffffffu, i);
-          const uint32_t below = peers & lt;
+          peers = __match_any_sync(0xffffffffu, i);   // lanes of the same window cell
+        };
+        bool vA;
+        uint32_t iA, pA, rA, xA, yA;
+        cell_of(0u, vA, iA, pA, rA, xA, yA);
+        for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+          bool vB = false;
+          uint32_t iB = 0xFFFFFFFFu, pB = 0u, rB = 0u, xB = 0u, yB = 0u;
+          if (k0 + 32u < total) cell_of(k0 + 32u, vB, iB, pB, rB, xB, yB);
+          const uint32_t below = pA & lt;
           uint32_t base = 0;
-          if (valid) {
-            base = run[i];
+          if (vA) {
+            base = run[iA];
             const uint32_t slot = base + __popc(below);
             if (slot < cap) {
-              out.rec[slot] = o_rec;
-              if (kTileIds) out.tile[slot] = c.tile_base + (ya + cy) * c.tiles_x + xa + cx;
+              out.rec[slot] = rA;
+              if (kTileIds) out.tile[slot] = c.tile_base + (ya + yA) * c.tiles_x + xa + xA;
             }
           }
           __syncwarp();
-          if (valid && below == 0u) run[i] = base + __popc(peers);   // lowest lane of the cell in this round
+          if (vA && below == 0u) run[iA] = base + __popc(pA);   // lowest lane of the cell in this round
           __syncwarp();
+          vA = vB;
+          iA = iB;
+          pA = pB;
+          rA = rB;
+          xA = xB;
+          yA = yB;
         }
       }
     }
@@ -420,6 +455,7 @@ size_t bin_ws_bytes(int64_t rec_cap, int64_t pair_cap, int64_t tile_cap, int n_v
   c.take<uint32_t>(rec_cap + 1);           // ... scanned: first pair of each sorted record
   c.take<uint32_t>(cnt_cap);               // per (tile, chunk) pair counts
   c.take<uint32_t>(cnt_cap);               // ... scanned
+  c.take<uint32_t>((int64_t)n_views * (K + 1));   // first sorted record of every chunk
   size_t t = sort_temp_bytes(rec_cap, n_views);
   size_t s = scan_temp_bytes(cnt_cap > rec_cap ? cnt_cap : rec_cap);
   c.take<char>(t > s ? t : s);
@@ -445,6 +481,7 @@ cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_vi
   uint32_t* poff = c.take<uint32_t>(rec_cap + 1);
   uint32_t* cnt = c.take<uint32_t>(cnt_cap);
   uint32_t* off = c.take<uint32_t>(cnt_cap);
+  uint32_t* bounds = c.take<uint32_t>((int64_t)n_views * (K + 1));
   size_t t = sort_temp_bytes(rec_cap, n_views);
   size_t s = scan_temp_bytes(cnt_cap > rec_cap ? cnt_cap : rec_cap);
   void* tmp = c.take<char>(t > s ? t : s);
@@ -470,10 +507,12 @@ cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_vi
   // 3. pair numbering
   e = scan_exclusive(rcnt, poff, proj.count, rec_cap, nullptr, tmp, st);
   if (e != cudaSuccess) return e;
-  // 4. per-chunk tile counts
+  // 4. chunk boundaries, per-chunk tile counts
+  k_chunk_bounds<<<grid_for((int64_t)n_views * (K + 1)), kBlock, 0, st>>>(seg, poff, n_views, K, bounds);
+  note_launch();
   const int64_t chunks = (int64_t)n_views * K;
   const unsigned bin_grid = (unsigned)((chunks + kBinWarps - 1) / kBinWarps);
-  k_bin_hist<<<bin_grid, kBinWarps * 32, 0, st>>>(proj, seg, srect, poff, n_views, K, tile_cap, cnt);
+  k_bin_hist<<<bin_grid, kBinWarps * 32, 0, st>>>(proj, bounds, srect, n_views, K, tile_cap, cnt);
   note_launch();
   // 5. slots of every (tile, chunk); ranges and totals
   e = scan_exclusive(cnt, off, &ctr[0], cnt_cap - 1, &ctr[1], tmp, st);
@@ -483,10 +522,9 @@ cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_vi
   note_launch();
   // 6. placement
   if (out.tile)
-    k_bin_place<true><<<bin_grid, kBinWarps * 32, 0, st>>>(proj, seg, srec, srect, poff, n_views, K, tile_cap, off, out);
+    k_bin_place<true><<<bin_grid, kBinWarps * 32, 0, st>>>(proj, bounds, srec, srect, n_views, K, tile_cap, off, out);
   else
-    k_bin_place<false><<<bin_grid, kBinWarps * 32, 0, st>>>(proj, seg, srec, srect, poff, n_views, K, tile_cap, off,
-                                                           out);
+    k_bin_place<false><<<bin_grid, kBinWarps * 32, 0, st>>>(proj, bounds, srec, srect, n_views, K, tile_cap, off, out);
   note_launch();
   return cudaGetLastError();
 }
