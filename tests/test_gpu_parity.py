@@ -141,6 +141,82 @@ def test_bin_sort_synthetic_records(n_gauss, max_extent, tie):
     _check_bins(fr, rec, cams)
 
 
+@pytest.mark.parametrize("span", [0, 1, (1 << 9) - 1, (1 << 27) - 1, 1 << 27, (1 << 31) + 12345, None])
+def test_bin_sort_key_span(span):
+    """Depth keys that span 0 bits (all equal), a few bits, 27 bits, just over 27 bits, 31
+    bits from a small base, or all 32 bits (None) give the oracle's pair lists bit for bit,
+    ties kept in record order: no pass of the sort may assume anything of the key range."""
+    cams = [Camera(100, 100, 60, 40, 120, 80), Camera(100, 100, 160, 120, 320, 240), Camera(50, 50, 8, 8, 17, 9)]
+    rec = scenes.synthetic_records(77, 4000, cams, max_extent=6, tie_frac=0.2)
+    rng = np.random.default_rng(5)
+    R = len(rec["gid"])
+    if span is None:
+        dkey = rng.integers(0, 1 << 32, R, dtype=np.uint64).astype(np.uint32)
+    else:
+        base = 0x3E4CCCCD if span < (1 << 31) else 0x1000
+        dkey = (base + rng.integers(0, span + 1, R, dtype=np.uint64)).astype(np.uint32)
+        dkey[: R // 5] = dkey[R // 5: 2 * (R // 5)]   # repeated keys (ties)
+        dkey[rng.integers(0, R)] = base
+        dkey[rng.integers(0, R)] = base + span
+        assert int(dkey.max()) - int(dkey.min()) == span
+    rec["dkey"] = dkey
+    fr = _bin_only(rec, cams)
+    _check_bins(fr, rec, cams)
+    fr.check_status()
+
+
+@pytest.mark.parametrize("span_bits", [26, 32])
+def test_bin_sort_large_batch_properties(span_bits):
+    """20M records over 8 views, so that sort partitions hold several 2,048-key tiles, as in
+    the 256-candidate batch.  The pair lists are fixed by two properties, checked on the
+    device: every record sits in exactly the tiles of its rectangle, once each, and every
+    tile's list is ordered by (depth key, record index); the ranges delimit the tiles."""
+    V, per = 8, 2_500_000
+    cams = [Camera(200, 200, 160, 120, 320, 240)] * V   # 20 x 15 tiles of 16 x 16
+    tx, ty = 20, 15
+    rng = np.random.default_rng(11 + span_bits)
+    R = V * per
+    w = rng.integers(1, 4, R)
+    h = rng.integers(1, 4, R)
+    x0 = (rng.random(R) * (tx - w + 1)).astype(np.int64)
+    y0 = (rng.random(R) * (ty - h + 1)).astype(np.int64)
+    if span_bits == 32:
+        dkey = rng.integers(0, 1 << 32, R, dtype=np.uint64).astype(np.uint32)
+    else:
+        dkey = (0x3E4CCCCD + rng.integers(0, 1 << span_bits, R, dtype=np.uint64)).astype(np.uint32)
+    dst = rng.integers(0, R, R // 10)
+    dkey[dst] = dkey[rng.integers(0, R, R // 10)]          # equal keys
+    rec = dict(gid=np.tile(np.arange(per, dtype=np.uint32), V), view=np.repeat(np.arange(V, dtype=np.uint32), per),
+               rect=np.stack([x0, y0, x0 + w, y0 + h], 1).astype(np.int32), dkey=dkey)
+    fr = _bin_only(rec, cams, pair_capacity=12 * R)
+    fr.check_status()
+    dev = fr.device
+    P = int(fr.pair_count[0].item())
+    assert P == int((w * h).sum())
+    i64 = lambda t: t.to(torch.int64) & 0xFFFFFFFF
+    tile = i64(fr.pair_tile[:P])
+    r = i64(fr.pair_rec[:P])
+    view = torch.from_numpy(rec["view"].astype(np.int64)).to(dev)
+    rect = torch.from_numpy(rec["rect"].astype(np.int64)).to(dev)
+    key = torch.from_numpy(dkey.astype(np.int64)).to(dev)
+    local = tile - view[r] * (tx * ty)
+    assert bool(((local >= 0) & (local < tx * ty)).all())
+    cx, cy = local % tx, local // tx
+    rr = rect[r]
+    assert bool(((cx >= rr[:, 0]) & (cx < rr[:, 2]) & (cy >= rr[:, 1]) & (cy < rr[:, 3])).all())
+    area = (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1])
+    assert torch.equal(torch.bincount(r, minlength=R), area)
+    assert torch.unique(r * (V * tx * ty) + tile).numel() == P       # no (record, tile) twice
+    same = tile[1:] == tile[:-1]
+    assert bool((tile[1:] >= tile[:-1]).all())
+    k0, k1 = key[r[:-1]], key[r[1:]]
+    assert bool((~same | (k1 > k0) | ((k1 == k0) & (r[1:] > r[:-1]))).all())
+    cnt = torch.bincount(tile, minlength=V * tx * ty)
+    ranges = i64(fr.ranges.reshape(-1)[:V * tx * ty * 2]).reshape(-1, 2)
+    ends = torch.cumsum(cnt, 0)
+    assert torch.equal(ranges[:, 1], ends) and torch.equal(ranges[:, 0], ends - cnt)
+
+
 def test_bin_sort_empty_and_overflow():
     cams = [Camera(100, 100, 60, 40, 120, 80)]
     rec = dict(gid=np.zeros(0, np.uint32), view=np.zeros(0, np.uint32), rect=np.zeros((0, 4), np.int32),
