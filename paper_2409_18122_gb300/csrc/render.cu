@@ -20,6 +20,7 @@ namespace {
 
 constexpr int kFwdWarps = 2;   // warps (work items) per CTA: small CTAs free their slot as soon as both finish
 constexpr int kIgWarps = 8;    // warps per CTA of the persistent information-gain kernel
+constexpr int kIgRing = 64;    // staged entries per warp of the information-gain kernel (a ring)
 constexpr int kPix = 1;        // pixels per lane of the forward and information-gain kernels
 // Chunk depth: overlapping entries whose alphas are computed together, a template argument
 // of both compositing kernels chosen per launch by gs_params (forward 1, 2 or 4, default 2;
@@ -178,6 +179,42 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 12) k_render_fwd(gs_map map, g
   }
 }
 
+// Composites `chunks` whole chunks of kIgBatch staged entries, starting at ring position
+// `head` (a multiple of kIgBatch, so no chunk wraps): the alphas of a chunk are independent
+// and computed together, the transmittance updates then run in list order.  A lane leaves
+// as soon as its pixel is saturated.
+template <int kIgBatch>
+__device__ __forceinline__ void composite_chunks(const float4* sm, const float4* sc, uint32_t head, uint32_t chunks,
+                                                 float pxc, const float* pyc, const gs_params& p, float* T,
+                                                 float* cu) {
+  for (uint32_t c = 0; c < chunks && live<kPix>(T); ++c) {
+    const uint32_t b0 = (head + c * kIgBatch) & (kIgRing - 1);
+    float al[kIgBatch][kPix], uu[kIgBatch];
+#pragma unroll
+    for (int k = 0; k < kIgBatch; ++k) {
+      const float4 mu = sm[b0 + k];
+      const float4 kk = sc[b0 + k];
+      uu[k] = mu.z;
+#pragma unroll
+      for (int q = 0; q < kPix; ++q)
+        al[k][q] = splat_alpha_lo(mu.x, mu.y, make_float3(kk.x, kk.y, kk.z), mu.w, pxc, pyc[q], p.alpha_max);
+    }
+#pragma unroll
+    for (int k = 0; k < kIgBatch; ++k) {
+#pragma unroll
+      for (int q = 0; q < kPix; ++q) {
+        const float alpha = al[k][q];
+        if (alpha < p.alpha_min) continue;
+        const float w = T[q] * alpha;   // T (1 - alpha) taken as T - w: one instruction less
+        const float Tn = T[q] - w;
+        if (Tn < p.T_min) { T[q] = 0.f; continue; }
+        cu[q] += w * uu[k];
+        T[q] = Tn;
+      }
+    }
+  }
+}
+
 // Persistent U-only compositing: every warp takes (tile, pixel block) work items
 // from a device counter, longest tile list first, until the batch is exhausted,
 // and writes the sum of U over its pixels to the item's own slot (fixed shuffle
@@ -188,7 +225,9 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
                                                              gs_params p, const uint32_t* __restrict__ order,
                                                              float* __restrict__ item_sum, int64_t item_cap,
                                                              uint32_t* __restrict__ work) {
-  __shared__ float4 s_stage[kIgWarps][2][32];   // (mu_x, mu_y, u, -), (a, b, c, o)
+  // staged entries of each warp, a ring of kIgRing: (mu_x, mu_y, u, log2 o), scaled conic
+  __shared__ float4 s_stage[kIgWarps][2][kIgRing];
+  static_assert(kIgRing % kIgBatch == 0 && kIgRing >= 32 + kIgBatch, "ring holds a group plus a partial chunk");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   float4* sm = s_stage[warp][0];
@@ -234,6 +273,7 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
     bool ovA = (uint32_t)lane < n && box_overlaps(mA, wb);
     float4 cA = z4;
     if (ovA) cA = __ldg(SP + 2 * (size_t)rA + 1);
+    uint32_t head = 0, tail = 0;   // ring entries [head, tail) are staged and not yet composited
     for (uint32_t g = 0; g < n; g += 32) {
       if (!__any_sync(0xffffffffu, live<kPix>(T))) break;
       const bool ovB = g + 32 + lane < n && box_overlaps(mB, wb);
@@ -246,53 +286,35 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
       ovA = ovA && ellipse_reaches(mA, cA, wb, ln_amin);
       const uint32_t m = __ballot_sync(0xffffffffu, ovA);
       if (m) {
-        // the overlapping entries, compacted in list order: (mu, u, log2 o), scaled conic;
-        // padded to whole batches with entries of log2 o = -inf (alpha = 0: adds nothing)
-        const int n_ov = __popc(m);
-        const int n_pad = (n_ov + kIgBatch - 1) / kIgBatch * kIgBatch;
+        // the overlapping entries join the ring in list order; whole chunks of kIgBatch
+        // are composited at once and a partial chunk waits for the next group's entries
         if (ovA) {
-          const int s = __popc(m & lt);
+          const uint32_t s = (tail + __popc(m & lt)) & (kIgRing - 1);
           const float3 k2 = scaled_conic(cA);
           sm[s] = make_float4(mA.x, mA.y, mA.w, __log2f(cA.w));
           sc[s] = make_float4(k2.x, k2.y, k2.z, 0.f);
         }
-        if (lane >= n_ov && lane < n_pad) {   // slots [n_ov, n_pad): disjoint from the staged ones
-          sm[lane] = make_float4(0.f, 0.f, 0.f, -INFINITY);
-          sc[lane] = z4;
-        }
+        tail += __popc(m);
         __syncwarp();
-        // kIgBatch entries at a time: their alphas are independent and computed
-        // together; the transmittance updates then run in list order
-        for (int i0 = 0; i0 < n_ov && live<kPix>(T); i0 += kIgBatch) {
-          float al[kIgBatch][kPix], uu[kIgBatch];
-#pragma unroll
-          for (int k = 0; k < kIgBatch; ++k) {
-            const float4 mu = sm[i0 + k];
-            const float4 kk = sc[i0 + k];
-            uu[k] = mu.z;
-#pragma unroll
-            for (int q = 0; q < kPix; ++q)
-              al[k][q] = splat_alpha_lo(mu.x, mu.y, make_float3(kk.x, kk.y, kk.z), mu.w, pxc, pyc[q], p.alpha_max);
-          }
-#pragma unroll
-          for (int k = 0; k < kIgBatch; ++k) {
-#pragma unroll
-            for (int q = 0; q < kPix; ++q) {
-              const float alpha = al[k][q];
-              if (alpha < p.alpha_min) continue;
-              const float w = T[q] * alpha;   // T (1 - alpha) taken as T - w: one instruction less
-              const float Tn = T[q] - w;
-              if (Tn < p.T_min) { T[q] = 0.f; continue; }
-              cu[q] += w * uu[k];
-              T[q] = Tn;
-            }
-          }
-        }
+        const uint32_t chunks = (tail - head) / kIgBatch;
+        composite_chunks<kIgBatch>(sm, sc, head, chunks, pxc, pyc, p, T, cu);
+        head += chunks * kIgBatch;
         __syncwarp();
       }
       mA = mB; ovA = ovB; cA = cB;
       rB = rC; mB = mC;
       rC = rD;
+    }
+    // the last partial chunk, padded with entries of log2 o = -inf (alpha = 0: adds nothing)
+    if (tail != head && __any_sync(0xffffffffu, live<kPix>(T))) {
+      const uint32_t b0 = head & (kIgRing - 1);
+      if ((uint32_t)lane >= tail - head && (uint32_t)lane < kIgBatch) {
+        sm[b0 + lane] = make_float4(0.f, 0.f, 0.f, -INFINITY);
+        sc[b0 + lane] = z4;
+      }
+      __syncwarp();
+      composite_chunks<kIgBatch>(sm, sc, head, 1u, pxc, pyc, p, T, cu);
+      __syncwarp();
     }
     float su = 0.f;
 #pragma unroll
