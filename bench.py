@@ -316,7 +316,7 @@ class IGStep:
         self.params = gs.RenderParams(ig_batch=int(batch or 0))
         self.frame = gs.Frame(self.gm.n, cams, self.params, pair_capacity=pair_capacity, with_color=False,
                               with_pair_tiles=False, record_capacity=record_capacity, with_gid=False,
-                              with_view=False)
+                              with_view=False, with_item_order=False)
         while True:
             self.frame.reset_status()
             self.frame.project(self.gm)

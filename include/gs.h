@@ -196,6 +196,13 @@ gs_status gs_project(const gs_map* map, const gs_camera* cams, int32_t n_views, 
  *   tile    [pair_capacity]   global tile id of each pair, ascending; may be NULL (not written)
  *   rec     [pair_capacity]   record index of each pair
  *   ranges  [tile_capacity][2] per global tile: [start, end) into tile/rec, clipped to pair_capacity
+ *   item_order [item_capacity] optional, may be NULL: the batch's warp items (32-pixel blocks
+ *           of tiles, tile_w * tile_h / 32 per tile, numbered view by view, tile by tile,
+ *           block by block) longest tile list first.  The lists are bucketed by length
+ *           (four buckets per doubling); the order inside a bucket is unspecified.
+ *           gs_bin_sort writes it when the batch has at most item_capacity items, and
+ *           gs_render_fwd / gs_render_bwd then take their items in this order, so that the
+ *           longest lists do not start last.  Any order gives the same outputs.
  * Global tile id of tile (x, y) of view v = view_info[v].first_tile + y * tiles_x(v) + x,
  * tiles_x(v) = ceil(W_v / tile_w(v)), tiles_y(v) = ceil(H_v / tile_h(v)) with the
  * view's tile size (its camera's, else gs_params'); a view whose camera is invalid
@@ -207,6 +214,8 @@ typedef struct {
   uint32_t* tile;
   uint32_t* rec;
   uint32_t* ranges;
+  uint32_t* item_order;
+  int64_t item_capacity;
 } gs_bins;
 
 /* gs_bin_sort -- Sec. III "sorted in increasing order of depth": emits one pair

@@ -58,7 +58,7 @@ class gs_proj(ctypes.Structure):
 
 class gs_bins(ctypes.Structure):
     _fields_ = [("pair_capacity", c_int64), ("tile_capacity", c_int64), ("count", c_void_p), ("tile", c_void_p),
-                ("rec", c_void_p), ("ranges", c_void_p)]
+                ("rec", c_void_p), ("ranges", c_void_p), ("item_order", c_void_p), ("item_capacity", c_int64)]
 
 
 class gs_utility_params(ctypes.Structure):
@@ -96,6 +96,7 @@ class gs_map_grad(ctypes.Structure):
 
 assert ctypes.sizeof(gs_camera) == 80
 assert ctypes.sizeof(gs_params) == 40
+assert ctypes.sizeof(gs_bins) == 64
 
 # name -> (restype, argtypes); the exported C ABI
 PROTOTYPES = {

@@ -78,6 +78,8 @@ gs_status check_bins(const gs_bins* b) {
   if (b->tile_capacity < 1 || b->tile_capacity >= ((int64_t)1 << 27)) return GS_ERR_ARG;
   if (!b->count || !b->rec || !b->ranges) return GS_ERR_NULL;   // tile may be NULL
   if (!aligned(b->count, 4) || !aligned(b->tile, 4) || !aligned(b->rec, 4) || !aligned(b->ranges, 8)) return GS_ERR_ALIGN;
+  if (b->item_order && (b->item_capacity < 0 || b->item_capacity >= ((int64_t)1 << 32))) return GS_ERR_ARG;
+  if (!aligned(b->item_order, 4)) return GS_ERR_ALIGN;
   return GS_OK;
 }
 

@@ -438,6 +438,95 @@ __global__ void __launch_bounds__(kBinWarps * 32, 5) k_bin_place(const gs_proj p
   }
 }
 
+// ---------------------------------------------------------------- item order
+// The warp items of the batch (32-pixel blocks of tiles; view_info[v][2] is the first item
+// of view v) ordered longest tile list first, by a counting sort over kOrderBuckets buckets
+// of list length, four per doubling.  The compositing kernels take their items in this
+// order, so that the longest lists start first instead of wherever their tile falls.
+constexpr int kOrderBuckets = 64;
+
+// Bucket of a list of `len` pairs: 0 for the longest lists.
+__device__ inline uint32_t order_bucket(uint32_t len) {
+  uint32_t key = 0;   // non-decreasing in len
+  if (len) {
+    const uint32_t lg = 31u - __clz(len);
+    const uint32_t two = lg >= 2u ? (len >> (lg - 2u)) & 3u : (len << (2u - lg)) & 3u;
+    key = 4u * lg + two;
+    if (key > (uint32_t)kOrderBuckets - 1u) key = kOrderBuckets - 1u;
+  }
+  return (uint32_t)kOrderBuckets - 1u - key;
+}
+
+// Pairs in the tile list of warp item i (0 for a view without tiles or a tile past tile_cap).
+__device__ inline uint32_t item_list_len(uint32_t i, const uint32_t* __restrict__ view_info, int n_views,
+                                         const uint32_t* __restrict__ ranges, int64_t tile_cap) {
+  const int v = find_view(view_info, n_views, i, 2);
+  const uint32_t code = view_info[kVI * v + 3];
+  const uint32_t wpt = ((code & 0xffu) * ((code >> 8) & 0xffu)) / 32u;   // items per tile
+  if (!wpt) return 0u;
+  const uint32_t tile = view_info[kVI * v] + (i - view_info[kVI * v + 2]) / wpt;
+  if ((int64_t)tile >= tile_cap) return 0u;
+  return ranges[2 * (size_t)tile + 1] - ranges[2 * (size_t)tile];
+}
+
+__global__ void k_order_zero(uint32_t* __restrict__ cnt) {   // counts and cursors
+  for (int i = threadIdx.x; i < 2 * kOrderBuckets; i += blockDim.x) cnt[i] = 0u;
+}
+
+// Items per bucket (nothing when the batch has more than item_cap items).
+__global__ void __launch_bounds__(kBlock) k_order_count(const uint32_t* __restrict__ view_info, int n_views,
+                                                        const uint32_t* __restrict__ ranges, int64_t tile_cap,
+                                                        int64_t item_cap, uint32_t* __restrict__ cnt) {
+  __shared__ uint32_t s_cnt[kOrderBuckets];
+  for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) s_cnt[i] = 0u;
+  __syncthreads();
+  const int64_t n = view_info[kVI * n_views + 2];
+  if (n <= item_cap) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+      atomicAdd(&s_cnt[order_bucket(item_list_len((uint32_t)i, view_info, n_views, ranges, tile_cap))], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x)
+    if (s_cnt[i]) atomicAdd(&cnt[i], s_cnt[i]);
+}
+
+// Every item to its bucket's next free position; one atomic per (warp, bucket).
+__global__ void __launch_bounds__(kBlock) k_order_place(const uint32_t* __restrict__ view_info, int n_views,
+                                                        const uint32_t* __restrict__ ranges, int64_t tile_cap,
+                                                        int64_t item_cap, const uint32_t* __restrict__ cnt,
+                                                        uint32_t* __restrict__ cur, uint32_t* __restrict__ order) {
+  __shared__ uint32_t s_base[kOrderBuckets];
+  const int64_t n = view_info[kVI * n_views + 2];
+  if (n > item_cap) return;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {   // exclusive scan of the bucket counts, two per lane
+    const uint32_t a = cnt[2 * lane], b = cnt[2 * lane + 1];
+    uint32_t x = a + b;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
+    }
+    s_base[2 * lane] = x - a - b;
+    s_base[2 * lane + 1] = x - b;
+  }
+  __syncthreads();
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w0 = wid * 32; w0 < n; w0 += n_warps * 32) {   // warp-uniform loop
+    const int64_t i = w0 + lane;
+    const bool ok = i < n;
+    const uint32_t b = ok ? order_bucket(item_list_len((uint32_t)i, view_info, n_views, ranges, tile_cap))
+                          : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(peers) - 1;
+    uint32_t pos = 0;
+    if (ok && lane == leader) pos = atomicAdd(&cur[b], (uint32_t)__popc(peers));
+    pos = __shfl_sync(0xffffffffu, pos, leader);
+    if (ok) order[s_base[b] + pos + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
+  }
+}
+
 }  // namespace
 
 size_t bin_ws_bytes(int64_t rec_cap, int64_t pair_cap, int64_t tile_cap, int n_views) {
@@ -456,6 +545,7 @@ size_t bin_ws_bytes(int64_t rec_cap, int64_t pair_cap, int64_t tile_cap, int n_v
   c.take<uint32_t>(cnt_cap);               // per (tile, chunk) pair counts
   c.take<uint32_t>(cnt_cap);               // ... scanned
   c.take<uint32_t>((int64_t)n_views * (K + 1));   // first sorted record of every chunk
+  c.take<uint32_t>(2 * kOrderBuckets);            // item order: bucket counts and cursors
   size_t t = sort_temp_bytes(rec_cap, n_views);
   size_t s = scan_temp_bytes(cnt_cap > rec_cap ? cnt_cap : rec_cap);
   c.take<char>(t > s ? t : s);
@@ -482,6 +572,7 @@ cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_vi
   uint32_t* cnt = c.take<uint32_t>(cnt_cap);
   uint32_t* off = c.take<uint32_t>(cnt_cap);
   uint32_t* bounds = c.take<uint32_t>((int64_t)n_views * (K + 1));
+  uint32_t* ocnt = c.take<uint32_t>(2 * kOrderBuckets);
   size_t t = sort_temp_bytes(rec_cap, n_views);
   size_t s = scan_temp_bytes(cnt_cap > rec_cap ? cnt_cap : rec_cap);
   void* tmp = c.take<char>(t > s ? t : s);
@@ -526,6 +617,17 @@ cudaError_t launch_bin_sort(const gs_proj& proj, const gs_camera* cams, int n_vi
   else
     k_bin_place<false><<<bin_grid, kBinWarps * 32, 0, st>>>(proj, bounds, srec, srect, n_views, K, tile_cap, off, out);
   note_launch();
+  // 7. warp items longest tile list first, for the compositing kernels (optional)
+  if (out.item_order && out.item_capacity > 0) {
+    k_order_zero<<<1, 2 * kOrderBuckets, 0, st>>>(ocnt);
+    note_launch();
+    const unsigned og = grid_for(out.item_capacity);
+    k_order_count<<<og, kBlock, 0, st>>>(proj.view_info, n_views, out.ranges, tile_cap, out.item_capacity, ocnt);
+    note_launch();
+    k_order_place<<<og, kBlock, 0, st>>>(proj.view_info, n_views, out.ranges, tile_cap, out.item_capacity, ocnt,
+                                         ocnt + kOrderBuckets, out.item_order);
+    note_launch();
+  }
   return cudaGetLastError();
 }
 

@@ -43,8 +43,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 12) k_render_fwd(gs_map map, g
   __shared__ float4 s_stage[kFwdWarps][3][32];   // (mu_x, mu_y, u, -), (a, b, c, o), (r, g, b, depth)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
-  const uint32_t item = blockIdx.x * kFwdWarps + warp;
+  uint32_t item = blockIdx.x * kFwdWarps + warp;
   if (item >= n_items) return;
+  static_assert(kPix == 1, "the binning's item order numbers 32-pixel blocks");
+  item = ordered_item(bins, proj.view_info, n_views, item);
   TileInfo ti;
   if (!warp_item_setup<kPix>(proj, bins, cams, n_views, item, ti)) return;
   WarpBlock wb;
@@ -500,6 +502,8 @@ cudaError_t launch_info_gain(const gs_map& map, const gs_camera* cams, int n_vie
   bins.tile = nullptr;   // compositing needs only the record of each pair and the ranges
   bins.rec = c.take<uint32_t>(pair_cap);
   bins.ranges = c.take<uint32_t>(2 * tile_cap);
+  bins.item_order = nullptr;   // the compositing orders its items by exact list length itself
+  bins.item_capacity = 0;
   size_t a = project_ws_bytes(map.n, n_views), b = bin_ws_bytes(rec_cap, pair_cap, tile_cap, n_views);
   const size_t o = ig_composite_ws_bytes(tile_cap);
   void* inner = c.take<char>(a > b ? (a > o ? a : o) : (b > o ? b : o));

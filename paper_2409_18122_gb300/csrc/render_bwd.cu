@@ -65,8 +65,9 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
   static_assert(kPix == 1, "the entry body below is written for one pixel per lane");
   __shared__ uint32_t s_rec[kBwdWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t item = blockIdx.x * kBwdWarps + warp;
+  uint32_t item = blockIdx.x * kBwdWarps + warp;
   if (item >= n_items) return;
+  item = ordered_item(bins, proj.view_info, n_views, item);   // longest tile lists first
   TileInfo ti;
   if (!warp_item_setup<kPix>(proj, bins, cams, n_views, item, ti)) return;
   WarpBlock wb;

@@ -140,6 +140,16 @@ __device__ __forceinline__ bool warp_item_setup(const gs_proj& proj, const gs_bi
   return ti.valid;
 }
 
+// The warp item that work slot i renders: the binning's longest-list-first order when it
+// was written (gs_bin_sort writes bins.item_order when the batch has at most item_capacity
+// items of 32 pixels), else slot i itself.  Any order gives the same pixels.
+__device__ __forceinline__ uint32_t ordered_item(const gs_bins& bins, const uint32_t* view_info, int n_views,
+                                                 uint32_t i) {
+  if (!bins.item_order) return i;
+  const uint32_t n = view_info[kVI * n_views + 2];
+  return ((int64_t)n <= bins.item_capacity && i < n) ? bins.item_order[i] : i;
+}
+
 template <int KP>
 __device__ __forceinline__ void warp_block(const TileInfo& ti, WarpBlock& wb) {
   const int lane = threadIdx.x & 31;

@@ -190,14 +190,17 @@ class Frame:
     out the global tile id of every pair (compositing needs only the ranges);
     with_gid=False leaves out the Gaussian id of every record (the kernels never read it);
     with_view=False leaves out the view id of every record (binning then finds each view's
-    records through the projection's group offsets).
+    records through the projection's group offsets).  with_item_order=False leaves out the
+    binning's longest-list-first order of the warp items (the render kernels then take
+    their items tile by tile; the outputs are the same).
     """
 
     def __init__(self, n: int, cams: Sequence, params: RenderParams = RenderParams(),
                  pair_capacity: Optional[int] = None, device="cuda", with_color: bool = True,
                  with_pair_tiles: bool = True, record_capacity: Optional[int] = None, with_gid: bool = True,
-                 with_view: bool = True):
+                 with_view: bool = True, with_item_order: bool = True):
         self.device = torch.device(device)
+        self.with_item_order = with_item_order
         self.params = params
         self.with_color = with_color
         self.with_gid = with_gid
@@ -210,6 +213,11 @@ class Frame:
         self.tiles_x, self.tiles_y, self.tile_base, self.pix_base = tile_grid(self.cams, params)
         self.n_tiles = int(self.tile_base[-1])
         self.n_pixels = int(self.pix_base[-1])
+        # warp items: 32-pixel blocks, tile_w * tile_h / 32 per tile
+        self.n_items = 0
+        for v in range(self.V):
+            tw, th = self.view_tile(v)
+            self.n_items += int(self.tiles_x[v] * self.tiles_y[v]) * tw * th // 32
         # records: at most n * V; a smaller capacity (large batches) grows on overflow
         self.rec_capacity = max(int(record_capacity) if record_capacity else self.n * self.V, 1)
         # bumped by every projection and binning: the backward pass replays the records and tile
@@ -241,6 +249,7 @@ class Frame:
         self.pair_tile = _alloc_u32(pair_capacity, d) if self.with_pair_tiles else None
         self.pair_rec = _alloc_u32(pair_capacity, d)
         self.ranges = torch.zeros((max(self.n_tiles, 1), 2), dtype=torch.int32, device=d)
+        self.item_order = _alloc_u32(self.n_items, d) if self.with_item_order else None
         ws = max(L.workspace_size(L.GS_OP_PROJECT, self.n, self.V),
                  L.workspace_size(L.GS_OP_BIN_SORT, self.n, self.V, rc, pair_capacity, max(self.n_tiles, 1)),
                  L.workspace_size(L.GS_OP_RENDER_BWD, self.n, self.V, rc))
@@ -249,7 +258,8 @@ class Frame:
                                 _ptr(self.view), _ptr(self.splat), _ptr(self.color_d), _ptr(self.rect),
                                 _ptr(self.depth_key), _ptr(self.grp_mask), _ptr(self.grp_base))
         self.c_bins = L.gs_bins(pair_capacity, max(self.n_tiles, 1), _ptr(self.pair_count), _ptr(self.pair_tile),
-                                _ptr(self.pair_rec), _ptr(self.ranges))
+                                _ptr(self.pair_rec), _ptr(self.ranges), _ptr(self.item_order),
+                                self.n_items if self.with_item_order else 0)
         self.c_params = self.params.c()
 
     def view_tile(self, v: int):

@@ -126,6 +126,12 @@ def test_host_side_argument_errors(lib):
     # bins capacity
     bins = L.gs_bins(0, 10, fake, fake, fake, fake)
     assert lib.gs_bin_sort(P(proj), fake, 1, P(prm), P(bins), fake, 1 << 30, None) == L.GS_ERR_ARG
+    # the optional item order: aligned, with a capacity in [0, 2^32)
+    bins = L.gs_bins(100, 10, fake, fake, fake, fake, ctypes.c_void_p(0x10002), 50)
+    assert lib.gs_bin_sort(P(proj), fake, 1, P(prm), P(bins), fake, 1 << 30, None) == L.GS_ERR_ALIGN
+    for cap in (-1, 1 << 32):
+        bins = L.gs_bins(100, 10, fake, fake, fake, fake, fake, cap)
+        assert lib.gs_bin_sort(P(proj), fake, 1, P(prm), P(bins), fake, 1 << 30, None) == L.GS_ERR_ARG
     # images: a misaligned output, saved image or image gradient is refused before any launch
     bins = L.gs_bins(100, 10, fake, fake, fake, fake)
     odd = ctypes.c_void_p(0x10002)

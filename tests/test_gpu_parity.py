@@ -307,6 +307,45 @@ def test_render_room_crop_ragged_tiles():
     compare_image(gpu, ref, "room crop", check_last=last_gid(fr, [gpu])[0])
 
 
+def test_item_order_longest_first_and_outputs_unchanged():
+    """gs_bin_sort's optional item order is a permutation of the warp items whose tile lists
+    never lengthen by more than a bucket (four per doubling) from one item to the next, and
+    the forward images and the adjoint are the same with and without it (bit for bit for the
+    images; the gradients up to the order of their atomic additions)."""
+    sc = scenes.config2(n=40_000, n_views=3)
+    cams = [sc.cams[0], sc.cams[1].crop(100, 60, 330, 250), sc.cams[2].with_tile(8, 8)]
+    gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
+    out = {}
+    for ordered in (True, False):
+        fr = gs.Frame(gm.n, cams, with_item_order=ordered, pair_capacity=1 << 23)
+        img = fr.forward(gm)
+        d_rgb = torch.linspace(-1, 1, 3 * fr.n_pixels, device="cuda")
+        d_dep = torch.linspace(0.5, -0.5, fr.n_pixels, device="cuda")
+        grads = fr.render_bwd(gm, img, d_rgb, d_dep)
+        torch.cuda.synchronize()
+        fr.check_status()
+        out[ordered] = (fr, {k: v.clone() for k, v in img.items() if v is not None},
+                        {k: v.cpu().numpy() for k, v in grads.items()})
+    fr = out[True][0]
+    order = fr.item_order[:fr.n_items].cpu().numpy().view(np.uint32).astype(np.int64)
+    np.testing.assert_array_equal(np.sort(order), np.arange(fr.n_items))
+    # list length of every item, from the tile grid and the ranges
+    ranges = fr.ranges.cpu().numpy().view(np.uint32).astype(np.int64)
+    lens = []
+    for v in range(fr.V):
+        tw, th = fr.view_tile(v)
+        tiles = np.arange(int(fr.tile_base[v]), int(fr.tile_base[v + 1]))
+        lens.append(np.repeat(ranges[tiles, 1] - ranges[tiles, 0], tw * th // 32))
+    lens = np.concatenate(lens)[order]
+    lg = np.floor(np.log2(np.maximum(lens, 1))).astype(np.int64)
+    two = np.where(lg >= 2, (lens >> np.maximum(lg - 2, 0)) & 3, (lens << np.maximum(2 - lg, 0)) & 3)
+    key = np.where(lens > 0, np.minimum(4 * lg + two, 63), 0)
+    assert (np.diff(key) <= 0).all(), "buckets must not grow along the order"
+    for k in out[True][1]:
+        assert torch.equal(out[True][1][k], out[False][1][k]), k
+    compare_grads(out[True][2], {k: v.astype(np.float64) for k, v in out[False][2].items()}, what="ordered vs tile order")
+
+
 def test_per_view_tile_sizes_match_oracle():
     """Views with their own tile sizes (8x8, 16x16, 32x8) in one batch: bit-exact binning, images within tolerance."""
     sc = scenes.config2(n=30_000, n_views=3)
