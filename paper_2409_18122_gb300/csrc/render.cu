@@ -276,8 +276,22 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
     float4 cA = z4;
     if (ovA) cA = __ldg(SP + 2 * (size_t)rA + 1);
     uint32_t head = 0, tail = 0;   // ring entries [head, tail) are staged and not yet composited
+    static_assert(kPix == 1, "the live-pixel box below assumes one pixel per lane");
+    const float bx_full = wb.bx0, by_full = wb.by0;   // centre of the block's first pixel
     for (uint32_t g = 0; g < n; g += 32) {
-      if (!__any_sync(0xffffffffu, live<kPix>(T))) break;
+      const uint32_t lm = __ballot_sync(0xffffffffu, live<kPix>(T));
+      if (!lm) break;
+      // the culls below test the bounding box of the block's live pixels (lane l holds pixel
+      // (l mod 8, l div 8)): an entry that reaches only saturated pixels adds nothing
+      {
+        const uint32_t cols = (lm | (lm >> 8) | (lm >> 16) | (lm >> 24)) & 0xFFu;
+        const uint32_t rows = ((lm & 0xFFu) ? 1u : 0u) | ((lm & 0xFF00u) ? 2u : 0u) |
+                              ((lm & 0xFF0000u) ? 4u : 0u) | ((lm & 0xFF000000u) ? 8u : 0u);
+        wb.bx0 = bx_full + (float)(__ffs(cols) - 1);
+        wb.bx1 = bx_full + (float)(31 - __clz(cols));
+        wb.by0 = by_full + (float)(__ffs(rows) - 1);
+        wb.by1 = by_full + (float)(31 - __clz(rows));
+      }
       const bool ovB = g + 32 + lane < n && box_overlaps(mB, wb);
       float4 cB = z4;
       if (ovB) cB = __ldg(SP + 2 * (size_t)rB + 1);
