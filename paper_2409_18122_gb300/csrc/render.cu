@@ -181,38 +181,54 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 12) k_render_fwd(gs_map map, g
   }
 }
 
+// Per-lane constants of the information-gain exponent: the lane's pixel centre relative to
+// the centre of its 8x4 block, (u, v), and u^2, u v, v^2.
+struct LaneOffsets {
+  float u, v, uu, uv, vv;
+};
+
+// Staged form of an entry for the information-gain kernel.  With (ex, ey) = mean - block
+// centre and k = the scaled conic, the exponent of alpha = 2^pw at the lane's pixel is
+//   pw = k.x (ex - u)^2 + k.y (ex - u)(ey - v) + k.z (ey - v)^2 + log2 o
+//      = C0 + Cu u + Cv v + k.x u^2 + k.y u v + k.z v^2,
+// so the staging lane computes C0, Cu, Cv once per entry and every pixel takes five fused
+// multiply-adds.  s0 = (C0, Cu, Cv, u), s1 = (k.x, k.y, k.z, 0).
+__device__ __forceinline__ void ig_stage(const float4& m, const float4& co, float ccx, float ccy, float4& s0,
+                                         float4& s1) {
+  const float3 k = scaled_conic(co);
+  const float ex = m.x - ccx, ey = m.y - ccy;
+  const float c0 = fmaf(k.z * ey, ey, fmaf(k.y * ex, ey, fmaf(k.x * ex, ex, __log2f(co.w))));
+  s0 = make_float4(c0, -fmaf(2.f * k.x, ex, k.y * ey), -fmaf(k.y, ex, 2.f * k.z * ey), m.w);
+  s1 = make_float4(k.x, k.y, k.z, 0.f);
+}
+
 // Composites `chunks` whole chunks of kIgBatch staged entries, starting at ring position
 // `head` (a multiple of kIgBatch, so no chunk wraps): the alphas of a chunk are independent
 // and computed together, the transmittance updates then run in list order.  A lane leaves
 // as soon as its pixel is saturated.
 template <int kIgBatch>
 __device__ __forceinline__ void composite_chunks(const float4* sm, const float4* sc, uint32_t head, uint32_t chunks,
-                                                 float pxc, const float* pyc, const gs_params& p, float* T,
-                                                 float* cu) {
-  for (uint32_t c = 0; c < chunks && live<kPix>(T); ++c) {
+                                                 const LaneOffsets& lo, const gs_params& p, float& T, float& cu) {
+  for (uint32_t c = 0; c < chunks && T != 0.f; ++c) {
     const uint32_t b0 = (head + c * kIgBatch) & (kIgRing - 1);
-    float al[kIgBatch][kPix], uu[kIgBatch];
+    float al[kIgBatch], uu[kIgBatch];
 #pragma unroll
     for (int k = 0; k < kIgBatch; ++k) {
-      const float4 mu = sm[b0 + k];
-      const float4 kk = sc[b0 + k];
-      uu[k] = mu.z;
-#pragma unroll
-      for (int q = 0; q < kPix; ++q)
-        al[k][q] = splat_alpha_lo(mu.x, mu.y, make_float3(kk.x, kk.y, kk.z), mu.w, pxc, pyc[q], p.alpha_max);
+      const float4 e0 = sm[b0 + k];
+      const float4 e1 = sc[b0 + k];
+      uu[k] = e0.w;
+      const float pw = fmaf(e1.z, lo.vv, fmaf(e1.y, lo.uv, fmaf(e1.x, lo.uu, fmaf(e0.z, lo.v, fmaf(e0.y, lo.u, e0.x)))));
+      al[k] = fminf(p.alpha_max, ex2_approx(pw));
     }
 #pragma unroll
     for (int k = 0; k < kIgBatch; ++k) {
-#pragma unroll
-      for (int q = 0; q < kPix; ++q) {
-        const float alpha = al[k][q];
-        if (alpha < p.alpha_min) continue;
-        const float w = T[q] * alpha;   // T (1 - alpha) taken as T - w: one instruction less
-        const float Tn = T[q] - w;
-        if (Tn < p.T_min) { T[q] = 0.f; continue; }
-        cu[q] += w * uu[k];
-        T[q] = Tn;
-      }
+      const float alpha = al[k];
+      if (alpha < p.alpha_min) continue;
+      const float w = T * alpha;   // T (1 - alpha) taken as T - w: one instruction less
+      const float Tn = T - w;
+      if (Tn < p.T_min) { T = 0.f; continue; }
+      cu += w * uu[k];
+      T = Tn;
     }
   }
 }
@@ -252,17 +268,19 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
     }
     WarpBlock wb;
     warp_block<kPix>(ti, wb);
-    const float pxc = (float)wb.px + 0.5f;
+    static_assert(kPix == 1, "one pixel per lane: the staged exponent and the live-pixel box assume it");
     const float ln_amin = __logf(p.alpha_min);
+    const float bx_full = wb.bx0, by_full = wb.by0;   // centre of the block's first pixel
+    const float ccx = bx_full + 3.5f, ccy = by_full + 1.5f;   // centre of the 8x4 block
+    LaneOffsets lo;
+    lo.u = (float)(lane & 7) - 3.5f;
+    lo.v = (float)(lane >> 3) - 1.5f;
+    lo.uu = lo.u * lo.u;
+    lo.uv = lo.u * lo.v;
+    lo.vv = lo.v * lo.v;
     // T = 0 marks a saturated pixel (and one outside the image): the stop rule sets it,
     // and a zero T adds nothing and stays zero, so no separate flag is kept
-    float pyc[kPix], T[kPix], cu[kPix];
-#pragma unroll
-    for (int q = 0; q < kPix; ++q) {
-      pyc[q] = (float)(wb.py + 4 * q) + 0.5f;
-      T[q] = (wb.px < ti.W && wb.py + 4 * q < ti.H) ? 1.f : 0.f;
-      cu[q] = 0.f;
-    }
+    float T = (wb.px < ti.W && wb.py < ti.H) ? 1.f : 0.f, cu = 0.f;
     const uint32_t n = ti.end - ti.beg;
     const uint32_t* rl = bins.rec + ti.beg;
     uint32_t rA = 0, rB = 0, rC = 0;
@@ -276,10 +294,8 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
     float4 cA = z4;
     if (ovA) cA = __ldg(SP + 2 * (size_t)rA + 1);
     uint32_t head = 0, tail = 0;   // ring entries [head, tail) are staged and not yet composited
-    static_assert(kPix == 1, "the live-pixel box below assumes one pixel per lane");
-    const float bx_full = wb.bx0, by_full = wb.by0;   // centre of the block's first pixel
     for (uint32_t g = 0; g < n; g += 32) {
-      const uint32_t lm = __ballot_sync(0xffffffffu, live<kPix>(T));
+      const uint32_t lm = __ballot_sync(0xffffffffu, T != 0.f);
       if (!lm) break;
       // the culls below test the bounding box of the block's live pixels (lane l holds pixel
       // (l mod 8, l div 8)): an entry that reaches only saturated pixels adds nothing
@@ -306,14 +322,12 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
         // are composited at once and a partial chunk waits for the next group's entries
         if (ovA) {
           const uint32_t s = (tail + __popc(m & lt)) & (kIgRing - 1);
-          const float3 k2 = scaled_conic(cA);
-          sm[s] = make_float4(mA.x, mA.y, mA.w, __log2f(cA.w));
-          sc[s] = make_float4(k2.x, k2.y, k2.z, 0.f);
+          ig_stage(mA, cA, ccx, ccy, sm[s], sc[s]);
         }
         tail += __popc(m);
         __syncwarp();
         const uint32_t chunks = (tail - head) / kIgBatch;
-        composite_chunks<kIgBatch>(sm, sc, head, chunks, pxc, pyc, p, T, cu);
+        composite_chunks<kIgBatch>(sm, sc, head, chunks, lo, p, T, cu);
         head += chunks * kIgBatch;
         __syncwarp();
       }
@@ -321,20 +335,18 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
       rB = rC; mB = mC;
       rC = rD;
     }
-    // the last partial chunk, padded with entries of log2 o = -inf (alpha = 0: adds nothing)
-    if (tail != head && __any_sync(0xffffffffu, live<kPix>(T))) {
+    // the last partial chunk, padded with entries of C0 = -inf (alpha = 0: adds nothing)
+    if (tail != head && __any_sync(0xffffffffu, T != 0.f)) {
       const uint32_t b0 = head & (kIgRing - 1);
       if ((uint32_t)lane >= tail - head && (uint32_t)lane < kIgBatch) {
-        sm[b0 + lane] = make_float4(0.f, 0.f, 0.f, -INFINITY);
+        sm[b0 + lane] = make_float4(-INFINITY, 0.f, 0.f, 0.f);
         sc[b0 + lane] = z4;
       }
       __syncwarp();
-      composite_chunks<kIgBatch>(sm, sc, head, 1u, pxc, pyc, p, T, cu);
+      composite_chunks<kIgBatch>(sm, sc, head, 1u, lo, p, T, cu);
       __syncwarp();
     }
-    float su = 0.f;
-#pragma unroll
-    for (int q = 0; q < kPix; ++q) su += cu[q];
+    float su = cu;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) su += __shfl_down_sync(0xffffffffu, su, d);
     if (lane == 0) item_sum[slot] = su;

@@ -49,17 +49,6 @@ __device__ __forceinline__ float splat_alpha2(float mx, float my, const float3& 
   return fminf(alpha_max, __fmul_rn(o, G));
 }
 
-// The same alpha with the opacity moved into the exponent, o exp(-q/2) = 2^(pw + log2 o)
-// (lo = log2 o, taken once per staged entry): one multiply less per evaluation.
-__device__ __forceinline__ float splat_alpha_lo(float mx, float my, const float3& k, float lo, float pxc, float pyc,
-                                                float alpha_max) {
-  const float dx = __fsub_rn(mx, pxc);
-  const float dy = __fsub_rn(my, pyc);
-  const float t = __fmaf_rn(k.x, dx, __fmul_rn(k.y, dy));
-  const float pw = __fmaf_rn(t, dx, __fmaf_rn(__fmul_rn(k.z, dy), dy, lo));
-  return fminf(alpha_max, ex2_approx(pw));
-}
-
 __device__ __forceinline__ float splat_alpha2(float mx, float my, const float3& k, float o, float pxc, float pyc,
                                               float alpha_max) {
   float dx, dy, G;
