@@ -317,6 +317,11 @@ __global__ void __launch_bounds__(kBinWarps * 32, 5) k_bin_place(const gs_proj p
                                                                  gs_bins out) {
   __shared__ uint32_t s_run[kBinWarps][kPlaceWin];
   __shared__ uint4 s_grp[kBinWarps][32];
+  // ceil(2^32 / w) for every clipped width w <= kWinCols (a table: an integer division by a
+  // variable is a long instruction sequence)
+  __shared__ uint32_t s_magic[kWinCols + 1];
+  for (int i = threadIdx.x; i <= kWinCols; i += blockDim.x) s_magic[i] = i > 1 ? 0xFFFFFFFFu / (uint32_t)i + 1u : 0u;
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   const uint32_t le = (2u << lane) - 1u;   // lanes 0 .. lane (all 32 for lane 31)
@@ -379,7 +384,7 @@ __global__ void __launch_bounds__(kBinWarps * 32, 5) k_bin_place(const gs_proj p
         __syncwarp();   // the previous group's rounds are done with grp
         if (cnt > 0u) {
           // floor(j / w) = umulhi(j, ceil(2^32 / w)) exactly for j w < 2^32 (here j < 2^9, w <= 2^8)
-          const uint32_t magic = w > 1u ? 0xFFFFFFFFu / w + 1u : 0u;
+          const uint32_t magic = s_magic[w];
           grp[__popc(nz & lt)] = make_uint4(x0 | (y0 << 8) | (w << 17), excl, rec_g, magic);
         }
         __syncwarp();
