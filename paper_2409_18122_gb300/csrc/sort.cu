@@ -4,7 +4,7 @@
 // Each 8-bit pass is reduce-then-scan: (1) every partition block counts its
 // digits, (2) one block turns the per-partition counts into global digit
 // offsets, (3) every partition block walks its tiles in order, ranks each key
-// stably inside the tile with warp-level match, stages the tile in shared
+// stably inside the tile with warp ballots, stages the tile in shared
 // memory in digit order and writes it out at the running digit offsets.  No
 // block ever waits on another, the result is deterministic, and the launch
 // shape depends only on the host-side capacity.

@@ -18,45 +18,39 @@ def test_multiply_high_division_is_exact_for_the_placement_window():
         assert (r < w).all()
 
 
-def _warp_sum10(v):
-    """The backward kernel's reduce-scatter of ten values over 32 lanes: four halving
-    exchanges (xor 16, 8, 4, 2) each keeping one half of the values and adding the partner's
-    copy of it, then a final exchange with xor 1."""
-    lanes = np.arange(32)
-    cur = v.copy()
-    for d, keep in ((16, 5), (8, 3), (4, 2), (2, 1)):
-        n = cur.shape[1]
-        pad = 2 * keep - n
-        if pad > 0:
-            cur = np.concatenate([cur, np.zeros((32, pad))], axis=1)
-        hi = (lanes & d) != 0
-        lo_part, hi_part = cur[:, :keep], cur[:, keep:2 * keep]
-        mine = np.where(hi[:, None], hi_part, lo_part)
-        give = np.where(hi[:, None], lo_part, hi_part)          # what this lane sends
-        cur = mine + give[lanes ^ d]
-    y = cur[:, 0]
-    return y + y[lanes ^ 1]
+RED_BATCH, RED_TERMS, RED_PITCH = 3, 10, 36   # the backward kernel's shared-memory reduction
 
 
-def test_reduce_scatter_lane_layout():
-    """After the 12 shuffles, lanes 2m and 2m + 1 hold the warp sum of value j = 5 b4 + s,
-    s = 3 b3 + 2 b2 + b1 (b_k the lane bits), valid when s <= 2 (b3 = 0) or s <= 4
-    (b3 = 1); the kernel issues its atomic for term j from exactly those even lanes, so every
-    term is added once."""
+def test_backward_row_reduction_layout():
+    """The backward kernel stores lane l's value of term j of batched entry e at
+    row (10 e + j), column l, rows RED_PITCH floats apart; lane r then sums row r with eight
+    16-byte loads and adds it to slot j' = j (j < 7) or j + 1 of the record's three
+    gradient float4s.  Every (entry, term) is summed over all 32 lanes exactly once, the rows
+    fit one pass of the warp, the slots skip the two padding floats (7 and 11), every row
+    starts 16-byte aligned, and the eight 16-byte reads of each quarter-warp fall on
+    different bank groups."""
     rng = np.random.default_rng(0)
-    for _ in range(50):
-        v = rng.normal(size=(32, 10))
-        tot = _warp_sum10(v)
-        ref = v.sum(axis=0)
-        seen = []
-        for L in range(32):
-            b4, b3, b2, b1 = (L >> 4) & 1, (L >> 3) & 1, (L >> 2) & 1, (L >> 1) & 1
-            s = 3 * b3 + 2 * b2 + b1
-            if (L & 1) == 0 and s <= (4 if b3 else 2):
-                j = 5 * b4 + s
-                assert abs(tot[L] - ref[j]) < 1e-9, (L, j)
-                seen.append(j)
-        assert sorted(seen) == list(range(10))
+    v = rng.normal(size=(RED_BATCH, RED_TERMS, 32))           # [entry][term][lane]
+    red = np.zeros(RED_BATCH * RED_TERMS * RED_PITCH)
+    for e in range(RED_BATCH):
+        for jt in range(RED_TERMS):
+            for lane in range(32):
+                red[(e * RED_TERMS + jt) * RED_PITCH + lane] = v[e, jt, lane]
+    rows = RED_BATCH * RED_TERMS
+    assert rows <= 32
+    slots = np.zeros((RED_BATCH, 12))
+    for r in range(rows):                                     # lane r sums row r
+        row = red[r * RED_PITCH: r * RED_PITCH + 32].reshape(8, 4).sum(axis=0)
+        e, jt = divmod(r, RED_TERMS)
+        slots[e, jt if jt < 7 else jt + 1] += row.sum()
+    ref = v.sum(axis=2)
+    np.testing.assert_allclose(slots[:, [0, 1, 2, 3, 4, 5, 6, 8, 9, 10]], ref, atol=1e-12)
+    assert (slots[:, [7, 11]] == 0).all()
+    assert (RED_PITCH * 4) % 16 == 0
+    for k in range(8):                                        # 16-byte read k of every lane
+        for q in range(4):                                    # quarter-warps
+            groups = {((r * RED_PITCH + 4 * k) % 32) // 4 for r in range(8 * q, 8 * q + 8)}
+            assert len(groups) == 8
 
 
 def _conics(rng, n):
@@ -111,3 +105,67 @@ def test_block_cull_never_drops_a_contributing_entry():
     reaches = (o[:, None] * np.exp(-0.5 * q) >= alpha_min).any(axis=1)
     assert not (reaches & ~keep).any()
     assert reaches.sum() > 100 and (~keep).sum() > 1000      # both cases exercised
+
+
+def test_information_gain_exponent_in_lane_offsets():
+    """The information-gain kernel stages an entry as C0 = k.x ex^2 + k.y ex ey + k.z ey^2 +
+    log2 o, Cu = -(2 k.x ex + k.y ey), Cv = -(k.y ex + 2 k.z ey), with (ex, ey) the mean
+    relative to the 8x4 block's centre; at lane offset (u, v) = (l mod 8 - 3.5, l div 8 - 1.5)
+    the exponent C0 + Cu u + Cv v + k.x u^2 + k.y u v + k.z v^2 equals the quadratic form
+    k.x dx^2 + k.y dx dy + k.z dy^2 + log2 o at (dx, dy) = mean - pixel centre."""
+    rng = np.random.default_rng(3)
+    a, b, c = _conics(rng, 500)
+    log2e = 1.4426950408889634
+    kx, ky, kz = -0.5 * log2e * a, -log2e * b, -0.5 * log2e * c
+    lo = np.log2(rng.uniform(0.01, 1.0, 500))
+    bx0, by0 = rng.uniform(0, 300, 500), rng.uniform(0, 200, 500)     # centre of the first pixel
+    mx, my = bx0 + rng.uniform(-20, 27, 500), by0 + rng.uniform(-20, 23, 500)
+    ccx, ccy = bx0 + 3.5, by0 + 1.5
+    ex, ey = mx - ccx, my - ccy
+    c0 = kx * ex * ex + ky * ex * ey + kz * ey * ey + lo
+    cu, cv = -(2 * kx * ex + ky * ey), -(ky * ex + 2 * kz * ey)
+    for lane in range(32):
+        u, v = (lane & 7) - 3.5, (lane >> 3) - 1.5
+        pw = c0 + cu * u + cv * v + kx * u * u + ky * u * v + kz * v * v
+        dx, dy = mx - (bx0 + (lane & 7)), my - (by0 + (lane >> 3))
+        ref = kx * dx * dx + ky * dx * dy + kz * dy * dy + lo
+        np.testing.assert_allclose(pw, ref, rtol=1e-9, atol=1e-9)
+
+
+def test_live_pixel_box_of_a_lane_mask():
+    """The information-gain kernel bounds the block's live pixels (lane l at column l mod 8,
+    row l div 8) by OR-ing the mask's four bytes for the columns and testing each byte for the
+    rows; first and last set bits give the box, which holds every live pixel and is the
+    smallest such box."""
+    rng = np.random.default_rng(4)
+    masks = list(rng.integers(1, 1 << 32, 3000, dtype=np.uint64)) + [1 << k for k in range(32)]
+    for m in masks:
+        m = int(m)
+        cols = (m | (m >> 8) | (m >> 16) | (m >> 24)) & 0xFF
+        rows = sum(1 << r for r in range(4) if (m >> (8 * r)) & 0xFF)
+        x0, x1 = (cols & -cols).bit_length() - 1, cols.bit_length() - 1
+        y0, y1 = (rows & -rows).bit_length() - 1, rows.bit_length() - 1
+        live = [(l & 7, l >> 3) for l in range(32) if (m >> l) & 1]
+        assert x0 == min(p[0] for p in live) and x1 == max(p[0] for p in live)
+        assert y0 == min(p[1] for p in live) and y1 == max(p[1] for p in live)
+
+
+def _order_bucket(n):
+    """The binning's item-order bucket of a list of n pairs (0: the longest lists)."""
+    key = 0
+    if n:
+        lg = n.bit_length() - 1
+        two = (n >> (lg - 2)) & 3 if lg >= 2 else (n << (2 - lg)) & 3
+        key = min(4 * lg + two, 63)
+    return 63 - key
+
+
+def test_item_order_buckets_follow_list_length():
+    """Buckets never put a longer list after a shorter one, split every doubling of the
+    length in four (so lists in one bucket differ by less than 25% below 2^16), and the
+    lengths from 2^16 on share bucket 0."""
+    b = np.array([_order_bucket(n) for n in range(1 << 17)])
+    assert (np.diff(b) <= 0).all()
+    assert b[0] == b[1] == 63 and b[-1] == 0 and b[1 << 16] == 0
+    for lg in range(2, 16):
+        assert len(set(b[1 << lg: 1 << (lg + 1)])) == 4
