@@ -741,15 +741,18 @@ def test_info_gain_uniform_uncertainty_is_mean_coverage():
 # batch on a GB300 (80x60, 160x120, 320x240 classes); set explicitly so that the test checks the
 # configuration that is timed
 CONFIG3_TILES = {(80, 60): (8, 8), (160, 120): (16, 8), (320, 240): (32, 16)}
+# the tile sets the autotuner has returned for the benchmark batch
+CONFIG3_TILE_SETS = [CONFIG3_TILES, {(80, 60): (8, 8), (160, 120): (16, 16), (320, 240): (32, 16)}]
 
 
-def test_info_gain_full_size_config3_autotuned_tiles():
+@pytest.mark.parametrize("tiles", CONFIG3_TILE_SETS, ids=["16x8", "16x16"])
+def test_info_gain_full_size_config3_autotuned_tiles(tiles):
     """1M Gaussians, all 256 candidates in one batch at the autotuned tiles; two views of each
     resolution class against the oracle (information gain over all pixels), and the number of
     contributing (pixel, Gaussian) evaluations per pixel of the forward kernel, at the same tiles,
     against the oracle's count (the work unit of the compositing roofline)."""
     sc = scenes.config3()
-    cams = gs.with_tiles(sc.cams, CONFIG3_TILES)
+    cams = gs.with_tiles(sc.cams, tiles)
     gm = gs.GaussianMapTensors.from_numpy(sc.gmap)
     ig_op = gs.InfoGain(gm.n, cams)
     ig = ig_op(gm)

@@ -230,6 +230,11 @@ def test_autotuner_keeps_the_default_within_the_margin():
     assert gs._pick({"d": 1.0, "a": 1.0 / (1 + m / 2)}, "d") == "d"
     assert gs._pick({"d": 1.0, "a": 1.0 / (1 + 2 * m)}, "d") == "a"
     assert gs._pick({"a": 2.0, "b": 1.0}, "missing") == "b"
+    # the tile tuner times whole batches, where one class's change is a part: a smaller margin
+    t = gs.TILE_TUNE_MARGIN
+    assert t < m
+    assert gs._pick({"d": 1.0, "a": 1.0 / (1 + 2 * t)}, "d", t) == "a"
+    assert gs._pick({"d": 1.0, "a": 1.0 / (1 + t / 2)}, "d", t) == "d"
 
 
 def test_tile_and_camera_checks_mirror_the_library():
