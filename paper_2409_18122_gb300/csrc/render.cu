@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
                                                              gs_params p, const uint32_t* __restrict__ order,
                                                              float* __restrict__ item_sum, int64_t item_cap,
                                                              uint32_t* __restrict__ work) {
-  // staged entries of each warp, a ring of kIgRing: (mu_x, mu_y, u, log2 o), scaled conic
+  // staged entries of each warp, a ring of kIgRing: (C0, Cu, Cv, u), (k.x, k.y, k.z, 0) (ig_stage)
   __shared__ float4 s_stage[kIgWarps][2][kIgRing];
   static_assert(kIgRing % kIgBatch == 0 && kIgRing >= 32 + kIgBatch, "ring holds a group plus a partial chunk");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
