@@ -265,7 +265,9 @@ typedef struct {
  * the Gaussians of its tile in depth order: alpha = min(alpha_max, o exp(-q/2)),
  * skip if alpha < alpha_min, stop (without adding) if T (1 - alpha) < T_min,
  * else w = alpha T, accumulate w c (RGB), w t_z (depth), w u (uncertainty) and
- * T <- T (1 - alpha).  Background is zero.
+ * T <- T (1 - alpha).  Background is zero.  The pixel blocks are taken in
+ * bins->item_order when gs_bin_sort wrote it (longest tile list first), else tile by tile;
+ * the outputs are the same either way.
  * Errors: GS_ERR_NULL, GS_ERR_ALIGN, GS_ERR_ARG, GS_ERR_CUDA. */
 gs_status gs_render_fwd(const gs_map* map, const gs_proj* proj, const gs_bins* bins, const gs_camera* cams,
                         int32_t n_views, const gs_params* prm, gs_image* out, void* stream);
