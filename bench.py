@@ -1057,7 +1057,9 @@ def run_ours(args):
                        "ig_batch": istep.params.ig_batch,
                        "map_tile": "%dx%d" % (mstep.render_params.tile_w, mstep.render_params.tile_h),
                        "map_fwd_batch": mstep.render_params.fwd_batch},
-            "autotune": {"ig_batch_ms": {str(k): v for k, v in istep.batch_timings.items()},
+            "autotune": {"ig_tile_ms": {"%dx%d" % res: {"%dx%d" % t: ms for t, ms in tt.items()}
+                                        for res, tt in getattr(istep, "tile_timings", {}).items()},
+                         "ig_batch_ms": {str(k): v for k, v in istep.batch_timings.items()},
                          "map_ms": {"%dx%d/%d" % k: v for k, v in mstep.tune_timings.items()}},
             "fwd_bwd": {"value": fwd_bwd, "unit": "iters/s", "ms": t_map_all / args.steps * 1e3},
             "ig_ms": t_ig_all / args.steps * 1e3,

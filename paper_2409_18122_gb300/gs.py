@@ -763,10 +763,12 @@ TILE_CANDIDATES = ((16, 16), (16, 8), (8, 8), (32, 8), (32, 16), (32, 32))
 
 
 def autotune_tiles(gmap: GaussianMapTensors, cams: Sequence, params: RenderParams = RenderParams(),
-                   candidates=TILE_CANDIDATES, reps: int = 5, pair_capacity: Optional[int] = None):
+                   candidates=TILE_CANDIDATES, reps: int = 5, pair_capacity: Optional[int] = None,
+                   sweeps: int = 2):
     """Pick a screen tile per resolution class by timing the batched information-gain pass.
 
-    One sweep of coordinate descent over the distinct (width, height) classes of `cams`:
+    `sweeps` sweeps of coordinate descent over the distinct (width, height) classes of `cams`
+    (the second revisits the classes tuned first, with the later classes' new tiles):
     every class starts at the default tile of `params`; in turn, each class's candidates are
     timed on the whole batch with the other classes' current tiles (CUDA events, median of
     `reps` after one warm-up, L2 flushed before each), and the fastest is kept unless the
@@ -775,7 +777,7 @@ def autotune_tiles(gmap: GaussianMapTensors, cams: Sequence, params: RenderParam
     alone, charges a tile what it costs in the pass that uses it (a class timed alone once
     preferred 8x8 tiles at 160x120 that made the full pass 4% slower).  Returns
     ({(W, H): (tile_w, tile_h)}, {(W, H): {tile: ms}}).  Use `with_tiles` to apply the choice
-    to a camera list.
+    to a camera list (the timings are those of the last sweep).
     """
     classes = []
     for c in cams:
@@ -795,14 +797,16 @@ def autotune_tiles(gmap: GaussianMapTensors, cams: Sequence, params: RenderParam
         del ig
         return ms
 
-    for res in classes:
-        for tw, th in candidates:
-            if not valid_tile(tw, th):
-                continue
-            ch = dict(choice)
-            ch[res] = (tw, th)
-            timings[res][(tw, th)] = batch_ms(ch)
-        choice[res] = _pick(timings[res], choice[res], TILE_TUNE_MARGIN)
+    for _ in range(max(int(sweeps), 1)):
+        for res in classes:
+            timings[res] = {}
+            for tw, th in candidates:
+                if not valid_tile(tw, th):
+                    continue
+                ch = dict(choice)
+                ch[res] = (tw, th)
+                timings[res][(tw, th)] = batch_ms(ch)
+            choice[res] = _pick(timings[res], choice[res], TILE_TUNE_MARGIN)
     return choice, timings
 
 
