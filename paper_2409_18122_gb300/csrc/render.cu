@@ -40,7 +40,8 @@ template <int kFwdBatch>
 __global__ void __launch_bounds__(kFwdWarps * 32, 12) k_render_fwd(gs_map map, gs_proj proj, gs_bins bins,
                                                                 const gs_camera* __restrict__ cams, int n_views,
                                                                 gs_params p, gs_image img, uint32_t n_items) {
-  __shared__ float4 s_stage[kFwdWarps][3][32];   // (mu_x, mu_y, u, -), (a, b, c, o), (r, g, b, depth)
+  // staged entries: (c0, cu, cv, u), (k.x, k.y, k.z, lane), (r, g, b, depth) (stage_exponent)
+  __shared__ float4 s_stage[kFwdWarps][3][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t item = blockIdx.x * kFwdWarps + warp;
@@ -54,15 +55,14 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 12) k_render_fwd(gs_map map, g
   float4* sm = s_stage[warp][0];
   float4* sc = s_stage[warp][1];
   float4* sk = s_stage[warp][2];
-  const float pxc = (float)wb.px + 0.5f;
   const float ln_amin = __logf(p.alpha_min);
-  float pyc[kPix];
+  const LaneOffsets lo = lane_offsets(lane);
+  const float ccx = wb.bx0 + 3.5f, ccy = wb.by0 + 1.5f;   // centre of the 8x4 block
   bool inside[kPix], done[kPix];
   float T[kPix], cr[kPix], cg[kPix], cb[kPix], cd[kPix], cu[kPix];
   int32_t last[kPix], n_contrib[kPix];
 #pragma unroll
   for (int q = 0; q < kPix; ++q) {
-    pyc[q] = (float)(wb.py + 4 * q) + 0.5f;
     inside[q] = wb.px < ti.W && wb.py + 4 * q < ti.H;
     done[q] = !inside[q];
     T[q] = 1.f;
@@ -102,20 +102,20 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 12) k_render_fwd(gs_map map, g
     ovA = ovA && ellipse_reaches(mA, cA, wb, ln_amin);
     const uint32_t m = __ballot_sync(0xffffffffu, ovA);
     if (m) {
-      // the overlapping entries, compacted in list order: (mu, u, o), (scaled conic,
-      // position in the group), colour
-      // padded to whole batches with entries of opacity -1 (alpha < 0: always skipped)
+      // the overlapping entries, compacted in list order: (c0, cu, cv, u), (k, position in
+      // the group), colour; padded to whole batches with entries of c0 = -inf (alpha = 0:
+      // always skipped)
       const int n_ov = __popc(m);
       const int n_pad = (n_ov + kFwdBatch - 1) / kFwdBatch * kFwdBatch;
       if (ovA) {
         const int s = __popc(m & lt);
-        const float3 k2 = scaled_conic(cA);
-        sm[s] = make_float4(mA.x, mA.y, mA.w, cA.w);
-        sc[s] = make_float4(k2.x, k2.y, k2.z, __int_as_float(lane));
+        const Exponent e = stage_exponent(mA.x, mA.y, cA, ccx, ccy);
+        sm[s] = make_float4(e.c0, e.cu, e.cv, mA.w);
+        sc[s] = make_float4(e.kx, e.ky, e.kz, __int_as_float(lane));
         sk[s] = kA;
       }
       if (lane >= n_ov && lane < n_pad) {   // slots [n_ov, n_pad): disjoint from the staged ones
-        sm[lane] = make_float4(0.f, 0.f, 0.f, -1.f);
+        sm[lane] = make_float4(-INFINITY, 0.f, 0.f, 0.f);
         sc[lane] = z4;
       }
       __syncwarp();
@@ -126,11 +126,11 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 12) k_render_fwd(gs_map map, g
 #pragma unroll
         for (int k = 0; k < kFwdBatch; ++k) {
           const int i = i0 + k;
-          const float4 mu = sm[i];
-          const float4 kk = sc[i];
+          const float4 e0 = sm[i];
+          const float4 e1 = sc[i];
 #pragma unroll
           for (int q = 0; q < kPix; ++q)
-            al[k][q] = splat_alpha2(mu.x, mu.y, make_float3(kk.x, kk.y, kk.z), mu.w, pxc, pyc[q], p.alpha_max);
+            al[k][q] = fminf(p.alpha_max, alpha_raw(e0.x, e0.y, e0.z, e1.x, e1.y, e1.z, lo));
         }
 #pragma unroll
         for (int k = 0; k < kFwdBatch; ++k) {
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 12) k_render_fwd(gs_map map, g
             cg[q] += w * c.y;
             cb[q] += w * c.z;
             cd[q] += w * c.w;
-            cu[q] += w * sm[i].z;
+            cu[q] += w * sm[i].w;
             T[q] = Tn;
             last[q] = (int32_t)(g + __float_as_int(sc[i].w) + 1);
             ++n_contrib[q];
@@ -181,25 +181,13 @@ __global__ void __launch_bounds__(kFwdWarps * 32, 12) k_render_fwd(gs_map map, g
   }
 }
 
-// Per-lane constants of the information-gain exponent: the lane's pixel centre relative to
-// the centre of its 8x4 block, (u, v), and u^2, u v, v^2.
-struct LaneOffsets {
-  float u, v, uu, uv, vv;
-};
-
-// Staged form of an entry for the information-gain kernel.  With (ex, ey) = mean - block
-// centre and k = the scaled conic, the exponent of alpha = 2^pw at the lane's pixel is
-//   pw = k.x (ex - u)^2 + k.y (ex - u)(ey - v) + k.z (ey - v)^2 + log2 o
-//      = C0 + Cu u + Cv v + k.x u^2 + k.y u v + k.z v^2,
-// so the staging lane computes C0, Cu, Cv once per entry and every pixel takes five fused
-// multiply-adds.  s0 = (C0, Cu, Cv, u), s1 = (k.x, k.y, k.z, 0).
+// Staged form of an entry for the information-gain kernel: s0 = (c0, cu, cv, u),
+// s1 = (k.x, k.y, k.z, 0) (stage_exponent).
 __device__ __forceinline__ void ig_stage(const float4& m, const float4& co, float ccx, float ccy, float4& s0,
                                          float4& s1) {
-  const float3 k = scaled_conic(co);
-  const float ex = m.x - ccx, ey = m.y - ccy;
-  const float c0 = fmaf(k.z * ey, ey, fmaf(k.y * ex, ey, fmaf(k.x * ex, ex, __log2f(co.w))));
-  s0 = make_float4(c0, -fmaf(2.f * k.x, ex, k.y * ey), -fmaf(k.y, ex, 2.f * k.z * ey), m.w);
-  s1 = make_float4(k.x, k.y, k.z, 0.f);
+  const Exponent e = stage_exponent(m.x, m.y, co, ccx, ccy);
+  s0 = make_float4(e.c0, e.cu, e.cv, m.w);
+  s1 = make_float4(e.kx, e.ky, e.kz, 0.f);
 }
 
 // Composites `chunks` whole chunks of kIgBatch staged entries, starting at ring position
@@ -217,8 +205,7 @@ __device__ __forceinline__ void composite_chunks(const float4* sm, const float4*
       const float4 e0 = sm[b0 + k];
       const float4 e1 = sc[b0 + k];
       uu[k] = e0.w;
-      const float pw = fmaf(e1.z, lo.vv, fmaf(e1.y, lo.uv, fmaf(e1.x, lo.uu, fmaf(e0.z, lo.v, fmaf(e0.y, lo.u, e0.x)))));
-      al[k] = fminf(p.alpha_max, ex2_approx(pw));
+      al[k] = fminf(p.alpha_max, alpha_raw(e0.x, e0.y, e0.z, e1.x, e1.y, e1.z, lo));
     }
 #pragma unroll
     for (int k = 0; k < kIgBatch; ++k) {
@@ -272,12 +259,7 @@ __global__ void __launch_bounds__(kIgWarps * 32) k_ig_items(gs_proj proj, gs_bin
     const float ln_amin = __logf(p.alpha_min);
     const float bx_full = wb.bx0, by_full = wb.by0;   // centre of the block's first pixel
     const float ccx = bx_full + 3.5f, ccy = by_full + 1.5f;   // centre of the 8x4 block
-    LaneOffsets lo;
-    lo.u = (float)(lane & 7) - 3.5f;
-    lo.v = (float)(lane >> 3) - 1.5f;
-    lo.uu = lo.u * lo.u;
-    lo.uv = lo.u * lo.v;
-    lo.vv = lo.v * lo.v;
+    const LaneOffsets lo = lane_offsets(lane);
     // T = 0 marks a saturated pixel (and one outside the image): the stop rule sets it,
     // and a zero T adds nothing and stays zero, so no separate flag is kept
     float T = (wb.px < ti.W && wb.py < ti.H) ? 1.f : 0.f, cu = 0.f;

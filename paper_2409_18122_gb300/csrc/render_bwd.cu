@@ -30,7 +30,7 @@ constexpr int kRedBatch = 3;
 constexpr int kRedPitch = 36;   // floats per row: 16-byte aligned, conflict-free vector reads
 constexpr int kPix = 1;        // pixels per lane (8x4 blocks: finer culling beats sharing reductions)
 
-__global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_proj proj, gs_bins bins,
+__global__ void __launch_bounds__(kBwdWarps * 32, 14) k_render_bwd(gs_map map, gs_proj proj, gs_bins bins,
                                                                 const gs_camera* __restrict__ cams, int n_views,
                                                                 gs_params p, gs_image fwd, gs_image_grad grad,
                                                                 float4* __restrict__ g2d, uint32_t n_items) {
@@ -78,6 +78,8 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
   };
   const float pxc = (float)wb.px + 0.5f;
   const float ln_amin = __logf(p.alpha_min);
+  const LaneOffsets lo = lane_offsets(lane);
+  const float ccx = wb.bx0 + 3.5f, ccy = wb.by0 + 1.5f;   // centre of the 8x4 block
   const size_t P = (size_t)ti.W * ti.H;
   float pyc[kPix], T[kPix], gr[kPix], gg[kPix], gb[kPix], gd[kPix];
   float Sr[kPix], Sg[kPix], Sb[kPix], Sd[kPix];
@@ -148,10 +150,10 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
     uint32_t m = __ballot_sync(0xffffffffu, ovA);
     if (m) {
       if (ovA) {
-        const float3 k2 = scaled_conic(cA);
-        sx[lane] = make_float4(mA.x, mA.y, 0.f, 0.f);
+        const Exponent e = stage_exponent(mA.x, mA.y, cA, ccx, ccy);
+        sx[lane] = make_float4(mA.x, mA.y, e.cu, e.cv);
         sr[lane] = kA;
-        sk[lane] = make_float4(k2.x, k2.y, k2.z, cA.w);
+        sk[lane] = make_float4(e.kx, e.ky, e.kz, e.c0);
         srec[lane] = rA;
       }
       __syncwarp();
@@ -161,15 +163,20 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
         const int pos = g + b;   // position in the tile's list
         const float4 mu = sx[b];
         const float4 ks = sk[b];
-        // the alpha of the forward pass (same staged scaled conic, same operations)
-        float dx = 0.f, dy = 0.f, G = 0.f, al = 0.f;
+        // the alpha of the forward pass (same staged coefficients, same operations); ar = o G
+        float dx = 0.f, dy = 0.f, ar = 0.f, al = 0.f;
         const bool live = inside[0] && pos < last[0];
-        if (live) al = splat_alpha2(mu.x, mu.y, make_float3(ks.x, ks.y, ks.z), ks.w, pxc, pyc[0], p.alpha_max, dx, dy, G);
+        if (live) {
+          ar = alpha_raw(ks.w, mu.z, mu.w, ks.x, ks.y, ks.z, lo);
+          al = fminf(p.alpha_max, ar);
+          dx = __fsub_rn(mu.x, pxc);
+          dy = __fsub_rn(mu.y, pyc[0]);
+        }
         const bool contrib = live && !(al < p.alpha_min);
         if (!__any_sync(0xffffffffu, contrib)) continue;
-        // A lane that does not contribute runs the same arithmetic with alpha = G = dx = dy = 0:
+        // A lane that does not contribute runs the same arithmetic with alpha = ar = dx = dy = 0:
         // its T and suffix sums stay exactly unchanged (T * 1, S + 0) and every term is zero.
-        if (!contrib) al = G = dx = dy = 0.f;
+        if (!contrib) al = ar = dx = dy = 0.f;
         const float4 c = sr[b];
         const float inv = __fdividef(1.f, 1.f - al);   // 1 - alpha in [1 - alpha_max, 1]: approximate reciprocal
         const float Ti = T[0] * inv;
@@ -181,7 +188,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
         Sb[0] += w * c.z;
         Sd[0] += w * c.w;
         T[0] = Ti;
-        const bool free = __fmul_rn(ks.w, G) < p.alpha_max;   // alpha not clamped
+        const bool free = ar < p.alpha_max;   // alpha not clamped
         const float dq = free ? -0.5f * al * dalpha : 0.f;    // dL/dq
         // dL/dmu_2D = 2 (a P + b Q, b P + c Q) with P = sum dq dx, Q = sum dq dy (dx = mu_x - p_x):
         // the conic is the record's, so P and Q are summed and k_proj_adjoint applies it
@@ -191,7 +198,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_render_bwd(gs_map map, gs_pr
         v[2] = v[0] * dx;            // dL/da
         v[3] = 2.f * v[0] * dy;      // dL/db
         v[4] = v[1] * dy;            // dL/dc
-        v[5] = free ? dalpha * G : 0.f;           // dL/do
+        v[5] = free ? dalpha * ar : 0.f;          // o dL/do (k_proj_adjoint divides by o)
         v[6] = gd[0] * w;
         v[7] = gr[0] * w;
         v[8] = gg[0] * w;
@@ -259,9 +266,9 @@ __global__ void __launch_bounds__(256) k_proj_adjoint(gs_map map, gs_proj proj, 
     const uint32_t r = proj.grp_base[v * n_grp + grp] + __popc(m & lt);
     if ((int64_t)r >= nrec) continue;
     const float4 A = g2d[3 * (size_t)r], Bv = g2d[3 * (size_t)r + 1], Cv = g2d[3 * (size_t)r + 2];
-    grgb[0] += Cv.x; grgb[1] += Cv.y; grgb[2] += Cv.z;
-    go += Bv.y;
     const float4 con = reinterpret_cast<const float4*>(proj.splat)[2 * (size_t)r + 1];
+    grgb[0] += Cv.x; grgb[1] += Cv.y; grgb[2] += Cv.z;
+    go += Bv.y / con.w;   // the compositing summed o dL/do (o = con.w >= alpha_min > 0)
     // slots A.x, A.y hold P = sum dq dx, Q = sum dq dy: dL/dmu_2D = 2 (a P + b Q, b P + c Q)
     const float gmx = 2.f * (con.x * A.x + con.y * A.y), gmy = 2.f * (con.y * A.x + con.z * A.y);
     const float ga = A.z, gb = A.w, gc = Bv.x, gdep = Bv.z;

@@ -21,11 +21,8 @@ struct TileInfo {
 // alpha = min(alpha_max, o exp(-q/2)), q = a dx^2 + 2 b dx dy + c dy^2 with
 // (dx, dy) = mu_2D - pixel centre and conic (a, b, c).  exp(-q/2) is evaluated
 // as 2^p with p = -q/2 log2(e): the conic is scaled once per Gaussian (per warp
-// staging, not per pixel) to k = (-a/2, -b, -c/2) log2(e), so that
-// p = (k.x dx + k.y dy) dx + k.z dy^2 and G = 2^p is one ex2 instruction.  Written
-// with explicit round-to-nearest intrinsics so that the forward, backward and
-// information-gain kernels compute bit-identical alphas (and so take identical
-// skip and stop decisions) whatever the compiler contracts.
+// staging, not per pixel) to k = (-a/2, -b, -c/2) log2(e), and the exponent is staged as
+// a quadratic in the lane's pixel offset (stage_exponent, alpha_raw below).
 constexpr float kLog2e = 1.4426950408889634f;
 
 __device__ __forceinline__ float3 scaled_conic(const float4& co) {
@@ -38,21 +35,52 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// Also returns (dx, dy) and G = exp(-q/2).
-__device__ __forceinline__ float splat_alpha2(float mx, float my, const float3& k, float o, float pxc, float pyc,
-                                              float alpha_max, float& dx, float& dy, float& G) {
-  dx = __fsub_rn(mx, pxc);
-  dy = __fsub_rn(my, pyc);
-  const float t = __fmaf_rn(k.x, dx, __fmul_rn(k.y, dy));
-  const float pw = __fmaf_rn(t, dx, __fmul_rn(__fmul_rn(k.z, dy), dy));
-  G = ex2_approx(pw);
-  return fminf(alpha_max, __fmul_rn(o, G));
+// alpha before the alpha_max clamp, o exp(-q/2), as 2^pw with pw a quadratic in the
+// lane's offset (u, v) from the centre of its 8x4 pixel block (lane l: u = l mod 8 - 3.5,
+// v = l div 8 - 1.5).  With (ex, ey) = mean - block centre and k = scaled_conic(conic),
+//   pw = k.x (ex - u)^2 + k.y (ex - u)(ey - v) + k.z (ey - v)^2 + log2 o
+//      = c0 + cu u + cv v + k.x u^2 + k.y u v + k.z v^2,
+// so an entry's coefficients are staged once per warp and every pixel takes five fused
+// multiply-adds.  Every kernel stages and evaluates it with these functions (explicit
+// round-to-nearest operations), so the forward, backward and one-launch renders take
+// bit-identical skip and stop decisions.
+struct LaneOffsets {
+  float u, v, uu, uv, vv;   // quarter-integers and their products: exact in FP32
+};
+
+__device__ __forceinline__ LaneOffsets lane_offsets(int lane) {
+  LaneOffsets o;
+  o.u = (float)(lane & 7) - 3.5f;
+  o.v = (float)(lane >> 3) - 1.5f;
+  o.uu = o.u * o.u;
+  o.uv = o.u * o.v;
+  o.vv = o.v * o.v;
+  return o;
 }
 
-__device__ __forceinline__ float splat_alpha2(float mx, float my, const float3& k, float o, float pxc, float pyc,
-                                              float alpha_max) {
-  float dx, dy, G;
-  return splat_alpha2(mx, my, k, o, pxc, pyc, alpha_max, dx, dy, G);
+struct Exponent {
+  float c0, cu, cv, kx, ky, kz;
+};
+
+// Coefficients of an entry with mean (mx, my) and conic co = (a, b, c, o) for the block
+// whose centre is (ccx, ccy).
+__device__ __forceinline__ Exponent stage_exponent(float mx, float my, const float4& co, float ccx, float ccy) {
+  const float3 k = scaled_conic(co);
+  const float ex = __fsub_rn(mx, ccx), ey = __fsub_rn(my, ccy);
+  Exponent e;
+  e.c0 = __fmaf_rn(__fmul_rn(k.z, ey), ey, __fmaf_rn(__fmul_rn(k.y, ex), ey, __fmaf_rn(__fmul_rn(k.x, ex), ex, __log2f(co.w))));
+  e.cu = -__fmaf_rn(__fmul_rn(2.f, k.x), ex, __fmul_rn(k.y, ey));
+  e.cv = -__fmaf_rn(k.y, ex, __fmul_rn(__fmul_rn(2.f, k.z), ey));
+  e.kx = k.x;
+  e.ky = k.y;
+  e.kz = k.z;
+  return e;
+}
+
+// o exp(-q/2) at the lane's pixel (before the alpha_max clamp).
+__device__ __forceinline__ float alpha_raw(float c0, float cu, float cv, float kx, float ky, float kz,
+                                           const LaneOffsets& lo) {
+  return ex2_approx(__fmaf_rn(kz, lo.vv, __fmaf_rn(ky, lo.uv, __fmaf_rn(kx, lo.uu, __fmaf_rn(cv, lo.v, __fmaf_rn(cu, lo.u, c0))))));
 }
 
 // Work item of the compositing kernels: one warp renders one 8 x (4 KP) pixel

@@ -227,7 +227,8 @@ __global__ void __launch_bounds__(kThreads) k_render_small(gs_map map, const gs_
       wb.bx1 = wb.bx0 + 7.f;
       wb.by0 = (float)y0 + 0.5f;
       wb.by1 = wb.by0 + 3.f;
-      const float pxc = (float)wb.px + 0.5f, pyc = (float)wb.py + 0.5f;
+      const LaneOffsets lo = lane_offsets(lane);
+      const float ccx = wb.bx0 + 3.5f, ccy = wb.by0 + 1.5f;   // centre of the 8x4 block
       const bool inside = wb.px < cam.W && wb.py < cam.H;
       bool done = !inside;
       float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, cdp = 0.f, cu = 0.f;
@@ -236,19 +237,24 @@ __global__ void __launch_bounds__(kThreads) k_render_small(gs_map map, const gs_
         if (!__any_sync(0xffffffffu, !done)) break;
         const int j = g + lane;
         bool ov = false;
+        Exponent ex{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // this lane's entry, staged as the tiled forward does
         if (j < n_all) {
           const int e = s.idx[0][j];
           ov = box_overlaps(s.m[e], wb) && ellipse_reaches(s.m[e], s.co[e], wb, ln_amin);
+          if (ov) ex = stage_exponent(s.m[e].x, s.m[e].y, s.co[e], ccx, ccy);
         }
         uint32_t mk = __ballot_sync(0xffffffffu, ov);
         while (mk) {
           const int k = __ffs(mk) - 1;
           mk &= mk - 1u;
+          // the entry's coefficients from the lane that staged it (every lane takes part)
+          const float c0 = __shfl_sync(0xffffffffu, ex.c0, k), cu_ = __shfl_sync(0xffffffffu, ex.cu, k);
+          const float cv = __shfl_sync(0xffffffffu, ex.cv, k), kx = __shfl_sync(0xffffffffu, ex.kx, k);
+          const float ky = __shfl_sync(0xffffffffu, ex.ky, k), kz = __shfl_sync(0xffffffffu, ex.kz, k);
           if (done) continue;
           const int e = s.idx[0][g + k];
           const float4 mu = s.m[e];
-          const float3 k2 = scaled_conic(s.co[e]);
-          const float alpha = splat_alpha2(mu.x, mu.y, k2, s.co[e].w, pxc, pyc, amax);
+          const float alpha = fminf(amax, alpha_raw(c0, cu_, cv, kx, ky, kz, lo));
           if (alpha < p.alpha_min) continue;
           const float w = alpha * T;
           const float Tn = T - w;   // T (1 - alpha)

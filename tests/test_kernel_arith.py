@@ -108,7 +108,7 @@ def test_block_cull_never_drops_a_contributing_entry():
 
 
 def test_information_gain_exponent_in_lane_offsets():
-    """The information-gain kernel stages an entry as C0 = k.x ex^2 + k.y ex ey + k.z ey^2 +
+    """The compositing kernels stage an entry as C0 = k.x ex^2 + k.y ex ey + k.z ey^2 +
     log2 o, Cu = -(2 k.x ex + k.y ey), Cv = -(k.y ex + 2 k.z ey), with (ex, ey) the mean
     relative to the 8x4 block's centre; at lane offset (u, v) = (l mod 8 - 3.5, l div 8 - 1.5)
     the exponent C0 + Cu u + Cv v + k.x u^2 + k.y u v + k.z v^2 equals the quadratic form
